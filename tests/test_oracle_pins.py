@@ -1,0 +1,277 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the mathematics.
+
+Each test ties one piece of the oracle to something other than its own code: a hand-derived
+closed-form case, the manufactured solution, the skew identity of the solenoidal convection
+form, the Euler identity of the quadratic term, a finite-difference Jacobian (exact for a
+quadratic residual), the C = 0 reduction to one linear solve, quadratic Newton convergence,
+nested truncation, the n = 1 closed form, and elimination against LAPACK.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_set(n=8, q_a=3, q_c=3, q_f=2, q_b=0, m=0, c_dtype="f64", manufactured=False,
+              wid=90, re_range=(100.0, 1000.0)):
+    wl = synth.Workload("test", wid, n_max=n, q_a=q_a, q_c=q_c, q_f=q_f, q_b=q_b, m=m,
+                        c_dtype=c_dtype, manufactured=manufactured, re_range=re_range,
+                        mu0=(10.0, 200.0) if manufactured else None)
+    return synth.make_operators(wl)
+
+
+def test_theta_closed_forms(oracle_lib):
+    ops = small_set(n=3, q_a=4, q_c=4, q_f=4)
+    o = oracle_lib.Oracle.from_set(ops)
+    # alpha = 0: sin terms vanish, cos terms are 1; theta^a carries 1/Re (Sec. 2.4 split)
+    t = o.theta(0.0, 250.0)
+    np.testing.assert_allclose(t[:4], [1 / 250.0, 0.0, 1 / 250.0, 0.0], atol=1e-18)
+    np.testing.assert_allclose(t[4:8], [1.0, 0.0, 1.0, 0.0], atol=1e-15)
+    # alpha = 90 deg: trig = (1, sin 90, cos 180, sin 270) = (1, 1, -1, -1)
+    t = o.theta(90.0, 1.0)
+    np.testing.assert_allclose(t[4:8], [1.0, 1.0, -1.0, -1.0], atol=1e-15)
+    np.testing.assert_allclose(t[8:12], [1.0, 1.0, -1.0, -1.0], atol=1e-15)
+
+
+def _golden_set():
+    with open(os.path.join(GOLDEN, "n2_closed_form.json")) as fh:
+        g = json.load(fh)
+    n, m = g["n"], g["m"]
+    C = np.zeros((1, n, n, n))
+    for q, j, l, k, v in g["C_nonzero"]:
+        C[q, j, l, k] = v
+    Cs = np.zeros((1, n, n, m))
+    for q, j, l, k, v in g["Cs_nonzero"]:
+        Cs[q, j, l, k] = v
+    return g, C, Cs
+
+
+def test_golden_n2_closed_form(oracle_lib):
+    g, C, Cs = _golden_set()
+    o = oracle_lib.Oracle(np.array(g["A"]), C, np.array(g["f"]), np.array(g["B"]),
+                          np.array(g["As"]), Cs, np.array(g["fs"]))
+    u, p, info = o.solve(np.array([g["mu"]]), tol_upd=1e-14, tol_res=1e-14)
+    assert info["status"][0] == oracle_lib.Q_OK
+    np.testing.assert_allclose(u[0], g["u"], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(p[0], g["p"], rtol=0, atol=1e-13)
+
+
+def test_manufactured_solution(oracle_lib):
+    """P1: with f_0 built from u* at mu0, Newton from u = 0 returns u* (and p*)."""
+    ops = small_set(n=12, q_a=4, q_c=4, q_f=2, q_b=3, m=7, manufactured=True, wid=91,
+                    re_range=(200.0, 200.0))
+    oracle_lib.manufacture(ops, (10.0, 200.0))
+    # the manufactured forcing is also checked by an independent restatement here
+    o = oracle_lib.Oracle.from_set(ops)
+    th = o.theta(10.0, 200.0)
+    ta, tc, tf = th[:4], th[4:8], th[8:10]
+    us = ops.u_star
+    r = (np.einsum("q,qkj,j->k", ta, ops.A, us)
+         + np.einsum("q,qjlk,j,l->k", tc, ops.C, us, us)
+         - np.einsum("q,qk->k", tf, ops.f))
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(ops.f[0])
+    u, p, info = o.solve(np.array([[10.0, 200.0]]), tol_upd=1e-10, tol_res=1e-12)
+    assert info["status"][0] == oracle_lib.Q_OK
+    assert np.linalg.norm(u[0] - us) <= 1e-12 * np.linalg.norm(us)
+    assert np.linalg.norm(p[0] - ops.p_star) <= 1e-11 * np.linalg.norm(ops.p_star)
+
+
+def test_manufactured_single_n20(oracle_lib):
+    """P1 on the plain single-query workload (n = 20, Q = 4, mu0 = (10 deg, Re 200))."""
+    ops = synth.make_operators(synth.WORKLOADS["single_n20"])
+    oracle_lib.manufacture(ops, (10.0, 200.0))
+    o = oracle_lib.Oracle.from_set(ops)
+    u, _, info = o.solve(np.array([[10.0, 200.0]]), tol_upd=1e-10, tol_res=1e-12)
+    assert info["status"][0] == oracle_lib.Q_OK
+    assert np.linalg.norm(u[0] - ops.u_star) <= 1e-12 * np.linalg.norm(ops.u_star)
+    assert info["iters"][0] >= 3
+
+
+@pytest.mark.parametrize("c_dtype", ["f64", "f32"])
+def test_skew_and_energy_identity(oracle_lib, c_dtype):
+    """P2: u^T Cmu(u, u) = 0 for C skew in its last two indices; so u^T R = u^T A u - u^T f."""
+    ops = small_set(n=10, c_dtype=c_dtype)
+    o = oracle_lib.Oracle.from_set(ops)
+    g = np.random.default_rng(5)
+    for _ in range(5):
+        th = o.theta(g.uniform(0, 35), 10 ** g.uniform(2, 3))
+        u = g.standard_normal(10)
+        cv = o.convection(10, th, u)
+        scale = np.sum(np.abs(ops.C)) * np.max(np.abs(u)) ** 3
+        assert abs(u @ cv) <= 1e-14 * scale
+        A, f = o.assemble(10, th)
+        R = o.residual(10, th, u)
+        assert abs(u @ R - (u @ A @ u - u @ f)) <= 1e-13 * (abs(u @ A @ u) + abs(u @ f) + scale)
+
+
+def test_skew_identity_detects_wrong_pair(oracle_lib):
+    """The skew identity fails when the tensor's test index is not the last one."""
+    ops = small_set(n=10)
+    C_wrong = np.ascontiguousarray(ops.C.transpose(0, 2, 3, 1))  # test index moved to front
+    o = oracle_lib.Oracle(ops.A, C_wrong, ops.f)
+    th = o.theta(20.0, 300.0)
+    u = np.random.default_rng(3).standard_normal(10)
+    cv = o.convection(10, th, u)
+    assert abs(u @ cv) > 1e-6 * np.linalg.norm(cv) * np.linalg.norm(u)
+
+
+@pytest.mark.parametrize("skew", [True, False])
+def test_euler_identity(oracle_lib, skew):
+    """P3: the convection Jacobian applied to u is twice the convection term (any C)."""
+    n = 9
+    ops = small_set(n=n)
+    C = ops.C if skew else np.random.default_rng(11).standard_normal(ops.C.shape)
+    o = oracle_lib.Oracle(ops.A, C, ops.f)
+    th = o.theta(17.0, 420.0)
+    u = np.random.default_rng(4).standard_normal(n)
+    A, _ = o.assemble(n, th)
+    Jc = o.jacobian(n, th, u) - A
+    cv = o.convection(n, th, u)
+    np.testing.assert_allclose(Jc @ u, 2 * cv, rtol=0, atol=1e-12 * np.abs(Jc).sum())
+
+
+@pytest.mark.parametrize("n,skew", [(2, True), (3, False), (4, True), (6, False)])
+def test_fd_jacobian_exact(oracle_lib, n, skew):
+    """P5: R is quadratic in u, so the central difference equals the Jacobian column up to
+    rounding, for every h."""
+    ops = small_set(n=n, wid=92 + n)
+    C = ops.C if skew else np.random.default_rng(n).standard_normal(ops.C.shape)
+    o = oracle_lib.Oracle(ops.A, C, ops.f)
+    th = o.theta(23.0, 150.0)
+    u = np.random.default_rng(7).standard_normal(n)
+    J = o.jacobian(n, th, u)
+    h = 0.5
+    Jfd = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = h
+        Jfd[:, j] = (o.residual(n, th, u + e) - o.residual(n, th, u - e)) / (2 * h)
+    assert np.max(np.abs(J - Jfd)) <= 1e-12 * np.max(np.abs(J))
+
+
+def test_c_zero_reduces_to_linear_solve(oracle_lib):
+    """P4: with C = 0 one Newton step gives A(mu)^-1 f(mu); the next update is ~0."""
+    ops = small_set(n=15)
+    o = oracle_lib.Oracle(ops.A, np.zeros_like(ops.C), ops.f)
+    mu = (12.0, 333.0)
+    th = o.theta(*mu)
+    A, f = o.assemble(15, th)
+    u, info, tr, tu = o.newton(15, th, tol_upd=1e-10, tol_res=1e-10)
+    x = np.linalg.solve(A, f)
+    assert info.status == 0 and info.iters == 2
+    assert np.linalg.norm(u - x) <= 1e-12 * np.linalg.norm(x)
+    assert np.linalg.norm(tu[0] - np.linalg.norm(x)) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_quadratic_convergence(oracle_lib):
+    """P6: ||delta_{k+1}|| <= K ||delta_k||^2 while above the rounding floor."""
+    ops = synth.make_operators(synth.WORKLOADS["sweep_n50"], n_max=30)
+    # viscous terms weakened 64x so that several iterations are in the quadratic phase
+    o = oracle_lib.Oracle(ops.A / 64.0, ops.C, ops.f)
+    th = o.theta(35.0, 1000.0)
+    u, info, tr, tu = o.newton(30, th, tol_upd=1e-13, tol_res=1e-13)
+    assert info.status == 0 and info.iters >= 5
+    ks = [tu[k + 1] / tu[k] ** 2 for k in range(len(tu) - 1) if tu[k + 1] > 1e-12 * tu[0]]
+    assert len(ks) >= 3, "no quadratic phase observed"
+    assert max(ks) <= 4 * min(ks)
+    # the ratio of successive updates falls (superlinear), unlike a linear rate
+    rs = [tu[k + 1] / tu[k] for k in range(len(tu) - 1) if tu[k + 1] > 1e-12 * tu[0]]
+    assert all(rs[i + 1] < rs[i] for i in range(len(rs) - 1))
+
+
+def test_truncation_invariance(oracle_lib):
+    """P7: a size-n query on the n_max set equals the oracle on the extracted leading blocks."""
+    ops = small_set(n=14, q_b=2, m=5)
+    o = oracle_lib.Oracle.from_set(ops)
+    n = 9
+    mu = np.array([[21.0, 640.0]])
+    u, p, info = o.solve(mu, n=np.array([n]))
+    o2 = oracle_lib.Oracle(ops.A[:, :n, :n], ops.C[:, :n, :n, :n], ops.f[:, :n], ops.B,
+                           ops.As[:, :, :n], ops.Cs[:, :n, :n, :], ops.fs)
+    u2, p2, info2 = o2.solve(mu)
+    assert info["status"][0] == 0 and info2["status"][0] == 0
+    np.testing.assert_array_equal(u[0, :n], u2[0])
+    np.testing.assert_array_equal(u[0, n:], 0.0)
+    np.testing.assert_array_equal(p[0], p2[0])
+
+
+def test_n1_closed_form(oracle_lib):
+    """P8: for n = 1 a skew C vanishes and u = f(mu) / a(mu)."""
+    ops = small_set(n=1, q_a=2, q_c=2, q_f=2)
+    assert np.all(ops.C == 0)
+    o = oracle_lib.Oracle.from_set(ops)
+    th = o.theta(30.0, 500.0)
+    u, info, _, _ = o.newton(1, th)
+    a = th[0] * ops.A[0, 0, 0] + th[1] * ops.A[1, 0, 0]
+    f = th[4] * ops.f[0, 0] + th[5] * ops.f[1, 0]
+    assert info.status == 0
+    assert abs(u[0] - f / a) <= 1e-15 * abs(f / a)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 40])
+def test_gepp_matches_lapack(oracle_lib, n):
+    g = np.random.default_rng(n)
+    M = g.standard_normal((n, n))
+    b = g.standard_normal(n)
+    x = b.copy()
+    Mc = M.copy()
+    assert oracle_lib.lib().oracle_gepp_solve(n, Mc.ctypes.data, x.ctypes.data) == 0
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-10, atol=1e-12)
+
+
+def test_gepp_needs_pivoting_and_detects_singular(oracle_lib):
+    M = np.array([[0.0, 1.0], [1.0, 0.0]])
+    x = np.array([2.0, 3.0])
+    assert oracle_lib.lib().oracle_gepp_solve(2, M.ctypes.data, x.ctypes.data) == 0
+    np.testing.assert_array_equal(x, [3.0, 2.0])
+    S = np.array([[1.0, 2.0], [2.0, 4.0]])
+    y = np.array([1.0, 1.0])
+    assert oracle_lib.lib().oracle_gepp_solve(2, S.ctypes.data, y.ctypes.data) == 1
+
+
+def test_pressure_linear_reduction(oracle_lib):
+    """With As = 0 and Cs = 0 the recovery is B(mu)^-1 fs(mu) (LAPACK)."""
+    ops = small_set(n=6, q_b=3, m=5)
+    o = oracle_lib.Oracle(ops.A, ops.C, ops.f, ops.B, np.zeros_like(ops.As),
+                          np.zeros_like(ops.Cs), ops.fs)
+    th = o.theta(5.0, 120.0)
+    u = np.random.default_rng(1).standard_normal(6)
+    p, rc = o.pressure(6, th, u)
+    tb, tf = th[3 + 3 + 2:], th[3 + 3:3 + 3 + 2]
+    Bm = np.tensordot(tb, ops.B, axes=1)
+    fs = np.tensordot(tf, ops.fs, axes=1)
+    np.testing.assert_allclose(p, np.linalg.solve(Bm, fs), rtol=1e-12)
+
+
+def test_status_singular_and_nonfinite(oracle_lib):
+    ops = small_set(n=5)
+    o = oracle_lib.Oracle(np.zeros_like(ops.A), np.zeros_like(ops.C), ops.f)
+    u, _, info = o.solve(np.array([[10.0, 200.0]]))
+    assert info["status"][0] == oracle_lib.Q_SINGULAR
+    A = ops.A.copy()
+    A[0, 0, 0] = np.nan
+    o = oracle_lib.Oracle(A, ops.C, ops.f)
+    u, _, info = o.solve(np.array([[10.0, 200.0]]))
+    assert info["status"][0] in (oracle_lib.Q_NONFINITE, oracle_lib.Q_SINGULAR)
+    o = oracle_lib.Oracle.from_set(ops)
+    u, _, info = o.solve(np.array([[10.0, 200.0]]), max_iter=1)
+    assert info["status"][0] == oracle_lib.Q_NOT_CONVERGED and info["iters"][0] == 1
+
+
+def test_sweep_workload_converges(oracle_lib):
+    """Every query of a sample of the n = 50 sweep converges from u = 0 (unique regime)."""
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl)
+    q = synth.make_queries(wl, batch=16)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    o = oracle_lib.Oracle.from_set(ops)
+    u, p, info = o.solve(mu, threads=4)
+    assert np.all(info["status"] == 0), info
+    assert np.all(info["iters"] <= 15)
+    assert np.all(np.isfinite(p))
