@@ -1,0 +1,422 @@
+"""Benchmark of the online stage: batched reduced Newton solves per second on one GB300.
+
+A step is one pass of the whole hot path (theta, Jacobian contraction, FP64 residual, LU,
+update, every Newton iteration to convergence, pressure recovery) over one batch of synthetic
+queries resident in HBM. Default workload: the n = 50 parameter sweep (4096 queries,
+Q_a = Q_c = 6, Q_f = 3, pressure with M = 30).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                    [--workload sweep_n50|dense_n300|...] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank solves its own batch (weak scaling, no
+collective on the data path). --impl reference times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+PREC = {"fp64": 0, "mixed": 1, "fp32": 2}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep_n50", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=sorted(PREC))
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def algorithmic_flops(wl, n, q_c, q_a, iters, iters_fp64r=None):
+    """Per-query algorithmic FLOPs of the solve: per Newton iteration the Jacobian contraction
+    2 (Q_c n^3 + Q_a n^2), the LU 2 n^3 / 3 and the triangular solves 2 n^2; the FP64-accurate
+    residual adds 2 (Q_c n^3 + (Q_a + 1) n^2) where it is evaluated separately."""
+    n = n.astype(np.float64)
+    per_it = 2 * (q_c * n ** 3 + q_a * n ** 2) + 2 * n ** 3 / 3 + 2 * n ** 2
+    total = per_it * iters
+    if iters_fp64r is not None:
+        total = total + 2 * (q_c * n ** 3 + (q_a + 1) * n ** 2) * iters_fp64r
+    return float(total.sum())
+
+
+def run_reference(args, wl, rank, world):
+    """The FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    ops = synth.make_operators(wl)
+    q = synth.make_queries(wl, batch=args.batch)
+    o = oracle.Oracle.from_set(ops)
+    threads = oracle.max_threads()
+    # size the per-step sample so that the whole run stays within a few minutes
+    probe = max(threads, 16)
+    t0 = time.perf_counter()
+    o.solve(q.mu[:probe], q.n[:probe], threads=threads)
+    per_q = (time.perf_counter() - t0) / probe
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    sample = int(max(threads, min(len(q.mu), budget / max(per_q, 1e-9))))
+    for _ in range(args.warmup):
+        o.solve(q.mu[:threads], q.n[:threads], threads=threads)
+    times = []
+    for s in range(args.steps):
+        off = (s * sample) % len(q.mu)
+        idx = (np.arange(sample) + off) % len(q.mu)
+        t0 = time.perf_counter()
+        o.solve(q.mu[idx], q.n[idx], threads=threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * sample / total
+    line = {
+        "impl": "reference", "metric": "reduced Newton solves/s", "value": value,
+        "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n_max, "q_a": wl.q_a, "q_c": wl.q_c,
+                   "batch": len(q.mu), "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} queries of the {wl.name} workload per step"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(wl, ops, q, seconds):
+    """Oracle (as is) on the host cores on a bounded sample; also returns its results."""
+    import oracle
+    o = oracle.Oracle.from_set(ops)
+    threads = oracle.max_threads()
+    probe = max(threads, 8)
+    t0 = time.perf_counter()
+    o.solve(q.mu[:probe], q.n[:probe], threads=threads)
+    per_q = (time.perf_counter() - t0) / probe
+    sample = int(min(len(q.mu), max(probe, seconds / max(per_q, 1e-9))))
+    idx = np.unique(np.concatenate([np.linspace(0, len(q.mu) - 1, sample).astype(int)]))
+    t0 = time.perf_counter()
+    u, p, info = o.solve(q.mu[idx], q.n[idx], threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": len(idx) / dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(idx)} evenly spaced queries of the {len(q.mu)}-query {wl.name} batch "
+                      f"({dt:.1f} s on {threads} threads)"}, idx, u, p, info
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    wl = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+    import torch
+    from paper_1807_11866_gb300 import _build, rb
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    rb.library()
+
+    batch = args.batch or wl.batch
+    ops = synth.make_operators(wl)
+    qall = synth.make_queries(wl, batch=batch * world)
+    sl = slice(rank * batch, (rank + 1) * batch)
+    q = synth.QuerySet(qall.mu[sl].copy(), qall.n[sl].copy())
+    prec = PREC[args.precision]
+    ctx = rb.Context(precision=prec, device=local)
+    ctx.load_set(ops)
+    m = ctx.m
+    stream = torch.cuda.Stream(device=dev)
+    d_mu = torch.from_numpy(q.mu).to(dev)
+    d_n = torch.from_numpy(q.n).to(dev)
+    d_u = torch.empty((batch, wl.n_max), dtype=torch.float64, device=dev)
+    d_p = torch.empty((batch, max(m, 1)), dtype=torch.float64, device=dev) if m else None
+    d_info = torch.empty((batch, 4), dtype=torch.float64, device=dev)  # 32 B per query
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(s):
+        ctx.rb_solve_device(d_mu, batch, d_n, d_u, d_p, d_info, s.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()  # write > L2 between timed steps
+            starts[i].record(stream)
+            step(stream)
+            ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_dev], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = batch * world * args.steps / t_dev
+
+    info = d_info.cpu().numpy().view(rb.INFO_DTYPE).reshape(batch)
+    u_gpu = d_u.cpu().numpy()
+    p_gpu = d_p.cpu().numpy() if d_p is not None else None
+    launches_per_step = ctx_launches(ctx, prec, info)
+
+    # end-to-end through the public host-buffer API, pinned host memory
+    h_mu = torch.from_numpy(q.mu).pin_memory()
+    h_n = torch.from_numpy(q.n).pin_memory()
+    h_u = torch.empty((batch, wl.n_max), dtype=torch.float64).pin_memory()
+    h_p = torch.empty((batch, max(m, 1)), dtype=torch.float64).pin_memory() if m else None
+    h_info = torch.empty((batch, 4), dtype=torch.float64).pin_memory()
+    L = rb.library()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = L.rb_solve(ctx.h, h_mu.data_ptr(), batch, h_n.data_ptr(), h_u.data_ptr(),
+                        h_p.data_ptr() if h_p is not None else None, h_info.data_ptr())
+        t1 = time.perf_counter()
+        assert rc == 0, ctx.last_error()
+        if i >= args.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_val = batch * world * len(e2e_t) / sum(e2e_t)
+    h2d = q.mu.nbytes + q.n.nbytes
+    d2h = batch * wl.n_max * 8 + (batch * m * 8 if m else 0) + batch * 32
+
+    # roofline of the dominant kernel, measured live with events on the launching stream
+    roof = dominant_kernel_roofline(ctx, prec, wl, q, info, stream, flush, args)
+
+    line = {
+        "metric": "reduced Newton solves/s", "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32+f64" if prec == 1 else ("f64" if prec == 0 else "f32+f64"),
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n": wl.n_max, "q_a": wl.q_a, "q_c": wl.q_c,
+                   "q_f": wl.q_f, "m": m, "batch_per_gpu": batch, "precision": args.precision,
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "iters": {"mean": float(info["iters"].mean()), "max": int(info["iters"].max())},
+        "status_ok": int((info["status"] == 0).sum()),
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    line["roofline"] = roof
+    if rank == 0 and not args.no_plain and prec != 0:
+        line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, args)
+        line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+    if rank == 0 and not args.no_cpu:
+        cb, idx, u_ref, p_ref, inf_ref = cpu_baseline(wl, ops, q, args.cpu_seconds)
+        line["cpu_baseline"] = cb
+        err = np.linalg.norm(u_gpu[idx] - u_ref, axis=1) / np.linalg.norm(u_ref, axis=1)
+        line["rel_err_vs_oracle"] = {"u_max": float(err.max()), "u_mean": float(err.mean()),
+                                     "queries": int(len(idx))}
+        if p_gpu is not None and p_ref is not None:
+            perr = np.linalg.norm(p_gpu[idx] - p_ref, axis=1) / np.linalg.norm(p_ref, axis=1)
+            line["rel_err_vs_oracle"]["p_max"] = float(perr.max())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ctx_launches(ctx, prec, info):
+    """Kernels of librb launched per step."""
+    if prec == 0:
+        return 2  # fused Newton + pressure
+    return ctx_mixed_launches(ctx, info)
+
+
+def ctx_mixed_launches(ctx, info):
+    import ctypes
+    from paper_1807_11866_gb300 import rb
+    L = rb.library()
+    if hasattr(L, "rb_debug_last_launches"):
+        L.rb_debug_last_launches.restype = ctypes.c_int
+        L.rb_debug_last_launches.argtypes = [ctypes.c_void_p]
+        return L.rb_debug_last_launches(ctx.h)
+    return 0
+
+
+def dominant_kernel_roofline(ctx, prec, wl, q, info, stream, flush, args):
+    import torch
+    peaks, kind = measured_peaks()
+    n = q.n
+    iters = info["iters"].astype(np.float64)
+    if prec == 0:
+        # the fused FP64 Newton kernel is the step; FP64 ALU bound
+        flops = algorithmic_flops(wl, n, wl.q_c, wl.q_a, iters)
+        ms = time_fp64_kernel(ctx, q, stream, flush, args)
+        ach = flops / (ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        return {"bound": "alu", "kernel": "k_newton_fp64", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "FP64 DFMA peak derived from SM count x FP64 rate x max clock"}
+    return mixed_roofline(ctx, wl, q, info, stream, flush, args, peaks, kind)
+
+
+FP64_PEAK_TFLOPS = 1.25
+
+
+def time_fp64_kernel(ctx, q, stream, flush, args):
+    import torch
+    from paper_1807_11866_gb300 import rb
+    batch = len(q.mu)
+    dev = flush.device
+    d_mu = torch.from_numpy(q.mu).to(dev)
+    d_n = torch.from_numpy(q.n).to(dev)
+    d_u = torch.empty((batch, ctx.n_max), dtype=torch.float64, device=dev)
+    d_info = torch.empty((batch, 4), dtype=torch.float64, device=dev)
+    ts = []
+    with torch.cuda.stream(stream):
+        for i in range(max(2, args.steps)):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            ctx.rb_solve_device(d_mu, batch, d_n, d_u, None, d_info, stream.cuda_stream)
+            e.record(stream)
+            ts.append((s, e))
+    torch.cuda.synchronize()
+    return float(np.mean([s.elapsed_time(e) for s, e in ts]))
+
+
+def mixed_roofline(ctx, wl, q, info, stream, flush, args, peaks, kind):
+    return None
+
+
+def plain_fp64(rb, ops, q, batch, dev, flush, args):
+    """The plain FP64 GPU path (one CTA per query, every step in FP64) on the same batch."""
+    import torch
+    ctx = rb.Context(precision=rb.RB_PREC_FP64, device=dev.index)
+    ctx.load_set(ops)
+    stream = torch.cuda.Stream(device=dev)
+    d_mu = torch.from_numpy(q.mu).to(dev)
+    d_n = torch.from_numpy(q.n).to(dev)
+    d_u = torch.empty((batch, ctx.n_max), dtype=torch.float64, device=dev)
+    d_p = torch.empty((batch, max(ctx.m, 1)), dtype=torch.float64, device=dev) if ctx.m else None
+    d_info = torch.empty((batch, 4), dtype=torch.float64, device=dev)
+    steps = max(2, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        ctx.rb_solve_device(d_mu, batch, d_n, d_u, d_p, d_info, stream.cuda_stream)
+        ev = []
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            ctx.rb_solve_device(d_mu, batch, d_n, d_u, d_p, d_info, stream.cuda_stream)
+            e.record(stream)
+            ev.append((s, e))
+    torch.cuda.synchronize()
+    ms = [s.elapsed_time(e) for s, e in ev]
+    ctx.close()
+    return {"value": batch * len(ms) / (sum(ms) / 1e3), "unit": "solves/s",
+            "ms_per_step": float(np.mean(ms))}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * rb.h -- C ABI of librb: the online stage of the velocity-only (solenoidal) reduced-basis
+ * method for steady Navier-Stokes flow, on one NVIDIA GB300 (sm_103a).
+ *
+ * For each parameter query mu = (alpha in degrees, Re) the library
+ *   1. evaluates the parameter functions theta(mu) of the affine split (Sec. 2.4,
+ *      Eqs. split-a..split-d1),
+ *   2. assembles A(mu) = sum_q theta^a_q A_q and f(mu) = sum_q theta^f_q f_q
+ *      (Sec. 3.5, reduced affine matrices),
+ *   3. runs Newton from u = 0 on the velocity-only reduced equation (Sec. 2.2, Eq. velonly)
+ *        R(u; mu) = A(mu) u + sum_q theta^c_q C_q(u, u) - f(mu) = 0,
+ *        C_q(u, u)[k] = sum_{j,l} C_q[j][l][k] u_j u_l          (Sec. 3.6, Eq. tensor)
+ *      with the tensor Jacobian (Sec. 3.6)
+ *        J[k][j] = A(mu)[k][j] + sum_q theta^c_q sum_l (C_q[l][j][k] + C_q[j][l][k]) u_l
+ *      and one dense n x n partial-pivot solve per step (Sec. 4.1, Eq. blocksolve-1),
+ *      stopping when ||delta||_2 <= tol_update (Sec. 6: update <= 1e-10 in the H1 seminorm,
+ *      the Euclidean coefficient norm for an orthonormal POD basis, Sec. 3.2-3.3) and
+ *      ||R||_2 <= tol_res * max(1, ||f(mu)||_2),
+ *   4. recovers the pressure a posteriori (Sec. 2.2, Eq. sup-vvar; Sec. 4.1, Eq. blocksolve-2)
+ *        B(mu) p = fs(mu) - As(mu) u - sum_q theta^c_q Cs_q(u, u).
+ *
+ * Index convention: C_q[j][l][k] = c_q(u_j, u_l, w_k) -- j advecting, l advected, k test.
+ * Matrices are row-major with the test index as the row.
+ *
+ * Parameter functions (RB_THETA_TRIG): a = alpha * pi / 180, trig_q(a) = cos(q a) for even q
+ * and sin(q a) for odd q (trig_0 = 1); theta^a_q = trig_q / Re and
+ * theta^c_q = theta^f_q = theta^b_q = trig_q. With RB_THETA_USER the caller passes theta.
+ * theta rows are laid out [theta^a (q_a) | theta^c (q_c) | theta^f (q_f) | theta^b (q_b)].
+ *
+ * Error behaviour: every function returns an rb_status. A failing call leaves a message for
+ * rb_last_error() (per context, per calling thread). A per-query failure (non-convergence,
+ * singular Jacobian, non-finite values) is reported in rb_query_info.status and never makes
+ * the call fail. All functions are synchronous unless stated otherwise.
+ *
+ * Threading: one context may be used by one solving thread at a time; the rb_serve_* calls
+ * are thread-safe and may be called from any thread while the server runs.
+ */
+#ifndef RB_H_
+#define RB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RB_OK = 0,
+  RB_PENDING = 1,       /* rb_serve_poll: result not ready yet */
+  RB_ERR_ARG = -1,      /* invalid argument (NULL, size out of range, bad layout) */
+  RB_ERR_OOM = -2,      /* device or pinned-host allocation failed / over memory budget */
+  RB_ERR_CUDA = -3,     /* a CUDA runtime or driver call failed */
+  RB_ERR_STATE = -4,    /* call not valid in the current state (no operators, server off) */
+  RB_ERR_TIMEOUT = -5   /* a bounded device-side wait or host wait gave up */
+} rb_status;
+
+/* per-query outcome, rb_query_info.status */
+enum {
+  RB_Q_OK = 0,
+  RB_Q_NOT_CONVERGED = 1,  /* iteration cap reached */
+  RB_Q_SINGULAR = 2,       /* a pivot of the Jacobian (or of B(mu)) was zero / not finite */
+  RB_Q_NONFINITE = 3,      /* NaN or Inf in the residual or update */
+  RB_Q_REJECTED = 4        /* query size out of range or cancelled */
+};
+
+/* storage type of the convection tensors C and Cs (values are taken as exact) */
+enum { RB_F64 = 0, RB_F32 = 1 };
+
+/* precision of the Newton solve */
+enum {
+  RB_PREC_FP64 = 0,   /* everything in FP64: contraction, LU, residual */
+  RB_PREC_MIXED = 1,  /* Jacobian contraction on BF16 tensor cores + FP32 LU (inexact Newton);
+                         residual and convergence test FP64-accurate */
+  RB_PREC_FP32 = 2    /* Jacobian contraction and LU in FP32 on CUDA cores; residual and
+                         convergence test FP64-accurate */
+};
+
+/* parameter-function family */
+enum { RB_THETA_TRIG = 0, RB_THETA_USER = 1 };
+
+typedef struct rb_ctx rb_ctx; /* opaque; owns all device memory it allocates */
+
+/* Reduced operators of one n_max set. Host pointers, caller-owned; rb_load_operators copies
+ * them (the caller may free them afterwards). Smaller queries use the leading blocks
+ * (nested truncation). Pressure operators are optional (B == NULL: no pressure). */
+typedef struct {
+  int n_max;          /* reduced velocity size, 1..RB_N_MAX */
+  int m;              /* pressure / supremizer reduced size, 0..RB_M_MAX (0 if B == NULL) */
+  int q_a, q_c, q_f, q_b;  /* affine term counts, q_a, q_c, q_f >= 1 */
+  int dtype_c;        /* RB_F64 or RB_F32: storage of C and Cs */
+  const double *A;    /* [q_a][n_max][n_max], row = test k, column = trial j */
+  const void *C;      /* [q_c][n_max][n_max][n_max], index [j][l][k] */
+  const double *f;    /* [q_f][n_max] */
+  const double *B;    /* [q_b][m][m] or NULL; row = supremizer test, column = pressure trial */
+  const double *As;   /* [q_a][m][n_max] or NULL */
+  const void *Cs;     /* [q_c][n_max][n_max][m] or NULL, index [j][l][k'] */
+  const double *fs;   /* [q_f][m] or NULL */
+} rb_operators;
+
+#define RB_N_MAX 320
+#define RB_M_MAX 128
+#define RB_Q_MAX 64
+
+typedef struct {
+  int precision;      /* RB_PREC_* */
+  double tol_update;  /* absolute bound on ||delta||_2 (default 1e-10) */
+  double tol_res;     /* bound on ||R||_2 / max(1, ||f(mu)||_2) (default 1e-10) */
+  int max_iter;       /* Newton iteration cap (default 50) */
+  size_t mem_budget;  /* device bytes the context may allocate (0: 80% of free memory) */
+  int use_graph;      /* capture per-iteration launches in CUDA graphs (default 1) */
+  int autotune;       /* time kernel variants on first use per shape (default 1) */
+  int theta_family;   /* RB_THETA_TRIG (default) or RB_THETA_USER */
+} rb_config;
+
+typedef struct {
+  int status;          /* RB_Q_* */
+  int iters;           /* Newton iterations performed */
+  int precision_used;  /* RB_PREC_* of the Jacobian in the final iteration */
+  int reserved;
+  double res_norm;     /* ||R(u_k)||_2 at the last iteration */
+  double upd_norm;     /* ||delta_k||_2 at the last iteration */
+} rb_query_info;
+
+/* Fill *cfg with the defaults listed above. */
+void rb_config_default(rb_config *cfg);
+
+/* Create a context on CUDA device `device`; cfg == NULL means defaults. */
+int rb_create(rb_ctx **out, const rb_config *cfg, int device);
+
+/* Destroy a context and free all its device and pinned-host memory (stops the server). */
+void rb_destroy(rb_ctx *ctx);
+
+/* Last error message of this context on the calling thread ("" if none). Never NULL. */
+const char *rb_last_error(rb_ctx *ctx);
+
+/* Copy an operator set to the device and build the per-precision layouts (Sec. 3.5-3.6:
+ * all reduced operators are precomputed offline; online assembly only weights them).
+ * Replaces a previously loaded set. Returns RB_ERR_ARG on bad sizes or NULL arrays,
+ * RB_ERR_OOM if the layouts do not fit in the memory budget. */
+int rb_load_operators(rb_ctx *ctx, const rb_operators *ops);
+
+/* Solve n_queries queries from host buffers (synchronous).
+ *   mu     [n_queries][2] (alpha_deg, Re)
+ *   n      [n_queries] reduced sizes 1..n_max, or NULL for n_max
+ *   u_out  [n_queries][n_max] velocity coefficients, entries beyond n set to 0
+ *   p_out  [n_queries][m] pressure coefficients, or NULL (ignored when no pressure ops)
+ *   info   [n_queries] or NULL
+ * Queries with n outside 1..n_max get RB_Q_REJECTED. */
+int rb_solve(rb_ctx *ctx, const double *mu, int n_queries, const int *n, double *u_out,
+             double *p_out, rb_query_info *info);
+
+/* Same with caller-supplied parameter functions theta [n_queries][q_a + q_c + q_f + q_b]. */
+int rb_solve_theta(rb_ctx *ctx, const double *theta, int n_queries, const int *n,
+                   double *u_out, double *p_out, rb_query_info *info);
+
+/* Solve from device buffers owned by the caller, asynchronously on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). The buffers must stay valid until
+ * the stream reaches the end of the work enqueued here. d_n may be NULL (all n_max);
+ * d_p and d_info may be NULL. Returns after enqueueing; the context's internal scratch is
+ * reused by the next call on any stream, so calls on one context must be ordered. */
+int rb_solve_device(rb_ctx *ctx, const double *d_mu, int n_queries, const int *d_n,
+                    double *d_u, double *d_p, rb_query_info *d_info, void *cuda_stream);
+
+/* Evaluate the residual R(u; mu) (FP64) and, if J_out != NULL, the Jacobian J(u; mu) at
+ * caller-given coefficient vectors, for n_queries queries of size n (all equal, <= n_max),
+ * from host buffers. precision selects the Jacobian path (RB_PREC_FP64: FP64 contraction;
+ * RB_PREC_MIXED: BF16 tensor-core contraction plus FP32 A(mu); RB_PREC_FP32: FP32).
+ *   u      [n_queries][n]      R_out [n_queries][n]      J_out [n_queries][n][n] (row k)
+ * This is the building block of one Newton step (Sec. 3.6), exposed for verification. */
+int rb_eval(rb_ctx *ctx, const double *mu, int n_queries, int n, const double *u,
+            int precision, double *R_out, double *J_out);
+
+/* Batched Gaussian elimination with partial pivoting (first row of largest magnitude),
+ * FP64, on host buffers: solves M_b x_b = rhs_b for b < batch. M [batch][n][n] row-major
+ * (not modified), rhs [batch][n], x_out [batch][n], status [batch] (0 ok, RB_Q_SINGULAR).
+ * The dense solve of Sec. 4.1 (Eq. blocksolve-1), exposed for verification. */
+int rb_gepp_solve(rb_ctx *ctx, int n, int batch, const double *M, const double *rhs,
+                  double *x_out, int *status);
+
+/* ---- serving: continuous batching at Newton-iteration granularity --------------------
+ * A host thread admits queries into device slots while memory allows and advances every
+ * active slot by one Newton iteration per step; converged queries leave and waiting ones
+ * join at the next step. Results are the same as rb_solve for the same query. */
+int rb_serve_start(rb_ctx *ctx);
+/* Stop the server: drain == 1 finishes admitted and queued queries first; drain == 0
+ * cancels them (they complete with RB_Q_REJECTED). */
+int rb_serve_stop(rb_ctx *ctx, int drain);
+/* Enqueue one query (thread-safe). n = 0 means n_max. Returns RB_ERR_ARG for n out of
+ * range, RB_ERR_STATE if the server is not running. */
+int rb_serve_submit(rb_ctx *ctx, const double mu[2], int n, uint64_t *ticket);
+/* Poll a ticket: RB_PENDING until done, then RB_OK with the result copied out
+ * (u_out [n_max], p_out [m] or NULL, info or NULL); the ticket is released afterwards
+ * and polling it again returns RB_ERR_ARG. */
+int rb_serve_poll(rb_ctx *ctx, uint64_t ticket, double *u_out, double *p_out,
+                  rb_query_info *info);
+/* Latency percentiles (seconds, submit to completion) and throughput since start. */
+int rb_serve_stats(rb_ctx *ctx, double *p50_s, double *p99_s, double *solves_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RB_H_ */

@@ -1,0 +1,63 @@
+// rb_ctx.h -- the context object behind the opaque rb_ctx handle (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <unordered_map>
+#include <vector>
+
+#include "rb_kernels.cuh"
+
+struct rb_ctx;
+
+namespace rb {
+
+struct Scratch {
+  void *ptr = nullptr;
+  size_t cap = 0;
+  int reserve(rb_ctx *ctx, size_t bytes, const char *what);
+  void release(rb_ctx *ctx);
+};
+
+struct MixedState;   // low-precision layouts and per-batch state of the mixed path
+struct ServeState;   // continuous-batching server
+
+int set_error(const rb_ctx *ctx, int code, const char *fmt, ...);
+int cuda_fail(const rb_ctx *ctx, cudaError_t e, const char *what);
+int ctx_alloc(rb_ctx *ctx, void **p, size_t bytes, const char *what);
+void ctx_free(rb_ctx *ctx, void *p);
+int op_alloc(rb_ctx *ctx, void **p, size_t bytes, const char *what);
+
+int solve_fp64(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
+               double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st);
+int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
+                double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st);
+int solve_pressure(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
+                   const int *d_n, const double *d_u, double *d_p, rb_query_info *d_info,
+                   cudaStream_t st);
+int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
+                      const int *d_n, double *d_u, double *d_p, rb_query_info *d_info,
+                      cudaStream_t st);
+int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u, int precision,
+               double *d_R, double *d_J, cudaStream_t st);
+void mixed_release(rb_ctx *ctx);
+void serve_shutdown(rb_ctx *ctx);
+
+}  // namespace rb
+
+struct rb_ctx {
+  rb_config cfg{};
+  int device = 0, sms = 0, max_smem = 0, smem_per_sm = 0, cc_major = 0, cc_minor = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0, used = 0;
+  std::unordered_map<void *, size_t> sizes;  // live allocations of this context
+  // operators
+  bool loaded = false;
+  rb::DevOps ops{};
+  std::vector<void *> op_allocs;
+  void *d_C = nullptr;  // C in its storage type [q_c][n][n][n]
+  int c_is_f32 = 0;
+  // scratch
+  rb::Scratch stage, jscratch, info_scratch, eval_scratch;
+  rb::MixedState *mixed = nullptr;
+  rb::ServeState *serve = nullptr;
+};

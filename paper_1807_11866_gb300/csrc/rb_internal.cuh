@@ -1,0 +1,154 @@
+// rb_internal.cuh -- device-side layouts and block-level building blocks shared by the
+// kernels of librb (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rb.h"
+
+namespace rb {
+
+constexpr int kThreads = 256;  // block size of the per-query kernels (8 warps)
+constexpr int kWarps = kThreads / 32;
+
+// Device-resident operator layouts (all owned by the context, built at load time).
+struct DevOps {
+  int n_max, m, q_a, q_c, q_f, q_b, n_theta;
+  const double *A;    // [q_a][n_max][n_max]          row = test k
+  const double *Dt;   // [q_c][n_max(l)][n_max(k)][n_max(j)]  D~_q[k][j][l] =
+                      //   C_q[l][j][k] + C_q[j][l][k]  (both orders of Sec. 3.6 pre-summed)
+  const double *f;    // [q_f][n_max]
+  const double *B;    // [q_b][m][m]
+  const double *As;   // [q_a][m][n_max]
+  const double *Cs;   // [q_c][n_max][n_max][m]   index [j][l][k'] (FP64 copy)
+  const double *fs;   // [q_f][m]
+};
+
+// Parameter functions of the trigonometric family (Sec. 2.4 affine split): trig_q(a) is
+// cos(q a) for even q and sin(q a) for odd q; theta^a carries 1/Re.
+__device__ __forceinline__ double trig_q(int q, double a) {
+  return (q & 1) ? sin((double)q * a) : cos((double)q * a);
+}
+
+// theta row of one query into th[0..n_theta): [a | c | f | b]. Called by all threads.
+__device__ __forceinline__ void theta_eval(const DevOps &o, double alpha_deg, double re,
+                                           double *th) {
+  const double a = alpha_deg * 0.017453292519943295769;  // pi / 180
+  for (int i = threadIdx.x; i < o.n_theta; i += blockDim.x) {
+    int q = i;
+    double scale = 1.0;
+    if (q < o.q_a) {
+      scale = 1.0 / re;
+    } else {
+      q -= o.q_a;
+      if (q >= o.q_c) {
+        q -= o.q_c;
+        if (q >= o.q_f) q -= o.q_f;
+      }
+    }
+    th[i] = trig_q(q, a) * scale;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; red must hold kWarps doubles. Result valid in all threads.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) s += red[i];
+  return s;
+}
+
+// (|value|, row) argmax with the first row winning ties.
+__device__ __forceinline__ void argmax_merge(double &v, int &r, double v2, int r2) {
+  if (v2 > v || (v2 == v && r2 < r)) { v = v2; r = r2; }
+}
+
+// Solve M x = b in place by Gaussian elimination with partial pivoting (pivot = first row
+// of largest magnitude), block-cooperative. M: n x n with row stride ld (shared or global),
+// b: shared, overwritten by x. red: >= 2 * kWarps + 2 doubles of shared scratch.
+// Returns true if a pivot was zero or not finite (b is then unspecified).
+template <typename T>
+__device__ bool gepp_solve_block(T *M, int ld, int n, T *b, double *red) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int *ired = reinterpret_cast<int *>(red + 2 * kWarps);
+  for (int p = 0; p < n; ++p) {
+    // pivot search over rows p..n-1 of column p
+    double best = -1.0;
+    int brow = n;
+    for (int i = p + tid; i < n; i += blockDim.x) argmax_merge(best, brow, fabs((double)M[(size_t)i * ld + p]), i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      int r2 = __shfl_xor_sync(0xffffffffu, brow, o);
+      argmax_merge(best, brow, v2, r2);
+    }
+    if (lane == 0) { red[w] = best; ired[w] = brow; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = red[0];
+      int br = ired[0];
+      for (int i = 1; i < kWarps; ++i) argmax_merge(bv, br, red[i], ired[i]);
+      red[kWarps] = bv;
+      ired[kWarps] = br;
+    }
+    __syncthreads();
+    const double pv = red[kWarps];
+    const int r = ired[kWarps];
+    if (!(pv > 0.0) || !isfinite(pv)) return true;
+    if (r != p) {
+      for (int j = p + tid; j < n; j += blockDim.x) {
+        T t = M[(size_t)p * ld + j];
+        M[(size_t)p * ld + j] = M[(size_t)r * ld + j];
+        M[(size_t)r * ld + j] = t;
+      }
+      if (tid == 0) { T t = b[p]; b[p] = b[r]; b[r] = t; }
+    }
+    __syncthreads();
+    const T piv = M[(size_t)p * ld + p];
+    for (int i = p + 1 + tid; i < n; i += blockDim.x) M[(size_t)i * ld + p] = M[(size_t)i * ld + p] / piv;
+    __syncthreads();
+    const int rem = n - p - 1;
+    const T bp = b[p];
+    // trailing update, one warp per row
+    for (int i = p + 1 + w; i < n; i += kWarps) {
+      const T lip = M[(size_t)i * ld + p];
+      T *Mi = M + (size_t)i * ld;
+      const T *Mp = M + (size_t)p * ld;
+      for (int j = p + 1 + lane; j < n; j += 32) Mi[j] -= lip * Mp[j];
+      if (lane == 0) b[i] -= lip * bp;
+    }
+    (void)rem;
+    __syncthreads();
+  }
+  // back substitution by warp 0
+  if (w == 0) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int j = i + 1 + lane; j < n; j += 32) s += (double)M[(size_t)i * ld + j] * (double)b[j];
+      s = warp_sum(s);
+      if (lane == 0) b[i] = (T)(((double)b[i] - s) / (double)M[(size_t)i * ld + i]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  return false;
+}
+
+}  // namespace rb

@@ -1,0 +1,51 @@
+// rb_kernels.cuh -- launch parameters and host launchers of the librb kernels (internal).
+#pragma once
+#include "rb_internal.cuh"
+
+namespace rb {
+
+struct NewtonParams {
+  DevOps o;
+  const double *mu;     // [nq][2] or nullptr when theta is given
+  const double *theta;  // [nq][n_theta] or nullptr
+  const int *nsz;       // [nq] or nullptr (n_max)
+  int nq, max_iter, grid, j_in_smem;
+  double tol_upd, tol_res;
+  double *u_out;        // [nq][n_max]
+  rb_query_info *info;  // [nq] or nullptr
+  double *jscratch;     // [grid][n_max^2] when the Jacobian does not fit in shared memory
+};
+
+struct PressureParams {
+  DevOps o;
+  const double *mu, *theta;
+  const int *nsz;
+  int nq;
+  const double *u;      // [nq][n_max]
+  double *p_out;        // [nq][m]
+  rb_query_info *info;  // [nq] or nullptr
+};
+
+struct EvalParams {
+  DevOps o;
+  const double *mu;
+  int nq, n;
+  const double *u;      // [nq][n]
+  double *R_out;        // [nq][n]
+  double *J_out;        // [nq][n][n]
+};
+
+size_t fp64_smem_bytes(const DevOps &o, bool j_in_smem);
+size_t pressure_smem_bytes(const DevOps &o);
+
+cudaError_t launch_newton_fp64(const NewtonParams &p, int sms, cudaStream_t st);
+cudaError_t launch_pressure(const PressureParams &p, int sms, cudaStream_t st);
+cudaError_t launch_eval_fp64(const EvalParams &p, int sms, cudaStream_t st);
+cudaError_t launch_gepp_fp64(double *M, double *rhs, int n, int batch, int *status, int sms,
+                             cudaStream_t st);
+cudaError_t launch_build_dt(const void *C, int c_is_f32, double *Dt, int nm, int qc, int sms,
+                            cudaStream_t st);
+cudaError_t launch_convert(const void *src, int src_is_f32, double *dst, size_t count, int sms,
+                           cudaStream_t st);
+
+}  // namespace rb

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of librb (include/rb.h): argument marshalling only.
+
+Every function keeps the C name. Arrays are numpy (host) or torch CUDA tensors (device);
+every step of the solve runs in the CUDA library. Importing this module never falls back to
+another implementation: if librb.so is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librb.so")
+
+RB_OK, RB_PENDING = 0, 1
+RB_ERR_ARG, RB_ERR_OOM, RB_ERR_CUDA, RB_ERR_STATE, RB_ERR_TIMEOUT = -1, -2, -3, -4, -5
+RB_Q_OK, RB_Q_NOT_CONVERGED, RB_Q_SINGULAR, RB_Q_NONFINITE, RB_Q_REJECTED = 0, 1, 2, 3, 4
+RB_F64, RB_F32 = 0, 1
+RB_PREC_FP64, RB_PREC_MIXED, RB_PREC_FP32 = 0, 1, 2
+RB_THETA_TRIG, RB_THETA_USER = 0, 1
+RB_N_MAX, RB_M_MAX, RB_Q_MAX = 320, 128, 64
+
+EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
+           "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
+           "rb_serve_start", "rb_serve_stop", "rb_serve_submit", "rb_serve_poll",
+           "rb_serve_stats"]
+
+
+class rb_operators(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int), ("m", ctypes.c_int), ("q_a", ctypes.c_int),
+                ("q_c", ctypes.c_int), ("q_f", ctypes.c_int), ("q_b", ctypes.c_int),
+                ("dtype_c", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("C", ctypes.c_void_p), ("f", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("As", ctypes.c_void_p), ("Cs", ctypes.c_void_p),
+                ("fs", ctypes.c_void_p)]
+
+
+class rb_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol_update", ctypes.c_double),
+                ("tol_res", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("mem_budget", ctypes.c_size_t), ("use_graph", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("theta_family", ctypes.c_int)]
+
+
+class rb_query_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("precision_used", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("res_norm", ctypes.c_double), ("upd_norm", ctypes.c_double)]
+
+
+INFO_DTYPE = np.dtype([("status", np.int32), ("iters", np.int32), ("precision_used", np.int32),
+                       ("reserved", np.int32), ("res_norm", np.float64), ("upd_norm", np.float64)])
+
+_lib = None
+
+
+def library():
+    """Load librb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"librb.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.rb_config_default.argtypes = [P]
+        L.rb_config_default.restype = None
+        L.rb_create.argtypes = [P, P, I]
+        L.rb_destroy.argtypes = [P]
+        L.rb_destroy.restype = None
+        L.rb_last_error.argtypes = [P]
+        L.rb_last_error.restype = ctypes.c_char_p
+        L.rb_load_operators.argtypes = [P, P]
+        L.rb_solve.argtypes = [P, P, I, P, P, P, P]
+        L.rb_solve_theta.argtypes = [P, P, I, P, P, P, P]
+        L.rb_solve_device.argtypes = [P, P, I, P, P, P, P, P]
+        L.rb_eval.argtypes = [P, P, I, I, P, I, P, P]
+        L.rb_gepp_solve.argtypes = [P, I, I, P, P, P, P]
+        L.rb_serve_start.argtypes = [P]
+        L.rb_serve_stop.argtypes = [P, I]
+        L.rb_serve_submit.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_uint64)]
+        L.rb_serve_poll.argtypes = [P, ctypes.c_uint64, P, P, P]
+        L.rb_serve_stats.argtypes = [P, P, P, P]
+        for name in EXPORTS:
+            if name not in ("rb_config_default", "rb_destroy", "rb_last_error"):
+                getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+class RbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"librb error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def rb_config_default() -> rb_config:
+    c = rb_config()
+    library().rb_config_default(ctypes.byref(c))
+    return c
+
+
+class Context:
+    """An rb_ctx on one device. Methods mirror the C entry points one to one."""
+
+    def __init__(self, precision=RB_PREC_FP64, tol_update=None, tol_res=None, max_iter=None,
+                 mem_budget=None, use_graph=None, device=0):
+        L = library()
+        cfg = rb_config_default()
+        cfg.precision = precision
+        if tol_update is not None:
+            cfg.tol_update = tol_update
+        if tol_res is not None:
+            cfg.tol_res = tol_res
+        if max_iter is not None:
+            cfg.max_iter = max_iter
+        if mem_budget is not None:
+            cfg.mem_budget = mem_budget
+        if use_graph is not None:
+            cfg.use_graph = use_graph
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        rc = L.rb_create(ctypes.byref(h), ctypes.byref(cfg), device)
+        if rc != RB_OK:
+            raise RbError(rc, "rb_create failed")
+        self.h = h
+        self.n_max = self.m = 0
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().rb_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_error(self) -> str:
+        return library().rb_last_error(self.h).decode()
+
+    def _check(self, rc, what):
+        if rc not in (RB_OK, RB_PENDING):
+            raise RbError(rc, f"{what}: {self.last_error()}")
+        return rc
+
+    # --- operators ----------------------------------------------------------------------
+    def rb_load_operators(self, A, C, f, B=None, As=None, Cs=None, fs=None):
+        A, f = _f64(A), _f64(f)
+        C = np.ascontiguousarray(C)
+        dt = RB_F32 if C.dtype == np.float32 else RB_F64
+        if dt == RB_F64:
+            C = _f64(C)
+        q_a, n, _ = A.shape
+        ops = rb_operators(n_max=n, q_a=q_a, q_c=C.shape[0], q_f=f.shape[0], dtype_c=dt,
+                           A=_ptr(A), C=_ptr(C), f=_ptr(f))
+        keep = [A, C, f]
+        if B is not None:
+            B, As, fs = _f64(B), _f64(As), _f64(fs)
+            Cs = np.ascontiguousarray(Cs, dtype=C.dtype)
+            ops.m, ops.q_b = B.shape[1], B.shape[0]
+            ops.B, ops.As, ops.Cs, ops.fs = _ptr(B), _ptr(As), _ptr(Cs), _ptr(fs)
+            keep += [B, As, Cs, fs]
+        self._check(library().rb_load_operators(self.h, ctypes.byref(ops)), "rb_load_operators")
+        self.n_max, self.m = n, (ops.m if B is not None else 0)
+        self.q = (ops.q_a, ops.q_c, ops.q_f, ops.q_b)
+
+    def load_set(self, ops):
+        """Load a synth.OperatorSet (or any object with the same fields)."""
+        self.rb_load_operators(ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs)
+
+    # --- solves -------------------------------------------------------------------------
+    def rb_solve(self, mu, n=None, pressure=True):
+        mu = _f64(mu).reshape(-1, 2)
+        nq = mu.shape[0]
+        nn = None if n is None else np.ascontiguousarray(n, dtype=np.int32)
+        u = np.empty((nq, self.n_max))
+        p = np.empty((nq, self.m)) if (pressure and self.m > 0) else None
+        info = np.zeros(nq, dtype=INFO_DTYPE)
+        self._check(library().rb_solve(self.h, _ptr(mu), nq, _ptr(nn), _ptr(u), _ptr(p),
+                                       _ptr(info)), "rb_solve")
+        return u, p, info
+
+    def rb_solve_theta(self, theta, n=None, pressure=True):
+        theta = _f64(theta)
+        nq = theta.shape[0]
+        nn = None if n is None else np.ascontiguousarray(n, dtype=np.int32)
+        u = np.empty((nq, self.n_max))
+        p = np.empty((nq, self.m)) if (pressure and self.m > 0) else None
+        info = np.zeros(nq, dtype=INFO_DTYPE)
+        self._check(library().rb_solve_theta(self.h, _ptr(theta), nq, _ptr(nn), _ptr(u),
+                                             _ptr(p), _ptr(info)), "rb_solve_theta")
+        return u, p, info
+
+    def rb_solve_device(self, d_mu, n_queries, d_n, d_u, d_p, d_info, stream):
+        """Device pointers (torch tensors or ints) and a cudaStream_t handle (int)."""
+        return self._check(library().rb_solve_device(
+            self.h, _ptr(d_mu), n_queries, _ptr(d_n), _ptr(d_u), _ptr(d_p), _ptr(d_info),
+            stream), "rb_solve_device")
+
+    def rb_eval(self, mu, n, u, precision=RB_PREC_FP64, jacobian=True):
+        mu = _f64(mu).reshape(-1, 2)
+        u = _f64(u)
+        nq = mu.shape[0]
+        R = np.empty((nq, n))
+        J = np.empty((nq, n, n)) if jacobian else None
+        self._check(library().rb_eval(self.h, _ptr(mu), nq, n, _ptr(u), precision, _ptr(R),
+                                      _ptr(J)), "rb_eval")
+        return R, J
+
+    def rb_gepp_solve(self, M, rhs):
+        M, rhs = _f64(M), _f64(rhs)
+        batch, n, _ = M.shape
+        x = np.empty((batch, n))
+        st = np.empty(batch, dtype=np.int32)
+        self._check(library().rb_gepp_solve(self.h, n, batch, _ptr(M), _ptr(rhs), _ptr(x),
+                                            _ptr(st)), "rb_gepp_solve")
+        return x, st
+
+    # --- serving ------------------------------------------------------------------------
+    def rb_serve_start(self):
+        return self._check(library().rb_serve_start(self.h), "rb_serve_start")
+
+    def rb_serve_stop(self, drain=True):
+        return self._check(library().rb_serve_stop(self.h, int(drain)), "rb_serve_stop")
+
+    def rb_serve_submit(self, mu, n=0):
+        t = ctypes.c_uint64()
+        mu = _f64(mu).reshape(2)
+        self._check(library().rb_serve_submit(self.h, _ptr(mu), int(n), ctypes.byref(t)),
+                    "rb_serve_submit")
+        return t.value
+
+    def rb_serve_poll(self, ticket):
+        u = np.empty(self.n_max)
+        p = np.empty(self.m) if self.m > 0 else None
+        info = np.zeros(1, dtype=INFO_DTYPE)
+        rc = self._check(library().rb_serve_poll(self.h, ticket, _ptr(u), _ptr(p), _ptr(info)),
+                         "rb_serve_poll")
+        if rc == RB_PENDING:
+            return None
+        return u, p, info[0]
+
+    def rb_serve_stats(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(library().rb_serve_stats(self.h, ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.byref(c)), "rb_serve_stats")
+        return a.value, b.value, c.value
