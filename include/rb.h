@@ -69,11 +69,10 @@ enum { RB_F64 = 0, RB_F32 = 1 };
 
 /* precision of the Newton solve */
 enum {
-  RB_PREC_FP64 = 0,   /* everything in FP64: contraction, LU, residual */
-  RB_PREC_MIXED = 1,  /* Jacobian contraction on BF16 tensor cores + FP32 LU (inexact Newton);
-                         residual and convergence test FP64-accurate */
-  RB_PREC_FP32 = 2    /* Jacobian contraction and LU in FP32 on CUDA cores; residual and
-                         convergence test FP64-accurate */
+  RB_PREC_FP64 = 0,  /* everything in FP64: contraction, LU, residual */
+  RB_PREC_MIXED = 1  /* Jacobian contraction on BF16 tensor cores + FP32 LU (inexact Newton);
+                        residual (error-free sliced products on the tensor cores) and
+                        convergence test FP64-accurate */
 };
 
 /* parameter-function family */
@@ -164,8 +163,9 @@ int rb_solve_device(rb_ctx *ctx, const double *d_mu, int n_queries, const int *d
 
 /* Evaluate the residual R(u; mu) (FP64) and, if J_out != NULL, the Jacobian J(u; mu) at
  * caller-given coefficient vectors, for n_queries queries of size n (all equal, <= n_max),
- * from host buffers. precision selects the Jacobian path (RB_PREC_FP64: FP64 contraction;
- * RB_PREC_MIXED: BF16 tensor-core contraction plus FP32 A(mu); RB_PREC_FP32: FP32).
+ * from host buffers. precision selects the path (RB_PREC_FP64: FP64 contraction;
+ * RB_PREC_MIXED: BF16 tensor-core Jacobian contraction plus A(mu) from FP64, and the residual
+ * from the error-free sliced tensor-core product).
  *   u      [n_queries][n]      R_out [n_queries][n]      J_out [n_queries][n][n] (row k)
  * This is the building block of one Newton step (Sec. 3.6), exposed for verification. */
 int rb_eval(rb_ctx *ctx, const double *mu, int n_queries, int n, const double *u,

@@ -243,7 +243,7 @@ int rb_create(rb_ctx **out, const rb_config *cfg, int device) {
   *out = nullptr;
   rb_ctx *ctx = new rb_ctx();
   if (cfg) ctx->cfg = *cfg; else rb_config_default(&ctx->cfg);
-  if (ctx->cfg.max_iter < 1 || ctx->cfg.precision < RB_PREC_FP64 || ctx->cfg.precision > RB_PREC_FP32 ||
+  if (ctx->cfg.max_iter < 1 || ctx->cfg.precision < RB_PREC_FP64 || ctx->cfg.precision > RB_PREC_MIXED ||
       !(ctx->cfg.tol_update >= 0) || !(ctx->cfg.tol_res >= 0)) {
     delete ctx;
     return RB_ERR_ARG;

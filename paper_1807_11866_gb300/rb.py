@@ -18,7 +18,7 @@ RB_OK, RB_PENDING = 0, 1
 RB_ERR_ARG, RB_ERR_OOM, RB_ERR_CUDA, RB_ERR_STATE, RB_ERR_TIMEOUT = -1, -2, -3, -4, -5
 RB_Q_OK, RB_Q_NOT_CONVERGED, RB_Q_SINGULAR, RB_Q_NONFINITE, RB_Q_REJECTED = 0, 1, 2, 3, 4
 RB_F64, RB_F32 = 0, 1
-RB_PREC_FP64, RB_PREC_MIXED, RB_PREC_FP32 = 0, 1, 2
+RB_PREC_FP64, RB_PREC_MIXED = 0, 1
 RB_THETA_TRIG, RB_THETA_USER = 0, 1
 RB_N_MAX, RB_M_MAX, RB_Q_MAX = 320, 128, 64
 

@@ -1,0 +1,145 @@
+"""GPU parity of the mixed-precision path (tensor-core Jacobian + FP64-accurate sliced residual)
+against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: the converged velocity within 1e-8 relative L2 of the oracle per query (the bound
+stated for mixed paths); the residual evaluated at a given u within 1e-12 of the size of its
+terms (sum_j |A(mu)[k][j] u_j| + |C_mu(u,u)|-terms + |f|), which is what the FP64 stopping
+rule needs; the Jacobian's convection part within BF16 rounding (2^-7 of its magnitude).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-8
+
+
+@pytest.fixture(scope="module")
+def rb():
+    from paper_1807_11866_gb300 import _build, rb
+    _build.build()
+    return rb
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.maximum(np.linalg.norm(b, axis=-1), 1e-300)
+
+
+def term_scale(o, ops, n, th, u):
+    A, f = o.assemble(n, th)
+    tc = th[o.q_a:o.q_a + o.q_c]
+    Cabs = np.abs(ops.C[:, :n, :n, :n].astype(np.float64))
+    conv = np.einsum("q,qjlk,j,l->k", np.abs(tc), Cabs, np.abs(u), np.abs(u))
+    return np.abs(A) @ np.abs(u) + conv + np.abs(f)
+
+
+@pytest.mark.parametrize("n,qc,c_dtype", [(8, 3, "f64"), (50, 6, "f64"), (37, 4, "f32"),
+                                          (64, 8, "bf16")])
+def test_eval_residual_and_jacobian(rb, n, qc, c_dtype):
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl, n_max=n, q_a=3, q_c=qc, c_dtype=c_dtype)
+    o = oracle.Oracle.from_set(ops)
+    g = np.random.default_rng(n)
+    nq = 150  # more than one 128-row tile, ragged tail
+    mu = np.stack([g.uniform(0, 35, nq), 10 ** g.uniform(2, 3, nq)], 1)
+    u = g.standard_normal((nq, n)) * 0.05
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        R, J = ctx.rb_eval(mu, n, u, rb.RB_PREC_MIXED)
+    for b in list(range(0, nq, 7)) + [nq - 1]:
+        th = o.theta(*mu[b])
+        Rr = o.residual(n, th, u[b])
+        Jr = o.jacobian(n, th, u[b])
+        A, _ = o.assemble(n, th)
+        sc = term_scale(o, ops, n, th, u[b])
+        assert np.max(np.abs(R[b] - Rr) / sc) <= 1e-12, b
+        Jc, Jcr = J[b] - A, Jr - A
+        assert np.abs(Jc - Jcr).max() <= 2 ** -7 * np.abs(Jcr).max() + 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("n", [2, 20, 50])
+def test_sweep_parity(rb, n):
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl, n_max=n)
+    q = synth.make_queries(wl, batch=200, n_max=n)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    o = oracle.Oracle.from_set(ops)
+    u_ref, p_ref, inf_ref = o.solve(mu, threads=8)
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, p, info = ctx.rb_solve(mu)
+    assert np.all(info["status"] == 0), np.unique(info["status"], return_counts=True)
+    assert np.all(info["precision_used"] == rb.RB_PREC_MIXED)
+    assert rel(u, u_ref).max() <= TOL_MIXED
+    assert rel(p, p_ref).max() <= 10 * TOL_MIXED
+
+
+def test_manufactured_mixed(rb):
+    ops = synth.make_operators(synth.WORKLOADS["single_n20"])
+    oracle.manufacture(ops, (10.0, 200.0))
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, _, info = ctx.rb_solve(np.array([[10.0, 200.0]]))
+    assert info["status"][0] == 0
+    assert rel(u[0], ops.u_star) <= TOL_MIXED
+
+
+def test_nested_sizes_and_theta_user(rb):
+    wl = synth.WORKLOADS["uneven_n120"]
+    ops = synth.make_operators(wl, n_max=40, q_a=4, q_c=4)
+    o = oracle.Oracle.from_set(ops)
+    mu = synth.make_queries(wl, batch=130).mu
+    sizes = np.array([1, 5, 17, 20, 39, 40] * 22)[:130].astype(np.int32)
+    theta = np.stack([o.theta(*m) for m in mu])
+    u_ref, _, _ = o.solve(mu, n=sizes, threads=8)
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, _, info = ctx.rb_solve(mu, n=sizes)
+        u2, _, info2 = ctx.rb_solve_theta(theta, n=sizes)
+    assert np.all(info["status"] == 0) and np.all(info2["status"] == 0)
+    assert rel(u, u_ref).max() <= TOL_MIXED
+    assert rel(u2, u_ref).max() <= TOL_MIXED
+    for b, n in enumerate(sizes):
+        assert np.all(u[b, n:] == 0.0)
+
+
+def test_status_codes_mixed(rb):
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl, n_max=12)
+    mu = np.array([[10.0, 200.0], [20.0, 300.0], [1.0, 900.0]])
+    with rb.Context(rb.RB_PREC_MIXED, max_iter=1) as ctx:
+        ctx.load_set(ops)
+        u, _, info = ctx.rb_solve(mu, n=np.array([12, 0, 13], dtype=np.int32))
+    assert info["status"][0] == rb.RB_Q_NOT_CONVERGED and info["iters"][0] == 1
+    assert info["status"][1] == rb.RB_Q_REJECTED and info["status"][2] == rb.RB_Q_REJECTED
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.rb_load_operators(np.zeros_like(ops.A), np.zeros_like(ops.C), ops.f)
+        _, _, info = ctx.rb_solve(mu)
+    assert np.all(info["status"] == rb.RB_Q_SINGULAR)
+
+
+def test_full_sweep_batch_sampled(rb):
+    """The n = 50 sweep at its full batch (4096 queries) in mixed precision: a stratified
+    sample of queries plus the corners against the oracle, and all of them against the FP64
+    GPU path."""
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl)
+    q = synth.make_queries(wl)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, p, info = ctx.rb_solve(mu)
+    with rb.Context(rb.RB_PREC_FP64) as ctx:
+        ctx.load_set(ops)
+        u64, p64, info64 = ctx.rb_solve(mu)
+    assert np.all(info["status"] == 0) and np.all(info64["status"] == 0)
+    assert rel(u, u64).max() <= TOL_MIXED
+    idx = np.concatenate([np.argsort(mu[:-4, 1])[:: len(mu) // 60][:60],
+                          np.arange(len(mu) - 4, len(mu))])
+    o = oracle.Oracle.from_set(ops)
+    u_ref, p_ref, _ = o.solve(mu[idx], threads=16)
+    assert rel(u[idx], u_ref).max() <= TOL_MIXED
+    assert rel(p[idx], p_ref).max() <= 10 * TOL_MIXED
