@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-PREC = {"fp64": 0, "mixed": 1, "fp32": 2}
+PREC = {"fp64": 0, "mixed": 1}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -235,6 +235,7 @@ def main():
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
+    ctx.rb_profile(True)  # per-kernel CUDA events on the launching stream, timed region only
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -248,6 +249,8 @@ def main():
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
+    kprof = ctx.rb_profile_read()
+    ctx.rb_profile(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(step_ms) / 1e3
     if world > 1:
@@ -259,7 +262,7 @@ def main():
     info = d_info.cpu().numpy().view(rb.INFO_DTYPE).reshape(batch)
     u_gpu = d_u.cpu().numpy()
     p_gpu = d_p.cpu().numpy() if d_p is not None else None
-    launches_per_step = ctx_launches(ctx, prec, info)
+    launches_total = sum(v[1] for v in kprof.values())
 
     # end-to-end through the public host-buffer API, pinned host memory
     h_mu = torch.from_numpy(q.mu).pin_memory()
@@ -284,13 +287,13 @@ def main():
     d2h = batch * wl.n_max * 8 + (batch * m * 8 if m else 0) + batch * 32
 
     # roofline of the dominant kernel, measured live with events on the launching stream
-    roof = dominant_kernel_roofline(ctx, prec, wl, q, info, stream, flush, args)
+    roof, kernels = dominant_kernel_roofline(prec, wl, q, info, kprof, args.steps)
 
     line = {
         "metric": "reduced Newton solves/s", "value": value, "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16+f32+f64" if prec == 1 else ("f64" if prec == 0 else "f32+f64"),
+        "vs_baseline": None, "dtype": "bf16+f32+f64" if prec == 1 else "f64",
         "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n_max, "q_a": wl.q_a, "q_c": wl.q_c,
                    "q_f": wl.q_f, "m": m, "batch_per_gpu": batch, "precision": args.precision,
@@ -301,7 +304,8 @@ def main():
         "status_ok": int((info["status"] == 0).sum()),
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches_per_step * args.steps),
+        "gpu_launches": int(launches_total),
+        "kernels": kernels,
         "clocks": clk,
         "wall_s": wall,
     }
@@ -325,68 +329,49 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def ctx_launches(ctx, prec, info):
-    """Kernels of librb launched per step."""
-    if prec == 0:
-        return 2  # fused Newton + pressure
-    return ctx_mixed_launches(ctx, info)
+FP64_PEAK_TFLOPS = 1.196  # DFMA probe on this machine's GB300 (152 SMs at 2070 MHz)
+DIGITS = int(os.environ.get("RB_DIGITS", "6"))            # convection segment
+DIGITS_LIN = int(os.environ.get("RB_DIGITS_LINEAR", "7"))  # linear (A) segment
 
 
-def ctx_mixed_launches(ctx, info):
-    import ctypes
-    from paper_1807_11866_gb300 import rb
-    L = rb.library()
-    if hasattr(L, "rb_debug_last_launches"):
-        L.rb_debug_last_launches.restype = ctypes.c_int
-        L.rb_debug_last_launches.argtypes = [ctypes.c_void_p]
-        return L.rb_debug_last_launches(ctx.h)
-    return 0
-
-
-def dominant_kernel_roofline(ctx, prec, wl, q, info, stream, flush, args):
-    import torch
+def dominant_kernel_roofline(prec, wl, q, info, kprof, steps):
+    """Roofline of the kernel with the largest device time in the timed region.
+    Algorithmic work counts only the useful part: per active query-iteration of size n,
+      fused FP64 Newton: 2 (Q_c n^3 + Q_a n^2) + 2 n^3 / 3 + 2 n^2  FLOP (FP64),
+      sliced residual GEMM: 2 n^2 (P0 Q_c n + P1 Q_a) FLOP of BF16 digit products
+        (P = S (S + 1) / 2 digit pairs per segment),
+      sliced pressure GEMM: 2 m n (P0 Q_c n + P1 Q_a) per converged query,
+      Jacobian GEMM: 2 Q_c n^3 FLOP (BF16)."""
     peaks, kind = measured_peaks()
-    n = q.n
-    iters = info["iters"].astype(np.float64)
-    if prec == 0:
-        # the fused FP64 Newton kernel is the step; FP64 ALU bound
-        flops = algorithmic_flops(wl, n, wl.q_c, wl.q_a, iters)
-        ms = time_fp64_kernel(ctx, q, stream, flush, args)
+    n = q.n.astype(np.float64)
+    it = info["iters"].astype(np.float64)
+    tot_ms = sum(v[0] for v in kprof.values()) or 1.0
+    kernels = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps,
+                   "share": v[0] / tot_ms} for k, v in kprof.items() if v[1]}
+    dom = max(kprof, key=lambda k: kprof[k][0])
+    ms, launches = kprof[dom]
+    # info holds one step's iteration counts; the timed region ran `steps` identical steps
+    if dom == "k_newton_fp64":
+        flops = steps * float(np.sum(it * (2 * (wl.q_c * n ** 3 + wl.q_a * n ** 2) + 2 * n ** 3 / 3 + 2 * n ** 2)))
         ach = flops / (ms * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS
-        return {"bound": "alu", "kernel": "k_newton_fp64", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "FP64 DFMA peak derived from SM count x FP64 rate x max clock"}
-    return mixed_roofline(ctx, wl, q, info, stream, flush, args, peaks, kind)
-
-
-FP64_PEAK_TFLOPS = 1.25
-
-
-def time_fp64_kernel(ctx, q, stream, flush, args):
-    import torch
-    from paper_1807_11866_gb300 import rb
-    batch = len(q.mu)
-    dev = flush.device
-    d_mu = torch.from_numpy(q.mu).to(dev)
-    d_n = torch.from_numpy(q.n).to(dev)
-    d_u = torch.empty((batch, ctx.n_max), dtype=torch.float64, device=dev)
-    d_info = torch.empty((batch, 4), dtype=torch.float64, device=dev)
-    ts = []
-    with torch.cuda.stream(stream):
-        for i in range(max(2, args.steps)):
-            flush.zero_()
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            ctx.rb_solve_device(d_mu, batch, d_n, d_u, None, d_info, stream.cuda_stream)
-            e.record(stream)
-            ts.append((s, e))
-    torch.cuda.synchronize()
-    return float(np.mean([s.elapsed_time(e) for s, e in ts]))
-
-
-def mixed_roofline(ctx, wl, q, info, stream, flush, args, peaks, kind):
-    return None
+        return ({"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                 "peak_source": "measured FP64 FMA probe (152 SMs, 2070 MHz)",
+                 "launches": launches}, kernels)
+    p0, p1 = DIGITS * (DIGITS + 1) // 2, DIGITS_LIN * (DIGITS_LIN + 1) // 2
+    if dom == "k_tc_gemm<sliced>":
+        per_q = 2.0 * n ** 2 * (p0 * wl.q_c * n + p1 * wl.q_a)
+    elif dom == "k_tc_gemm<sliced,pressure>":
+        per_q = 2.0 * wl.m * n * (p0 * wl.q_c * n + p1 * wl.q_a) / np.maximum(it, 1)
+    else:
+        per_q = 2.0 * wl.q_c * n ** 3
+    flops = steps * float(np.sum(it * per_q))
+    ach = flops / (ms * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    return ({"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "frac": ach / peak, "traffic": None,
+             "peak_source": f"bf16 sustained, {kind} (MEASURED_PEAKS.json)",
+             "launches": launches}, kernels)
 
 
 def plain_fp64(rb, ops, q, batch, dev, flush, args):

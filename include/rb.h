@@ -178,6 +178,24 @@ int rb_eval(rb_ctx *ctx, const double *mu, int n_queries, int n, const double *u
 int rb_gepp_solve(rb_ctx *ctx, int n, int batch, const double *M, const double *rhs,
                   double *x_out, int *status);
 
+/* ---- per-kernel timing ------------------------------------------------------------------
+ * While enabled, every kernel the context launches is bracketed by CUDA events on its
+ * launching stream; rb_profile_read returns the accumulated device time and launch count of
+ * one kernel kind. rb_profile(ctx, 1) resets the counters; timing adds about 1 us per launch. */
+enum {
+  RB_K_NEWTON_FP64 = 0,  /* fused FP64 Newton (one CTA per query) */
+  RB_K_PRESSURE = 1,     /* pressure recovery (FP64 path) / B(mu) p = r solve (mixed) */
+  RB_K_BUILD_X = 2,      /* mixed: operand build (theta (x) u, digit slices) */
+  RB_K_GEMM_JAC = 3,     /* mixed: tcgen05 Jacobian contraction (BF16 -> FP32) */
+  RB_K_GEMM_RES = 4,     /* mixed: tcgen05 sliced residual contraction (-> FP64) */
+  RB_K_LU = 5,           /* mixed: FP32 LU, triangular solves, update, stopping test */
+  RB_K_INIT = 6,         /* mixed: batch initialisation */
+  RB_K_GEMM_PRES = 7,    /* mixed: tcgen05 sliced pressure right-hand side (-> FP64) */
+  RB_K_COUNT = 8
+};
+int rb_profile(rb_ctx *ctx, int enable);
+int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launches);
+
 /* ---- serving: continuous batching at Newton-iteration granularity --------------------
  * A host thread admits queries into device slots while memory allows and advances every
  * active slot by one Newton iteration per step; converged queries leave and waiting ones

@@ -1,28 +1,32 @@
 // k_tc_gemm.cu -- the tensor-Jacobian contraction of Sec. 3.6 as a dense GEMM on the tcgen05
 // tensor cores, for a whole batch of queries.
 //
-// GEMM form: rows b = queries (M), columns c = (k, j) of the n_b x n_b Jacobian (N),
-// reduction kappa = (q, l) (K):
-//     T[b][c] = sum_kappa X[b][kappa] * W[c][kappa],
-//     X[b][(q,l)] = s * theta^c_q(mu_b) u_b[l],   W[(k,j)][(q,l)] = D~_q[k][j][l]
-// with D~_q[k][j][l] = C_q[l][j][k] + C_q[j][l][k] (both index orders of Sec. 3.6 summed once at
-// load). With s = 1, T is the convection Jacobian J^c(u_b); with s = 1/2, sum_j T[b][(k,j)] u_b[j]
-// is the convection term C_mu(u_b, u_b)[k] (Euler identity of a quadratic form).
+// GEMM form: rows b = queries (M), columns c = (k, j) (N), reduction kappa (K):
+//     T[b][c] = sum_kappa X[b][kappa] * W[c][kappa].
+// Jacobian/residual: kappa = (q, l), X[b][(q,l)] = s theta^c_q(mu_b) u_b[l],
+// W[(k,j)][(q,l)] = D~_q[k][j][l] = C_q[l][j][k] + C_q[j][l][k] (both index orders of Sec. 3.6
+// summed once at load). With s = 1, T is the convection Jacobian J^c(u_b); with s = 1/2,
+// sum_j T[b][(k,j)] u_b[j] = C_mu(u_b, u_b)[k] (Euler identity of the quadratic term).
+// A second K segment kappa = q with X[b][q] = theta^a_q(mu_b), W[(k,j)][q] = A_q[k][j] adds
+// A(mu)[k][j], so the contraction with u gives A(mu) u + C_mu(u, u) (Eq. velonly without f).
+// The pressure right-hand side (Eq. sup-vvar) uses the same X with W = (2 Cs, As).
 //
 // Two epilogues:
 //  * kPlain: X, W rounded to BF16, FP32 accumulation; writes T (FP32) -> Jacobian for the LU.
-//  * kSliced: error-free sliced product (after Ozaki et al., 2012) for the FP64-accurate
-//    residual. X rows and W are split into S signed 7-bit digit slices on fixed-point grids
-//    (per-row exponent for X, one exponent for W): X = 2^ex sum_i x_i 2^-7i, W = 2^ew sum_j w_j 2^-7j.
-//    Products of two digits are below 2^14, so up to 1024 of them add exactly in an FP32
-//    accumulator. Pairs (i, j) with i + j = L share the scale 2^(ex + ew - 7L); the kernel
-//    accumulates each level in TMEM chunks of at most 1024 terms, drains every chunk exactly,
-//    contracts it with u_b[j] in double-float arithmetic, and adds the level-scaled result into
-//    the FP64 output R^c[b][k]. Pairs with i + j > S + 1 are dropped (truncation 2^-7S relative).
+//  * kSliced: error-free sliced product (after Ozaki, Ogita, Oishi and Rump, 2012). Per segment,
+//    X rows and W are split into S signed 7-bit digit slices on fixed-point grids (per-row
+//    exponent for X, one exponent for W): X = 2^ex sum_i x_i 2^-7i, W = 2^ew sum_j w_j 2^-7j
+//    (S may differ per segment).
+//    A product of two digits is below 2^14, so up to 1024 of them add exactly in FP32. Pairs
+//    (i, j) with i + j = L share the scale 2^(ex + ew - 7L); each level is accumulated in TMEM
+//    in chunks of at most 1024 terms, every chunk is drained exactly, contracted with u_b[j] in
+//    double-float arithmetic and added, scaled, into the FP64 output. Pairs with i + j > S + 1
+//    are dropped (relative truncation ~2^-7S of the fixed-point range).
 //
-// Roles (192 threads): warp 0 issues TMA loads into a STAGES-deep shared-memory ring, warp 1
-// allocates TMEM and issues tcgen05.mma (one elected lane), warps 2-5 drain the two TMEM
-// accumulator buffers (128 lanes = 128 query rows). Persistent over output tiles.
+// Roles (320 threads): warp 0 issues TMA loads into a STAGES-deep shared-memory ring, warp 1
+// allocates TMEM and issues tcgen05.mma (one lane), warps 2-9 drain the two TMEM accumulator
+// buffers (128 lanes = 128 query rows; two warps per lane quarter split the columns).
+// Persistent over output tiles (m fastest).
 #include <cuda.h>
 
 #include "rb_mixed.cuh"
@@ -33,63 +37,84 @@ namespace rb {
 using namespace tc;
 
 constexpr int kBM = 128, kBK = 64;
-constexpr int kStages = 4;
 constexpr int kChunkSteps = 16;  // 16 k-blocks of 64 = 1024 exact terms per chunk (7-bit digits)
+constexpr int kEpiWarps = 8;     // epilogue warps: 2 per TMEM lane quarter
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreadsTc = 64 + kEpiThreads;
+// Levels whose scale is at most 2^-21 of the leading level are contracted in plain FP32: their
+// rounding (2^-24 relative) stays below 2^-45 of the result.
+constexpr int kFastLevel = 5;
 
-template <int BN>
+template <int BN, int STAGES, int UW>
 struct TcSmem {
   static constexpr int kTileA = kBM * kBK * 2;
   static constexpr int kTileB = BN * kBK * 2;
   static constexpr int kStage = kTileA + kTileB;
-  static constexpr int kBarOff = kStages * kStage;
+  static constexpr int kUOff = STAGES * kStage;        // u window: [UW][kBM] float2
+  static constexpr int kBarOff = kUOff + UW * kBM * 8;
   static constexpr int kBytes = kBarOff + 256 + 1024;  // barriers + alignment slack
 };
 
 struct Level {
-  int L, ilo, npairs;
+  int seg, kb_off, kb, L, ilo, npairs;
 };
 
-__device__ __forceinline__ Level level_of(int mode, int S, int li) {
+// The (segment, level) sequence every role walks through for one output tile.
+__device__ __forceinline__ int num_levels(int mode, const TcGemmParams &p) {
+  if (mode == kPlain) return 1;
+  return (p.kb[0] > 0 ? p.S[0] : 0) + (p.kb[1] > 0 ? p.S[1] : 0);
+}
+
+__device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int idx) {
   Level v;
   if (mode == kPlain) {
-    v.L = 0; v.ilo = 1; v.npairs = 1;
-  } else {
-    v.L = li + 2;
-    v.ilo = max(1, v.L - S);
-    v.npairs = min(S, v.L - 1) - v.ilo + 1;
+    v.seg = 0; v.kb_off = 0; v.kb = p.kb[0]; v.L = 0; v.ilo = 1; v.npairs = 1;
+    return v;
   }
+  const int n0 = p.kb[0] > 0 ? p.S[0] : 0;  // levels of segment 0
+  v.seg = idx < n0 ? 0 : 1;
+  const int S = p.S[v.seg];
+  v.kb_off = v.seg == 0 ? 0 : p.kb[0];
+  v.kb = p.kb[v.seg];
+  v.L = (idx - (v.seg ? n0 : 0)) + 2;
+  v.ilo = max(1, v.L - S);
+  v.npairs = min(S, v.L - 1) - v.ilo + 1;
   return v;
 }
 
-template <int MODE, int BN>
-__global__ void __launch_bounds__(192, 1)
+template <int MODE, int BN, int STAGES, int UW>
+__global__ void __launch_bounds__(kThreadsTc, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
               TcGemmParams p) {
   extern __shared__ uint8_t smem_raw[];
-  using SM = TcSmem<BN>;
+  using SM = TcSmem<BN, STAGES, UW>;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + SM::kBarOff);
-  uint64_t *empty = full + kStages;
-  uint64_t *tfull = empty + kStages;   // [2]
-  uint64_t *tempty = tfull + 2;        // [2]
-  uint64_t *mdone = tempty + 2;        // [1]
-  uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
+  uint64_t *empty = full + STAGES;
+  uint64_t *tfull = empty + STAGES;  // [2]
+  uint64_t *tempty = tfull + 2;      // [2]
+  uint64_t *mdone = tempty + 2;      // [1]
+  uint64_t *ufull = mdone + 1;       // [1] u window loaded (epilogue threads)
+  uint64_t *uempty = ufull + 1;      // [1] u window no longer read (epilogue threads)
+  uint32_t *tmem_slot = (uint32_t *)(uempty + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_levels = (MODE == kPlain) ? 1 : p.S;
+  const int n_levels = num_levels(MODE, p);
   const int chunk_steps = (MODE == kPlain) ? (1 << 30) : kChunkSteps;
   const int num_tiles = p.m_tiles * p.n_tiles;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], kEpiThreads);
     }
     mbar_init(mdone, 1);
+    mbar_init(ufull, kEpiThreads);
+    mbar_init(uempty, kEpiThreads);
     fence_barrier_init();
     fence_proxy_async();
   }
@@ -112,15 +137,15 @@ __global__ void __launch_bounds__(192, 1)
       for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
         const int m0 = (t % p.m_tiles) * kBM, n0 = (t / p.m_tiles) * BN;
         for (int li = 0; li < n_levels && !bad; ++li) {
-          const Level lv = level_of(MODE, p.S, li);
-          const int nsteps = lv.npairs * p.kb;
+          const Level lv = level_of(MODE, p, li);
+          const int nsteps = lv.npairs * lv.kb;
           for (int idx = 0; idx < nsteps; ++idx, ++step) {
-            const int s = step % kStages;
-            const uint32_t ph = (step / kStages) & 1;
+            const int s = step % STAGES;
+            const uint32_t ph = (step / STAGES) & 1;
             if (!mbar_wait(&empty[s], ph ^ 1, p.err, 1)) { bad = true; break; }
             uint8_t *sa = smem + s * SM::kStage;
             uint8_t *sb = sa + SM::kTileA;
-            const int pr = idx / p.kb, kk = idx % p.kb;
+            const int pr = idx / lv.kb, kk = lv.kb_off + idx % lv.kb;
             const int xi = (MODE == kPlain) ? 0 : (lv.ilo + pr - 1);
             const int wj = (MODE == kPlain) ? 0 : (lv.L - (lv.ilo + pr) - 1);
             mbar_expect_tx(&full[s], SM::kStage);
@@ -131,9 +156,8 @@ __global__ void __launch_bounds__(192, 1)
       }
       if (bad) {  // let loads already in flight land before the CTA exits
         const uint32_t last = step;
-        for (uint32_t st = (last > (uint32_t)kStages ? last - kStages : 0); st < last; ++st) {
-          mbar_wait(&full[st % kStages], (st / kStages) & 1, nullptr, 1);
-        }
+        for (uint32_t st = (last > (uint32_t)STAGES ? last - STAGES : 0); st < last; ++st)
+          mbar_wait(&full[st % STAGES], (st / STAGES) & 1, nullptr, 1);
       }
     }
   } else if (warp == 1) {
@@ -144,8 +168,8 @@ __global__ void __launch_bounds__(192, 1)
       bool bad = false;
       for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
         for (int li = 0; li < n_levels && !bad; ++li) {
-          const Level lv = level_of(MODE, p.S, li);
-          const int nsteps = lv.npairs * p.kb;
+          const Level lv = level_of(MODE, p, li);
+          const int nsteps = lv.npairs * lv.kb;
           for (int c0 = 0; c0 < nsteps && !bad; c0 += chunk_steps, ++chunk) {
             const int buf = chunk & 1;
             const uint32_t tph = (chunk >> 1) & 1;
@@ -154,8 +178,8 @@ __global__ void __launch_bounds__(192, 1)
             const uint32_t dt = tmem_base + buf * BN;
             const int c1 = min(nsteps, c0 + chunk_steps);
             for (int idx = c0; idx < c1; ++idx, ++step) {
-              const int s = step % kStages;
-              const uint32_t ph = (step / kStages) & 1;
+              const int s = step % STAGES;
+              const uint32_t ph = (step / STAGES) & 1;
               if (!mbar_wait(&full[s], ph, p.err, 3)) { bad = true; break; }
               tc_fence_after();
               const uint32_t sa = smem_u32(smem + s * SM::kStage);
@@ -174,17 +198,35 @@ __global__ void __launch_bounds__(192, 1)
       mbar_wait(mdone, 0, nullptr, 4);
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
-    const int q = warp & 3;              // TMEM lane quarter of this warp
-    const int row = q * 32 + lane;       // row of the tile
-    uint32_t chunk = 0;
+    // ---------------- epilogue (warps 2..9) ----------------
+    const int q = warp & 3;                  // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;        // which half of the tile's columns
+    const int row = q * 32 + lane;           // row of the tile owned by this thread
+    const int et = (warp - 2) * 32 + lane;   // epilogue thread index
+    constexpr int HC = BN / 2;               // columns per thread
+    float2 *uw = (float2 *)(smem + SM::kUOff);
+    uint32_t chunk = 0, tile_it = 0;
     bool bad = false;
-    for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
+    for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x, ++tile_it) {
       const int m0 = (t % p.m_tiles) * kBM, n0 = (t / p.m_tiles) * BN;
       const int b = m0 + row;
+      const int nj = p.nj, total = p.nk * p.nj;
+      const int jb = n0 % nj;
+      if (MODE == kSliced) {
+        // window of u_b[j] for the tile's columns, [w][row]; the two halves load alternate
+        // entries and share them (bounded mbarrier handoff, no unbounded named barrier)
+        if (tile_it > 0 && !mbar_wait(uempty, (tile_it - 1) & 1, p.err, 6)) { bad = true; break; }
+        const int wl = nj <= UW ? nj : BN;
+        for (int w = half; w < wl; w += 2) {
+          const int j = nj <= UW ? w : (jb + w) % nj;
+          uw[w * kBM + row] = p.ufT[(size_t)j * p.b_pad + b];
+        }
+        mbar_arrive(ufull);
+        if (!mbar_wait(ufull, tile_it & 1, p.err, 7)) { bad = true; break; }
+      }
       for (int li = 0; li < n_levels && !bad; ++li) {
-        const Level lv = level_of(MODE, p.S, li);
-        const int nsteps = lv.npairs * p.kb;
+        const Level lv = level_of(MODE, p, li);
+        const int nsteps = lv.npairs * lv.kb;
         for (int c0 = 0; c0 < nsteps; c0 += chunk_steps, ++chunk) {
           const int buf = chunk & 1;
           const uint32_t tph = (chunk >> 1) & 1;
@@ -192,11 +234,11 @@ __global__ void __launch_bounds__(192, 1)
           const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], tph, p.err, 5));
           if (!ok) { bad = true; break; }
           tc_fence_after();
-          const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + buf * BN;
+          const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + buf * BN + half * HC;
           if (MODE == kPlain) {
-            float *out = p.Jc + (size_t)b * p.ldj + n0;
+            float *out = p.Jc + (size_t)b * p.ldj + n0 + half * HC;
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
+            for (int c = 0; c < HC; c += 32) {
               uint32_t r[32];
               tmem_ld_x32(taddr + c, r);
               tmem_ld_wait();
@@ -207,52 +249,67 @@ __global__ void __launch_bounds__(192, 1)
                                     __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
             }
           } else {
-            // contract the exact chunk with u_b[j] over the tile's columns (k, j)
+            // contract the exact chunk with u_b[j] over this thread's columns (k, j)
             const bool live = b < p.nq;
-            const int nb = p.nb, nn = nb * nb;
-            const double scale = live ? ldexp(1.0, p.xexp[b] + p.wexp - 7 * lv.L) : 0.0;
-            const float2 *ub = p.uf + (size_t)b * nb;
-            int g = n0, k = n0 / nb, j = n0 - (n0 / nb) * nb;
-            float ah = 0.f, al = 0.f;
+            const bool fast = lv.L >= kFastLevel + 2;
+            const double scale =
+                live ? ldexp(1.0, p.xexp[lv.seg * p.b_pad + b] + p.wexp[lv.seg] - kDigitBits * lv.L)
+                     : 0.0;
+            const int c_begin = n0 + half * HC;
+            int g = c_begin, k = c_begin / nj, j = c_begin % nj;
+            int jw = nj <= UW ? j : (j - jb + nj) % nj;
+            // four independent double-float accumulators (ILP), merged at each row end
+            float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
+            for (int c = 0; c < HC; c += 32) {
               uint32_t r[32];
               tmem_ld_x32(taddr + c, r);
               tmem_ld_wait();
               if (live) {
 #pragma unroll
                 for (int v = 0; v < 32; ++v, ++g) {
-                  if (g < nn) {
+                  if (g < total) {
                     const float x = __uint_as_float(r[v]);
-                    const float2 u2 = ub[j];
-                    // x * (uh + ul) as p + e + x*ul, p = fl(x*uh) and e its exact error
-                    const float pp = x * u2.x;
-                    const float e = fmaf(x, u2.x, -pp);
-                    const float tl = fmaf(x, u2.y, e);
-                    // two-sum (ah, pp)
-                    const float s = ah + pp;
-                    const float bb = s - ah;
-                    const float er = (ah - (s - bb)) + (pp - bb);
-                    ah = s;
-                    al += er + tl;
-                    if (++j == nb) {
-                      atomicAdd(p.Rc + (size_t)b * nb + k, ((double)ah + (double)al) * scale);
-                      ah = al = 0.f;
+                    const float2 u2 = uw[jw * kBM + row];
+                    if (fast) {
+                      ah[v & 3] = fmaf(x, u2.x, ah[v & 3]);
+                    } else {
+                      // x (uh + ul) = pp + e + x ul, pp = fl(x uh), e its exact error
+                      const float pp = x * u2.x;
+                      const float e = fmaf(x, u2.x, -pp);
+                      const float tl = fmaf(x, u2.y, e);
+                      const float a = ah[v & 3];
+                      const float s = a + pp;  // two-sum (a, pp)
+                      const float bb = s - a;
+                      al[v & 3] += ((a - (s - bb)) + (pp - bb)) + tl;
+                      ah[v & 3] = s;
+                    }
+                    ++jw;
+                    if (++j == nj) {
+                      const double tot = ((double)ah[0] + (double)ah[1]) + ((double)ah[2] + (double)ah[3]) +
+                                         (((double)al[0] + (double)al[1]) + ((double)al[2] + (double)al[3]));
+                      atomicAdd(p.out + (size_t)b * p.nk + k, tot * scale);
+#pragma unroll
+                      for (int i = 0; i < 4; ++i) ah[i] = al[i] = 0.f;
                       j = 0;
                       ++k;
+                      if (nj <= UW) jw = 0;
                     }
                   }
                 }
               }
             }
-            if (live && (ah != 0.f || al != 0.f) && k < nb)
-              atomicAdd(p.Rc + (size_t)b * nb + k, ((double)ah + (double)al) * scale);
+            if (live && k < p.nk) {
+              const double tot = ((double)ah[0] + (double)ah[1]) + ((double)ah[2] + (double)ah[3]) +
+                                 (((double)al[0] + (double)al[1]) + ((double)al[2] + (double)al[3]));
+              if (tot != 0.0) atomicAdd(p.out + (size_t)b * p.nk + k, tot * scale);
+            }
           }
           tc_fence_before();
           mbar_arrive(&tempty[buf]);
         }
-        if (bad) break;
       }
+      if (MODE == kSliced) mbar_arrive(uempty);
     }
   }
   tc_fence_before();
@@ -265,14 +322,14 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 // ---------------------------------------------------------------------------------------
-template <int MODE, int BN>
+template <int MODE, int STAGES, int UW>
 static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
                                const TcGemmParams &p, int grid, cudaStream_t st) {
-  const int smem = TcSmem<BN>::kBytes;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<MODE, BN>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem = TcSmem<kTcBN, STAGES, UW>::kBytes;
+  auto kern = k_tc_gemm<MODE, kTcBN, STAGES, UW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_tc_gemm<MODE, BN><<<grid, 192, smem, st>>>(tmX, tmW, p);
+  kern<<<grid, kThreadsTc, smem, st>>>(tmX, tmW, p);
   return cudaGetLastError();
 }
 
@@ -280,8 +337,9 @@ cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &
                            const TcGemmParams &p, int sms, cudaStream_t st) {
   const int tiles = p.m_tiles * p.n_tiles;
   const int grid = tiles < sms ? tiles : sms;
-  if (mode == kPlain) return launch_impl<kPlain, kTcBN>(tmX, tmW, p, grid, st);
-  return launch_impl<kSliced, kTcBN>(tmX, tmW, p, grid, st);
+  if (mode == kPlain) return launch_impl<kPlain, 4, 0>(tmX, tmW, p, grid, st);
+  if (p.nj <= 64) return launch_impl<kSliced, 4, 64>(tmX, tmW, p, grid, st);
+  return launch_impl<kSliced, 3, 128>(tmX, tmW, p, grid, st);
 }
 
 }  // namespace rb

@@ -42,6 +42,15 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
 void mixed_release(rb_ctx *ctx);
 void serve_shutdown(rb_ctx *ctx);
 
+// per-kernel event timing (active only while profiling is enabled)
+struct ProfMark {
+  int kind;
+  cudaEvent_t a, b;
+};
+int prof_begin(rb_ctx *ctx, int kind, cudaStream_t st);  // returns a mark index or -1
+void prof_end(rb_ctx *ctx, int mark, cudaStream_t st);
+void prof_collect(rb_ctx *ctx);  // waits for recorded marks and accumulates them
+
 }  // namespace rb
 
 struct rb_ctx {
@@ -59,5 +68,11 @@ struct rb_ctx {
   // scratch
   rb::Scratch stage, jscratch, info_scratch, eval_scratch;
   rb::MixedState *mixed = nullptr;
+  // profiling
+  bool prof = false;
+  std::vector<rb::ProfMark> marks;
+  std::vector<cudaEvent_t> event_pool;
+  double prof_ms[RB_K_COUNT] = {};
+  long long prof_n[RB_K_COUNT] = {};
   rb::ServeState *serve = nullptr;
 };

@@ -30,11 +30,11 @@ __device__ __forceinline__ double trig_q(int q, double a) {
   return (q & 1) ? sin((double)q * a) : cos((double)q * a);
 }
 
-// theta row of one query into th[0..n_theta): [a | c | f | b]. Called by all threads.
-__device__ __forceinline__ void theta_eval(const DevOps &o, double alpha_deg, double re,
-                                           double *th) {
+// theta row of one query into th[0..n_theta): [a | c | f | b], entries start, start + stride, ...
+__device__ __forceinline__ void theta_eval_strided(const DevOps &o, double alpha_deg, double re,
+                                                   double *th, int start, int stride) {
   const double a = alpha_deg * 0.017453292519943295769;  // pi / 180
-  for (int i = threadIdx.x; i < o.n_theta; i += blockDim.x) {
+  for (int i = start; i < o.n_theta; i += stride) {
     int q = i;
     double scale = 1.0;
     if (q < o.q_a) {
@@ -48,6 +48,12 @@ __device__ __forceinline__ void theta_eval(const DevOps &o, double alpha_deg, do
     }
     th[i] = trig_q(q, a) * scale;
   }
+}
+
+// theta row of one query, all threads of the block
+__device__ __forceinline__ void theta_eval(const DevOps &o, double alpha_deg, double re,
+                                           double *th) {
+  theta_eval_strided(o, alpha_deg, re, th, threadIdx.x, blockDim.x);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -76,42 +82,49 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 // (|value|, row) argmax with the first row winning ties.
-__device__ __forceinline__ void argmax_merge(double &v, int &r, double v2, int r2) {
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T &v, int &r, T v2, int r2) {
   if (v2 > v || (v2 == v && r2 < r)) { v = v2; r = r2; }
 }
 
 // Solve M x = b in place by Gaussian elimination with partial pivoting (pivot = first row
-// of largest magnitude), block-cooperative. M: n x n with row stride ld (shared or global),
-// b: shared, overwritten by x. red: >= 2 * kWarps + 2 doubles of shared scratch.
+// of largest magnitude), block-cooperative, every operation in the precision T (FP32 work
+// stays off the FP64 pipe). M: n x n with row stride ld (shared or global), b: shared,
+// overwritten by x. red: >= 2 * kWarps + 2 doubles of shared scratch.
 // Returns true if a pivot was zero or not finite (b is then unspecified).
 template <typename T>
 __device__ bool gepp_solve_block(T *M, int ld, int n, T *b, double *red) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  int *ired = reinterpret_cast<int *>(red + 2 * kWarps);
+  T *tred = reinterpret_cast<T *>(red);
+  int *ired = reinterpret_cast<int *>(red + kWarps + 1);
   for (int p = 0; p < n; ++p) {
-    // pivot search over rows p..n-1 of column p
-    double best = -1.0;
-    int brow = n;
-    for (int i = p + tid; i < n; i += blockDim.x) argmax_merge(best, brow, fabs((double)M[(size_t)i * ld + p]), i);
+    // pivot search over rows p..n-1 of column p, only by the warps that hold rows
+    const int rows = n - p;
+    if (w * 32 < rows) {
+      T best = T(-1);
+      int brow = n;
+      for (int i = p + tid; i < n; i += blockDim.x) argmax_merge<T>(best, brow, fabs(M[(size_t)i * ld + p]), i);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double v2 = __shfl_xor_sync(0xffffffffu, best, o);
-      int r2 = __shfl_xor_sync(0xffffffffu, brow, o);
-      argmax_merge(best, brow, v2, r2);
+      for (int o = 16; o > 0; o >>= 1) {
+        const T v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int r2 = __shfl_xor_sync(0xffffffffu, brow, o);
+        argmax_merge<T>(best, brow, v2, r2);
+      }
+      if (lane == 0) { tred[w] = best; ired[w] = brow; }
     }
-    if (lane == 0) { red[w] = best; ired[w] = brow; }
     __syncthreads();
     if (tid == 0) {
-      double bv = red[0];
+      T bv = tred[0];
       int br = ired[0];
-      for (int i = 1; i < kWarps; ++i) argmax_merge(bv, br, red[i], ired[i]);
-      red[kWarps] = bv;
+      const int nw = min(kWarps, (rows + 31) / 32);
+      for (int i = 1; i < nw; ++i) argmax_merge<T>(bv, br, tred[i], ired[i]);
+      tred[kWarps] = bv;
       ired[kWarps] = br;
     }
     __syncthreads();
-    const double pv = red[kWarps];
+    const T pv = tred[kWarps];
     const int r = ired[kWarps];
-    if (!(pv > 0.0) || !isfinite(pv)) return true;
+    if (!(pv > T(0)) || !isfinite(pv)) return true;
     if (r != p) {
       for (int j = p + tid; j < n; j += blockDim.x) {
         T t = M[(size_t)p * ld + j];
@@ -124,7 +137,6 @@ __device__ bool gepp_solve_block(T *M, int ld, int n, T *b, double *red) {
     const T piv = M[(size_t)p * ld + p];
     for (int i = p + 1 + tid; i < n; i += blockDim.x) M[(size_t)i * ld + p] = M[(size_t)i * ld + p] / piv;
     __syncthreads();
-    const int rem = n - p - 1;
     const T bp = b[p];
     // trailing update, one warp per row
     for (int i = p + 1 + w; i < n; i += kWarps) {
@@ -134,20 +146,65 @@ __device__ bool gepp_solve_block(T *M, int ld, int n, T *b, double *red) {
       for (int j = p + 1 + lane; j < n; j += 32) Mi[j] -= lip * Mp[j];
       if (lane == 0) b[i] -= lip * bp;
     }
-    (void)rem;
     __syncthreads();
   }
   // back substitution by warp 0
   if (w == 0) {
     for (int i = n - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int j = i + 1 + lane; j < n; j += 32) s += (double)M[(size_t)i * ld + j] * (double)b[j];
+      T s = T(0);
+      for (int j = i + 1 + lane; j < n; j += 32) s += M[(size_t)i * ld + j] * b[j];
       s = warp_sum(s);
-      if (lane == 0) b[i] = (T)(((double)b[i] - s) / (double)M[(size_t)i * ld + i]);
+      if (lane == 0) b[i] = (b[i] - s) / M[(size_t)i * ld + i];
       __syncwarp();
     }
   }
   __syncthreads();
+  return false;
+}
+
+// Warp-cooperative variant of gepp_solve_block for one small system per warp (no block
+// barriers): same pivoting rule, same operation order per entry.
+template <typename T>
+__device__ bool gepp_solve_warp(T *M, int ld, int n, T *b) {
+  const int lane = threadIdx.x & 31;
+  for (int p = 0; p < n; ++p) {
+    T best = T(-1);
+    int brow = n;
+    for (int i = p + lane; i < n; i += 32) argmax_merge<T>(best, brow, fabs(M[(size_t)i * ld + p]), i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int r2 = __shfl_xor_sync(0xffffffffu, brow, o);
+      argmax_merge<T>(best, brow, v2, r2);
+    }
+    if (!(best > T(0)) || !isfinite(best)) return true;
+    if (brow != p) {
+      for (int j = p + lane; j < n; j += 32) {
+        const T t = M[(size_t)p * ld + j];
+        M[(size_t)p * ld + j] = M[(size_t)brow * ld + j];
+        M[(size_t)brow * ld + j] = t;
+      }
+      if (lane == 0) { const T t = b[p]; b[p] = b[brow]; b[brow] = t; }
+    }
+    __syncwarp();
+    const T piv = M[(size_t)p * ld + p];
+    for (int i = p + 1 + lane; i < n; i += 32) M[(size_t)i * ld + p] = M[(size_t)i * ld + p] / piv;
+    __syncwarp();
+    const T bp = b[p];
+    for (int j = p + 1 + lane; j < n; j += 32) {
+      const T mpj = M[(size_t)p * ld + j];
+      for (int i = p + 1; i < n; ++i) M[(size_t)i * ld + j] -= M[(size_t)i * ld + p] * mpj;
+    }
+    for (int i = p + 1 + lane; i < n; i += 32) b[i] -= M[(size_t)i * ld + p] * bp;
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    T s = T(0);
+    for (int j = i + 1 + lane; j < n; j += 32) s += M[(size_t)i * ld + j] * b[j];
+    s = warp_sum(s);
+    if (lane == 0) b[i] = (b[i] - s) / M[(size_t)i * ld + i];
+    __syncwarp();
+  }
   return false;
 }
 

@@ -1,47 +1,60 @@
 // rb_mixed.cu -- mixed-precision batched Newton (inexact Newton, Sec. 3.6 Jacobian on tensor cores).
 //
 // Per iteration, for every active query b of the batch:
-//   1. k_build_x: X_b = theta^c(mu_b) (x) u_b (BF16) for the Jacobian GEMM, and the 7-bit digit
-//      slices of X'_b = X_b / 2 for the sliced residual GEMM; u_b as (hi, lo) floats; R^c_b = 0.
+//   1. k_build_x: X_b = theta^c(mu_b) (x) u_b (BF16) for the Jacobian GEMM; the 7-bit digit
+//      slices of [theta^c (x) u_b / 2 | theta^a(mu_b)] for the sliced GEMM; u_b as (hi, lo)
+//      floats (transposed); R_b = 0.
 //   2. k_tc_gemm<kPlain>:  J^c = X W^T on tcgen05 (BF16 in, FP32 accumulate) -> Jc (FP32).
-//   3. k_tc_gemm<kSliced>: R^c_b[k] = sum_j u_b[j] (X'_b W^T)[(k,j)], exact digit products,
-//      double-float contraction -> FP64 (the convection term C_mu(u_b, u_b), Eq. velonly).
-//   4. k_lu_mixed: R = A(mu) u - f(mu) + R^c in FP64; J = fl32(A(mu)) + J^c; GEPP in FP32 on
+//   3. k_tc_gemm<kSliced>: R_b[k] = sum_j u_b[j] (X'_b W'^T)[(k,j)] with W' = [D~ | A]:
+//      A(mu) u_b + C_mu(u_b, u_b) from exact digit products, contracted in double-float -> FP64.
+//   4. k_lu_mixed: R = (A u + C(u,u)) - f(mu); J = fl32(A(mu)) + J^c; GEPP in FP32 on
 //      J delta = -R; u += delta in FP64; stopping rule (Sec. 6) on the FP64 norms.
-// The Jacobian is inexact (BF16 convection part), the residual and the test are FP64-accurate,
-// so the iteration converges to the FP64 solution (linearly at rate ~ ||J^-1 (J~ - J)||).
+// The Jacobian is inexact (BF16 convection part, FP32 elimination); the residual and the test
+// are FP64-accurate, so the iteration converges to the FP64 solution at the linear rate
+// ||J~^-1 (J~ - J)||. After the last iteration the pressure right-hand side
+// fs(mu) - As(mu) u - Cs_mu(u, u) (Eq. sup-vvar) comes from the same sliced GEMM with W = [2 Cs | As]
+// and B(mu) p = r is solved in FP64 (Eq. blocksolve-2).
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "rb_ctx.h"
 #include "rb_mixed.cuh"
 
 namespace rb {
 
+struct SlicedW {  // one sliced weight operand [S][Npad][Kpad]
+  __nv_bfloat16 *d = nullptr;
+  int Npad = 0, nk = 0, wexp[2] = {0, 0};
+  CUtensorMap tm;
+};
+
 struct MixedState {
   // operator layouts for the Jacobian size nb (= n_max)
-  int nb = 0, K = 0, Kpad = 0, kb = 0, Npad = 0, S = 0, wexp = 0;
-  __nv_bfloat16 *Wj = nullptr;  // [Npad][Kpad]
-  __nv_bfloat16 *Wd = nullptr;  // [S][Npad][Kpad]
-  CUtensorMap tmWj, tmWd;
+  int nb = 0, Kpad0 = 0, kb0 = 0, kb1 = 0, Kpad = 0, Npad = 0, S0 = 0, S1 = 0, Smax = 0;
+  __nv_bfloat16 *Wj = nullptr;  // [Npad][Kpad0] BF16(D~)
+  CUtensorMap tmWj;
+  SlicedW WR, WP;               // residual [D~ | A], pressure [2 Cs | As]
+  float *A32 = nullptr;         // [q_a][n_max][n_max] FP32 copy of A_q
   // batch scratch
   int bcap = 0;
   __nv_bfloat16 *Xj = nullptr, *Xd = nullptr;
-  int *xexp = nullptr;
-  float2 *uf = nullptr;
-  float *Jc = nullptr;
-  double *Rc = nullptr;
+  int *xexp = nullptr;          // [2][bcap]
+  float2 *ufT = nullptr;        // [nb][bcap]
+  float *Jc = nullptr;          // [bcap][Npad]
+  double *Rc = nullptr;         // [bcap][nb]
+  double *Rp = nullptr;         // [bcap][m]
   CUtensorMap tmXj, tmXd;
   float *lu_scratch = nullptr;
   int lu_grid = 0;
-  int *dev_words = nullptr;  // [0] active count, [1] error word
-  int *h_words = nullptr;    // pinned mirror
+  int *dev_words = nullptr;     // [0] active count, [1] error word, [8..] scratch
+  int *h_words = nullptr;       // pinned mirror
   rb_query_info *info_own = nullptr;
   int info_cap = 0;
-  int last_launches = 0;
 };
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -77,8 +90,7 @@ static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 // signed 7-bit digits of v on the grid 2^(e - 7 i), i = 1..S (|v| < 2^e), truncated toward 0
 __device__ __forceinline__ void digits7(double v, double scale /* 2^(7S - e) */, int S,
                                         __nv_bfloat16 *out, size_t slice_stride) {
-  const double a = fabs(v) * scale;
-  const long long F = __double2ll_rz(a);
+  const long long F = __double2ll_rz(fabs(v) * scale);
   const float sg = v < 0 ? -1.f : 1.f;
   for (int i = 1; i <= S; ++i) {
     const int d = (int)((F >> (kDigitBits * (S - i))) & 127);
@@ -95,27 +107,56 @@ __global__ void k_absmax(const double *x, size_t count, unsigned long long *out)
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// W[(k,j)][(q,l)] = D~_q[k][j][l] from Dt [q][l][k][j] (n_max strides): BF16 copy and S digit
-// slices on the grid 2^(wexp - 7 i).
-__global__ void k_build_w(const double *Dt, int nm, int qc, int nb, int Kpad, int Npad, int S,
-                          int wexp, __nv_bfloat16 *Wj, __nv_bfloat16 *Wd) {
-  const size_t total = (size_t)Npad * Kpad;
-  const double scale = ldexp(1.0, kDigitBits * S - wexp);
+__global__ void k_to_f32(const double *x, float *y, size_t count) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
+       e += (size_t)gridDim.x * blockDim.x)
+    y[e] = (float)x[e];
+}
+
+// Sliced weight operand W[c][kappa], c = k * nb + j (k < nk, j < nb):
+//   kind 0 (residual): kappa = q * nb + l < Kpad0 -> D~_q[k][j][l] (Dt [q][l][k][j]);
+//                      kappa = Kpad0 + q          -> A_q[k][j]
+//   kind 1 (pressure): kappa = q * nb + l         -> 2 Cs_q[j][l][k] (Cs [q][j][l][m]);
+//                      kappa = Kpad0 + q          -> As_q[k][j]
+// plus, for kind 0, the BF16 copy of the convection part (Wj [Npad][Kpad0]).
+struct BuildWParams {
+  DevOps o;
+  int kind, nb, nk, Kpad0, Kpad, Npad, S0, S1, wexp0, wexp1;
+  __nv_bfloat16 *Wd, *Wj;
+};
+
+__global__ void k_build_w(BuildWParams p) {
+  const DevOps &o = p.o;
+  const size_t total = (size_t)p.Npad * p.Kpad;
+  const size_t nm = (size_t)o.n_max;
+  const double sc0 = ldexp(1.0, kDigitBits * p.S0 - p.wexp0);
+  const double sc1 = ldexp(1.0, kDigitBits * p.S1 - p.wexp1);
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
-    const int kap = (int)(e % Kpad);
-    const int c = (int)(e / Kpad);
+    const int kap = (int)(e % p.Kpad);
+    const int c = (int)(e / p.Kpad);
     double v = 0.0;
-    if (c < nb * nb && kap < qc * nb) {
-      const int k = c / nb, j = c % nb, q = kap / nb, l = kap % nb;
-      v = Dt[(((size_t)q * nm + l) * nm + k) * nm + j];
+    const bool seg1 = kap >= p.Kpad0;
+    if (c < p.nk * p.nb) {
+      const int k = c / p.nb, j = c % p.nb;
+      if (!seg1) {
+        if (kap < o.q_c * p.nb) {
+          const int q = kap / p.nb, l = kap % p.nb;
+          v = p.kind == 0 ? o.Dt[(((size_t)q * nm + l) * nm + k) * nm + j]
+                          : 2.0 * o.Cs[(((size_t)q * nm + j) * nm + l) * o.m + k];
+        }
+      } else {
+        const int q = kap - p.Kpad0;
+        if (q < o.q_a)
+          v = p.kind == 0 ? o.A[((size_t)q * nm + k) * nm + j] : o.As[((size_t)q * o.m + k) * nm + j];
+      }
     }
-    Wj[e] = __float2bfloat16_rn((float)v);
-    digits7(v, scale, S, Wd + e, total);
+    if (p.Wj && !seg1) p.Wj[(size_t)c * p.Kpad0 + kap] = __float2bfloat16_rn((float)v);
+    digits7(v, seg1 ? sc1 : sc0, seg1 ? p.S1 : p.S0, p.Wd + e, total);
   }
 }
 
-// Start of a batch: status NOT_CONVERGED (active) or REJECTED, u = 0.
+// Start of a batch: status NOT_CONVERGED (active) or REJECTED, u = 0 (if u is given).
 __global__ void k_mixed_init(int nq, int nm, const int *nsz, double *u, rb_query_info *info) {
   for (int b = blockIdx.x; b < nq; b += gridDim.x) {
     const int n = nsz ? nsz[b] : nm;
@@ -133,26 +174,35 @@ struct BuildXParams {
   DevOps o;
   const double *mu, *theta;
   const int *nsz;
-  int nq, nb, Kpad, S, b_pad, max_iter;
+  int nq, nb, Kpad0, Kpad, S0, S1, b_pad, max_iter, mode;  // mode 0: active, 1: converged
   const double *u;  // [nq][n_max]
   const rb_query_info *info;
   __nv_bfloat16 *Xj, *Xd;
-  int *xexp;
-  float2 *uf;
-  double *Rc;
+  int *xexp;        // [2][b_pad]
+  float2 *ufT;      // [nb][b_pad]
+  double *out;      // [b_pad][nout], zeroed for each built query
+  int nout;
 };
 
 __device__ __forceinline__ bool is_active(const rb_query_info &q, int max_iter) {
   return q.status == RB_Q_NOT_CONVERGED && q.iters < max_iter;
 }
 
+__device__ __forceinline__ int exp_of_max(double m) {
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+
 __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
   __shared__ double th[4 * RB_Q_MAX];
-  __shared__ double red[4 * kWarps];
+  __shared__ double red[2 * kWarps];
   const DevOps &o = p.o;
   const int tid = threadIdx.x;
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
-    if (!is_active(p.info[b], p.max_iter)) continue;
+    const rb_query_info qi = p.info[b];
+    const bool want = p.mode == 0 ? is_active(qi, p.max_iter) : qi.status == RB_Q_OK;
+    if (!want) continue;
     const int n = p.nsz ? p.nsz[b] : o.n_max;
     if (p.theta) {
       for (int i = tid; i < o.n_theta; i += blockDim.x) th[i] = p.theta[(size_t)b * o.n_theta + i];
@@ -160,39 +210,56 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
       theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
     }
     __syncthreads();
-    const double *tc = th + o.q_a;
+    const double *ta = th, *tc = th + o.q_a;
     const double *ub = p.u + (size_t)b * o.n_max;
-    double m = 0.0;
+    double m0 = 0.0, m1 = 0.0;
     for (int kap = tid; kap < o.q_c * p.nb; kap += blockDim.x) {
       const int q = kap / p.nb, l = kap % p.nb;
-      if (l < n) m = fmax(m, fabs(0.5 * tc[q] * ub[l]));
+      if (l < n) m0 = fmax(m0, fabs(0.5 * tc[q] * ub[l]));
     }
-    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if ((tid & 31) == 0) red[tid >> 5] = m;
+    for (int q = tid; q < o.q_a; q += blockDim.x) m1 = fmax(m1, fabs(ta[q]));
+    for (int off = 16; off > 0; off >>= 1) {
+      m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, off));
+      m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, off));
+    }
+    if ((tid & 31) == 0) {
+      red[tid >> 5] = m0;
+      red[kWarps + (tid >> 5)] = m1;
+    }
     __syncthreads();
-    double mx = 0.0;
-    for (int i = 0; i < kWarps; ++i) mx = fmax(mx, red[i]);
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);
-    const double scale = ldexp(1.0, kDigitBits * p.S - e);
+    double mx0 = 0.0, mx1 = 0.0;
+    for (int i = 0; i < kWarps; ++i) {
+      mx0 = fmax(mx0, red[i]);
+      mx1 = fmax(mx1, red[kWarps + i]);
+    }
+    const int e0 = exp_of_max(mx0), e1 = exp_of_max(mx1);
+    const double sc0 = ldexp(1.0, kDigitBits * p.S0 - e0), sc1 = ldexp(1.0, kDigitBits * p.S1 - e1);
     const size_t sstride = (size_t)p.b_pad * p.Kpad;
     for (int kap = tid; kap < p.Kpad; kap += blockDim.x) {
-      double x = 0.0;
-      if (kap < o.q_c * p.nb) {
-        const int q = kap / p.nb, l = kap % p.nb;
-        if (l < n) x = tc[q] * ub[l];
-      }
       const size_t off = (size_t)b * p.Kpad + kap;
-      p.Xj[off] = __float2bfloat16_rn((float)x);
-      digits7(0.5 * x, scale, p.S, p.Xd + off, sstride);
+      if (kap < p.Kpad0) {
+        double x = 0.0;
+        if (kap < o.q_c * p.nb) {
+          const int q = kap / p.nb, l = kap % p.nb;
+          if (l < n) x = tc[q] * ub[l];
+        }
+        if (p.mode == 0) p.Xj[(size_t)b * p.Kpad0 + kap] = __float2bfloat16_rn((float)x);
+        digits7(0.5 * x, sc0, p.S0, p.Xd + off, sstride);
+      } else {
+        const int q = kap - p.Kpad0;
+        digits7(q < o.q_a ? ta[q] : 0.0, sc1, p.S1, p.Xd + off, sstride);
+      }
     }
     for (int j = tid; j < p.nb; j += blockDim.x) {
       const double v = j < n ? ub[j] : 0.0;
       const float hi = (float)v;
-      p.uf[(size_t)b * p.nb + j] = make_float2(hi, (float)(v - (double)hi));
-      p.Rc[(size_t)b * p.nb + j] = 0.0;
+      p.ufT[(size_t)j * p.b_pad + b] = make_float2(hi, (float)(v - (double)hi));
     }
-    if (tid == 0) p.xexp[b] = e;
+    for (int k = tid; k < p.nout; k += blockDim.x) p.out[(size_t)b * p.nout + k] = 0.0;
+    if (tid == 0) {
+      p.xexp[b] = e0;
+      p.xexp[p.b_pad + b] = e1;
+    }
     __syncthreads();
   }
 }
@@ -203,8 +270,9 @@ struct LuParams {
   const int *nsz;
   int nq, nb, ldj, max_iter, j_in_smem;
   double tol_upd, tol_res;
-  const float *Jc;
-  const double *Rc;
+  const float *A32;      // [q_a][n_max][n_max]
+  const float *Jc;       // [b_pad][ldj]
+  const double *Rc;      // [b_pad][nb]: A(mu) u + C_mu(u, u)
   double *u;             // [nq][n_max], updated in place
   rb_query_info *info;   // [nq]
   float *scratch;        // [grid][nb * nb] when J is not in shared memory
@@ -214,11 +282,10 @@ struct LuParams {
 };
 
 struct LuSmem {
-  int th, u, R, fm, red, rhs, J, total;  // offsets in bytes
+  int th, R, fm, red, rhs, J, total;  // offsets in bytes
   __host__ __device__ LuSmem(const DevOps &o, int nb, bool j_in_smem) {
     int p = 0;
     th = p; p += 8 * ((o.n_theta + 1) & ~1);
-    u = p; p += 8 * nb;
     R = p; p += 8 * nb;
     fm = p; p += 8 * nb;
     red = p; p += 8 * 4 * kWarps;
@@ -232,9 +299,10 @@ struct LuSmem {
 
 __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
+  __shared__ float ta[RB_Q_MAX];  // theta^a in FP32
   const DevOps &o = p.o;
   const LuSmem L(o, p.nb, p.j_in_smem != 0);
-  double *th = (double *)(smb + L.th), *u = (double *)(smb + L.u), *R = (double *)(smb + L.R);
+  double *th = (double *)(smb + L.th), *R = (double *)(smb + L.R);
   double *fm = (double *)(smb + L.fm), *red = (double *)(smb + L.red);
   float *rhs = (float *)(smb + L.rhs);
   float *J = p.j_in_smem ? (float *)(smb + L.J) : p.scratch + (size_t)blockIdx.x * p.nb * p.nb;
@@ -250,31 +318,28 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
     } else {
       theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
     }
-    double *ub = p.u + (size_t)b * nm;
-    for (int i = tid; i < n; i += blockDim.x) u[i] = ub[i];
     __syncthreads();
     const double *tf = th + o.q_a + o.q_c;
     for (int k = tid; k < n; k += blockDim.x) {
       double s = 0.0;
       for (int q = 0; q < o.q_f; ++q) s = fma(tf[q], o.f[(size_t)q * nm + k], s);
       fm[k] = s;
+      R[k] = p.Rc[(size_t)b * p.nb + k] - s;
     }
-    __syncthreads();
-    // A(mu) in FP64: J = fl32(A(mu)) + J^c, R = A(mu) u - f + R^c; one warp per row
+    // J = fl32(A(mu)) + J^c, one warp per row, FP32 only
     const float *jc = p.Jc + (size_t)b * p.ldj;
+    if (tid < o.q_a) ta[tid] = (float)th[tid];
+    __syncthreads();
     for (int k = w; k < n; k += kWarps) {
-      double r = 0.0;
       for (int j = lane; j < n; j += 32) {
-        double a = 0.0;
-        for (int q = 0; q < o.q_a; ++q) a = fma(th[q], __ldg(o.A + ((size_t)q * nm + k) * nm + j), a);
-        r = fma(a, u[j], r);
+        float a = 0.f;
+        for (int q = 0; q < o.q_a; ++q) a = fmaf(ta[q], __ldg(p.A32 + ((size_t)q * nm + k) * nm + j), a);
+        const float v = a + jc[k * p.nb + j];
         if (p.eval_only)
-          p.J_out[((size_t)b * n + k) * n + j] = a + (double)jc[k * p.nb + j];
+          p.J_out[((size_t)b * n + k) * n + j] = (double)v;
         else
-          J[(size_t)k * n + j] = (float)a + jc[k * p.nb + j];
+          J[(size_t)k * n + j] = v;
       }
-      r = warp_sum(r);
-      if (lane == 0) R[k] = r - fm[k] + p.Rc[(size_t)b * p.nb + k];
     }
     __syncthreads();
     if (p.eval_only) {
@@ -298,11 +363,12 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
     } else if (gepp_solve_block<float>(J, n, n, rhs, red)) {
       qi.status = RB_Q_SINGULAR;
     } else {
+      double *ub = p.u + (size_t)b * nm;
       double dl = 0.0;
       for (int i = tid; i < n; i += blockDim.x) {
         const double d = (double)rhs[i];
         dl += d * d;
-        ub[i] = u[i] + d;
+        ub[i] += d;
       }
       const double dn = sqrt(block_sum(dl, red));
       qi.upd_norm = dn;
@@ -318,31 +384,266 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
   if (tid == 0 && my_active) atomicAdd(p.active, my_active);
 }
 
+// Warp-per-query variant of k_lu_mixed for small Jacobians (no block barriers): each warp
+// owns one query at a time and its own shared-memory slab.
+struct WarpLuSmem {
+  int th, R, fm, tha, rhs, J, per_warp;  // byte offsets within a warp's slab
+  __host__ __device__ WarpLuSmem(const DevOps &o, int nb) {
+    int p = 0;
+    th = p; p += 8 * ((o.n_theta + 1) & ~1);
+    R = p; p += 8 * nb;
+    fm = p; p += 8 * nb;
+    tha = p; p += 4 * ((o.q_a + 3) & ~3);
+    rhs = p; p += 4 * ((nb + 3) & ~3);
+    p = (p + 15) & ~15;
+    J = p; p += 4 * nb * (nb + 1);
+    per_warp = (p + 15) & ~15;
+  }
+};
+
+__global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  const DevOps &o = p.o;
+  const WarpLuSmem L(o, p.nb);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  uint8_t *slab = smb + (size_t)w * L.per_warp;
+  double *th = (double *)(slab + L.th), *R = (double *)(slab + L.R), *fm = (double *)(slab + L.fm);
+  float *tha = (float *)(slab + L.tha), *rhs = (float *)(slab + L.rhs), *J = (float *)(slab + L.J);
+  const int ld = p.nb + 1;
+  const size_t nm = (size_t)o.n_max;
+  int my_active = 0;
+  for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
+    rb_query_info qi = p.info[b];
+    if (!is_active(qi, p.max_iter)) continue;
+    const int n = p.nsz ? p.nsz[b] : o.n_max;
+    if (p.theta) {
+      for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta[(size_t)b * o.n_theta + i];
+    } else {
+      theta_eval_strided(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane, 32);
+    }
+    __syncwarp();
+    for (int q = lane; q < o.q_a; q += 32) tha[q] = (float)th[q];
+    const double *tf = th + o.q_a + o.q_c;
+    for (int k = lane; k < n; k += 32) {
+      double sf = 0.0;
+      for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.f[(size_t)q * nm + k], sf);
+      fm[k] = sf;
+      R[k] = p.Rc[(size_t)b * p.nb + k] - sf;
+    }
+    __syncwarp();
+    const float *jc = p.Jc + (size_t)b * p.ldj;
+    for (int k = 0; k < n; ++k) {
+      for (int j = lane; j < n; j += 32) {
+        float a = 0.f;
+        for (int q = 0; q < o.q_a; ++q) a = fmaf(tha[q], __ldg(p.A32 + ((size_t)q * nm + k) * nm + j), a);
+        const float v = a + jc[k * p.nb + j];
+        if (p.eval_only)
+          p.J_out[((size_t)b * n + k) * n + j] = (double)v;
+        else
+          J[k * ld + j] = v;
+      }
+    }
+    __syncwarp();
+    if (p.eval_only) {
+      for (int k = lane; k < n; k += 32) p.R_out[(size_t)b * n + k] = R[k];
+      __syncwarp();
+      continue;
+    }
+    double rl = 0.0, fl = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      rl += R[i] * R[i];
+      fl += fm[i] * fm[i];
+      rhs[i] = (float)(-R[i]);
+    }
+    const double rn = sqrt(warp_sum(rl));
+    const double fscale = fmax(1.0, sqrt(warp_sum(fl)));
+    __syncwarp();
+    qi.iters += 1;
+    qi.res_norm = rn;
+    qi.precision_used = RB_PREC_MIXED;
+    if (!isfinite(rn)) {
+      qi.status = RB_Q_NONFINITE;
+    } else if (gepp_solve_warp<float>(J, ld, n, rhs)) {
+      qi.status = RB_Q_SINGULAR;
+    } else {
+      double *ub = p.u + (size_t)b * nm;
+      double dl = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        const double d = (double)rhs[i];
+        dl += d * d;
+        ub[i] += d;
+      }
+      const double dn = sqrt(warp_sum(dl));
+      qi.upd_norm = dn;
+      if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
+      else if (dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+    }
+    if (lane == 0) {
+      p.info[b] = qi;
+      if (is_active(qi, p.max_iter)) ++my_active;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && my_active) atomicAdd(p.active, my_active);
+}
+
+// Pressure: r = fs(mu) - (As(mu) u + Cs_mu(u, u)), B(mu) p = r in FP64 (Eq. blocksolve-2).
+struct PresSolveParams {
+  DevOps o;
+  const double *mu, *theta;
+  int nq;
+  const double *Rp;  // [b_pad][m]
+  double *p_out;     // [nq][m]
+  rb_query_info *info;
+};
+
+__global__ void __launch_bounds__(kThreads) k_pressure_solve(PresSolveParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  const DevOps &o = p.o;
+  const int m = o.m;
+  double *th = (double *)smb;
+  double *r = th + ((o.n_theta + 1) & ~1);
+  double *red = r + ((m + 1) & ~1);
+  double *Bm = red + 4 * kWarps;
+  const int tid = threadIdx.x;
+  for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
+    double *prow = p.p_out + (size_t)b * m;
+    if (p.info[b].status != RB_Q_OK) {
+      for (int i = tid; i < m; i += blockDim.x) prow[i] = 0.0;
+      continue;
+    }
+    if (p.theta) {
+      for (int i = tid; i < o.n_theta; i += blockDim.x) th[i] = p.theta[(size_t)b * o.n_theta + i];
+    } else {
+      theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
+    }
+    __syncthreads();
+    const double *tf = th + o.q_a + o.q_c, *tb = tf + o.q_f;
+    for (int k = tid; k < m; k += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q < o.q_f; ++q) s = fma(tf[q], o.fs[(size_t)q * m + k], s);
+      r[k] = s - p.Rp[(size_t)b * m + k];
+    }
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      double s = 0.0;
+      for (int q = 0; q < o.q_b; ++q) s = fma(tb[q], __ldg(o.B + (size_t)q * m * m + e), s);
+      Bm[e] = s;
+    }
+    __syncthreads();
+    const bool sing = gepp_solve_block<double>(Bm, m, m, r, red);
+    for (int i = tid; i < m; i += blockDim.x) prow[i] = sing ? 0.0 : r[i];
+    if (sing && tid == 0) p.info[b].status = RB_Q_SINGULAR;
+    __syncthreads();
+  }
+}
+
+// Warp-per-query variant of k_pressure_solve for small m.
+__global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  const DevOps &o = p.o;
+  const int m = o.m;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const int per_warp = ((o.n_theta + 1) & ~1) + ((m + 1) & ~1) + m * (m + 1);
+  double *th = (double *)smb + (size_t)w * per_warp;
+  double *r = th + ((o.n_theta + 1) & ~1);
+  double *Bm = r + ((m + 1) & ~1);
+  const int ld = m + 1;
+  for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
+    double *prow = p.p_out + (size_t)b * m;
+    if (p.info[b].status != RB_Q_OK) {
+      for (int i = lane; i < m; i += 32) prow[i] = 0.0;
+      continue;
+    }
+    if (p.theta) {
+      for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta[(size_t)b * o.n_theta + i];
+    } else {
+      theta_eval_strided(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane, 32);
+    }
+    __syncwarp();
+    const double *tf = th + o.q_a + o.q_c, *tb = tf + o.q_f;
+    for (int k = lane; k < m; k += 32) {
+      double sf = 0.0;
+      for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
+      r[k] = sf - p.Rp[(size_t)b * m + k];
+    }
+    for (int k = 0; k < m; ++k)
+      for (int i = lane; i < m; i += 32) {
+        double sb = 0.0;
+        for (int q = 0; q < o.q_b; ++q) sb = fma(tb[q], __ldg(o.B + ((size_t)q * m + k) * m + i), sb);
+        Bm[k * ld + i] = sb;
+      }
+    __syncwarp();
+    const bool sing = gepp_solve_warp<double>(Bm, ld, m, r);
+    for (int i = lane; i < m; i += 32) prow[i] = sing ? 0.0 : r[i];
+    if (sing && lane == 0) p.info[b].status = RB_Q_SINGULAR;
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 void mixed_release(rb_ctx *ctx) {
   MixedState *M = ctx->mixed;
   if (!M) return;
-  ctx_free(ctx, M->Wj);
-  ctx_free(ctx, M->Wd);
-  ctx_free(ctx, M->Xj);
-  ctx_free(ctx, M->Xd);
-  ctx_free(ctx, M->xexp);
-  ctx_free(ctx, M->uf);
-  ctx_free(ctx, M->Jc);
-  ctx_free(ctx, M->Rc);
-  ctx_free(ctx, M->lu_scratch);
-  ctx_free(ctx, M->dev_words);
-  ctx_free(ctx, M->info_own);
+  for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A32, (void *)M->Xj,
+                  (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc, (void *)M->Rc,
+                  (void *)M->Rp, (void *)M->lu_scratch, (void *)M->dev_words, (void *)M->info_own})
+    ctx_free(ctx, q);
   if (M->h_words) cudaFreeHost(M->h_words);
   delete M;
   ctx->mixed = nullptr;
 }
 
-static int sliced_digits() {
-  const char *e = getenv("RB_DIGITS");
-  int s = e ? atoi(e) : 6;
+// digits of the convection segment (RB_DIGITS) and of the linear segment (RB_DIGITS_LINEAR)
+static int sliced_digits(const char *var, int dflt) {
+  const char *e = getenv(var);
+  const int s = e ? atoi(e) : dflt;
   return std::min(8, std::max(2, s));
+}
+
+static int absmax_exp(rb_ctx *ctx, const double *x, size_t count, int *e_out, cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  unsigned long long *mx = (unsigned long long *)(M->dev_words + 8);
+  cudaMemsetAsync(mx, 0, 8, st);
+  k_absmax<<<ctx->sms * 4, 256, 0, st>>>(x, count, mx);
+  unsigned long long hm = 0;
+  cudaError_t e = cudaMemcpyAsync(&hm, mx, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "operator exponent");
+  double dmax;
+  memcpy(&dmax, &hm, 8);
+  int ex = 0;
+  if (dmax > 0) frexp(dmax, &ex);
+  *e_out = ex;
+  return RB_OK;
+}
+
+static int build_sliced(rb_ctx *ctx, SlicedW &W, int kind, int nk, __nv_bfloat16 *Wj,
+                        cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  const DevOps &o = ctx->ops;
+  W.nk = nk;
+  W.Npad = round_up(nk * M->nb, kTcBN);
+  void *p;
+  int rc = ctx_alloc(ctx, &p, 2 * (size_t)M->Smax * W.Npad * M->Kpad, "W digit slices");
+  if (rc != RB_OK) return rc;
+  W.d = (__nv_bfloat16 *)p;
+  const size_t nm = o.n_max;
+  if (kind == 0) {
+    if ((rc = absmax_exp(ctx, o.Dt, (size_t)o.q_c * nm * nm * nm, &W.wexp[0], st)) != RB_OK) return rc;
+    if ((rc = absmax_exp(ctx, o.A, (size_t)o.q_a * nm * nm, &W.wexp[1], st)) != RB_OK) return rc;
+  } else {
+    if ((rc = absmax_exp(ctx, o.Cs, (size_t)o.q_c * nm * nm * o.m, &W.wexp[0], st)) != RB_OK) return rc;
+    W.wexp[0] += 1;  // the operand holds 2 Cs
+    if ((rc = absmax_exp(ctx, o.As, (size_t)o.q_a * o.m * nm, &W.wexp[1], st)) != RB_OK) return rc;
+  }
+  BuildWParams bw{o, kind, M->nb, nk, M->Kpad0, M->Kpad, W.Npad, M->S0, M->S1, W.wexp[0], W.wexp[1], W.d, Wj};
+  k_build_w<<<ctx->sms * 8, 256, 0, st>>>(bw);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_build_w");
+  if (!make_map(&W.tm, W.d, (uint64_t)M->Smax * W.Npad, M->Kpad, kTcBN))
+    return set_error(ctx, RB_ERR_CUDA, "tensor map encode (W)");
+  return RB_OK;
 }
 
 // Build the operator layouts of the mixed path (once per operator set).
@@ -354,42 +655,30 @@ static int mixed_layouts(rb_ctx *ctx, cudaStream_t st) {
   MixedState *M = ctx->mixed;
   const DevOps &o = ctx->ops;
   M->nb = o.n_max;
-  M->K = o.q_c * M->nb;
-  M->Kpad = round_up(M->K, 64);
-  M->kb = M->Kpad / 64;
+  M->Kpad0 = round_up(o.q_c * M->nb, 64);
+  M->kb0 = M->Kpad0 / 64;
+  M->kb1 = 1;  // q_a <= 64 affine terms in one K block
+  M->Kpad = M->Kpad0 + 64 * M->kb1;
   M->Npad = round_up(M->nb * M->nb, kTcBN);
-  M->S = sliced_digits();
+  M->S0 = sliced_digits("RB_DIGITS", 6);
+  M->S1 = sliced_digits("RB_DIGITS_LINEAR", 7);
+  M->Smax = std::max(M->S0, M->S1);
   int rc;
   void *p;
-  const size_t wsz = (size_t)M->Npad * M->Kpad;
-  if ((rc = ctx_alloc(ctx, &p, 2 * wsz, "W (BF16)")) != RB_OK) return rc;
-  M->Wj = (__nv_bfloat16 *)p;
-  if ((rc = ctx_alloc(ctx, &p, 2 * wsz * M->S, "W digit slices")) != RB_OK) return rc;
-  M->Wd = (__nv_bfloat16 *)p;
   if ((rc = ctx_alloc(ctx, &p, 64, "mixed words")) != RB_OK) return rc;
   M->dev_words = (int *)p;
-  if (cudaMallocHost(&M->h_words, 64) != cudaSuccess) return set_error(ctx, RB_ERR_OOM, "pinned words");
-  // global exponent of the W grid
   cudaMemsetAsync(M->dev_words, 0, 64, st);
-  unsigned long long *mx = (unsigned long long *)(M->dev_words + 8);
-  const size_t dcount = (size_t)o.q_c * o.n_max * o.n_max * o.n_max;
-  k_absmax<<<ctx->sms * 4, 256, 0, st>>>(o.Dt, dcount, mx);
-  unsigned long long hm = 0;
-  cudaError_t e = cudaMemcpyAsync(&hm, mx, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "W exponent");
-  double dmax;
-  memcpy(&dmax, &hm, 8);
-  int we = 0;
-  if (dmax > 0) frexp(dmax, &we);
-  M->wexp = we;
-  k_build_w<<<ctx->sms * 8, 256, 0, st>>>(o.Dt, o.n_max, o.q_c, M->nb, M->Kpad, M->Npad, M->S,
-                                          M->wexp, M->Wj, M->Wd);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_build_w");
-  if (!make_map(&M->tmWj, M->Wj, M->Npad, M->Kpad, kTcBN) ||
-      !make_map(&M->tmWd, M->Wd, (uint64_t)M->S * M->Npad, M->Kpad, kTcBN))
-    return set_error(ctx, RB_ERR_CUDA, "tensor map encode (W)");
+  if (cudaMallocHost(&M->h_words, 64) != cudaSuccess) return set_error(ctx, RB_ERR_OOM, "pinned words");
+  const size_t nm = o.n_max;
+  if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)o.q_a * nm * nm, "A (FP32)")) != RB_OK) return rc;
+  M->A32 = (float *)p;
+  k_to_f32<<<ctx->sms * 4, 256, 0, st>>>(o.A, M->A32, (size_t)o.q_a * nm * nm);
+  if ((rc = ctx_alloc(ctx, &p, 2 * (size_t)M->Npad * M->Kpad0, "W (BF16)")) != RB_OK) return rc;
+  M->Wj = (__nv_bfloat16 *)p;
+  if ((rc = build_sliced(ctx, M->WR, 0, M->nb, M->Wj, st)) != RB_OK) return rc;
+  if (o.m > 0 && o.B && (rc = build_sliced(ctx, M->WP, 1, o.m, nullptr, st)) != RB_OK) return rc;
+  if (!make_map(&M->tmWj, M->Wj, M->Npad, M->Kpad0, kTcBN))
+    return set_error(ctx, RB_ERR_CUDA, "tensor map encode (Wj)");
   return RB_OK;
 }
 
@@ -397,35 +686,89 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
   MixedState *M = ctx->mixed;
   const int b_pad = round_up(std::max(nq, 1), 128);
   if (b_pad <= M->bcap) return RB_OK;
-  ctx_free(ctx, M->Xj); ctx_free(ctx, M->Xd); ctx_free(ctx, M->xexp); ctx_free(ctx, M->uf);
-  ctx_free(ctx, M->Jc); ctx_free(ctx, M->Rc);
-  M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->uf = nullptr; M->Jc = nullptr; M->Rc = nullptr;
+  for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
+                  (void *)M->Rc, (void *)M->Rp})
+    ctx_free(ctx, q);
+  M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->ufT = nullptr; M->Jc = nullptr;
+  M->Rc = M->Rp = nullptr;
   M->bcap = 0;
   int rc;
   void *p;
-  const size_t xs = (size_t)b_pad * M->Kpad;
-  if ((rc = ctx_alloc(ctx, &p, 2 * xs, "X (BF16)")) != RB_OK) return rc;
+  const int m = std::max(ctx->ops.m, 1);
+  const size_t xs0 = (size_t)b_pad * M->Kpad0, xs = (size_t)b_pad * M->Kpad;
+  if ((rc = ctx_alloc(ctx, &p, 2 * xs0, "X (BF16)")) != RB_OK) return rc;
   M->Xj = (__nv_bfloat16 *)p;
-  if ((rc = ctx_alloc(ctx, &p, 2 * xs * M->S, "X digit slices")) != RB_OK) return rc;
+  if ((rc = ctx_alloc(ctx, &p, 2 * xs * M->Smax, "X digit slices")) != RB_OK) return rc;
   M->Xd = (__nv_bfloat16 *)p;
-  if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad, "X exponents")) != RB_OK) return rc;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad, "X exponents")) != RB_OK) return rc;
   M->xexp = (int *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "u (float pairs)")) != RB_OK) return rc;
-  M->uf = (float2 *)p;
+  M->ufT = (float2 *)p;
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->Npad, "J^c (FP32)")) != RB_OK) return rc;
   M->Jc = (float *)p;
-  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "R^c (FP64)")) != RB_OK) return rc;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "R (FP64)")) != RB_OK) return rc;
   M->Rc = (double *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * m, "pressure rhs (FP64)")) != RB_OK) return rc;
+  M->Rp = (double *)p;
   // zero once so that padded rows never hold NaN bit patterns
-  cudaMemsetAsync(M->Xj, 0, 2 * xs, ctx->stream);
-  cudaMemsetAsync(M->Xd, 0, 2 * xs * M->S, ctx->stream);
-  cudaMemsetAsync(M->xexp, 0, 4 * (size_t)b_pad, ctx->stream);
-  cudaMemsetAsync(M->uf, 0, 8 * (size_t)b_pad * M->nb, ctx->stream);
-  if (!make_map(&M->tmXj, M->Xj, b_pad, M->Kpad, 128) ||
-      !make_map(&M->tmXd, M->Xd, (uint64_t)M->S * b_pad, M->Kpad, 128))
+  cudaMemsetAsync(M->Xj, 0, 2 * xs0, ctx->stream);
+  cudaMemsetAsync(M->Xd, 0, 2 * xs * M->Smax, ctx->stream);
+  cudaMemsetAsync(M->xexp, 0, 8 * (size_t)b_pad, ctx->stream);
+  cudaMemsetAsync(M->ufT, 0, 8 * (size_t)b_pad * M->nb, ctx->stream);
+  if (!make_map(&M->tmXj, M->Xj, b_pad, M->Kpad0, 128) ||
+      !make_map(&M->tmXd, M->Xd, (uint64_t)M->Smax * b_pad, M->Kpad, 128))
     return set_error(ctx, RB_ERR_CUDA, "tensor map encode (X)");
   M->bcap = b_pad;
   return RB_OK;
+}
+
+static int launch_build_x(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
+                          const int *d_n, const double *d_u, const rb_query_info *d_info,
+                          int mode, double *out, int nout, cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  BuildXParams bx{};
+  bx.o = ctx->ops;
+  bx.mu = d_mu;
+  bx.theta = d_theta;
+  bx.nsz = d_n;
+  bx.nq = nq;
+  bx.nb = M->nb;
+  bx.Kpad0 = M->Kpad0;
+  bx.Kpad = M->Kpad;
+  bx.S0 = M->S0;
+  bx.S1 = M->S1;
+  bx.b_pad = M->bcap;
+  bx.max_iter = ctx->cfg.max_iter;
+  bx.mode = mode;
+  bx.u = d_u;
+  bx.info = d_info;
+  bx.Xj = M->Xj;
+  bx.Xd = M->Xd;
+  bx.xexp = M->xexp;
+  bx.ufT = M->ufT;
+  bx.out = out;
+  bx.nout = nout;
+  const int mk = prof_begin(ctx, RB_K_BUILD_X, st);
+  k_build_x<<<std::min(nq, ctx->sms * 8), kThreads, 0, st>>>(bx);
+  prof_end(ctx, mk, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_build_x");
+  return RB_OK;
+}
+
+static TcGemmParams gemm_params(rb_ctx *ctx, int nq) {
+  MixedState *M = ctx->mixed;
+  TcGemmParams g{};
+  g.m_tiles = round_up(nq, 128) / 128;
+  g.S[0] = M->S0;
+  g.S[1] = M->S1;
+  g.b_pad = M->bcap;
+  g.nq = nq;
+  g.nj = M->nb;
+  g.xexp = M->xexp;
+  g.ufT = M->ufT;
+  g.err = M->dev_words + 1;
+  return g;
 }
 
 // One Newton step's contraction work for the whole batch: X build + both GEMMs.
@@ -433,53 +776,52 @@ static int mixed_contract(rb_ctx *ctx, const double *d_mu, const double *d_theta
                           const int *d_n, const double *d_u, const rb_query_info *d_info,
                           cudaStream_t st) {
   MixedState *M = ctx->mixed;
-  const DevOps &o = ctx->ops;
-  BuildXParams bx{};
-  bx.o = o;
-  bx.mu = d_mu;
-  bx.theta = d_theta;
-  bx.nsz = d_n;
-  bx.nq = nq;
-  bx.nb = M->nb;
-  bx.Kpad = M->Kpad;
-  bx.S = M->S;
-  bx.b_pad = M->bcap;
-  bx.max_iter = ctx->cfg.max_iter;
-  bx.u = d_u;
-  bx.info = d_info;
-  bx.Xj = M->Xj;
-  bx.Xd = M->Xd;
-  bx.xexp = M->xexp;
-  bx.uf = M->uf;
-  bx.Rc = M->Rc;
-  k_build_x<<<std::min(nq, ctx->sms * 8), kThreads, 0, st>>>(bx);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_build_x");
-  TcGemmParams g{};
-  g.m_tiles = round_up(nq, 128) / 128;
+  int rc = launch_build_x(ctx, d_mu, d_theta, nq, d_n, d_u, d_info, 0, M->Rc, M->nb, st);
+  if (rc != RB_OK) return rc;
+  TcGemmParams g = gemm_params(ctx, nq);
   g.n_tiles = M->Npad / kTcBN;
-  g.kb = M->kb;
-  g.S = M->S;
-  g.b_pad = M->bcap;
+  g.kb[0] = M->kb0;
+  g.kb[1] = 0;
   g.n_pad = M->Npad;
-  g.nq = nq;
-  g.nb = M->nb;
-  g.wexp = M->wexp;
+  g.nk = M->nb;
   g.ldj = M->Npad;
   g.Jc = M->Jc;
-  g.xexp = M->xexp;
-  g.uf = M->uf;
-  g.Rc = M->Rc;
-  g.err = M->dev_words + 1;
-  e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st);
+  int mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
+  cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st);
+  prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (Jacobian)");
-  e = launch_tc_gemm(kSliced, M->tmXd, M->tmWd, g, ctx->sms, st);
+  g.kb[1] = M->kb1;
+  g.n_tiles = M->WR.Npad / kTcBN;
+  g.n_pad = M->WR.Npad;
+  g.wexp[0] = M->WR.wexp[0];
+  g.wexp[1] = M->WR.wexp[1];
+  g.out = M->Rc;
+  mk = prof_begin(ctx, RB_K_GEMM_RES, st);
+  e = launch_tc_gemm(kSliced, M->tmXd, M->WR.tm, g, ctx->sms, st);
+  prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (residual)");
   return RB_OK;
 }
 
+constexpr int kWarpLuMaxN = 80;  // warp-per-query elimination up to this size
+
 static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
   MixedState *M = ctx->mixed;
+  if (M->nb <= kWarpLuMaxN) {
+    const int per_warp = WarpLuSmem(ctx->ops, M->nb).per_warp;
+    const int wpc = std::max(1, std::min(8, (200 * 1024) / per_warp));
+    const size_t smem = (size_t)wpc * per_warp;
+    const int per_sm = std::max(1, std::min(64 / wpc, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
+    const int grid = std::max(1, std::min((nq + wpc - 1) / wpc, per_sm * ctx->sms));
+    cudaError_t e = cudaFuncSetAttribute(k_lu_mixed_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp attr");
+    const int mk = prof_begin(ctx, RB_K_LU, st);
+    k_lu_mixed_warp<<<grid, 32 * wpc, smem, st>>>(lp);
+    prof_end(ctx, mk, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp");
+    return RB_OK;
+  }
   const size_t smem_in = LuSmem(ctx->ops, M->nb, true).total;
   lp.j_in_smem = smem_in <= (size_t)ctx->max_smem ? 1 : 0;
   const size_t smem = LuSmem(ctx->ops, M->nb, lp.j_in_smem != 0).total;
@@ -500,7 +842,9 @@ static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
   }
   cudaError_t e = cudaFuncSetAttribute(k_lu_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed attr");
+  const int mk = prof_begin(ctx, RB_K_LU, st);
   k_lu_mixed<<<grid, kThreads, smem, st>>>(lp);
+  prof_end(ctx, mk, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed");
   return RB_OK;
@@ -510,6 +854,8 @@ static rb_query_info *own_info(rb_ctx *ctx, int nq) {
   MixedState *M = ctx->mixed;
   if (M->info_cap < nq) {
     ctx_free(ctx, M->info_own);
+    M->info_own = nullptr;
+    M->info_cap = 0;
     void *p;
     if (ctx_alloc(ctx, &p, sizeof(rb_query_info) * (size_t)nq, "info") != RB_OK) return nullptr;
     M->info_own = (rb_query_info *)p;
@@ -518,8 +864,62 @@ static rb_query_info *own_info(rb_ctx *ctx, int nq) {
   return M->info_own;
 }
 
+static int check_words(rb_ctx *ctx, cudaStream_t st, const char *what) {
+  MixedState *M = ctx->mixed;
+  cudaError_t e = cudaMemcpyAsync(M->h_words, M->dev_words, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  if (M->h_words[1])
+    return set_error(ctx, RB_ERR_TIMEOUT, "%s: tensor-core pipeline wait gave up (code %d)", what,
+                     M->h_words[1]);
+  return RB_OK;
+}
+
+static int mixed_pressure(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
+                          const int *d_n, const double *d_u, double *d_p, rb_query_info *info,
+                          cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  const DevOps &o = ctx->ops;
+  int rc = launch_build_x(ctx, d_mu, d_theta, nq, d_n, d_u, info, 1, M->Rp, o.m, st);
+  if (rc != RB_OK) return rc;
+  TcGemmParams g = gemm_params(ctx, nq);
+  g.kb[0] = M->kb0;
+  g.kb[1] = M->kb1;
+  g.n_tiles = M->WP.Npad / kTcBN;
+  g.n_pad = M->WP.Npad;
+  g.nk = o.m;
+  g.wexp[0] = M->WP.wexp[0];
+  g.wexp[1] = M->WP.wexp[1];
+  g.out = M->Rp;
+  int mk = prof_begin(ctx, RB_K_GEMM_PRES, st);
+  cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WP.tm, g, ctx->sms, st);
+  prof_end(ctx, mk, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (pressure)");
+  PresSolveParams pp{o, d_mu, d_theta, nq, M->Rp, d_p, info};
+  const size_t per_warp = 8 * (size_t)(((o.n_theta + 1) & ~1) + ((o.m + 1) & ~1) + o.m * (o.m + 1));
+  if (per_warp <= 24 * 1024) {
+    const int wpc = std::max(1, std::min(8, (int)((192 * 1024) / per_warp)));
+    const size_t smem = wpc * per_warp;
+    e = cudaFuncSetAttribute(k_pressure_solve_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure_solve_warp attr");
+    mk = prof_begin(ctx, RB_K_PRESSURE, st);
+    k_pressure_solve_warp<<<std::min((nq + wpc - 1) / wpc, ctx->sms * 8), 32 * wpc, smem, st>>>(pp);
+    prof_end(ctx, mk, st);
+  } else {
+    const size_t smem = 8 * (size_t)(((o.n_theta + 1) & ~1) + ((o.m + 1) & ~1) + 4 * kWarps + o.m * o.m);
+    e = cudaFuncSetAttribute(k_pressure_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure_solve attr");
+    mk = prof_begin(ctx, RB_K_PRESSURE, st);
+    k_pressure_solve<<<std::min(nq, ctx->sms * 8), kThreads, smem, st>>>(pp);
+    prof_end(ctx, mk, st);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure_solve");
+  return RB_OK;
+}
+
 int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
-                double *d_u, double *, rb_query_info *d_info, cudaStream_t st) {
+                double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st) {
   int rc = mixed_layouts(ctx, st);
   if (rc != RB_OK) return rc;
   if ((rc = mixed_batch_scratch(ctx, nq)) != RB_OK) return rc;
@@ -527,7 +927,9 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   rb_query_info *info = d_info ? d_info : own_info(ctx, nq);
   if (!info) return set_error(ctx, RB_ERR_OOM, "info scratch");
   const DevOps &o = ctx->ops;
+  int mk = prof_begin(ctx, RB_K_INIT, st);
   k_mixed_init<<<std::min(nq, ctx->sms * 8), 128, 0, st>>>(nq, o.n_max, d_n, d_u, info);
+  prof_end(ctx, mk, st);
   cudaMemsetAsync(M->dev_words, 0, 8, st);
   LuParams lp{};
   lp.o = o;
@@ -540,24 +942,24 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   lp.max_iter = ctx->cfg.max_iter;
   lp.tol_upd = ctx->cfg.tol_update;
   lp.tol_res = ctx->cfg.tol_res;
+  lp.A32 = M->A32;
   lp.Jc = M->Jc;
   lp.Rc = M->Rc;
   lp.u = d_u;
   lp.info = info;
   lp.active = M->dev_words;
-  int launches = 1;
   for (int it = 0; it < ctx->cfg.max_iter; ++it) {
     cudaMemsetAsync(M->dev_words, 0, 4, st);
     if ((rc = mixed_contract(ctx, d_mu, d_theta, nq, d_n, d_u, info, st)) != RB_OK) return rc;
     if ((rc = launch_lu(ctx, lp, nq, st)) != RB_OK) return rc;
-    launches += 4;
-    cudaError_t e = cudaMemcpyAsync(M->h_words, M->dev_words, 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "mixed Newton step");
-    if (M->h_words[1]) return set_error(ctx, RB_ERR_TIMEOUT, "tensor-core pipeline wait gave up (code %d)", M->h_words[1]);
+    if ((rc = check_words(ctx, st, "mixed Newton step")) != RB_OK) return rc;
     if (M->h_words[0] == 0) break;
   }
-  M->last_launches = launches;
+  if (d_p && o.m > 0 && o.B) {
+    if ((rc = mixed_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st)) != RB_OK) return rc;
+    if ((rc = check_words(ctx, st, "pressure recovery")) != RB_OK) return rc;
+  }
+  if (ctx->prof) prof_collect(ctx);
   return RB_OK;
 }
 
@@ -570,10 +972,9 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   MixedState *M = ctx->mixed;
   const DevOps &o = ctx->ops;
   // the layouts use n_max-length rows: widen u and pass sizes
-  void *p;
-  if ((rc = ctx->jscratch.reserve(ctx, 8 * (size_t)nq * o.n_max + 4 * (size_t)nq + 256, "eval staging")) != RB_OK) return rc;
-  p = ctx->jscratch.ptr;
-  double *uw = (double *)p;
+  if ((rc = ctx->jscratch.reserve(ctx, 8 * (size_t)nq * o.n_max + 4 * (size_t)nq + 256, "eval staging")) != RB_OK)
+    return rc;
+  double *uw = (double *)ctx->jscratch.ptr;
   int *nsz = (int *)(uw + (size_t)nq * o.n_max);
   rb_query_info *info = own_info(ctx, nq);
   if (!info) return set_error(ctx, RB_ERR_OOM, "info scratch");
@@ -584,6 +985,7 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   k_mixed_init<<<std::min(nq, ctx->sms * 8), 128, 0, st>>>(nq, o.n_max, nsz, nullptr, info);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
+  cudaMemsetAsync(M->dev_words, 0, 8, st);
   if ((rc = mixed_contract(ctx, d_mu, nullptr, nq, nsz, uw, info, st)) != RB_OK) return rc;
   LuParams lp{};
   lp.o = o;
@@ -593,6 +995,7 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   lp.nb = M->nb;
   lp.ldj = M->Npad;
   lp.max_iter = ctx->cfg.max_iter;
+  lp.A32 = M->A32;
   lp.Jc = M->Jc;
   lp.Rc = M->Rc;
   lp.u = uw;
@@ -602,15 +1005,7 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   lp.R_out = d_R;
   lp.J_out = d_J;
   if ((rc = launch_lu(ctx, lp, nq, st)) != RB_OK) return rc;
-  e = cudaMemcpyAsync(M->h_words, M->dev_words, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "rb_eval (mixed)");
-  if (M->h_words[1]) return set_error(ctx, RB_ERR_TIMEOUT, "tensor-core pipeline wait gave up (code %d)", M->h_words[1]);
-  return RB_OK;
+  return check_words(ctx, st, "rb_eval (mixed)");
 }
 
 }  // namespace rb
-
-extern "C" int rb_debug_last_launches(rb_ctx *ctx) {
-  return (ctx && ctx->mixed) ? ctx->mixed->last_launches : 0;
-}

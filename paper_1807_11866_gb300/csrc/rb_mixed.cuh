@@ -10,19 +10,22 @@ enum { kPlain = 0, kSliced = 1 };
 constexpr int kTcBN = 128;     // output tile width (columns (k, j))
 constexpr int kDigitBits = 7;  // signed digits |d| <= 127 of the sliced product
 
+// One tcgen05 GEMM launch. Columns c = k * nj + j (k < nk, j < nj) of W; rows b = queries.
+// K is split in up to two segments with their own fixed-point grids (sliced mode):
+// segment 0 = convection (q, l), segment 1 = linear affine term (q).
 struct TcGemmParams {
   int m_tiles, n_tiles;  // 128-row (query) and kTcBN-column tiles
-  int kb;                // K blocks of 64
-  int S;                 // digit slices (sliced mode)
+  int kb[2];             // K blocks of 64 per segment (kb[1] = 0: no second segment)
+  int S[2];              // digit slices per segment (sliced mode)
   int b_pad, n_pad;      // rows between consecutive slices of X and of W
   int nq;                // valid query rows
-  int nb;                // Jacobian size of the layout (columns valid: nb * nb)
-  int wexp;              // exponent of the W fixed-point grid
+  int nk, nj;            // output rows per query and contraction length (columns = nk * nj)
+  int wexp[2];           // exponent of the W fixed-point grid per segment
   int ldj;               // row stride of Jc
   float *Jc;             // plain: [b_pad][n_pad] FP32
-  const int *xexp;       // sliced: per-row exponent of X
-  const float2 *uf;      // sliced: u_b[j] as (hi, lo) floats, [b_pad][nb]
-  double *Rc;            // sliced: [b_pad][nb], accumulated with atomics
+  const int *xexp;       // sliced: per-row exponent of X, [2][b_pad]
+  const float2 *ufT;     // sliced: u_b[j] as (hi, lo) floats, transposed [nj][b_pad]
+  double *out;           // sliced: [b_pad][nk], accumulated with atomics
   int *err;              // device error word (bounded waits)
 };
 

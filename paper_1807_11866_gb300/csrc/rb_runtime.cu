@@ -103,6 +103,46 @@ static int upload(rb_ctx *ctx, void **dst, const void *src, size_t bytes, const 
 }
 
 // ---------------------------------------------------------------------------------------
+// per-kernel event timing
+static cudaEvent_t pool_event(rb_ctx *ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int prof_begin(rb_ctx *ctx, int kind, cudaStream_t st) {
+  if (!ctx->prof) return -1;
+  ProfMark m{kind, pool_event(ctx), pool_event(ctx)};
+  if (!m.a || !m.b) return -1;
+  cudaEventRecord(m.a, st);
+  ctx->marks.push_back(m);
+  return (int)ctx->marks.size() - 1;
+}
+
+void prof_end(rb_ctx *ctx, int mark, cudaStream_t st) {
+  if (mark < 0 || mark >= (int)ctx->marks.size()) return;
+  cudaEventRecord(ctx->marks[mark].b, st);
+}
+
+void prof_collect(rb_ctx *ctx) {
+  for (auto &m : ctx->marks) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(m.b) == cudaSuccess && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+      ctx->prof_ms[m.kind] += ms;
+      ctx->prof_n[m.kind] += 1;
+    }
+    ctx->event_pool.push_back(m.a);
+    ctx->event_pool.push_back(m.b);
+  }
+  ctx->marks.clear();
+}
+
+// ---------------------------------------------------------------------------------------
 // FP64 path: one fused kernel per batch (all Newton iterations in-kernel), then pressure.
 int solve_fp64(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
                double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st) {
@@ -133,7 +173,9 @@ int solve_fp64(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, c
     if (rc != RB_OK) return rc;
     p.jscratch = (double *)ctx->jscratch.ptr;
   }
+  const int mk = prof_begin(ctx, RB_K_NEWTON_FP64, st);
   cudaError_t e = launch_newton_fp64(p, ctx->sms, st);
+  prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_fp64 launch");
   return RB_OK;
 }
@@ -154,7 +196,9 @@ int solve_pressure(rb_ctx *ctx, const double *d_mu, const double *d_theta, int n
   pp.info = d_info;
   if (pressure_smem_bytes(o) > (size_t)ctx->max_smem)
     return set_error(ctx, RB_ERR_ARG, "pressure system too large");
+  const int mk = prof_begin(ctx, RB_K_PRESSURE, st);
   cudaError_t e = launch_pressure(pp, ctx->sms, st);
+  prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure launch");
   return RB_OK;
 }
@@ -171,11 +215,9 @@ int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, in
     if (rc != RB_OK) return rc;
     info = (rb_query_info *)ctx->info_scratch.ptr;
   }
-  int rc;
-  if (ctx->cfg.precision == RB_PREC_FP64)
-    rc = solve_fp64(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
-  else
-    rc = solve_mixed(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
+  if (ctx->cfg.precision == RB_PREC_MIXED)  // pressure recovery included
+    return solve_mixed(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
+  int rc = solve_fp64(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
   if (rc != RB_OK) return rc;
   return solve_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
 }
@@ -281,6 +323,9 @@ void rb_destroy(rb_ctx *ctx) {
   ctx->eval_scratch.release(ctx);
   for (auto &kv : ctx->sizes) cudaFree(kv.first);
   ctx->sizes.clear();
+  prof_collect(ctx);
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  ctx->event_pool.clear();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   t_err.erase(ctx);
   delete ctx;
@@ -423,6 +468,28 @@ int rb_eval(rb_ctx *ctx, const double *mu, int n_queries, int n, const double *u
   if (e == cudaSuccess && J_out) e = cudaMemcpyAsync(J_out, d_J, 8 * nq * nn * nn, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rb_eval");
+  return RB_OK;
+}
+
+int rb_profile(rb_ctx *ctx, int enable) {
+  if (!ctx) return RB_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  prof_collect(ctx);
+  for (int k = 0; k < RB_K_COUNT; ++k) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_n[k] = 0;
+  }
+  ctx->prof = enable != 0;
+  return RB_OK;
+}
+
+int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launches) {
+  if (!ctx) return RB_ERR_ARG;
+  if (kernel < 0 || kernel >= RB_K_COUNT) return set_error(ctx, RB_ERR_ARG, "kernel id %d", kernel);
+  cudaSetDevice(ctx->device);
+  prof_collect(ctx);
+  if (total_ms) *total_ms = ctx->prof_ms[kernel];
+  if (launches) *launches = ctx->prof_n[kernel];
   return RB_OK;
 }
 

@@ -24,8 +24,10 @@ RB_N_MAX, RB_M_MAX, RB_Q_MAX = 320, 128, 64
 
 EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
            "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
-           "rb_serve_start", "rb_serve_stop", "rb_serve_submit", "rb_serve_poll",
-           "rb_serve_stats"]
+           "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
+           "rb_serve_submit", "rb_serve_poll", "rb_serve_stats"]
+RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
+              "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>"]
 
 
 class rb_operators(ctypes.Structure):
@@ -77,6 +79,8 @@ def library():
         L.rb_solve_device.argtypes = [P, P, I, P, P, P, P, P]
         L.rb_eval.argtypes = [P, P, I, I, P, I, P, P]
         L.rb_gepp_solve.argtypes = [P, I, I, P, P, P, P]
+        L.rb_profile.argtypes = [P, I]
+        L.rb_profile_read.argtypes = [P, I, P, P]
         L.rb_serve_start.argtypes = [P]
         L.rb_serve_stop.argtypes = [P, I]
         L.rb_serve_submit.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_uint64)]
@@ -233,6 +237,20 @@ class Context:
         self._check(library().rb_gepp_solve(self.h, n, batch, _ptr(M), _ptr(rhs), _ptr(x),
                                             _ptr(st)), "rb_gepp_solve")
         return x, st
+
+    # --- profiling ----------------------------------------------------------------------
+    def rb_profile(self, enable=True):
+        return self._check(library().rb_profile(self.h, int(enable)), "rb_profile")
+
+    def rb_profile_read(self):
+        """{kernel name: (total ms, launches)} of the calls made since rb_profile(1)."""
+        out = {}
+        for k, name in enumerate(RB_K_NAMES):
+            ms, n = ctypes.c_double(), ctypes.c_longlong()
+            self._check(library().rb_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)),
+                        "rb_profile_read")
+            out[name] = (ms.value, n.value)
+        return out
 
     # --- serving ------------------------------------------------------------------------
     def rb_serve_start(self):

@@ -57,7 +57,8 @@ def test_eval_residual_and_jacobian(rb, n, qc, c_dtype):
         sc = term_scale(o, ops, n, th, u[b])
         assert np.max(np.abs(R[b] - Rr) / sc) <= 1e-12, b
         Jc, Jcr = J[b] - A, Jr - A
-        assert np.abs(Jc - Jcr).max() <= 2 ** -7 * np.abs(Jcr).max() + 1e-12 * np.abs(A).max()
+        # A(mu) enters the FP32 Jacobian rounded to FP32, the convection part from BF16 operands
+        assert np.abs(Jc - Jcr).max() <= 2 ** -7 * np.abs(Jcr).max() + 2e-7 * np.abs(A).max()
 
 
 @pytest.mark.parametrize("n", [2, 20, 50])
