@@ -330,18 +330,16 @@ def main():
 
 
 FP64_PEAK_TFLOPS = 1.196  # DFMA probe on this machine's GB300 (152 SMs at 2070 MHz)
-DIGITS = int(os.environ.get("RB_DIGITS", "6"))            # convection segment
-DIGITS_LIN = int(os.environ.get("RB_DIGITS_LINEAR", "7"))  # linear (A) segment
+DIGITS = int(os.environ.get("RB_DIGITS", "6"))  # digit slices of the sliced convection product
 
 
 def dominant_kernel_roofline(prec, wl, q, info, kprof, steps):
     """Roofline of the kernel with the largest device time in the timed region.
     Algorithmic work counts only the useful part: per active query-iteration of size n,
       fused FP64 Newton: 2 (Q_c n^3 + Q_a n^2) + 2 n^3 / 3 + 2 n^2  FLOP (FP64),
-      sliced residual GEMM: 2 n^2 (P0 Q_c n + P1 Q_a) FLOP of BF16 digit products
-        (P = S (S + 1) / 2 digit pairs per segment),
-      sliced pressure GEMM: 2 m n (P0 Q_c n + P1 Q_a) per converged query,
-      Jacobian GEMM: 2 Q_c n^3 FLOP (BF16)."""
+      sliced residual GEMM: P 2 Q_c n^3 FLOP of BF16 digit products (P = S (S + 1) / 2 pairs),
+      sliced pressure GEMM: P 2 Q_c m n^2 per converged query,
+      Jacobian GEMM: 3 x 2 Q_c n^3 FLOP (split BF16 products)."""
     peaks, kind = measured_peaks()
     n = q.n.astype(np.float64)
     it = info["iters"].astype(np.float64)
@@ -358,13 +356,13 @@ def dominant_kernel_roofline(prec, wl, q, info, kprof, steps):
                  "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                  "peak_source": "measured FP64 FMA probe (152 SMs, 2070 MHz)",
                  "launches": launches}, kernels)
-    p0, p1 = DIGITS * (DIGITS + 1) // 2, DIGITS_LIN * (DIGITS_LIN + 1) // 2
+    p0 = DIGITS * (DIGITS + 1) // 2
     if dom == "k_tc_gemm<sliced>":
-        per_q = 2.0 * n ** 2 * (p0 * wl.q_c * n + p1 * wl.q_a)
+        per_q = 2.0 * n ** 2 * p0 * wl.q_c * n
     elif dom == "k_tc_gemm<sliced,pressure>":
-        per_q = 2.0 * wl.m * n * (p0 * wl.q_c * n + p1 * wl.q_a) / np.maximum(it, 1)
+        per_q = 2.0 * wl.m * n * p0 * wl.q_c * n / np.maximum(it, 1)
     else:
-        per_q = 2.0 * wl.q_c * n ** 3
+        per_q = 3 * 2.0 * wl.q_c * n ** 3
     flops = steps * float(np.sum(it * per_q))
     ach = flops / (ms * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))

@@ -12,7 +12,8 @@
 // The pressure right-hand side (Eq. sup-vvar) uses the same X with W = (2 Cs, As).
 //
 // Two epilogues:
-//  * kPlain: X, W rounded to BF16, FP32 accumulation; writes T (FP32) -> Jacobian for the LU.
+//  * kPlain: X, W split into BF16 hi + lo parts, x_hi w_hi + x_hi w_lo + x_lo w_hi accumulated in
+//    FP32 (about 16 significant bits); writes T (FP32) -> Jacobian for the LU.
 //  * kSliced: error-free sliced product (after Ozaki, Ogita, Oishi and Rump, 2012). Per segment,
 //    X rows and W are split into S signed 7-bit digit slices on fixed-point grids (per-row
 //    exponent for X, one exponent for W): X = 2^ex sum_i x_i 2^-7i, W = 2^ew sum_j w_j 2^-7j
@@ -67,8 +68,8 @@ __device__ __forceinline__ int num_levels(int mode, const TcGemmParams &p) {
 
 __device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int idx) {
   Level v;
-  if (mode == kPlain) {
-    v.seg = 0; v.kb_off = 0; v.kb = p.kb[0]; v.L = 0; v.ilo = 1; v.npairs = 1;
+  if (mode == kPlain) {  // products of the split operands, one accumulator
+    v.seg = 0; v.kb_off = 0; v.kb = p.kb[0]; v.L = 0; v.ilo = 1; v.npairs = p.nsplit;
     return v;
   }
   const int n0 = p.kb[0] > 0 ? p.S[0] : 0;  // levels of segment 0
@@ -146,8 +147,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             uint8_t *sa = smem + s * SM::kStage;
             uint8_t *sb = sa + SM::kTileA;
             const int pr = idx / lv.kb, kk = lv.kb_off + idx % lv.kb;
-            const int xi = (MODE == kPlain) ? 0 : (lv.ilo + pr - 1);
-            const int wj = (MODE == kPlain) ? 0 : (lv.L - (lv.ilo + pr) - 1);
+            // plain split products: (x_hi, w_hi), (x_hi, w_lo), (x_lo, w_hi)
+            const int xi = (MODE == kPlain) ? pr : (lv.ilo + pr - 1);
+            const int wj = (MODE == kPlain) ? (pr == 1 ? 1 : 0) : (lv.L - (lv.ilo + pr) - 1);
             mbar_expect_tx(&full[s], SM::kStage);
             tma_load_2d(sa, &tmX, &full[s], kk * kBK, xi * p.b_pad + m0);
             tma_load_2d(sb, &tmW, &full[s], kk * kBK, wj * p.n_pad + n0);

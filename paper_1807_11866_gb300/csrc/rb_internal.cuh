@@ -81,6 +81,45 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return s;
 }
 
+// ---- double-float ("float-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2 ----
+// Used where FP64 accuracy is needed for O(n^2) work per query: GB300's FP64 pipe is narrow.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (ah, al) += (xh + xl) (yh + yl), the product's error kept by an FMA split
+__device__ __forceinline__ void df_fma(float &ah, float &al, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float pe = fmaf(xh, yh, -p);
+  pe = fmaf(xh, yl, pe);
+  pe = fmaf(xl, yh, pe);
+  float s, e;
+  two_sum(ah, p, s, e);
+  ah = s;
+  al += e + pe;
+}
+
+__device__ __forceinline__ void df_split(double v, float &h, float &l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+// warp-wide sum of double-float values, result in every lane as a double
+__device__ __forceinline__ double df_warp_sum(float h, float l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum(h, h2, s, e);
+    h = s;
+    l = l + l2 + e;
+  }
+  return (double)h + (double)l;
+}
+
 // (|value|, row) argmax with the first row winning ties.
 template <typename T>
 __device__ __forceinline__ void argmax_merge(T &v, int &r, T v2, int r2) {
@@ -191,11 +230,23 @@ __device__ bool gepp_solve_warp(T *M, int ld, int n, T *b) {
     for (int i = p + 1 + lane; i < n; i += 32) M[(size_t)i * ld + p] = M[(size_t)i * ld + p] / piv;
     __syncwarp();
     const T bp = b[p];
-    for (int j = p + 1 + lane; j < n; j += 32) {
-      const T mpj = M[(size_t)p * ld + j];
-      for (int i = p + 1; i < n; ++i) M[(size_t)i * ld + j] -= M[(size_t)i * ld + p] * mpj;
+    // trailing update: lanes over rows, 4 columns per step (independent loads in flight)
+    for (int i = p + 1 + lane; i < n; i += 32) {
+      T *Mi = M + (size_t)i * ld;
+      const T *Mp = M + (size_t)p * ld;
+      const T lip = Mi[p];
+      int j = p + 1;
+      for (; j + 4 <= n; j += 4) {
+        const T a0 = Mi[j], a1 = Mi[j + 1], a2 = Mi[j + 2], a3 = Mi[j + 3];
+        const T p0 = Mp[j], p1 = Mp[j + 1], p2 = Mp[j + 2], p3 = Mp[j + 3];
+        Mi[j] = a0 - lip * p0;
+        Mi[j + 1] = a1 - lip * p1;
+        Mi[j + 2] = a2 - lip * p2;
+        Mi[j + 3] = a3 - lip * p3;
+      }
+      for (; j < n; ++j) Mi[j] -= lip * Mp[j];
+      b[i] -= lip * bp;
     }
-    for (int i = p + 1 + lane; i < n; i += 32) b[i] -= M[(size_t)i * ld + p] * bp;
     __syncwarp();
   }
   for (int i = n - 1; i >= 0; --i) {

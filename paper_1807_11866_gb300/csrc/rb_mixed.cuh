@@ -17,6 +17,7 @@ struct TcGemmParams {
   int m_tiles, n_tiles;  // 128-row (query) and kTcBN-column tiles
   int kb[2];             // K blocks of 64 per segment (kb[1] = 0: no second segment)
   int S[2];              // digit slices per segment (sliced mode)
+  int nsplit;            // plain mode: 1 (BF16) or 3 (split BF16: hi*hi + hi*lo + lo*hi)
   int b_pad, n_pad;      // rows between consecutive slices of X and of W
   int nq;                // valid query rows
   int nk, nj;            // output rows per query and contraction length (columns = nk * nj)
