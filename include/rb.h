@@ -130,7 +130,8 @@ int rb_create(rb_ctx **out, const rb_config *cfg, int device);
 /* Destroy a context and free all its device and pinned-host memory (stops the server). */
 void rb_destroy(rb_ctx *ctx);
 
-/* Last error message of this context on the calling thread ("" if none). Never NULL. */
+/* Last error message of this context on the calling thread ("" if none). Never NULL.
+ * ctx == NULL gives the last error of a context-free call (rb_gepp_solve_static). */
 const char *rb_last_error(rb_ctx *ctx);
 
 /* Copy an operator set to the device and build the per-precision layouts (Sec. 3.5-3.6:
@@ -177,6 +178,26 @@ int rb_eval(rb_ctx *ctx, const double *mu, int n_queries, int n, const double *u
  * The dense solve of Sec. 4.1 (Eq. blocksolve-1), exposed for verification. */
 int rb_gepp_solve(rb_ctx *ctx, int n, int batch, const double *M, const double *rhs,
                   double *x_out, int *status);
+
+/* ---- batched solve without allocation -----------------------------------------------------
+ * No counterpart in the paper: this entry point serves callers that cannot allocate device
+ * memory when they solve -- work recorded into a CUDA graph capture, processes held to a fixed
+ * memory budget, or hosts that only lend the library pre-allocated buffers. It solves
+ * M_s x_s = rhs_s for s < batch with the same partial pivoting as rb_gepp_solve, from DEVICE
+ * buffers: d_M [batch][n][n] row-major (not modified), d_rhs [batch][n], d_x [batch][n],
+ * d_status [batch] (0 or RB_Q_SINGULAR), asynchronously on cuda_stream (NULL: legacy stream).
+ * The working copies of the matrices live in one file-scope device array of
+ * RB_STATIC_SCRATCH_BYTES, which every GPU that loads this library holds until the process
+ * exits; the call makes no cudaMalloc, cudaFree or other allocating call. n outside
+ * 1..RB_STATIC_N_MAX or batch < 0 returns RB_ERR_ARG with a message for rb_last_error(NULL).
+ * The first call on a device looks up the array's device address with that device current, so
+ * make that first call before any stream capture. Every call uses the same array and it keeps
+ * the previous call's contents (each system is copied in before use): calls whose GPU work
+ * overlaps (other streams or threads) race on it, so the caller must order them. */
+#define RB_STATIC_N_MAX 512
+#define RB_STATIC_SCRATCH_BYTES (16u << 20)
+int rb_gepp_solve_static(int n, int batch, const double *d_M, const double *d_rhs, double *d_x,
+                         int *d_status, void *cuda_stream);
 
 /* ---- per-kernel timing ------------------------------------------------------------------
  * While enabled, every kernel the context launches is bracketed by CUDA events on its

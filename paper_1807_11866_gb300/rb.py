@@ -21,10 +21,11 @@ RB_F64, RB_F32 = 0, 1
 RB_PREC_FP64, RB_PREC_MIXED = 0, 1
 RB_THETA_TRIG, RB_THETA_USER = 0, 1
 RB_N_MAX, RB_M_MAX, RB_Q_MAX = 320, 128, 64
+RB_STATIC_N_MAX, RB_STATIC_SCRATCH_BYTES = 512, 16 << 20
 
 EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
            "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
-           "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
+           "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
            "rb_serve_submit", "rb_serve_poll", "rb_serve_stats"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>"]
@@ -79,6 +80,7 @@ def library():
         L.rb_solve_device.argtypes = [P, P, I, P, P, P, P, P]
         L.rb_eval.argtypes = [P, P, I, I, P, I, P, P]
         L.rb_gepp_solve.argtypes = [P, I, I, P, P, P, P]
+        L.rb_gepp_solve_static.argtypes = [I, I, P, P, P, P, P]
         L.rb_profile.argtypes = [P, I]
         L.rb_profile_read.argtypes = [P, I, P, P]
         L.rb_serve_start.argtypes = [P]
@@ -109,6 +111,17 @@ def _ptr(a):
 
 def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def rb_gepp_solve_static(n, batch, d_M, d_rhs, d_x, d_status, stream=None):
+    """No-allocation batched solve on caller-owned device buffers (torch tensors or ints)."""
+    return library().rb_gepp_solve_static(n, batch, _ptr(d_M), _ptr(d_rhs), _ptr(d_x),
+                                          _ptr(d_status), stream)
+
+
+def rb_last_error_global() -> str:
+    """Last error of a context-free call on this thread."""
+    return library().rb_last_error(None).decode()
 
 
 def rb_config_default() -> rb_config:
