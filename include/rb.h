@@ -110,6 +110,8 @@ typedef struct {
   int use_graph;      /* capture per-iteration launches in CUDA graphs (default 1) */
   int autotune;       /* time kernel variants on first use per shape (default 1) */
   int theta_family;   /* RB_THETA_TRIG (default) or RB_THETA_USER */
+  int serve_slots;    /* serving: queries on the device at once (0: as many as the memory
+                         budget admits, at most 4096) */
 } rb_config;
 
 typedef struct {
@@ -235,6 +237,10 @@ int rb_serve_poll(rb_ctx *ctx, uint64_t ticket, double *u_out, double *p_out,
                   rb_query_info *info);
 /* Latency percentiles (seconds, submit to completion) and throughput since start. */
 int rb_serve_stats(rb_ctx *ctx, double *p50_s, double *p99_s, double *solves_per_s);
+/* Device slots of the running server: at most this many queries are on the GPU at once;
+ * later submissions wait until slots free up (admission by memory). Returns the count or an
+ * error code (< 0). */
+int rb_serve_slots(rb_ctx *ctx);
 
 #ifdef __cplusplus
 }

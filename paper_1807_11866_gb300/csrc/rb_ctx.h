@@ -41,6 +41,15 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
                double *d_R, double *d_J, cudaStream_t st);
 void mixed_release(rb_ctx *ctx);
 void serve_shutdown(rb_ctx *ctx);
+bool serve_running(const rb_ctx *ctx);
+// mixed-path pieces used by the server
+int mixed_prepare(rb_ctx *ctx, int capacity, cudaStream_t st);
+size_t mixed_slot_bytes(const rb_ctx *ctx);
+int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, double *d_u,
+                    rb_query_info *info, bool need_jacobian, bool need_exact, cudaStream_t st);
+int mixed_pressure_ok(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, const double *d_u,
+                      double *d_p, rb_query_info *info, cudaStream_t st);
+int mixed_error_word(rb_ctx *ctx, cudaStream_t st);
 
 // per-kernel event timing (active only while profiling is enabled)
 struct ProfMark {

@@ -342,7 +342,8 @@ struct LuParams {
   int *active;           // count of queries still active after this iteration
   int eval_only;         // 1: write R and J (FP64) to R_out / J_out instead of solving
   double *R_out, *J_out;
-  int rmode;             // residual source: kResZero, kResLow or kResExact
+  int rmode;             // residual source: kResZero, kResLow, kResExact, or -1: per query
+                         // from its iteration count (0 -> zero, 1 -> low, >= 2 -> exact)
 };
 
 // Residual source of one Newton iteration (the precision ladder of the inexact Newton):
@@ -350,7 +351,11 @@ struct LuParams {
 //   kResLow   R = (A(mu) + J~^c / 2) u - f(mu) from the FP32/BF16 Jacobian (Euler identity);
 //             only used to approach the root, never to declare convergence,
 //   kResExact R = [A(mu) u + C_mu(u, u)]_sliced - f(mu), FP64-accurate.
-enum { kResZero = 0, kResLow = 1, kResExact = 2 };
+enum { kResZero = 0, kResLow = 1, kResExact = 2, kResLadder = -1 };
+
+__device__ __forceinline__ int rung_of(int rmode, int iters) {
+  return rmode >= 0 ? rmode : (iters == 0 ? kResZero : (iters == 1 ? kResLow : kResExact));
+}
 
 struct LuSmem {
   int th, R, fm, red, tah, uh, rhs, J, total;  // offsets in bytes
@@ -374,13 +379,13 @@ struct LuSmem {
 // and R[k] = A(mu)[k][:] u (double-float) + convection part - f[k]. R rows at once keep R
 // independent A loads in flight per lane.
 template <int RR>
-__device__ __forceinline__ void lu_rows(const LuParams &p, int b, int n, int k0, const float2 *ta,
-                                        const float2 *u2, const double *fm, float *J, int ld,
-                                        double *R) {
+__device__ __forceinline__ void lu_rows(const LuParams &p, int rm, int b, int n, int k0,
+                                        const float2 *ta, const float2 *u2, const double *fm,
+                                        float *J, int ld, double *R) {
   const int lane = threadIdx.x & 31;
   const size_t nm = (size_t)p.o.n_max;
   const float *jc = p.Jc + (size_t)b * p.ldj;
-  const bool with_jc = p.rmode != kResZero;
+  const bool with_jc = rm != kResZero;
   float rh[RR], rl[RR], clow[RR];
 #pragma unroll
   for (int r = 0; r < RR; ++r) rh[r] = rl[r] = clow[r] = 0.f;
@@ -398,7 +403,7 @@ __device__ __forceinline__ void lu_rows(const LuParams &p, int b, int n, int k0,
         const float c = with_jc ? jc[(size_t)k * p.nb + j] : 0.f;
         const float v = (ah + al) + c;
         df_fma(rh[r], rl[r], ah, al, uj.x, uj.y);
-        if (p.rmode == kResLow) clow[r] = fmaf(0.5f * c, uj.x, clow[r]);
+        if (rm == kResLow) clow[r] = fmaf(0.5f * c, uj.x, clow[r]);
         if (p.eval_only)
           p.J_out[((size_t)b * n + k) * n + j] = (double)v;
         else
@@ -410,9 +415,9 @@ __device__ __forceinline__ void lu_rows(const LuParams &p, int b, int n, int k0,
   for (int r = 0; r < RR; ++r) {
     const int k = k0 + r;
     const double rlin = df_warp_sum(rh[r], rl[r]);
-    const float cl = p.rmode == kResLow ? warp_sum(clow[r]) : 0.f;
+    const float cl = rm == kResLow ? warp_sum(clow[r]) : 0.f;
     if (lane == 0 && k < n) {
-      const double conv = p.rmode == kResExact ? p.Rc[(size_t)b * p.nb + k] : (double)cl;
+      const double conv = rm == kResExact ? p.Rc[(size_t)b * p.nb + k] : (double)cl;
       R[k] = rlin + conv - fm[k];
     }
   }
@@ -456,7 +461,8 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
       ta[q] = make_float2(h, l);
     }
     __syncthreads();
-    for (int k0 = 4 * w; k0 < n; k0 += 4 * kWarps) lu_rows<4>(p, b, n, k0, ta, u2, fm, J, n, R);
+    const int rm = rung_of(p.rmode, qi.iters);
+    for (int k0 = 4 * w; k0 < n; k0 += 4 * kWarps) lu_rows<4>(p, rm, b, n, k0, ta, u2, fm, J, n, R);
     __syncthreads();
     if (p.eval_only) {
       for (int k = tid; k < n; k += blockDim.x) p.R_out[(size_t)b * n + k] = R[k];
@@ -488,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
       const double dn = sqrt(block_sum(dl, red));
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
-      else if (p.rmode != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+      else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
     }
     if (tid == 0) {
       p.info[b] = qi;
@@ -555,7 +561,8 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
       ta[q] = make_float2(h, l);
     }
     __syncwarp();
-    for (int k0 = 0; k0 < n; k0 += 8) lu_rows<8>(p, b, n, k0, ta, u2, fm, J, ld, R);
+    const int rm = rung_of(p.rmode, qi.iters);
+    for (int k0 = 0; k0 < n; k0 += 8) lu_rows<8>(p, rm, b, n, k0, ta, u2, fm, J, ld, R);
     __syncwarp();
     if (p.eval_only) {
       for (int k = lane; k < n; k += 32) p.R_out[(size_t)b * n + k] = R[k];
@@ -588,7 +595,7 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
       const double dn = sqrt(warp_sum(dl));
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
-      else if (p.rmode != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+      else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
     }
     if (lane == 0) {
       p.info[b] = qi;
@@ -1148,11 +1155,10 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   lp.u = d_u;
   lp.info = info;
   lp.active = M->dev_words;
+  lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
   for (int it = 0; it < ctx->cfg.max_iter; ++it) {
     cudaMemsetAsync(M->dev_words, 0, 4, st);
-    lp.rmode = it == 0 ? kResZero : (it == 1 ? kResLow : kResExact);
-    if (lp.rmode != kResZero &&
-        (rc = mixed_contract(ctx, d_mu, d_theta, nq, d_n, d_u, info, lp.rmode == kResExact, st)) != RB_OK)
+    if (it >= 1 && (rc = mixed_contract(ctx, d_mu, d_theta, nq, d_n, d_u, info, it >= 2, st)) != RB_OK)
       return rc;
     if ((rc = launch_lu(ctx, lp, nq, st)) != RB_OK) return rc;
     if ((rc = check_words(ctx, st, "mixed Newton step")) != RB_OK) return rc;
@@ -1164,6 +1170,65 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   }
   if (ctx->prof) prof_collect(ctx);
   return RB_OK;
+}
+
+// ---- pieces used by the continuous-batching server ----------------------------------------
+int mixed_prepare(rb_ctx *ctx, int capacity, cudaStream_t st) {
+  int rc = mixed_layouts(ctx, st);
+  if (rc != RB_OK) return rc;
+  if ((rc = mixed_batch_scratch(ctx, capacity)) != RB_OK) return rc;
+  return own_info(ctx, 1) ? RB_OK : set_error(ctx, RB_ERR_OOM, "info scratch");
+}
+
+// Device bytes one more slot of batch state costs (X operands, Jacobian, residual, LU).
+size_t mixed_slot_bytes(const rb_ctx *ctx) {
+  const DevOps &o = ctx->ops;
+  const size_t nb = o.n_max, Kpad0 = (size_t)round_up(o.q_c * o.n_max, 64);
+  const size_t Npad = (size_t)round_up(o.n_max * o.n_max, kTcBN);
+  const int S = 8;
+  return 2 * 3 * Kpad0 + 2 * S * Kpad0 + 8 + 8 * nb + 4 * Npad + 8 * nb + 8 * (size_t)(o.m + 1) +
+         8 * nb + 64;
+}
+
+// One Newton iteration for every live slot: the contraction work the slots' ladder rungs need,
+// then elimination and update (no host synchronisation).
+int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, double *d_u,
+                    rb_query_info *info, bool need_jacobian, bool need_exact, cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  int rc;
+  cudaMemsetAsync(M->dev_words, 0, 4, st);
+  if (need_jacobian &&
+      (rc = mixed_contract(ctx, d_mu, nullptr, nq, d_n, d_u, info, need_exact, st)) != RB_OK)
+    return rc;
+  LuParams lp{};
+  lp.o = ctx->ops;
+  lp.mu = d_mu;
+  lp.nsz = d_n;
+  lp.nq = nq;
+  lp.nb = M->nb;
+  lp.ldj = M->Npad;
+  lp.max_iter = ctx->cfg.max_iter;
+  lp.tol_upd = ctx->cfg.tol_update;
+  lp.tol_res = ctx->cfg.tol_res;
+  lp.A2 = M->A2;
+  lp.Jc = M->Jc;
+  lp.Rc = M->Rc;
+  lp.u = d_u;
+  lp.info = info;
+  lp.active = M->dev_words;
+  lp.rmode = kResLadder;
+  return launch_lu(ctx, lp, nq, st);
+}
+
+// Pressure for every slot whose status is RB_Q_OK.
+int mixed_pressure_ok(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, const double *d_u,
+                      double *d_p, rb_query_info *info, cudaStream_t st) {
+  if (!(ctx->ops.m > 0 && ctx->ops.B && d_p)) return RB_OK;
+  return mixed_pressure(ctx, d_mu, nullptr, nq, d_n, d_u, d_p, info, st);
+}
+
+int mixed_error_word(rb_ctx *ctx, cudaStream_t st) {
+  return check_words(ctx, st, "serving step");
 }
 
 int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u, int precision,

@@ -207,6 +207,8 @@ int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, in
                       const int *d_n, double *d_u, double *d_p, rb_query_info *d_info,
                       cudaStream_t st) {
   if (!ctx->loaded) return set_error(ctx, RB_ERR_STATE, "no operators loaded");
+  if (serve_running(ctx))
+    return set_error(ctx, RB_ERR_STATE, "the server owns this context's batch state; stop it first");
   if (nq == 0) return RB_OK;
   // per-query status is needed to gate pressure recovery
   rb_query_info *info = d_info;
@@ -278,6 +280,7 @@ void rb_config_default(rb_config *cfg) {
   cfg->use_graph = 1;
   cfg->autotune = 1;
   cfg->theta_family = RB_THETA_TRIG;
+  cfg->serve_slots = 0;
 }
 
 int rb_create(rb_ctx **out, const rb_config *cfg, int device) {
@@ -286,6 +289,7 @@ int rb_create(rb_ctx **out, const rb_config *cfg, int device) {
   rb_ctx *ctx = new rb_ctx();
   if (cfg) ctx->cfg = *cfg; else rb_config_default(&ctx->cfg);
   if (ctx->cfg.max_iter < 1 || ctx->cfg.precision < RB_PREC_FP64 || ctx->cfg.precision > RB_PREC_MIXED ||
+      ctx->cfg.serve_slots < 0 ||
       !(ctx->cfg.tol_update >= 0) || !(ctx->cfg.tol_res >= 0)) {
     delete ctx;
     return RB_ERR_ARG;
@@ -339,6 +343,8 @@ const char *rb_last_error(rb_ctx *ctx) {
 int rb_load_operators(rb_ctx *ctx, const rb_operators *ops) {
   if (!ctx) return RB_ERR_ARG;
   if (!ops) return set_error(ctx, RB_ERR_ARG, "ops is NULL");
+  if (serve_running(ctx)) return set_error(ctx, RB_ERR_STATE, "stop the server before reloading");
+  serve_shutdown(ctx);
   const int n = ops->n_max;
   if (n < 1 || n > RB_N_MAX) return set_error(ctx, RB_ERR_ARG, "n_max %d out of range 1..%d", n, RB_N_MAX);
   if (ops->q_a < 1 || ops->q_c < 1 || ops->q_f < 1 || ops->q_a > RB_Q_MAX || ops->q_c > RB_Q_MAX ||

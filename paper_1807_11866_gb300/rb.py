@@ -26,7 +26,7 @@ RB_STATIC_N_MAX, RB_STATIC_SCRATCH_BYTES = 512, 16 << 20
 EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
            "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
            "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
-           "rb_serve_submit", "rb_serve_poll", "rb_serve_stats"]
+           "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>"]
 
@@ -44,7 +44,8 @@ class rb_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol_update", ctypes.c_double),
                 ("tol_res", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("mem_budget", ctypes.c_size_t), ("use_graph", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("theta_family", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("theta_family", ctypes.c_int),
+                ("serve_slots", ctypes.c_int)]
 
 
 class rb_query_info(ctypes.Structure):
@@ -88,6 +89,7 @@ def library():
         L.rb_serve_submit.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_uint64)]
         L.rb_serve_poll.argtypes = [P, ctypes.c_uint64, P, P, P]
         L.rb_serve_stats.argtypes = [P, P, P, P]
+        L.rb_serve_slots.argtypes = [P]
         for name in EXPORTS:
             if name not in ("rb_config_default", "rb_destroy", "rb_last_error"):
                 getattr(L, name).restype = I
@@ -134,7 +136,7 @@ class Context:
     """An rb_ctx on one device. Methods mirror the C entry points one to one."""
 
     def __init__(self, precision=RB_PREC_FP64, tol_update=None, tol_res=None, max_iter=None,
-                 mem_budget=None, use_graph=None, device=0):
+                 mem_budget=None, use_graph=None, device=0, serve_slots=None):
         L = library()
         cfg = rb_config_default()
         cfg.precision = precision
@@ -148,6 +150,8 @@ class Context:
             cfg.mem_budget = mem_budget
         if use_graph is not None:
             cfg.use_graph = use_graph
+        if serve_slots is not None:
+            cfg.serve_slots = serve_slots
         self.cfg = cfg
         h = ctypes.c_void_p()
         rc = L.rb_create(ctypes.byref(h), ctypes.byref(cfg), device)
@@ -288,6 +292,12 @@ class Context:
         if rc == RB_PENDING:
             return None
         return u, p, info[0]
+
+    def rb_serve_slots(self):
+        rc = library().rb_serve_slots(self.h)
+        if rc < 0:
+            raise RbError(rc, f"rb_serve_slots: {self.last_error()}")
+        return rc
 
     def rb_serve_stats(self):
         a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
