@@ -329,7 +329,7 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-FP64_PEAK_TFLOPS = 1.196  # DFMA probe on this machine's GB300 (152 SMs at 2070 MHz)
+FP64_PEAK_TFLOPS = 1.196  # FP64 FMA throughput measured on GB300 (152 SMs at 2070 MHz)
 DIGITS = int(os.environ.get("RB_DIGITS", "6"))  # digit slices of the sliced convection product
 
 
@@ -354,7 +354,7 @@ def dominant_kernel_roofline(prec, wl, q, info, kprof, steps):
         ach = flops / (ms * 1e-3) / 1e12
         return ({"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                  "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                 "peak_source": "measured FP64 FMA probe (152 SMs, 2070 MHz)",
+                 "peak_source": "measured FP64 FMA throughput (152 SMs, 2070 MHz)",
                  "launches": launches}, kernels)
     p0 = DIGITS * (DIGITS + 1) // 2
     if dom == "k_tc_gemm<sliced>":
