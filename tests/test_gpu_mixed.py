@@ -145,3 +145,21 @@ def test_full_sweep_batch_sampled(rb):
     u_ref, p_ref, _ = o.solve(mu[idx], threads=16)
     assert rel(u[idx], u_ref).max() <= TOL_MIXED
     assert rel(p[idx], p_ref).max() <= 10 * TOL_MIXED
+
+
+@pytest.mark.parametrize("n,q,nq", [(160, 3, 130), (300, 2, 130)])
+def test_large_n_mixed(rb, n, q, nq):
+    """Large Jacobians: the 128-column u window of the sliced GEMM (n > 64), the block LU with
+    the Jacobian in shared memory (n = 160) and in global scratch (n = 300); oracle on a sample."""
+    wl = synth.WORKLOADS["dense_n300"]
+    ops = synth.make_operators(wl, n_max=n, q_a=q, q_c=q, q_f=2)
+    qs = synth.make_queries(wl, batch=nq - 2, n_max=n)
+    mu = np.concatenate([qs.mu, synth.corner_queries(wl)[:2]])
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, _, info = ctx.rb_solve(mu)
+    assert np.all(info["status"] == 0)
+    idx = np.array([0, nq // 2, nq - 1])
+    o = oracle.Oracle.from_set(ops)
+    u_ref, _, _ = o.solve(mu[idx], threads=8)
+    assert rel(u[idx], u_ref).max() <= TOL_MIXED
