@@ -20,9 +20,10 @@
 //    (S may differ per segment).
 //    A product of two digits is below 2^14, so up to 1024 of them add exactly in FP32. Pairs
 //    (i, j) with i + j = L share the scale 2^(ex + ew - 7L); each level is accumulated in TMEM
-//    in chunks of at most 1024 terms, every chunk is drained exactly, contracted with u_b[j] in
-//    double-float arithmetic and added, scaled, into the FP64 output. Pairs with i + j > S + 1
-//    are dropped (relative truncation ~2^-7S of the fixed-point range).
+//    in chunks of at most 1024 terms, every chunk is drained exactly and added, scaled by its
+//    power of two, into per-column double-float sums held in registers; at the end of the tile
+//    the sums are contracted with u_b[j] (double-float) and added into the FP64 output. Pairs
+//    with i + j > S + 1 are dropped (relative truncation ~2^-7S of the fixed-point range).
 //
 // Roles (320 threads): warp 0 issues TMA loads into a STAGES-deep shared-memory ring, warp 1
 // allocates TMEM and issues tcgen05.mma (one lane), warps 2-9 drain the two TMEM accumulator
@@ -42,9 +43,6 @@ constexpr int kChunkSteps = 16;  // 16 k-blocks of 64 = 1024 exact terms per chu
 constexpr int kEpiWarps = 8;     // epilogue warps: 2 per TMEM lane quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreadsTc = 64 + kEpiThreads;
-// Levels whose scale is at most 2^-21 of the leading level are contracted in plain FP32: their
-// rounding (2^-24 relative) stays below 2^-45 of the result.
-constexpr int kFastLevel = 5;
 
 template <int BN, int STAGES, int UW>
 struct TcSmem {
@@ -119,8 +117,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     fence_barrier_init();
     fence_proxy_async();
   }
+  // TMEM columns: [0, 2 BN) two accumulator buffers; sliced mode adds [2 BN, 4 BN) for the
+  // per-column double-float sums (hi, lo) of each epilogue half
+  constexpr uint32_t kTmemCols = MODE == kSliced ? 4 * BN : 2 * BN;
   if (warp == 1) {
-    tmem_alloc(tmem_slot, 2 * BN);
+    tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -226,6 +227,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         mbar_arrive(ufull);
         if (!mbar_wait(ufull, tile_it & 1, p.err, 7)) { bad = true; break; }
       }
+      // sliced mode: per-column double-float sums over all level chunks of this tile, in TMEM
+      // columns [2 BN + half 2 HC, +HC) (hi) and [+HC, +2 HC) (lo) of this thread's lane
+      const uint32_t tsum = tmem_base + ((uint32_t)(q * 32) << 16) + 2 * BN + half * 2 * HC;
+      if (MODE == kSliced) {
+        uint32_t z[16];
+#pragma unroll
+        for (int v = 0; v < 16; ++v) z[v] = 0u;
+#pragma unroll
+        for (int g = 0; g < 2 * HC / 16; ++g) tmem_st_x16(tsum + g * 16, z);
+        tmem_st_wait();
+      }
       for (int li = 0; li < n_levels && !bad; ++li) {
         const Level lv = level_of(MODE, p, li);
         const int nsteps = lv.npairs * lv.kb;
@@ -251,67 +263,72 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                                     __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
             }
           } else {
-            // contract the exact chunk with u_b[j] over this thread's columns (k, j)
-            const bool live = b < p.nq;
-            const bool fast = lv.L >= kFastLevel + 2;
-            const double scale =
-                live ? ldexp(1.0, p.xexp[lv.seg * p.b_pad + b] + p.wexp[lv.seg] - kDigitBits * lv.L)
-                     : 0.0;
-            const int c_begin = n0 + half * HC;
-            int g = c_begin, k = c_begin / nj, j = c_begin % nj;
-            int jw = nj <= UW ? j : (j - jb + nj) % nj;
-            // four independent double-float accumulators (ILP), merged at each row end
-            float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+            // add the exact chunk, scaled by its level (and segment) relative to segment 0, into
+            // this thread's per-column double-float sums (exact power-of-two scaling)
+            const int d = (lv.seg ? (p.xexp[p.b_pad + b] + p.wexp[1] - p.xexp[b] - p.wexp[0]) : 0) -
+                          kDigitBits * lv.L;
+            const float sc = ldexpf(1.0f, d);
 #pragma unroll 1
-            for (int c = 0; c < HC; c += 32) {
-              uint32_t r[32];
-              tmem_ld_x32(taddr + c, r);
+            for (int g = 0; g < HC / 16; ++g) {
+              uint32_t r[16], hi[16], lo[16];
+              tmem_ld_x16(taddr + g * 16, r);
+              tmem_ld_x16(tsum + g * 16, hi);
+              tmem_ld_x16(tsum + HC + g * 16, lo);
               tmem_ld_wait();
-              if (live) {
 #pragma unroll
-                for (int v = 0; v < 32; ++v, ++g) {
-                  if (g < total) {
-                    const float x = __uint_as_float(r[v]);
-                    const float2 u2 = uw[jw * kBM + row];
-                    if (fast) {
-                      ah[v & 3] = fmaf(x, u2.x, ah[v & 3]);
-                    } else {
-                      // x (uh + ul) = pp + e + x ul, pp = fl(x uh), e its exact error
-                      const float pp = x * u2.x;
-                      const float e = fmaf(x, u2.x, -pp);
-                      const float tl = fmaf(x, u2.y, e);
-                      const float a = ah[v & 3];
-                      const float s = a + pp;  // two-sum (a, pp)
-                      const float bb = s - a;
-                      al[v & 3] += ((a - (s - bb)) + (pp - bb)) + tl;
-                      ah[v & 3] = s;
-                    }
-                    ++jw;
-                    if (++j == nj) {
-                      const double tot = ((double)ah[0] + (double)ah[1]) + ((double)ah[2] + (double)ah[3]) +
-                                         (((double)al[0] + (double)al[1]) + ((double)al[2] + (double)al[3]));
-                      atomicAdd(p.out + (size_t)b * p.nk + k, tot * scale);
-#pragma unroll
-                      for (int i = 0; i < 4; ++i) ah[i] = al[i] = 0.f;
-                      j = 0;
-                      ++k;
-                      if (nj <= UW) jw = 0;
-                    }
-                  }
-                }
+              for (int v = 0; v < 16; ++v) {
+                const float x = __uint_as_float(r[v]) * sc;
+                float sh, e;
+                two_sum(__uint_as_float(hi[v]), x, sh, e);
+                hi[v] = __float_as_uint(sh);
+                lo[v] = __float_as_uint(__uint_as_float(lo[v]) + e);
               }
+              tmem_st_x16(tsum + g * 16, hi);
+              tmem_st_x16(tsum + HC + g * 16, lo);
             }
-            if (live && k < p.nk) {
-              const double tot = ((double)ah[0] + (double)ah[1]) + ((double)ah[2] + (double)ah[3]) +
-                                 (((double)al[0] + (double)al[1]) + ((double)al[2] + (double)al[3]));
-              if (tot != 0.0) atomicAdd(p.out + (size_t)b * p.nk + k, tot * scale);
-            }
+            tmem_st_wait();
           }
           tc_fence_before();
           mbar_arrive(&tempty[buf]);
         }
       }
-      if (MODE == kSliced) mbar_arrive(uempty);
+      if (MODE == kSliced && !bad) {
+        // contract the tile's column sums with u_b[j]: out[b][k] += 2^(ex + ew) sum_j T[(k,j)] u_j
+        // every lane executes the warp-collective TMEM loads; rows beyond the batch only skip the
+        // arithmetic and the stores
+        const bool live = b < p.nq;
+        const double scale = live ? ldexp(1.0, p.xexp[b] + p.wexp[0]) : 0.0;
+        const int c_begin = n0 + half * HC;
+        int k = c_begin / nj, j = c_begin % nj;
+        int jw = nj <= UW ? j : (j - jb + nj) % nj;
+        const int cend = min(HC, total - c_begin);
+        float ah = 0.f, al = 0.f;
+#pragma unroll 1
+        for (int g = 0; g < HC / 16; ++g) {
+          uint32_t hi[16], lo[16];
+          tmem_ld_x16(tsum + g * 16, hi);
+          tmem_ld_x16(tsum + HC + g * 16, lo);
+          tmem_ld_wait();
+#pragma unroll
+          for (int v = 0; v < 16; ++v) {
+            if (g * 16 + v < cend) {
+              const float2 u2 = uw[jw * kBM + row];
+              df_fma(ah, al, __uint_as_float(hi[v]), __uint_as_float(lo[v]), u2.x, u2.y);
+              ++jw;
+              if (++j == nj) {
+                if (live) atomicAdd(p.out + (size_t)b * p.nk + k, ((double)ah + (double)al) * scale);
+                ah = al = 0.f;
+                j = 0;
+                ++k;
+                if (nj <= UW) jw = 0;
+              }
+            }
+          }
+        }
+        if (live && k < p.nk && cend > 0 && (ah != 0.f || al != 0.f))
+          atomicAdd(p.out + (size_t)b * p.nk + k, ((double)ah + (double)al) * scale);
+        mbar_arrive(uempty);
+      }
     }
   }
   tc_fence_before();
@@ -319,7 +336,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem_base, 2 * BN);
+    tmem_dealloc(tmem_base, kTmemCols);
   }
 }
 
