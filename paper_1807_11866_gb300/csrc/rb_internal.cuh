@@ -201,62 +201,171 @@ __device__ bool gepp_solve_block(T *M, int ld, int n, T *b, double *red) {
   return false;
 }
 
-// Warp-cooperative variant of gepp_solve_block for one small system per warp (no block
-// barriers): same pivoting rule, same operation order per entry.
-template <typename T>
-__device__ bool gepp_solve_warp(T *M, int ld, int n, T *b) {
+// ---- warp-level elimination for small systems (one warp per system, FP32) ----------------
+// Lane r % 32 owns row r of the register-held vectors below: kWarpRows slots per lane.
+constexpr int kWarpRows = 3;  // n <= 96
+
+// Pivot key of |v| in row i (i < 256): the magnitude's leading 15 mantissa bits, then the lower
+// row index on ties, so that one unsigned warp maximum picks the pivot (partial pivoting, up to
+// a relative 2^-15 preference for the first row).
+__device__ __forceinline__ unsigned pivot_key(float v, int i) {
+  return (__float_as_uint(fabsf(v)) & 0xFFFFFF00u) | (unsigned)(255 - i);
+}
+
+// The value that row k's owner lane holds in y[k / 32], broadcast to all lanes.
+__device__ __forceinline__ float row_value(const float (&y)[kWarpRows], int k) {
+  const int s = k >> 5;
+  const float v = s == 0 ? y[0] : (s == 1 ? y[1] : y[2]);
+  return __shfl_sync(0xffffffffu, v, k & 31);
+}
+
+// Back substitution with the upper triangle of M (row stride ld): y holds the right-hand side
+// (lane-owned rows) and receives the solution.
+__device__ __forceinline__ void backsub_warp(const float *M, int ld, int n, float (&y)[kWarpRows]) {
   const int lane = threadIdx.x & 31;
-  for (int p = 0; p < n; ++p) {
-    T best = T(-1);
-    int brow = n;
-    for (int i = p + lane; i < n; i += 32) argmax_merge<T>(best, brow, fabs(M[(size_t)i * ld + p]), i);
+  float d[kWarpRows];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T v2 = __shfl_xor_sync(0xffffffffu, best, o);
-      const int r2 = __shfl_xor_sync(0xffffffffu, brow, o);
-      argmax_merge<T>(best, brow, v2, r2);
+  for (int s = 0; s < kWarpRows; ++s) {
+    const int k = lane + 32 * s;
+    d[s] = k < n ? __frcp_rn(M[(size_t)k * ld + k]) : 0.f;
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    float own[kWarpRows];
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s) own[s] = y[s] * d[s];
+    const float xj = row_value(own, j);
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s) {
+      const int k = lane + 32 * s;
+      if (k < j) y[s] = fmaf(-M[(size_t)k * ld + j], xj, y[s]);
     }
-    if (!(best > T(0)) || !isfinite(best)) return true;
-    if (brow != p) {
-      for (int j = p + lane; j < n; j += 32) {
-        const T t = M[(size_t)p * ld + j];
-        M[(size_t)p * ld + j] = M[(size_t)brow * ld + j];
-        M[(size_t)brow * ld + j] = t;
+  }
+#pragma unroll
+  for (int s = 0; s < kWarpRows; ++s) y[s] *= d[s];
+}
+
+// Solve the n x n system stored with its right-hand side as the augmented matrix M = [A | b]
+// (column n holds b; row stride ld a multiple of 4 with ld / 4 odd and M 16-byte aligned, so
+// that lanes updating float4 chunks of consecutive rows hit distinct banks) by one warp:
+// Gaussian elimination with partial pivoting (pivot_key), b eliminated along, then back
+// substitution. Row k of the solution is returned in x[k / 32] of lane k % 32 (n <= 96).
+// Columns left of the pivot are not kept: the multipliers are not needed once b is eliminated.
+// Returns true if a pivot was zero or not finite.
+__device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x)[kWarpRows]) {
+  const int lane = threadIdx.x & 31;
+  const int c_end = n >> 2;  // last float4 chunk: the one holding column n
+  for (int p = 0; p < n; ++p) {
+    unsigned key = 0;
+    for (int i = p + lane; i < n; i += 32) {
+      const unsigned k = pivot_key(M[(size_t)i * ld + p], i);
+      key = k > key ? k : key;
+    }
+    key = __reduce_max_sync(0xffffffffu, key);
+    const int piv = 255 - (int)(key & 255u);
+    if (piv != p) {
+      float4 *rp = reinterpret_cast<float4 *>(M + (size_t)p * ld);
+      float4 *rq = reinterpret_cast<float4 *>(M + (size_t)piv * ld);
+      for (int c = (p >> 2) + lane; c <= c_end; c += 32) {
+        const float4 t = rp[c];
+        rp[c] = rq[c];
+        rq[c] = t;
       }
-      if (lane == 0) { const T t = b[p]; b[p] = b[brow]; b[brow] = t; }
+      __syncwarp();
     }
-    __syncwarp();
-    const T piv = M[(size_t)p * ld + p];
-    for (int i = p + 1 + lane; i < n; i += 32) M[(size_t)i * ld + p] = M[(size_t)i * ld + p] / piv;
-    __syncwarp();
-    const T bp = b[p];
-    // trailing update: lanes over rows, 4 columns per step (independent loads in flight)
+    const float pv = M[(size_t)p * ld + p];
+    if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
+    const float rinv = __frcp_rn(pv);
+    const float4 *mp = reinterpret_cast<const float4 *>(M + (size_t)p * ld);
+    const int c0 = (p + 1) >> 2;
     for (int i = p + 1 + lane; i < n; i += 32) {
-      T *Mi = M + (size_t)i * ld;
-      const T *Mp = M + (size_t)p * ld;
-      const T lip = Mi[p];
-      int j = p + 1;
-      for (; j + 4 <= n; j += 4) {
-        const T a0 = Mi[j], a1 = Mi[j + 1], a2 = Mi[j + 2], a3 = Mi[j + 3];
-        const T p0 = Mp[j], p1 = Mp[j + 1], p2 = Mp[j + 2], p3 = Mp[j + 3];
-        Mi[j] = a0 - lip * p0;
-        Mi[j + 1] = a1 - lip * p1;
-        Mi[j + 2] = a2 - lip * p2;
-        Mi[j + 3] = a3 - lip * p3;
+      float *row = M + (size_t)i * ld;
+      const float l = row[p] * rinv;
+      float4 *mi = reinterpret_cast<float4 *>(row);
+#pragma unroll 4
+      for (int c = c0; c <= c_end; ++c) {
+        float4 a = mi[c];
+        const float4 q = mp[c];
+        a.x = fmaf(-l, q.x, a.x);
+        a.y = fmaf(-l, q.y, a.y);
+        a.z = fmaf(-l, q.z, a.z);
+        a.w = fmaf(-l, q.w, a.w);
+        mi[c] = a;
       }
-      for (; j < n; ++j) Mi[j] -= lip * Mp[j];
-      b[i] -= lip * bp;
     }
     __syncwarp();
   }
-  for (int i = n - 1; i >= 0; --i) {
-    T s = T(0);
-    for (int j = i + 1 + lane; j < n; j += 32) s += M[(size_t)i * ld + j] * b[j];
-    s = warp_sum(s);
-    if (lane == 0) b[i] = (b[i] - s) / M[(size_t)i * ld + i];
+#pragma unroll
+  for (int s = 0; s < kWarpRows; ++s) {
+    const int k = lane + 32 * s;
+    x[s] = k < n ? M[(size_t)k * ld + n] : 0.f;
+  }
+  backsub_warp(M, ld, n, x);
+  return false;
+}
+
+// Warp LU factorisation with partial pivoting (pivot_key) and whole-row swaps, kept for several
+// right-hand sides: M (row stride ld, odd for conflict-free column reads) receives U on and above
+// the diagonal and the unit-lower multipliers below it; perm[i] = original row now at row i.
+// Returns true if a pivot was zero or not finite.
+__device__ __forceinline__ bool lu_factor_warp(float *M, int ld, int n, int *perm) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < n; i += 32) perm[i] = i;
+  __syncwarp();
+  for (int p = 0; p < n; ++p) {
+    unsigned key = 0;
+    for (int i = p + lane; i < n; i += 32) {
+      const unsigned k = pivot_key(M[(size_t)i * ld + p], i);
+      key = k > key ? k : key;
+    }
+    key = __reduce_max_sync(0xffffffffu, key);
+    const int piv = 255 - (int)(key & 255u);
+    if (piv != p) {
+      for (int j = lane; j < n; j += 32) {
+        const float t = M[(size_t)p * ld + j];
+        M[(size_t)p * ld + j] = M[(size_t)piv * ld + j];
+        M[(size_t)piv * ld + j] = t;
+      }
+      if (lane == 0) {
+        const int t = perm[p];
+        perm[p] = perm[piv];
+        perm[piv] = t;
+      }
+      __syncwarp();
+    }
+    const float pv = M[(size_t)p * ld + p];
+    if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
+    const float rinv = __frcp_rn(pv);
+    const float *mp = M + (size_t)p * ld;
+    for (int i = p + 1 + lane; i < n; i += 32) {
+      float *mi = M + (size_t)i * ld;
+      const float l = mi[p] * rinv;
+      mi[p] = l;
+      for (int j = p + 1; j < n; ++j) mi[j] = fmaf(-l, mp[j], mi[j]);
+    }
     __syncwarp();
   }
   return false;
+}
+
+// Solve with the factors of lu_factor_warp: x = U^-1 L^-1 (b permuted by perm). b is in shared
+// memory (length n); row k of the solution is returned in x[k / 32] of lane k % 32.
+__device__ __forceinline__ void lu_solve_warp(const float *M, int ld, int n, const int *perm,
+                                              const float *b, float (&x)[kWarpRows]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < kWarpRows; ++s) {
+    const int k = lane + 32 * s;
+    x[s] = k < n ? b[perm[k]] : 0.f;
+  }
+  for (int j = 0; j + 1 < n; ++j) {  // unit lower triangle
+    const float xj = row_value(x, j);
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s) {
+      const int k = lane + 32 * s;
+      if (k > j && k < n) x[s] = fmaf(-M[(size_t)k * ld + j], xj, x[s]);
+    }
+  }
+  backsub_warp(M, ld, n, x);
 }
 
 }  // namespace rb

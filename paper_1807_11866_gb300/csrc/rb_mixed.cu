@@ -42,6 +42,7 @@ struct MixedState {
   SlicedW WR, WP;               // residual [D~ | A], pressure [2 Cs | As]
   float2 *A2 = nullptr;         // [q_a][n_max][n_max] A_q as double-float (hi, lo)
   float2 *As2 = nullptr;        // [q_a][m][n_max] As_q as double-float
+  float2 *B2 = nullptr;         // [q_b][m][m] B_q as double-float
   // batch scratch
   int bcap = 0;
   __nv_bfloat16 *Xj = nullptr, *Xd = nullptr;  // Xj: [3][bcap][Kpad0] (hi, hi, lo)
@@ -50,6 +51,10 @@ struct MixedState {
   float *Jc = nullptr;          // [bcap][Npad]
   double *Rc = nullptr;         // [bcap][nb]
   double *Rp = nullptr;         // [bcap][m]
+  double *Th = nullptr;         // [bcap][n_theta] theta rows
+  double *Fm = nullptr;         // [bcap][nb] f(mu)
+  float2 *Amu = nullptr;        // [bcap][nb * nb] A(mu) as double-float
+  double *Asu = nullptr;        // [bcap][m] As(mu) u
   CUtensorMap tmXj, tmXd;
   float *lu_scratch = nullptr;
   int lu_grid = 0;
@@ -327,15 +332,107 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
   }
 }
 
+// ---- per-query data computed once, when a query starts (iteration count 0) --------------
+// theta row (FP64), f(mu) (FP64) and A(mu) = sum_q theta^a_q A_q (double-float, Sec. 2.4 affine
+// split) are fixed for the whole Newton solve of a query: every later kernel reads them instead
+// of evaluating the parameter functions and re-assembling the affine sums.
+struct PrepParams {
+  DevOps o;
+  const double *mu, *theta_in;  // theta_in: [nq][n_theta] caller rows, or null: from mu
+  int nq, nb, max_iter;
+  const rb_query_info *info;
+  const float2 *A2;             // [q_a][nb][nb] A_q as double-float
+  double *Th;                   // [nq][n_theta]
+  double *Fm;                   // [nq][nb]
+  float2 *Amu;                  // [nq][nb * nb]
+};
+
+__device__ __forceinline__ bool starts(const rb_query_info &q, int max_iter) {
+  return is_active(q, max_iter) && q.iters == 0;
+}
+
+// theta and f(mu) of the starting queries, one warp per query.
+__global__ void k_prep_theta(PrepParams p) {
+  const DevOps &o = p.o;
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < p.nq; b += nw) {
+    if (!starts(p.info[b], p.max_iter)) continue;
+    double *th = p.Th + (size_t)b * o.n_theta;
+    if (p.theta_in) {
+      for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta_in[(size_t)b * o.n_theta + i];
+    } else {
+      theta_eval_strided(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane, 32);
+    }
+    __syncwarp();
+    const double *tf = th + o.q_a + o.q_c;
+    for (int k = lane; k < p.nb; k += 32) {
+      double s = 0.0;
+      for (int q = 0; q < o.q_f; ++q) s = fma(tf[q], o.f[(size_t)q * o.n_max + k], s);
+      p.Fm[(size_t)b * p.nb + k] = s;
+    }
+    __syncwarp();
+  }
+}
+
+// A(mu) of the starting queries: a block holds kAsmQ queries' theta^a (double-float) and each
+// thread one element (k, j), so every A_q element read serves kAsmQ queries.
+constexpr int kAsmQ = 8;
+
+__global__ void __launch_bounds__(256) k_assemble_a(PrepParams p) {
+  extern __shared__ float2 ta_s[];  // [kAsmQ][q_a]
+  __shared__ int flag[kAsmQ];
+  const int qa = p.o.q_a;
+  const size_t nn = (size_t)p.nb * p.nb;
+  for (int g = blockIdx.y; g * kAsmQ < p.nq; g += gridDim.y) {
+    const int b0 = g * kAsmQ;
+    __syncthreads();
+    if (threadIdx.x < kAsmQ) {
+      const int b = b0 + threadIdx.x;
+      flag[threadIdx.x] = b < p.nq && starts(p.info[b], p.max_iter);
+    }
+    __syncthreads();
+    int any = 0;
+#pragma unroll
+    for (int r = 0; r < kAsmQ; ++r) any |= flag[r];
+    if (!any) continue;
+    for (int i = threadIdx.x; i < kAsmQ * qa; i += blockDim.x) {
+      const int r = i / qa, q = i - r * qa;
+      float h = 0.f, l = 0.f;
+      if (flag[r]) df_split(p.Th[(size_t)(b0 + r) * p.o.n_theta + q], h, l);
+      ta_s[i] = make_float2(h, l);
+    }
+    __syncthreads();
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn;
+         e += (size_t)gridDim.x * blockDim.x) {
+      float ah[kAsmQ], al[kAsmQ];
+#pragma unroll
+      for (int r = 0; r < kAsmQ; ++r) ah[r] = al[r] = 0.f;
+#pragma unroll 2
+      for (int q = 0; q < qa; ++q) {
+        const float2 a2 = __ldg(p.A2 + (size_t)q * nn + e);
+#pragma unroll
+        for (int r = 0; r < kAsmQ; ++r) {
+          const float2 t = ta_s[r * qa + q];
+          df_fma(ah[r], al[r], t.x, t.y, a2.x, a2.y);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kAsmQ; ++r)
+        if (flag[r]) p.Amu[(size_t)(b0 + r) * nn + e] = make_float2(ah[r], al[r]);
+    }
+  }
+}
+
 struct LuParams {
   DevOps o;
-  const double *mu, *theta;
   const int *nsz;
   int nq, nb, ldj, max_iter, j_in_smem;
   double tol_upd, tol_res;
-  const float2 *A2;      // [q_a][n_max][n_max] A_q as double-float (hi, lo)
+  const float2 *Amu;     // [nq][nb * nb] A(mu) as double-float (k_assemble_a)
+  const double *Fm;      // [nq][nb] f(mu)
   const float *Jc;       // [b_pad][ldj]
-  const double *Rc;      // [b_pad][nb]: A(mu) u + C_mu(u, u)
+  const double *Rc;      // [b_pad][nb]: C_mu(u, u)
   double *u;             // [nq][n_max], updated in place
   rb_query_info *info;   // [nq]
   float *scratch;        // [grid][nb * nb] when J is not in shared memory
@@ -350,22 +447,70 @@ struct LuParams {
 //   kResZero  u = 0: R = -f(mu) exactly and J = A(mu) (no contraction needed),
 //   kResLow   R = (A(mu) + J~^c / 2) u - f(mu) from the FP32/BF16 Jacobian (Euler identity);
 //             only used to approach the root, never to declare convergence,
-//   kResExact R = [A(mu) u + C_mu(u, u)]_sliced - f(mu), FP64-accurate.
+//   kResExact R = A(mu) u + [C_mu(u, u)]_sliced - f(mu), FP64-accurate.
 enum { kResZero = 0, kResLow = 1, kResExact = 2, kResLadder = -1 };
 
 __device__ __forceinline__ int rung_of(int rmode, int iters) {
   return rmode >= 0 ? rmode : (iters == 0 ? kResZero : (iters == 1 ? kResLow : kResExact));
 }
 
+// Rows k0 .. k0 + RR - 1 of the Newton system, by one warp (lanes over columns):
+// J[k][:] = fl32(A(mu)[k][:]) + J^c[k][:] and R[k] = A(mu)[k][:] u (double-float) + convection
+// part - f[k]. All RR rows' loads of a column block are issued before their arithmetic.
+template <int RR>
+__device__ __forceinline__ void newton_rows(const LuParams &p, int rm, int b, int n, int k0,
+                                            const float2 *u2, float *J, int ld, double *R) {
+  const int lane = threadIdx.x & 31;
+  const size_t nb = (size_t)p.nb;
+  const float2 *am = p.Amu + (size_t)b * nb * nb;
+  const float *jc = p.Jc + (size_t)b * p.ldj;
+  const bool with_u = rm != kResZero;
+  float rh[RR], rl[RR], clow[RR];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) rh[r] = rl[r] = clow[r] = 0.f;
+  for (int j = lane; j < n; j += 32) {
+    float2 a[RR];
+    float c[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const int k = k0 + r;
+      a[r] = k < n ? __ldg(am + k * nb + j) : make_float2(0.f, 0.f);
+      c[r] = (with_u && k < n) ? __ldg(jc + k * nb + j) : 0.f;
+    }
+    const float2 uj = with_u ? u2[j] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const int k = k0 + r;
+      if (k < n) {
+        const float v = (a[r].x + a[r].y) + c[r];
+        if (with_u) df_fma(rh[r], rl[r], a[r].x, a[r].y, uj.x, uj.y);
+        if (rm == kResLow) clow[r] = fmaf(0.5f * c[r], uj.x, clow[r]);
+        if (p.eval_only)
+          p.J_out[((size_t)b * n + k) * n + j] = (double)v;
+        else
+          J[(size_t)k * ld + j] = v;
+      }
+    }
+  }
+  const double *fb = p.Fm + (size_t)b * nb;
+#pragma unroll
+  for (int r = 0; r < RR; ++r) {
+    const int k = k0 + r;
+    const double rlin = with_u ? df_warp_sum(rh[r], rl[r]) : 0.0;
+    const float cl = rm == kResLow ? warp_sum(clow[r]) : 0.f;
+    if (lane == 0 && k < n) {
+      const double conv = rm == kResExact ? p.Rc[(size_t)b * nb + k] : (double)cl;
+      R[k] = rlin + conv - fb[k];
+    }
+  }
+}
+
 struct LuSmem {
-  int th, R, fm, red, tah, uh, rhs, J, total;  // offsets in bytes
-  __host__ __device__ LuSmem(const DevOps &o, int nb, bool j_in_smem) {
+  int R, red, uh, rhs, J, total;  // offsets in bytes
+  __host__ __device__ LuSmem(int nb, bool j_in_smem) {
     int p = 0;
-    th = p; p += 8 * ((o.n_theta + 1) & ~1);
     R = p; p += 8 * nb;
-    fm = p; p += 8 * nb;
     red = p; p += 8 * 4 * kWarps;
-    tah = p; p += 8 * o.q_a;           // theta^a as (hi, lo) floats
     uh = p; p += 8 * nb;               // u as (hi, lo) floats
     rhs = p; p += 4 * ((nb + 3) & ~3);
     p = (p + 15) & ~15;
@@ -375,104 +520,41 @@ struct LuSmem {
   }
 };
 
-// Rows k0 .. k0 + R - 1 of the Newton system, by one warp: J[k][:] = fl32(A(mu)[k][:]) + J^c[k][:]
-// and R[k] = A(mu)[k][:] u (double-float) + convection part - f[k]. R rows at once keep R
-// independent A loads in flight per lane.
-template <int RR>
-__device__ __forceinline__ void lu_rows(const LuParams &p, int rm, int b, int n, int k0,
-                                        const float2 *ta, const float2 *u2, const double *fm,
-                                        float *J, int ld, double *R) {
-  const int lane = threadIdx.x & 31;
-  const size_t nm = (size_t)p.o.n_max;
-  const float *jc = p.Jc + (size_t)b * p.ldj;
-  const bool with_jc = rm != kResZero;
-  float rh[RR], rl[RR], clow[RR];
-#pragma unroll
-  for (int r = 0; r < RR; ++r) rh[r] = rl[r] = clow[r] = 0.f;
-  for (int j = lane; j < n; j += 32) {
-    const float2 uj = u2[j];
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-      const int k = k0 + r;
-      if (k < n) {
-        float ah = 0.f, al = 0.f;
-        for (int q = 0; q < p.o.q_a; ++q) {
-          const float2 a2 = __ldg(p.A2 + ((size_t)q * nm + k) * nm + j);
-          df_fma(ah, al, ta[q].x, ta[q].y, a2.x, a2.y);
-        }
-        const float c = with_jc ? jc[(size_t)k * p.nb + j] : 0.f;
-        const float v = (ah + al) + c;
-        df_fma(rh[r], rl[r], ah, al, uj.x, uj.y);
-        if (rm == kResLow) clow[r] = fmaf(0.5f * c, uj.x, clow[r]);
-        if (p.eval_only)
-          p.J_out[((size_t)b * n + k) * n + j] = (double)v;
-        else
-          J[(size_t)k * ld + j] = v;
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < RR; ++r) {
-    const int k = k0 + r;
-    const double rlin = df_warp_sum(rh[r], rl[r]);
-    const float cl = rm == kResLow ? warp_sum(clow[r]) : 0.f;
-    if (lane == 0 && k < n) {
-      const double conv = rm == kResExact ? p.Rc[(size_t)b * p.nb + k] : (double)cl;
-      R[k] = rlin + conv - fm[k];
-    }
-  }
-}
-
+// One Newton iteration per active query, one block per query (large n).
 __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
-  const DevOps &o = p.o;
-  const LuSmem L(o, p.nb, p.j_in_smem != 0);
-  double *th = (double *)(smb + L.th), *R = (double *)(smb + L.R);
-  double *fm = (double *)(smb + L.fm), *red = (double *)(smb + L.red);
-  float2 *ta = (float2 *)(smb + L.tah), *u2 = (float2 *)(smb + L.uh);
+  const LuSmem L(p.nb, p.j_in_smem != 0);
+  double *R = (double *)(smb + L.R), *red = (double *)(smb + L.red);
+  float2 *u2 = (float2 *)(smb + L.uh);
   float *rhs = (float *)(smb + L.rhs);
   float *J = p.j_in_smem ? (float *)(smb + L.J) : p.scratch + (size_t)blockIdx.x * p.nb * p.nb;
   const int tid = threadIdx.x, w = tid >> 5;
-  const size_t nm = (size_t)o.n_max;
   int my_active = 0;
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
     rb_query_info qi = p.info[b];
     if (!is_active(qi, p.max_iter)) continue;
-    const int n = p.nsz ? p.nsz[b] : o.n_max;
-    if (p.theta) {
-      for (int i = tid; i < o.n_theta; i += blockDim.x) th[i] = p.theta[(size_t)b * o.n_theta + i];
-    } else {
-      theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
-    }
-    __syncthreads();
-    const double *tf = th + o.q_a + o.q_c;
-    double *ub = p.u + (size_t)b * nm;
-    for (int k = tid; k < n; k += blockDim.x) {
-      double s = 0.0;
-      for (int q = 0; q < o.q_f; ++q) s = fma(tf[q], o.f[(size_t)q * nm + k], s);
-      fm[k] = s;
-      float h, l;
-      df_split(ub[k], h, l);
-      u2[k] = make_float2(h, l);
-    }
-    for (int q = tid; q < o.q_a; q += blockDim.x) {
-      float h, l;
-      df_split(th[q], h, l);
-      ta[q] = make_float2(h, l);
-    }
-    __syncthreads();
+    const int n = p.nsz ? p.nsz[b] : p.nb;
+    double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
-    for (int k0 = 4 * w; k0 < n; k0 += 4 * kWarps) lu_rows<4>(p, rm, b, n, k0, ta, u2, fm, J, n, R);
+    if (rm != kResZero)
+      for (int k = tid; k < n; k += blockDim.x) {
+        float h, l;
+        df_split(ub[k], h, l);
+        u2[k] = make_float2(h, l);
+      }
+    __syncthreads();
+    for (int k0 = 4 * w; k0 < n; k0 += 4 * kWarps) newton_rows<4>(p, rm, b, n, k0, u2, J, n, R);
     __syncthreads();
     if (p.eval_only) {
       for (int k = tid; k < n; k += blockDim.x) p.R_out[(size_t)b * n + k] = R[k];
       __syncthreads();
       continue;
     }
+    const double *fb = p.Fm + (size_t)b * p.nb;
     double rl = 0.0, fl = 0.0;
     for (int i = tid; i < n; i += blockDim.x) {
       rl += R[i] * R[i];
-      fl += fm[i] * fm[i];
+      fl += fb[i] * fb[i];
       rhs[i] = (float)(-R[i]);
     }
     const double rn = sqrt(block_sum(rl, red));
@@ -505,75 +587,68 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
   if (tid == 0 && my_active) atomicAdd(p.active, my_active);
 }
 
+// Row stride of the augmented Newton matrix [J | -R] of the warp kernel: >= nb + 1, a multiple
+// of 4 with an odd number of float4 chunks (bank-conflict-free float4 rows, see gepp_aug_warp).
+__host__ __device__ inline int aug_ld(int nb) {
+  int ld = (nb + 1 + 3) & ~3;
+  if (((ld >> 2) & 1) == 0) ld += 4;
+  return ld;
+}
+
 // Warp-per-query variant of k_lu_mixed for small Jacobians (no block barriers): each warp
 // owns one query at a time and its own shared-memory slab.
 struct WarpLuSmem {
-  int th, R, fm, tah, uh, rhs, J, per_warp;  // byte offsets within a warp's slab
-  __host__ __device__ WarpLuSmem(const DevOps &o, int nb) {
+  int R, uh, J, ld, per_warp;  // byte offsets within a warp's slab; ld in floats
+  __host__ __device__ WarpLuSmem(int nb) {
     int p = 0;
-    th = p; p += 8 * ((o.n_theta + 1) & ~1);
     R = p; p += 8 * nb;
-    fm = p; p += 8 * nb;
-    tah = p; p += 8 * o.q_a;
     uh = p; p += 8 * nb;
-    rhs = p; p += 4 * ((nb + 3) & ~3);
     p = (p + 15) & ~15;
-    J = p; p += 4 * nb * (nb + 1);
+    ld = aug_ld(nb);
+    J = p; p += 4 * nb * ld;
     per_warp = (p + 15) & ~15;
   }
 };
 
-__global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
+__global__ void __launch_bounds__(kThreads, 2) k_lu_mixed_warp(LuParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
-  const DevOps &o = p.o;
-  const WarpLuSmem L(o, p.nb);
+  const WarpLuSmem L(p.nb);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   uint8_t *slab = smb + (size_t)w * L.per_warp;
-  double *th = (double *)(slab + L.th), *R = (double *)(slab + L.R), *fm = (double *)(slab + L.fm);
-  float2 *ta = (float2 *)(slab + L.tah), *u2 = (float2 *)(slab + L.uh);
-  float *rhs = (float *)(slab + L.rhs), *J = (float *)(slab + L.J);
-  const int ld = p.nb + 1;
-  const size_t nm = (size_t)o.n_max;
+  double *R = (double *)(slab + L.R);
+  float2 *u2 = (float2 *)(slab + L.uh);
+  float *J = (float *)(slab + L.J);
+  const int ld = L.ld;
   int my_active = 0;
   for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
     rb_query_info qi = p.info[b];
     if (!is_active(qi, p.max_iter)) continue;
-    const int n = p.nsz ? p.nsz[b] : o.n_max;
-    if (p.theta) {
-      for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta[(size_t)b * o.n_theta + i];
-    } else {
-      theta_eval_strided(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane, 32);
-    }
-    __syncwarp();
-    const double *tf = th + o.q_a + o.q_c;
-    double *ub = p.u + (size_t)b * nm;
-    for (int k = lane; k < n; k += 32) {
-      double sf = 0.0;
-      for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.f[(size_t)q * nm + k], sf);
-      fm[k] = sf;
-      float h, l;
-      df_split(ub[k], h, l);
-      u2[k] = make_float2(h, l);
-    }
-    for (int q = lane; q < o.q_a; q += 32) {
-      float h, l;
-      df_split(th[q], h, l);
-      ta[q] = make_float2(h, l);
-    }
-    __syncwarp();
+    const int n = p.nsz ? p.nsz[b] : p.nb;
+    double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
-    for (int k0 = 0; k0 < n; k0 += 8) lu_rows<8>(p, rm, b, n, k0, ta, u2, fm, J, ld, R);
+    if (rm != kResZero)
+      for (int k = lane; k < n; k += 32) {
+        float h, l;
+        df_split(ub[k], h, l);
+        u2[k] = make_float2(h, l);
+      }
+    __syncwarp();
+    for (int k0 = 0; k0 < n; k0 += 4) newton_rows<4>(p, rm, b, n, k0, u2, J, ld, R);
     __syncwarp();
     if (p.eval_only) {
       for (int k = lane; k < n; k += 32) p.R_out[(size_t)b * n + k] = R[k];
       __syncwarp();
       continue;
     }
+    const double *fb = p.Fm + (size_t)b * p.nb;
+    const int c_pad = ((n >> 2) << 2) + 4;  // columns n + 1 .. c_pad - 1 pad the last chunk
     double rl = 0.0, fl = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      rl += R[i] * R[i];
-      fl += fm[i] * fm[i];
-      rhs[i] = (float)(-R[i]);
+    for (int k = lane; k < n; k += 32) {
+      rl += R[k] * R[k];
+      fl += fb[k] * fb[k];
+      float *row = J + (size_t)k * ld;
+      row[n] = (float)(-R[k]);
+      for (int c = n + 1; c < c_pad; ++c) row[c] = 0.f;
     }
     const double rn = sqrt(warp_sum(rl));
     const double fscale = fmax(1.0, sqrt(warp_sum(fl)));
@@ -581,16 +656,21 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
     qi.iters += 1;
     qi.res_norm = rn;
     qi.precision_used = RB_PREC_MIXED;
+    float x[kWarpRows];
     if (!isfinite(rn)) {
       qi.status = RB_Q_NONFINITE;
-    } else if (gepp_solve_warp<float>(J, ld, n, rhs)) {
+    } else if (gepp_aug_warp(J, ld, n, x)) {
       qi.status = RB_Q_SINGULAR;
     } else {
       double dl = 0.0;
-      for (int i = lane; i < n; i += 32) {
-        const double d = (double)rhs[i];
-        dl += d * d;
-        ub[i] += d;
+#pragma unroll
+      for (int s = 0; s < kWarpRows; ++s) {
+        const int k = lane + 32 * s;
+        if (k < n) {
+          const double d = (double)x[s];
+          dl += d * d;
+          ub[k] += d;
+        }
       }
       const double dn = sqrt(warp_sum(dl));
       qi.upd_norm = dn;
@@ -606,119 +686,253 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
   if (lane == 0 && my_active) atomicAdd(p.active, my_active);
 }
 
-// Pressure: r = fs(mu) - (As(mu) u + Cs_mu(u, u)), B(mu) p = r in FP64 (Eq. blocksolve-2).
-struct PresSolveParams {
+// ---- pressure (Eq. sup-vvar, Eq. blocksolve-2) ----------------------------------------------
+// As(mu) u for the converged queries, double-float on the CUDA cores:
+//   out[b][k] = sum_q theta^a_q(b) sum_j As_q[k][j] u_b[j].
+// A block holds kAsQ queries' u and kAsR rows of one As_q at a time in shared memory; thread
+// (b, k) accumulates the dot product of its pair for each q.
+constexpr int kAsQ = 16, kAsR = 16;
+
+struct AsuParams {
   DevOps o;
-  const double *mu, *theta;
+  const double *theta;  // [nq][n_theta]
   const int *nsz;
   int nq;
-  const double *u;    // [nq][n_max]
-  const float2 *As2;  // [q_a][m][n_max] double-float
-  const double *Rp;   // [b_pad][m]: Cs_mu(u, u) (sliced GEMM)
-  double *p_out;     // [nq][m]
-  rb_query_info *info;
+  const double *u;      // [nq][n_max]
+  const rb_query_info *info;
+  const float2 *As2;    // [q_a][m][n_max] double-float
+  double *out;          // [b_pad][m]
 };
 
-// (As(mu) u)[k] for rows k0 .. k0 + RR - 1 by one warp in double-float:
-// sum_j sum_q theta^a_q As_q[k][j] u_j, with theta^a (ta) and u (u2) pre-split.
-template <int RR>
-__device__ __forceinline__ void as_u_rows(const PresSolveParams &p, int n, int k0, int m,
-                                          const float2 *ta, const float2 *u2, double *out) {
-  const int lane = threadIdx.x & 31;
-  const size_t nm = (size_t)p.o.n_max;
-  float rh[RR], rl[RR];
+__host__ __device__ inline int odd_ld(int n) { return n | 1; }
+
+__global__ void __launch_bounds__(256) k_as_u(AsuParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  __shared__ float2 ts[kAsQ * RB_Q_MAX];
+  __shared__ int flag[kAsQ];
+  const DevOps &o = p.o;
+  const int nm = o.n_max, ldr = odd_ld(nm), m = o.m, qa = o.q_a;
+  float2 *us = (float2 *)smb;        // [kAsQ][ldr]
+  float2 *as = us + kAsQ * ldr;      // [kAsR][ldr]
+  const int tid = threadIdx.x, bi = tid >> 4, ki = tid & 15;
+  const int k = blockIdx.x * kAsR + ki;
+  for (int g = blockIdx.y; g * kAsQ < p.nq; g += gridDim.y) {
+    const int b0 = g * kAsQ;
+    __syncthreads();
+    if (tid < kAsQ) flag[tid] = b0 + tid < p.nq && p.info[b0 + tid].status == RB_Q_OK;
+    __syncthreads();
+    int any = 0;
 #pragma unroll
-  for (int r = 0; r < RR; ++r) rh[r] = rl[r] = 0.f;
-  for (int j = lane; j < n; j += 32) {
-    const float2 uj = u2[j];
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-      const int k = k0 + r;
-      if (k < m) {
-        float ah = 0.f, al = 0.f;
-        for (int q = 0; q < p.o.q_a; ++q) {
-          const float2 a2 = __ldg(p.As2 + ((size_t)q * p.o.m + k) * nm + j);
-          df_fma(ah, al, ta[q].x, ta[q].y, a2.x, a2.y);
-        }
-        df_fma(rh[r], rl[r], ah, al, uj.x, uj.y);
-      }
+    for (int r = 0; r < kAsQ; ++r) any |= flag[r];
+    if (!any) continue;
+    for (int i = tid; i < kAsQ * nm; i += blockDim.x) {
+      const int r = i / nm, j = i - r * nm, b = b0 + r;
+      float h = 0.f, l = 0.f;
+      if (flag[r] && j < (p.nsz ? p.nsz[b] : nm)) df_split(p.u[(size_t)b * nm + j], h, l);
+      us[r * ldr + j] = make_float2(h, l);
     }
-  }
-#pragma unroll
-  for (int r = 0; r < RR; ++r) {
-    const double v = df_warp_sum(rh[r], rl[r]);
-    if (lane == 0 && k0 + r < m) out[k0 + r] = v;
+    for (int i = tid; i < kAsQ * qa; i += blockDim.x) {
+      const int r = i / qa, q = i - r * qa;
+      float h = 0.f, l = 0.f;
+      if (flag[r]) df_split(p.theta[(size_t)(b0 + r) * o.n_theta + q], h, l);
+      ts[i] = make_float2(h, l);
+    }
+    float ah = 0.f, al = 0.f;
+    for (int q = 0; q < qa; ++q) {
+      __syncthreads();
+      for (int i = tid; i < kAsR * nm; i += blockDim.x) {
+        const int r = i / nm, j = i - r * nm, kk = blockIdx.x * kAsR + r;
+        as[r * ldr + j] = kk < m ? __ldg(p.As2 + ((size_t)q * m + kk) * nm + j) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      float dh = 0.f, dl = 0.f;
+      const float2 *ur = us + bi * ldr, *ar = as + ki * ldr;
+#pragma unroll 4
+      for (int j = 0; j < nm; ++j) {
+        const float2 uu = ur[j], aa = ar[j];
+        df_fma(dh, dl, uu.x, uu.y, aa.x, aa.y);
+      }
+      const float2 t = ts[bi * qa + q];
+      df_fma(ah, al, t.x, t.y, dh, dl);
+    }
+    if (flag[bi] && k < m) p.out[(size_t)(b0 + bi) * m + k] = (double)ah + (double)al;
   }
 }
 
-// shared-memory slab of one pressure solve (bytes)
+// Pressure solve per converged query: r = fs(mu) - As(mu) u - Cs_mu(u, u) in FP64, B(mu) in
+// double-float, B(mu) p = r by FP32 LU plus two steps of iterative refinement with the residual
+// r - B(mu) p in double-float (B(mu) is well conditioned, so each step gains the FP32 digits).
+struct PresSolveParams {
+  DevOps o;
+  const double *theta;  // [nq][n_theta]
+  int nq;
+  const float2 *B2;     // [q_b][m][m] double-float
+  const double *Rp;     // [b_pad][m]: Cs_mu(u, u) (sliced GEMM)
+  const double *Asu;    // [b_pad][m]: As(mu) u (k_as_u)
+  double *p_out;        // [nq][m]
+  rb_query_info *info;
+};
+
+constexpr int kPresRefine = 2;
+
+// shared-memory slab of one warp's pressure solve (bytes)
 struct PresSmem {
-  int th, r, asu, ta, u2, red, Bm, total;
-  __host__ __device__ PresSmem(const DevOps &o, bool with_red) {
+  int th, r, pv, pf, tb, Bd, Bf, rf, perm, total, ldd, ldb;
+  __host__ __device__ PresSmem(const DevOps &o) {
+    const int m = o.m;
+    ldd = odd_ld(m);
+    ldb = odd_ld(m);
     int p = 0;
     th = p; p += 8 * ((o.n_theta + 1) & ~1);
-    r = p; p += 8 * o.m;
-    asu = p; p += 8 * o.m;
-    ta = p; p += 8 * o.q_a;
-    u2 = p; p += 8 * o.n_max;
-    red = p; p += with_red ? 8 * 4 * kWarps : 0;
-    Bm = p; p += 8 * o.m * (o.m + 1);
+    r = p; p += 8 * m;
+    pv = p; p += 8 * m;
+    pf = p; p += 8 * m;
+    tb = p; p += 8 * o.q_b;
+    Bd = p; p += 8 * m * ldd;
+    Bf = p; p += 4 * m * ldb;
+    rf = p; p += 4 * m;
+    perm = p; p += 4 * m;
     total = (p + 15) & ~15;
   }
 };
 
-__device__ __forceinline__ void pressure_rhs_prep(const PresSolveParams &p, int b, int n,
-                                                  const double *th, float2 *ta, float2 *u2,
-                                                  int t0, int stride) {
-  const double *ub = p.u + (size_t)b * p.o.n_max;
-  for (int j = t0; j < n; j += stride) {
-    float h, l;
-    df_split(ub[j], h, l);
-    u2[j] = make_float2(h, l);
-  }
-  for (int q = t0; q < p.o.q_a; q += stride) {
-    float h, l;
-    df_split(th[q], h, l);
-    ta[q] = make_float2(h, l);
+__global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  const DevOps &o = p.o;
+  const int m = o.m, mm = m * m;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const PresSmem L(o);
+  uint8_t *slab = smb + (size_t)w * L.total;
+  double *th = (double *)(slab + L.th), *r = (double *)(slab + L.r), *pv = (double *)(slab + L.pv);
+  float2 *pf = (float2 *)(slab + L.pf), *tb = (float2 *)(slab + L.tb), *Bd = (float2 *)(slab + L.Bd);
+  float *Bf = (float *)(slab + L.Bf), *rf = (float *)(slab + L.rf);
+  int *perm = (int *)(slab + L.perm);
+  const int ldd = L.ldd, ldb = L.ldb;
+  for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
+    double *prow = p.p_out + (size_t)b * m;
+    if (p.info[b].status != RB_Q_OK) {
+      for (int i = lane; i < m; i += 32) prow[i] = 0.0;
+      continue;
+    }
+    for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta[(size_t)b * o.n_theta + i];
+    __syncwarp();
+    const double *tf = th + o.q_a + o.q_c, *tbd = tf + o.q_f;
+    for (int q = lane; q < o.q_b; q += 32) {
+      float h, l;
+      df_split(tbd[q], h, l);
+      tb[q] = make_float2(h, l);
+    }
+    for (int k = lane; k < m; k += 32) {
+      double sf = 0.0;
+      for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
+      r[k] = sf - p.Rp[(size_t)b * m + k] - p.Asu[(size_t)b * m + k];
+      rf[k] = (float)r[k];
+    }
+    __syncwarp();
+    // B(mu) = sum_q theta^b_q B_q in double-float; its FP32 rounding for the factorisation
+    for (int e0 = lane; e0 < mm; e0 += 128) {
+      float bh[4], bl[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) bh[t] = bl[t] = 0.f;
+      for (int q = 0; q < o.q_b; ++q) {
+        float2 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int e = e0 + 32 * t;
+          v[t] = e < mm ? __ldg(p.B2 + (size_t)q * mm + e) : make_float2(0.f, 0.f);
+        }
+        const float2 c = tb[q];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) df_fma(bh[t], bl[t], c.x, c.y, v[t].x, v[t].y);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = e0 + 32 * t;
+        if (e < mm) {
+          const int k = e / m, j = e - k * m;
+          Bd[k * ldd + j] = make_float2(bh[t], bl[t]);
+          Bf[k * ldb + j] = bh[t] + bl[t];
+        }
+      }
+    }
+    __syncwarp();
+    if (lu_factor_warp(Bf, ldb, m, perm)) {
+      for (int i = lane; i < m; i += 32) prow[i] = 0.0;
+      if (lane == 0) p.info[b].status = RB_Q_SINGULAR;
+      __syncwarp();
+      continue;
+    }
+    float x[kWarpRows];
+    lu_solve_warp(Bf, ldb, m, perm, rf, x);
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s)
+      if (lane + 32 * s < m) pv[lane + 32 * s] = (double)x[s];
+    __syncwarp();
+    for (int it = 0; it < kPresRefine; ++it) {
+      // residual r - B(mu) p, rows owned by lanes, p as double-float pairs
+      for (int j = lane; j < m; j += 32) {
+        float ph, pl;
+        df_split(pv[j], ph, pl);
+        pf[j] = make_float2(ph, pl);
+      }
+      __syncwarp();
+      for (int k = lane; k < m; k += 32) {
+        float h = 0.f, l = 0.f;
+        const float2 *bk = Bd + k * ldd;
+        for (int j = 0; j < m; ++j) df_fma(h, l, bk[j].x, bk[j].y, pf[j].x, pf[j].y);
+        rf[k] = (float)(r[k] - ((double)h + (double)l));
+      }
+      __syncwarp();
+      lu_solve_warp(Bf, ldb, m, perm, rf, x);
+#pragma unroll
+      for (int s = 0; s < kWarpRows; ++s)
+        if (lane + 32 * s < m) pv[lane + 32 * s] += (double)x[s];
+      __syncwarp();
+    }
+    for (int i = lane; i < m; i += 32) prow[i] = pv[i];
+    __syncwarp();
   }
 }
+
+// Block variant for large m: B(mu) in FP64 and block-cooperative FP64 elimination.
+struct PresBlockSmem {
+  int th, r, red, Bm, total;
+  __host__ __device__ PresBlockSmem(const DevOps &o) {
+    int p = 0;
+    th = p; p += 8 * ((o.n_theta + 1) & ~1);
+    r = p; p += 8 * o.m;
+    red = p; p += 8 * 4 * kWarps;
+    Bm = p; p += 8 * o.m * o.m;
+    total = (p + 15) & ~15;
+  }
+};
 
 __global__ void __launch_bounds__(kThreads) k_pressure_solve(PresSolveParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
   const DevOps &o = p.o;
   const int m = o.m;
-  const PresSmem L(o, true);
-  double *th = (double *)(smb + L.th), *r = (double *)(smb + L.r), *asu = (double *)(smb + L.asu);
-  float2 *ta = (float2 *)(smb + L.ta), *u2 = (float2 *)(smb + L.u2);
+  const PresBlockSmem L(o);
+  double *th = (double *)(smb + L.th), *r = (double *)(smb + L.r);
   double *red = (double *)(smb + L.red), *Bm = (double *)(smb + L.Bm);
-  const int tid = threadIdx.x, w = tid >> 5;
+  const int tid = threadIdx.x;
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
     double *prow = p.p_out + (size_t)b * m;
     if (p.info[b].status != RB_Q_OK) {
       for (int i = tid; i < m; i += blockDim.x) prow[i] = 0.0;
       continue;
     }
-    if (p.theta) {
-      for (int i = tid; i < o.n_theta; i += blockDim.x) th[i] = p.theta[(size_t)b * o.n_theta + i];
-    } else {
-      theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
-    }
+    for (int i = tid; i < o.n_theta; i += blockDim.x) th[i] = p.theta[(size_t)b * o.n_theta + i];
     __syncthreads();
-    const int n = p.nsz ? p.nsz[b] : o.n_max;
-    pressure_rhs_prep(p, b, n, th, ta, u2, tid, blockDim.x);
-    __syncthreads();
-    for (int k0 = 4 * w; k0 < m; k0 += 4 * kWarps) as_u_rows<4>(p, n, k0, m, ta, u2, asu);
     const double *tf = th + o.q_a + o.q_c, *tb = tf + o.q_f;
     for (int e = tid; e < m * m; e += blockDim.x) {
       double s = 0.0;
       for (int q = 0; q < o.q_b; ++q) s = fma(tb[q], __ldg(o.B + (size_t)q * m * m + e), s);
       Bm[e] = s;
     }
-    __syncthreads();
     for (int k = tid; k < m; k += blockDim.x) {
       double sf = 0.0;
       for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
-      r[k] = sf - p.Rp[(size_t)b * m + k] - asu[k];
+      r[k] = sf - p.Rp[(size_t)b * m + k] - p.Asu[(size_t)b * m + k];
     }
     __syncthreads();
     const bool sing = gepp_solve_block<double>(Bm, m, m, r, red);
@@ -728,63 +942,16 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve(PresSolveParams p) 
   }
 }
 
-// Warp-per-query variant of k_pressure_solve for small m.
-__global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParams p) {
-  extern __shared__ __align__(16) uint8_t smb[];
-  const DevOps &o = p.o;
-  const int m = o.m;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  const PresSmem L(o, false);
-  uint8_t *slab = smb + (size_t)w * L.total;
-  double *th = (double *)(slab + L.th), *r = (double *)(slab + L.r), *asu = (double *)(slab + L.asu);
-  float2 *ta = (float2 *)(slab + L.ta), *u2 = (float2 *)(slab + L.u2);
-  double *Bm = (double *)(slab + L.Bm);
-  const int ld = m + 1;
-  for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
-    double *prow = p.p_out + (size_t)b * m;
-    if (p.info[b].status != RB_Q_OK) {
-      for (int i = lane; i < m; i += 32) prow[i] = 0.0;
-      continue;
-    }
-    if (p.theta) {
-      for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta[(size_t)b * o.n_theta + i];
-    } else {
-      theta_eval_strided(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane, 32);
-    }
-    __syncwarp();
-    const int n = p.nsz ? p.nsz[b] : o.n_max;
-    pressure_rhs_prep(p, b, n, th, ta, u2, lane, 32);
-    __syncwarp();
-    for (int k0 = 0; k0 < m; k0 += 8) as_u_rows<8>(p, n, k0, m, ta, u2, asu);
-    const double *tf = th + o.q_a + o.q_c, *tb = tf + o.q_f;
-    for (int k = 0; k < m; ++k)
-      for (int i = lane; i < m; i += 32) {
-        double sb = 0.0;
-        for (int q = 0; q < o.q_b; ++q) sb = fma(tb[q], __ldg(o.B + ((size_t)q * m + k) * m + i), sb);
-        Bm[k * ld + i] = sb;
-      }
-    __syncwarp();
-    for (int k = lane; k < m; k += 32) {
-      double sf = 0.0;
-      for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
-      r[k] = sf - p.Rp[(size_t)b * m + k] - asu[k];
-    }
-    __syncwarp();
-    const bool sing = gepp_solve_warp<double>(Bm, ld, m, r);
-    for (int i = lane; i < m; i += 32) prow[i] = sing ? 0.0 : r[i];
-    if (sing && lane == 0) p.info[b].status = RB_Q_SINGULAR;
-    __syncwarp();
-  }
-}
-
 // ---------------------------------------------------------------------------------------
 // host side
 void mixed_release(rb_ctx *ctx) {
   MixedState *M = ctx->mixed;
   if (!M) return;
-  for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2, (void *)M->Xj,
-                  (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc, (void *)M->Rc,
-                  (void *)M->Rp, (void *)M->lu_scratch, (void *)M->dev_words, (void *)M->info_own})
+  for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2,
+                  (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
+                  (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
+                  (void *)M->Amu, (void *)M->Asu, (void *)M->lu_scratch, (void *)M->dev_words,
+                  (void *)M->info_own})
     ctx_free(ctx, q);
   if (M->h_words) cudaFreeHost(M->h_words);
   delete M;
@@ -876,6 +1043,9 @@ static int mixed_layouts(rb_ctx *ctx, cudaStream_t st) {
     if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_a * o.m * nm, "As (double-float)")) != RB_OK) return rc;
     M->As2 = (float2 *)p;
     k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.As, M->As2, (size_t)o.q_a * o.m * nm);
+    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_b * o.m * o.m, "B (double-float)")) != RB_OK) return rc;
+    M->B2 = (float2 *)p;
+    k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.B, M->B2, (size_t)o.q_b * o.m * o.m);
   }
   if ((rc = ctx_alloc(ctx, &p, 2 * 2 * (size_t)M->Npad * M->Kpad0, "W (split BF16)")) != RB_OK) return rc;
   M->Wj = (__nv_bfloat16 *)p;
@@ -891,10 +1061,12 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
   const int b_pad = round_up(std::max(nq, 1), 128);
   if (b_pad <= M->bcap) return RB_OK;
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
-                  (void *)M->Rc, (void *)M->Rp})
+                  (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
+                  (void *)M->Asu})
     ctx_free(ctx, q);
   M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->ufT = nullptr; M->Jc = nullptr;
-  M->Rc = M->Rp = nullptr;
+  M->Rc = M->Rp = M->Th = M->Fm = M->Asu = nullptr;
+  M->Amu = nullptr;
   M->bcap = 0;
   int rc;
   void *p;
@@ -914,6 +1086,14 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
   M->Rc = (double *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * m, "pressure rhs (FP64)")) != RB_OK) return rc;
   M->Rp = (double *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * ctx->ops.n_theta, "theta rows")) != RB_OK) return rc;
+  M->Th = (double *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "f(mu)")) != RB_OK) return rc;
+  M->Fm = (double *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb * M->nb, "A(mu) (double-float)")) != RB_OK) return rc;
+  M->Amu = (float2 *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * m, "As(mu) u")) != RB_OK) return rc;
+  M->Asu = (double *)p;
   // zero once so that padded rows never hold NaN bit patterns
   cudaMemsetAsync(M->Xj, 0, 2 * 3 * xs0, ctx->stream);
   cudaMemsetAsync(M->Xd, 0, 2 * xs * M->Smax, ctx->stream);
@@ -976,12 +1156,40 @@ static TcGemmParams gemm_params(rb_ctx *ctx, int nq) {
   return g;
 }
 
-// One Newton step's contraction work for the whole batch: X build + both GEMMs.
-static int mixed_contract(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
-                          const int *d_n, const double *d_u, const rb_query_info *d_info,
-                          bool exact, cudaStream_t st) {
+// theta rows, f(mu) and A(mu) of the queries that start (active, iteration count 0).
+static int launch_prep(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
+                       const rb_query_info *info, cudaStream_t st) {
   MixedState *M = ctx->mixed;
-  int rc = launch_build_x(ctx, d_mu, d_theta, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st);
+  const DevOps &o = ctx->ops;
+  PrepParams pp{};
+  pp.o = o;
+  pp.mu = d_mu;
+  pp.theta_in = d_theta;
+  pp.nq = nq;
+  pp.nb = M->nb;
+  pp.max_iter = ctx->cfg.max_iter;
+  pp.info = info;
+  pp.A2 = M->A2;
+  pp.Th = M->Th;
+  pp.Fm = M->Fm;
+  pp.Amu = M->Amu;
+  const int mk = prof_begin(ctx, RB_K_INIT, st);
+  k_prep_theta<<<std::max(1, std::min((nq + 7) / 8, ctx->sms * 16)), 256, 0, st>>>(pp);
+  const size_t nn = (size_t)M->nb * M->nb;
+  dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024),
+            (unsigned)std::min((nq + kAsmQ - 1) / kAsmQ, 65535));
+  k_assemble_a<<<grid, 256, sizeof(float2) * kAsmQ * o.q_a, st>>>(pp);
+  prof_end(ctx, mk, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_assemble_a");
+  return RB_OK;
+}
+
+// One Newton step's contraction work for the whole batch: X build + both GEMMs.
+static int mixed_contract(rb_ctx *ctx, int nq, const int *d_n, const double *d_u,
+                          const rb_query_info *d_info, bool exact, cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  int rc = launch_build_x(ctx, nullptr, M->Th, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st);
   if (rc != RB_OK) return rc;
   TcGemmParams g = gemm_params(ctx, nq);
   g.n_tiles = M->Npad / kTcBN;
@@ -1014,8 +1222,10 @@ constexpr int kWarpLuMaxN = 80;  // warp-per-query elimination up to this size
 
 static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
   MixedState *M = ctx->mixed;
+  lp.Amu = M->Amu;
+  lp.Fm = M->Fm;
   if (M->nb <= kWarpLuMaxN) {
-    const int per_warp = WarpLuSmem(ctx->ops, M->nb).per_warp;
+    const int per_warp = WarpLuSmem(M->nb).per_warp;
     const int wpc = std::max(1, std::min(8, (200 * 1024) / per_warp));
     const size_t smem = (size_t)wpc * per_warp;
     const int per_sm = std::max(1, std::min(64 / wpc, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
@@ -1029,9 +1239,9 @@ static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp");
     return RB_OK;
   }
-  const size_t smem_in = LuSmem(ctx->ops, M->nb, true).total;
+  const size_t smem_in = LuSmem(M->nb, true).total;
   lp.j_in_smem = smem_in <= (size_t)ctx->max_smem ? 1 : 0;
-  const size_t smem = LuSmem(ctx->ops, M->nb, lp.j_in_smem != 0).total;
+  const size_t smem = LuSmem(M->nb, lp.j_in_smem != 0).total;
   const int per_sm = std::max(1, std::min(2048 / kThreads, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
   const int grid = std::max(1, std::min(nq, per_sm * ctx->sms));
   if (!lp.j_in_smem) {
@@ -1082,12 +1292,11 @@ static int check_words(rb_ctx *ctx, cudaStream_t st, const char *what) {
   return RB_OK;
 }
 
-static int mixed_pressure(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
-                          const int *d_n, const double *d_u, double *d_p, rb_query_info *info,
-                          cudaStream_t st) {
+static int mixed_pressure(rb_ctx *ctx, int nq, const int *d_n, const double *d_u, double *d_p,
+                          rb_query_info *info, cudaStream_t st) {
   MixedState *M = ctx->mixed;
   const DevOps &o = ctx->ops;
-  int rc = launch_build_x(ctx, d_mu, d_theta, nq, d_n, d_u, info, 1, 1, M->Rp, o.m, st);
+  int rc = launch_build_x(ctx, nullptr, M->Th, nq, d_n, d_u, info, 1, 1, M->Rp, o.m, st);
   if (rc != RB_OK) return rc;
   TcGemmParams g = gemm_params(ctx, nq);
   g.kb[0] = M->kb0;
@@ -1102,24 +1311,28 @@ static int mixed_pressure(rb_ctx *ctx, const double *d_mu, const double *d_theta
   cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WP.tm, g, ctx->sms, st);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (pressure)");
-  PresSolveParams pp{o, d_mu, d_theta, d_n, nq, d_u, M->As2, M->Rp, d_p, info};
-  const size_t per_warp = PresSmem(o, false).total;
-  if (per_warp <= 24 * 1024) {
+  mk = prof_begin(ctx, RB_K_PRESSURE, st);
+  AsuParams ap{o, M->Th, d_n, nq, d_u, info, M->As2, M->Asu};
+  const size_t asmem = sizeof(float2) * (size_t)(kAsQ + kAsR) * odd_ld(o.n_max);
+  e = cudaFuncSetAttribute(k_as_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_as_u attr");
+  dim3 agrid((unsigned)((o.m + kAsR - 1) / kAsR), (unsigned)std::min((nq + kAsQ - 1) / kAsQ, 65535));
+  k_as_u<<<agrid, 256, asmem, st>>>(ap);
+  PresSolveParams pp{o, M->Th, nq, M->B2, M->Rp, M->Asu, d_p, info};
+  const size_t per_warp = PresSmem(o).total;
+  if (o.m <= 32 * kWarpRows && per_warp <= 24 * 1024) {
     const int wpc = std::max(1, std::min(8, (int)((192 * 1024) / per_warp)));
     const size_t smem = wpc * per_warp;
     e = cudaFuncSetAttribute(k_pressure_solve_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure_solve_warp attr");
-    mk = prof_begin(ctx, RB_K_PRESSURE, st);
-    k_pressure_solve_warp<<<std::min((nq + wpc - 1) / wpc, ctx->sms * 8), 32 * wpc, smem, st>>>(pp);
-    prof_end(ctx, mk, st);
+    k_pressure_solve_warp<<<std::max(1, std::min((nq + wpc - 1) / wpc, ctx->sms * 8)), 32 * wpc, smem, st>>>(pp);
   } else {
-    const size_t smem = PresSmem(o, true).total;
+    const size_t smem = PresBlockSmem(o).total;
     e = cudaFuncSetAttribute(k_pressure_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure_solve attr");
-    mk = prof_begin(ctx, RB_K_PRESSURE, st);
-    k_pressure_solve<<<std::min(nq, ctx->sms * 8), kThreads, smem, st>>>(pp);
-    prof_end(ctx, mk, st);
+    k_pressure_solve<<<std::max(1, std::min(nq, ctx->sms * 8)), kThreads, smem, st>>>(pp);
   }
+  prof_end(ctx, mk, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure_solve");
   return RB_OK;
@@ -1137,11 +1350,10 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   int mk = prof_begin(ctx, RB_K_INIT, st);
   k_mixed_init<<<std::min(nq, ctx->sms * 8), 128, 0, st>>>(nq, o.n_max, d_n, d_u, info);
   prof_end(ctx, mk, st);
+  if ((rc = launch_prep(ctx, d_mu, d_theta, nq, info, st)) != RB_OK) return rc;
   cudaMemsetAsync(M->dev_words, 0, 8, st);
   LuParams lp{};
   lp.o = o;
-  lp.mu = d_mu;
-  lp.theta = d_theta;
   lp.nsz = d_n;
   lp.nq = nq;
   lp.nb = M->nb;
@@ -1149,7 +1361,6 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   lp.max_iter = ctx->cfg.max_iter;
   lp.tol_upd = ctx->cfg.tol_update;
   lp.tol_res = ctx->cfg.tol_res;
-  lp.A2 = M->A2;
   lp.Jc = M->Jc;
   lp.Rc = M->Rc;
   lp.u = d_u;
@@ -1158,14 +1369,14 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
   for (int it = 0; it < ctx->cfg.max_iter; ++it) {
     cudaMemsetAsync(M->dev_words, 0, 4, st);
-    if (it >= 1 && (rc = mixed_contract(ctx, d_mu, d_theta, nq, d_n, d_u, info, it >= 2, st)) != RB_OK)
+    if (it >= 1 && (rc = mixed_contract(ctx, nq, d_n, d_u, info, it >= 2, st)) != RB_OK)
       return rc;
     if ((rc = launch_lu(ctx, lp, nq, st)) != RB_OK) return rc;
     if ((rc = check_words(ctx, st, "mixed Newton step")) != RB_OK) return rc;
     if (M->h_words[0] == 0) break;
   }
   if (d_p && o.m > 0 && o.B) {
-    if ((rc = mixed_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st)) != RB_OK) return rc;
+    if ((rc = mixed_pressure(ctx, nq, d_n, d_u, d_p, info, st)) != RB_OK) return rc;
     if ((rc = check_words(ctx, st, "pressure recovery")) != RB_OK) return rc;
   }
   if (ctx->prof) prof_collect(ctx);
@@ -1187,7 +1398,7 @@ size_t mixed_slot_bytes(const rb_ctx *ctx) {
   const size_t Npad = (size_t)round_up(o.n_max * o.n_max, kTcBN);
   const int S = 8;
   return 2 * 3 * Kpad0 + 2 * S * Kpad0 + 8 + 8 * nb + 4 * Npad + 8 * nb + 8 * (size_t)(o.m + 1) +
-         8 * nb + 64;
+         8 * nb + 64 + 8 * (size_t)o.n_theta + 8 * nb + 8 * nb * nb + 8 * (size_t)(o.m + 1);
 }
 
 // One Newton iteration for every live slot: the contraction work the slots' ladder rungs need,
@@ -1197,12 +1408,11 @@ int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, dou
   MixedState *M = ctx->mixed;
   int rc;
   cudaMemsetAsync(M->dev_words, 0, 4, st);
-  if (need_jacobian &&
-      (rc = mixed_contract(ctx, d_mu, nullptr, nq, d_n, d_u, info, need_exact, st)) != RB_OK)
+  if ((rc = launch_prep(ctx, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
+  if (need_jacobian && (rc = mixed_contract(ctx, nq, d_n, d_u, info, need_exact, st)) != RB_OK)
     return rc;
   LuParams lp{};
   lp.o = ctx->ops;
-  lp.mu = d_mu;
   lp.nsz = d_n;
   lp.nq = nq;
   lp.nb = M->nb;
@@ -1210,7 +1420,6 @@ int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, dou
   lp.max_iter = ctx->cfg.max_iter;
   lp.tol_upd = ctx->cfg.tol_update;
   lp.tol_res = ctx->cfg.tol_res;
-  lp.A2 = M->A2;
   lp.Jc = M->Jc;
   lp.Rc = M->Rc;
   lp.u = d_u;
@@ -1224,7 +1433,8 @@ int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, dou
 int mixed_pressure_ok(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, const double *d_u,
                       double *d_p, rb_query_info *info, cudaStream_t st) {
   if (!(ctx->ops.m > 0 && ctx->ops.B && d_p)) return RB_OK;
-  return mixed_pressure(ctx, d_mu, nullptr, nq, d_n, d_u, d_p, info, st);
+  (void)d_mu;
+  return mixed_pressure(ctx, nq, d_n, d_u, d_p, info, st);
 }
 
 int mixed_error_word(rb_ctx *ctx, cudaStream_t st) {
@@ -1254,17 +1464,16 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
   cudaMemsetAsync(M->dev_words, 0, 8, st);
-  if ((rc = mixed_contract(ctx, d_mu, nullptr, nq, nsz, uw, info, true, st)) != RB_OK) return rc;
+  if ((rc = launch_prep(ctx, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
+  if ((rc = mixed_contract(ctx, nq, nsz, uw, info, true, st)) != RB_OK) return rc;
   LuParams lp{};
   lp.rmode = kResExact;
   lp.o = o;
-  lp.mu = d_mu;
   lp.nsz = nsz;
   lp.nq = nq;
   lp.nb = M->nb;
   lp.ldj = M->Npad;
   lp.max_iter = ctx->cfg.max_iter;
-  lp.A2 = M->A2;
   lp.Jc = M->Jc;
   lp.Rc = M->Rc;
   lp.u = uw;
