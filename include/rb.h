@@ -214,7 +214,9 @@ enum {
   RB_K_LU = 5,           /* mixed: FP32 LU, triangular solves, update, stopping test */
   RB_K_INIT = 6,         /* mixed: batch initialisation */
   RB_K_GEMM_PRES = 7,    /* mixed: tcgen05 sliced pressure right-hand side (-> FP64) */
-  RB_K_COUNT = 8
+  RB_K_SYSTEM = 8,       /* mixed: Newton system assembly [J | -R] and residual norms */
+  RB_K_PREP = 9,         /* mixed: per-query theta, f(mu), A(mu) at the start of a solve */
+  RB_K_COUNT = 10
 };
 int rb_profile(rb_ctx *ctx, int enable);
 int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launches);

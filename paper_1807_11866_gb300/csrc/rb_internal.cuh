@@ -120,6 +120,67 @@ __device__ __forceinline__ double df_warp_sum(float h, float l) {
   return (double)h + (double)l;
 }
 
+// (h1, l1) += (h2, l2) in double-float
+__device__ __forceinline__ void df_add(float &h1, float &l1, float h2, float l2) {
+  float s, e;
+  two_sum(h1, h2, s, e);
+  h1 = s;
+  l1 = l1 + l2 + e;
+}
+
+// Reduce-scatter of 8 double-float values per lane (one per row r = 0..7) over the warp:
+// after it, the lanes 4 r .. 4 r + 3 hold the warp total of row r in (h[0], l[0]).
+// 18 shuffle pairs instead of 8 full butterflies.
+__device__ __forceinline__ void df_warp_reduce8(float (&h)[8], float (&l)[8]) {
+  const int lane = threadIdx.x & 31;
+  // level xor 16: lanes with bit 4 set keep rows 4..7 (moved to slots 0..3), the others 0..3
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float sh = up ? h[i] : h[i + 4], sl = up ? l[i] : l[i + 4];
+      const float kh = up ? h[i + 4] : h[i], kl = up ? l[i + 4] : l[i];
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, 16);
+      const float rl = __shfl_xor_sync(0xffffffffu, sl, 16);
+      h[i] = kh;
+      l[i] = kl;
+      df_add(h[i], l[i], rh, rl);
+    }
+  }
+  // level xor 8: bit 3 selects slots 2..3 or 0..1
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float sh = up ? h[i] : h[i + 2], sl = up ? l[i] : l[i + 2];
+      const float kh = up ? h[i + 2] : h[i], kl = up ? l[i + 2] : l[i];
+      const float rh = __shfl_xor_sync(0xffffffffu, sh, 8);
+      const float rl = __shfl_xor_sync(0xffffffffu, sl, 8);
+      h[i] = kh;
+      l[i] = kl;
+      df_add(h[i], l[i], rh, rl);
+    }
+  }
+  // level xor 4: bit 2 selects slot 1 or 0
+  {
+    const bool up = lane & 4;
+    const float sh = up ? h[0] : h[1], sl = up ? l[0] : l[1];
+    const float kh = up ? h[1] : h[0], kl = up ? l[1] : l[0];
+    const float rh = __shfl_xor_sync(0xffffffffu, sh, 4);
+    const float rl = __shfl_xor_sync(0xffffffffu, sl, 4);
+    h[0] = kh;
+    l[0] = kl;
+    df_add(h[0], l[0], rh, rl);
+  }
+  // levels xor 2, 1: the group of four lanes holding one row
+#pragma unroll
+  for (int o = 2; o > 0; o >>= 1) {
+    const float rh = __shfl_xor_sync(0xffffffffu, h[0], o);
+    const float rl = __shfl_xor_sync(0xffffffffu, l[0], o);
+    df_add(h[0], l[0], rh, rl);
+  }
+}
+
 // (|value|, row) argmax with the first row winning ties.
 template <typename T>
 __device__ __forceinline__ void argmax_merge(T &v, int &r, T v2, int r2) {
@@ -227,7 +288,7 @@ __device__ __forceinline__ void backsub_warp(const float *M, int ld, int n, floa
 #pragma unroll
   for (int s = 0; s < kWarpRows; ++s) {
     const int k = lane + 32 * s;
-    d[s] = k < n ? __frcp_rn(M[(size_t)k * ld + k]) : 0.f;
+    d[s] = k < n ? __frcp_rn(M[k * ld + k]) : 0.f;
   }
   for (int j = n - 1; j >= 0; --j) {
     float own[kWarpRows];
@@ -237,54 +298,82 @@ __device__ __forceinline__ void backsub_warp(const float *M, int ld, int n, floa
 #pragma unroll
     for (int s = 0; s < kWarpRows; ++s) {
       const int k = lane + 32 * s;
-      if (k < j) y[s] = fmaf(-M[(size_t)k * ld + j], xj, y[s]);
+      if (k < j) y[s] = fmaf(-M[k * ld + j], xj, y[s]);
     }
   }
 #pragma unroll
   for (int s = 0; s < kWarpRows; ++s) y[s] *= d[s];
 }
 
+// Select lane-slot s of a 3-slot register vector (s warp-uniform or per lane).
+__device__ __forceinline__ float slot3(const float (&v)[kWarpRows], int s) {
+  return s == 0 ? v[0] : (s == 1 ? v[1] : v[2]);
+}
+
+__device__ __forceinline__ float comp4(const float4 &a, int t) {
+  return t == 0 ? a.x : (t == 1 ? a.y : (t == 2 ? a.z : a.w));
+}
+
 // Solve the n x n system stored with its right-hand side as the augmented matrix M = [A | b]
 // (column n holds b; row stride ld a multiple of 4 with ld / 4 odd and M 16-byte aligned, so
-// that lanes updating float4 chunks of consecutive rows hit distinct banks) by one warp:
-// Gaussian elimination with partial pivoting (pivot_key), b eliminated along, then back
-// substitution. Row k of the solution is returned in x[k / 32] of lane k % 32 (n <= 96).
-// Columns left of the pivot are not kept: the multipliers are not needed once b is eliminated.
+// that lanes reading float4 chunks of rows i, i + 1, ... hit distinct banks) by one warp:
+// Gaussian elimination with partial pivoting (pivot_key over the rows not yet used as pivots),
+// b eliminated along, then back substitution. Rows stay in place (implicit pivoting): row r is
+// owned by lane r % 32, which keeps the row's entry in the next pivot column in a register, so
+// a step needs no pivot-column reads and no row swap. pseq (shared, n ints) receives the pivot
+// row of every step. Row k of the solution is returned in x[k / 32] of lane k % 32 (n <= 96).
 // Returns true if a pivot was zero or not finite.
-__device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x)[kWarpRows]) {
+__device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x)[kWarpRows],
+                                              int *pseq) {
   const int lane = threadIdx.x & 31;
   const int c_end = n >> 2;  // last float4 chunk: the one holding column n
+  float cur[kWarpRows], dinv[kWarpRows];
+  int step[kWarpRows];       // step at which the row was the pivot; n: not yet; -1: no row
+#pragma unroll
+  for (int s = 0; s < kWarpRows; ++s) {
+    const int r = lane + 32 * s;
+    cur[s] = r < n ? M[r * ld] : 0.f;
+    step[s] = r < n ? n : -1;
+    dinv[s] = 0.f;
+  }
   for (int p = 0; p < n; ++p) {
     unsigned key = 0;
-    for (int i = p + lane; i < n; i += 32) {
-      const unsigned k = pivot_key(M[(size_t)i * ld + p], i);
-      key = k > key ? k : key;
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s) {
+      const unsigned k = pivot_key(cur[s], lane + 32 * s);
+      if (step[s] == n && k > key) key = k;
     }
     key = __reduce_max_sync(0xffffffffu, key);
     const int piv = 255 - (int)(key & 255u);
-    if (piv != p) {
-      float4 *rp = reinterpret_cast<float4 *>(M + (size_t)p * ld);
-      float4 *rq = reinterpret_cast<float4 *>(M + (size_t)piv * ld);
-      for (int c = (p >> 2) + lane; c <= c_end; c += 32) {
-        const float4 t = rp[c];
-        rp[c] = rq[c];
-        rq[c] = t;
-      }
-      __syncwarp();
-    }
-    const float pv = M[(size_t)p * ld + p];
+    const float pv = __shfl_sync(0xffffffffu, slot3(cur, piv >> 5), piv & 31);
     if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
     const float rinv = __frcp_rn(pv);
-    const float4 *mp = reinterpret_cast<const float4 *>(M + (size_t)p * ld);
-    const int c0 = (p + 1) >> 2;
-    for (int i = p + 1 + lane; i < n; i += 32) {
-      float *row = M + (size_t)i * ld;
-      const float l = row[p] * rinv;
-      float4 *mi = reinterpret_cast<float4 *>(row);
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s)
+      if (lane + 32 * s == piv) {
+        step[s] = p;
+        dinv[s] = rinv;
+      }
+    if (lane == 0) pseq[p] = piv;
+    const float4 *mp = reinterpret_cast<const float4 *>(M + piv * ld);
+    const int c0 = (p + 1) >> 2, tn = (p + 1) & 3;
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s) {
+      if (step[s] != n) continue;
+      float4 *mi = reinterpret_cast<float4 *>(M + (lane + 32 * s) * ld);
+      const float l = cur[s] * rinv;
+      float4 a = mi[c0];
+      float4 q = mp[c0];
+      a.x = fmaf(-l, q.x, a.x);
+      a.y = fmaf(-l, q.y, a.y);
+      a.z = fmaf(-l, q.z, a.z);
+      a.w = fmaf(-l, q.w, a.w);
+      mi[c0] = a;
+      cur[s] = comp4(a, tn);
 #pragma unroll 4
-      for (int c = c0; c <= c_end; ++c) {
-        float4 a = mi[c];
-        const float4 q = mp[c];
+      for (int c = c0 + 1; c <= c_end; ++c) {
+        a = mi[c];
+        q = mp[c];
         a.x = fmaf(-l, q.x, a.x);
         a.y = fmaf(-l, q.y, a.y);
         a.z = fmaf(-l, q.z, a.z);
@@ -294,12 +383,47 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
     }
     __syncwarp();
   }
+  // back substitution in step order: the solution entry of column j comes from row pseq[j]
+  float y[kWarpRows];
+#pragma unroll
+  for (int s = 0; s < kWarpRows; ++s) {
+    const int r = lane + 32 * s;
+    y[s] = r < n ? M[r * ld + n] : 0.f;
+  }
+  for (int c = (n - 1) >> 2; c >= 0; --c) {
+    float4 mc[kWarpRows];
+#pragma unroll
+    for (int s = 0; s < kWarpRows; ++s)
+      mc[s] = step[s] >= 0 ? reinterpret_cast<const float4 *>(M + (lane + 32 * s) * ld)[c]
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int4 pq = reinterpret_cast<const int4 *>(pseq)[c];
+#pragma unroll
+    for (int t = 3; t >= 0; --t) {
+      const int j = 4 * c + t;
+      if (j >= n) continue;
+      const int pr = t == 0 ? pq.x : (t == 1 ? pq.y : (t == 2 ? pq.z : pq.w));
+      float own[kWarpRows];
+#pragma unroll
+      for (int s = 0; s < kWarpRows; ++s) own[s] = y[s] * dinv[s];
+      const float xj = __shfl_sync(0xffffffffu, slot3(own, pr >> 5), pr & 31);
+#pragma unroll
+      for (int s = 0; s < kWarpRows; ++s)
+        if (step[s] >= 0 && step[s] < j) y[s] = fmaf(-comp4(mc[s], t), xj, y[s]);
+    }
+  }
+  // row r holds the solution entry of the column it pivoted; gather by column
+  float xr[kWarpRows];
+#pragma unroll
+  for (int s = 0; s < kWarpRows; ++s) xr[s] = y[s] * dinv[s];
 #pragma unroll
   for (int s = 0; s < kWarpRows; ++s) {
     const int k = lane + 32 * s;
-    x[s] = k < n ? M[(size_t)k * ld + n] : 0.f;
+    const int pr = k < n ? pseq[k] : 0;
+    const float v0 = __shfl_sync(0xffffffffu, xr[0], pr & 31);
+    const float v1 = __shfl_sync(0xffffffffu, xr[1], pr & 31);
+    const float v2 = __shfl_sync(0xffffffffu, xr[2], pr & 31);
+    x[s] = (pr >> 5) == 0 ? v0 : ((pr >> 5) == 1 ? v1 : v2);
   }
-  backsub_warp(M, ld, n, x);
   return false;
 }
 
@@ -314,16 +438,16 @@ __device__ __forceinline__ bool lu_factor_warp(float *M, int ld, int n, int *per
   for (int p = 0; p < n; ++p) {
     unsigned key = 0;
     for (int i = p + lane; i < n; i += 32) {
-      const unsigned k = pivot_key(M[(size_t)i * ld + p], i);
+      const unsigned k = pivot_key(M[i * ld + p], i);
       key = k > key ? k : key;
     }
     key = __reduce_max_sync(0xffffffffu, key);
     const int piv = 255 - (int)(key & 255u);
     if (piv != p) {
       for (int j = lane; j < n; j += 32) {
-        const float t = M[(size_t)p * ld + j];
-        M[(size_t)p * ld + j] = M[(size_t)piv * ld + j];
-        M[(size_t)piv * ld + j] = t;
+        const float t = M[p * ld + j];
+        M[p * ld + j] = M[piv * ld + j];
+        M[piv * ld + j] = t;
       }
       if (lane == 0) {
         const int t = perm[p];
@@ -332,12 +456,12 @@ __device__ __forceinline__ bool lu_factor_warp(float *M, int ld, int n, int *per
       }
       __syncwarp();
     }
-    const float pv = M[(size_t)p * ld + p];
+    const float pv = M[p * ld + p];
     if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
     const float rinv = __frcp_rn(pv);
-    const float *mp = M + (size_t)p * ld;
+    const float *mp = M + p * ld;
     for (int i = p + 1 + lane; i < n; i += 32) {
-      float *mi = M + (size_t)i * ld;
+      float *mi = M + i * ld;
       const float l = mi[p] * rinv;
       mi[p] = l;
       for (int j = p + 1; j < n; ++j) mi[j] = fmaf(-l, mp[j], mi[j]);
@@ -362,7 +486,7 @@ __device__ __forceinline__ void lu_solve_warp(const float *M, int ld, int n, con
 #pragma unroll
     for (int s = 0; s < kWarpRows; ++s) {
       const int k = lane + 32 * s;
-      if (k > j && k < n) x[s] = fmaf(-M[(size_t)k * ld + j], xj, x[s]);
+      if (k > j && k < n) x[s] = fmaf(-M[k * ld + j], xj, x[s]);
     }
   }
   backsub_warp(M, ld, n, x);

@@ -55,6 +55,8 @@ struct MixedState {
   double *Fm = nullptr;         // [bcap][nb] f(mu)
   float2 *Amu = nullptr;        // [bcap][nb * nb] A(mu) as double-float
   double *Asu = nullptr;        // [bcap][m] As(mu) u
+  float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices (nb <= 80)
+  double2 *Rn = nullptr;        // [bcap] residual norms of the assembled systems
   CUtensorMap tmXj, tmXd;
   float *lu_scratch = nullptr;
   int lu_grid = 0;
@@ -431,6 +433,9 @@ struct LuParams {
   double tol_upd, tol_res;
   const float2 *Amu;     // [nq][nb * nb] A(mu) as double-float (k_assemble_a)
   const double *Fm;      // [nq][nb] f(mu)
+  float *Jaug;           // [nq][nb][lda] augmented Newton matrices [J | -R] (warp path)
+  double2 *Rn;           // [nq]: (||R||, max(1, ||f||)) of the assembled system
+  int lda;
   const float *Jc;       // [b_pad][ldj]
   const double *Rc;      // [b_pad][nb]: C_mu(u, u)
   double *u;             // [nq][n_max], updated in place
@@ -488,7 +493,7 @@ __device__ __forceinline__ void newton_rows(const LuParams &p, int rm, int b, in
         if (p.eval_only)
           p.J_out[((size_t)b * n + k) * n + j] = (double)v;
         else
-          J[(size_t)k * ld + j] = v;
+          J[k * ld + j] = v;
       }
     }
   }
@@ -587,6 +592,8 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
   if (tid == 0 && my_active) atomicAdd(p.active, my_active);
 }
 
+constexpr int kWarpLuMaxN = 80;  // warp-per-query elimination up to this size
+
 // Row stride of the augmented Newton matrix [J | -R] of the warp kernel: >= nb + 1, a multiple
 // of 4 with an odd number of float4 chunks (bank-conflict-free float4 rows, see gepp_aug_warp).
 __host__ __device__ inline int aug_ld(int nb) {
@@ -595,36 +602,68 @@ __host__ __device__ inline int aug_ld(int nb) {
   return ld;
 }
 
-// Warp-per-query variant of k_lu_mixed for small Jacobians (no block barriers): each warp
-// owns one query at a time and its own shared-memory slab.
-struct WarpLuSmem {
-  int R, uh, J, ld, per_warp;  // byte offsets within a warp's slab; ld in floats
-  __host__ __device__ WarpLuSmem(int nb) {
-    int p = 0;
-    R = p; p += 8 * nb;
-    uh = p; p += 8 * nb;
-    p = (p + 15) & ~15;
-    ld = aug_ld(nb);
-    J = p; p += 4 * nb * ld;
-    per_warp = (p + 15) & ~15;
+// Rows k0 .. k0 + 7 of the Newton system, by one warp (lanes over columns), as newton_rows but
+// with the row sums reduce-scattered over the warp (df_warp_reduce8).
+__device__ __forceinline__ void newton_rows8(const LuParams &p, int rm, int b, int n, int k0,
+                                             const float2 *u2, float *J, int ld, double *R) {
+  const int lane = threadIdx.x & 31;
+  const size_t nb = (size_t)p.nb;
+  const float2 *am = p.Amu + (size_t)b * nb * nb;
+  const float *jc = p.Jc + (size_t)b * p.ldj;
+  const bool with_u = rm != kResZero;
+  float rh[8], rl[8], ch[8], cl[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) rh[r] = rl[r] = ch[r] = cl[r] = 0.f;
+  for (int j = lane; j < n; j += 32) {
+    float2 a[8];
+    float c[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int k = k0 + r;
+      a[r] = k < n ? __ldg(am + k * nb + j) : make_float2(0.f, 0.f);
+      c[r] = (with_u && k < n) ? __ldg(jc + k * nb + j) : 0.f;
+    }
+    const float2 uj = with_u ? u2[j] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int k = k0 + r;
+      if (k < n) {
+        const float v = (a[r].x + a[r].y) + c[r];
+        if (with_u) df_fma(rh[r], rl[r], a[r].x, a[r].y, uj.x, uj.y);
+        if (rm == kResLow) ch[r] = fmaf(0.5f * c[r], uj.x, ch[r]);
+        if (p.eval_only)
+          p.J_out[((size_t)b * n + k) * n + j] = (double)v;
+        else
+          J[k * ld + j] = v;
+      }
+    }
   }
-};
+  if (with_u) df_warp_reduce8(rh, rl);
+  if (rm == kResLow) df_warp_reduce8(ch, cl);
+  const int k = k0 + (lane >> 2);
+  if ((lane & 3) == 0 && k < n) {
+    const double rlin = with_u ? (double)rh[0] + (double)rl[0] : 0.0;
+    const double conv = rm == kResExact ? p.Rc[(size_t)b * nb + k]
+                                        : (rm == kResLow ? (double)ch[0] + (double)cl[0] : 0.0);
+    R[k] = rlin + conv - p.Fm[(size_t)b * nb + k];
+  }
+}
 
-__global__ void __launch_bounds__(kThreads, 2) k_lu_mixed_warp(LuParams p) {
+// Newton system of every active query, one warp per query with lanes over columns: the
+// augmented matrix [J | -R] (FP32, row stride lda, the right-hand side in column n, zero
+// padding up to the next multiple of 4) and the residual norms. Small shared footprint, so
+// many warps keep the A(mu) and J^c streams in flight. With eval_only, J and R go to
+// J_out / R_out in FP64 instead.
+__global__ void __launch_bounds__(kThreads, 3) k_newton_system(LuParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
-  const WarpLuSmem L(p.nb);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  uint8_t *slab = smb + (size_t)w * L.per_warp;
-  double *R = (double *)(slab + L.R);
-  float2 *u2 = (float2 *)(slab + L.uh);
-  float *J = (float *)(slab + L.J);
-  const int ld = L.ld;
-  int my_active = 0;
+  double *R = reinterpret_cast<double *>(smb + (size_t)w * 16 * p.nb);
+  float2 *u2 = reinterpret_cast<float2 *>(R + p.nb);
   for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
-    rb_query_info qi = p.info[b];
+    const rb_query_info qi = p.info[b];
     if (!is_active(qi, p.max_iter)) continue;
     const int n = p.nsz ? p.nsz[b] : p.nb;
-    double *ub = p.u + (size_t)b * p.o.n_max;
+    const double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
     if (rm != kResZero)
       for (int k = lane; k < n; k += 32) {
@@ -633,7 +672,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_mixed_warp(LuParams p) {
         u2[k] = make_float2(h, l);
       }
     __syncwarp();
-    for (int k0 = 0; k0 < n; k0 += 4) newton_rows<4>(p, rm, b, n, k0, u2, J, ld, R);
+    float *Jb = p.eval_only ? nullptr : p.Jaug + (size_t)b * p.nb * p.lda;
+    for (int k0 = 0; k0 < n; k0 += 8) newton_rows8(p, rm, b, n, k0, u2, Jb, p.lda, R);
     __syncwarp();
     if (p.eval_only) {
       for (int k = lane; k < n; k += 32) p.R_out[(size_t)b * n + k] = R[k];
@@ -646,12 +686,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_mixed_warp(LuParams p) {
     for (int k = lane; k < n; k += 32) {
       rl += R[k] * R[k];
       fl += fb[k] * fb[k];
-      float *row = J + (size_t)k * ld;
+      float *row = Jb + (size_t)k * p.lda;
       row[n] = (float)(-R[k]);
       for (int c = n + 1; c < c_pad; ++c) row[c] = 0.f;
     }
-    const double rn = sqrt(warp_sum(rl));
-    const double fscale = fmax(1.0, sqrt(warp_sum(fl)));
+    rl = warp_sum(rl);
+    fl = warp_sum(fl);
+    if (lane == 0) p.Rn[b] = make_double2(sqrt(rl), fmax(1.0, sqrt(fl)));
+    __syncwarp();
+  }
+}
+
+// Warp-per-query elimination of the systems k_newton_system assembled: copy the query's
+// augmented matrix into the warp's shared slab, solve, update u, apply the stopping rule.
+struct WarpLuSmem {
+  int pseq, J, per_warp;  // byte offsets within a warp's slab
+  __host__ __device__ WarpLuSmem(int nb, int lda) {
+    int p = 0;
+    pseq = p; p += 4 * ((nb + 3) & ~3);
+    p = (p + 15) & ~15;
+    J = p; p += 4 * nb * lda;
+    per_warp = (p + 15) & ~15;
+  }
+};
+
+__global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  const WarpLuSmem L(p.nb, p.lda);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  uint8_t *slab = smb + (size_t)w * L.per_warp;
+  float *J = reinterpret_cast<float *>(slab + L.J);
+  int *pseq = reinterpret_cast<int *>(slab + L.pseq);
+  const int ld = p.lda;
+  int my_active = 0;
+  for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
+    rb_query_info qi = p.info[b];
+    if (!is_active(qi, p.max_iter)) continue;
+    const int n = p.nsz ? p.nsz[b] : p.nb;
+    double *ub = p.u + (size_t)b * p.o.n_max;
+    const int rm = rung_of(p.rmode, qi.iters);
+    const double2 rr = p.Rn[b];
+    const double rn = rr.x, fscale = rr.y;
+    {
+      const float4 *src = reinterpret_cast<const float4 *>(p.Jaug + (size_t)b * p.nb * ld);
+      float4 *dst = reinterpret_cast<float4 *>(J);
+      const int n4 = n * ld / 4;
+#pragma unroll 4
+      for (int i = lane; i < n4; i += 32) dst[i] = __ldg(src + i);
+    }
     __syncwarp();
     qi.iters += 1;
     qi.res_norm = rn;
@@ -659,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_mixed_warp(LuParams p) {
     float x[kWarpRows];
     if (!isfinite(rn)) {
       qi.status = RB_Q_NONFINITE;
-    } else if (gepp_aug_warp(J, ld, n, x)) {
+    } else if (gepp_aug_warp(J, ld, n, x, pseq)) {
       qi.status = RB_Q_SINGULAR;
     } else {
       double dl = 0.0;
@@ -950,8 +1032,8 @@ void mixed_release(rb_ctx *ctx) {
   for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2,
                   (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
-                  (void *)M->Amu, (void *)M->Asu, (void *)M->lu_scratch, (void *)M->dev_words,
-                  (void *)M->info_own})
+                  (void *)M->Amu, (void *)M->Asu, (void *)M->Jaug, (void *)M->Rn,
+                  (void *)M->lu_scratch, (void *)M->dev_words, (void *)M->info_own})
     ctx_free(ctx, q);
   if (M->h_words) cudaFreeHost(M->h_words);
   delete M;
@@ -1062,8 +1144,10 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
   if (b_pad <= M->bcap) return RB_OK;
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
                   (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
-                  (void *)M->Asu})
+                  (void *)M->Asu, (void *)M->Jaug, (void *)M->Rn})
     ctx_free(ctx, q);
+  M->Jaug = nullptr;
+  M->Rn = nullptr;
   M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->ufT = nullptr; M->Jc = nullptr;
   M->Rc = M->Rp = M->Th = M->Fm = M->Asu = nullptr;
   M->Amu = nullptr;
@@ -1094,6 +1178,12 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
   M->Amu = (float2 *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * m, "As(mu) u")) != RB_OK) return rc;
   M->Asu = (double *)p;
+  if (M->nb <= kWarpLuMaxN) {
+    if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
+    M->Jaug = (float *)p;
+    if ((rc = ctx_alloc(ctx, &p, 16 * (size_t)b_pad, "residual norms")) != RB_OK) return rc;
+    M->Rn = (double2 *)p;
+  }
   // zero once so that padded rows never hold NaN bit patterns
   cudaMemsetAsync(M->Xj, 0, 2 * 3 * xs0, ctx->stream);
   cudaMemsetAsync(M->Xd, 0, 2 * xs * M->Smax, ctx->stream);
@@ -1173,7 +1263,7 @@ static int launch_prep(rb_ctx *ctx, const double *d_mu, const double *d_theta, i
   pp.Th = M->Th;
   pp.Fm = M->Fm;
   pp.Amu = M->Amu;
-  const int mk = prof_begin(ctx, RB_K_INIT, st);
+  const int mk = prof_begin(ctx, RB_K_PREP, st);
   k_prep_theta<<<std::max(1, std::min((nq + 7) / 8, ctx->sms * 16)), 256, 0, st>>>(pp);
   const size_t nn = (size_t)M->nb * M->nb;
   dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024),
@@ -1218,15 +1308,35 @@ static int mixed_contract(rb_ctx *ctx, int nq, const int *d_n, const double *d_u
   return RB_OK;
 }
 
-constexpr int kWarpLuMaxN = 80;  // warp-per-query elimination up to this size
 
 static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
   MixedState *M = ctx->mixed;
   lp.Amu = M->Amu;
   lp.Fm = M->Fm;
   if (M->nb <= kWarpLuMaxN) {
-    const int per_warp = WarpLuSmem(M->nb).per_warp;
-    const int wpc = std::max(1, std::min(8, (200 * 1024) / per_warp));
+    lp.Jaug = M->Jaug;
+    lp.Rn = M->Rn;
+    lp.lda = aug_ld(M->nb);
+    {
+      const size_t smem = 8 * (size_t)16 * M->nb;
+      const int grid = std::max(1, std::min((nq + 7) / 8, ctx->sms * 8));
+      const int mk = prof_begin(ctx, RB_K_SYSTEM, st);
+      k_newton_system<<<grid, kThreads, smem, st>>>(lp);
+      prof_end(ctx, mk, st);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
+    }
+    if (lp.eval_only) return RB_OK;
+    // warps per block: the most resident warps per SM that shared memory allows
+    const int per_warp = WarpLuSmem(M->nb, lp.lda).per_warp;
+    int wpc = 1, best = 0;
+    for (int c = 1; c <= 8; ++c) {
+      const int blocks = std::min(64 / c, (int)((size_t)ctx->smem_per_sm / ((size_t)c * per_warp + 1024)));
+      if (blocks * c > best && (size_t)c * per_warp <= (size_t)ctx->max_smem) {
+        best = blocks * c;
+        wpc = c;
+      }
+    }
     const size_t smem = (size_t)wpc * per_warp;
     const int per_sm = std::max(1, std::min(64 / wpc, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
     const int grid = std::max(1, std::min((nq + wpc - 1) / wpc, per_sm * ctx->sms));
@@ -1398,7 +1508,8 @@ size_t mixed_slot_bytes(const rb_ctx *ctx) {
   const size_t Npad = (size_t)round_up(o.n_max * o.n_max, kTcBN);
   const int S = 8;
   return 2 * 3 * Kpad0 + 2 * S * Kpad0 + 8 + 8 * nb + 4 * Npad + 8 * nb + 8 * (size_t)(o.m + 1) +
-         8 * nb + 64 + 8 * (size_t)o.n_theta + 8 * nb + 8 * nb * nb + 8 * (size_t)(o.m + 1);
+         8 * nb + 64 + 8 * (size_t)o.n_theta + 8 * nb + 8 * nb * nb + 8 * (size_t)(o.m + 1) +
+         (nb <= (size_t)kWarpLuMaxN ? 4 * nb * (size_t)aug_ld((int)nb) + 16 : 0);
 }
 
 // One Newton iteration for every live slot: the contraction work the slots' ladder rungs need,

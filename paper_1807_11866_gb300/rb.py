@@ -28,7 +28,8 @@ EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_
            "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
            "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
-              "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>"]
+              "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>",
+              "k_newton_system", "k_prep"]
 
 
 class rb_operators(ctypes.Structure):
