@@ -290,7 +290,7 @@ def main():
     d2h = batch * wl.n_max * 8 + (batch * m * 8 if m else 0) + batch * 32
 
     # roofline of the dominant kernel, measured live with events on the launching stream
-    roof, kernels = dominant_kernel_roofline(prec, wl, q, info, kprof, args.steps)
+    roof, roofs, kernels = kernel_rooflines(prec, wl, q, info, kprof, args.steps)
 
     line = {
         "metric": "reduced Newton solves/s", "value": value, "unit": "solves/s",
@@ -313,6 +313,7 @@ def main():
         "wall_s": wall,
     }
     line["roofline"] = roof
+    line["rooflines"] = roofs
     if rank == 0 and not args.no_plain and prec != 0:
         line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, args)
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
@@ -333,46 +334,68 @@ def main():
 
 
 FP64_PEAK_TFLOPS = 1.196  # FP64 FMA throughput measured on GB300 (152 SMs at 2070 MHz)
+# FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DIGITS = int(os.environ.get("RB_DIGITS", "6"))  # digit slices of the sliced convection product
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels as they
+# stand, from one ncu capture each of a 4096-query n = 50 solve (profiles/kernels_sweep_n50.md);
+# a kernel changed since its capture has no entry.
+NCU_TRAFFIC = {
+    "sweep_n50": {
+        "k_newton_system": 151.0e6,
+        "k_lu_mixed": 44.5e6,
+    },
+}
 
 
-def dominant_kernel_roofline(prec, wl, q, info, kprof, steps):
-    """Roofline of the kernel with the largest device time in the timed region.
-    Algorithmic work counts only the useful part: per active query-iteration of size n,
-      fused FP64 Newton: 2 (Q_c n^3 + Q_a n^2) + 2 n^3 / 3 + 2 n^2  FLOP (FP64),
-      sliced residual GEMM: P 2 Q_c n^3 FLOP of BF16 digit products (P = S (S + 1) / 2 pairs),
-      sliced pressure GEMM: P 2 Q_c m n^2 per converged query,
-      Jacobian GEMM: 3 x 2 Q_c n^3 FLOP (split BF16 products)."""
+def kernel_rooflines(prec, wl, q, info, kprof, steps):
+    """Roofline of every timed kernel kind, and of the one with the largest device time.
+    Algorithmic work counts only the useful part, per active query-iteration of size n:
+      fused FP64 Newton: 2 (Q_c n^3 + Q_a n^2) + 2 n^3 / 3 + 2 n^2 FLOP (FP64 ALU);
+      Jacobian GEMM: 3 x 2 Q_c n^3 FLOP of split-BF16 products (tensor);
+      sliced residual GEMM: P 2 Q_c n^3 FLOP of BF16 digit products, P = S (S + 1) / 2 (tensor);
+      sliced pressure GEMM: P 2 Q_c m n^2 per converged query (tensor);
+      elimination: 2 n^3 / 3 + 2 n^2 FLOP in FP32 (ALU);
+      system assembly: 8 n^2 (A(mu)) + 4 n^2 (J^c, after the first iteration) bytes read and
+        4 n (n + 1) bytes written (HBM);
+      per-query preparation: 8 n^2 bytes of A(mu) written, once per query (HBM)."""
     peaks, kind = measured_peaks()
     n = q.n.astype(np.float64)
     it = info["iters"].astype(np.float64)
     tot_ms = sum(v[0] for v in kprof.values()) or 1.0
     kernels = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps,
                    "share": v[0] / tot_ms} for k, v in kprof.items() if v[1]}
-    dom = max(kprof, key=lambda k: kprof[k][0])
-    ms, launches = kprof[dom]
-    # info holds one step's iteration counts; the timed region ran `steps` identical steps
-    if dom == "k_newton_fp64":
-        flops = steps * float(np.sum(it * (2 * (wl.q_c * n ** 3 + wl.q_a * n ** 2) + 2 * n ** 3 / 3 + 2 * n ** 2)))
-        ach = flops / (ms * 1e-3) / 1e12
-        return ({"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                 "peak_source": "measured FP64 FMA throughput (152 SMs, 2070 MHz)",
-                 "launches": launches}, kernels)
     p0 = DIGITS * (DIGITS + 1) // 2
-    if dom == "k_tc_gemm<sliced>":
-        per_q = 2.0 * n ** 2 * p0 * wl.q_c * n
-    elif dom == "k_tc_gemm<sliced,pressure>":
-        per_q = 2.0 * wl.m * n * p0 * wl.q_c * n / np.maximum(it, 1)
-    else:
-        per_q = 3 * 2.0 * wl.q_c * n ** 3
-    flops = steps * float(np.sum(it * per_q))
-    ach = flops / (ms * 1e-3) / 1e12
-    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    return ({"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-             "frac": ach / peak, "traffic": None,
-             "peak_source": f"bf16 sustained, {kind} (MEASURED_PEAKS.json)",
-             "launches": launches}, kernels)
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    hbm = peaks.get("hbm_gbs")
+    work = {  # kernel -> (bound, algorithmic units per step, peak, unit, peak source)
+        "k_newton_fp64": ("alu", float(np.sum(it * (2 * (wl.q_c * n ** 3 + wl.q_a * n ** 2) + 2 * n ** 3 / 3 + 2 * n ** 2))),
+                          FP64_PEAK_TFLOPS, "TFLOP/s", "measured FP64 FMA throughput (152 SMs, 2070 MHz)"),
+        "k_tc_gemm<plain>": ("tensor", float(np.sum(np.maximum(it - 1, 0) * 3 * 2.0 * wl.q_c * n ** 3)),
+                             bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
+        "k_tc_gemm<sliced>": ("tensor", float(np.sum(np.maximum(it - 2, 0) * 2.0 * n ** 2 * p0 * wl.q_c * n)),
+                              bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
+        "k_tc_gemm<sliced,pressure>": ("tensor", float(np.sum(2.0 * (wl.m or 0) * n * p0 * wl.q_c * n)),
+                                       bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
+        "k_lu_mixed": ("alu", float(np.sum(it * (2 * n ** 3 / 3 + 2 * n ** 2))), FP32_PEAK_TFLOPS, "TFLOP/s",
+                       "FP32 FMA peak from unit counts and clock (152 x 128 x 2 x 2.07 GHz)"),
+        "k_newton_system": ("hbm", float(np.sum(it * (8 * n ** 2 + 4 * n * (n + 1)) + np.maximum(it - 1, 0) * 4 * n ** 2)),
+                            hbm, "GB/s",
+                            f"HBM copy, {kind} (MEASURED_PEAKS.json)"),
+        "k_prep": ("hbm", float(np.sum(8 * n ** 2)), hbm, "GB/s", f"HBM copy, {kind} (MEASURED_PEAKS.json)"),
+    }
+    rl = {}
+    for k, (ms, launches) in kprof.items():
+        if not launches or k not in work:
+            continue
+        bound, units, peak, unit, src = work[k]
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = steps * units / (ms * 1e-3) / scale
+        traffic = NCU_TRAFFIC.get(wl.name, {}).get(k)
+        rl[k] = {"bound": bound, "kernel": k, "achieved": ach, "peak": peak, "unit": unit,
+                 "frac": ach / peak, "traffic": traffic, "peak_source": src, "launches": launches}
+    dom = max(kprof, key=lambda k: kprof[k][0])
+    return rl.get(dom), rl, kernels
 
 
 def plain_fp64(rb, ops, q, batch, dev, flush, args):
