@@ -25,9 +25,10 @@
 //    the sums are contracted with u_b[j] (double-float) and added into the FP64 output. Pairs
 //    with i + j > S + 1 are dropped (relative truncation ~2^-7S of the fixed-point range).
 //
-// Roles (320 threads): warp 0 issues TMA loads into a STAGES-deep shared-memory ring, warp 1
-// allocates TMEM and issues tcgen05.mma (one lane), warps 2-9 drain the two TMEM accumulator
-// buffers (128 lanes = 128 query rows; two warps per lane quarter split the columns).
+// Roles (576 threads): warp 0 issues TMA loads into a STAGES-deep shared-memory ring, warp 1
+// allocates TMEM and issues tcgen05.mma (one lane), warps 2-17 drain the two TMEM accumulator
+// buffers (128 lanes = 128 query rows; four warps per lane quarter split the columns, so that
+// a chunk drains in a quarter of the MMA time it took to fill).
 // Persistent over output tiles (m fastest).
 #include <cuda.h>
 
@@ -40,7 +41,8 @@ using namespace tc;
 
 constexpr int kBM = 128, kBK = 64;
 constexpr int kChunkSteps = 16;  // 16 k-blocks of 64 = 1024 exact terms per chunk (7-bit digits)
-constexpr int kEpiWarps = 8;     // epilogue warps: 2 per TMEM lane quarter
+constexpr int kEpiWarps = 16;    // epilogue warps: kEpiParts per TMEM lane quarter
+constexpr int kEpiParts = kEpiWarps / 4;  // column parts of a tile, one per warp of a quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreadsTc = 64 + kEpiThreads;
 
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     fence_proxy_async();
   }
   // TMEM columns: [0, 2 BN) two accumulator buffers; sliced mode adds [2 BN, 4 BN) for the
-  // per-column double-float sums (hi, lo) of each epilogue half
+  // per-column double-float sums (hi, lo) of each epilogue column part
   constexpr uint32_t kTmemCols = MODE == kSliced ? 4 * BN : 2 * BN;
   if (warp == 1) {
     tmem_alloc(tmem_slot, kTmemCols);
@@ -203,10 +205,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   } else {
     // ---------------- epilogue (warps 2..9) ----------------
     const int q = warp & 3;                  // TMEM lane quarter of this warp
-    const int half = (warp - 2) >> 2;        // which half of the tile's columns
+    const int half = (warp - 2) >> 2;        // which column part of the tile this warp drains
     const int row = q * 32 + lane;           // row of the tile owned by this thread
     const int et = (warp - 2) * 32 + lane;   // epilogue thread index
-    constexpr int HC = BN / 2;               // columns per thread
+    constexpr int HC = BN / kEpiParts;       // columns per thread
     float2 *uw = (float2 *)(smem + SM::kUOff);
     uint32_t chunk = 0, tile_it = 0;
     bool bad = false;
@@ -216,11 +218,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       const int nj = p.nj, total = p.nk * p.nj;
       const int jb = n0 % nj;
       if (MODE == kSliced) {
-        // window of u_b[j] for the tile's columns, [w][row]; the two halves load alternate
+        // window of u_b[j] for the tile's columns, [w][row]; the column parts load alternate
         // entries and share them (bounded mbarrier handoff, no unbounded named barrier)
         if (tile_it > 0 && !mbar_wait(uempty, (tile_it - 1) & 1, p.err, 6)) { bad = true; break; }
         const int wl = nj <= UW ? nj : BN;
-        for (int w = half; w < wl; w += 2) {
+        for (int w = half; w < wl; w += kEpiParts) {
           const int j = nj <= UW ? w : (jb + w) % nj;
           uw[w * kBM + row] = p.ufT[(size_t)j * p.b_pad + b];
         }
