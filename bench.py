@@ -238,7 +238,6 @@ def main():
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    ctx.rb_profile(True)  # per-kernel CUDA events on the launching stream, timed region only
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -252,9 +251,17 @@ def main():
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # per-kernel breakdown: the same steps again with the library's per-launch CUDA events on the
+    # launching stream (these launch kernel by kernel instead of replaying the solve graph)
+    ctx.rb_profile(True)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            step(stream)
+    torch.cuda.synchronize()
     kprof = ctx.rb_profile_read()
     ctx.rb_profile(False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(step_ms) / 1e3
     if world > 1:
         t = torch.tensor([t_dev], device=dev)
@@ -265,7 +272,9 @@ def main():
     info = d_info.cpu().numpy().view(rb.INFO_DTYPE).reshape(batch)
     u_gpu = d_u.cpu().numpy()
     p_gpu = d_p.cpu().numpy() if d_p is not None else None
-    launches_total = sum(v[1] for v in kprof.values())
+    # kernels of one step: those the profiled pass counted plus the graph's loop-condition kernel
+    # (one per Newton iteration of the batch)
+    launches_total = sum(v[1] for v in kprof.values()) + args.steps * int(info["iters"].max())
 
     # end-to-end through the public host-buffer API, pinned host memory
     h_mu = torch.from_numpy(q.mu).pin_memory()

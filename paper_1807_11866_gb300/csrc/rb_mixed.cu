@@ -64,6 +64,15 @@ struct MixedState {
   int *h_words = nullptr;       // pinned mirror
   rb_query_info *info_own = nullptr;
   int info_cap = 0;
+  // whole-solve CUDA graph (prologue, two ladder iterations, a device-side while loop over
+  // FP64-residual iterations, pressure), keyed by the solve's buffers and the scratch epoch
+  uint64_t epoch = 1;
+  cudaStream_t cap[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec = nullptr;
+  struct {
+    const double *mu, *theta, *p; const int *n; double *u; rb_query_info *info; int nq;
+    uint64_t epoch;
+  } gkey{};
 };
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1036,6 +1045,9 @@ void mixed_release(rb_ctx *ctx) {
                   (void *)M->lu_scratch, (void *)M->dev_words, (void *)M->info_own})
     ctx_free(ctx, q);
   if (M->h_words) cudaFreeHost(M->h_words);
+  if (M->gexec) cudaGraphExecDestroy(M->gexec);
+  for (cudaStream_t c : M->cap)
+    if (c) cudaStreamDestroy(c);
   delete M;
   ctx->mixed = nullptr;
 }
@@ -1193,6 +1205,7 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
       !make_map(&M->tmXd, M->Xd, (uint64_t)M->Smax * b_pad, M->Kpad, 128))
     return set_error(ctx, RB_ERR_CUDA, "tensor map encode (X)");
   M->bcap = b_pad;
+  M->epoch += 1;
   return RB_OK;
 }
 
@@ -1309,6 +1322,35 @@ static int mixed_contract(rb_ctx *ctx, int nq, const int *d_n, const double *d_u
 }
 
 
+// Block elimination (n > 80): J in shared memory when it fits the opt-in limit, otherwise in a
+// per-CTA global slab reserved here (before any graph capture).
+static bool block_lu_j_in_smem(const rb_ctx *ctx) {
+  return LuSmem(ctx->mixed->nb, true).total <= (size_t)ctx->max_smem;
+}
+
+static int block_lu_grid(const rb_ctx *ctx, int nq) {
+  const size_t smem = LuSmem(ctx->mixed->nb, block_lu_j_in_smem(ctx)).total;
+  const int per_sm = std::max(1, std::min(2048 / kThreads, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
+  return std::max(1, std::min(nq, per_sm * ctx->sms));
+}
+
+static int lu_reserve(rb_ctx *ctx, int nq) {
+  MixedState *M = ctx->mixed;
+  if (M->nb <= kWarpLuMaxN || block_lu_j_in_smem(ctx)) return RB_OK;
+  const int grid = block_lu_grid(ctx, nq);
+  if (M->lu_grid >= grid) return RB_OK;
+  ctx_free(ctx, M->lu_scratch);
+  M->lu_scratch = nullptr;
+  M->lu_grid = 0;
+  void *p;
+  const int rc = ctx_alloc(ctx, &p, 4 * (size_t)grid * M->nb * M->nb, "LU scratch");
+  if (rc != RB_OK) return rc;
+  M->lu_scratch = (float *)p;
+  M->lu_grid = grid;
+  M->epoch += 1;
+  return RB_OK;
+}
+
 static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
   MixedState *M = ctx->mixed;
   lp.Amu = M->Amu;
@@ -1349,22 +1391,12 @@ static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp");
     return RB_OK;
   }
-  const size_t smem_in = LuSmem(M->nb, true).total;
-  lp.j_in_smem = smem_in <= (size_t)ctx->max_smem ? 1 : 0;
+  lp.j_in_smem = block_lu_j_in_smem(ctx) ? 1 : 0;
   const size_t smem = LuSmem(M->nb, lp.j_in_smem != 0).total;
-  const int per_sm = std::max(1, std::min(2048 / kThreads, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
-  const int grid = std::max(1, std::min(nq, per_sm * ctx->sms));
+  const int grid = block_lu_grid(ctx, nq);
   if (!lp.j_in_smem) {
-    if (M->lu_grid < grid) {
-      ctx_free(ctx, M->lu_scratch);
-      M->lu_scratch = nullptr;
-      M->lu_grid = 0;
-      void *p;
-      int rc = ctx_alloc(ctx, &p, 4 * (size_t)grid * M->nb * M->nb, "LU scratch");
-      if (rc != RB_OK) return rc;
-      M->lu_scratch = (float *)p;
-      M->lu_grid = grid;
-    }
+    int rc = lu_reserve(ctx, nq);
+    if (rc != RB_OK) return rc;
     lp.scratch = M->lu_scratch;
   }
   cudaError_t e = cudaFuncSetAttribute(k_lu_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1448,6 +1480,138 @@ static int mixed_pressure(rb_ctx *ctx, int nq, const int *d_n, const double *d_u
   return RB_OK;
 }
 
+// One batch solve, split into the pieces that the stream path runs with a host check per
+// iteration and that the graph path captures once.
+struct SolveArgs {
+  const double *mu, *theta;
+  int nq;
+  const int *n;
+  double *u, *p;
+  rb_query_info *info;
+};
+
+static LuParams solve_lu_params(rb_ctx *ctx, const SolveArgs &a) {
+  MixedState *M = ctx->mixed;
+  LuParams lp{};
+  lp.o = ctx->ops;
+  lp.nsz = a.n;
+  lp.nq = a.nq;
+  lp.nb = M->nb;
+  lp.ldj = M->Npad;
+  lp.max_iter = ctx->cfg.max_iter;
+  lp.tol_upd = ctx->cfg.tol_update;
+  lp.tol_res = ctx->cfg.tol_res;
+  lp.Jc = M->Jc;
+  lp.Rc = M->Rc;
+  lp.u = a.u;
+  lp.info = a.info;
+  lp.active = M->dev_words;
+  lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
+  return lp;
+}
+
+// words[0] active count of the last iteration, [1] error word, [2] iterations done
+static int solve_prologue(rb_ctx *ctx, const SolveArgs &a, cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  const int mk = prof_begin(ctx, RB_K_INIT, st);
+  k_mixed_init<<<std::min(a.nq, ctx->sms * 8), 128, 0, st>>>(a.nq, ctx->ops.n_max, a.n, a.u, a.info);
+  prof_end(ctx, mk, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
+  int rc = launch_prep(ctx, a.mu, a.theta, a.nq, a.info, st);
+  if (rc != RB_OK) return rc;
+  e = cudaMemsetAsync(M->dev_words, 0, 16, st);
+  return e == cudaSuccess ? RB_OK : cuda_fail(ctx, e, "words");
+}
+
+// Newton iteration `rung` (0: u = 0, 1: low-precision residual, 2: FP64-accurate residual;
+// the kernels pick each query's rung from its own iteration count).
+static int solve_iteration(rb_ctx *ctx, const SolveArgs &a, int rung, cudaStream_t st) {
+  MixedState *M = ctx->mixed;
+  cudaError_t e = cudaMemsetAsync(M->dev_words, 0, 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
+  int rc;
+  if (rung >= 1 && (rc = mixed_contract(ctx, a.nq, a.n, a.u, a.info, rung >= 2, st)) != RB_OK) return rc;
+  LuParams lp = solve_lu_params(ctx, a);
+  return launch_lu(ctx, lp, a.nq, st);
+}
+
+// words[2] += 1; keep looping while queries are active and the iteration cap is not reached
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, int *words, int max_iter) {
+  const int it = ++words[2];
+  cudaGraphSetConditional(h, (words[0] > 0 && it < max_iter) ? 1u : 0u);
+}
+
+static int build_solve_graph(rb_ctx *ctx, const SolveArgs &a) {
+  MixedState *M = ctx->mixed;
+  const bool pres = a.p && ctx->ops.m > 0 && ctx->ops.B;
+  for (cudaStream_t &c : M->cap)
+    if (!c && cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess)
+      return set_error(ctx, RB_ERR_CUDA, "capture stream");
+  cudaStream_t cs = M->cap[0], cb = M->cap[1];
+  if (M->gexec) {
+    cudaGraphExecDestroy(M->gexec);
+    M->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(ctx, e, "graph capture begin");
+  }
+  int rc = RB_OK;
+  bool body_open = false;
+  do {
+    if ((rc = solve_prologue(ctx, a, cs)) != RB_OK) break;
+    for (int r = 0; r < 2 && rc == RB_OK; ++r) {
+      if ((rc = solve_iteration(ctx, a, r, cs)) != RB_OK) break;
+      k_loop_cond<<<1, 1, 0, cs>>>(h, M->dev_words, ctx->cfg.max_iter);
+    }
+    if (rc != RB_OK) break;
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd)) != cudaSuccess) break;
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t cn;
+    if ((e = cudaGraphAddNode(&cn, g, dv.data(), nullptr, dv.size(), &np)) != cudaSuccess) break;
+    if ((e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess) break;
+    if ((e = cudaStreamBeginCaptureToGraph(cb, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)) != cudaSuccess) break;
+    body_open = true;
+    if ((rc = solve_iteration(ctx, a, 2, cb)) != RB_OK) break;
+    k_loop_cond<<<1, 1, 0, cb>>>(h, M->dev_words, ctx->cfg.max_iter);
+    cudaGraph_t bg;
+    body_open = false;
+    if ((e = cudaStreamEndCapture(cb, &bg)) != cudaSuccess) break;
+    if (pres && (rc = mixed_pressure(ctx, a.nq, a.n, a.u, a.p, a.info, cs)) != RB_OK) break;
+  } while (false);
+  if (body_open) {
+    cudaGraph_t bg;
+    cudaStreamEndCapture(cb, &bg);
+  }
+  cudaGraph_t gout = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &gout);
+  if (rc == RB_OK && e == cudaSuccess && e2 == cudaSuccess) {
+    e = cudaGraphInstantiate(&M->gexec, g, 0);
+    if (e != cudaSuccess) M->gexec = nullptr;
+  }
+  cudaGraphDestroy(g);
+  if (rc != RB_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve graph");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "solve graph capture");
+  M->gkey = {a.mu, a.theta, a.p, a.n, a.u, a.info, a.nq, M->epoch};
+  return RB_OK;
+}
+
 int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
                 double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st) {
   int rc = mixed_layouts(ctx, st);
@@ -1456,36 +1620,26 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   MixedState *M = ctx->mixed;
   rb_query_info *info = d_info ? d_info : own_info(ctx, nq);
   if (!info) return set_error(ctx, RB_ERR_OOM, "info scratch");
-  const DevOps &o = ctx->ops;
-  int mk = prof_begin(ctx, RB_K_INIT, st);
-  k_mixed_init<<<std::min(nq, ctx->sms * 8), 128, 0, st>>>(nq, o.n_max, d_n, d_u, info);
-  prof_end(ctx, mk, st);
-  if ((rc = launch_prep(ctx, d_mu, d_theta, nq, info, st)) != RB_OK) return rc;
-  cudaMemsetAsync(M->dev_words, 0, 8, st);
-  LuParams lp{};
-  lp.o = o;
-  lp.nsz = d_n;
-  lp.nq = nq;
-  lp.nb = M->nb;
-  lp.ldj = M->Npad;
-  lp.max_iter = ctx->cfg.max_iter;
-  lp.tol_upd = ctx->cfg.tol_update;
-  lp.tol_res = ctx->cfg.tol_res;
-  lp.Jc = M->Jc;
-  lp.Rc = M->Rc;
-  lp.u = d_u;
-  lp.info = info;
-  lp.active = M->dev_words;
-  lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
+  if ((rc = lu_reserve(ctx, nq)) != RB_OK) return rc;
+  const SolveArgs a{d_mu, d_theta, nq, d_n, d_u, d_p, info};
+  const bool pres = d_p && ctx->ops.m > 0 && ctx->ops.B;
+  if (ctx->cfg.use_graph && !ctx->prof) {
+    const auto &k = M->gkey;
+    if (!M->gexec || k.mu != d_mu || k.theta != d_theta || k.p != d_p || k.n != d_n || k.u != d_u ||
+        k.info != info || k.nq != nq || k.epoch != M->epoch) {
+      if ((rc = build_solve_graph(ctx, a)) != RB_OK) return rc;
+    }
+    const cudaError_t e = cudaGraphLaunch(M->gexec, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve graph launch");
+    return check_words(ctx, st, "mixed solve");
+  }
+  if ((rc = solve_prologue(ctx, a, st)) != RB_OK) return rc;
   for (int it = 0; it < ctx->cfg.max_iter; ++it) {
-    cudaMemsetAsync(M->dev_words, 0, 4, st);
-    if (it >= 1 && (rc = mixed_contract(ctx, nq, d_n, d_u, info, it >= 2, st)) != RB_OK)
-      return rc;
-    if ((rc = launch_lu(ctx, lp, nq, st)) != RB_OK) return rc;
+    if ((rc = solve_iteration(ctx, a, std::min(it, 2), st)) != RB_OK) return rc;
     if ((rc = check_words(ctx, st, "mixed Newton step")) != RB_OK) return rc;
     if (M->h_words[0] == 0) break;
   }
-  if (d_p && o.m > 0 && o.B) {
+  if (pres) {
     if ((rc = mixed_pressure(ctx, nq, d_n, d_u, d_p, info, st)) != RB_OK) return rc;
     if ((rc = check_words(ctx, st, "pressure recovery")) != RB_OK) return rc;
   }

@@ -163,3 +163,30 @@ def test_large_n_mixed(rb, n, q, nq):
     o = oracle.Oracle.from_set(ops)
     u_ref, _, _ = o.solve(mu[idx], threads=8)
     assert rel(u[idx], u_ref).max() <= TOL_MIXED
+
+
+def test_graph_and_stream_paths_agree(rb):
+    """The captured whole-solve graph (device-side while loop over FP64-residual iterations)
+    gives bit-identical results to the stream path that checks convergence on the host after
+    every iteration; the graph is rebuilt when the batch changes, and honours the iteration cap."""
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl, n_max=30)
+    q = synth.make_queries(wl, batch=300, n_max=30)
+    res = {}
+    for g in (0, 1):
+        with rb.Context(rb.RB_PREC_MIXED, use_graph=g) as ctx:
+            ctx.load_set(ops)
+            a = ctx.rb_solve(q.mu)
+            b = ctx.rb_solve(q.mu[:77])          # another batch: graph rebuilt
+            c = ctx.rb_solve(q.mu)               # back to the first
+        res[g] = (a, b, c)
+    for x, y in zip(res[0], res[1]):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        assert np.array_equal(x[2]["iters"], y[2]["iters"]) and np.array_equal(x[2]["status"], y[2]["status"])
+    assert np.array_equal(res[1][0][0], res[1][2][0])
+    assert np.array_equal(res[1][0][0][:77], res[1][1][0])
+    with rb.Context(rb.RB_PREC_MIXED, use_graph=1, max_iter=3) as ctx:
+        ctx.load_set(ops)
+        _, _, info = ctx.rb_solve(q.mu[:50])
+    assert np.all(info["iters"] <= 3)
+    assert set(np.unique(info["status"])) <= {rb.RB_Q_OK, rb.RB_Q_NOT_CONVERGED}
