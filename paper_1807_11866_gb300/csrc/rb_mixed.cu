@@ -1,20 +1,25 @@
 // rb_mixed.cu -- mixed-precision batched Newton (inexact Newton, Sec. 3.6 Jacobian on tensor cores).
 //
-// Per iteration, for every active query b of the batch:
+// Once per query at its start: theta(mu_b), f(mu_b) (k_prep_theta) and A(mu_b) in double-float
+// (k_assemble_a). Per Newton iteration, for every active query b of the batch:
 //   1. k_build_x: X_b = theta^c(mu_b) (x) u_b as split BF16 (hi, lo) for the Jacobian GEMM; the
 //      7-bit digit slices of theta^c (x) u_b / 2 for the sliced GEMM; u_b as (hi, lo) floats
 //      (transposed); R^c_b = 0.
 //   2. k_tc_gemm<kPlain>:  J^c = X W^T on tcgen05 (split BF16, FP32 accumulate) -> Jc (FP32).
 //   3. k_tc_gemm<kSliced>: R^c_b[k] = sum_j u_b[j] (X'_b W^T)[(k,j)] = C_mu(u_b, u_b)[k] from
 //      exact digit products, contracted in double-float -> FP64.
-//   4. k_lu_mixed(_warp): A(mu) and A(mu) u in double-float on the CUDA cores;
-//      R = A(mu) u + C_mu(u, u) - f(mu); J = fl32(A(mu)) + J^c; GEPP in FP32 on J delta = -R;
-//      u += delta in FP64; stopping rule (Sec. 6) on the FP64 norms.
+//   4. k_newton_system: [J | -R] with J = fl32(A(mu)) + J^c and R = A(mu) u (double-float)
+//      + C_mu(u, u) - f(mu); residual norms.
+//   5. k_lu_mixed_warp (warp per query, n <= 80) or k_lu_blocked (CTA per query, blocked
+//      right-looking elimination): FP32 GEPP on [J | -R]; u += delta in FP64; stopping rule
+//      (Sec. 6) on the FP64 norms.
 // The Jacobian is inexact (BF16 convection part, FP32 elimination); the residual and the test
 // are FP64-accurate, so the iteration converges to the FP64 solution at the linear rate
 // ||J~^-1 (J~ - J)||. After the last iteration the pressure right-hand side
 // fs(mu) - As(mu) u - Cs_mu(u, u) (Eq. sup-vvar) takes Cs_mu(u, u) from the same sliced GEMM with
-// W = 2 Cs and As(mu) u in double-float, and B(mu) p = r is solved in FP64 (Eq. blocksolve-2).
+// W = 2 Cs and As(mu) u in double-float (k_as_u); B(mu) p = r is solved by FP32 LU with
+// double-float iterative refinement (Eq. blocksolve-2). The whole solve is one CUDA graph with a
+// device-side loop over the FP64-residual iterations.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -58,8 +63,6 @@ struct MixedState {
   float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices (nb <= 80)
   double2 *Rn = nullptr;        // [bcap] residual norms of the assembled systems
   CUtensorMap tmXj, tmXd;
-  float *lu_scratch = nullptr;
-  int lu_grid = 0;
   int *dev_words = nullptr;     // [0] active count, [1] error word, [8..] scratch
   int *h_words = nullptr;       // pinned mirror
   rb_query_info *info_own = nullptr;
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(256) k_assemble_a(PrepParams p) {
 struct LuParams {
   DevOps o;
   const int *nsz;
-  int nq, nb, ldj, max_iter, j_in_smem;
+  int nq, nb, ldj, max_iter;
   double tol_upd, tol_res;
   const float2 *Amu;     // [nq][nb * nb] A(mu) as double-float (k_assemble_a)
   const double *Fm;      // [nq][nb] f(mu)
@@ -449,7 +452,6 @@ struct LuParams {
   const double *Rc;      // [b_pad][nb]: C_mu(u, u)
   double *u;             // [nq][n_max], updated in place
   rb_query_info *info;   // [nq]
-  float *scratch;        // [grid][nb * nb] when J is not in shared memory
   int *active;           // count of queries still active after this iteration
   int eval_only;         // 1: write R and J (FP64) to R_out / J_out instead of solving
   double *R_out, *J_out;
@@ -468,138 +470,6 @@ __device__ __forceinline__ int rung_of(int rmode, int iters) {
   return rmode >= 0 ? rmode : (iters == 0 ? kResZero : (iters == 1 ? kResLow : kResExact));
 }
 
-// Rows k0 .. k0 + RR - 1 of the Newton system, by one warp (lanes over columns):
-// J[k][:] = fl32(A(mu)[k][:]) + J^c[k][:] and R[k] = A(mu)[k][:] u (double-float) + convection
-// part - f[k]. All RR rows' loads of a column block are issued before their arithmetic.
-template <int RR>
-__device__ __forceinline__ void newton_rows(const LuParams &p, int rm, int b, int n, int k0,
-                                            const float2 *u2, float *J, int ld, double *R) {
-  const int lane = threadIdx.x & 31;
-  const size_t nb = (size_t)p.nb;
-  const float2 *am = p.Amu + (size_t)b * nb * nb;
-  const float *jc = p.Jc + (size_t)b * p.ldj;
-  const bool with_u = rm != kResZero;
-  float rh[RR], rl[RR], clow[RR];
-#pragma unroll
-  for (int r = 0; r < RR; ++r) rh[r] = rl[r] = clow[r] = 0.f;
-  for (int j = lane; j < n; j += 32) {
-    float2 a[RR];
-    float c[RR];
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-      const int k = k0 + r;
-      a[r] = k < n ? __ldg(am + k * nb + j) : make_float2(0.f, 0.f);
-      c[r] = (with_u && k < n) ? __ldg(jc + k * nb + j) : 0.f;
-    }
-    const float2 uj = with_u ? u2[j] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int r = 0; r < RR; ++r) {
-      const int k = k0 + r;
-      if (k < n) {
-        const float v = (a[r].x + a[r].y) + c[r];
-        if (with_u) df_fma(rh[r], rl[r], a[r].x, a[r].y, uj.x, uj.y);
-        if (rm == kResLow) clow[r] = fmaf(0.5f * c[r], uj.x, clow[r]);
-        if (p.eval_only)
-          p.J_out[((size_t)b * n + k) * n + j] = (double)v;
-        else
-          J[k * ld + j] = v;
-      }
-    }
-  }
-  const double *fb = p.Fm + (size_t)b * nb;
-#pragma unroll
-  for (int r = 0; r < RR; ++r) {
-    const int k = k0 + r;
-    const double rlin = with_u ? df_warp_sum(rh[r], rl[r]) : 0.0;
-    const float cl = rm == kResLow ? warp_sum(clow[r]) : 0.f;
-    if (lane == 0 && k < n) {
-      const double conv = rm == kResExact ? p.Rc[(size_t)b * nb + k] : (double)cl;
-      R[k] = rlin + conv - fb[k];
-    }
-  }
-}
-
-struct LuSmem {
-  int R, red, uh, rhs, J, total;  // offsets in bytes
-  __host__ __device__ LuSmem(int nb, bool j_in_smem) {
-    int p = 0;
-    R = p; p += 8 * nb;
-    red = p; p += 8 * 4 * kWarps;
-    uh = p; p += 8 * nb;               // u as (hi, lo) floats
-    rhs = p; p += 4 * ((nb + 3) & ~3);
-    p = (p + 15) & ~15;
-    J = p;
-    if (j_in_smem) p += 4 * nb * nb;
-    total = p;
-  }
-};
-
-// One Newton iteration per active query, one block per query (large n).
-__global__ void __launch_bounds__(kThreads) k_lu_mixed(LuParams p) {
-  extern __shared__ __align__(16) uint8_t smb[];
-  const LuSmem L(p.nb, p.j_in_smem != 0);
-  double *R = (double *)(smb + L.R), *red = (double *)(smb + L.red);
-  float2 *u2 = (float2 *)(smb + L.uh);
-  float *rhs = (float *)(smb + L.rhs);
-  float *J = p.j_in_smem ? (float *)(smb + L.J) : p.scratch + (size_t)blockIdx.x * p.nb * p.nb;
-  const int tid = threadIdx.x, w = tid >> 5;
-  int my_active = 0;
-  for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
-    rb_query_info qi = p.info[b];
-    if (!is_active(qi, p.max_iter)) continue;
-    const int n = p.nsz ? p.nsz[b] : p.nb;
-    double *ub = p.u + (size_t)b * p.o.n_max;
-    const int rm = rung_of(p.rmode, qi.iters);
-    if (rm != kResZero)
-      for (int k = tid; k < n; k += blockDim.x) {
-        float h, l;
-        df_split(ub[k], h, l);
-        u2[k] = make_float2(h, l);
-      }
-    __syncthreads();
-    for (int k0 = 4 * w; k0 < n; k0 += 4 * kWarps) newton_rows<4>(p, rm, b, n, k0, u2, J, n, R);
-    __syncthreads();
-    if (p.eval_only) {
-      for (int k = tid; k < n; k += blockDim.x) p.R_out[(size_t)b * n + k] = R[k];
-      __syncthreads();
-      continue;
-    }
-    const double *fb = p.Fm + (size_t)b * p.nb;
-    double rl = 0.0, fl = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) {
-      rl += R[i] * R[i];
-      fl += fb[i] * fb[i];
-      rhs[i] = (float)(-R[i]);
-    }
-    const double rn = sqrt(block_sum(rl, red));
-    const double fscale = fmax(1.0, sqrt(block_sum(fl, red)));
-    qi.iters += 1;
-    qi.res_norm = rn;
-    qi.precision_used = RB_PREC_MIXED;
-    if (!isfinite(rn)) {
-      qi.status = RB_Q_NONFINITE;
-    } else if (gepp_solve_block<float>(J, n, n, rhs, red)) {
-      qi.status = RB_Q_SINGULAR;
-    } else {
-      double dl = 0.0;
-      for (int i = tid; i < n; i += blockDim.x) {
-        const double d = (double)rhs[i];
-        dl += d * d;
-        ub[i] += d;
-      }
-      const double dn = sqrt(block_sum(dl, red));
-      qi.upd_norm = dn;
-      if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
-      else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
-    }
-    if (tid == 0) {
-      p.info[b] = qi;
-      if (is_active(qi, p.max_iter)) ++my_active;
-    }
-    __syncthreads();
-  }
-  if (tid == 0 && my_active) atomicAdd(p.active, my_active);
-}
 
 constexpr int kWarpLuMaxN = 80;  // warp-per-query elimination up to this size
 
@@ -611,8 +481,10 @@ __host__ __device__ inline int aug_ld(int nb) {
   return ld;
 }
 
-// Rows k0 .. k0 + 7 of the Newton system, by one warp (lanes over columns), as newton_rows but
-// with the row sums reduce-scattered over the warp (df_warp_reduce8).
+// Rows k0 .. k0 + 7 of the Newton system, by one warp (lanes over columns):
+// J[k][:] = fl32(A(mu)[k][:]) + J^c[k][:] and R[k] = A(mu)[k][:] u (double-float) + convection
+// part - f[k]. The 8 rows' loads of a column block are issued before their arithmetic, and the
+// row sums are reduce-scattered over the warp (df_warp_reduce8).
 __device__ __forceinline__ void newton_rows8(const LuParams &p, int rm, int b, int n, int k0,
                                              const float2 *u2, float *J, int ld, double *R) {
   const int lane = threadIdx.x & 31;
@@ -775,6 +647,233 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
     __syncwarp();
   }
   if (lane == 0 && my_active) atomicAdd(p.active, my_active);
+}
+
+// ---- blocked elimination for large systems (n_max > 80), one CTA per query --------------
+// Right-looking blocked Gaussian elimination with partial pivoting on the query's augmented
+// matrix [J | -R] (global, row stride lda, the right-hand side in column n): for each panel of
+// kPB columns, (a) the tall panel is factored in shared memory with partial pivoting,
+// (b) its row interchanges are applied to the columns right of it, (c) the panel's row block
+// becomes U12 = L11^-1 A12, (d) the trailing matrix takes the rank-kPB update
+// A22 -= L21 U12 in 4 x 4 register tiles. The right-hand side is eliminated along, so back
+// substitution on U (blocks of 32 rows from the bottom) ends the solve.
+constexpr int kPB = 32;           // panel width
+constexpr int kPLd = kPB + 1;     // panel row stride in shared memory (odd: conflict-free columns)
+
+struct BlkLuSmem {
+  int P, U, perm, red, x, dred, total;  // byte offsets
+  __host__ __device__ BlkLuSmem(int nb, int lda) {
+    int p = 0;
+    P = p; p += 4 * nb * kPLd;
+    p = (p + 15) & ~15;
+    U = p; p += 4 * kPB * lda;
+    perm = p; p += 4 * kPB;
+    red = p; p += 4 * kWarps;
+    x = p; p += 4 * ((nb + 3) & ~3);
+    p = (p + 7) & ~7;
+    dred = p; p += 8 * 4 * kWarps;
+    total = (p + 15) & ~15;
+  }
+};
+
+// pivot key for panel rows r < 512: leading 14 mantissa bits of |v|, then the lower row
+__device__ __forceinline__ unsigned pivot_key9(float v, int r) {
+  return (__float_as_uint(fabsf(v)) & 0xFFFFFE00u) | (unsigned)(511 - r);
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  const int nb = p.nb, lda = p.lda;
+  const BlkLuSmem L(nb, lda);
+  float *P = reinterpret_cast<float *>(smb + L.P);
+  float *U = reinterpret_cast<float *>(smb + L.U);
+  int *perm = reinterpret_cast<int *>(smb + L.perm);
+  unsigned *red = reinterpret_cast<unsigned *>(smb + L.red);
+  float *xs = reinterpret_cast<float *>(smb + L.x);
+  double *dred = reinterpret_cast<double *>(smb + L.dred);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  int my_active = 0;
+  for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
+    rb_query_info qi = p.info[b];
+    if (!is_active(qi, p.max_iter)) continue;
+    const int n = p.nsz ? p.nsz[b] : nb;
+    double *ub = p.u + (size_t)b * p.o.n_max;
+    const int rm = rung_of(p.rmode, qi.iters);
+    const double2 rr = p.Rn[b];
+    const double rn = rr.x, fscale = rr.y;
+    float *M = p.Jaug + (size_t)b * nb * lda;
+    bool sing = !isfinite(rn);
+    for (int k0 = 0; k0 < n && !sing; k0 += kPB) {
+      const int kb = min(kPB, n - k0), rows = n - k0;
+      // (a) load and factor the panel: rows k0 .. n-1, columns k0 .. k0+kb-1
+      for (int e = tid; e < rows * kPB; e += blockDim.x) {
+        const int r = e / kPB, c = e - r * kPB;
+        P[r * kPLd + c] = c < kb ? M[(size_t)(k0 + r) * lda + k0 + c] : 0.f;
+      }
+      __syncthreads();
+      for (int j = 0; j < kb; ++j) {
+        unsigned key = 0;
+        for (int r = j + tid; r < rows; r += blockDim.x) {
+          const unsigned k = pivot_key9(P[r * kPLd + j], r);
+          key = k > key ? k : key;
+        }
+        key = __reduce_max_sync(0xffffffffu, key);
+        if (lane == 0) red[w] = key;
+        __syncthreads();
+        key = red[0];
+#pragma unroll
+        for (int i = 1; i < kWarps; ++i) key = red[i] > key ? red[i] : key;
+        const int pr = 511 - (int)(key & 511u);
+        const float pv = P[pr * kPLd + j];
+        if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+          sing = true;
+          break;
+        }
+        if (pr != j && tid < kPB) {
+          const float t = P[j * kPLd + tid];
+          P[j * kPLd + tid] = P[pr * kPLd + tid];
+          P[pr * kPLd + tid] = t;
+        }
+        if (tid == 0) perm[j] = pr;
+        __syncthreads();
+        const float rinv = __frcp_rn(pv);
+        for (int r = j + 1 + tid; r < rows; r += blockDim.x) {
+          float *Pr = P + r * kPLd;
+          const float l = Pr[j] * rinv;
+          Pr[j] = l;
+          for (int c = j + 1; c < kb; ++c) Pr[c] = fmaf(-l, P[j * kPLd + c], Pr[c]);
+        }
+        __syncthreads();
+      }
+      if (sing) break;
+      // U11 (the panel's top rows) back to the matrix for the back substitution
+      for (int e = tid; e < kb * kb; e += blockDim.x) {
+        const int r = e / kb, c = e - r * kb;
+        M[(size_t)(k0 + r) * lda + k0 + c] = P[r * kPLd + c];
+      }
+      // (b) row interchanges on the columns right of the panel, then (c) U12 = L11^-1 A12;
+      // one thread per column
+      const int c_lo = k0 + kb;
+      for (int c = c_lo + tid; c <= n; c += blockDim.x) {
+        for (int j = 0; j < kb; ++j) {
+          const int pr = perm[j];
+          if (pr != j) {
+            float *a = M + (size_t)(k0 + j) * lda + c, *q = M + (size_t)(k0 + pr) * lda + c;
+            const float t = *a;
+            *a = *q;
+            *q = t;
+          }
+        }
+        // the column's kb entries in this thread's column of U (shared), solved in place
+        for (int j = 0; j < kb; ++j) U[j * lda + c] = M[(size_t)(k0 + j) * lda + c];
+        for (int j = 1; j < kb; ++j) {
+          float v = U[j * lda + c];
+          for (int i = 0; i < j; ++i) v = fmaf(-P[j * kPLd + i], U[i * lda + c], v);
+          U[j * lda + c] = v;
+        }
+        for (int j = 0; j < kb; ++j) M[(size_t)(k0 + j) * lda + c] = U[j * lda + c];
+      }
+      __syncthreads();
+      // (d) trailing update of rows k0+kb .. n-1, columns c_lo .. n, in tiles of 4 rows x 4 columns
+      const int r_lo = kb, nrow = rows - kb;
+      if (nrow > 0) {
+        const int cc_lo = c_lo >> 2, cc_hi = n >> 2;  // float4 chunks covering columns c_lo .. n
+        const int nch = cc_hi - cc_lo + 1, nrb = (nrow + 3) >> 2;
+        for (int t = tid; t < nch * nrb; t += blockDim.x) {
+          const int rb4 = t / nch, cc = cc_lo + (t - rb4 * nch);
+          const int r0 = r_lo + 4 * rb4;
+          float4 acc[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            acc[i] = r0 + i < rows ? reinterpret_cast<const float4 *>(M + (size_t)(k0 + r0 + i) * lda)[cc]
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int j = 0; j < kb; ++j) {
+            const float4 u = reinterpret_cast<const float4 *>(U + j * lda)[cc];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float l = r0 + i < rows ? P[(r0 + i) * kPLd + j] : 0.f;
+              acc[i].x = fmaf(-l, u.x, acc[i].x);
+              acc[i].y = fmaf(-l, u.y, acc[i].y);
+              acc[i].z = fmaf(-l, u.z, acc[i].z);
+              acc[i].w = fmaf(-l, u.w, acc[i].w);
+            }
+          }
+          const int c4 = 4 * cc;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (r0 + i >= rows) break;
+            float *row = M + (size_t)(k0 + r0 + i) * lda + c4;
+            if (c4 >= c_lo && c4 + 3 <= n) {
+              reinterpret_cast<float4 *>(row)[0] = acc[i];
+            } else {  // first or last chunk: only columns c_lo .. n
+              if (c4 + 0 >= c_lo && c4 + 0 <= n) row[0] = acc[i].x;
+              if (c4 + 1 >= c_lo && c4 + 1 <= n) row[1] = acc[i].y;
+              if (c4 + 2 >= c_lo && c4 + 2 <= n) row[2] = acc[i].z;
+              if (c4 + 3 >= c_lo && c4 + 3 <= n) row[3] = acc[i].w;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    qi.iters += 1;
+    qi.res_norm = rn;
+    qi.precision_used = RB_PREC_MIXED;
+    if (!isfinite(rn)) {
+      qi.status = RB_Q_NONFINITE;
+    } else if (sing) {
+      qi.status = RB_Q_SINGULAR;
+    } else {
+      // back substitution, blocks of 32 rows from the bottom: warp 0 solves the diagonal block,
+      // then every thread updates the right-hand side of one row above it
+      for (int i = tid; i < n; i += blockDim.x) xs[i] = M[(size_t)i * lda + n];
+      __syncthreads();
+      for (int i1 = n; i1 > 0; i1 -= 32) {
+        const int i0 = max(0, i1 - 32);
+        if (w == 0) {
+          const int r = i0 + lane;
+          const bool own = r < i1;
+          float mrow[32];  // the lane's row of the diagonal block, loaded before the chain
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj)
+            mrow[jj] = (own && i0 + jj < i1) ? M[(size_t)r * lda + i0 + jj] : 0.f;
+          float y = own ? xs[r] : 0.f;
+          const float d = own ? __frcp_rn(M[(size_t)r * lda + r]) : 0.f;
+#pragma unroll
+          for (int jj = 31; jj >= 0; --jj) {
+            if (i0 + jj >= i1) continue;
+            const float xj = __shfl_sync(0xffffffffu, y * d, jj);
+            if (own && lane < jj) y = fmaf(-mrow[jj], xj, y);
+          }
+          if (own) xs[r] = y * d;
+        }
+        __syncthreads();
+        for (int r = tid; r < i0; r += blockDim.x) {
+          const float *row = M + (size_t)r * lda;
+          float s = xs[r];
+          for (int j = i0; j < i1; ++j) s = fmaf(-row[j], xs[j], s);
+          xs[r] = s;
+        }
+        __syncthreads();
+      }
+      double dl = 0.0;
+      for (int i = tid; i < n; i += blockDim.x) {
+        const double d = (double)xs[i];
+        dl += d * d;
+        ub[i] += d;
+      }
+      const double dn = sqrt(block_sum(dl, dred));
+      qi.upd_norm = dn;
+      if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
+      else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+    }
+    if (tid == 0) {
+      p.info[b] = qi;
+      if (is_active(qi, p.max_iter)) ++my_active;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && my_active) atomicAdd(p.active, my_active);
 }
 
 // ---- pressure (Eq. sup-vvar, Eq. blocksolve-2) ----------------------------------------------
@@ -1042,7 +1141,7 @@ void mixed_release(rb_ctx *ctx) {
                   (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
                   (void *)M->Amu, (void *)M->Asu, (void *)M->Jaug, (void *)M->Rn,
-                  (void *)M->lu_scratch, (void *)M->dev_words, (void *)M->info_own})
+                  (void *)M->dev_words, (void *)M->info_own})
     ctx_free(ctx, q);
   if (M->h_words) cudaFreeHost(M->h_words);
   if (M->gexec) cudaGraphExecDestroy(M->gexec);
@@ -1190,12 +1289,10 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
   M->Amu = (float2 *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * m, "As(mu) u")) != RB_OK) return rc;
   M->Asu = (double *)p;
-  if (M->nb <= kWarpLuMaxN) {
-    if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
-    M->Jaug = (float *)p;
-    if ((rc = ctx_alloc(ctx, &p, 16 * (size_t)b_pad, "residual norms")) != RB_OK) return rc;
-    M->Rn = (double2 *)p;
-  }
+  if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
+  M->Jaug = (float *)p;
+  if ((rc = ctx_alloc(ctx, &p, 16 * (size_t)b_pad, "residual norms")) != RB_OK) return rc;
+  M->Rn = (double2 *)p;
   // zero once so that padded rows never hold NaN bit patterns
   cudaMemsetAsync(M->Xj, 0, 2 * 3 * xs0, ctx->stream);
   cudaMemsetAsync(M->Xd, 0, 2 * xs * M->Smax, ctx->stream);
@@ -1322,90 +1419,60 @@ static int mixed_contract(rb_ctx *ctx, int nq, const int *d_n, const double *d_u
 }
 
 
-// Block elimination (n > 80): J in shared memory when it fits the opt-in limit, otherwise in a
-// per-CTA global slab reserved here (before any graph capture).
-static bool block_lu_j_in_smem(const rb_ctx *ctx) {
-  return LuSmem(ctx->mixed->nb, true).total <= (size_t)ctx->max_smem;
-}
-
-static int block_lu_grid(const rb_ctx *ctx, int nq) {
-  const size_t smem = LuSmem(ctx->mixed->nb, block_lu_j_in_smem(ctx)).total;
-  const int per_sm = std::max(1, std::min(2048 / kThreads, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
-  return std::max(1, std::min(nq, per_sm * ctx->sms));
-}
-
-static int lu_reserve(rb_ctx *ctx, int nq) {
-  MixedState *M = ctx->mixed;
-  if (M->nb <= kWarpLuMaxN || block_lu_j_in_smem(ctx)) return RB_OK;
-  const int grid = block_lu_grid(ctx, nq);
-  if (M->lu_grid >= grid) return RB_OK;
-  ctx_free(ctx, M->lu_scratch);
-  M->lu_scratch = nullptr;
-  M->lu_grid = 0;
-  void *p;
-  const int rc = ctx_alloc(ctx, &p, 4 * (size_t)grid * M->nb * M->nb, "LU scratch");
-  if (rc != RB_OK) return rc;
-  M->lu_scratch = (float *)p;
-  M->lu_grid = grid;
-  M->epoch += 1;
-  return RB_OK;
-}
-
+// Newton step of the batch: k_newton_system assembles [J | -R] per query, then one warp
+// (n_max <= 80) or one CTA (blocked elimination) per query solves it.
 static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
   MixedState *M = ctx->mixed;
   lp.Amu = M->Amu;
   lp.Fm = M->Fm;
-  if (M->nb <= kWarpLuMaxN) {
-    lp.Jaug = M->Jaug;
-    lp.Rn = M->Rn;
-    lp.lda = aug_ld(M->nb);
-    {
-      const size_t smem = 8 * (size_t)16 * M->nb;
-      const int grid = std::max(1, std::min((nq + 7) / 8, ctx->sms * 8));
-      const int mk = prof_begin(ctx, RB_K_SYSTEM, st);
-      k_newton_system<<<grid, kThreads, smem, st>>>(lp);
-      prof_end(ctx, mk, st);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
-    }
-    if (lp.eval_only) return RB_OK;
-    // warps per block: the most resident warps per SM that shared memory allows
-    const int per_warp = WarpLuSmem(M->nb, lp.lda).per_warp;
-    int wpc = 1, best = 0;
-    for (int c = 1; c <= 8; ++c) {
-      const int blocks = std::min(64 / c, (int)((size_t)ctx->smem_per_sm / ((size_t)c * per_warp + 1024)));
-      if (blocks * c > best && (size_t)c * per_warp <= (size_t)ctx->max_smem) {
-        best = blocks * c;
-        wpc = c;
-      }
-    }
-    const size_t smem = (size_t)wpc * per_warp;
-    const int per_sm = std::max(1, std::min(64 / wpc, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
-    const int grid = std::max(1, std::min((nq + wpc - 1) / wpc, per_sm * ctx->sms));
-    cudaError_t e = cudaFuncSetAttribute(k_lu_mixed_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp attr");
+  lp.Jaug = M->Jaug;
+  lp.Rn = M->Rn;
+  lp.lda = aug_ld(M->nb);
+  {
+    const size_t smem = 8 * (size_t)16 * M->nb;
+    const int grid = std::max(1, std::min((nq + 7) / 8, ctx->sms * 8));
+    const int mk = prof_begin(ctx, RB_K_SYSTEM, st);
+    k_newton_system<<<grid, kThreads, smem, st>>>(lp);
+    prof_end(ctx, mk, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
+  }
+  if (lp.eval_only) return RB_OK;
+  if (M->nb > kWarpLuMaxN) {
+    const size_t smem = BlkLuSmem(M->nb, lp.lda).total;
+    cudaError_t e = cudaFuncSetAttribute(k_lu_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_blocked attr");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_blocked, kThreads, smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_blocked occupancy");
+    const int grid = std::max(1, std::min(nq, std::max(1, per_sm) * ctx->sms));
     const int mk = prof_begin(ctx, RB_K_LU, st);
-    k_lu_mixed_warp<<<grid, 32 * wpc, smem, st>>>(lp);
+    k_lu_blocked<<<grid, kThreads, smem, st>>>(lp);
     prof_end(ctx, mk, st);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_blocked");
     return RB_OK;
   }
-  lp.j_in_smem = block_lu_j_in_smem(ctx) ? 1 : 0;
-  const size_t smem = LuSmem(M->nb, lp.j_in_smem != 0).total;
-  const int grid = block_lu_grid(ctx, nq);
-  if (!lp.j_in_smem) {
-    int rc = lu_reserve(ctx, nq);
-    if (rc != RB_OK) return rc;
-    lp.scratch = M->lu_scratch;
+  // warps per block: the most resident warps per SM that shared memory allows
+  const int per_warp = WarpLuSmem(M->nb, lp.lda).per_warp;
+  int wpc = 1, best = 0;
+  for (int c = 1; c <= 8; ++c) {
+    const int blocks = std::min(64 / c, (int)((size_t)ctx->smem_per_sm / ((size_t)c * per_warp + 1024)));
+    if (blocks * c > best && (size_t)c * per_warp <= (size_t)ctx->max_smem) {
+      best = blocks * c;
+      wpc = c;
+    }
   }
-  cudaError_t e = cudaFuncSetAttribute(k_lu_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed attr");
+  const size_t smem = (size_t)wpc * per_warp;
+  const int per_sm = std::max(1, std::min(64 / wpc, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
+  const int grid = std::max(1, std::min((nq + wpc - 1) / wpc, per_sm * ctx->sms));
+  cudaError_t e = cudaFuncSetAttribute(k_lu_mixed_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp attr");
   const int mk = prof_begin(ctx, RB_K_LU, st);
-  k_lu_mixed<<<grid, kThreads, smem, st>>>(lp);
+  k_lu_mixed_warp<<<grid, 32 * wpc, smem, st>>>(lp);
   prof_end(ctx, mk, st);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp");
   return RB_OK;
 }
 
@@ -1620,7 +1687,6 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   MixedState *M = ctx->mixed;
   rb_query_info *info = d_info ? d_info : own_info(ctx, nq);
   if (!info) return set_error(ctx, RB_ERR_OOM, "info scratch");
-  if ((rc = lu_reserve(ctx, nq)) != RB_OK) return rc;
   const SolveArgs a{d_mu, d_theta, nq, d_n, d_u, d_p, info};
   const bool pres = d_p && ctx->ops.m > 0 && ctx->ops.B;
   if (ctx->cfg.use_graph && !ctx->prof) {
@@ -1663,7 +1729,7 @@ size_t mixed_slot_bytes(const rb_ctx *ctx) {
   const int S = 8;
   return 2 * 3 * Kpad0 + 2 * S * Kpad0 + 8 + 8 * nb + 4 * Npad + 8 * nb + 8 * (size_t)(o.m + 1) +
          8 * nb + 64 + 8 * (size_t)o.n_theta + 8 * nb + 8 * nb * nb + 8 * (size_t)(o.m + 1) +
-         (nb <= (size_t)kWarpLuMaxN ? 4 * nb * (size_t)aug_ld((int)nb) + 16 : 0);
+         4 * nb * (size_t)aug_ld((int)nb) + 16;
 }
 
 // One Newton iteration for every live slot: the contraction work the slots' ladder rungs need,
