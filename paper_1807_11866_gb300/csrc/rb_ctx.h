@@ -29,14 +29,15 @@ int op_alloc(rb_ctx *ctx, void **p, size_t bytes, const char *what);
 
 int solve_fp64(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
                double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st);
+// h_n: host copy of d_n if the caller has one (else read back when the batch needs bucketing)
 int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
-                double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st);
+                const int *h_n, double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st);
 int solve_pressure(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
                    const int *d_n, const double *d_u, double *d_p, rb_query_info *d_info,
                    cudaStream_t st);
 int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
                       const int *d_n, double *d_u, double *d_p, rb_query_info *d_info,
-                      cudaStream_t st);
+                      cudaStream_t st, const int *h_n = nullptr);
 int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u, int precision,
                double *d_R, double *d_J, cudaStream_t st);
 void mixed_release(rb_ctx *ctx);

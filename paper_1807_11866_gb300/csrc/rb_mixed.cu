@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "rb_ctx.h"
@@ -39,14 +40,19 @@ struct SlicedW {  // one sliced weight operand [S][Npad][Kpad]
   CUtensorMap tm;
 };
 
+// Mixed-path state of one size bucket: operator layouts truncated to nb (the reduced bases are
+// nested, so a size-n query is the leading n-block of any bucket nb >= n) and the batch
+// scratch of the queries solved at that size. The root bucket (nb = n_max) also owns what all
+// buckets share: the device words, the gather scratch of a bucketed batch and the solve graph.
 struct MixedState {
-  // operator layouts for the Jacobian size nb (= n_max)
+  MixedState *root = nullptr;   // the n_max bucket (itself for the root)
+  // operator layouts for the Jacobian size nb
   int nb = 0, Kpad0 = 0, kb0 = 0, kb1 = 0, Kpad = 0, Npad = 0, S0 = 0, S1 = 0, Smax = 0;
   __nv_bfloat16 *Wj = nullptr;  // [2][Npad][Kpad0] split BF16 D~ (hi, lo)
   CUtensorMap tmWj;
   SlicedW WR, WP;               // residual [D~ | A], pressure [2 Cs | As]
-  float2 *A2 = nullptr;         // [q_a][n_max][n_max] A_q as double-float (hi, lo)
-  float2 *As2 = nullptr;        // [q_a][m][n_max] As_q as double-float
+  float2 *A2 = nullptr;         // [q_a][nb][nb] A_q as double-float (hi, lo)
+  float2 *As2 = nullptr;        // [q_a][m][nb] As_q as double-float
   float2 *B2 = nullptr;         // [q_b][m][m] B_q as double-float
   // batch scratch
   int bcap = 0;
@@ -60,21 +66,29 @@ struct MixedState {
   double *Fm = nullptr;         // [bcap][nb] f(mu)
   float2 *Amu = nullptr;        // [bcap][nb * nb] A(mu) as double-float
   double *Asu = nullptr;        // [bcap][m] As(mu) u
-  float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices (nb <= 80)
+  float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices
   double2 *Rn = nullptr;        // [bcap] residual norms of the assembled systems
   CUtensorMap tmXj, tmXd;
-  int *dev_words = nullptr;     // [0] active count, [1] error word, [8..] scratch
+  // shared, owned by the root
+  int *dev_words = nullptr;     // [0] active count, [1] error word, [2] iterations, [8..] scratch
   int *h_words = nullptr;       // pinned mirror
   rb_query_info *info_own = nullptr;
   int info_cap = 0;
+  std::map<int, MixedState *> buckets;  // nb < n_max
+  // gather scratch of a bucketed batch (query order sorted by bucket)
+  int gcap = 0;
+  int *perm = nullptr, *n_g = nullptr;
+  double *mu_g = nullptr, *theta_g = nullptr, *u_g = nullptr, *p_g = nullptr;
+  rb_query_info *info_g = nullptr;
   // whole-solve CUDA graph (prologue, two ladder iterations, a device-side while loop over
-  // FP64-residual iterations, pressure), keyed by the solve's buffers and the scratch epoch
+  // FP64-residual iterations, pressure), keyed by the solve's buffers, buckets and scratch epoch
   uint64_t epoch = 1;
   cudaStream_t cap[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec = nullptr;
   struct {
     const double *mu, *theta, *p; const int *n; double *u; rb_query_info *info; int nq;
     uint64_t epoch;
+    std::vector<int> parts;
   } gkey{};
 };
 
@@ -160,6 +174,53 @@ __global__ void k_split_f2(const double *x, float2 *y, size_t count) {
        e += (size_t)gridDim.x * blockDim.x) {
     const float h = (float)x[e];
     y[e] = make_float2(h, (float)(x[e] - (double)h));
+  }
+}
+
+// y[q][r][c] = (hi, lo) of x[(q * src_rows + r) * ldx + c] for r < rows, c < cols: the
+// double-float copy of the leading rows x cols block of q_count matrices (a bucket's
+// truncation of an operator).
+__global__ void k_split_trunc(const double *x, float2 *y, int q_count, int rows, int src_rows,
+                              int ldx, int cols) {
+  const size_t total = (size_t)q_count * rows * cols;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t qr = e / cols;
+    const int c = (int)(e - qr * cols);
+    const size_t q = qr / rows, r = qr - q * rows;
+    const double v = x[(q * src_rows + r) * ldx + c];
+    const float h = (float)v;
+    y[e] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+// Rows of a bucketed batch in bucket order: dst[i] = src[perm[i]].
+__global__ void k_gather(int nq, const int *perm, const double *mu, const double *theta,
+                         int n_theta, const int *n, double *mu_g, double *theta_g, int *n_g) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += gridDim.x * blockDim.x) {
+    const int s = perm[i];
+    if (mu) {
+      mu_g[2 * i] = mu[2 * s];
+      mu_g[2 * i + 1] = mu[2 * s + 1];
+    }
+    if (theta)
+      for (int t = 0; t < n_theta; ++t) theta_g[(size_t)i * n_theta + t] = theta[(size_t)s * n_theta + t];
+    n_g[i] = n[s];
+  }
+}
+
+// Results back to the caller's order: dst[perm[i]] = src[i] (one warp per query).
+__global__ void k_scatter(int nq, const int *perm, int nm, int m, const double *u_g,
+                          const double *p_g, const rb_query_info *info_g, double *u, double *p,
+                          rb_query_info *info) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nq; i += nw) {
+    const int d = perm[i];
+    for (int j = lane; j < nm; j += 32) u[(size_t)d * nm + j] = u_g[(size_t)i * nm + j];
+    if (p)
+      for (int j = lane; j < m; j += 32) p[(size_t)d * m + j] = p_g[(size_t)i * m + j];
+    if (lane == 0) info[d] = info_g[i];
   }
 }
 
@@ -887,10 +948,10 @@ struct AsuParams {
   DevOps o;
   const double *theta;  // [nq][n_theta]
   const int *nsz;
-  int nq;
+  int nq, nb;           // nb: the bucket size (columns of As2)
   const double *u;      // [nq][n_max]
   const rb_query_info *info;
-  const float2 *As2;    // [q_a][m][n_max] double-float
+  const float2 *As2;    // [q_a][m][nb] double-float
   double *out;          // [b_pad][m]
 };
 
@@ -901,7 +962,7 @@ __global__ void __launch_bounds__(256) k_as_u(AsuParams p) {
   __shared__ float2 ts[kAsQ * RB_Q_MAX];
   __shared__ int flag[kAsQ];
   const DevOps &o = p.o;
-  const int nm = o.n_max, ldr = odd_ld(nm), m = o.m, qa = o.q_a;
+  const int nm = p.nb, ldr = odd_ld(nm), m = o.m, qa = o.q_a;
   float2 *us = (float2 *)smb;        // [kAsQ][ldr]
   float2 *as = us + kAsQ * ldr;      // [kAsR][ldr]
   const int tid = threadIdx.x, bi = tid >> 4, ki = tid & 15;
@@ -918,7 +979,7 @@ __global__ void __launch_bounds__(256) k_as_u(AsuParams p) {
     for (int i = tid; i < kAsQ * nm; i += blockDim.x) {
       const int r = i / nm, j = i - r * nm, b = b0 + r;
       float h = 0.f, l = 0.f;
-      if (flag[r] && j < (p.nsz ? p.nsz[b] : nm)) df_split(p.u[(size_t)b * nm + j], h, l);
+      if (flag[r] && j < (p.nsz ? p.nsz[b] : nm)) df_split(p.u[(size_t)b * o.n_max + j], h, l);
       us[r * ldr + j] = make_float2(h, l);
     }
     for (int i = tid; i < kAsQ * qa; i += blockDim.x) {
@@ -1134,19 +1195,32 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve(PresSolveParams p) 
 
 // ---------------------------------------------------------------------------------------
 // host side
-void mixed_release(rb_ctx *ctx) {
-  MixedState *M = ctx->mixed;
-  if (!M) return;
+static void release_state(rb_ctx *ctx, MixedState *M) {
   for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2,
                   (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
-                  (void *)M->Amu, (void *)M->Asu, (void *)M->Jaug, (void *)M->Rn,
-                  (void *)M->dev_words, (void *)M->info_own})
+                  (void *)M->Amu, (void *)M->Asu, (void *)M->Jaug, (void *)M->Rn})
     ctx_free(ctx, q);
-  if (M->h_words) cudaFreeHost(M->h_words);
-  if (M->gexec) cudaGraphExecDestroy(M->gexec);
-  for (cudaStream_t c : M->cap)
-    if (c) cudaStreamDestroy(c);
+  if (M->root == M) {
+    for (auto &kv : M->buckets) {
+      release_state(ctx, kv.second);
+      delete kv.second;
+    }
+    for (void *q : {(void *)M->dev_words, (void *)M->info_own, (void *)M->perm, (void *)M->n_g,
+                    (void *)M->mu_g, (void *)M->theta_g, (void *)M->u_g, (void *)M->p_g,
+                    (void *)M->info_g})
+      ctx_free(ctx, q);
+    if (M->h_words) cudaFreeHost(M->h_words);
+    if (M->gexec) cudaGraphExecDestroy(M->gexec);
+    for (cudaStream_t c : M->cap)
+      if (c) cudaStreamDestroy(c);
+  }
+}
+
+void mixed_release(rb_ctx *ctx) {
+  MixedState *M = ctx->mixed;
+  if (!M) return;
+  release_state(ctx, M);
   delete M;
   ctx->mixed = nullptr;
 }
@@ -1158,9 +1232,9 @@ static int sliced_digits(const char *var, int dflt) {
   return std::min(8, std::max(2, s));
 }
 
-static int absmax_exp(rb_ctx *ctx, const double *x, size_t count, int *e_out, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
-  unsigned long long *mx = (unsigned long long *)(M->dev_words + 8);
+static int absmax_exp(rb_ctx *ctx, MixedState *M, const double *x, size_t count, int *e_out,
+                      cudaStream_t st) {
+  unsigned long long *mx = (unsigned long long *)(M->root->dev_words + 8);
   cudaMemsetAsync(mx, 0, 8, st);
   k_absmax<<<ctx->sms * 4, 256, 0, st>>>(x, count, mx);
   unsigned long long hm = 0;
@@ -1175,9 +1249,10 @@ static int absmax_exp(rb_ctx *ctx, const double *x, size_t count, int *e_out, cu
   return RB_OK;
 }
 
-static int build_sliced(rb_ctx *ctx, SlicedW &W, int kind, int nk, __nv_bfloat16 *Wj,
-                        cudaStream_t st) {
-  MixedState *M = ctx->mixed;
+// One sliced weight operand at the bucket's size. The grid exponent comes from the whole
+// operator (an upper bound for every truncation), so all buckets share one fixed-point grid.
+static int build_sliced(rb_ctx *ctx, MixedState *M, SlicedW &W, int kind, int nk,
+                        __nv_bfloat16 *Wj, cudaStream_t st) {
   const DevOps &o = ctx->ops;
   W.nk = nk;
   W.Npad = round_up(nk * M->nb, kTcBN);
@@ -1187,12 +1262,12 @@ static int build_sliced(rb_ctx *ctx, SlicedW &W, int kind, int nk, __nv_bfloat16
   W.d = (__nv_bfloat16 *)p;
   const size_t nm = o.n_max;
   if (kind == 0) {
-    if ((rc = absmax_exp(ctx, o.Dt, (size_t)o.q_c * nm * nm * nm, &W.wexp[0], st)) != RB_OK) return rc;
-    if (M->kb1 && (rc = absmax_exp(ctx, o.A, (size_t)o.q_a * nm * nm, &W.wexp[1], st)) != RB_OK) return rc;
+    if ((rc = absmax_exp(ctx, M, o.Dt, (size_t)o.q_c * nm * nm * nm, &W.wexp[0], st)) != RB_OK) return rc;
+    if (M->kb1 && (rc = absmax_exp(ctx, M, o.A, (size_t)o.q_a * nm * nm, &W.wexp[1], st)) != RB_OK) return rc;
   } else {
-    if ((rc = absmax_exp(ctx, o.Cs, (size_t)o.q_c * nm * nm * o.m, &W.wexp[0], st)) != RB_OK) return rc;
+    if ((rc = absmax_exp(ctx, M, o.Cs, (size_t)o.q_c * nm * nm * o.m, &W.wexp[0], st)) != RB_OK) return rc;
     W.wexp[0] += 1;  // the operand holds 2 Cs
-    if (M->kb1 && (rc = absmax_exp(ctx, o.As, (size_t)o.q_a * o.m * nm, &W.wexp[1], st)) != RB_OK) return rc;
+    if (M->kb1 && (rc = absmax_exp(ctx, M, o.As, (size_t)o.q_a * o.m * nm, &W.wexp[1], st)) != RB_OK) return rc;
   }
   BuildWParams bw{o, kind, M->nb, nk, M->Kpad0, M->Kpad, W.Npad, M->S0, M->S1, W.wexp[0], W.wexp[1], W.d, Wj};
   k_build_w<<<ctx->sms * 8, 256, 0, st>>>(bw);
@@ -1203,15 +1278,28 @@ static int build_sliced(rb_ctx *ctx, SlicedW &W, int kind, int nk, __nv_bfloat16
   return RB_OK;
 }
 
-// Build the operator layouts of the mixed path (once per operator set).
-static int mixed_layouts(rb_ctx *ctx, cudaStream_t st) {
-  if (ctx->mixed && ctx->mixed->Wj) return RB_OK;
+// The root state (nb = n_max) with the shared words; its layouts are built on first use.
+static int mixed_root(rb_ctx *ctx, cudaStream_t st) {
+  if (ctx->mixed) return RB_OK;
   if (!encode_fn()) return set_error(ctx, RB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   if (ctx->cc_major != 10) return set_error(ctx, RB_ERR_ARG, "tensor-core path needs an sm_10x GPU");
-  if (!ctx->mixed) ctx->mixed = new MixedState();
-  MixedState *M = ctx->mixed;
+  MixedState *M = new MixedState();
+  M->root = M;
+  M->nb = ctx->ops.n_max;
+  ctx->mixed = M;
+  void *p;
+  int rc;
+  if ((rc = ctx_alloc(ctx, &p, 64, "mixed words")) != RB_OK) return rc;
+  M->dev_words = (int *)p;
+  cudaMemsetAsync(M->dev_words, 0, 64, st);
+  if (cudaMallocHost(&M->h_words, 64) != cudaSuccess) return set_error(ctx, RB_ERR_OOM, "pinned words");
+  return RB_OK;
+}
+
+// Build the operator layouts of one bucket (once per operator set and bucket size).
+static int mixed_layouts(rb_ctx *ctx, MixedState *M, cudaStream_t st) {
+  if (M->Wj) return RB_OK;
   const DevOps &o = ctx->ops;
-  M->nb = o.n_max;
   M->Kpad0 = round_up(o.q_c * M->nb, 64);
   M->kb0 = M->Kpad0 / 64;
   // the linear affine term A(mu) u is evaluated in double-float on the CUDA cores, so the
@@ -1224,33 +1312,50 @@ static int mixed_layouts(rb_ctx *ctx, cudaStream_t st) {
   M->Smax = M->kb1 ? std::max(M->S0, M->S1) : M->S0;
   int rc;
   void *p;
-  if ((rc = ctx_alloc(ctx, &p, 64, "mixed words")) != RB_OK) return rc;
-  M->dev_words = (int *)p;
-  cudaMemsetAsync(M->dev_words, 0, 64, st);
-  if (cudaMallocHost(&M->h_words, 64) != cudaSuccess) return set_error(ctx, RB_ERR_OOM, "pinned words");
-  const size_t nm = o.n_max;
-  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_a * nm * nm, "A (double-float)")) != RB_OK) return rc;
+  const int nm = o.n_max, nb = M->nb;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_a * nb * nb, "A (double-float)")) != RB_OK) return rc;
   M->A2 = (float2 *)p;
-  k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.A, M->A2, (size_t)o.q_a * nm * nm);
+  k_split_trunc<<<ctx->sms * 4, 256, 0, st>>>(o.A, M->A2, o.q_a, nb, nm, nm, nb);
   if (o.m > 0 && o.B) {
-    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_a * o.m * nm, "As (double-float)")) != RB_OK) return rc;
+    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_a * o.m * nb, "As (double-float)")) != RB_OK) return rc;
     M->As2 = (float2 *)p;
-    k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.As, M->As2, (size_t)o.q_a * o.m * nm);
+    k_split_trunc<<<ctx->sms * 4, 256, 0, st>>>(o.As, M->As2, o.q_a, o.m, o.m, nm, nb);
     if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_b * o.m * o.m, "B (double-float)")) != RB_OK) return rc;
     M->B2 = (float2 *)p;
     k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.B, M->B2, (size_t)o.q_b * o.m * o.m);
   }
   if ((rc = ctx_alloc(ctx, &p, 2 * 2 * (size_t)M->Npad * M->Kpad0, "W (split BF16)")) != RB_OK) return rc;
   M->Wj = (__nv_bfloat16 *)p;
-  if ((rc = build_sliced(ctx, M->WR, 0, M->nb, M->Wj, st)) != RB_OK) return rc;
-  if (o.m > 0 && o.B && (rc = build_sliced(ctx, M->WP, 1, o.m, nullptr, st)) != RB_OK) return rc;
+  if ((rc = build_sliced(ctx, M, M->WR, 0, M->nb, M->Wj, st)) != RB_OK) return rc;
+  if (o.m > 0 && o.B && (rc = build_sliced(ctx, M, M->WP, 1, o.m, nullptr, st)) != RB_OK) return rc;
   if (!make_map(&M->tmWj, M->Wj, 2 * (uint64_t)M->Npad, M->Kpad0, kTcBN))
     return set_error(ctx, RB_ERR_CUDA, "tensor map encode (Wj)");
+  M->root->epoch += 1;
   return RB_OK;
 }
 
-static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
-  MixedState *M = ctx->mixed;
+// Bucket size of a query of size n: n rounded up to 8 (n <= 64), 16 (n <= 128) or 32, at most
+// n_max. The bucket's layouts are built on its first use.
+static int bucket_size(int n, int n_max) {
+  const int g = n <= 64 ? 8 : (n <= 128 ? 16 : 32);
+  return std::min((n + g - 1) / g * g, n_max);
+}
+
+static MixedState *bucket(rb_ctx *ctx, int nb) {
+  MixedState *R = ctx->mixed;
+  if (nb >= R->nb) return R;
+  auto it = R->buckets.find(nb);
+  if (it != R->buckets.end()) return it->second;
+  MixedState *M = new MixedState();
+  M->root = R;
+  M->nb = nb;
+  M->dev_words = R->dev_words;
+  M->h_words = R->h_words;
+  R->buckets[nb] = M;
+  return M;
+}
+
+static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   const int b_pad = round_up(std::max(nq, 1), 128);
   if (b_pad <= M->bcap) return RB_OK;
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
@@ -1302,18 +1407,17 @@ static int mixed_batch_scratch(rb_ctx *ctx, int nq) {
       !make_map(&M->tmXd, M->Xd, (uint64_t)M->Smax * b_pad, M->Kpad, 128))
     return set_error(ctx, RB_ERR_CUDA, "tensor map encode (X)");
   M->bcap = b_pad;
-  M->epoch += 1;
+  M->root->epoch += 1;
   return RB_OK;
 }
 
-static int launch_build_x(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
-                          const int *d_n, const double *d_u, const rb_query_info *d_info,
-                          int mode, int digits, double *out, int nout, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
+static int launch_build_x(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
+                          const rb_query_info *d_info, int mode, int digits, double *out, int nout,
+                          cudaStream_t st) {
   BuildXParams bx{};
   bx.o = ctx->ops;
-  bx.mu = d_mu;
-  bx.theta = d_theta;
+  bx.mu = nullptr;
+  bx.theta = M->Th;
   bx.nsz = d_n;
   bx.nq = nq;
   bx.nb = M->nb;
@@ -1334,15 +1438,14 @@ static int launch_build_x(rb_ctx *ctx, const double *d_mu, const double *d_theta
   bx.out = out;
   bx.nout = nout;
   const int mk = prof_begin(ctx, RB_K_BUILD_X, st);
-  k_build_x<<<std::min(nq, ctx->sms * 8), kThreads, 0, st>>>(bx);
+  k_build_x<<<std::max(1, std::min(nq, ctx->sms * 8)), kThreads, 0, st>>>(bx);
   prof_end(ctx, mk, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_build_x");
   return RB_OK;
 }
 
-static TcGemmParams gemm_params(rb_ctx *ctx, int nq) {
-  MixedState *M = ctx->mixed;
+static TcGemmParams gemm_params(MixedState *M, int nq) {
   TcGemmParams g{};
   g.m_tiles = round_up(nq, 128) / 128;
   g.S[0] = M->S0;
@@ -1352,14 +1455,13 @@ static TcGemmParams gemm_params(rb_ctx *ctx, int nq) {
   g.nj = M->nb;
   g.xexp = M->xexp;
   g.ufT = M->ufT;
-  g.err = M->dev_words + 1;
+  g.err = M->root->dev_words + 1;
   return g;
 }
 
 // theta rows, f(mu) and A(mu) of the queries that start (active, iteration count 0).
-static int launch_prep(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
-                       const rb_query_info *info, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
+static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const double *d_theta,
+                       int nq, const rb_query_info *info, cudaStream_t st) {
   const DevOps &o = ctx->ops;
   PrepParams pp{};
   pp.o = o;
@@ -1377,7 +1479,7 @@ static int launch_prep(rb_ctx *ctx, const double *d_mu, const double *d_theta, i
   k_prep_theta<<<std::max(1, std::min((nq + 7) / 8, ctx->sms * 16)), 256, 0, st>>>(pp);
   const size_t nn = (size_t)M->nb * M->nb;
   dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024),
-            (unsigned)std::min((nq + kAsmQ - 1) / kAsmQ, 65535));
+            (unsigned)std::max(1, std::min((nq + kAsmQ - 1) / kAsmQ, 65535)));
   k_assemble_a<<<grid, 256, sizeof(float2) * kAsmQ * o.q_a, st>>>(pp);
   prof_end(ctx, mk, st);
   cudaError_t e = cudaGetLastError();
@@ -1386,12 +1488,11 @@ static int launch_prep(rb_ctx *ctx, const double *d_mu, const double *d_theta, i
 }
 
 // One Newton step's contraction work for the whole batch: X build + both GEMMs.
-static int mixed_contract(rb_ctx *ctx, int nq, const int *d_n, const double *d_u,
+static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
                           const rb_query_info *d_info, bool exact, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
-  int rc = launch_build_x(ctx, nullptr, M->Th, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st);
+  int rc = launch_build_x(ctx, M, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st);
   if (rc != RB_OK) return rc;
-  TcGemmParams g = gemm_params(ctx, nq);
+  TcGemmParams g = gemm_params(M, nq);
   g.n_tiles = M->Npad / kTcBN;
   g.kb[0] = M->kb0;
   g.kb[1] = 0;
@@ -1418,11 +1519,9 @@ static int mixed_contract(rb_ctx *ctx, int nq, const int *d_n, const double *d_u
   return RB_OK;
 }
 
-
 // Newton step of the batch: k_newton_system assembles [J | -R] per query, then one warp
-// (n_max <= 80) or one CTA (blocked elimination) per query solves it.
-static int launch_lu(rb_ctx *ctx, LuParams &lp, int nq, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
+// (nb <= 80) or one CTA (blocked elimination) per query solves it.
+static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStream_t st) {
   lp.Amu = M->Amu;
   lp.Fm = M->Fm;
   lp.Jaug = M->Jaug;
@@ -1501,13 +1600,12 @@ static int check_words(rb_ctx *ctx, cudaStream_t st, const char *what) {
   return RB_OK;
 }
 
-static int mixed_pressure(rb_ctx *ctx, int nq, const int *d_n, const double *d_u, double *d_p,
-                          rb_query_info *info, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
+static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
+                          double *d_p, rb_query_info *info, cudaStream_t st) {
   const DevOps &o = ctx->ops;
-  int rc = launch_build_x(ctx, nullptr, M->Th, nq, d_n, d_u, info, 1, 1, M->Rp, o.m, st);
+  int rc = launch_build_x(ctx, M, nq, d_n, d_u, info, 1, 1, M->Rp, o.m, st);
   if (rc != RB_OK) return rc;
-  TcGemmParams g = gemm_params(ctx, nq);
+  TcGemmParams g = gemm_params(M, nq);
   g.kb[0] = M->kb0;
   g.kb[1] = M->kb1;
   g.n_tiles = M->WP.Npad / kTcBN;
@@ -1521,11 +1619,11 @@ static int mixed_pressure(rb_ctx *ctx, int nq, const int *d_n, const double *d_u
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (pressure)");
   mk = prof_begin(ctx, RB_K_PRESSURE, st);
-  AsuParams ap{o, M->Th, d_n, nq, d_u, info, M->As2, M->Asu};
-  const size_t asmem = sizeof(float2) * (size_t)(kAsQ + kAsR) * odd_ld(o.n_max);
+  AsuParams ap{o, M->Th, d_n, nq, M->nb, d_u, info, M->As2, M->Asu};
+  const size_t asmem = sizeof(float2) * (size_t)(kAsQ + kAsR) * odd_ld(M->nb);
   e = cudaFuncSetAttribute(k_as_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_as_u attr");
-  dim3 agrid((unsigned)((o.m + kAsR - 1) / kAsR), (unsigned)std::min((nq + kAsQ - 1) / kAsQ, 65535));
+  dim3 agrid((unsigned)((o.m + kAsR - 1) / kAsR), (unsigned)std::max(1, std::min((nq + kAsQ - 1) / kAsQ, 65535)));
   k_as_u<<<agrid, 256, asmem, st>>>(ap);
   PresSolveParams pp{o, M->Th, nq, M->B2, M->Rp, M->Asu, d_p, info};
   const size_t per_warp = PresSmem(o).total;
@@ -1547,8 +1645,10 @@ static int mixed_pressure(rb_ctx *ctx, int nq, const int *d_n, const double *d_u
   return RB_OK;
 }
 
-// One batch solve, split into the pieces that the stream path runs with a host check per
-// iteration and that the graph path captures once.
+// ---- one batch solve ----------------------------------------------------------------------
+// The batch is split into size buckets (contiguous ranges of a bucket-sorted copy, or the
+// caller's buffers themselves when every query uses the n_max layouts); the pieces below are run
+// by the stream path with a host check per iteration and captured once by the graph path.
 struct SolveArgs {
   const double *mu, *theta;
   int nq;
@@ -1557,8 +1657,12 @@ struct SolveArgs {
   rb_query_info *info;
 };
 
-static LuParams solve_lu_params(rb_ctx *ctx, const SolveArgs &a) {
-  MixedState *M = ctx->mixed;
+struct Part {
+  MixedState *M;
+  SolveArgs a;
+};
+
+static LuParams solve_lu_params(rb_ctx *ctx, MixedState *M, const SolveArgs &a) {
   LuParams lp{};
   lp.o = ctx->ops;
   lp.nsz = a.n;
@@ -1572,35 +1676,50 @@ static LuParams solve_lu_params(rb_ctx *ctx, const SolveArgs &a) {
   lp.Rc = M->Rc;
   lp.u = a.u;
   lp.info = a.info;
-  lp.active = M->dev_words;
+  lp.active = M->root->dev_words;  // one active count over all buckets
   lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
   return lp;
 }
 
 // words[0] active count of the last iteration, [1] error word, [2] iterations done
-static int solve_prologue(rb_ctx *ctx, const SolveArgs &a, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
-  const int mk = prof_begin(ctx, RB_K_INIT, st);
-  k_mixed_init<<<std::min(a.nq, ctx->sms * 8), 128, 0, st>>>(a.nq, ctx->ops.n_max, a.n, a.u, a.info);
-  prof_end(ctx, mk, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
-  int rc = launch_prep(ctx, a.mu, a.theta, a.nq, a.info, st);
-  if (rc != RB_OK) return rc;
-  e = cudaMemsetAsync(M->dev_words, 0, 16, st);
-  return e == cudaSuccess ? RB_OK : cuda_fail(ctx, e, "words");
+static int solve_prologue(rb_ctx *ctx, const std::vector<Part> &parts, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ctx->mixed->dev_words, 0, 16, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
+  for (const Part &pt : parts) {
+    const SolveArgs &a = pt.a;
+    const int mk = prof_begin(ctx, RB_K_INIT, st);
+    k_mixed_init<<<std::max(1, std::min(a.nq, ctx->sms * 8)), 128, 0, st>>>(a.nq, ctx->ops.n_max, a.n, a.u, a.info);
+    prof_end(ctx, mk, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
+    const int rc = launch_prep(ctx, pt.M, a.mu, a.theta, a.nq, a.info, st);
+    if (rc != RB_OK) return rc;
+  }
+  return RB_OK;
 }
 
-// Newton iteration `rung` (0: u = 0, 1: low-precision residual, 2: FP64-accurate residual;
-// the kernels pick each query's rung from its own iteration count).
-static int solve_iteration(rb_ctx *ctx, const SolveArgs &a, int rung, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
-  cudaError_t e = cudaMemsetAsync(M->dev_words, 0, 4, st);
+// Newton iteration `rung` of every bucket (0: u = 0, 1: low-precision residual, 2: FP64-accurate
+// residual; the kernels pick each query's rung from its own iteration count).
+static int solve_iteration(rb_ctx *ctx, const std::vector<Part> &parts, int rung, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ctx->mixed->dev_words, 0, 4, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
   int rc;
-  if (rung >= 1 && (rc = mixed_contract(ctx, a.nq, a.n, a.u, a.info, rung >= 2, st)) != RB_OK) return rc;
-  LuParams lp = solve_lu_params(ctx, a);
-  return launch_lu(ctx, lp, a.nq, st);
+  for (const Part &pt : parts) {
+    if (rung >= 1 &&
+        (rc = mixed_contract(ctx, pt.M, pt.a.nq, pt.a.n, pt.a.u, pt.a.info, rung >= 2, st)) != RB_OK)
+      return rc;
+    LuParams lp = solve_lu_params(ctx, pt.M, pt.a);
+    if ((rc = launch_lu(ctx, pt.M, lp, pt.a.nq, st)) != RB_OK) return rc;
+  }
+  return RB_OK;
+}
+
+static int solve_pressure(rb_ctx *ctx, const std::vector<Part> &parts, cudaStream_t st) {
+  for (const Part &pt : parts) {
+    const int rc = mixed_pressure(ctx, pt.M, pt.a.nq, pt.a.n, pt.a.u, pt.a.p, pt.a.info, st);
+    if (rc != RB_OK) return rc;
+  }
+  return RB_OK;
 }
 
 // words[2] += 1; keep looping while queries are active and the iteration cap is not reached
@@ -1609,9 +1728,35 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, int *words, int max_it
   cudaGraphSetConditional(h, (words[0] > 0 && it < max_iter) ? 1u : 0u);
 }
 
-static int build_solve_graph(rb_ctx *ctx, const SolveArgs &a) {
+// The whole solve: gather (bucketed batches), prologue, rungs 0 and 1, a while-loop node over
+// FP64-residual iterations, pressure, scatter.
+struct SolvePlan {
+  SolveArgs caller;                // the caller's buffers
+  std::vector<Part> parts;
+  bool gathered = false;           // parts work on the bucket-sorted copy
+  bool pres = false;
+};
+
+static int plan_edges(rb_ctx *ctx, const SolvePlan &pl, bool first, cudaStream_t st) {
+  MixedState *R = ctx->mixed;
+  const DevOps &o = ctx->ops;
+  const SolveArgs &c = pl.caller;
+  if (first) {
+    if (!pl.gathered) return RB_OK;
+    k_gather<<<std::max(1, std::min((c.nq + 255) / 256, ctx->sms * 4)), 256, 0, st>>>(
+        c.nq, R->perm, c.theta ? nullptr : c.mu, c.theta, o.n_theta, c.n, R->mu_g, R->theta_g, R->n_g);
+  } else {
+    if (!pl.gathered) return RB_OK;
+    k_scatter<<<std::max(1, std::min((c.nq + 7) / 8, ctx->sms * 8)), 256, 0, st>>>(
+        c.nq, R->perm, o.n_max, std::max(o.m, 1), R->u_g, pl.pres ? R->p_g : nullptr, R->info_g,
+        c.u, pl.pres ? c.p : nullptr, c.info);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RB_OK : cuda_fail(ctx, e, first ? "k_gather" : "k_scatter");
+}
+
+static int build_solve_graph(rb_ctx *ctx, const SolvePlan &pl, const std::vector<int> &key_parts) {
   MixedState *M = ctx->mixed;
-  const bool pres = a.p && ctx->ops.m > 0 && ctx->ops.B;
   for (cudaStream_t &c : M->cap)
     if (!c && cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess)
       return set_error(ctx, RB_ERR_CUDA, "capture stream");
@@ -1632,9 +1777,10 @@ static int build_solve_graph(rb_ctx *ctx, const SolveArgs &a) {
   int rc = RB_OK;
   bool body_open = false;
   do {
-    if ((rc = solve_prologue(ctx, a, cs)) != RB_OK) break;
+    if ((rc = plan_edges(ctx, pl, true, cs)) != RB_OK) break;
+    if ((rc = solve_prologue(ctx, pl.parts, cs)) != RB_OK) break;
     for (int r = 0; r < 2 && rc == RB_OK; ++r) {
-      if ((rc = solve_iteration(ctx, a, r, cs)) != RB_OK) break;
+      if ((rc = solve_iteration(ctx, pl.parts, r, cs)) != RB_OK) break;
       k_loop_cond<<<1, 1, 0, cs>>>(h, M->dev_words, ctx->cfg.max_iter);
     }
     if (rc != RB_OK) break;
@@ -1654,12 +1800,13 @@ static int build_solve_graph(rb_ctx *ctx, const SolveArgs &a) {
     if ((e = cudaStreamBeginCaptureToGraph(cb, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed)) != cudaSuccess) break;
     body_open = true;
-    if ((rc = solve_iteration(ctx, a, 2, cb)) != RB_OK) break;
+    if ((rc = solve_iteration(ctx, pl.parts, 2, cb)) != RB_OK) break;
     k_loop_cond<<<1, 1, 0, cb>>>(h, M->dev_words, ctx->cfg.max_iter);
     cudaGraph_t bg;
     body_open = false;
     if ((e = cudaStreamEndCapture(cb, &bg)) != cudaSuccess) break;
-    if (pres && (rc = mixed_pressure(ctx, a.nq, a.n, a.u, a.p, a.info, cs)) != RB_OK) break;
+    if (pl.pres && (rc = solve_pressure(ctx, pl.parts, cs)) != RB_OK) break;
+    if ((rc = plan_edges(ctx, pl, false, cs)) != RB_OK) break;
   } while (false);
   if (body_open) {
     cudaGraph_t bg;
@@ -1675,49 +1822,147 @@ static int build_solve_graph(rb_ctx *ctx, const SolveArgs &a) {
   if (rc != RB_OK) return rc;
   if (e != cudaSuccess) return cuda_fail(ctx, e, "solve graph");
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "solve graph capture");
-  M->gkey = {a.mu, a.theta, a.p, a.n, a.u, a.info, a.nq, M->epoch};
+  const SolveArgs &c = pl.caller;
+  M->gkey.mu = c.mu;
+  M->gkey.theta = c.theta;
+  M->gkey.p = c.p;
+  M->gkey.n = c.n;
+  M->gkey.u = c.u;
+  M->gkey.info = c.info;
+  M->gkey.nq = c.nq;
+  M->gkey.epoch = M->epoch;
+  M->gkey.parts = key_parts;
+  return RB_OK;
+}
+
+// Gather scratch of a bucketed batch (grow-only).
+static int gather_scratch(rb_ctx *ctx, int nq, bool theta) {
+  MixedState *R = ctx->mixed;
+  const DevOps &o = ctx->ops;
+  const int need = std::max(nq, 1);
+  if (need <= R->gcap && (!theta || R->theta_g)) return RB_OK;
+  for (void *q : {(void *)R->perm, (void *)R->n_g, (void *)R->mu_g, (void *)R->theta_g,
+                  (void *)R->u_g, (void *)R->p_g, (void *)R->info_g})
+    ctx_free(ctx, q);
+  R->perm = R->n_g = nullptr;
+  R->mu_g = R->theta_g = R->u_g = R->p_g = nullptr;
+  R->info_g = nullptr;
+  R->gcap = 0;
+  const int cap = std::max(need, R->gcap);
+  void *p;
+  int rc;
+  if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)cap, "bucket order")) != RB_OK) return rc;
+  R->perm = (int *)p;
+  if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)cap, "bucket sizes")) != RB_OK) return rc;
+  R->n_g = (int *)p;
+  if ((rc = ctx_alloc(ctx, &p, 16 * (size_t)cap, "bucket mu")) != RB_OK) return rc;
+  R->mu_g = (double *)p;
+  if (theta) {
+    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)cap * o.n_theta, "bucket theta")) != RB_OK) return rc;
+    R->theta_g = (double *)p;
+  }
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)cap * o.n_max, "bucket u")) != RB_OK) return rc;
+  R->u_g = (double *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)cap * std::max(o.m, 1), "bucket p")) != RB_OK) return rc;
+  R->p_g = (double *)p;
+  if ((rc = ctx_alloc(ctx, &p, sizeof(rb_query_info) * (size_t)cap, "bucket info")) != RB_OK) return rc;
+  R->info_g = (rb_query_info *)p;
+  R->gcap = cap;
+  R->epoch += 1;
   return RB_OK;
 }
 
 int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
-                double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st) {
-  int rc = mixed_layouts(ctx, st);
+                const int *h_n, double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st) {
+  int rc = mixed_root(ctx, st);
   if (rc != RB_OK) return rc;
-  if ((rc = mixed_batch_scratch(ctx, nq)) != RB_OK) return rc;
-  MixedState *M = ctx->mixed;
+  MixedState *R = ctx->mixed;
+  const DevOps &o = ctx->ops;
   rb_query_info *info = d_info ? d_info : own_info(ctx, nq);
   if (!info) return set_error(ctx, RB_ERR_OOM, "info scratch");
-  const SolveArgs a{d_mu, d_theta, nq, d_n, d_u, d_p, info};
-  const bool pres = d_p && ctx->ops.m > 0 && ctx->ops.B;
-  if (ctx->cfg.use_graph && !ctx->prof) {
-    const auto &k = M->gkey;
-    if (!M->gexec || k.mu != d_mu || k.theta != d_theta || k.p != d_p || k.n != d_n || k.u != d_u ||
-        k.info != info || k.nq != nq || k.epoch != M->epoch) {
-      if ((rc = build_solve_graph(ctx, a)) != RB_OK) return rc;
+  SolvePlan pl;
+  pl.caller = {d_mu, d_theta, nq, d_n, d_u, d_p, info};
+  pl.pres = d_p && o.m > 0 && o.B;
+  // size buckets from the host copy of the sizes
+  std::vector<int> hn;
+  if (d_n) {
+    hn.resize(nq);
+    if (h_n) {
+      std::copy(h_n, h_n + nq, hn.begin());
+    } else {
+      cudaError_t e = cudaMemcpyAsync(hn.data(), d_n, 4 * (size_t)nq, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "query sizes");
     }
-    const cudaError_t e = cudaGraphLaunch(M->gexec, st);
+  }
+  std::map<int, std::vector<int>> groups;  // bucket size -> query indices
+  for (int i = 0; i < nq && d_n; ++i) {
+    const int n = hn[i];
+    groups[(n >= 1 && n <= o.n_max) ? bucket_size(n, o.n_max) : o.n_max].push_back(i);
+  }
+  std::vector<int> key_parts;
+  if (groups.size() <= 1 && (groups.empty() || groups.begin()->first == o.n_max)) {
+    if ((rc = mixed_layouts(ctx, R, st)) != RB_OK) return rc;
+    if ((rc = mixed_batch_scratch(ctx, R, nq)) != RB_OK) return rc;
+    pl.parts.push_back({R, pl.caller});
+    key_parts = {R->nb, 0, nq};
+  } else {
+    if ((rc = gather_scratch(ctx, nq, d_theta != nullptr)) != RB_OK) return rc;
+    std::vector<int> perm;
+    perm.reserve(nq);
+    std::vector<std::pair<MixedState *, std::pair<int, int>>> ranges;
+    for (auto &kv : groups) {
+      MixedState *M = bucket(ctx, kv.first);
+      if ((rc = mixed_layouts(ctx, M, st)) != RB_OK) return rc;
+      if ((rc = mixed_batch_scratch(ctx, M, (int)kv.second.size())) != RB_OK) return rc;
+      ranges.push_back({M, {(int)perm.size(), (int)kv.second.size()}});
+      perm.insert(perm.end(), kv.second.begin(), kv.second.end());
+    }
+    cudaError_t e = cudaMemcpyAsync(R->perm, perm.data(), 4 * (size_t)nq, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vector goes out of scope
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bucket order");
+    const int mm = std::max(o.m, 1);
+    for (auto &r : ranges) {
+      const int off = r.second.first, cnt = r.second.second;
+      SolveArgs a{d_theta ? nullptr : R->mu_g + 2 * (size_t)off,
+                  d_theta ? R->theta_g + (size_t)off * o.n_theta : nullptr, cnt, R->n_g + off,
+                  R->u_g + (size_t)off * o.n_max, pl.pres ? R->p_g + (size_t)off * mm : nullptr,
+                  R->info_g + off};
+      pl.parts.push_back({r.first, a});
+      key_parts.insert(key_parts.end(), {r.first->nb, off, cnt});
+    }
+    pl.gathered = true;
+  }
+  if (ctx->cfg.use_graph && !ctx->prof) {
+    const auto &k = R->gkey;
+    if (!R->gexec || k.mu != d_mu || k.theta != d_theta || k.p != d_p || k.n != d_n || k.u != d_u ||
+        k.info != info || k.nq != nq || k.epoch != R->epoch || k.parts != key_parts) {
+      if ((rc = build_solve_graph(ctx, pl, key_parts)) != RB_OK) return rc;
+    }
+    const cudaError_t e = cudaGraphLaunch(R->gexec, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve graph launch");
     return check_words(ctx, st, "mixed solve");
   }
-  if ((rc = solve_prologue(ctx, a, st)) != RB_OK) return rc;
+  if ((rc = plan_edges(ctx, pl, true, st)) != RB_OK) return rc;
+  if ((rc = solve_prologue(ctx, pl.parts, st)) != RB_OK) return rc;
   for (int it = 0; it < ctx->cfg.max_iter; ++it) {
-    if ((rc = solve_iteration(ctx, a, std::min(it, 2), st)) != RB_OK) return rc;
+    if ((rc = solve_iteration(ctx, pl.parts, std::min(it, 2), st)) != RB_OK) return rc;
     if ((rc = check_words(ctx, st, "mixed Newton step")) != RB_OK) return rc;
-    if (M->h_words[0] == 0) break;
+    if (R->h_words[0] == 0) break;
   }
-  if (pres) {
-    if ((rc = mixed_pressure(ctx, nq, d_n, d_u, d_p, info, st)) != RB_OK) return rc;
-    if ((rc = check_words(ctx, st, "pressure recovery")) != RB_OK) return rc;
-  }
+  if (pl.pres && (rc = solve_pressure(ctx, pl.parts, st)) != RB_OK) return rc;
+  if ((rc = plan_edges(ctx, pl, false, st)) != RB_OK) return rc;
+  if ((rc = check_words(ctx, st, "mixed solve")) != RB_OK) return rc;
   if (ctx->prof) prof_collect(ctx);
   return RB_OK;
 }
 
-// ---- pieces used by the continuous-batching server ----------------------------------------
+// ---- pieces used by the continuous-batching server (the n_max layouts) --------------------
 int mixed_prepare(rb_ctx *ctx, int capacity, cudaStream_t st) {
-  int rc = mixed_layouts(ctx, st);
+  int rc = mixed_root(ctx, st);
   if (rc != RB_OK) return rc;
-  if ((rc = mixed_batch_scratch(ctx, capacity)) != RB_OK) return rc;
+  if ((rc = mixed_layouts(ctx, ctx->mixed, st)) != RB_OK) return rc;
+  if ((rc = mixed_batch_scratch(ctx, ctx->mixed, capacity)) != RB_OK) return rc;
   return own_info(ctx, 1) ? RB_OK : set_error(ctx, RB_ERR_OOM, "info scratch");
 }
 
@@ -1739,25 +1984,12 @@ int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, dou
   MixedState *M = ctx->mixed;
   int rc;
   cudaMemsetAsync(M->dev_words, 0, 4, st);
-  if ((rc = launch_prep(ctx, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
-  if (need_jacobian && (rc = mixed_contract(ctx, nq, d_n, d_u, info, need_exact, st)) != RB_OK)
+  if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
+  if (need_jacobian && (rc = mixed_contract(ctx, M, nq, d_n, d_u, info, need_exact, st)) != RB_OK)
     return rc;
-  LuParams lp{};
-  lp.o = ctx->ops;
-  lp.nsz = d_n;
-  lp.nq = nq;
-  lp.nb = M->nb;
-  lp.ldj = M->Npad;
-  lp.max_iter = ctx->cfg.max_iter;
-  lp.tol_upd = ctx->cfg.tol_update;
-  lp.tol_res = ctx->cfg.tol_res;
-  lp.Jc = M->Jc;
-  lp.Rc = M->Rc;
-  lp.u = d_u;
-  lp.info = info;
-  lp.active = M->dev_words;
-  lp.rmode = kResLadder;
-  return launch_lu(ctx, lp, nq, st);
+  const SolveArgs a{d_mu, nullptr, nq, d_n, d_u, nullptr, info};
+  LuParams lp = solve_lu_params(ctx, M, a);
+  return launch_lu(ctx, M, lp, nq, st);
 }
 
 // Pressure for every slot whose status is RB_Q_OK.
@@ -1765,7 +1997,7 @@ int mixed_pressure_ok(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, c
                       double *d_p, rb_query_info *info, cudaStream_t st) {
   if (!(ctx->ops.m > 0 && ctx->ops.B && d_p)) return RB_OK;
   (void)d_mu;
-  return mixed_pressure(ctx, nq, d_n, d_u, d_p, info, st);
+  return mixed_pressure(ctx, ctx->mixed, nq, d_n, d_u, d_p, info, st);
 }
 
 int mixed_error_word(rb_ctx *ctx, cudaStream_t st) {
@@ -1775,10 +2007,11 @@ int mixed_error_word(rb_ctx *ctx, cudaStream_t st) {
 int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u, int precision,
                double *d_R, double *d_J, cudaStream_t st) {
   if (precision != RB_PREC_MIXED) return set_error(ctx, RB_ERR_ARG, "unknown precision %d", precision);
-  int rc = mixed_layouts(ctx, st);
+  int rc = mixed_root(ctx, st);
   if (rc != RB_OK) return rc;
-  if ((rc = mixed_batch_scratch(ctx, nq)) != RB_OK) return rc;
   MixedState *M = ctx->mixed;
+  if ((rc = mixed_layouts(ctx, M, st)) != RB_OK) return rc;
+  if ((rc = mixed_batch_scratch(ctx, M, nq)) != RB_OK) return rc;
   const DevOps &o = ctx->ops;
   // the layouts use n_max-length rows: widen u and pass sizes
   if ((rc = ctx->jscratch.reserve(ctx, 8 * (size_t)nq * o.n_max + 4 * (size_t)nq + 256, "eval staging")) != RB_OK)
@@ -1795,26 +2028,18 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
   cudaMemsetAsync(M->dev_words, 0, 8, st);
-  if ((rc = launch_prep(ctx, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
-  if ((rc = mixed_contract(ctx, nq, nsz, uw, info, true, st)) != RB_OK) return rc;
-  LuParams lp{};
+  if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
+  if ((rc = mixed_contract(ctx, M, nq, nsz, uw, info, true, st)) != RB_OK) return rc;
+  const SolveArgs a{d_mu, nullptr, nq, nsz, uw, nullptr, info};
+  LuParams lp = solve_lu_params(ctx, M, a);
   lp.rmode = kResExact;
-  lp.o = o;
-  lp.nsz = nsz;
-  lp.nq = nq;
-  lp.nb = M->nb;
-  lp.ldj = M->Npad;
-  lp.max_iter = ctx->cfg.max_iter;
-  lp.Jc = M->Jc;
-  lp.Rc = M->Rc;
-  lp.u = uw;
-  lp.info = info;
-  lp.active = M->dev_words;
   lp.eval_only = 1;
   lp.R_out = d_R;
   lp.J_out = d_J;
-  if ((rc = launch_lu(ctx, lp, nq, st)) != RB_OK) return rc;
-  return check_words(ctx, st, "rb_eval (mixed)");
+  if ((rc = launch_lu(ctx, M, lp, nq, st)) != RB_OK) return rc;
+  rc = check_words(ctx, st, "rb_eval (mixed)");
+  cudaStreamSynchronize(st);  // hn is a host vector read by the copy above
+  return rc;
 }
 
 }  // namespace rb

@@ -205,7 +205,7 @@ int solve_pressure(rb_ctx *ctx, const double *d_mu, const double *d_theta, int n
 
 int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
                       const int *d_n, double *d_u, double *d_p, rb_query_info *d_info,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int *h_n) {
   if (!ctx->loaded) return set_error(ctx, RB_ERR_STATE, "no operators loaded");
   if (serve_running(ctx))
     return set_error(ctx, RB_ERR_STATE, "the server owns this context's batch state; stop it first");
@@ -218,7 +218,7 @@ int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, in
     info = (rb_query_info *)ctx->info_scratch.ptr;
   }
   if (ctx->cfg.precision == RB_PREC_MIXED)  // pressure recovery included
-    return solve_mixed(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
+    return solve_mixed(ctx, d_mu, d_theta, nq, d_n, h_n, d_u, d_p, info, st);
   int rc = solve_fp64(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
   if (rc != RB_OK) return rc;
   return solve_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
@@ -253,7 +253,7 @@ int stage_solve(rb_ctx *ctx, const double *mu, const double *theta, int nq, cons
   if (e == cudaSuccess && n) e = cudaMemcpyAsync(d_n, n, sizeof(int) * (size_t)nq, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rb_solve upload");
   rc = solve_device_impl(ctx, theta ? nullptr : d_in, theta ? d_in : nullptr, nq, d_n, d_u, d_p,
-                         d_info, st);
+                         d_info, st, n);
   if (rc != RB_OK) return rc;
   e = cudaMemcpyAsync(u_out, d_u, sizeof(double) * (size_t)nq * o.n_max, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && m) e = cudaMemcpyAsync(p_out, d_p, sizeof(double) * (size_t)nq * m, cudaMemcpyDeviceToHost, st);

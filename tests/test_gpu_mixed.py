@@ -190,3 +190,23 @@ def test_graph_and_stream_paths_agree(rb):
         _, _, info = ctx.rb_solve(q.mu[:50])
     assert np.all(info["iters"] <= 3)
     assert set(np.unique(info["status"])) <= {rb.RB_Q_OK, rb.RB_Q_NOT_CONVERGED}
+
+
+def test_uneven_sizes_bucketed(rb):
+    """Queries of sizes 20 / 40 / 80 / 120 from one n_max = 120 set run in size buckets (warp
+    elimination up to 80, blocked above) inside one solve, in any order, and match the oracle."""
+    wl = synth.WORKLOADS["uneven_n120"]
+    ops = synth.make_operators(wl, n_max=120, q_a=4, q_c=4)
+    q = synth.make_queries(wl, batch=48, n_max=120)
+    rng = np.random.default_rng(5)
+    sizes = rng.choice(np.array([20, 40, 80, 120, 7, 97], dtype=np.int32), size=48)
+    o = oracle.Oracle.from_set(ops)
+    u_ref, _, _ = o.solve(q.mu, n=sizes, threads=8)
+    for g in (1, 0):
+        with rb.Context(rb.RB_PREC_MIXED, use_graph=g) as ctx:
+            ctx.load_set(ops)
+            u, _, info = ctx.rb_solve(q.mu, n=sizes)
+        assert np.all(info["status"] == 0)
+        assert rel(u, u_ref).max() <= TOL_MIXED
+        for b, n in enumerate(sizes):
+            assert np.all(u[b, n:] == 0.0)
