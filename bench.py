@@ -323,6 +323,7 @@ def main():
     }
     line["roofline"] = roof
     line["rooflines"] = roofs
+    line["autotune"] = ctx.rb_tuning()
     if rank == 0 and not args.no_plain and prec != 0:
         line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, args)
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]

@@ -221,6 +221,17 @@ enum {
 int rb_profile(rb_ctx *ctx, int enable);
 int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launches);
 
+/* ---- autotuner (no counterpart in the paper) -----------------------------------------------
+ * With cfg.autotune, the first mixed-precision solve of each size bucket and batch-size class
+ * (ceil(log2(batch))) times the candidate launch variants on the bucket's shapes and keeps the
+ * fastest: the elimination (1 = one warp per query, for n <= 80; 2 = blocked, 32-column panels;
+ * 3 = blocked, 16-column panels) and the TMA ring depths of the Jacobian and sliced GEMMs.
+ * rb_tuning returns the number of tuned buckets; for bucket i < that number it fills
+ * out6 = {bucket size, batch class, elimination, Jacobian GEMM stages, sliced GEMM stages, 0}
+ * and ms3 = the best times (ms) of the elimination, Jacobian GEMM and sliced GEMM. Either
+ * pointer may be NULL. */
+int rb_tuning(rb_ctx *ctx, int i, int *out6, float *ms3);
+
 /* ---- serving: continuous batching at Newton-iteration granularity --------------------
  * A host thread admits queries into device slots while memory allows and advances every
  * active slot by one Newton iteration per step; converged queries leave and waiting ones

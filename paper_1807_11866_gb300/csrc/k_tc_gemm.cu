@@ -354,12 +354,20 @@ static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
   return cudaGetLastError();
 }
 
+// stages: depth of the TMA ring (0: default). Plain: 4 or 6; sliced with a 64-column u window:
+// 3, 4 or 5; sliced with a 128-column window: 3 (the shared-memory limit).
 cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &tmW,
-                           const TcGemmParams &p, int sms, cudaStream_t st) {
+                           const TcGemmParams &p, int sms, cudaStream_t st, int stages) {
   const int tiles = p.m_tiles * p.n_tiles;
   const int grid = tiles < sms ? tiles : sms;
-  if (mode == kPlain) return launch_impl<kPlain, 4, 0>(tmX, tmW, p, grid, st);
-  if (p.nj <= 64) return launch_impl<kSliced, 4, 64>(tmX, tmW, p, grid, st);
+  if (mode == kPlain)
+    return stages == 6 ? launch_impl<kPlain, 6, 0>(tmX, tmW, p, grid, st)
+                       : launch_impl<kPlain, 4, 0>(tmX, tmW, p, grid, st);
+  if (p.nj <= 64) {
+    if (stages == 3) return launch_impl<kSliced, 3, 64>(tmX, tmW, p, grid, st);
+    if (stages == 5) return launch_impl<kSliced, 5, 64>(tmX, tmW, p, grid, st);
+    return launch_impl<kSliced, 4, 64>(tmX, tmW, p, grid, st);
+  }
   return launch_impl<kSliced, 3, 128>(tmX, tmW, p, grid, st);
 }
 

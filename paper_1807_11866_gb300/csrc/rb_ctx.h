@@ -51,6 +51,7 @@ int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, dou
 int mixed_pressure_ok(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, const double *d_u,
                       double *d_p, rb_query_info *info, cudaStream_t st);
 int mixed_error_word(rb_ctx *ctx, cudaStream_t st);
+int mixed_tuning(rb_ctx *ctx, int i, int *out6, float *ms3);
 
 // per-kernel event timing (active only while profiling is enabled)
 struct ProfMark {

@@ -69,6 +69,13 @@ struct MixedState {
   float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices
   double2 *Rn = nullptr;        // [bcap] residual norms of the assembled systems
   CUtensorMap tmXj, tmXd;
+  // autotuned launch variants of this bucket (0 = not tuned: defaults), per batch-size class
+  struct Tune {
+    int klass = -1;      // ceil(log2(batch)) the choice was made for
+    int lu = 0;          // 1 warp per query, 2 blocked with 32-column panels, 3 blocked 16
+    int st_plain = 0, st_sliced = 0;  // TMA ring depths of the two GEMMs
+    float ms[4] = {0, 0, 0, 0};       // best times: elimination, plain GEMM, sliced GEMM
+  } tune;
   // shared, owned by the root
   int *dev_words = nullptr;     // [0] active count, [1] error word, [2] iterations, [8..] scratch
   int *h_words = nullptr;       // pinned mirror
@@ -718,17 +725,18 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
 // becomes U12 = L11^-1 A12, (d) the trailing matrix takes the rank-kPB update
 // A22 -= L21 U12 in 4 x 4 register tiles. The right-hand side is eliminated along, so back
 // substitution on U (blocks of 32 rows from the bottom) ends the solve.
-constexpr int kPB = 32;           // panel width
-constexpr int kPLd = kPB + 1;     // panel row stride in shared memory (odd: conflict-free columns)
-
+// Panel width PB (32 or 16, picked by the autotuner); panel row stride PB + 1 in shared memory
+// (odd: conflict-free column reads).
+template <int PB>
 struct BlkLuSmem {
+  static constexpr int kPLd = PB + 1;
   int P, U, perm, red, x, dred, total;  // byte offsets
   __host__ __device__ BlkLuSmem(int nb, int lda) {
     int p = 0;
     P = p; p += 4 * nb * kPLd;
     p = (p + 15) & ~15;
-    U = p; p += 4 * kPB * lda;
-    perm = p; p += 4 * kPB;
+    U = p; p += 4 * PB * lda;
+    perm = p; p += 4 * PB;
     red = p; p += 4 * kWarps;
     x = p; p += 4 * ((nb + 3) & ~3);
     p = (p + 7) & ~7;
@@ -742,10 +750,12 @@ __device__ __forceinline__ unsigned pivot_key9(float v, int r) {
   return (__float_as_uint(fabsf(v)) & 0xFFFFFE00u) | (unsigned)(511 - r);
 }
 
+template <int PB>
 __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
+  constexpr int kPB = PB, kPLd = PB + 1;
   const int nb = p.nb, lda = p.lda;
-  const BlkLuSmem L(nb, lda);
+  const BlkLuSmem<PB> L(nb, lda);
   float *P = reinterpret_cast<float *>(smb + L.P);
   float *U = reinterpret_cast<float *>(smb + L.U);
   int *perm = reinterpret_cast<int *>(smb + L.perm);
@@ -1502,7 +1512,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.Jc = M->Jc;
   g.nsplit = 3;
   int mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
-  cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st);
+  cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (Jacobian)");
   if (!exact) return RB_OK;
@@ -1513,14 +1523,17 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
   mk = prof_begin(ctx, RB_K_GEMM_RES, st);
-  e = launch_tc_gemm(kSliced, M->tmXd, M->WR.tm, g, ctx->sms, st);
+  e = launch_tc_gemm(kSliced, M->tmXd, M->WR.tm, g, ctx->sms, st, M->tune.st_sliced);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (residual)");
   return RB_OK;
 }
 
+static int launch_elimination(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStream_t st,
+                              int kind);
+
 // Newton step of the batch: k_newton_system assembles [J | -R] per query, then one warp
-// (nb <= 80) or one CTA (blocked elimination) per query solves it.
+// (nb <= 80) or one CTA (blocked elimination) per query solves it, as the autotuner chose.
 static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStream_t st) {
   lp.Amu = M->Amu;
   lp.Fm = M->Fm;
@@ -1537,18 +1550,30 @@ static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStrea
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
   }
   if (lp.eval_only) return RB_OK;
-  if (M->nb > kWarpLuMaxN) {
-    const size_t smem = BlkLuSmem(M->nb, lp.lda).total;
-    cudaError_t e = cudaFuncSetAttribute(k_lu_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_blocked attr");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_blocked, kThreads, smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_blocked occupancy");
-    const int grid = std::max(1, std::min(nq, std::max(1, per_sm) * ctx->sms));
+  return launch_elimination(ctx, M, lp, nq, st, M->tune.lu ? M->tune.lu : (M->nb <= kWarpLuMaxN ? 1 : 2));
+}
+
+template <int PB>
+static cudaError_t launch_blocked(const rb_ctx *ctx, const LuParams &lp, int nq, cudaStream_t st) {
+  const size_t smem = BlkLuSmem<PB>(lp.nb, lp.lda).total;
+  cudaError_t e = cudaFuncSetAttribute(k_lu_blocked<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_blocked<PB>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(nq, std::max(1, per_sm) * ctx->sms));
+  k_lu_blocked<PB><<<grid, kThreads, smem, st>>>(lp);
+  return cudaGetLastError();
+}
+
+// Elimination variant `kind`: 1 warp per query (nb <= 80), 2 blocked (32-column panels),
+// 3 blocked (16-column panels).
+static int launch_elimination(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStream_t st,
+                              int kind) {
+  if (kind >= 2 || M->nb > kWarpLuMaxN) {
     const int mk = prof_begin(ctx, RB_K_LU, st);
-    k_lu_blocked<<<grid, kThreads, smem, st>>>(lp);
+    const cudaError_t e = kind == 3 ? launch_blocked<16>(ctx, lp, nq, st) : launch_blocked<32>(ctx, lp, nq, st);
     prof_end(ctx, mk, st);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_blocked");
     return RB_OK;
   }
@@ -1615,7 +1640,7 @@ static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[1] = M->WP.wexp[1];
   g.out = M->Rp;
   int mk = prof_begin(ctx, RB_K_GEMM_PRES, st);
-  cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WP.tm, g, ctx->sms, st);
+  cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WP.tm, g, ctx->sms, st, M->tune.st_sliced);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (pressure)");
   mk = prof_begin(ctx, RB_K_PRESSURE, st);
@@ -1726,6 +1751,156 @@ static int solve_pressure(rb_ctx *ctx, const std::vector<Part> &parts, cudaStrea
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, int *words, int max_iter) {
   const int it = ++words[2];
   cudaGraphSetConditional(h, (words[0] > 0 && it < max_iter) ? 1u : 0u);
+}
+
+// ---- autotuner ------------------------------------------------------------------------------
+// Synthetic, well-conditioned systems of the bucket's shape for timing the elimination variants:
+// [J | -R] = [4 I + noise | 1], unit norms, every query active on the FP64-residual rung.
+__global__ void k_tune_fill(int nq, int nb, int lda, float *Jaug, double2 *Rn, rb_query_info *info,
+                            double *u, int ldu, int max_iter) {
+  const size_t total = (size_t)nq * nb * lda;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % lda), r = (int)((e / lda) % nb);
+    uint32_t h = (uint32_t)e * 2654435761u;
+    h ^= h >> 15;
+    const float v = ((float)(h & 0xFFFF) / 65536.f - 0.5f) * 0.1f;
+    Jaug[e] = c < nb ? (c == r ? 4.f + v : v) : (c == nb ? 1.f : 0.f);
+  }
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nq; b += gridDim.x * blockDim.x) {
+    Rn[b] = make_double2(1.0, 1.0);
+    rb_query_info q = {RB_Q_NOT_CONVERGED, 2, RB_PREC_MIXED, 0, 0.0, 0.0};
+    (void)max_iter;
+    info[b] = q;
+    for (int j = 0; j < ldu; ++j) u[(size_t)b * ldu + j] = 0.0;
+  }
+}
+
+static int ceil_log2(int v) {
+  int k = 0;
+  while ((1 << k) < v) ++k;
+  return k;
+}
+
+// Time the candidate launch variants of one bucket on `cnt` queries (once per batch-size class)
+// and keep the fastest: elimination (warp per query if nb <= 80, blocked with 32- or 16-column
+// panels) and the TMA ring depths of the two GEMMs. Run before the solve graph is captured.
+static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
+  const int klass = ceil_log2(std::max(cnt, 1));
+  if (M->tune.klass == klass) return RB_OK;
+  const DevOps &o = ctx->ops;
+  void *pu = nullptr, *pi = nullptr;
+  int rc = ctx_alloc(ctx, &pu, 8 * (size_t)cnt * o.n_max, "tuning u");
+  if (rc != RB_OK) return rc;
+  if ((rc = ctx_alloc(ctx, &pi, sizeof(rb_query_info) * (size_t)cnt, "tuning info")) != RB_OK) {
+    ctx_free(ctx, pu);
+    return rc;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto timed = [&](auto &&launch) -> float {  // best of two, ms
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, st);
+      if (launch() != RB_OK) return -1.f;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  MixedState::Tune t;
+  t.klass = klass;
+  // elimination
+  LuParams lp{};
+  lp.o = o;
+  lp.nq = cnt;
+  lp.nb = M->nb;
+  lp.ldj = M->Npad;
+  lp.max_iter = 1 << 20;
+  lp.u = (double *)pu;
+  lp.info = (rb_query_info *)pi;
+  lp.active = M->root->dev_words + 8;
+  lp.rmode = kResExact;
+  lp.Jaug = M->Jaug;
+  lp.Rn = M->Rn;
+  lp.lda = aug_ld(M->nb);
+  float best = 1e30f;
+  for (int kind = (M->nb <= kWarpLuMaxN ? 1 : 2); kind <= 3; ++kind) {
+    const float ms = timed([&]() {
+      k_tune_fill<<<ctx->sms * 4, 256, 0, st>>>(cnt, M->nb, lp.lda, M->Jaug, M->Rn, lp.info, lp.u, o.n_max, 0);
+      cudaEventRecord(e0, st);  // time the elimination only
+      return launch_elimination(ctx, M, lp, cnt, st, kind);
+    });
+    if (ms < 0.f) { rc = set_error(ctx, RB_ERR_CUDA, "autotune (elimination)"); break; }
+    if (ms < best) { best = ms; t.lu = kind; t.ms[0] = ms; }
+  }
+  // GEMMs on the bucket's operands (their outputs are rebuilt before every use)
+  TcGemmParams g = gemm_params(M, cnt);
+  g.n_tiles = M->Npad / kTcBN;
+  g.kb[0] = M->kb0;
+  g.n_pad = M->Npad;
+  g.nk = M->nb;
+  g.ldj = M->Npad;
+  g.Jc = M->Jc;
+  g.nsplit = 3;
+  best = 1e30f;
+  for (int stg : {4, 6}) {
+    if (rc != RB_OK) break;
+    const float ms = timed([&]() {
+      const cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, stg);
+      return e == cudaSuccess ? RB_OK : RB_ERR_CUDA;
+    });
+    if (ms < 0.f) { rc = set_error(ctx, RB_ERR_CUDA, "autotune (Jacobian GEMM)"); break; }
+    if (ms < best) { best = ms; t.st_plain = stg; t.ms[1] = ms; }
+  }
+  g.n_tiles = M->WR.Npad / kTcBN;
+  g.n_pad = M->WR.Npad;
+  g.wexp[0] = M->WR.wexp[0];
+  g.wexp[1] = M->WR.wexp[1];
+  g.out = M->Rc;
+  best = 1e30f;
+  for (int stg : {3, 4, 5}) {
+    if (rc != RB_OK) break;
+    if (M->nb > 64 && stg != 3) continue;
+    const float ms = timed([&]() {
+      const cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WR.tm, g, ctx->sms, st, stg);
+      return e == cudaSuccess ? RB_OK : RB_ERR_CUDA;
+    });
+    if (ms < 0.f) { rc = set_error(ctx, RB_ERR_CUDA, "autotune (sliced GEMM)"); break; }
+    if (ms < best) { best = ms; t.st_sliced = stg; t.ms[2] = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  ctx_free(ctx, pu);
+  ctx_free(ctx, pi);
+  if (rc != RB_OK) return rc;
+  M->tune = t;
+  M->root->epoch += 1;  // the solve graph holds the previous variants
+  return check_words(ctx, st, "autotune");
+}
+
+int mixed_tuning(rb_ctx *ctx, int i, int *out6, float *ms3) {
+  MixedState *R = ctx->mixed;
+  if (!R) return 0;
+  std::vector<MixedState *> tuned;
+  for (auto &kv : R->buckets)
+    if (kv.second->tune.klass >= 0) tuned.push_back(kv.second);
+  if (R->tune.klass >= 0) tuned.push_back(R);
+  if (i >= 0 && i < (int)tuned.size()) {
+    const MixedState *M = tuned[i];
+    if (out6) {
+      const int v[6] = {M->nb, M->tune.klass, M->tune.lu, M->tune.st_plain, M->tune.st_sliced, 0};
+      for (int k = 0; k < 6; ++k) out6[k] = v[k];
+    }
+    if (ms3)
+      for (int k = 0; k < 3; ++k) ms3[k] = M->tune.ms[k];
+  }
+  return (int)tuned.size();
 }
 
 // The whole solve: gather (bucketed batches), prologue, rungs 0 and 1, a while-loop node over
@@ -1933,6 +2108,9 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
     }
     pl.gathered = true;
   }
+  if (ctx->cfg.autotune)
+    for (const Part &pt : pl.parts)
+      if ((rc = autotune(ctx, pt.M, pt.a.nq, st)) != RB_OK) return rc;
   if (ctx->cfg.use_graph && !ctx->prof) {
     const auto &k = R->gkey;
     if (!R->gexec || k.mu != d_mu || k.theta != d_theta || k.p != d_p || k.n != d_n || k.u != d_u ||

@@ -31,6 +31,6 @@ struct TcGemmParams {
 };
 
 cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &tmW,
-                           const TcGemmParams &p, int sms, cudaStream_t st);
+                           const TcGemmParams &p, int sms, cudaStream_t st, int stages = 0);
 
 }  // namespace rb

@@ -477,6 +477,11 @@ int rb_eval(rb_ctx *ctx, const double *mu, int n_queries, int n, const double *u
   return RB_OK;
 }
 
+int rb_tuning(rb_ctx *ctx, int i, int *out6, float *ms3) {
+  if (!ctx) return RB_ERR_ARG;
+  return mixed_tuning(ctx, i, out6, ms3);
+}
+
 int rb_profile(rb_ctx *ctx, int enable) {
   if (!ctx) return RB_ERR_ARG;
   cudaSetDevice(ctx->device);

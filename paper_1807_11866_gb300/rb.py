@@ -26,7 +26,7 @@ RB_STATIC_N_MAX, RB_STATIC_SCRATCH_BYTES = 512, 16 << 20
 EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
            "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
            "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
-           "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots"]
+           "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots", "rb_tuning"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>",
               "k_newton_system", "k_prep"]
@@ -91,6 +91,7 @@ def library():
         L.rb_serve_poll.argtypes = [P, ctypes.c_uint64, P, P, P]
         L.rb_serve_stats.argtypes = [P, P, P, P]
         L.rb_serve_slots.argtypes = [P]
+        L.rb_tuning.argtypes = [P, I, P, P]
         for name in EXPORTS:
             if name not in ("rb_config_default", "rb_destroy", "rb_last_error"):
                 getattr(L, name).restype = I
@@ -137,7 +138,7 @@ class Context:
     """An rb_ctx on one device. Methods mirror the C entry points one to one."""
 
     def __init__(self, precision=RB_PREC_FP64, tol_update=None, tol_res=None, max_iter=None,
-                 mem_budget=None, use_graph=None, device=0, serve_slots=None):
+                 mem_budget=None, use_graph=None, device=0, serve_slots=None, autotune=None):
         L = library()
         cfg = rb_config_default()
         cfg.precision = precision
@@ -153,6 +154,8 @@ class Context:
             cfg.use_graph = use_graph
         if serve_slots is not None:
             cfg.serve_slots = serve_slots
+        if autotune is not None:
+            cfg.autotune = autotune
         self.cfg = cfg
         h = ctypes.c_void_p()
         rc = L.rb_create(ctypes.byref(h), ctypes.byref(cfg), device)
@@ -268,6 +271,26 @@ class Context:
             self._check(library().rb_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)),
                         "rb_profile_read")
             out[name] = (ms.value, n.value)
+        return out
+
+    # --- autotuner ----------------------------------------------------------------------
+    ELIMINATION = {1: "warp per query", 2: "blocked, 32-column panels", 3: "blocked, 16-column panels"}
+
+    def rb_tuning(self):
+        """Autotuned launch variants of every tuned size bucket (list of dicts)."""
+        L = library()
+        count = L.rb_tuning(self.h, -1, None, None)
+        if count < 0:
+            raise RbError(count, f"rb_tuning: {self.last_error()}")
+        out = []
+        for i in range(count):
+            v = (ctypes.c_int * 6)()
+            ms = (ctypes.c_float * 3)()
+            L.rb_tuning(self.h, i, v, ms)
+            out.append({"n_bucket": v[0], "batch_class": v[1],
+                        "elimination": self.ELIMINATION.get(v[2], str(v[2])),
+                        "jacobian_gemm_stages": v[3], "sliced_gemm_stages": v[4],
+                        "best_ms": {"elimination": ms[0], "jacobian_gemm": ms[1], "sliced_gemm": ms[2]}})
         return out
 
     # --- serving ------------------------------------------------------------------------

@@ -210,3 +210,33 @@ def test_uneven_sizes_bucketed(rb):
         assert rel(u, u_ref).max() <= TOL_MIXED
         for b, n in enumerate(sizes):
             assert np.all(u[b, n:] == 0.0)
+
+
+def test_autotuner_choices(rb):
+    """The autotuner times the candidate variants of every bucket it meets and records a valid
+    choice; with it off nothing is recorded. Either way the solution is the oracle's."""
+    wl = synth.WORKLOADS["uneven_n120"]
+    ops = synth.make_operators(wl, n_max=96, q_a=4, q_c=4)
+    q = synth.make_queries(wl, batch=160, n_max=96)
+    sizes = np.array([30, 96, 60, 12] * 40, dtype=np.int32)
+    o = oracle.Oracle.from_set(ops)
+    u_ref, _, _ = o.solve(q.mu, n=sizes, threads=8)
+    with rb.Context(rb.RB_PREC_MIXED, autotune=1) as ctx:
+        ctx.load_set(ops)
+        u1, _, i1 = ctx.rb_solve(q.mu, n=sizes)
+        tune = ctx.rb_tuning()
+    with rb.Context(rb.RB_PREC_MIXED, autotune=0) as ctx:
+        ctx.load_set(ops)
+        u0, _, i0 = ctx.rb_solve(q.mu, n=sizes)
+        assert ctx.rb_tuning() == []
+    assert sorted(t["n_bucket"] for t in tune) == [16, 32, 64, 96]
+    for t in tune:
+        assert t["batch_class"] == 6  # 40 queries per bucket
+        assert t["jacobian_gemm_stages"] in (4, 6)
+        assert t["sliced_gemm_stages"] in ((3, 4, 5) if t["n_bucket"] <= 64 else (3,))
+        if t["n_bucket"] > 80:
+            assert t["elimination"].startswith("blocked")
+        assert all(v > 0 for v in t["best_ms"].values())
+    for u, info in ((u1, i1), (u0, i0)):
+        assert np.all(info["status"] == 0)
+        assert rel(u, u_ref).max() <= TOL_MIXED
