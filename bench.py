@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mode: saturation throughput of the continuous-batching server "
+                         "and p50/p99 submit-to-completion latency under Poisson arrivals")
+    ap.add_argument("--serve-burst", type=int, default=2048)
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     return ap.parse_args()
 
 
@@ -195,6 +200,9 @@ def main():
     wl = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
+        return
+    if args.serve:
+        run_serve(args, wl, rank, world, local)
         return
     import torch
     from paper_1807_11866_gb300 import _build, rb
@@ -406,6 +414,108 @@ def kernel_rooflines(prec, wl, q, info, kprof, steps):
                  "frac": ach / peak, "traffic": traffic, "peak_source": src, "launches": launches}
     dom = max(kprof, key=lambda k: kprof[k][0])
     return rl.get(dom), rl, kernels
+
+
+def run_serve(args, wl, rank, world, local):
+    """Serving: the server takes queries one by one through the public C API (rb_serve_submit /
+    rb_serve_poll, host buffers), each of its own size n. (1) Saturation: a burst of
+    --serve-burst queries, throughput = queries / time to the last completion. (2) Load points at
+    25%, 50% and 80% of saturation: Poisson arrivals for --serve-seconds, with the server's own
+    submit-to-completion p50 / p99. Every rank serves its own stream (replicas); rank 0 prints
+    the sum of the ranks' saturation rates and its own latencies."""
+    import torch
+    from paper_1807_11866_gb300 import _build, rb
+    torch.cuda.set_device(local)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+    ops = synth.make_operators(wl)
+    q = synth.make_queries(wl, batch=wl.batch)
+    ctx = rb.Context(precision=PREC[args.precision], device=local)
+    ctx.load_set(ops)
+    B = len(q.mu)
+
+    def point(rate, count, seed):
+        ctx.rb_serve_start()
+        g = np.random.default_rng(seed)
+        pending = []
+        t0 = time.perf_counter()
+        nxt = t0
+        for i in range(count):
+            if rate:
+                nxt += g.exponential(1.0 / rate)
+                while True:
+                    d = nxt - time.perf_counter()
+                    if d <= 0:
+                        break
+                    time.sleep(min(d, 1e-3))
+            pending.append(ctx.rb_serve_submit(q.mu[i % B], n=int(q.n[i % B])))
+        status = []
+        while pending:
+            left = []
+            for t in pending:
+                r = ctx.rb_serve_poll(t)
+                if r is None:
+                    left.append(t)
+                else:
+                    status.append(int(r[2]["status"]))
+            pending = left
+            if pending:
+                time.sleep(2e-4)
+        t1 = time.perf_counter()
+        p50, p99, sps = ctx.rb_serve_stats()
+        ctx.rb_serve_stop(True)
+        return {"offered_per_s": rate, "queries": count, "served_per_s": count / (t1 - t0),
+                "server_solves_per_s": sps, "p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99,
+                "ok": int(sum(1 for s in status if s == 0))}
+
+    point(None, min(256, args.serve_burst), 1)  # warm-up: layouts, slot tables, first graphs
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.rb_profile(True)  # counts the server's launches (events on its stream, read after stop)
+    sat = point(None, args.serve_burst, 2)
+    kprof = ctx.rb_profile_read()
+    ctx.rb_profile(False)
+    launches = int(sum(v[1] for v in kprof.values()))
+    kernels = {k: {"ms": v[0], "launches": v[1]} for k, v in kprof.items() if v[1]}
+    loads = []
+    for frac in (0.25, 0.5, 0.8):
+        rate = frac * sat["served_per_s"]
+        loads.append(point(rate, max(64, int(rate * args.serve_seconds)), 3 + len(loads)))
+    clk = clocks.stop()
+    value = sat["served_per_s"]
+    if world > 1:
+        t = torch.tensor([value], device="cuda")
+        torch.distributed.all_reduce(t)
+        value = float(t.item())
+    slots = None
+    if rank == 0:
+        m = ctx.m
+        line = {
+            "metric": "served reduced Newton solves/s (saturation) and p99 latency", "value": value,
+            "unit": "solves/s", "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * args.serve_burst / sat["served_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32+f64" if PREC[args.precision] == 1 else "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n": f"U[{wl.size_range[0]},{wl.size_range[1]}]" if wl.size_range else wl.n_max,
+                       "q_a": wl.q_a, "q_c": wl.q_c, "q_f": wl.q_f, "m": wl.m,
+                       "precision": args.precision, "burst": args.serve_burst,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "not flushed (serving: operators stay resident by design)"},
+            "latency_ms": {"p50": loads[-1]["p50_ms"], "p99": loads[-1]["p99_ms"],
+                           "at_offered_per_s": loads[-1]["offered_per_s"]},
+            "saturation": sat, "load_points": loads,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 20 * args.serve_burst,
+                    "d2h_bytes_per_step": (8 * (wl.n_max + m) + 32) * args.serve_burst},
+            "gpu_launches": launches, "kernels": kernels, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def plain_fp64(rb, ops, q, batch, dev, flush, args):

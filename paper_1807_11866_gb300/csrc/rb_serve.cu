@@ -18,6 +18,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -57,7 +58,7 @@ struct ServeState {
   std::vector<uint64_t> slot_ticket;
   std::vector<int> slot_iters;
   std::vector<Clock::time_point> slot_t0;
-  std::vector<int> free_slots;
+  std::set<int> free_slots;   // lowest index first, so live slots stay packed at the front
   // device slot arrays
   double *d_mu = nullptr, *d_u = nullptr, *d_p = nullptr, *d_out = nullptr;
   int *d_n = nullptr, *d_idx = nullptr, *d_cnt = nullptr;
@@ -172,13 +173,13 @@ static int serve_step(rb_ctx *ctx, ServeState *S, bool &idle) {
     if (S->stop_req && !S->drain) return RB_OK;
     if (!mixed) {  // FP64 steps finish every admitted query: admit into slots 0, 1, 2, ...
       S->free_slots.clear();
-      for (int s = S->cap - 1; s >= 0; --s) S->free_slots.push_back(s);
+      for (int s = 0; s < S->cap; ++s) S->free_slots.insert(s);
     }
     while (!S->queue.empty() && !S->free_slots.empty()) {
       const Pending q = S->queue.front();
       S->queue.pop_front();
-      const int s = S->free_slots.back();
-      S->free_slots.pop_back();
+      const int s = *S->free_slots.begin();
+      S->free_slots.erase(S->free_slots.begin());
       S->slot_ticket[s] = q.ticket;
       S->slot_iters[s] = 0;
       S->slot_t0[s] = q.t0;
@@ -201,18 +202,21 @@ static int serve_step(rb_ctx *ctx, ServeState *S, bool &idle) {
   // 2. one Newton iteration for every live slot (the whole solve for FP64 contexts)
   int rc;
   if (mixed) {
+    // the step covers slots 0 .. live - 1 (admission fills the lowest free slots first)
     bool need_j = false, need_x = false;
+    int live = 0;
     for (int s = 0; s < S->cap; ++s)
       if (S->slot_ticket[s]) {
         need_j |= S->slot_iters[s] >= 1;
         need_x |= S->slot_iters[s] >= 2;
+        live = s + 1;
       }
-    rc = mixed_iteration(ctx, S->d_mu, S->cap, S->d_n, S->d_u, S->d_info, need_j, need_x, st);
+    rc = live ? mixed_iteration(ctx, S->d_mu, live, S->d_n, S->d_u, S->d_info, need_j, need_x, st) : RB_OK;
     if (rc != RB_OK) return rc;
     for (int s = 0; s < S->cap; ++s)
       if (S->slot_ticket[s]) S->slot_iters[s] += 1;
     // 3. pressure of the slots that converged in this step
-    if (m > 0 && (rc = mixed_pressure_ok(ctx, S->d_mu, S->cap, S->d_n, S->d_u, S->d_p, S->d_info, st)) != RB_OK)
+    if (m > 0 && live && (rc = mixed_pressure_ok(ctx, S->d_mu, live, S->d_n, S->d_u, S->d_p, S->d_info, st)) != RB_OK)
       return rc;
     if ((rc = mixed_error_word(ctx, st)) != RB_OK) return rc;
   } else if (K > 0) {  // the admitted queries occupy slots 0..K-1
@@ -242,7 +246,7 @@ static int serve_step(rb_ctx *ctx, ServeState *S, bool &idle) {
       const double *row = S->h_out + (size_t)i * (nm + m);
       complete(S, S->slot_ticket[s], S->slot_t0[s], row, row + nm, nm, m, S->h_info[i]);
       S->slot_ticket[s] = 0;
-      S->free_slots.push_back(s);
+      S->free_slots.insert(s);
     }
   }
   return RB_OK;
@@ -275,7 +279,7 @@ static void serve_loop(rb_ctx *ctx) {
     if (S->slot_ticket[s]) {
       complete(S, S->slot_ticket[s], S->slot_t0[s], zu.data(), zp.data(), nm, m, rej);
       S->slot_ticket[s] = 0;
-      S->free_slots.push_back(s);
+      S->free_slots.insert(s);
     }
   S->running = false;
   S->cv.notify_all();
@@ -369,7 +373,7 @@ int rb_serve_start(rb_ctx *ctx) {
   S->slot_iters.assign(cap, 0);
   S->slot_t0.assign(cap, Clock::now());
   S->free_slots.clear();
-  for (int s = cap - 1; s >= 0; --s) S->free_slots.push_back(s);
+  for (int s = 0; s < cap; ++s) S->free_slots.insert(s);
   S->t_start = S->t_last = Clock::now();
   S->running = true;
   S->th = std::thread(serve_loop, ctx);
