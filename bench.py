@@ -361,7 +361,6 @@ DIGITS = int(os.environ.get("RB_DIGITS", "6"))  # digit slices of the sliced con
 NCU_TRAFFIC = {
     "sweep_n50": {
         "k_newton_system": 151.0e6,
-        "k_lu_mixed": 44.5e6,
     },
 }
 

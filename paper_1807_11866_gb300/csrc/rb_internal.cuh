@@ -314,71 +314,133 @@ __device__ __forceinline__ float comp4(const float4 &a, int t) {
   return t == 0 ? a.x : (t == 1 ? a.y : (t == 2 ? a.z : a.w));
 }
 
+__device__ __forceinline__ void set4(float4 &a, int t, float v) {
+  if (t == 0) a.x = v; else if (t == 1) a.y = v; else if (t == 2) a.z = v; else a.w = v;
+}
+
+__device__ __forceinline__ float4 shfl4(const float4 &v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+__device__ __forceinline__ float4 fms4(float4 a, float l, const float4 &u) {  // a - l u
+  a.x = fmaf(-l, u.x, a.x);
+  a.y = fmaf(-l, u.y, a.y);
+  a.z = fmaf(-l, u.z, a.z);
+  a.w = fmaf(-l, u.w, a.w);
+  return a;
+}
+
 // Solve the n x n system stored with its right-hand side as the augmented matrix M = [A | b]
 // (column n holds b; row stride ld a multiple of 4 with ld / 4 odd and M 16-byte aligned, so
 // that lanes reading float4 chunks of rows i, i + 1, ... hit distinct banks) by one warp:
 // Gaussian elimination with partial pivoting (pivot_key over the rows not yet used as pivots),
 // b eliminated along, then back substitution. Rows stay in place (implicit pivoting): row r is
-// owned by lane r % 32, which keeps the row's entry in the next pivot column in a register, so
-// a step needs no pivot-column reads and no row swap. pseq (shared, n ints) receives the pivot
-// row of every step. Row k of the solution is returned in x[k / 32] of lane k % 32 (n <= 96).
-// Returns true if a pivot was zero or not finite.
+// owned by lane r % 32. The elimination goes by panels of 4 columns (one float4 chunk): the
+// lanes factor the panel in registers (4 pivot steps), finish the 4 pivot rows right of the
+// panel (U rows, lanes over chunks), then apply one rank-4 update to every other row, so each
+// trailing element passes through shared memory once per 4 steps. pseq (shared, n ints rounded
+// up to 4) receives the pivot row of every step. Row k of the solution is returned in
+// x[k / 32] of lane k % 32 (n <= 96). Returns true if a pivot was zero or not finite.
 __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x)[kWarpRows],
                                               int *pseq) {
   const int lane = threadIdx.x & 31;
   const int c_end = n >> 2;  // last float4 chunk: the one holding column n
-  float cur[kWarpRows], dinv[kWarpRows];
+  float4 *M4 = reinterpret_cast<float4 *>(M);
+  const int ld4 = ld >> 2;
+  float dinv[kWarpRows];
   int step[kWarpRows];       // step at which the row was the pivot; n: not yet; -1: no row
 #pragma unroll
   for (int s = 0; s < kWarpRows; ++s) {
     const int r = lane + 32 * s;
-    cur[s] = r < n ? M[r * ld] : 0.f;
     step[s] = r < n ? n : -1;
     dinv[s] = 0.f;
   }
-  for (int p = 0; p < n; ++p) {
-    unsigned key = 0;
+  for (int c0 = 0; 4 * c0 < n; ++c0) {
+    float4 pc[kWarpRows];    // own rows' panel chunk
+    float lm[kWarpRows][4];  // own rows' multipliers of the panel's steps
 #pragma unroll
     for (int s = 0; s < kWarpRows; ++s) {
-      const unsigned k = pivot_key(cur[s], lane + 32 * s);
-      if (step[s] == n && k > key) key = k;
+      pc[s] = step[s] >= 0 ? M4[(lane + 32 * s) * ld4 + c0] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) lm[s][t] = 0.f;
     }
-    key = __reduce_max_sync(0xffffffffu, key);
-    const int piv = 255 - (int)(key & 255u);
-    const float pv = __shfl_sync(0xffffffffu, slot3(cur, piv >> 5), piv & 31);
-    if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
-    const float rinv = __frcp_rn(pv);
+    int prow[4] = {0, 0, 0, 0};
+    const int steps = min(4, n - 4 * c0);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t >= steps) break;
+      const int p = 4 * c0 + t;
+      unsigned key = 0;
+#pragma unroll
+      for (int s = 0; s < kWarpRows; ++s) {
+        const unsigned k = pivot_key(comp4(pc[s], t), lane + 32 * s);
+        if (step[s] == n && k > key) key = k;
+      }
+      key = __reduce_max_sync(0xffffffffu, key);
+      const int piv = 255 - (int)(key & 255u), ps = piv >> 5;
+      const float4 pp = shfl4(ps == 0 ? pc[0] : (ps == 1 ? pc[1] : pc[2]), piv & 31);
+      const float pv = comp4(pp, t);
+      if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
+      const float rinv = __frcp_rn(pv);
+      prow[t] = piv;
+      if (lane == 0) pseq[p] = piv;
+#pragma unroll
+      for (int s = 0; s < kWarpRows; ++s) {
+        if (lane + 32 * s == piv) {
+          step[s] = p;
+          dinv[s] = rinv;
+        } else if (step[s] == n) {
+          const float l = comp4(pc[s], t) * rinv;
+          lm[s][t] = l;
+#pragma unroll
+          for (int t2 = t + 1; t2 < 4; ++t2) set4(pc[s], t2, fmaf(-l, comp4(pp, t2), comp4(pc[s], t2)));
+        }
+      }
+    }
+    // panel chunks back (U entries of the pivot rows, the remaining rows' next values)
 #pragma unroll
     for (int s = 0; s < kWarpRows; ++s)
-      if (lane + 32 * s == piv) {
-        step[s] = p;
-        dinv[s] = rinv;
+      if (step[s] >= 0) M4[(lane + 32 * s) * ld4 + c0] = pc[s];
+    // multipliers of the later pivot rows with respect to the earlier ones, in all lanes
+    float lp[4][4];
+#pragma unroll
+    for (int t = 1; t < 4; ++t) {
+      const int pr = prow[t], ps = pr >> 5;
+#pragma unroll
+      for (int t2 = 0; t2 < t; ++t2) {
+        const float v = ps == 0 ? lm[0][t2] : (ps == 1 ? lm[1][t2] : lm[2][t2]);
+        lp[t][t2] = __shfl_sync(0xffffffffu, v, pr & 31);
       }
-    if (lane == 0) pseq[p] = piv;
-    const float4 *mp = reinterpret_cast<const float4 *>(M + piv * ld);
-    const int c0 = (p + 1) >> 2, tn = (p + 1) & 3;
+    }
+    __syncwarp();
+    // U rows right of the panel, lanes over chunks: U_t = row_t - sum_{t2 < t} l(t, t2) U_t2
+    for (int c = c0 + 1 + lane; c <= c_end; c += 32) {
+      float4 u[4];
+      u[0] = M4[prow[0] * ld4 + c];
+#pragma unroll
+      for (int t = 1; t < 4; ++t) {
+        if (t >= steps) break;
+        float4 a = M4[prow[t] * ld4 + c];
+#pragma unroll
+        for (int t2 = 0; t2 < t; ++t2) a = fms4(a, lp[t][t2], u[t2]);
+        u[t] = a;
+        M4[prow[t] * ld4 + c] = a;
+      }
+    }
+    __syncwarp();
+    // rank-`steps` update of the rows not yet used as pivots
 #pragma unroll
     for (int s = 0; s < kWarpRows; ++s) {
       if (step[s] != n) continue;
-      float4 *mi = reinterpret_cast<float4 *>(M + (lane + 32 * s) * ld);
-      const float l = cur[s] * rinv;
-      float4 a = mi[c0];
-      float4 q = mp[c0];
-      a.x = fmaf(-l, q.x, a.x);
-      a.y = fmaf(-l, q.y, a.y);
-      a.z = fmaf(-l, q.z, a.z);
-      a.w = fmaf(-l, q.w, a.w);
-      mi[c0] = a;
-      cur[s] = comp4(a, tn);
-#pragma unroll 4
+      float4 *row = M4 + (lane + 32 * s) * ld4;
+#pragma unroll 2
       for (int c = c0 + 1; c <= c_end; ++c) {
-        a = mi[c];
-        q = mp[c];
-        a.x = fmaf(-l, q.x, a.x);
-        a.y = fmaf(-l, q.y, a.y);
-        a.z = fmaf(-l, q.z, a.z);
-        a.w = fmaf(-l, q.w, a.w);
-        mi[c] = a;
+        float4 a = row[c];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < steps) a = fms4(a, lm[s][t], M4[prow[t] * ld4 + c]);
+        row[c] = a;
       }
     }
     __syncwarp();
@@ -394,8 +456,7 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
     float4 mc[kWarpRows];
 #pragma unroll
     for (int s = 0; s < kWarpRows; ++s)
-      mc[s] = step[s] >= 0 ? reinterpret_cast<const float4 *>(M + (lane + 32 * s) * ld)[c]
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      mc[s] = step[s] >= 0 ? M4[(lane + 32 * s) * ld4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int4 pq = reinterpret_cast<const int4 *>(pseq)[c];
 #pragma unroll
     for (int t = 3; t >= 0; --t) {
