@@ -1,7 +1,7 @@
 // rb_mixed.cu -- mixed-precision batched Newton (inexact Newton, Sec. 3.6 Jacobian on tensor cores).
 //
-// Once per query at its start: theta(mu_b), f(mu_b) (k_prep_theta) and A(mu_b) in double-float
-// (k_assemble_a). Per Newton iteration, for every active query b of the batch:
+// Once per query at its start: theta(mu_b), f(mu_b) (k_prep_theta) and A(mu_b), B(mu_b) in
+// double-float (k_affine_sum). Per Newton iteration, for every active query b of the batch:
 //   1. k_build_x: X_b = theta^c(mu_b) (x) u_b as split BF16 (hi, lo) for the Jacobian GEMM; the
 //      7-bit digit slices of theta^c (x) u_b / 2 for the sliced GEMM; u_b as (hi, lo) floats
 //      (transposed); R^c_b = 0.
@@ -66,6 +66,7 @@ struct MixedState {
   double *Fm = nullptr;         // [bcap][nb] f(mu)
   float2 *Amu = nullptr;        // [bcap][nb * nb] A(mu) as double-float
   double *Asu = nullptr;        // [bcap][m] As(mu) u
+  float2 *Bmu = nullptr;        // [bcap][m][m] B(mu) as double-float
   float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices
   double2 *Rn = nullptr;        // [bcap] residual norms of the assembled systems
   CUtensorMap tmXj, tmXd;
@@ -423,10 +424,8 @@ struct PrepParams {
   const double *mu, *theta_in;  // theta_in: [nq][n_theta] caller rows, or null: from mu
   int nq, nb, max_iter;
   const rb_query_info *info;
-  const float2 *A2;             // [q_a][nb][nb] A_q as double-float
   double *Th;                   // [nq][n_theta]
   double *Fm;                   // [nq][nb]
-  float2 *Amu;                  // [nq][nb * nb]
 };
 
 __device__ __forceinline__ bool starts(const rb_query_info &q, int max_iter) {
@@ -457,15 +456,25 @@ __global__ void k_prep_theta(PrepParams p) {
   }
 }
 
-// A(mu) of the starting queries: a block holds kAsmQ queries' theta^a (double-float) and each
-// thread one element (k, j), so every A_q element read serves kAsmQ queries.
+// Affine sums of the starting queries: out_b = sum_q theta_{off+q}(b) Q_q in double-float, for
+// A(mu) (A_q, theta^a) and B(mu) (B_q, theta^b). A block holds kAsmQ queries' coefficients and
+// each thread one element, so every Q_q element read serves kAsmQ queries.
 constexpr int kAsmQ = 8;
 
-__global__ void __launch_bounds__(256) k_assemble_a(PrepParams p) {
-  extern __shared__ float2 ta_s[];  // [kAsmQ][q_a]
+struct AffineParams {
+  int nq, max_iter, n_theta, th_off, qn;
+  size_t nn;                  // elements per matrix
+  const rb_query_info *info;
+  const double *Th;           // [nq][n_theta]
+  const float2 *Q2;           // [qn][nn] double-float terms
+  float2 *out;                // [nq][nn]
+};
+
+__global__ void __launch_bounds__(256) k_affine_sum(AffineParams p) {
+  extern __shared__ float2 ta_s[];  // [kAsmQ][qn]
   __shared__ int flag[kAsmQ];
-  const int qa = p.o.q_a;
-  const size_t nn = (size_t)p.nb * p.nb;
+  const int qa = p.qn;
+  const size_t nn = p.nn;
   for (int g = blockIdx.y; g * kAsmQ < p.nq; g += gridDim.y) {
     const int b0 = g * kAsmQ;
     __syncthreads();
@@ -481,7 +490,7 @@ __global__ void __launch_bounds__(256) k_assemble_a(PrepParams p) {
     for (int i = threadIdx.x; i < kAsmQ * qa; i += blockDim.x) {
       const int r = i / qa, q = i - r * qa;
       float h = 0.f, l = 0.f;
-      if (flag[r]) df_split(p.Th[(size_t)(b0 + r) * p.o.n_theta + q], h, l);
+      if (flag[r]) df_split(p.Th[(size_t)(b0 + r) * p.n_theta + p.th_off + q], h, l);
       ta_s[i] = make_float2(h, l);
     }
     __syncthreads();
@@ -492,7 +501,7 @@ __global__ void __launch_bounds__(256) k_assemble_a(PrepParams p) {
       for (int r = 0; r < kAsmQ; ++r) ah[r] = al[r] = 0.f;
 #pragma unroll 2
       for (int q = 0; q < qa; ++q) {
-        const float2 a2 = __ldg(p.A2 + (size_t)q * nn + e);
+        const float2 a2 = __ldg(p.Q2 + (size_t)q * nn + e);
 #pragma unroll
         for (int r = 0; r < kAsmQ; ++r) {
           const float2 t = ta_s[r * qa + q];
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(256) k_assemble_a(PrepParams p) {
       }
 #pragma unroll
       for (int r = 0; r < kAsmQ; ++r)
-        if (flag[r]) p.Amu[(size_t)(b0 + r) * nn + e] = make_float2(ah[r], al[r]);
+        if (flag[r]) p.out[(size_t)(b0 + r) * nn + e] = make_float2(ah[r], al[r]);
     }
   }
 }
@@ -511,7 +520,7 @@ struct LuParams {
   const int *nsz;
   int nq, nb, ldj, max_iter;
   double tol_upd, tol_res;
-  const float2 *Amu;     // [nq][nb * nb] A(mu) as double-float (k_assemble_a)
+  const float2 *Amu;     // [nq][nb * nb] A(mu) as double-float (k_affine_sum)
   const double *Fm;      // [nq][nb] f(mu)
   float *Jaug;           // [nq][nb][lda] augmented Newton matrices [J | -R] (warp path)
   double2 *Rn;           // [nq]: (||R||, max(1, ||f||)) of the assembled system
@@ -1027,7 +1036,7 @@ struct PresSolveParams {
   DevOps o;
   const double *theta;  // [nq][n_theta]
   int nq;
-  const float2 *B2;     // [q_b][m][m] double-float
+  const float2 *Bmu;    // [nq][m][m] B(mu) double-float (k_affine_sum)
   const double *Rp;     // [b_pad][m]: Cs_mu(u, u) (sliced GEMM)
   const double *Asu;    // [b_pad][m]: As(mu) u (k_as_u)
   double *p_out;        // [nq][m]
@@ -1038,7 +1047,7 @@ constexpr int kPresRefine = 2;
 
 // shared-memory slab of one warp's pressure solve (bytes)
 struct PresSmem {
-  int th, r, pv, pf, tb, Bd, Bf, rf, perm, total, ldd, ldb;
+  int th, r, pv, pf, Bd, Bf, rf, perm, total, ldd, ldb;
   __host__ __device__ PresSmem(const DevOps &o) {
     const int m = o.m;
     ldd = odd_ld(m);
@@ -1048,7 +1057,6 @@ struct PresSmem {
     r = p; p += 8 * m;
     pv = p; p += 8 * m;
     pf = p; p += 8 * m;
-    tb = p; p += 8 * o.q_b;
     Bd = p; p += 8 * m * ldd;
     Bf = p; p += 4 * m * ldb;
     rf = p; p += 4 * m;
@@ -1065,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParam
   const PresSmem L(o);
   uint8_t *slab = smb + (size_t)w * L.total;
   double *th = (double *)(slab + L.th), *r = (double *)(slab + L.r), *pv = (double *)(slab + L.pv);
-  float2 *pf = (float2 *)(slab + L.pf), *tb = (float2 *)(slab + L.tb), *Bd = (float2 *)(slab + L.Bd);
+  float2 *pf = (float2 *)(slab + L.pf), *Bd = (float2 *)(slab + L.Bd);
   float *Bf = (float *)(slab + L.Bf), *rf = (float *)(slab + L.rf);
   int *perm = (int *)(slab + L.perm);
   const int ldd = L.ldd, ldb = L.ldb;
@@ -1077,12 +1085,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParam
     }
     for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta[(size_t)b * o.n_theta + i];
     __syncwarp();
-    const double *tf = th + o.q_a + o.q_c, *tbd = tf + o.q_f;
-    for (int q = lane; q < o.q_b; q += 32) {
-      float h, l;
-      df_split(tbd[q], h, l);
-      tb[q] = make_float2(h, l);
-    }
+    const double *tf = th + o.q_a + o.q_c;
     for (int k = lane; k < m; k += 32) {
       double sf = 0.0;
       for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
@@ -1090,30 +1093,14 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParam
       rf[k] = (float)r[k];
     }
     __syncwarp();
-    // B(mu) = sum_q theta^b_q B_q in double-float; its FP32 rounding for the factorisation
-    for (int e0 = lane; e0 < mm; e0 += 128) {
-      float bh[4], bl[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) bh[t] = bl[t] = 0.f;
-      for (int q = 0; q < o.q_b; ++q) {
-        float2 v[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int e = e0 + 32 * t;
-          v[t] = e < mm ? __ldg(p.B2 + (size_t)q * mm + e) : make_float2(0.f, 0.f);
-        }
-        const float2 c = tb[q];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) df_fma(bh[t], bl[t], c.x, c.y, v[t].x, v[t].y);
-      }
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int e = e0 + 32 * t;
-        if (e < mm) {
-          const int k = e / m, j = e - k * m;
-          Bd[k * ldd + j] = make_float2(bh[t], bl[t]);
-          Bf[k * ldb + j] = bh[t] + bl[t];
-        }
+    // B(mu) (double-float, built at the query's start) and its FP32 rounding for the factorisation
+    {
+      const float2 *bq = p.Bmu + (size_t)b * mm;
+      for (int e = lane; e < mm; e += 32) {
+        const float2 v = __ldg(bq + e);
+        const int k = e / m, j = e - k * m;
+        Bd[k * ldd + j] = v;
+        Bf[k * ldb + j] = v.x + v.y;
       }
     }
     __syncwarp();
@@ -1209,7 +1196,7 @@ static void release_state(rb_ctx *ctx, MixedState *M) {
   for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2,
                   (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
-                  (void *)M->Amu, (void *)M->Asu, (void *)M->Jaug, (void *)M->Rn})
+                  (void *)M->Amu, (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn})
     ctx_free(ctx, q);
   if (M->root == M) {
     for (auto &kv : M->buckets) {
@@ -1370,9 +1357,10 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   if (b_pad <= M->bcap) return RB_OK;
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
                   (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
-                  (void *)M->Asu, (void *)M->Jaug, (void *)M->Rn})
+                  (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn})
     ctx_free(ctx, q);
   M->Jaug = nullptr;
+  M->Bmu = nullptr;
   M->Rn = nullptr;
   M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->ufT = nullptr; M->Jc = nullptr;
   M->Rc = M->Rp = M->Th = M->Fm = M->Asu = nullptr;
@@ -1404,6 +1392,11 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   M->Amu = (float2 *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * m, "As(mu) u")) != RB_OK) return rc;
   M->Asu = (double *)p;
+  if (ctx->ops.m > 0 && ctx->ops.B) {
+    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * ctx->ops.m * ctx->ops.m, "B(mu) (double-float)")) != RB_OK)
+      return rc;
+    M->Bmu = (float2 *)p;
+  }
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
   M->Jaug = (float *)p;
   if ((rc = ctx_alloc(ctx, &p, 16 * (size_t)b_pad, "residual norms")) != RB_OK) return rc;
@@ -1481,19 +1474,22 @@ static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const dou
   pp.nb = M->nb;
   pp.max_iter = ctx->cfg.max_iter;
   pp.info = info;
-  pp.A2 = M->A2;
   pp.Th = M->Th;
   pp.Fm = M->Fm;
-  pp.Amu = M->Amu;
   const int mk = prof_begin(ctx, RB_K_PREP, st);
   k_prep_theta<<<std::max(1, std::min((nq + 7) / 8, ctx->sms * 16)), 256, 0, st>>>(pp);
-  const size_t nn = (size_t)M->nb * M->nb;
-  dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024),
-            (unsigned)std::max(1, std::min((nq + kAsmQ - 1) / kAsmQ, 65535)));
-  k_assemble_a<<<grid, 256, sizeof(float2) * kAsmQ * o.q_a, st>>>(pp);
+  auto affine = [&](const float2 *Q2, int qn, int th_off, size_t nn, float2 *out) {
+    AffineParams ap{nq, ctx->cfg.max_iter, o.n_theta, th_off, qn, nn, info, M->Th, Q2, out};
+    dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024),
+              (unsigned)std::max(1, std::min((nq + kAsmQ - 1) / kAsmQ, 65535)));
+    k_affine_sum<<<grid, 256, sizeof(float2) * kAsmQ * qn, st>>>(ap);
+  };
+  affine(M->A2, o.q_a, 0, (size_t)M->nb * M->nb, M->Amu);  // A(mu), theta^a
+  if (M->B2 && M->Bmu)                                      // B(mu), theta^b
+    affine(M->B2, o.q_b, o.q_a + o.q_c + o.q_f, (size_t)o.m * o.m, M->Bmu);
   prof_end(ctx, mk, st);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_assemble_a");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_affine_sum");
   return RB_OK;
 }
 
@@ -1650,7 +1646,7 @@ static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_as_u attr");
   dim3 agrid((unsigned)((o.m + kAsR - 1) / kAsR), (unsigned)std::max(1, std::min((nq + kAsQ - 1) / kAsQ, 65535)));
   k_as_u<<<agrid, 256, asmem, st>>>(ap);
-  PresSolveParams pp{o, M->Th, nq, M->B2, M->Rp, M->Asu, d_p, info};
+  PresSolveParams pp{o, M->Th, nq, M->Bmu, M->Rp, M->Asu, d_p, info};
   const size_t per_warp = PresSmem(o).total;
   if (o.m <= 32 * kWarpRows && per_warp <= 24 * 1024) {
     const int wpc = std::max(1, std::min(8, (int)((192 * 1024) / per_warp)));
@@ -2152,7 +2148,7 @@ size_t mixed_slot_bytes(const rb_ctx *ctx) {
   const int S = 8;
   return 2 * 3 * Kpad0 + 2 * S * Kpad0 + 8 + 8 * nb + 4 * Npad + 8 * nb + 8 * (size_t)(o.m + 1) +
          8 * nb + 64 + 8 * (size_t)o.n_theta + 8 * nb + 8 * nb * nb + 8 * (size_t)(o.m + 1) +
-         4 * nb * (size_t)aug_ld((int)nb) + 16;
+         4 * nb * (size_t)aug_ld((int)nb) + 16 + 8 * (size_t)o.m * o.m;
 }
 
 // One Newton iteration for every live slot: the contraction work the slots' ladder rungs need,
