@@ -15,12 +15,12 @@
 //  * kPlain: X, W split into BF16 hi + lo parts, x_hi w_hi + x_hi w_lo + x_lo w_hi accumulated in
 //    FP32 (about 16 significant bits); writes T (FP32) -> Jacobian for the LU.
 //  * kSliced: error-free sliced product (after Ozaki, Ogita, Oishi and Rump, 2012). Per segment,
-//    X rows and W are split into S signed 7-bit digit slices on fixed-point grids (per-row
-//    exponent for X, one exponent for W): X = 2^ex sum_i x_i 2^-7i, W = 2^ew sum_j w_j 2^-7j
-//    (S may differ per segment).
-//    A product of two digits is below 2^14, so up to 1024 of them add exactly in FP32. Pairs
+//    X rows and W are split into S balanced base-128 digit slices (|digit| <= 64) on fixed-point
+//    grids (per-row exponent for X, one exponent for W): X = 2^ex sum_i x_i 2^-7i,
+//    W = 2^ew sum_j w_j 2^-7j (S may differ per segment).
+//    A product of two digits is at most 2^12, so up to 4096 of them add exactly in FP32. Pairs
 //    (i, j) with i + j = L share the scale 2^(ex + ew - 7L); each level is accumulated in TMEM
-//    in chunks of at most 1024 terms, every chunk is drained exactly and added, scaled by its
+//    in chunks of at most 4096 terms, every chunk is drained exactly and added, scaled by its
 //    power of two, into per-column double-float sums held in registers; at the end of the tile
 //    the sums are contracted with u_b[j] (double-float) and added into the FP64 output. Pairs
 //    with i + j > S + 1 are dropped (relative truncation ~2^-7S of the fixed-point range).
@@ -40,7 +40,7 @@ namespace rb {
 using namespace tc;
 
 constexpr int kBM = 128, kBK = 64;
-constexpr int kChunkSteps = 16;  // 16 k-blocks of 64 = 1024 exact terms per chunk (7-bit digits)
+constexpr int kChunkSteps = 64;  // 64 k-blocks of 64 = 4096 exact terms per chunk (|digit| <= 64)
 constexpr int kEpiWarps = 16;    // epilogue warps: kEpiParts per TMEM lane quarter
 constexpr int kEpiParts = kEpiWarps / 4;  // column parts of a tile, one per warp of a quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;

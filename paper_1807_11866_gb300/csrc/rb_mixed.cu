@@ -3,7 +3,7 @@
 // Once per query at its start: theta(mu_b), f(mu_b) (k_prep_theta) and A(mu_b), B(mu_b) in
 // double-float (k_affine_sum). Per Newton iteration, for every active query b of the batch:
 //   1. k_build_x: X_b = theta^c(mu_b) (x) u_b as split BF16 (hi, lo) for the Jacobian GEMM; the
-//      7-bit digit slices of theta^c (x) u_b / 2 for the sliced GEMM; u_b as (hi, lo) floats
+//      base-128 digit slices of theta^c (x) u_b / 2 for the sliced GEMM; u_b as (hi, lo) floats
 //      (transposed); R^c_b = 0.
 //   2. k_tc_gemm<kPlain>:  J^c = X W^T on tcgen05 (split BF16, FP32 accumulate) -> Jc (FP32).
 //   3. k_tc_gemm<kSliced>: R^c_b[k] = sum_j u_b[j] (X'_b W^T)[(k,j)] = C_mu(u_b, u_b)[k] from
@@ -130,19 +130,34 @@ static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t c
 static inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 // ---------------------------------------------------------------------------------------
-// signed 7-bit digits of v on the grid 2^(e - 7 i), i = 1..S (|v| < 2^e), truncated toward 0
+// Balanced base-128 digits of the fixed-point magnitude F < 2^(7S - 1): d_S .. d_2 in [-64, 63]
+// (a digit of 64 or more borrows from the next one), d_1 in [0, 64]; every |d| <= 64, so the
+// product of two digits is at most 2^12 and 4096 of them add exactly in FP32. Written with the
+// sign of v to slices 0 .. S-1.
+__device__ __forceinline__ void balanced_digits(long long F, float sg, int S, __nv_bfloat16 *out,
+                                                size_t slice_stride) {
+  for (int i = S; i >= 2; --i) {
+    int r = (int)(F & 127);
+    F >>= kDigitBits;
+    if (r >= 64) {
+      r -= 128;
+      F += 1;
+    }
+    out[(size_t)(i - 1) * slice_stride] = __float2bfloat16_rn(sg * (float)r);
+  }
+  out[0] = __float2bfloat16_rn(sg * (float)F);
+}
+
+// digits of v on the grid 2^(e - 7 i), i = 1..S, with one binade of headroom (|v| < 2^(e-1)),
+// the magnitude truncated toward 0 on the finest grid
 __device__ __forceinline__ void digits7(double v, double scale /* 2^(7S - e) */, int S,
                                         __nv_bfloat16 *out, size_t slice_stride) {
   const long long F = __double2ll_rz(fabs(v) * scale);
-  const float sg = v < 0 ? -1.f : 1.f;
-  for (int i = 1; i <= S; ++i) {
-    const int d = (int)((F >> (kDigitBits * (S - i))) & 127);
-    out[(size_t)(i - 1) * slice_stride] = __float2bfloat16_rn(sg * (float)d);
-  }
+  balanced_digits(F, v < 0 ? -1.f : 1.f, S, out, slice_stride);
 }
 
 // Same digits from the FP64 bit pattern with integer operations only (GB300's FP64 pipe is
-// narrow and its conversions slow). e is the grid exponent (|v| < 2^e).
+// narrow and its conversions slow). e is the grid exponent.
 __device__ __forceinline__ long long fixed_bits(double v, int e, int S) {
   const unsigned long long mag = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
   const int E = (int)(mag >> 52);
@@ -155,12 +170,7 @@ __device__ __forceinline__ long long fixed_bits(double v, int e, int S) {
 
 __device__ __forceinline__ void digits7_int(double v, int e, int S, __nv_bfloat16 *out,
                                             size_t slice_stride) {
-  const long long F = fixed_bits(v, e, S);
-  const float sg = v < 0 ? -1.f : 1.f;
-  for (int i = 1; i <= S; ++i) {
-    const int d = (int)((F >> (kDigitBits * (S - i))) & 127);
-    out[(size_t)(i - 1) * slice_stride] = __float2bfloat16_rn(sg * (float)d);
-  }
+  balanced_digits(fixed_bits(v, e, S), v < 0 ? -1.f : 1.f, S, out, slice_stride);
 }
 
 // exponent e with |v| < 2^e from the bit pattern of a nonnegative maximum (frexp convention)
@@ -369,8 +379,9 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
       mx0 = ured[i] > mx0 ? ured[i] : mx0;
       mx1 = ured[kWarps + i] > mx1 ? ured[kWarps + i] : mx1;
     }
-    // the sliced operand holds x / 2: same digits as x on the grid one binade higher
-    const int ex0 = exp_of_bits(mx0), e0 = ex0 - 1, e1 = exp_of_bits(mx1);
+    // digits on the grid with one binade of headroom (balanced digits); the sliced operand holds
+    // x / 2: the same digits recorded one binade lower
+    const int ex0 = exp_of_bits(mx0) + 1, e0 = ex0 - 1, e1 = exp_of_bits(mx1) + 1;
     const size_t sstride = (size_t)p.b_pad * p.Kpad;
     const size_t jstride = (size_t)p.b_pad * p.Kpad0;
     for (int kap = tid; kap < p.Kpad; kap += blockDim.x) {
@@ -1242,7 +1253,7 @@ static int absmax_exp(rb_ctx *ctx, MixedState *M, const double *x, size_t count,
   memcpy(&dmax, &hm, 8);
   int ex = 0;
   if (dmax > 0) frexp(dmax, &ex);
-  *e_out = ex;
+  *e_out = ex + 1;  // one binade of headroom for the balanced digits
   return RB_OK;
 }
 

@@ -8,7 +8,7 @@ namespace rb {
 
 enum { kPlain = 0, kSliced = 1 };
 constexpr int kTcBN = 128;     // output tile width (columns (k, j))
-constexpr int kDigitBits = 7;  // signed digits |d| <= 127 of the sliced product
+constexpr int kDigitBits = 7;  // base-128 balanced digits (|d| <= 64) of the sliced product
 
 // One tcgen05 GEMM launch. Columns c = k * nj + j (k < nk, j < nj) of W; rows b = queries.
 // K is split in up to two segments with their own fixed-point grids (sliced mode):
