@@ -29,8 +29,12 @@
 // allocates TMEM and issues tcgen05.mma (one lane), warps 2-17 drain the two TMEM accumulator
 // buffers (128 lanes = 128 query rows; four warps per lane quarter split the columns, so that
 // a chunk drains in a quarter of the MMA time it took to fill).
-// Persistent over output tiles (m fastest).
+// Persistent over output tiles, in groups of kGroupM row tiles (rows fastest inside a group).
+// The sliced epilogue reads u_b[j] straight from L2 at the end of a tile, so all shared memory
+// but the barriers goes to the TMA ring.
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "rb_mixed.cuh"
 #include "tc_ptx.cuh"
@@ -45,16 +49,29 @@ constexpr int kEpiWarps = 16;    // epilogue warps: kEpiParts per TMEM lane quar
 constexpr int kEpiParts = kEpiWarps / 4;  // column parts of a tile, one per warp of a quarter
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreadsTc = 64 + kEpiThreads;
+constexpr int kGroupM = 8;  // row tiles per group of the tile order
 
-template <int BN, int STAGES, int UW>
+template <int BN, int STAGES>
 struct TcSmem {
   static constexpr int kTileA = kBM * kBK * 2;
   static constexpr int kTileB = BN * kBK * 2;
   static constexpr int kStage = kTileA + kTileB;
-  static constexpr int kUOff = STAGES * kStage;        // u window: [UW][kBM] float2
-  static constexpr int kBarOff = kUOff + UW * kBM * 8;
+  static constexpr int kBarOff = STAGES * kStage;
   static constexpr int kBytes = kBarOff + 256 + 1024;  // barriers + alignment slack
 };
+
+// Output tile t -> (first row, first column). Tiles run in groups of group_m row tiles, rows
+// fastest inside a group: the CTAs resident at one time share the operand tiles of a few row
+// and column tiles, so both operands stream from L2 when neither fits in it.
+__device__ __forceinline__ void tile_origin(int t, const TcGemmParams &p, int bn, int &m0,
+                                            int &n0) {
+  const int G = p.group_m;
+  const int per = G * p.n_tiles;
+  const int g = t / per, r = t - g * per;
+  const int gsz = min(G, p.m_tiles - g * G);
+  m0 = (g * G + r % gsz) * kBM;
+  n0 = (r / gsz) * bn;
+}
 
 struct Level {
   int seg, kb_off, kb, L, ilo, npairs;
@@ -83,21 +100,19 @@ __device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int i
   return v;
 }
 
-template <int MODE, int BN, int STAGES, int UW>
+template <int MODE, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
               TcGemmParams p) {
   extern __shared__ uint8_t smem_raw[];
-  using SM = TcSmem<BN, STAGES, UW>;
+  using SM = TcSmem<BN, STAGES>;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + SM::kBarOff);
   uint64_t *empty = full + STAGES;
   uint64_t *tfull = empty + STAGES;  // [2]
   uint64_t *tempty = tfull + 2;      // [2]
   uint64_t *mdone = tempty + 2;      // [1]
-  uint64_t *ufull = mdone + 1;       // [1] u window loaded (epilogue threads)
-  uint64_t *uempty = ufull + 1;      // [1] u window no longer read (epilogue threads)
-  uint32_t *tmem_slot = (uint32_t *)(uempty + 1);
+  uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_levels = num_levels(MODE, p);
@@ -114,8 +129,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       mbar_init(&tempty[b], kEpiThreads);
     }
     mbar_init(mdone, 1);
-    mbar_init(ufull, kEpiThreads);
-    mbar_init(uempty, kEpiThreads);
     fence_barrier_init();
     fence_proxy_async();
   }
@@ -139,7 +152,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       uint32_t step = 0;
       bool bad = false;
       for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
-        const int m0 = (t % p.m_tiles) * kBM, n0 = (t / p.m_tiles) * BN;
+        int m0, n0;
+        tile_origin(t, p, BN, m0, n0);
         for (int li = 0; li < n_levels && !bad; ++li) {
           const Level lv = level_of(MODE, p, li);
           const int nsteps = lv.npairs * lv.kb;
@@ -203,32 +217,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       mbar_wait(mdone, 0, nullptr, 4);
     }
   } else {
-    // ---------------- epilogue (warps 2..9) ----------------
+    // ---------------- epilogue (warps 2..17) ----------------
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int half = (warp - 2) >> 2;        // which column part of the tile this warp drains
     const int row = q * 32 + lane;           // row of the tile owned by this thread
     const int et = (warp - 2) * 32 + lane;   // epilogue thread index
     constexpr int HC = BN / kEpiParts;       // columns per thread
-    float2 *uw = (float2 *)(smem + SM::kUOff);
-    uint32_t chunk = 0, tile_it = 0;
+    uint32_t chunk = 0;
     bool bad = false;
-    for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x, ++tile_it) {
-      const int m0 = (t % p.m_tiles) * kBM, n0 = (t / p.m_tiles) * BN;
+    for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
+      int m0, n0;
+      tile_origin(t, p, BN, m0, n0);
       const int b = m0 + row;
       const int nj = p.nj, total = p.nk * p.nj;
-      const int jb = n0 % nj;
-      if (MODE == kSliced) {
-        // window of u_b[j] for the tile's columns, [w][row]; the column parts load alternate
-        // entries and share them (bounded mbarrier handoff, no unbounded named barrier)
-        if (tile_it > 0 && !mbar_wait(uempty, (tile_it - 1) & 1, p.err, 6)) { bad = true; break; }
-        const int wl = nj <= UW ? nj : BN;
-        for (int w = half; w < wl; w += kEpiParts) {
-          const int j = nj <= UW ? w : (jb + w) % nj;
-          uw[w * kBM + row] = p.ufT[(size_t)j * p.b_pad + b];
-        }
-        mbar_arrive(ufull);
-        if (!mbar_wait(ufull, tile_it & 1, p.err, 7)) { bad = true; break; }
-      }
       // sliced mode: per-column double-float sums over all level chunks of this tile, in TMEM
       // columns [2 BN + half 2 HC, +HC) (hi) and [+HC, +2 HC) (lo) of this thread's lane
       const uint32_t tsum = tmem_base + ((uint32_t)(q * 32) << 16) + 2 * BN + half * 2 * HC;
@@ -302,11 +303,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         const double scale = live ? ldexp(1.0, p.xexp[b] + p.wexp[0]) : 0.0;
         const int c_begin = n0 + half * HC;
         int k = c_begin / nj, j = c_begin % nj;
-        int jw = nj <= UW ? j : (j - jb + nj) % nj;
         const int cend = min(HC, total - c_begin);
+        const float2 *ub = p.ufT + b;  // u_b[j] at ub[j b_pad] (row b < b_pad: in bounds)
         float ah = 0.f, al = 0.f;
 #pragma unroll 1
         for (int g = 0; g < HC / 16; ++g) {
+          // u_b[j] of the group's columns: L2-resident, coalesced over the warp's rows
+          float2 u2[16];
+          int jj = j;
+#pragma unroll
+          for (int v = 0; v < 16; ++v) {
+            u2[v] = ub[(size_t)jj * p.b_pad];
+            if (++jj == nj) jj = 0;
+          }
           uint32_t hi[16], lo[16];
           tmem_ld_x16(tsum + g * 16, hi);
           tmem_ld_x16(tsum + HC + g * 16, lo);
@@ -314,22 +323,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 #pragma unroll
           for (int v = 0; v < 16; ++v) {
             if (g * 16 + v < cend) {
-              const float2 u2 = uw[jw * kBM + row];
-              df_fma(ah, al, __uint_as_float(hi[v]), __uint_as_float(lo[v]), u2.x, u2.y);
-              ++jw;
+              df_fma(ah, al, __uint_as_float(hi[v]), __uint_as_float(lo[v]), u2[v].x, u2[v].y);
               if (++j == nj) {
                 if (live) atomicAdd(p.out + (size_t)b * p.nk + k, ((double)ah + (double)al) * scale);
                 ah = al = 0.f;
                 j = 0;
                 ++k;
-                if (nj <= UW) jw = 0;
               }
             }
           }
         }
         if (live && k < p.nk && cend > 0 && (ah != 0.f || al != 0.f))
           atomicAdd(p.out + (size_t)b * p.nk + k, ((double)ah + (double)al) * scale);
-        mbar_arrive(uempty);
       }
     }
   }
@@ -343,32 +348,35 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 }
 
 // ---------------------------------------------------------------------------------------
-template <int MODE, int STAGES, int UW>
+template <int MODE, int STAGES>
 static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
                                const TcGemmParams &p, int grid, cudaStream_t st) {
-  const int smem = TcSmem<kTcBN, STAGES, UW>::kBytes;
-  auto kern = k_tc_gemm<MODE, kTcBN, STAGES, UW>;
+  const int smem = TcSmem<kTcBN, STAGES>::kBytes;
+  auto kern = k_tc_gemm<MODE, kTcBN, STAGES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreadsTc, smem, st>>>(tmX, tmW, p);
   return cudaGetLastError();
 }
 
-// stages: depth of the TMA ring (0: default). Plain: 4 or 6; sliced with a 64-column u window:
-// 3, 4 or 5; sliced with a 128-column window: 3 (the shared-memory limit).
+template <int MODE>
+static cudaError_t launch_stages(const CUtensorMap &tmX, const CUtensorMap &tmW,
+                                 const TcGemmParams &p, int grid, cudaStream_t st, int stages) {
+  if (stages == 4) return launch_impl<MODE, 4>(tmX, tmW, p, grid, st);
+  if (stages == 7) return launch_impl<MODE, 7>(tmX, tmW, p, grid, st);
+  return launch_impl<MODE, 6>(tmX, tmW, p, grid, st);
+}
+
+// stages: depth of the TMA ring, 4, 6 (default) or 7 (7 x 32 KB: the shared-memory limit).
 cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &tmW,
                            const TcGemmParams &p, int sms, cudaStream_t st, int stages) {
   const int tiles = p.m_tiles * p.n_tiles;
   const int grid = tiles < sms ? tiles : sms;
-  if (mode == kPlain)
-    return stages == 6 ? launch_impl<kPlain, 6, 0>(tmX, tmW, p, grid, st)
-                       : launch_impl<kPlain, 4, 0>(tmX, tmW, p, grid, st);
-  if (p.nj <= 64) {
-    if (stages == 3) return launch_impl<kSliced, 3, 64>(tmX, tmW, p, grid, st);
-    if (stages == 5) return launch_impl<kSliced, 5, 64>(tmX, tmW, p, grid, st);
-    return launch_impl<kSliced, 4, 64>(tmX, tmW, p, grid, st);
-  }
-  return launch_impl<kSliced, 3, 128>(tmX, tmW, p, grid, st);
+  TcGemmParams q = p;
+  q.group_m = std::min(p.m_tiles, kGroupM);
+  if (q.m_tiles < 1 || q.n_tiles < 1) return cudaErrorInvalidValue;
+  return mode == kPlain ? launch_stages<kPlain>(tmX, tmW, q, grid, st, stages)
+                        : launch_stages<kSliced>(tmX, tmW, q, grid, st, stages);
 }
 
 }  // namespace rb

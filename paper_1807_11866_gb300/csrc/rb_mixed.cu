@@ -1855,7 +1855,7 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   g.Jc = M->Jc;
   g.nsplit = 3;
   best = 1e30f;
-  for (int stg : {4, 6}) {
+  for (int stg : {4, 6, 7}) {
     if (rc != RB_OK) break;
     const float ms = timed([&]() {
       const cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, stg);
@@ -1870,9 +1870,8 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
   best = 1e30f;
-  for (int stg : {3, 4, 5}) {
+  for (int stg : {4, 6, 7}) {
     if (rc != RB_OK) break;
-    if (M->nb > 64 && stg != 3) continue;
     const float ms = timed([&]() {
       const cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WR.tm, g, ctx->sms, st, stg);
       return e == cudaSuccess ? RB_OK : RB_ERR_CUDA;
