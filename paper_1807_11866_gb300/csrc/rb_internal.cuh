@@ -310,6 +310,17 @@ __device__ __forceinline__ float slot3(const float (&v)[kWarpRows], int s) {
   return s == 0 ? v[0] : (s == 1 ? v[1] : v[2]);
 }
 
+// Element s of a register vector of R lane slots (s warp-uniform or per lane), without local
+// memory: a chain of selects.
+template <typename T, int R>
+__device__ __forceinline__ T pick(const T (&a)[R], int s) {
+  T v = a[0];
+#pragma unroll
+  for (int i = 1; i < R; ++i)
+    if (s == i) v = a[i];
+  return v;
+}
+
 __device__ __forceinline__ float comp4(const float4 &a, int t) {
   return t == 0 ? a.x : (t == 1 ? a.y : (t == 2 ? a.z : a.w));
 }
@@ -341,26 +352,26 @@ __device__ __forceinline__ float4 fms4(float4 a, float l, const float4 &u) {  //
 // panel (U rows, lanes over chunks), then apply one rank-4 update to every other row, so each
 // trailing element passes through shared memory once per 4 steps. pseq (shared, n ints rounded
 // up to 4) receives the pivot row of every step. Row k of the solution is returned in
-// x[k / 32] of lane k % 32 (n <= 96). Returns true if a pivot was zero or not finite.
-__device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x)[kWarpRows],
-                                              int *pseq) {
+// x[k / 32] of lane k % 32 (n <= 32 R). Returns true if a pivot was zero or not finite.
+template <int R>
+__device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x)[R], int *pseq) {
   const int lane = threadIdx.x & 31;
   const int c_end = n >> 2;  // last float4 chunk: the one holding column n
   float4 *M4 = reinterpret_cast<float4 *>(M);
   const int ld4 = ld >> 2;
-  float dinv[kWarpRows];
-  int step[kWarpRows];       // step at which the row was the pivot; n: not yet; -1: no row
+  float dinv[R];
+  int step[R];       // step at which the row was the pivot; n: not yet; -1: no row
 #pragma unroll
-  for (int s = 0; s < kWarpRows; ++s) {
+  for (int s = 0; s < R; ++s) {
     const int r = lane + 32 * s;
     step[s] = r < n ? n : -1;
     dinv[s] = 0.f;
   }
   for (int c0 = 0; 4 * c0 < n; ++c0) {
-    float4 pc[kWarpRows];    // own rows' panel chunk
-    float lm[kWarpRows][4];  // own rows' multipliers of the panel's steps
+    float4 pc[R];    // own rows' panel chunk
+    float lm[R][4];  // own rows' multipliers of the panel's steps
 #pragma unroll
-    for (int s = 0; s < kWarpRows; ++s) {
+    for (int s = 0; s < R; ++s) {
       pc[s] = step[s] >= 0 ? M4[(lane + 32 * s) * ld4 + c0] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int t = 0; t < 4; ++t) lm[s][t] = 0.f;
@@ -373,20 +384,21 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
       const int p = 4 * c0 + t;
       unsigned key = 0;
 #pragma unroll
-      for (int s = 0; s < kWarpRows; ++s) {
+      for (int s = 0; s < R; ++s) {
         const unsigned k = pivot_key(comp4(pc[s], t), lane + 32 * s);
         if (step[s] == n && k > key) key = k;
       }
       key = __reduce_max_sync(0xffffffffu, key);
       const int piv = 255 - (int)(key & 255u), ps = piv >> 5;
-      const float4 pp = shfl4(ps == 0 ? pc[0] : (ps == 1 ? pc[1] : pc[2]), piv & 31);
+      const float4 pp = shfl4(pick(pc, ps), piv & 31);
       const float pv = comp4(pp, t);
-      if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
-      const float rinv = __frcp_rn(pv);
+      // (the fast reciprocal is within 2 ulp below 2^126 in magnitude)
+      if (!(fabsf(pv) > 0.f) || !(fabsf(pv) < 0x1p126f)) return true;
+      const float rinv = __fdividef(1.0f, pv);
       prow[t] = piv;
       if (lane == 0) pseq[p] = piv;
 #pragma unroll
-      for (int s = 0; s < kWarpRows; ++s) {
+      for (int s = 0; s < R; ++s) {
         if (lane + 32 * s == piv) {
           step[s] = p;
           dinv[s] = rinv;
@@ -400,7 +412,7 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
     }
     // panel chunks back (U entries of the pivot rows, the remaining rows' next values)
 #pragma unroll
-    for (int s = 0; s < kWarpRows; ++s)
+    for (int s = 0; s < R; ++s)
       if (step[s] >= 0) M4[(lane + 32 * s) * ld4 + c0] = pc[s];
     // multipliers of the later pivot rows with respect to the earlier ones, in all lanes
     float lp[4][4];
@@ -409,7 +421,10 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
       const int pr = prow[t], ps = pr >> 5;
 #pragma unroll
       for (int t2 = 0; t2 < t; ++t2) {
-        const float v = ps == 0 ? lm[0][t2] : (ps == 1 ? lm[1][t2] : lm[2][t2]);
+        float v = lm[0][t2];
+#pragma unroll
+        for (int s = 1; s < R; ++s)
+          if (ps == s) v = lm[s][t2];
         lp[t][t2] = __shfl_sync(0xffffffffu, v, pr & 31);
       }
     }
@@ -431,7 +446,7 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
     __syncwarp();
     // rank-`steps` update of the rows not yet used as pivots
 #pragma unroll
-    for (int s = 0; s < kWarpRows; ++s) {
+    for (int s = 0; s < R; ++s) {
       if (step[s] != n) continue;
       float4 *row = M4 + (lane + 32 * s) * ld4;
 #pragma unroll 2
@@ -446,16 +461,16 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
     __syncwarp();
   }
   // back substitution in step order: the solution entry of column j comes from row pseq[j]
-  float y[kWarpRows];
+  float y[R];
 #pragma unroll
-  for (int s = 0; s < kWarpRows; ++s) {
+  for (int s = 0; s < R; ++s) {
     const int r = lane + 32 * s;
     y[s] = r < n ? M[r * ld + n] : 0.f;
   }
   for (int c = (n - 1) >> 2; c >= 0; --c) {
-    float4 mc[kWarpRows];
+    float4 mc[R];
 #pragma unroll
-    for (int s = 0; s < kWarpRows; ++s)
+    for (int s = 0; s < R; ++s)
       mc[s] = step[s] >= 0 ? M4[(lane + 32 * s) * ld4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int4 pq = reinterpret_cast<const int4 *>(pseq)[c];
 #pragma unroll
@@ -463,27 +478,30 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
       const int j = 4 * c + t;
       if (j >= n) continue;
       const int pr = t == 0 ? pq.x : (t == 1 ? pq.y : (t == 2 ? pq.z : pq.w));
-      float own[kWarpRows];
+      float own[R];
 #pragma unroll
-      for (int s = 0; s < kWarpRows; ++s) own[s] = y[s] * dinv[s];
-      const float xj = __shfl_sync(0xffffffffu, slot3(own, pr >> 5), pr & 31);
+      for (int s = 0; s < R; ++s) own[s] = y[s] * dinv[s];
+      const float xj = __shfl_sync(0xffffffffu, pick(own, pr >> 5), pr & 31);
 #pragma unroll
-      for (int s = 0; s < kWarpRows; ++s)
+      for (int s = 0; s < R; ++s)
         if (step[s] >= 0 && step[s] < j) y[s] = fmaf(-comp4(mc[s], t), xj, y[s]);
     }
   }
   // row r holds the solution entry of the column it pivoted; gather by column
-  float xr[kWarpRows];
+  float xr[R];
 #pragma unroll
-  for (int s = 0; s < kWarpRows; ++s) xr[s] = y[s] * dinv[s];
+  for (int s = 0; s < R; ++s) xr[s] = y[s] * dinv[s];
 #pragma unroll
-  for (int s = 0; s < kWarpRows; ++s) {
+  for (int s = 0; s < R; ++s) {
     const int k = lane + 32 * s;
     const int pr = k < n ? pseq[k] : 0;
-    const float v0 = __shfl_sync(0xffffffffu, xr[0], pr & 31);
-    const float v1 = __shfl_sync(0xffffffffu, xr[1], pr & 31);
-    const float v2 = __shfl_sync(0xffffffffu, xr[2], pr & 31);
-    x[s] = (pr >> 5) == 0 ? v0 : ((pr >> 5) == 1 ? v1 : v2);
+    float v = 0.f;
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) {
+      const float t = __shfl_sync(0xffffffffu, xr[s2], pr & 31);
+      if ((pr >> 5) == s2) v = t;
+    }
+    x[s] = v;
   }
   return false;
 }

@@ -679,7 +679,11 @@ struct WarpLuSmem {
   }
 };
 
-__global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
+// R lane slots of rows (n <= 32 R). Blocks of at most kLuWarpBlock threads; with two slots the
+// kernel stays within 96 registers, so that 20 warps (5 per scheduler) can be resident.
+constexpr int kLuWarpBlock = 128;
+template <int R>
+__global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(LuParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
   const WarpLuSmem L(p.nb, p.lda);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
@@ -707,15 +711,15 @@ __global__ void __launch_bounds__(kThreads) k_lu_mixed_warp(LuParams p) {
     qi.iters += 1;
     qi.res_norm = rn;
     qi.precision_used = RB_PREC_MIXED;
-    float x[kWarpRows];
+    float x[R];
     if (!isfinite(rn)) {
       qi.status = RB_Q_NONFINITE;
-    } else if (gepp_aug_warp(J, ld, n, x, pseq)) {
+    } else if (gepp_aug_warp<R>(J, ld, n, x, pseq)) {
       qi.status = RB_Q_SINGULAR;
     } else {
       double dl = 0.0;
 #pragma unroll
-      for (int s = 0; s < kWarpRows; ++s) {
+      for (int s = 0; s < R; ++s) {
         const int k = lane + 32 * s;
         if (k < n) {
           const double d = (double)x[s];
@@ -1584,23 +1588,32 @@ static int launch_elimination(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_blocked");
     return RB_OK;
   }
-  // warps per block: the most resident warps per SM that shared memory allows
+  // warps per block: the most resident warps per SM (shared memory and registers)
   const int per_warp = WarpLuSmem(M->nb, lp.lda).per_warp;
-  int wpc = 1, best = 0;
-  for (int c = 1; c <= 8; ++c) {
-    const int blocks = std::min(64 / c, (int)((size_t)ctx->smem_per_sm / ((size_t)c * per_warp + 1024)));
-    if (blocks * c > best && (size_t)c * per_warp <= (size_t)ctx->max_smem) {
+  const bool two = M->nb <= 64;
+  const void *kern = two ? (const void *)k_lu_mixed_warp<2> : (const void *)k_lu_mixed_warp<3>;
+  int wpc = 1, best = 0, best_blocks = 1;
+  for (int c = 1; c <= kLuWarpBlock / 32; ++c) {
+    const size_t sm = (size_t)c * per_warp;
+    if (sm > (size_t)ctx->max_smem) break;
+    int blocks = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * c, sm) != cudaSuccess)
+      return cuda_fail(ctx, cudaGetLastError(), "k_lu_mixed_warp occupancy");
+    if (blocks * c > best) {
       best = blocks * c;
+      best_blocks = std::max(1, blocks);
       wpc = c;
     }
   }
   const size_t smem = (size_t)wpc * per_warp;
-  const int per_sm = std::max(1, std::min(64 / wpc, (int)((size_t)ctx->smem_per_sm / (smem + 1024))));
-  const int grid = std::max(1, std::min((nq + wpc - 1) / wpc, per_sm * ctx->sms));
-  cudaError_t e = cudaFuncSetAttribute(k_lu_mixed_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = std::max(1, std::min((nq + wpc - 1) / wpc, best_blocks * ctx->sms));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp attr");
   const int mk = prof_begin(ctx, RB_K_LU, st);
-  k_lu_mixed_warp<<<grid, 32 * wpc, smem, st>>>(lp);
+  if (two) k_lu_mixed_warp<2><<<grid, 32 * wpc, smem, st>>>(lp);
+  else k_lu_mixed_warp<3><<<grid, 32 * wpc, smem, st>>>(lp);
   prof_end(ctx, mk, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_mixed_warp");
