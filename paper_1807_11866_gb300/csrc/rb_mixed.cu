@@ -68,7 +68,8 @@ struct MixedState {
   double *Asu = nullptr;        // [bcap][m] As(mu) u
   float2 *Bmu = nullptr;        // [bcap][m][m] B(mu) as double-float
   float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices
-  double2 *Rn = nullptr;        // [bcap] residual norms of the assembled systems
+  double2 *Rn = nullptr;        // [bcap] (unused, max(1, ||f(mu)||)) of the queries
+  double *Rg = nullptr;         // [bcap][(nb + 7) / 8] row-group sums of R^2 (in Rn's block)
   CUtensorMap tmXj, tmXd;
   // autotuned launch variants of this bucket (0 = not tuned: defaults), per batch-size class
   struct Tune {
@@ -437,6 +438,8 @@ struct PrepParams {
   const rb_query_info *info;
   double *Th;                   // [nq][n_theta]
   double *Fm;                   // [nq][nb]
+  const int *nsz;               // [nq] sizes, or null: all nb
+  double2 *Rn;                  // [nq]: (0, max(1, ||f(mu)||)) of the starting queries
 };
 
 __device__ __forceinline__ bool starts(const rb_query_info &q, int max_iter) {
@@ -458,11 +461,16 @@ __global__ void k_prep_theta(PrepParams p) {
     }
     __syncwarp();
     const double *tf = th + o.q_a + o.q_c;
+    const int n = p.nsz ? p.nsz[b] : p.nb;
+    double ff = 0.0;
     for (int k = lane; k < p.nb; k += 32) {
       double s = 0.0;
       for (int q = 0; q < o.q_f; ++q) s = fma(tf[q], o.f[(size_t)q * o.n_max + k], s);
       p.Fm[(size_t)b * p.nb + k] = s;
+      if (k < n) ff += s * s;
     }
+    ff = warp_sum(ff);
+    if (lane == 0) p.Rn[b] = make_double2(0.0, fmax(1.0, sqrt(ff)));  // scale of the residual test
     __syncwarp();
   }
 }
@@ -534,7 +542,8 @@ struct LuParams {
   const float2 *Amu;     // [nq][nb * nb] A(mu) as double-float (k_affine_sum)
   const double *Fm;      // [nq][nb] f(mu)
   float *Jaug;           // [nq][nb][lda] augmented Newton matrices [J | -R] (warp path)
-  double2 *Rn;           // [nq]: (||R||, max(1, ||f||)) of the assembled system
+  double2 *Rn;           // [nq]: (unused, max(1, ||f||)), set when the query starts
+  double *Rg;            // [nq][(nb + 7) / 8]: sums of R[k]^2 over the system's row groups
   int lda;
   const float *Jc;       // [b_pad][ldj]
   const double *Rc;      // [b_pad][nb]: C_mu(u, u)
@@ -569,101 +578,125 @@ __host__ __device__ inline int aug_ld(int nb) {
   return ld;
 }
 
-// Rows k0 .. k0 + 7 of the Newton system, by one warp (lanes over columns):
+// Rows k0 .. k0 + 7 of query b's Newton system, by one warp (lanes over column pairs):
 // J[k][:] = fl32(A(mu)[k][:]) + J^c[k][:] and R[k] = A(mu)[k][:] u (double-float) + convection
-// part - f[k]. The 8 rows' loads of a column block are issued before their arithmetic, and the
-// row sums are reduce-scattered over the warp (df_warp_reduce8).
-__device__ __forceinline__ void newton_rows8(const LuParams &p, int rm, int b, int n, int k0,
-                                             const float2 *u2, float *J, int ld, double *R) {
+// part - f[k] (residual source RM). The 8 rows' loads of a column block are issued before their
+// arithmetic, and the row sums are reduce-scattered over the warp (df_warp_reduce8). Rows
+// k >= n are skipped. Returns sum_k R[k]^2 of the group in lane 0 (not EVAL).
+template <int RM, bool EVAL>
+__device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, int k0) {
   const int lane = threadIdx.x & 31;
-  const size_t nb = (size_t)p.nb;
-  const float2 *am = p.Amu + (size_t)b * nb * nb;
-  const float *jc = p.Jc + (size_t)b * p.ldj;
-  const bool with_u = rm != kResZero;
+  const int nb = p.nb;
+  const bool vec = (nb & 1) == 0;  // even rows: 16-byte A(mu) and 8-byte J^c pairs are aligned
+  const float2 *am = p.Amu + ((size_t)b * nb + k0) * nb;
+  const float *jc = p.Jc + (size_t)b * p.ldj + (size_t)k0 * nb;
+  const double *ub = p.u + (size_t)b * p.o.n_max;
+  float *J = EVAL ? nullptr : p.Jaug + ((size_t)b * nb + k0) * p.lda;
+  const int rows = min(8, n - k0);
   float rh[8], rl[8], ch[8], cl[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) rh[r] = rl[r] = ch[r] = cl[r] = 0.f;
-  for (int j = lane; j < n; j += 32) {
-    float2 a[8];
-    float c[8];
+  for (int j = 2 * lane; j < n; j += 64) {
+    const bool two = j + 1 < n;
+    float4 a[8];
+    float2 c[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int k = k0 + r;
-      a[r] = k < n ? __ldg(am + k * nb + j) : make_float2(0.f, 0.f);
-      c[r] = (with_u && k < n) ? __ldg(jc + k * nb + j) : 0.f;
+      a[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      c[r] = make_float2(0.f, 0.f);
+      if (r < rows) {
+        const float2 *ar = am + (size_t)r * nb + j;
+        const float *cr = jc + (size_t)r * nb + j;
+        if (two && vec) {
+          a[r] = __ldg(reinterpret_cast<const float4 *>(ar));
+          if (RM != kResZero) c[r] = __ldg(reinterpret_cast<const float2 *>(cr));
+        } else {
+          const float2 a0 = __ldg(ar), a1 = two ? __ldg(ar + 1) : make_float2(0.f, 0.f);
+          a[r] = make_float4(a0.x, a0.y, a1.x, a1.y);
+          if (RM != kResZero) c[r] = make_float2(__ldg(cr), two ? __ldg(cr + 1) : 0.f);
+        }
+      }
     }
-    const float2 uj = with_u ? u2[j] : make_float2(0.f, 0.f);
+    float uh0 = 0.f, ul0 = 0.f, uh1 = 0.f, ul1 = 0.f;
+    if (RM != kResZero) {
+      df_split(ub[j], uh0, ul0);
+      if (two) df_split(ub[j + 1], uh1, ul1);
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int k = k0 + r;
-      if (k < n) {
-        const float v = (a[r].x + a[r].y) + c[r];
-        if (with_u) df_fma(rh[r], rl[r], a[r].x, a[r].y, uj.x, uj.y);
-        if (rm == kResLow) ch[r] = fmaf(0.5f * c[r], uj.x, ch[r]);
-        if (p.eval_only)
-          p.J_out[((size_t)b * n + k) * n + j] = (double)v;
-        else
-          J[k * ld + j] = v;
+      if (r < rows) {
+        const float v0 = (a[r].x + a[r].y) + c[r].x, v1 = (a[r].z + a[r].w) + c[r].y;
+        if (RM != kResZero) {
+          df_fma(rh[r], rl[r], a[r].x, a[r].y, uh0, ul0);
+          df_fma(rh[r], rl[r], a[r].z, a[r].w, uh1, ul1);
+        }
+        if (RM == kResLow) ch[r] = fmaf(0.5f * c[r].y, uh1, fmaf(0.5f * c[r].x, uh0, ch[r]));
+        if (EVAL) {
+          double *jo = p.J_out + ((size_t)b * n + k0 + r) * n + j;
+          jo[0] = (double)v0;
+          if (two) jo[1] = (double)v1;
+        } else {
+          float *jr = J + (size_t)r * p.lda + j;
+          if (two) *reinterpret_cast<float2 *>(jr) = make_float2(v0, v1);
+          else jr[0] = v0;
+        }
       }
     }
   }
-  if (with_u) df_warp_reduce8(rh, rl);
-  if (rm == kResLow) df_warp_reduce8(ch, cl);
-  const int k = k0 + (lane >> 2);
-  if ((lane & 3) == 0 && k < n) {
-    const double rlin = with_u ? (double)rh[0] + (double)rl[0] : 0.0;
-    const double conv = rm == kResExact ? p.Rc[(size_t)b * nb + k]
-                                        : (rm == kResLow ? (double)ch[0] + (double)cl[0] : 0.0);
-    R[k] = rlin + conv - p.Fm[(size_t)b * nb + k];
+  if (RM != kResZero) df_warp_reduce8(rh, rl);
+  if (RM == kResLow) df_warp_reduce8(ch, cl);
+  const int r = lane >> 2, k = k0 + r;
+  double r2 = 0.0;
+  if ((lane & 3) == 0 && r < rows) {
+    const double rlin = RM != kResZero ? (double)rh[0] + (double)rl[0] : 0.0;
+    const double conv = RM == kResExact ? p.Rc[(size_t)b * nb + k]
+                                        : (RM == kResLow ? (double)ch[0] + (double)cl[0] : 0.0);
+    const double R = rlin + conv - p.Fm[(size_t)b * nb + k];
+    if (EVAL) {
+      p.R_out[(size_t)b * n + k] = R;
+    } else {
+      float *row = J + (size_t)r * p.lda;
+      row[n] = (float)(-R);
+      const int c_pad = ((n >> 2) << 2) + 4;  // columns n + 1 .. c_pad - 1 pad the last chunk
+      for (int c = n + 1; c < c_pad; ++c) row[c] = 0.f;
+      r2 = R * R;
+    }
   }
+  return warp_sum(r2);
 }
 
-// Newton system of every active query, one warp per query with lanes over columns: the
-// augmented matrix [J | -R] (FP32, row stride lda, the right-hand side in column n, zero
-// padding up to the next multiple of 4) and the residual norms. Small shared footprint, so
-// many warps keep the A(mu) and J^c streams in flight. With eval_only, J and R go to
-// J_out / R_out in FP64 instead.
-__global__ void __launch_bounds__(kThreads, 3) k_newton_system(LuParams p) {
-  extern __shared__ __align__(16) uint8_t smb[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  double *R = reinterpret_cast<double *>(smb + (size_t)w * 16 * p.nb);
-  float2 *u2 = reinterpret_cast<float2 *>(R + p.nb);
-  for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
+// Newton systems of the active queries: one warp per (query, group of 8 rows), so the work
+// splits evenly over the resident warps whatever the batch size. Writes the augmented matrix
+// [J | -R] (FP32, row stride lda, the right-hand side in column n, zero padding up to the next
+// multiple of 4) and the group's sum of R[k]^2 to Rg[b][g] (the elimination adds the groups in
+// order: deterministic). With EVAL, J and R go to J_out / R_out in FP64 instead.
+template <bool EVAL>
+__global__ void __launch_bounds__(kThreads, 2) k_newton_system(LuParams p) {
+  const int lane = threadIdx.x & 31;
+  const int G = (p.nb + 7) >> 3;
+  const long long units = (long long)p.nq * G;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < units; t += nw) {
+    const int b = (int)(t / G), g = (int)(t - (long long)b * G);
     const rb_query_info qi = p.info[b];
     if (!is_active(qi, p.max_iter)) continue;
     const int n = p.nsz ? p.nsz[b] : p.nb;
-    const double *ub = p.u + (size_t)b * p.o.n_max;
+    const int k0 = 8 * g;
+    if (k0 >= n) continue;
     const int rm = rung_of(p.rmode, qi.iters);
-    if (rm != kResZero)
-      for (int k = lane; k < n; k += 32) {
-        float h, l;
-        df_split(ub[k], h, l);
-        u2[k] = make_float2(h, l);
-      }
-    __syncwarp();
-    float *Jb = p.eval_only ? nullptr : p.Jaug + (size_t)b * p.nb * p.lda;
-    for (int k0 = 0; k0 < n; k0 += 8) newton_rows8(p, rm, b, n, k0, u2, Jb, p.lda, R);
-    __syncwarp();
-    if (p.eval_only) {
-      for (int k = lane; k < n; k += 32) p.R_out[(size_t)b * n + k] = R[k];
-      __syncwarp();
-      continue;
-    }
-    const double *fb = p.Fm + (size_t)b * p.nb;
-    const int c_pad = ((n >> 2) << 2) + 4;  // columns n + 1 .. c_pad - 1 pad the last chunk
-    double rl = 0.0, fl = 0.0;
-    for (int k = lane; k < n; k += 32) {
-      rl += R[k] * R[k];
-      fl += fb[k] * fb[k];
-      float *row = Jb + (size_t)k * p.lda;
-      row[n] = (float)(-R[k]);
-      for (int c = n + 1; c < c_pad; ++c) row[c] = 0.f;
-    }
-    rl = warp_sum(rl);
-    fl = warp_sum(fl);
-    if (lane == 0) p.Rn[b] = make_double2(sqrt(rl), fmax(1.0, sqrt(fl)));
-    __syncwarp();
+    const double r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL>(p, b, n, k0)
+                      : rm == kResLow ? newton_rows8<kResLow, EVAL>(p, b, n, k0)
+                                      : newton_rows8<kResExact, EVAL>(p, b, n, k0);
+    if (!EVAL && lane == 0) p.Rg[(size_t)b * G + g] = r2;
   }
+}
+
+// ||R|| of query b from its row groups' sums of squares, added in group order.
+__device__ __forceinline__ double residual_norm(const LuParams &p, int b, int n) {
+  const int G = (p.nb + 7) >> 3, gn = (n + 7) >> 3;
+  double s = 0.0;
+  for (int g = 0; g < gn; ++g) s += p.Rg[(size_t)b * G + g];
+  return sqrt(s);
 }
 
 // Warp-per-query elimination of the systems k_newton_system assembled: copy the query's
@@ -698,8 +731,7 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
     const int n = p.nsz ? p.nsz[b] : p.nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
-    const double2 rr = p.Rn[b];
-    const double rn = rr.x, fscale = rr.y;
+    const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
     {
       const float4 *src = reinterpret_cast<const float4 *>(p.Jaug + (size_t)b * p.nb * ld);
       float4 *dst = reinterpret_cast<float4 *>(J);
@@ -794,8 +826,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
     const int n = p.nsz ? p.nsz[b] : nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
-    const double2 rr = p.Rn[b];
-    const double rn = rr.x, fscale = rr.y;
+    const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
     float *M = p.Jaug + (size_t)b * nb * lda;
     bool sing = !isfinite(rn);
     for (int k0 = 0; k0 < n && !sing; k0 += kPB) {
@@ -1377,6 +1408,7 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   M->Jaug = nullptr;
   M->Bmu = nullptr;
   M->Rn = nullptr;
+  M->Rg = nullptr;
   M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->ufT = nullptr; M->Jc = nullptr;
   M->Rc = M->Rp = M->Th = M->Fm = M->Asu = nullptr;
   M->Amu = nullptr;
@@ -1414,8 +1446,11 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   }
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
   M->Jaug = (float *)p;
-  if ((rc = ctx_alloc(ctx, &p, 16 * (size_t)b_pad, "residual norms")) != RB_OK) return rc;
+  const size_t groups = (size_t)(M->nb + 7) / 8;
+  if ((rc = ctx_alloc(ctx, &p, 16 * (size_t)b_pad + 8 * (size_t)b_pad * groups, "residual norms")) != RB_OK)
+    return rc;
   M->Rn = (double2 *)p;
+  M->Rg = (double *)(M->Rn + b_pad);
   // zero once so that padded rows never hold NaN bit patterns
   cudaMemsetAsync(M->Xj, 0, 2 * 3 * xs0, ctx->stream);
   cudaMemsetAsync(M->Xd, 0, 2 * xs * M->Smax, ctx->stream);
@@ -1479,7 +1514,7 @@ static TcGemmParams gemm_params(MixedState *M, int nq) {
 
 // theta rows, f(mu) and A(mu) of the queries that start (active, iteration count 0).
 static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const double *d_theta,
-                       int nq, const rb_query_info *info, cudaStream_t st) {
+                       int nq, const int *nsz, const rb_query_info *info, cudaStream_t st) {
   const DevOps &o = ctx->ops;
   PrepParams pp{};
   pp.o = o;
@@ -1491,6 +1526,8 @@ static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const dou
   pp.info = info;
   pp.Th = M->Th;
   pp.Fm = M->Fm;
+  pp.nsz = nsz;
+  pp.Rn = M->Rn;
   const int mk = prof_begin(ctx, RB_K_PREP, st);
   k_prep_theta<<<std::max(1, std::min((nq + 7) / 8, ctx->sms * 16)), 256, 0, st>>>(pp);
   auto affine = [&](const float2 *Q2, int qn, int th_off, size_t nn, float2 *out) {
@@ -1550,12 +1587,15 @@ static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStrea
   lp.Fm = M->Fm;
   lp.Jaug = M->Jaug;
   lp.Rn = M->Rn;
+  lp.Rg = M->Rg;
   lp.lda = aug_ld(M->nb);
   {
-    const size_t smem = 8 * (size_t)16 * M->nb;
-    const int grid = std::max(1, std::min((nq + 7) / 8, ctx->sms * 8));
+    // one warp per (query, 8-row group), two blocks of 8 warps per SM, grid-stride
+    const long long units = (long long)nq * ((M->nb + 7) / 8);
+    const int grid = (int)std::max(1LL, std::min((units + kWarps - 1) / kWarps, 2LL * ctx->sms));
     const int mk = prof_begin(ctx, RB_K_SYSTEM, st);
-    k_newton_system<<<grid, kThreads, smem, st>>>(lp);
+    if (lp.eval_only) k_newton_system<true><<<grid, kThreads, 0, st>>>(lp);
+    else k_newton_system<false><<<grid, kThreads, 0, st>>>(lp);
     prof_end(ctx, mk, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
@@ -1737,7 +1777,7 @@ static int solve_prologue(rb_ctx *ctx, const std::vector<Part> &parts, cudaStrea
     prof_end(ctx, mk, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
-    const int rc = launch_prep(ctx, pt.M, a.mu, a.theta, a.nq, a.info, st);
+    const int rc = launch_prep(ctx, pt.M, a.mu, a.theta, a.nq, a.n, a.info, st);
     if (rc != RB_OK) return rc;
   }
   return RB_OK;
@@ -1776,8 +1816,8 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, int *words, int max_it
 // ---- autotuner ------------------------------------------------------------------------------
 // Synthetic, well-conditioned systems of the bucket's shape for timing the elimination variants:
 // [J | -R] = [4 I + noise | 1], unit norms, every query active on the FP64-residual rung.
-__global__ void k_tune_fill(int nq, int nb, int lda, float *Jaug, double2 *Rn, rb_query_info *info,
-                            double *u, int ldu, int max_iter) {
+__global__ void k_tune_fill(int nq, int nb, int lda, float *Jaug, double2 *Rn, double *Rg,
+                            rb_query_info *info, double *u, int ldu, int max_iter) {
   const size_t total = (size_t)nq * nb * lda;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -1788,7 +1828,9 @@ __global__ void k_tune_fill(int nq, int nb, int lda, float *Jaug, double2 *Rn, r
     Jaug[e] = c < nb ? (c == r ? 4.f + v : v) : (c == nb ? 1.f : 0.f);
   }
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nq; b += gridDim.x * blockDim.x) {
-    Rn[b] = make_double2(1.0, 1.0);
+    Rn[b] = make_double2(0.0, 1.0);
+    const int G = (nb + 7) / 8;
+    for (int g = 0; g < G; ++g) Rg[(size_t)b * G + g] = g == 0 ? 1.0 : 0.0;
     rb_query_info q = {RB_Q_NOT_CONVERGED, 2, RB_PREC_MIXED, 0, 0.0, 0.0};
     (void)max_iter;
     info[b] = q;
@@ -1847,11 +1889,12 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   lp.rmode = kResExact;
   lp.Jaug = M->Jaug;
   lp.Rn = M->Rn;
+  lp.Rg = M->Rg;
   lp.lda = aug_ld(M->nb);
   float best = 1e30f;
   for (int kind = (M->nb <= kWarpLuMaxN ? 1 : 2); kind <= 3; ++kind) {
     const float ms = timed([&]() {
-      k_tune_fill<<<ctx->sms * 4, 256, 0, st>>>(cnt, M->nb, lp.lda, M->Jaug, M->Rn, lp.info, lp.u, o.n_max, 0);
+      k_tune_fill<<<ctx->sms * 4, 256, 0, st>>>(cnt, M->nb, lp.lda, M->Jaug, M->Rn, M->Rg, lp.info, lp.u, o.n_max, 0);
       cudaEventRecord(e0, st);  // time the elimination only
       return launch_elimination(ctx, M, lp, cnt, st, kind);
     });
@@ -2171,7 +2214,7 @@ size_t mixed_slot_bytes(const rb_ctx *ctx) {
   const int S = 8;
   return 2 * 3 * Kpad0 + 2 * S * Kpad0 + 8 + 8 * nb + 4 * Npad + 8 * nb + 8 * (size_t)(o.m + 1) +
          8 * nb + 64 + 8 * (size_t)o.n_theta + 8 * nb + 8 * nb * nb + 8 * (size_t)(o.m + 1) +
-         4 * nb * (size_t)aug_ld((int)nb) + 16 + 8 * (size_t)o.m * o.m;
+         4 * nb * (size_t)aug_ld((int)nb) + 16 + 8 * ((nb + 7) / 8) + 8 * (size_t)o.m * o.m;
 }
 
 // One Newton iteration for every live slot: the contraction work the slots' ladder rungs need,
@@ -2181,7 +2224,7 @@ int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, dou
   MixedState *M = ctx->mixed;
   int rc;
   cudaMemsetAsync(M->dev_words, 0, 4, st);
-  if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
+  if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, d_n, info, st)) != RB_OK) return rc;
   if (need_jacobian && (rc = mixed_contract(ctx, M, nq, d_n, d_u, info, need_exact, st)) != RB_OK)
     return rc;
   const SolveArgs a{d_mu, nullptr, nq, d_n, d_u, nullptr, info};
@@ -2225,7 +2268,7 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
   cudaMemsetAsync(M->dev_words, 0, 8, st);
-  if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, info, st)) != RB_OK) return rc;
+  if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, nsz, info, st)) != RB_OK) return rc;
   if ((rc = mixed_contract(ctx, M, nq, nsz, uw, info, true, st)) != RB_OK) return rc;
   const SolveArgs a{d_mu, nullptr, nq, nsz, uw, nullptr, info};
   LuParams lp = solve_lu_params(ctx, M, a);
