@@ -308,7 +308,7 @@ __global__ void k_mixed_init(int nq, int nm, const int *nsz, double *u, rb_query
 
 struct BuildXParams {
   DevOps o;
-  const double *mu, *theta;
+  const double *theta;  // [nq][n_theta] per-query theta rows
   const int *nsz;
   int nq, nb, Kpad0, Kpad, S0, S1, b_pad, max_iter, mode;  // mode 0: active, 1: converged
   int digits;       // 1: also write the digit slices, exponents and u pairs (sliced GEMM)
@@ -331,99 +331,105 @@ __device__ __forceinline__ int exp_of_max(double m) {
   return e;
 }
 
+// Balanced digits of two neighbouring elements, stored as BF16 pairs (4-byte stores).
+__device__ __forceinline__ void digits_pair(double v0, double v1, int e, int S, __nv_bfloat16 *out,
+                                            size_t slice_stride) {
+  long long F0 = fixed_bits(v0, e, S), F1 = fixed_bits(v1, e, S);
+  const float s0 = v0 < 0 ? -1.f : 1.f, s1 = v1 < 0 ? -1.f : 1.f;
+  for (int i = S; i >= 1; --i) {
+    int r0 = (int)F0, r1 = (int)F1;
+    if (i > 1) {
+      r0 = (int)(F0 & 127);
+      r1 = (int)(F1 & 127);
+      F0 >>= kDigitBits;
+      F1 >>= kDigitBits;
+      if (r0 >= 64) { r0 -= 128; F0 += 1; }
+      if (r1 >= 64) { r1 -= 128; F1 += 1; }
+    }
+    *reinterpret_cast<__nv_bfloat162 *>(out + (size_t)(i - 1) * slice_stride) =
+        __floats2bfloat162_rn(s0 * (float)r0, s1 * (float)r1);
+  }
+}
+
+// X operands of one Newton iteration, one warp per query (lanes over pairs of K columns):
+// the split BF16 rows of theta^c (x) u for the Jacobian GEMM and, with `digits`, the digit
+// slices of theta^c (x) u / 2 and theta^a on their grids, the row exponents, u as float pairs
+// (transposed) and a zeroed output row for the sliced GEMM. theta comes from the per-query rows.
 __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
-  __shared__ double th[4 * RB_Q_MAX];
-  __shared__ double red[2 * kWarps];
   const DevOps &o = p.o;
-  const int tid = threadIdx.x;
-  for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < p.nq; b += nw) {
     const rb_query_info qi = p.info[b];
     const bool want = p.mode == 0 ? is_active(qi, p.max_iter) : qi.status == RB_Q_OK;
     if (!want) continue;
     const int n = p.nsz ? p.nsz[b] : o.n_max;
-    if (p.theta) {
-      for (int i = tid; i < o.n_theta; i += blockDim.x) th[i] = p.theta[(size_t)b * o.n_theta + i];
-    } else {
-      theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
-    }
-    __syncthreads();
-    const double *ta = th, *tc = th + o.q_a;
+    const double *ta = p.theta + (size_t)b * o.n_theta, *tc = ta + o.q_a;
     const double *ub = p.u + (size_t)b * o.n_max;
+    const int nk = o.q_c * p.nb;
+    auto xval = [&](int kap) -> double {  // (theta^c (x) u)[kap], zero past the query's size
+      if (kap >= nk) return 0.0;
+      const int q = kap / p.nb, l = kap - q * p.nb;
+      return l < n ? tc[q] * ub[l] : 0.0;
+    };
     // grid exponents from the integer bit patterns (|x| orders like its bits)
-    unsigned long long m0 = 0, m1 = 0;
     const unsigned long long absmask = 0x7FFFFFFFFFFFFFFFull;
-    for (int kap = tid; kap < o.q_c * p.nb; kap += blockDim.x) {
-      const int q = kap / p.nb, l = kap % p.nb;
-      if (l < n) {
-        const unsigned long long v = (unsigned long long)__double_as_longlong(tc[q] * ub[l]) & absmask;
+    unsigned long long m0 = 0, m1 = 0;
+    if (p.digits) {
+      for (int kap = lane; kap < nk; kap += 32) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(xval(kap)) & absmask;
         m0 = v > m0 ? v : m0;
       }
-    }
-    for (int q = tid; q < o.q_a; q += blockDim.x) {
-      const unsigned long long v = (unsigned long long)__double_as_longlong(ta[q]) & absmask;
-      m1 = v > m1 ? v : m1;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      const unsigned long long a = __shfl_xor_sync(0xffffffffu, m0, off);
-      const unsigned long long c = __shfl_xor_sync(0xffffffffu, m1, off);
-      m0 = a > m0 ? a : m0;
-      m1 = c > m1 ? c : m1;
-    }
-    unsigned long long *ured = reinterpret_cast<unsigned long long *>(red);
-    if ((tid & 31) == 0) {
-      ured[tid >> 5] = m0;
-      ured[kWarps + (tid >> 5)] = m1;
-    }
-    __syncthreads();
-    unsigned long long mx0 = 0, mx1 = 0;
-    for (int i = 0; i < kWarps; ++i) {
-      mx0 = ured[i] > mx0 ? ured[i] : mx0;
-      mx1 = ured[kWarps + i] > mx1 ? ured[kWarps + i] : mx1;
+      for (int q = lane; q < o.q_a; q += 32) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(ta[q]) & absmask;
+        m1 = v > m1 ? v : m1;
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, m0, off);
+        const unsigned long long c = __shfl_xor_sync(0xffffffffu, m1, off);
+        m0 = a > m0 ? a : m0;
+        m1 = c > m1 ? c : m1;
+      }
     }
     // digits on the grid with one binade of headroom (balanced digits); the sliced operand holds
     // x / 2: the same digits recorded one binade lower
-    const int ex0 = exp_of_bits(mx0) + 1, e0 = ex0 - 1, e1 = exp_of_bits(mx1) + 1;
+    const int ex0 = exp_of_bits(m0) + 1, e0 = ex0 - 1, e1 = exp_of_bits(m1) + 1;
     const size_t sstride = (size_t)p.b_pad * p.Kpad;
     const size_t jstride = (size_t)p.b_pad * p.Kpad0;
-    for (int kap = tid; kap < p.Kpad; kap += blockDim.x) {
+    // Kpad0 and Kpad are multiples of 64: a pair never straddles the segment boundary
+    for (int kap = 2 * lane; kap < p.Kpad; kap += 64) {
       const size_t off = (size_t)b * p.Kpad + kap;
       if (kap < p.Kpad0) {
-        double x = 0.0;
-        if (kap < o.q_c * p.nb) {
-          const int q = kap / p.nb, l = kap % p.nb;
-          if (l < n) x = tc[q] * ub[l];
-        }
+        const double x0 = xval(kap), x1 = xval(kap + 1);
         if (p.mode == 0) {
           // split BF16 operand of the Jacobian GEMM: [x_hi | x_hi | x_lo]
-          const float xf = (float)x;
-          const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
-          __nv_bfloat16 *xj = p.Xj + (size_t)b * p.Kpad0 + kap;
+          const float f0 = (float)x0, f1 = (float)x1;
+          const __nv_bfloat162 hi = __floats2bfloat162_rn(f0, f1);
+          const __nv_bfloat162 lo =
+              __floats2bfloat162_rn(f0 - __low2float(hi), f1 - __high2float(hi));
+          __nv_bfloat162 *xj = reinterpret_cast<__nv_bfloat162 *>(p.Xj + (size_t)b * p.Kpad0 + kap);
           xj[0] = hi;
-          xj[jstride] = hi;
-          xj[2 * jstride] = lo;
+          xj[jstride / 2] = hi;
+          xj[jstride] = lo;
         }
-        if (p.digits) digits7_int(x, ex0, p.S0, p.Xd + off, sstride);
+        if (p.digits) digits_pair(x0, x1, ex0, p.S0, p.Xd + off, sstride);
       } else if (p.digits) {
         const int q = kap - p.Kpad0;
-        digits7_int(q < o.q_a ? ta[q] : 0.0, e1, p.S1, p.Xd + off, sstride);
+        digits_pair(q < o.q_a ? ta[q] : 0.0, q + 1 < o.q_a ? ta[q + 1] : 0.0, e1, p.S1, p.Xd + off,
+                    sstride);
       }
     }
-    if (!p.digits) {
-      __syncthreads();
-      continue;
-    }
-    for (int j = tid; j < p.nb; j += blockDim.x) {
+    if (!p.digits) continue;
+    for (int j = lane; j < p.nb; j += 32) {
       const double v = j < n ? ub[j] : 0.0;
       const float hi = (float)v;
       p.ufT[(size_t)j * p.b_pad + b] = make_float2(hi, (float)(v - (double)hi));
     }
-    for (int k = tid; k < p.nout; k += blockDim.x) p.out[(size_t)b * p.nout + k] = 0.0;
-    if (tid == 0) {
+    for (int k = lane; k < p.nout; k += 32) p.out[(size_t)b * p.nout + k] = 0.0;
+    if (lane == 0) {
       p.xexp[b] = e0;
       p.xexp[p.b_pad + b] = e1;
     }
-    __syncthreads();
   }
 }
 
@@ -1469,7 +1475,6 @@ static int launch_build_x(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
                           cudaStream_t st) {
   BuildXParams bx{};
   bx.o = ctx->ops;
-  bx.mu = nullptr;
   bx.theta = M->Th;
   bx.nsz = d_n;
   bx.nq = nq;
@@ -1491,7 +1496,7 @@ static int launch_build_x(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   bx.out = out;
   bx.nout = nout;
   const int mk = prof_begin(ctx, RB_K_BUILD_X, st);
-  k_build_x<<<std::max(1, std::min(nq, ctx->sms * 8)), kThreads, 0, st>>>(bx);
+  k_build_x<<<std::max(1, std::min((nq + kWarps - 1) / kWarps, ctx->sms * 8)), kThreads, 0, st>>>(bx);
   prof_end(ctx, mk, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_build_x");
