@@ -51,10 +51,11 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreadsTc = 64 + kEpiThreads;
 constexpr int kGroupM = 8;  // row tiles per group of the tile order
 
-template <int BN, int STAGES>
+// PAIR: the CTA holds half of the B tile (the pair's MMA reads the other half from the peer).
+template <int BN, int STAGES, bool PAIR>
 struct TcSmem {
   static constexpr int kTileA = kBM * kBK * 2;
-  static constexpr int kTileB = BN * kBK * 2;
+  static constexpr int kTileB = (PAIR ? BN / 2 : BN) * kBK * 2;
   static constexpr int kStage = kTileA + kTileB;
   static constexpr int kBarOff = STAGES * kStage;
   static constexpr int kBytes = kBarOff + 256 + 1024;  // barriers + alignment slack
@@ -63,13 +64,14 @@ struct TcSmem {
 // Output tile t -> (first row, first column). Tiles run in groups of group_m row tiles, rows
 // fastest inside a group: the CTAs resident at one time share the operand tiles of a few row
 // and column tiles, so both operands stream from L2 when neither fits in it.
-__device__ __forceinline__ void tile_origin(int t, const TcGemmParams &p, int bn, int &m0,
+// bm: rows of an output tile (128, or 256 for a CTA pair).
+__device__ __forceinline__ void tile_origin(int t, const TcGemmParams &p, int bm, int bn, int &m0,
                                             int &n0) {
   const int G = p.group_m;
   const int per = G * p.n_tiles;
   const int g = t / per, r = t - g * per;
   const int gsz = min(G, p.m_tiles - g * G);
-  m0 = (g * G + r % gsz) * kBM;
+  m0 = (g * G + r % gsz) * bm;
   n0 = (r / gsz) * bn;
 }
 
@@ -100,12 +102,18 @@ __device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int i
   return v;
 }
 
-template <int MODE, int BN, int STAGES>
+// PAIR: clusters of two CTAs share each 256-row output tile through tcgen05 .cta_group::2
+// (the leader, rank 0, issues the M = 256 MMAs; each CTA loads its 128 rows of X and half of
+// the W tile into its own shared memory, signalling the leader's barriers, and drains its own
+// TMEM). p.m_tiles then counts 256-row tiles.
+template <int MODE, int BN, int STAGES, bool PAIR>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
               TcGemmParams p) {
   extern __shared__ uint8_t smem_raw[];
-  using SM = TcSmem<BN, STAGES>;
+  using SM = TcSmem<BN, STAGES, PAIR>;
+  constexpr int kBMT = PAIR ? 2 * kBM : kBM;  // rows of an output tile
+  constexpr int kBH = PAIR ? BN / 2 : BN;     // W rows this CTA loads per tile
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + SM::kBarOff);
   uint64_t *empty = full + STAGES;
@@ -118,6 +126,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int n_levels = num_levels(MODE, p);
   const int chunk_steps = (MODE == kPlain) ? (1 << 30) : kChunkSteps;
   const int num_tiles = p.m_tiles * p.n_tiles;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;  // 0: the pair's leader
+  const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int t_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kEpiThreads);
+      mbar_init(&tempty[b], PAIR ? 2 * kEpiWarps : kEpiThreads);  // pair: one arrive per warp
     }
     mbar_init(mdone, 1);
     fence_barrier_init();
@@ -136,11 +147,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   // per-column double-float sums (hi, lo) of each epilogue column part
   constexpr uint32_t kTmemCols = MODE == kSliced ? 4 * BN : 2 * BN;
   if (warp == 1) {
-    tmem_alloc(tmem_slot, kTmemCols);
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(tmem_slot, kTmemCols);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(tmem_slot, kTmemCols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  __syncwarp();
+  if (PAIR) cluster_sync();  // barriers initialised and TMEM allocated in both CTAs
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -151,9 +169,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tma_prefetch_desc(&tmW);
       uint32_t step = 0;
       bool bad = false;
-      for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
+      for (int t = t_first; t < num_tiles && !bad; t += t_step) {
         int m0, n0;
-        tile_origin(t, p, BN, m0, n0);
+        tile_origin(t, p, kBMT, BN, m0, n0);
+        const int mr = m0 + (int)rank * kBM, nr = n0 + (int)rank * kBH;  // this CTA's part
         for (int li = 0; li < n_levels && !bad; ++li) {
           const Level lv = level_of(MODE, p, li);
           const int nsteps = lv.npairs * lv.kb;
@@ -167,25 +186,39 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             // plain split products: (x_hi, w_hi), (x_hi, w_lo), (x_lo, w_hi)
             const int xi = (MODE == kPlain) ? pr : (lv.ilo + pr - 1);
             const int wj = (MODE == kPlain) ? (pr == 1 ? 1 : 0) : (lv.L - (lv.ilo + pr) - 1);
-            mbar_expect_tx(&full[s], SM::kStage);
-            tma_load_2d(sa, &tmX, &full[s], kk * kBK, xi * p.b_pad + m0);
-            tma_load_2d(sb, &tmW, &full[s], kk * kBK, wj * p.n_pad + n0);
+            if (PAIR) {
+              // both CTAs' loads complete on the leader's barrier, which expects all the bytes
+              const uint32_t cbar = mapa_shared(smem_u32(&full[s]), 0);
+              if (rank == 0) mbar_expect_tx(&full[s], 2 * SM::kStage);
+              tma_load_2d_pair(sa, &tmX, cbar, kk * kBK, xi * p.b_pad + mr);
+              tma_load_2d_pair(sb, &tmW, cbar, kk * kBK, wj * p.n_pad + nr);
+            } else {
+              mbar_expect_tx(&full[s], SM::kStage);
+              tma_load_2d(sa, &tmX, &full[s], kk * kBK, xi * p.b_pad + mr);
+              tma_load_2d(sb, &tmW, &full[s], kk * kBK, wj * p.n_pad + nr);
+            }
           }
         }
       }
       if (bad) {  // let loads already in flight land before the CTA exits
-        const uint32_t last = step;
-        for (uint32_t st = (last > (uint32_t)STAGES ? last - STAGES : 0); st < last; ++st)
-          mbar_wait(&full[st % STAGES], (st / STAGES) & 1, nullptr, 1);
+        if (PAIR) {  // they complete on the leader's barriers: give them a fixed grace time
+          const uint64_t t0 = globaltimer();
+          while (globaltimer() - t0 < 100000ull) {
+          }
+        } else {
+          const uint32_t last = step;
+          for (uint32_t st = (last > (uint32_t)STAGES ? last - STAGES : 0); st < last; ++st)
+            mbar_wait(&full[st % STAGES], (st / STAGES) & 1, nullptr, 1);
+        }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(kBMT, BN);
       uint32_t step = 0, chunk = 0;
       bool bad = false;
-      for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
+      for (int t = t_first; t < num_tiles && !bad; t += t_step) {
         for (int li = 0; li < n_levels && !bad; ++li) {
           const Level lv = level_of(MODE, p, li);
           const int nsteps = lv.npairs * lv.kb;
@@ -204,31 +237,37 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
               const uint32_t sa = smem_u32(smem + s * SM::kStage);
               const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sa + SM::kTileA);
 #pragma unroll
-              for (int k4 = 0; k4 < kBK / 16; ++k4)
-                mma_bf16(dt, ad + 2 * k4, bd + 2 * k4, idesc, (idx > c0 || k4 > 0) ? 1u : 0u);
-              mma_commit(&empty[s]);
+              for (int k4 = 0; k4 < kBK / 16; ++k4) {
+                if (PAIR) mma_bf16_pair(dt, ad + 2 * k4, bd + 2 * k4, idesc, (idx > c0 || k4 > 0) ? 1u : 0u);
+                else mma_bf16(dt, ad + 2 * k4, bd + 2 * k4, idesc, (idx > c0 || k4 > 0) ? 1u : 0u);
+              }
+              if (PAIR) mma_commit_pair(&empty[s]);  // frees the stage in both CTAs
+              else mma_commit(&empty[s]);
             }
-            mma_commit(&tfull[buf]);
+            if (PAIR) mma_commit_pair(&tfull[buf]);
+            else mma_commit(&tfull[buf]);
           }
         }
       }
-      // all issued MMAs complete before TMEM is released
-      mma_commit(mdone);
+      // all issued MMAs complete before TMEM is released (pair: in both CTAs)
+      if (PAIR) mma_commit_pair(mdone);
+      else mma_commit(mdone);
       mbar_wait(mdone, 0, nullptr, 4);
+    } else if (PAIR && lane == 0) {
+      mbar_wait(mdone, 0, nullptr, 4);  // the peer: the leader's last MMAs have completed
     }
   } else {
     // ---------------- epilogue (warps 2..17) ----------------
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int half = (warp - 2) >> 2;        // which column part of the tile this warp drains
     const int row = q * 32 + lane;           // row of the tile owned by this thread
-    const int et = (warp - 2) * 32 + lane;   // epilogue thread index
     constexpr int HC = BN / kEpiParts;       // columns per thread
     uint32_t chunk = 0;
     bool bad = false;
-    for (int t = blockIdx.x; t < num_tiles && !bad; t += gridDim.x) {
+    for (int t = t_first; t < num_tiles && !bad; t += t_step) {
       int m0, n0;
-      tile_origin(t, p, BN, m0, n0);
-      const int b = m0 + row;
+      tile_origin(t, p, kBMT, BN, m0, n0);
+      const int b = m0 + (int)rank * kBM + row;  // b < b_pad (a multiple of the tile rows)
       const int nj = p.nj, total = p.nk * p.nj;
       // sliced mode: per-column double-float sums over all level chunks of this tile, in TMEM
       // columns [2 BN + half 2 HC, +HC) (hi) and [+HC, +2 HC) (lo) of this thread's lane
@@ -254,8 +293,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + buf * BN + half * HC;
           if (MODE == kPlain) {
             float *out = p.Jc + (size_t)b * p.ldj + n0 + half * HC;
+            // columns past n_pad (a ragged last tile of a 256-column pair tile) are not stored
+            const int cend = min(HC, p.n_pad - (n0 + half * HC));
 #pragma unroll 1
-            for (int c = 0; c < HC; c += 32) {
+            for (int c = 0; c < cend; c += 32) {
               uint32_t r[32];
               tmem_ld_x32(taddr + c, r);
               tmem_ld_wait();
@@ -292,7 +333,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             tmem_st_wait();
           }
           tc_fence_before();
-          mbar_arrive(&tempty[buf]);
+          if (PAIR) {  // one arrival per warp on the leader's barrier
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[buf]), 0));
+          } else {
+            mbar_arrive(&tempty[buf]);
+          }
         }
       }
       if (MODE == kSliced && !bad) {
@@ -339,44 +385,86 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
   }
   tc_fence_before();
-  __syncthreads();
+  __syncwarp();
+  if (PAIR) cluster_sync();  // no arrivals or MMAs target a CTA of the pair after this
+  else __syncthreads();
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem_base, kTmemCols);
+    if (PAIR) tmem_dealloc_pair(tmem_base, kTmemCols);
+    else tmem_dealloc(tmem_base, kTmemCols);
   }
 }
 
 // ---------------------------------------------------------------------------------------
-template <int MODE, int STAGES>
+template <int MODE, int BN, int STAGES, bool PAIR>
 static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
-                               const TcGemmParams &p, int grid, cudaStream_t st) {
-  const int smem = TcSmem<kTcBN, STAGES>::kBytes;
-  auto kern = k_tc_gemm<MODE, kTcBN, STAGES>;
+                               const TcGemmParams &p, int sms, cudaStream_t st) {
+  const int smem = TcSmem<BN, STAGES, PAIR>::kBytes;
+  auto kern = k_tc_gemm<MODE, BN, STAGES, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreadsTc, smem, st>>>(tmX, tmW, p);
+  const int tiles = p.m_tiles * p.n_tiles;
+  if (!PAIR) {
+    kern<<<std::min(tiles, sms), kThreadsTc, smem, st>>>(tmX, tmW, p);
+    return cudaGetLastError();
+  }
+  // persistent clusters of two: no more than can be resident at once
+  static int max_clusters = 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreadsTc);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (max_clusters == 0) {
+    cfg.gridDim = dim3(2 * (sms / 2));
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    max_clusters = n;
+  }
+  cfg.gridDim = dim3(2 * std::min(tiles, max_clusters));
+  e = cudaLaunchKernelEx(&cfg, kern, tmX, tmW, p);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, int BN, bool PAIR>
 static cudaError_t launch_stages(const CUtensorMap &tmX, const CUtensorMap &tmW,
-                                 const TcGemmParams &p, int grid, cudaStream_t st, int stages) {
-  if (stages == 4) return launch_impl<MODE, 4>(tmX, tmW, p, grid, st);
-  if (stages == 7) return launch_impl<MODE, 7>(tmX, tmW, p, grid, st);
-  return launch_impl<MODE, 6>(tmX, tmW, p, grid, st);
+                                 const TcGemmParams &p, int sms, cudaStream_t st, int stages) {
+  if (stages == 4) return launch_impl<MODE, BN, 4, PAIR>(tmX, tmW, p, sms, st);
+  if (stages == 7) return launch_impl<MODE, BN, 7, PAIR>(tmX, tmW, p, sms, st);
+  return launch_impl<MODE, BN, 6, PAIR>(tmX, tmW, p, sms, st);
 }
 
-// stages: depth of the TMA ring, 4, 6 (default) or 7 (7 x 32 KB: the shared-memory limit).
+// stages: depth of the TMA ring, 4, 6 (default) or 7 (7 x 32 KB: the shared-memory limit of
+// the single-CTA tiles). pair: CTA pairs on 256-row tiles; the plain mode then uses 256-column
+// tiles (tmW with 128-row boxes), the sliced mode 128-column tiles (tmW with 64-row boxes). The
+// batch stride b_pad must then be a multiple of 256.
 cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &tmW,
-                           const TcGemmParams &p, int sms, cudaStream_t st, int stages) {
-  const int tiles = p.m_tiles * p.n_tiles;
-  const int grid = tiles < sms ? tiles : sms;
+                           const TcGemmParams &p, int sms, cudaStream_t st, int stages, bool pair) {
+  if (p.m_tiles < 1 || p.n_tiles < 1) return cudaErrorInvalidValue;
   TcGemmParams q = p;
-  q.group_m = std::min(p.m_tiles, kGroupM);
-  if (q.m_tiles < 1 || q.n_tiles < 1) return cudaErrorInvalidValue;
-  return mode == kPlain ? launch_stages<kPlain>(tmX, tmW, q, grid, st, stages)
-                        : launch_stages<kSliced>(tmX, tmW, q, grid, st, stages);
+  if (!pair) {
+    q.group_m = std::min(q.m_tiles, kGroupM);
+    return mode == kPlain ? launch_stages<kPlain, kTcBN, false>(tmX, tmW, q, sms, st, stages)
+                          : launch_stages<kSliced, kTcBN, false>(tmX, tmW, q, sms, st, stages);
+  }
+  if (p.b_pad % (2 * kBM) != 0) return cudaErrorInvalidValue;
+  q.m_tiles = (p.m_tiles + 1) / 2;
+  q.group_m = std::min(q.m_tiles, kGroupM / 2);
+  if (mode == kPlain) {
+    q.n_tiles = (p.n_pad + 2 * kTcBN - 1) / (2 * kTcBN);
+    return launch_stages<kPlain, 2 * kTcBN, true>(tmX, tmW, q, sms, st, stages);
+  }
+  return launch_stages<kSliced, kTcBN, true>(tmX, tmW, q, sms, st, stages);
 }
 
 }  // namespace rb

@@ -37,7 +37,7 @@ namespace rb {
 struct SlicedW {  // one sliced weight operand [S][Npad][Kpad]
   __nv_bfloat16 *d = nullptr;
   int Npad = 0, nk = 0, wexp[2] = {0, 0};
-  CUtensorMap tm;
+  CUtensorMap tm, tm64;  // 128-row boxes (single-CTA tiles), 64-row boxes (CTA pairs)
 };
 
 // Mixed-path state of one size bucket: operator layouts truncated to nb (the reduced bases are
@@ -76,6 +76,7 @@ struct MixedState {
     int klass = -1;      // ceil(log2(batch)) the choice was made for
     int lu = 0;          // 1 warp per query, 2 blocked with 32-column panels, 3 blocked 16
     int st_plain = 0, st_sliced = 0;  // TMA ring depths of the two GEMMs
+    int pair_plain = 0, pair_sliced = 0;  // 1: CTA pairs (tcgen05 cta_group::2)
     float ms[4] = {0, 0, 0, 0};       // best times: elimination, plain GEMM, sliced GEMM
   } tune;
   // shared, owned by the root
@@ -1281,6 +1282,18 @@ static int sliced_digits(const char *var, int dflt) {
   return std::min(8, std::max(2, s));
 }
 
+// CTA-pair policy of the tcgen05 GEMMs (RB_GEMM_PAIRS): -1 unset (the autotuner decides; single
+// CTAs untuned), 0 single CTAs only, 1 CTA pairs only.
+static int pair_policy() {
+  const char *e = getenv("RB_GEMM_PAIRS");
+  if (!e || !*e) return -1;
+  return atoi(e) != 0 ? 1 : 0;
+}
+static bool use_pairs(const MixedState *M, bool sliced) {
+  if (M->tune.klass >= 0) return (sliced ? M->tune.pair_sliced : M->tune.pair_plain) != 0;
+  return pair_policy() == 1;
+}
+
 static int absmax_exp(rb_ctx *ctx, MixedState *M, const double *x, size_t count, int *e_out,
                       cudaStream_t st) {
   unsigned long long *mx = (unsigned long long *)(M->root->dev_words + 8);
@@ -1322,7 +1335,8 @@ static int build_sliced(rb_ctx *ctx, MixedState *M, SlicedW &W, int kind, int nk
   k_build_w<<<ctx->sms * 8, 256, 0, st>>>(bw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_build_w");
-  if (!make_map(&W.tm, W.d, (uint64_t)M->Smax * W.Npad, M->Kpad, kTcBN))
+  if (!make_map(&W.tm, W.d, (uint64_t)M->Smax * W.Npad, M->Kpad, kTcBN) ||
+      !make_map(&W.tm64, W.d, (uint64_t)M->Smax * W.Npad, M->Kpad, kTcBN / 2))
     return set_error(ctx, RB_ERR_CUDA, "tensor map encode (W)");
   return RB_OK;
 }
@@ -1405,7 +1419,7 @@ static MixedState *bucket(rb_ctx *ctx, int nb) {
 }
 
 static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
-  const int b_pad = round_up(std::max(nq, 1), 128);
+  const int b_pad = round_up(std::max(nq, 1), 256);  // whole 256-row tiles of a CTA pair
   if (b_pad <= M->bcap) return RB_OK;
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
                   (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
@@ -1565,7 +1579,8 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.Jc = M->Jc;
   g.nsplit = 3;
   int mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
-  cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain);
+  cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain,
+                                 use_pairs(M, false));
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (Jacobian)");
   if (!exact) return RB_OK;
@@ -1576,7 +1591,9 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
   mk = prof_begin(ctx, RB_K_GEMM_RES, st);
-  e = launch_tc_gemm(kSliced, M->tmXd, M->WR.tm, g, ctx->sms, st, M->tune.st_sliced);
+  const bool ps = use_pairs(M, true);
+  e = launch_tc_gemm(kSliced, M->tmXd, ps ? M->WR.tm64 : M->WR.tm, g, ctx->sms, st, M->tune.st_sliced,
+                     ps);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (residual)");
   return RB_OK;
@@ -1705,7 +1722,9 @@ static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[1] = M->WP.wexp[1];
   g.out = M->Rp;
   int mk = prof_begin(ctx, RB_K_GEMM_PRES, st);
-  cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WP.tm, g, ctx->sms, st, M->tune.st_sliced);
+  const bool ps = use_pairs(M, true);
+  cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, ps ? M->WP.tm64 : M->WP.tm, g, ctx->sms, st,
+                                 M->tune.st_sliced, ps);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (pressure)");
   mk = prof_begin(ctx, RB_K_PRESSURE, st);
@@ -1916,14 +1935,18 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   g.Jc = M->Jc;
   g.nsplit = 3;
   best = 1e30f;
-  for (int stg : {4, 6, 7}) {
+  const int policy = pair_policy();
+  for (int v = 0; v < 6; ++v) {  // stages 4, 6, 7; single CTAs, then CTA pairs
+    const int stg = v % 3 == 0 ? 4 : (v % 3 == 1 ? 6 : 7);
+    const bool pair = v >= 3;
+    if (policy >= 0 && pair != (policy == 1)) continue;
     if (rc != RB_OK) break;
     const float ms = timed([&]() {
-      const cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, stg);
+      const cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, stg, pair);
       return e == cudaSuccess ? RB_OK : RB_ERR_CUDA;
     });
     if (ms < 0.f) { rc = set_error(ctx, RB_ERR_CUDA, "autotune (Jacobian GEMM)"); break; }
-    if (ms < best) { best = ms; t.st_plain = stg; t.ms[1] = ms; }
+    if (ms < best) { best = ms; t.st_plain = stg; t.pair_plain = pair; t.ms[1] = ms; }
   }
   g.n_tiles = M->WR.Npad / kTcBN;
   g.n_pad = M->WR.Npad;
@@ -1931,14 +1954,18 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
   best = 1e30f;
-  for (int stg : {4, 6, 7}) {
+  for (int v = 0; v < 6; ++v) {
+    const int stg = v % 3 == 0 ? 4 : (v % 3 == 1 ? 6 : 7);
+    const bool pair = v >= 3;
+    if (policy >= 0 && pair != (policy == 1)) continue;
     if (rc != RB_OK) break;
     const float ms = timed([&]() {
-      const cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, M->WR.tm, g, ctx->sms, st, stg);
+      const cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, pair ? M->WR.tm64 : M->WR.tm, g, ctx->sms,
+                                           st, stg, pair);
       return e == cudaSuccess ? RB_OK : RB_ERR_CUDA;
     });
     if (ms < 0.f) { rc = set_error(ctx, RB_ERR_CUDA, "autotune (sliced GEMM)"); break; }
-    if (ms < best) { best = ms; t.st_sliced = stg; t.ms[2] = ms; }
+    if (ms < best) { best = ms; t.st_sliced = stg; t.pair_sliced = pair; t.ms[2] = ms; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1961,7 +1988,8 @@ int mixed_tuning(rb_ctx *ctx, int i, int *out6, float *ms3) {
   if (i >= 0 && i < (int)tuned.size()) {
     const MixedState *M = tuned[i];
     if (out6) {
-      const int v[6] = {M->nb, M->tune.klass, M->tune.lu, M->tune.st_plain, M->tune.st_sliced, 0};
+      const int v[6] = {M->nb, M->tune.klass, M->tune.lu, M->tune.st_plain, M->tune.st_sliced,
+                        M->tune.pair_plain | (M->tune.pair_sliced << 1)};
       for (int k = 0; k < 6; ++k) out6[k] = v[k];
     }
     if (ms3)

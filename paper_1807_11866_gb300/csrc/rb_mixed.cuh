@@ -32,6 +32,7 @@ struct TcGemmParams {
 };
 
 cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &tmW,
-                           const TcGemmParams &p, int sms, cudaStream_t st, int stages = 0);
+                           const TcGemmParams &p, int sms, cudaStream_t st, int stages = 0,
+                           bool pair = false);
 
 }  // namespace rb

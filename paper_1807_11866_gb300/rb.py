@@ -290,6 +290,8 @@ class Context:
             out.append({"n_bucket": v[0], "batch_class": v[1],
                         "elimination": self.ELIMINATION.get(v[2], str(v[2])),
                         "jacobian_gemm_stages": v[3], "sliced_gemm_stages": v[4],
+                        "jacobian_gemm_cta_pairs": bool(v[5] & 1),
+                        "sliced_gemm_cta_pairs": bool(v[5] & 2),
                         "best_ms": {"elimination": ms[0], "jacobian_gemm": ms[1], "sliced_gemm": ms[2]}})
         return out
 
