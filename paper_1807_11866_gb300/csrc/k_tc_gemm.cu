@@ -269,6 +269,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tile_origin(t, p, kBMT, BN, m0, n0);
       const int b = m0 + (int)rank * kBM + row;  // b < b_pad (a multiple of the tile rows)
       const int nj = p.nj, total = p.nk * p.nj;
+      // wide sliced mode: the thread's HC <= nj columns hold rows k_first and k_first + 1
+      const int c_begin = n0 + half * HC;
+      const int k_first = c_begin / nj, j_first = c_begin - k_first * nj;
+      float kah = 0.f, kal = 0.f, kbh = 0.f, kbl = 0.f;
       // sliced mode: per-column double-float sums over all level chunks of this tile, in TMEM
       // columns [2 BN + half 2 HC, +HC) (hi) and [+HC, +2 HC) (lo) of this thread's lane
       const uint32_t tsum = tmem_base + ((uint32_t)(q * 32) << 16) + 2 * BN + half * 2 * HC;
@@ -306,6 +310,42 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                 o4[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
                                     __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
             }
+          } else if (MODE == kSlicedWide) {
+            // contract the exact chunk, scaled by its level (and segment) relative to segment 0,
+            // with u_b[j] at once: two double-float row sums per thread (k_first, k_first + 1)
+            const int d = (lv.seg ? (p.xexp[p.b_pad + b] + p.wexp[1] - p.xexp[b] - p.wexp[0]) : 0) -
+                          kDigitBits * lv.L;
+            const float sc = ldexpf(1.0f, d);
+            const float2 *ub = p.ufT + b;  // u_b[j] at ub[j b_pad] (L2-resident)
+#pragma unroll 1
+            for (int g = 0; g < HC / 16; ++g) {
+              float2 u2[16];
+#pragma unroll
+              for (int v = 0; v < 16; ++v) {
+                int j = j_first + g * 16 + v;
+                if (j >= nj) j -= nj;  // HC <= nj: at most one wrap
+                u2[v] = ub[(size_t)j * p.b_pad];
+              }
+              uint32_t r[16];
+              tmem_ld_x16(taddr + g * 16, r);
+              tmem_ld_wait();
+#pragma unroll
+              for (int v = 0; v < 16; ++v) {
+                const int cl = g * 16 + v;
+                if (c_begin + cl < total) {  // warp-uniform
+                  const float x = __uint_as_float(r[v]) * sc;
+                  if (j_first + cl < nj) df_fma(kah, kal, x, 0.f, u2[v].x, u2[v].y);
+                  else df_fma(kbh, kbl, x, 0.f, u2[v].x, u2[v].y);
+                }
+              }
+            }
+            float s, e;  // renormalise the sums once per chunk
+            two_sum(kah, kal, s, e);
+            kah = s;
+            kal = e;
+            two_sum(kbh, kbl, s, e);
+            kbh = s;
+            kbl = e;
           } else {
             // add the exact chunk, scaled by its level (and segment) relative to segment 0, into
             // this thread's per-column double-float sums (exact power-of-two scaling)
@@ -341,14 +381,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           }
         }
       }
+      if (MODE == kSlicedWide && !bad && b < p.nq && c_begin < total) {
+        // out[b][k] += 2^(ex + ew) sum_j T[(k,j)] u_j over this thread's columns
+        const double scale = ldexp(1.0, p.xexp[b] + p.wexp[0]);
+        atomicAdd(p.out + (size_t)b * p.nk + k_first, ((double)kah + (double)kal) * scale);
+        const int cnt = min(HC, total - c_begin);
+        if (j_first + cnt > nj)
+          atomicAdd(p.out + (size_t)b * p.nk + k_first + 1, ((double)kbh + (double)kbl) * scale);
+      }
       if (MODE == kSliced && !bad) {
         // contract the tile's column sums with u_b[j]: out[b][k] += 2^(ex + ew) sum_j T[(k,j)] u_j
         // every lane executes the warp-collective TMEM loads; rows beyond the batch only skip the
         // arithmetic and the stores
         const bool live = b < p.nq;
         const double scale = live ? ldexp(1.0, p.xexp[b] + p.wexp[0]) : 0.0;
-        const int c_begin = n0 + half * HC;
-        int k = c_begin / nj, j = c_begin % nj;
+        int k = k_first, j = j_first;
         const int cend = min(HC, total - c_begin);
         const float2 *ub = p.ufT + b;  // u_b[j] at ub[j b_pad] (row b < b_pad: in bounds)
         float ah = 0.f, al = 0.f;
@@ -453,6 +500,7 @@ cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &
   if (p.m_tiles < 1 || p.n_tiles < 1) return cudaErrorInvalidValue;
   TcGemmParams q = p;
   if (!pair) {
+    if (mode == kSlicedWide) return cudaErrorInvalidValue;  // pairs only
     q.group_m = std::min(q.m_tiles, kGroupM);
     return mode == kPlain ? launch_stages<kPlain, kTcBN, false>(tmX, tmW, q, sms, st, stages)
                           : launch_stages<kSliced, kTcBN, false>(tmX, tmW, q, sms, st, stages);
@@ -460,9 +508,11 @@ cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &
   if (p.b_pad % (2 * kBM) != 0) return cudaErrorInvalidValue;
   q.m_tiles = (p.m_tiles + 1) / 2;
   q.group_m = std::min(q.m_tiles, kGroupM / 2);
-  if (mode == kPlain) {
+  if (mode == kPlain || mode == kSlicedWide) {
+    if (mode == kSlicedWide && p.nj < 2 * kTcBN / kEpiParts) return cudaErrorInvalidValue;
     q.n_tiles = (p.n_pad + 2 * kTcBN - 1) / (2 * kTcBN);
-    return launch_stages<kPlain, 2 * kTcBN, true>(tmX, tmW, q, sms, st, stages);
+    return mode == kPlain ? launch_stages<kPlain, 2 * kTcBN, true>(tmX, tmW, q, sms, st, stages)
+                          : launch_stages<kSlicedWide, 2 * kTcBN, true>(tmX, tmW, q, sms, st, stages);
   }
   return launch_stages<kSliced, kTcBN, true>(tmX, tmW, q, sms, st, stages);
 }

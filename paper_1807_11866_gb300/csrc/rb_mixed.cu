@@ -76,7 +76,8 @@ struct MixedState {
     int klass = -1;      // ceil(log2(batch)) the choice was made for
     int lu = 0;          // 1 warp per query, 2 blocked with 32-column panels, 3 blocked 16
     int st_plain = 0, st_sliced = 0;  // TMA ring depths of the two GEMMs
-    int pair_plain = 0, pair_sliced = 0;  // 1: CTA pairs (tcgen05 cta_group::2)
+    int pair_plain = 0;   // 1: CTA pairs (tcgen05 cta_group::2)
+    int pair_sliced = 0;  // 0 single CTAs, 1 CTA pairs, 2 CTA pairs on 256-column tiles
     float ms[4] = {0, 0, 0, 0};       // best times: elimination, plain GEMM, sliced GEMM
   } tune;
   // shared, owned by the root
@@ -1283,15 +1284,29 @@ static int sliced_digits(const char *var, int dflt) {
 }
 
 // CTA-pair policy of the tcgen05 GEMMs (RB_GEMM_PAIRS): -1 unset (the autotuner decides; single
-// CTAs untuned), 0 single CTAs only, 1 CTA pairs only.
+// CTAs untuned), 0 single CTAs only, 1 CTA pairs only, 2 CTA pairs with the wide sliced variant
+// wherever it applies (nb >= 64).
 static int pair_policy() {
   const char *e = getenv("RB_GEMM_PAIRS");
   if (!e || !*e) return -1;
-  return atoi(e) != 0 ? 1 : 0;
+  const int v = atoi(e);
+  return v <= 0 ? 0 : (v == 1 ? 1 : 2);
 }
-static bool use_pairs(const MixedState *M, bool sliced) {
-  if (M->tune.klass >= 0) return (sliced ? M->tune.pair_sliced : M->tune.pair_plain) != 0;
-  return pair_policy() == 1;
+constexpr int kWideMinN = 64;  // the wide sliced variant needs nj >= 64 (one row change per part)
+static bool use_pairs_plain(const MixedState *M) {
+  if (M->tune.klass >= 0) return M->tune.pair_plain != 0;
+  return pair_policy() >= 1;
+}
+// sliced GEMM variant: 0 single CTAs, 1 CTA pairs, 2 CTA pairs with 256-column tiles
+static int sliced_variant(const MixedState *M) {
+  if (M->tune.klass >= 0) return M->tune.pair_sliced;
+  const int pol = pair_policy();
+  return pol == 2 ? (M->nb >= kWideMinN ? 2 : 1) : (pol == 1 ? 1 : 0);
+}
+static cudaError_t launch_sliced(const MixedState *M, const SlicedW &W, const TcGemmParams &g,
+                                 int sms, cudaStream_t st, int stages, int variant) {
+  if (variant == 2) return launch_tc_gemm(kSlicedWide, M->tmXd, W.tm, g, sms, st, stages, true);
+  return launch_tc_gemm(kSliced, M->tmXd, variant == 1 ? W.tm64 : W.tm, g, sms, st, stages, variant == 1);
 }
 
 static int absmax_exp(rb_ctx *ctx, MixedState *M, const double *x, size_t count, int *e_out,
@@ -1580,7 +1595,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.nsplit = 3;
   int mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
   cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain,
-                                 use_pairs(M, false));
+                                 use_pairs_plain(M));
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (Jacobian)");
   if (!exact) return RB_OK;
@@ -1591,9 +1606,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
   mk = prof_begin(ctx, RB_K_GEMM_RES, st);
-  const bool ps = use_pairs(M, true);
-  e = launch_tc_gemm(kSliced, M->tmXd, ps ? M->WR.tm64 : M->WR.tm, g, ctx->sms, st, M->tune.st_sliced,
-                     ps);
+  e = launch_sliced(M, M->WR, g, ctx->sms, st, M->tune.st_sliced, sliced_variant(M));
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (residual)");
   return RB_OK;
@@ -1722,9 +1735,7 @@ static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[1] = M->WP.wexp[1];
   g.out = M->Rp;
   int mk = prof_begin(ctx, RB_K_GEMM_PRES, st);
-  const bool ps = use_pairs(M, true);
-  cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, ps ? M->WP.tm64 : M->WP.tm, g, ctx->sms, st,
-                                 M->tune.st_sliced, ps);
+  cudaError_t e = launch_sliced(M, M->WP, g, ctx->sms, st, M->tune.st_sliced, sliced_variant(M));
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (pressure)");
   mk = prof_begin(ctx, RB_K_PRESSURE, st);
@@ -1939,7 +1950,7 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   for (int v = 0; v < 6; ++v) {  // stages 4, 6, 7; single CTAs, then CTA pairs
     const int stg = v % 3 == 0 ? 4 : (v % 3 == 1 ? 6 : 7);
     const bool pair = v >= 3;
-    if (policy >= 0 && pair != (policy == 1)) continue;
+    if (policy >= 0 && pair != (policy >= 1)) continue;
     if (rc != RB_OK) break;
     const float ms = timed([&]() {
       const cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, stg, pair);
@@ -1954,18 +1965,20 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
   best = 1e30f;
-  for (int v = 0; v < 6; ++v) {
+  for (int v = 0; v < 9; ++v) {  // single CTAs, CTA pairs, CTA pairs with 256-column tiles
     const int stg = v % 3 == 0 ? 4 : (v % 3 == 1 ? 6 : 7);
-    const bool pair = v >= 3;
-    if (policy >= 0 && pair != (policy == 1)) continue;
+    const int variant = v / 3;
+    if (variant == 2 && M->nb < kWideMinN) continue;
+    if (policy == 0 && variant != 0) continue;
+    if (policy == 1 && variant == 0) continue;
+    if (policy == 2 && variant != (M->nb >= kWideMinN ? 2 : 1)) continue;
     if (rc != RB_OK) break;
     const float ms = timed([&]() {
-      const cudaError_t e = launch_tc_gemm(kSliced, M->tmXd, pair ? M->WR.tm64 : M->WR.tm, g, ctx->sms,
-                                           st, stg, pair);
+      const cudaError_t e = launch_sliced(M, M->WR, g, ctx->sms, st, stg, variant);
       return e == cudaSuccess ? RB_OK : RB_ERR_CUDA;
     });
     if (ms < 0.f) { rc = set_error(ctx, RB_ERR_CUDA, "autotune (sliced GEMM)"); break; }
-    if (ms < best) { best = ms; t.st_sliced = stg; t.pair_sliced = pair; t.ms[2] = ms; }
+    if (ms < best) { best = ms; t.st_sliced = stg; t.pair_sliced = variant; t.ms[2] = ms; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1989,7 +2002,8 @@ int mixed_tuning(rb_ctx *ctx, int i, int *out6, float *ms3) {
     const MixedState *M = tuned[i];
     if (out6) {
       const int v[6] = {M->nb, M->tune.klass, M->tune.lu, M->tune.st_plain, M->tune.st_sliced,
-                        M->tune.pair_plain | (M->tune.pair_sliced << 1)};
+                        M->tune.pair_plain | (M->tune.pair_sliced >= 1 ? 2 : 0) |
+                            (M->tune.pair_sliced == 2 ? 4 : 0)};
       for (int k = 0; k < 6; ++k) out6[k] = v[k];
     }
     if (ms3)

@@ -6,7 +6,9 @@
 
 namespace rb {
 
-enum { kPlain = 0, kSliced = 1 };
+// kSliced: per-column double-float sums in TMEM, contracted with u at the end of a tile;
+// kSlicedWide: 256-column tiles, every chunk contracted with u at once (needs nj >= 64).
+enum { kPlain = 0, kSliced = 1, kSlicedWide = 2 };
 constexpr int kTcBN = 128;     // output tile width (columns (k, j))
 constexpr int kDigitBits = 7;  // base-128 balanced digits (|d| <= 64) of the sliced product
 

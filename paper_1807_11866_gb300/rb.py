@@ -292,6 +292,7 @@ class Context:
                         "jacobian_gemm_stages": v[3], "sliced_gemm_stages": v[4],
                         "jacobian_gemm_cta_pairs": bool(v[5] & 1),
                         "sliced_gemm_cta_pairs": bool(v[5] & 2),
+                        "sliced_gemm_wide": bool(v[5] & 4),
                         "best_ms": {"elimination": ms[0], "jacobian_gemm": ms[1], "sliced_gemm": ms[2]}})
         return out
 

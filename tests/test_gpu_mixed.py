@@ -36,12 +36,13 @@ def term_scale(o, ops, n, th, u):
     return np.abs(A) @ np.abs(u) + conv + np.abs(f)
 
 
-@pytest.mark.parametrize("pairs", ["0", "1"])
+@pytest.mark.parametrize("pairs", ["0", "1", "2"])
 @pytest.mark.parametrize("n,qc,c_dtype", [(8, 3, "f64"), (50, 6, "f64"), (37, 4, "f32"),
-                                          (64, 8, "bf16")])
+                                          (64, 8, "bf16"), (72, 3, "f64")])
 def test_eval_residual_and_jacobian(rb, n, qc, c_dtype, pairs, monkeypatch):
     """Residual and Jacobian at given u, with the GEMMs on single CTAs and on CTA pairs
-    (256-row tiles; 256-column Jacobian tiles with a ragged last tile for n = 8 and 37)."""
+    (256-row tiles; 256-column Jacobian tiles with a ragged last tile for n = 8, 37 and 72;
+    with pairs = 2 and n >= 64 the sliced GEMM on 256-column tiles contracted chunk by chunk)."""
     monkeypatch.setenv("RB_GEMM_PAIRS", pairs)
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n, q_a=3, q_c=qc, c_dtype=c_dtype)
@@ -83,11 +84,12 @@ def test_sweep_parity(rb, n):
     assert rel(p, p_ref).max() <= 10 * TOL_MIXED
 
 
-@pytest.mark.parametrize("n,nq", [(50, 300), (30, 130)])
-def test_cta_pair_gemms_solve(rb, n, nq, monkeypatch):
-    """Whole solves (velocity and pressure) with both GEMMs restricted to CTA pairs: the tuner
-    records pairs, and the result is the oracle's; batches not a multiple of 256 rows."""
-    monkeypatch.setenv("RB_GEMM_PAIRS", "1")
+@pytest.mark.parametrize("n,nq,pairs", [(50, 300, "1"), (30, 130, "1"), (80, 300, "2")])
+def test_cta_pair_gemms_solve(rb, n, nq, pairs, monkeypatch):
+    """Whole solves (velocity and pressure) with both GEMMs restricted to CTA pairs (and, for
+    pairs = 2, the 256-column sliced tiles): the tuner records them, and the result is the
+    oracle's; batches not a multiple of 256 rows."""
+    monkeypatch.setenv("RB_GEMM_PAIRS", pairs)
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n)
     q = synth.make_queries(wl, batch=nq, n_max=n)
@@ -98,6 +100,7 @@ def test_cta_pair_gemms_solve(rb, n, nq, monkeypatch):
         u, p, info = ctx.rb_solve(q.mu)
         tune = ctx.rb_tuning()
     assert tune and all(t["jacobian_gemm_cta_pairs"] and t["sliced_gemm_cta_pairs"] for t in tune)
+    assert all(t["sliced_gemm_wide"] == (pairs == "2") for t in tune)
     assert np.all(info["status"] == 0)
     assert rel(u, u_ref).max() <= TOL_MIXED
     assert rel(p, p_ref).max() <= 10 * TOL_MIXED
@@ -171,10 +174,13 @@ def test_full_sweep_batch_sampled(rb):
     assert rel(p[idx], p_ref).max() <= 10 * TOL_MIXED
 
 
+@pytest.mark.parametrize("pairs", ["0", "2"])
 @pytest.mark.parametrize("n,q,nq", [(160, 3, 130), (300, 2, 130)])
-def test_large_n_mixed(rb, n, q, nq):
+def test_large_n_mixed(rb, n, q, nq, pairs, monkeypatch):
     """Large Jacobians: sliced-GEMM tiles whose 128 columns hold fewer than one output row
-    (n > 128), the blocked elimination (n = 160, 300); oracle on a sample."""
+    (n > 128), the blocked elimination (n = 160, 300); oracle on a sample. Single CTAs, and
+    CTA pairs with the 256-column sliced tiles."""
+    monkeypatch.setenv("RB_GEMM_PAIRS", pairs)
     wl = synth.WORKLOADS["dense_n300"]
     ops = synth.make_operators(wl, n_max=n, q_a=q, q_c=q, q_f=2)
     qs = synth.make_queries(wl, batch=nq - 2, n_max=n)
