@@ -228,7 +228,7 @@ int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launch
  * 3 = blocked, 16-column panels), the TMA ring depths of the Jacobian and sliced GEMMs and
  * whether each GEMM runs on single CTAs or on CTA pairs (tcgen05 cta_group::2, 256-row tiles).
  * The environment variable RB_GEMM_PAIRS = 0 / 1 restricts the GEMMs to single CTAs / pairs;
- * 2 also forces the 256-column sliced tiles where the bucket allows them (n >= 64).
+ * 2 also forces the 256-column sliced tiles where the bucket allows them (n >= 32).
  * rb_tuning returns the number of tuned buckets; for bucket i < that number it fills
  * out6 = {bucket size, batch class, elimination, Jacobian GEMM stages, sliced GEMM stages,
  *         flags: bit 0 the Jacobian GEMM, bit 1 the sliced GEMM runs on CTA pairs, bit 2 the

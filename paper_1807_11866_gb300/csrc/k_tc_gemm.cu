@@ -80,12 +80,12 @@ struct Level {
 };
 
 // The (segment, level) sequence every role walks through for one output tile.
-__device__ __forceinline__ int num_levels(int mode, const TcGemmParams &p) {
+__host__ __device__ __forceinline__ int num_levels(int mode, const TcGemmParams &p) {
   if (mode == kPlain) return 1;
   return (p.kb[0] > 0 ? p.S[0] : 0) + (p.kb[1] > 0 ? p.S[1] : 0);
 }
 
-__device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int idx) {
+__host__ __device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int idx) {
   Level v;
   if (mode == kPlain) {  // products of the split operands, one accumulator
     v.seg = 0; v.kb_off = 0; v.kb = p.kb[0]; v.L = 0; v.ilo = 1; v.npairs = p.nsplit;
@@ -97,8 +97,8 @@ __device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int i
   v.kb_off = v.seg == 0 ? 0 : p.kb[0];
   v.kb = p.kb[v.seg];
   v.L = (idx - (v.seg ? n0 : 0)) + 2;
-  v.ilo = max(1, v.L - S);
-  v.npairs = min(S, v.L - 1) - v.ilo + 1;
+  v.ilo = v.L - S > 1 ? v.L - S : 1;
+  v.npairs = (S < v.L - 1 ? S : v.L - 1) - v.ilo + 1;
   return v;
 }
 
@@ -106,6 +106,37 @@ __device__ __forceinline__ Level level_of(int mode, const TcGemmParams &p, int i
 // (the leader, rank 0, issues the M = 256 MMAs; each CTA loads its 128 rows of X and half of
 // the W tile into its own shared memory, signalling the leader's barriers, and drains its own
 // TMEM). p.m_tiles then counts 256-row tiles.
+// Level range [lo, hi) of part `part` of a tile split into p.lsplit work units: contiguous
+// levels, each in the part that holds the midpoint of its cost (pairs x K blocks), so the parts
+// carry about equal work. Their contributions add up in the output (atomics).
+__device__ __forceinline__ void level_range(int mode, const TcGemmParams &p, int n_levels, int part,
+                                            int &lo, int &hi) {
+  if (p.lsplit <= 1) {
+    lo = 0;
+    hi = n_levels;
+    return;
+  }
+  int total = 0;
+  for (int li = 0; li < n_levels; ++li) {
+    const Level v = level_of(mode, p, li);
+    total += v.npairs * v.kb;
+  }
+  lo = n_levels;
+  hi = 0;
+  int cum = 0;
+  for (int li = 0; li < n_levels; ++li) {
+    const Level v = level_of(mode, p, li);
+    const int c = v.npairs * v.kb;
+    const int owner = (int)(((long long)(2 * cum + c) * p.lsplit) / (2LL * total));
+    if (owner == part) {
+      lo = min(lo, li);
+      hi = max(hi, li + 1);
+    }
+    cum += c;
+  }
+  if (hi < lo) hi = lo;  // empty part
+}
+
 template <int MODE, int BN, int STAGES, bool PAIR>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
@@ -125,7 +156,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_levels = num_levels(MODE, p);
   const int chunk_steps = (MODE == kPlain) ? (1 << 30) : kChunkSteps;
-  const int num_tiles = p.m_tiles * p.n_tiles;
+  const int lsplit = p.lsplit > 1 ? p.lsplit : 1;
+  const int num_units = p.m_tiles * p.n_tiles * lsplit;  // (tile, level part) work units
   const uint32_t rank = PAIR ? cluster_rank() : 0u;  // 0: the pair's leader
   const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int t_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
@@ -169,11 +201,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tma_prefetch_desc(&tmW);
       uint32_t step = 0;
       bool bad = false;
-      for (int t = t_first; t < num_tiles && !bad; t += t_step) {
-        int m0, n0;
-        tile_origin(t, p, kBMT, BN, m0, n0);
+      for (int t = t_first; t < num_units && !bad; t += t_step) {
+        int m0, n0, l0, l1;
+        tile_origin(t / lsplit, p, kBMT, BN, m0, n0);
+        level_range(MODE, p, n_levels, t % lsplit, l0, l1);
         const int mr = m0 + (int)rank * kBM, nr = n0 + (int)rank * kBH;  // this CTA's part
-        for (int li = 0; li < n_levels && !bad; ++li) {
+        for (int li = l0; li < l1 && !bad; ++li) {
           const Level lv = level_of(MODE, p, li);
           const int nsteps = lv.npairs * lv.kb;
           for (int idx = 0; idx < nsteps; ++idx, ++step) {
@@ -218,8 +251,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       constexpr uint32_t idesc = idesc_bf16_f32(kBMT, BN);
       uint32_t step = 0, chunk = 0;
       bool bad = false;
-      for (int t = t_first; t < num_tiles && !bad; t += t_step) {
-        for (int li = 0; li < n_levels && !bad; ++li) {
+      for (int t = t_first; t < num_units && !bad; t += t_step) {
+        int l0, l1;
+        level_range(MODE, p, n_levels, t % lsplit, l0, l1);
+        for (int li = l0; li < l1 && !bad; ++li) {
           const Level lv = level_of(MODE, p, li);
           const int nsteps = lv.npairs * lv.kb;
           for (int c0 = 0; c0 < nsteps && !bad; c0 += chunk_steps, ++chunk) {
@@ -264,15 +299,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     constexpr int HC = BN / kEpiParts;       // columns per thread
     uint32_t chunk = 0;
     bool bad = false;
-    for (int t = t_first; t < num_tiles && !bad; t += t_step) {
-      int m0, n0;
-      tile_origin(t, p, kBMT, BN, m0, n0);
+    for (int t = t_first; t < num_units && !bad; t += t_step) {
+      int m0, n0, l0, l1;
+      tile_origin(t / lsplit, p, kBMT, BN, m0, n0);
+      level_range(MODE, p, n_levels, t % lsplit, l0, l1);
       const int b = m0 + (int)rank * kBM + row;  // b < b_pad (a multiple of the tile rows)
       const int nj = p.nj, total = p.nk * p.nj;
-      // wide sliced mode: the thread's HC <= nj columns hold rows k_first and k_first + 1
+      // wide sliced mode: the thread's HC <= 2 nj columns hold rows k_first .. k_first + 2
       const int c_begin = n0 + half * HC;
       const int k_first = c_begin / nj, j_first = c_begin - k_first * nj;
-      float kah = 0.f, kal = 0.f, kbh = 0.f, kbl = 0.f;
+      float kah = 0.f, kal = 0.f, kbh = 0.f, kbl = 0.f, kch = 0.f, kcl = 0.f;
       // sliced mode: per-column double-float sums over all level chunks of this tile, in TMEM
       // columns [2 BN + half 2 HC, +HC) (hi) and [+HC, +2 HC) (lo) of this thread's lane
       const uint32_t tsum = tmem_base + ((uint32_t)(q * 32) << 16) + 2 * BN + half * 2 * HC;
@@ -284,7 +320,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         for (int g = 0; g < 2 * HC / 16; ++g) tmem_st_x16(tsum + g * 16, z);
         tmem_st_wait();
       }
-      for (int li = 0; li < n_levels && !bad; ++li) {
+      for (int li = l0; li < l1 && !bad; ++li) {
         const Level lv = level_of(MODE, p, li);
         const int nsteps = lv.npairs * lv.kb;
         for (int c0 = 0; c0 < nsteps; c0 += chunk_steps, ++chunk) {
@@ -312,30 +348,33 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             }
           } else if (MODE == kSlicedWide) {
             // contract the exact chunk, scaled by its level (and segment) relative to segment 0,
-            // with u_b[j] at once: two double-float row sums per thread (k_first, k_first + 1)
+            // with u_b[j] at once: three double-float row sums per thread (k_first + 0, 1, 2)
             const int d = (lv.seg ? (p.xexp[p.b_pad + b] + p.wexp[1] - p.xexp[b] - p.wexp[0]) : 0) -
                           kDigitBits * lv.L;
             const float sc = ldexpf(1.0f, d);
             const float2 *ub = p.ufT + b;  // u_b[j] at ub[j b_pad] (L2-resident)
 #pragma unroll 1
-            for (int g = 0; g < HC / 16; ++g) {
-              float2 u2[16];
+            for (int g = 0; g < HC / 8; ++g) {
+              float2 u2[8];
 #pragma unroll
-              for (int v = 0; v < 16; ++v) {
-                int j = j_first + g * 16 + v;
-                if (j >= nj) j -= nj;  // HC <= nj: at most one wrap
+              for (int v = 0; v < 8; ++v) {
+                int j = j_first + g * 8 + v;
+                if (j >= nj) j -= nj;  // HC <= 2 nj: at most two wraps
+                if (j >= nj) j -= nj;
                 u2[v] = ub[(size_t)j * p.b_pad];
               }
-              uint32_t r[16];
-              tmem_ld_x16(taddr + g * 16, r);
+              uint32_t r[8];
+              tmem_ld_x8(taddr + g * 8, r);
               tmem_ld_wait();
 #pragma unroll
-              for (int v = 0; v < 16; ++v) {
-                const int cl = g * 16 + v;
-                if (c_begin + cl < total) {  // warp-uniform
+              for (int v = 0; v < 8; ++v) {
+                const int cl = g * 8 + v;
+                if (c_begin + cl < total) {  // warp-uniform, as is the row below
                   const float x = __uint_as_float(r[v]) * sc;
-                  if (j_first + cl < nj) df_fma(kah, kal, x, 0.f, u2[v].x, u2[v].y);
-                  else df_fma(kbh, kbl, x, 0.f, u2[v].x, u2[v].y);
+                  const int js = j_first + cl;
+                  if (js < nj) df_fma(kah, kal, x, 0.f, u2[v].x, u2[v].y);
+                  else if (js < 2 * nj) df_fma(kbh, kbl, x, 0.f, u2[v].x, u2[v].y);
+                  else df_fma(kch, kcl, x, 0.f, u2[v].x, u2[v].y);
                 }
               }
             }
@@ -346,6 +385,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             two_sum(kbh, kbl, s, e);
             kbh = s;
             kbl = e;
+            two_sum(kch, kcl, s, e);
+            kch = s;
+            kcl = e;
           } else {
             // add the exact chunk, scaled by its level (and segment) relative to segment 0, into
             // this thread's per-column double-float sums (exact power-of-two scaling)
@@ -388,6 +430,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         const int cnt = min(HC, total - c_begin);
         if (j_first + cnt > nj)
           atomicAdd(p.out + (size_t)b * p.nk + k_first + 1, ((double)kbh + (double)kbl) * scale);
+        if (j_first + cnt > 2 * nj)
+          atomicAdd(p.out + (size_t)b * p.nk + k_first + 2, ((double)kch + (double)kcl) * scale);
       }
       if (MODE == kSliced && !bad) {
         // contract the tile's column sums with u_b[j]: out[b][k] += 2^(ex + ew) sum_j T[(k,j)] u_j
@@ -444,16 +488,52 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 }
 
 // ---------------------------------------------------------------------------------------
+// Level parts per tile of a sliced GEMM (1 .. 6): the split that minimises the rounds of
+// `slots` concurrent work units times the costliest part (the same midpoint rule as
+// level_range), with 15% per extra part for the repeated passes over the tile (measured).
+static int choose_lsplit(int mode, const TcGemmParams &p, int tiles, int slots) {
+  if (mode == kPlain || slots < 1) return 1;
+  const int nl = num_levels(mode, p);
+  int total = 0;
+  for (int li = 0; li < nl; ++li) {
+    const Level v = level_of(mode, p, li);
+    total += v.npairs * v.kb;
+  }
+  if (total <= 0) return 1;
+  int best = 1;
+  double best_t = 0.0;
+  for (int s = 1; s <= 6 && s <= nl; ++s) {
+    int part_cost[6] = {0, 0, 0, 0, 0, 0}, cum = 0;
+    for (int li = 0; li < nl; ++li) {
+      const Level v = level_of(mode, p, li);
+      const int c = v.npairs * v.kb;
+      part_cost[(int)(((long long)(2 * cum + c) * s) / (2LL * total))] += c;
+      cum += c;
+    }
+    int mx = 0;
+    for (int i = 0; i < s; ++i) mx = std::max(mx, part_cost[i]);
+    const long long rounds = ((long long)tiles * s + slots - 1) / slots;
+    const double t = (double)rounds * mx * (1.0 + 0.15 * (s - 1));
+    if (s == 1 || t < best_t) {
+      best = s;
+      best_t = t;
+    }
+  }
+  return best;
+}
+
 template <int MODE, int BN, int STAGES, bool PAIR>
 static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
-                               const TcGemmParams &p, int sms, cudaStream_t st) {
+                               const TcGemmParams &p0, int sms, cudaStream_t st) {
   const int smem = TcSmem<BN, STAGES, PAIR>::kBytes;
   auto kern = k_tc_gemm<MODE, BN, STAGES, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  TcGemmParams p = p0;
   const int tiles = p.m_tiles * p.n_tiles;
   if (!PAIR) {
-    kern<<<std::min(tiles, sms), kThreadsTc, smem, st>>>(tmX, tmW, p);
+    p.lsplit = choose_lsplit(MODE, p, tiles, sms);
+    kern<<<std::min(tiles * p.lsplit, sms), kThreadsTc, smem, st>>>(tmX, tmW, p);
     return cudaGetLastError();
   }
   // persistent clusters of two: no more than can be resident at once
@@ -477,7 +557,8 @@ static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
     if (n < 1) return cudaErrorInvalidConfiguration;
     max_clusters = n;
   }
-  cfg.gridDim = dim3(2 * std::min(tiles, max_clusters));
+  p.lsplit = choose_lsplit(MODE, p, tiles, max_clusters);
+  cfg.gridDim = dim3(2 * std::min(tiles * p.lsplit, max_clusters));
   e = cudaLaunchKernelEx(&cfg, kern, tmX, tmW, p);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -509,7 +590,7 @@ cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &
   q.m_tiles = (p.m_tiles + 1) / 2;
   q.group_m = std::min(q.m_tiles, kGroupM / 2);
   if (mode == kPlain || mode == kSlicedWide) {
-    if (mode == kSlicedWide && p.nj < 2 * kTcBN / kEpiParts) return cudaErrorInvalidValue;
+    if (mode == kSlicedWide && 2 * p.nj < 2 * kTcBN / kEpiParts) return cudaErrorInvalidValue;
     q.n_tiles = (p.n_pad + 2 * kTcBN - 1) / (2 * kTcBN);
     return mode == kPlain ? launch_stages<kPlain, 2 * kTcBN, true>(tmX, tmW, q, sms, st, stages)
                           : launch_stages<kSlicedWide, 2 * kTcBN, true>(tmX, tmW, q, sms, st, stages);

@@ -1285,14 +1285,14 @@ static int sliced_digits(const char *var, int dflt) {
 
 // CTA-pair policy of the tcgen05 GEMMs (RB_GEMM_PAIRS): -1 unset (the autotuner decides; single
 // CTAs untuned), 0 single CTAs only, 1 CTA pairs only, 2 CTA pairs with the wide sliced variant
-// wherever it applies (nb >= 64).
+// wherever it applies (nb >= 32).
 static int pair_policy() {
   const char *e = getenv("RB_GEMM_PAIRS");
   if (!e || !*e) return -1;
   const int v = atoi(e);
   return v <= 0 ? 0 : (v == 1 ? 1 : 2);
 }
-constexpr int kWideMinN = 64;  // the wide sliced variant needs nj >= 64 (one row change per part)
+constexpr int kWideMinN = 32;  // the wide sliced variant needs nj >= 32 (two row changes per part)
 static bool use_pairs_plain(const MixedState *M) {
   if (M->tune.klass >= 0) return M->tune.pair_plain != 0;
   return pair_policy() >= 1;

@@ -7,7 +7,7 @@
 namespace rb {
 
 // kSliced: per-column double-float sums in TMEM, contracted with u at the end of a tile;
-// kSlicedWide: 256-column tiles, every chunk contracted with u at once (needs nj >= 64).
+// kSlicedWide: 256-column tiles, every chunk contracted with u at once (needs nj >= 32).
 enum { kPlain = 0, kSliced = 1, kSlicedWide = 2 };
 constexpr int kTcBN = 128;     // output tile width (columns (k, j))
 constexpr int kDigitBits = 7;  // base-128 balanced digits (|d| <= 64) of the sliced product
@@ -18,6 +18,7 @@ constexpr int kDigitBits = 7;  // base-128 balanced digits (|d| <= 64) of the sl
 struct TcGemmParams {
   int m_tiles, n_tiles;  // 128-row (query) and kTcBN-column tiles
   int group_m;           // row tiles per group of the tile order (set by launch_tc_gemm)
+  int lsplit;            // sliced: work units per tile, by level ranges (set by launch_tc_gemm)
   int kb[2];             // K blocks of 64 per segment (kb[1] = 0: no second segment)
   int S[2];              // digit slices per segment (sliced mode)
   int nsplit;            // plain mode: 1 (BF16) or 3 (split BF16: hi*hi + hi*lo + lo*hi)

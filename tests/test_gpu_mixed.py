@@ -42,7 +42,7 @@ def term_scale(o, ops, n, th, u):
 def test_eval_residual_and_jacobian(rb, n, qc, c_dtype, pairs, monkeypatch):
     """Residual and Jacobian at given u, with the GEMMs on single CTAs and on CTA pairs
     (256-row tiles; 256-column Jacobian tiles with a ragged last tile for n = 8, 37 and 72;
-    with pairs = 2 and n >= 64 the sliced GEMM on 256-column tiles contracted chunk by chunk)."""
+    with pairs = 2 and n >= 32 the sliced GEMM on 256-column tiles contracted chunk by chunk)."""
     monkeypatch.setenv("RB_GEMM_PAIRS", pairs)
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n, q_a=3, q_c=qc, c_dtype=c_dtype)
@@ -100,7 +100,8 @@ def test_cta_pair_gemms_solve(rb, n, nq, pairs, monkeypatch):
         u, p, info = ctx.rb_solve(q.mu)
         tune = ctx.rb_tuning()
     assert tune and all(t["jacobian_gemm_cta_pairs"] and t["sliced_gemm_cta_pairs"] for t in tune)
-    assert all(t["sliced_gemm_wide"] == (pairs == "2") for t in tune)
+    if pairs == "2":  # with pairs = 1 the tuner may pick either pair variant
+        assert all(t["sliced_gemm_wide"] for t in tune)
     assert np.all(info["status"] == 0)
     assert rel(u, u_ref).max() <= TOL_MIXED
     assert rel(p, p_ref).max() <= 10 * TOL_MIXED
