@@ -108,7 +108,8 @@ typedef struct {
   int max_iter;       /* Newton iteration cap (default 50) */
   size_t mem_budget;  /* device bytes the context may allocate (0: 80% of free memory) */
   int use_graph;      /* capture per-iteration launches in CUDA graphs (default 1) */
-  int autotune;       /* time kernel variants on first use per shape (default 1) */
+  int autotune;       /* time kernel variants on first use per shape (default 1; the
+                         environment variable RB_AUTOTUNE=0 makes the default 0) */
   int theta_family;   /* RB_THETA_TRIG (default) or RB_THETA_USER */
   int serve_slots;    /* serving: queries on the device at once (0: as many as the memory
                          budget admits, at most 4096) */

@@ -1,5 +1,6 @@
 // rb_runtime.cu -- host runtime of librb: context, operator residency on the device,
 // solve dispatch and error reporting. Implements the C ABI declared in include/rb.h.
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -278,7 +279,10 @@ void rb_config_default(rb_config *cfg) {
   cfg->max_iter = 50;
   cfg->mem_budget = 0;
   cfg->use_graph = 1;
-  cfg->autotune = 1;
+  // RB_AUTOTUNE=0 starts from the untuned launch variants (for profilers, whose serialised
+  // timing would skew the tuner's choices; RB_GEMM_PAIRS then fixes the GEMM variants)
+  const char *at = getenv("RB_AUTOTUNE");
+  cfg->autotune = (at && *at) ? (atoi(at) != 0) : 1;
   cfg->theta_family = RB_THETA_TRIG;
   cfg->serve_slots = 0;
 }
