@@ -226,7 +226,8 @@ int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launch
  * With cfg.autotune, the first mixed-precision solve of each size bucket and batch-size class
  * (ceil(log2(batch))) times the candidate launch variants on the bucket's shapes and keeps the
  * fastest: the elimination (1 = one warp per query, for n <= 80; 2 = blocked, 32-column panels;
- * 3 = blocked, 16-column panels), the TMA ring depths of the Jacobian and sliced GEMMs and
+ * 3 = blocked, 16-column panels; 4 = one CTA per query with a row per thread, 32 < n <= 128;
+ * RB_ELIMINATION = 1..4 forces one where it applies), the TMA ring depths of the Jacobian and sliced GEMMs and
  * whether each GEMM runs on single CTAs or on CTA pairs (tcgen05 cta_group::2, 256-row tiles).
  * The environment variable RB_GEMM_PAIRS = 0 / 1 restricts the GEMMs to single CTAs / pairs;
  * 2 also forces the 256-column sliced tiles where the bucket allows them (n >= 32).

@@ -506,6 +506,137 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
   return false;
 }
 
+// The same elimination by a CTA of W = ceil(n / 32) warps, one row per thread (row r owned by
+// thread r; n <= 128): the matrix in shared memory as for gepp_aug_warp, panels of 4 columns.
+// Each pivot step takes one CTA barrier: every warp's maximum key (redux) goes to `keys`
+// (double-buffered by step parity), after the barrier every thread takes the maximum over the
+// warps and reads the pivot row's current panel chunk from shared memory (every non-pivot row
+// writes its updated chunk back after each step). After the panel's pivot steps the pivot rows'
+// multipliers go through `lmp`, the threads finish the pivot rows right of the panel (threads
+// over chunks) and every remaining row takes its rank-4 update. Back substitution runs in warp 0
+// (rows in 4 lane slots, the pivot steps and reciprocals from `stepv` / `dinvv`); the solution
+// entry of column k is left in xs[k]. Every thread must call this; returns true (all threads)
+// if a pivot was zero or not finite. Scratch: pseq[n rounded to 4], keys[2 W], lmp[16],
+// stepv[n], dinvv[n], xs[n].
+__device__ __forceinline__ bool gepp_aug_cta(float *M, int ld, int n, int *pseq, unsigned *keys,
+                                             float *lmp, int *stepv, float *dinvv, float *xs) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, W = blockDim.x >> 5;
+  const int c_end = n >> 2;
+  float4 *M4 = reinterpret_cast<float4 *>(M);
+  const int ld4 = ld >> 2;
+  int step = tid < n ? n : -1;  // step at which the row was the pivot; n: not yet; -1: no row
+  float dinv = 0.f;
+  for (int c0 = 0; 4 * c0 < n; ++c0) {
+    float4 pc = step >= 0 ? M4[tid * ld4 + c0] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float lm[4] = {0.f, 0.f, 0.f, 0.f};
+    int prow[4] = {0, 0, 0, 0};
+    const int steps = min(4, n - 4 * c0);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t >= steps) break;
+      const int p = 4 * c0 + t;
+      unsigned key = step == n ? pivot_key(comp4(pc, t), tid) : 0u;
+      key = __reduce_max_sync(0xffffffffu, key);
+      if (lane == 0) keys[(p & 1) * W + w] = key;
+      __syncthreads();
+      unsigned kmax = 0;
+      for (int i = 0; i < W; ++i) kmax = max(kmax, keys[(p & 1) * W + i]);
+      const int piv = 255 - (int)(kmax & 255u);
+      const float4 pp = M4[piv * ld4 + c0];
+      const float pv = comp4(pp, t);
+      // (the fast reciprocal is within 2 ulp below 2^126 in magnitude)
+      if (!(fabsf(pv) > 0.f) || !(fabsf(pv) < 0x1p126f)) return true;  // uniform
+      const float rinv = __fdividef(1.0f, pv);
+      prow[t] = piv;
+      if (tid == 0) pseq[p] = piv;
+      if (tid == piv) {
+        step = p;
+        dinv = rinv;
+      } else if (step == n) {
+        const float l = comp4(pc, t) * rinv;
+        lm[t] = l;
+#pragma unroll
+        for (int t2 = t + 1; t2 < 4; ++t2) set4(pc, t2, fmaf(-l, comp4(pp, t2), comp4(pc, t2)));
+        M4[tid * ld4 + c0] = pc;  // current chunk for the next pivot step
+      }
+    }
+    // multipliers of the panel's pivot rows with respect to its earlier pivots
+    if (step >= 4 * c0 && step < 4 * c0 + steps) {
+      const int t = step - 4 * c0;
+      for (int t2 = 0; t2 < t; ++t2) lmp[4 * t + t2] = lm[t2];
+    }
+    __syncthreads();
+    // U rows right of the panel, threads over chunks: U_t = row_t - sum_{t2 < t} l(t, t2) U_t2
+    for (int c = c0 + 1 + tid; c <= c_end; c += blockDim.x) {
+      float4 u[4];
+      u[0] = M4[prow[0] * ld4 + c];
+#pragma unroll
+      for (int t = 1; t < 4; ++t) {
+        if (t >= steps) break;
+        float4 a = M4[prow[t] * ld4 + c];
+#pragma unroll
+        for (int t2 = 0; t2 < t; ++t2) a = fms4(a, lmp[4 * t + t2], u[t2]);
+        u[t] = a;
+        M4[prow[t] * ld4 + c] = a;
+      }
+    }
+    __syncthreads();
+    // rank-`steps` update of the rows not yet used as pivots
+    if (step == n) {
+      float4 *row = M4 + tid * ld4;
+#pragma unroll 2
+      for (int c = c0 + 1; c <= c_end; ++c) {
+        float4 a = row[c];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < steps) a = fms4(a, lm[t], M4[prow[t] * ld4 + c]);
+        row[c] = a;
+      }
+    }
+    // the next panel reads other rows only after its first pivot barrier
+  }
+  if (tid < n) {
+    stepv[tid] = step;
+    dinvv[tid] = dinv;
+  }
+  __syncthreads();
+  if (w == 0) {  // back substitution in step order, rows r = lane + 32 s
+    constexpr int RS = 4;
+    int st[RS];
+    float y[RS], dv[RS];
+#pragma unroll
+    for (int s = 0; s < RS; ++s) {
+      const int r = lane + 32 * s;
+      st[s] = r < n ? stepv[r] : -1;
+      dv[s] = r < n ? dinvv[r] : 0.f;
+      y[s] = r < n ? M[r * ld + n] : 0.f;
+    }
+    for (int c = (n - 1) >> 2; c >= 0; --c) {
+      float4 mc[RS];
+#pragma unroll
+      for (int s = 0; s < RS; ++s)
+        mc[s] = st[s] >= 0 ? M4[(lane + 32 * s) * ld4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int4 pq = reinterpret_cast<const int4 *>(pseq)[c];
+#pragma unroll
+      for (int t = 3; t >= 0; --t) {
+        const int j = 4 * c + t;
+        if (j >= n) continue;
+        const int pr = t == 0 ? pq.x : (t == 1 ? pq.y : (t == 2 ? pq.z : pq.w));
+        float own[RS];
+#pragma unroll
+        for (int s = 0; s < RS; ++s) own[s] = y[s] * dv[s];
+        const float xj = __shfl_sync(0xffffffffu, pick(own, pr >> 5), pr & 31);
+        if (lane == 0) xs[j] = xj;
+#pragma unroll
+        for (int s = 0; s < RS; ++s)
+          if (st[s] >= 0 && st[s] < j) y[s] = fmaf(-comp4(mc[s], t), xj, y[s]);
+      }
+    }
+  }
+  __syncthreads();
+  return false;
+}
+
 // Warp LU factorisation with partial pivoting (pivot_key) and whole-row swaps, kept for several
 // right-hand sides: M (row stride ld, odd for conflict-free column reads) receives U on and above
 // the diagonal and the unit-lower multipliers below it; perm[i] = original row now at row i.

@@ -781,6 +781,91 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
   if (lane == 0 && my_active) atomicAdd(p.active, my_active);
 }
 
+// ---- CTA-per-query elimination in shared memory (32 < n <= 128) --------------------------
+// One CTA of ceil(nb / 32) warps per query, one row per thread (gepp_aug_cta): the augmented
+// matrix copied into shared memory, FP32 elimination by panels of 4 columns with one barrier
+// per pivot step; update and stopping rule as in the warp kernel.
+constexpr int kCtaLuMaxN = 128;
+struct CtaLuSmem {
+  int J, pseq, keys, lmp, stepv, dinvv, xs, red, total;  // byte offsets
+  __host__ __device__ CtaLuSmem(int nb, int lda) {
+    const int n4 = (nb + 3) & ~3;
+    int p = 0;
+    J = p; p += 4 * nb * lda;
+    pseq = p; p += 4 * n4;
+    keys = p; p += 4 * 8;
+    lmp = p; p += 4 * 16;
+    stepv = p; p += 4 * n4;
+    dinvv = p; p += 4 * n4;
+    xs = p; p += 4 * n4;
+    p = (p + 7) & ~7;
+    red = p; p += 8 * 4;
+    total = (p + 15) & ~15;
+  }
+};
+
+__global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
+  extern __shared__ __align__(16) uint8_t smb[];
+  const CtaLuSmem L(p.nb, p.lda);
+  float *J = reinterpret_cast<float *>(smb + L.J);
+  int *pseq = reinterpret_cast<int *>(smb + L.pseq);
+  unsigned *keys = reinterpret_cast<unsigned *>(smb + L.keys);
+  float *lmp = reinterpret_cast<float *>(smb + L.lmp);
+  int *stepv = reinterpret_cast<int *>(smb + L.stepv);
+  float *dinvv = reinterpret_cast<float *>(smb + L.dinvv);
+  float *xs = reinterpret_cast<float *>(smb + L.xs);
+  double *red = reinterpret_cast<double *>(smb + L.red);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ld = p.lda;
+  int my_active = 0;
+  for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
+    rb_query_info qi = p.info[b];
+    if (!is_active(qi, p.max_iter)) continue;  // uniform over the CTA
+    const int n = p.nsz ? p.nsz[b] : p.nb;
+    double *ub = p.u + (size_t)b * p.o.n_max;
+    const int rm = rung_of(p.rmode, qi.iters);
+    const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
+    {
+      const float4 *src = reinterpret_cast<const float4 *>(p.Jaug + (size_t)b * p.nb * ld);
+      float4 *dst = reinterpret_cast<float4 *>(J);
+      const int n4 = n * ld / 4;
+#pragma unroll 4
+      for (int i = tid; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    qi.iters += 1;
+    qi.res_norm = rn;
+    qi.precision_used = RB_PREC_MIXED;
+    if (!isfinite(rn)) {
+      qi.status = RB_Q_NONFINITE;
+    } else if (gepp_aug_cta(J, ld, n, pseq, keys, lmp, stepv, dinvv, xs)) {
+      qi.status = RB_Q_SINGULAR;
+    } else {
+      double dl = 0.0;
+      if (tid < n) {
+        const double d = (double)xs[tid];
+        dl = d * d;
+        ub[tid] += d;
+      }
+      dl = warp_sum(dl);
+      if (lane == 0) red[w] = dl;
+      __syncthreads();
+      double tot = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+      const double dn = sqrt(tot);
+      qi.upd_norm = dn;
+      if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
+      else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+    }
+    if (tid == 0) {
+      p.info[b] = qi;
+      if (is_active(qi, p.max_iter)) ++my_active;
+    }
+    __syncthreads();  // shared memory is reused by the next query
+  }
+  if (tid == 0 && my_active) atomicAdd(p.active, my_active);
+}
+
 // ---- blocked elimination for large systems (n_max > 80), one CTA per query --------------
 // Right-looking blocked Gaussian elimination with partial pivoting on the query's augmented
 // matrix [J | -R] (global, row stride lda, the right-hand side in column n): for each panel of
@@ -1283,6 +1368,17 @@ static int sliced_digits(const char *var, int dflt) {
   return std::min(8, std::max(2, s));
 }
 
+// Elimination variant forced by RB_ELIMINATION (1 warp per query, 2 / 3 blocked with 32- / 16-
+// column panels, 4 CTA per query with a row per thread), where it applies to size nb; 0: none.
+static int elim_policy(int nb) {
+  const char *e = getenv("RB_ELIMINATION");
+  const int k = (e && *e) ? atoi(e) : 0;
+  if (k == 1 && nb <= kWarpLuMaxN) return 1;
+  if (k == 2 || k == 3) return k;
+  if (k == 4 && nb > 32 && nb <= kCtaLuMaxN) return 4;
+  return 0;
+}
+
 // CTA-pair policy of the tcgen05 GEMMs (RB_GEMM_PAIRS): -1 unset (the autotuner decides; single
 // CTAs untuned), 0 single CTAs only, 1 CTA pairs only, 2 CTA pairs with the wide sliced variant
 // wherever it applies (nb >= 32).
@@ -1636,7 +1732,9 @@ static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStrea
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
   }
   if (lp.eval_only) return RB_OK;
-  return launch_elimination(ctx, M, lp, nq, st, M->tune.lu ? M->tune.lu : (M->nb <= kWarpLuMaxN ? 1 : 2));
+  const int epol = elim_policy(M->nb);
+  return launch_elimination(ctx, M, lp, nq, st,
+                            M->tune.lu ? M->tune.lu : (epol ? epol : (M->nb <= kWarpLuMaxN ? 1 : 2)));
 }
 
 template <int PB>
@@ -1656,6 +1754,22 @@ static cudaError_t launch_blocked(const rb_ctx *ctx, const LuParams &lp, int nq,
 // 3 blocked (16-column panels).
 static int launch_elimination(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStream_t st,
                               int kind) {
+  if (kind == 4 && M->nb <= kCtaLuMaxN) {
+    const size_t smem = CtaLuSmem(M->nb, lp.lda).total;
+    const int threads = 32 * ((M->nb + 31) / 32);
+    cudaError_t e = cudaFuncSetAttribute(k_lu_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lu_cta, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu_cta, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_cta attr");
+    const int grid = std::max(1, std::min(nq, std::max(1, per_sm) * ctx->sms));
+    const int mk = prof_begin(ctx, RB_K_LU, st);
+    k_lu_cta<<<grid, threads, smem, st>>>(lp);
+    prof_end(ctx, mk, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_lu_cta");
+    return RB_OK;
+  }
   if (kind >= 2 || M->nb > kWarpLuMaxN) {
     const int mk = prof_begin(ctx, RB_K_LU, st);
     const cudaError_t e = kind == 3 ? launch_blocked<16>(ctx, lp, nq, st) : launch_blocked<32>(ctx, lp, nq, st);
@@ -1927,7 +2041,10 @@ static int autotune(rb_ctx *ctx, MixedState *M, int cnt, cudaStream_t st) {
   lp.Rg = M->Rg;
   lp.lda = aug_ld(M->nb);
   float best = 1e30f;
-  for (int kind = (M->nb <= kWarpLuMaxN ? 1 : 2); kind <= 3; ++kind) {
+  const int epol = elim_policy(M->nb);
+  for (int kind = (M->nb <= kWarpLuMaxN ? 1 : 2); kind <= 4; ++kind) {
+    if (kind == 4 && (M->nb <= 32 || M->nb > kCtaLuMaxN)) continue;
+    if (epol && kind != epol) continue;
     const float ms = timed([&]() {
       k_tune_fill<<<ctx->sms * 4, 256, 0, st>>>(cnt, M->nb, lp.lda, M->Jaug, M->Rn, M->Rg, lp.info, lp.u, o.n_max, 0);
       cudaEventRecord(e0, st);  // time the elimination only

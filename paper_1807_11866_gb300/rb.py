@@ -274,7 +274,8 @@ class Context:
         return out
 
     # --- autotuner ----------------------------------------------------------------------
-    ELIMINATION = {1: "warp per query", 2: "blocked, 32-column panels", 3: "blocked, 16-column panels"}
+    ELIMINATION = {1: "warp per query", 2: "blocked, 32-column panels", 3: "blocked, 16-column panels",
+                   4: "CTA per query, row per thread"}
 
     def rb_tuning(self):
         """Autotuned launch variants of every tuned size bucket (list of dicts)."""

@@ -107,6 +107,27 @@ def test_cta_pair_gemms_solve(rb, n, nq, pairs, monkeypatch):
     assert rel(p, p_ref).max() <= 10 * TOL_MIXED
 
 
+@pytest.mark.parametrize("n", [33, 64, 100, 128])
+def test_cta_elimination(rb, n, monkeypatch):
+    """The CTA-per-query elimination (one row per thread, ceil(n / 32) warps, one barrier per
+    pivot step) forced where it applies: velocity and pressure match the oracle."""
+    monkeypatch.setenv("RB_ELIMINATION", "4")
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl, n_max=n, q_a=4, q_c=4)
+    q = synth.make_queries(wl, batch=150, n_max=n)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    o = oracle.Oracle.from_set(ops)
+    u_ref, p_ref, _ = o.solve(mu, threads=8)
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, p, info = ctx.rb_solve(mu)
+        tune = ctx.rb_tuning()
+    assert all(t["elimination"].startswith("CTA") for t in tune if t["n_bucket"] > 32)
+    assert np.all(info["status"] == 0)
+    assert rel(u, u_ref).max() <= TOL_MIXED
+    assert rel(p, p_ref).max() <= 10 * TOL_MIXED
+
+
 def test_manufactured_mixed(rb):
     ops = synth.make_operators(synth.WORKLOADS["single_n20"])
     oracle.manufacture(ops, (10.0, 200.0))
@@ -266,7 +287,7 @@ def test_autotuner_choices(rb):
         assert t["jacobian_gemm_stages"] in (4, 6, 7)
         assert t["sliced_gemm_stages"] in (4, 6, 7)
         if t["n_bucket"] > 80:
-            assert t["elimination"].startswith("blocked")
+            assert t["elimination"].startswith("blocked") or t["elimination"].startswith("CTA")
         assert all(v > 0 for v in t["best_ms"].values())
     for u, info in ((u1, i1), (u0, i0)):
         assert np.all(info["status"] == 0)
