@@ -106,12 +106,12 @@ __host__ __device__ __forceinline__ Level level_of(int mode, const TcGemmParams 
 // (the leader, rank 0, issues the M = 256 MMAs; each CTA loads its 128 rows of X and half of
 // the W tile into its own shared memory, signalling the leader's barriers, and drains its own
 // TMEM). p.m_tiles then counts 256-row tiles.
-// Level range [lo, hi) of part `part` of a tile split into p.lsplit work units: contiguous
+// Level range [lo, hi) of part `part` of a tile split into `split` work units: contiguous
 // levels, each in the part that holds the midpoint of its cost (pairs x K blocks), so the parts
 // carry about equal work. Their contributions add up in the output (atomics).
 __device__ __forceinline__ void level_range(int mode, const TcGemmParams &p, int n_levels, int part,
-                                            int &lo, int &hi) {
-  if (p.lsplit <= 1) {
+                                            int split, int &lo, int &hi) {
+  if (split <= 1) {
     lo = 0;
     hi = n_levels;
     return;
@@ -127,7 +127,7 @@ __device__ __forceinline__ void level_range(int mode, const TcGemmParams &p, int
   for (int li = 0; li < n_levels; ++li) {
     const Level v = level_of(mode, p, li);
     const int c = v.npairs * v.kb;
-    const int owner = (int)(((long long)(2 * cum + c) * p.lsplit) / (2LL * total));
+    const int owner = (int)(((long long)(2 * cum + c) * split) / (2LL * total));
     if (owner == part) {
       lo = min(lo, li);
       hi = max(hi, li + 1);
@@ -156,8 +156,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_levels = num_levels(MODE, p);
   const int chunk_steps = (MODE == kPlain) ? (1 << 30) : kChunkSteps;
+  // work units: tiles [0, full) whole, the tail tiles split into lsplit level parts each
+  const int num_tiles = p.m_tiles * p.n_tiles;
   const int lsplit = p.lsplit > 1 ? p.lsplit : 1;
-  const int num_units = p.m_tiles * p.n_tiles * lsplit;  // (tile, level part) work units
+  const int whole = lsplit > 1 ? p.full_tiles : num_tiles;
+  const int num_units = whole + (num_tiles - whole) * lsplit;
+  auto unit = [&](int t, int &tile, int &l0, int &l1) {
+    if (t < whole) {
+      tile = t;
+      level_range(MODE, p, n_levels, 0, 1, l0, l1);
+    } else {
+      tile = whole + (t - whole) / lsplit;
+      level_range(MODE, p, n_levels, (t - whole) % lsplit, lsplit, l0, l1);
+    }
+  };
   const uint32_t rank = PAIR ? cluster_rank() : 0u;  // 0: the pair's leader
   const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int t_step = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
@@ -202,9 +214,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       uint32_t step = 0;
       bool bad = false;
       for (int t = t_first; t < num_units && !bad; t += t_step) {
-        int m0, n0, l0, l1;
-        tile_origin(t / lsplit, p, kBMT, BN, m0, n0);
-        level_range(MODE, p, n_levels, t % lsplit, l0, l1);
+        int m0, n0, l0, l1, tile;
+        unit(t, tile, l0, l1);
+        tile_origin(tile, p, kBMT, BN, m0, n0);
         const int mr = m0 + (int)rank * kBM, nr = n0 + (int)rank * kBH;  // this CTA's part
         for (int li = l0; li < l1 && !bad; ++li) {
           const Level lv = level_of(MODE, p, li);
@@ -252,8 +264,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       uint32_t step = 0, chunk = 0;
       bool bad = false;
       for (int t = t_first; t < num_units && !bad; t += t_step) {
-        int l0, l1;
-        level_range(MODE, p, n_levels, t % lsplit, l0, l1);
+        int l0, l1, tile;
+        unit(t, tile, l0, l1);
         for (int li = l0; li < l1 && !bad; ++li) {
           const Level lv = level_of(MODE, p, li);
           const int nsteps = lv.npairs * lv.kb;
@@ -300,9 +312,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     uint32_t chunk = 0;
     bool bad = false;
     for (int t = t_first; t < num_units && !bad; t += t_step) {
-      int m0, n0, l0, l1;
-      tile_origin(t / lsplit, p, kBMT, BN, m0, n0);
-      level_range(MODE, p, n_levels, t % lsplit, l0, l1);
+      int m0, n0, l0, l1, tile;
+      unit(t, tile, l0, l1);
+      tile_origin(tile, p, kBMT, BN, m0, n0);
       const int b = m0 + (int)rank * kBM + row;  // b < b_pad (a multiple of the tile rows)
       const int nj = p.nj, total = p.nk * p.nj;
       // wide sliced mode: the thread's HC <= 2 nj columns hold rows k_first .. k_first + 2
@@ -488,38 +500,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 }
 
 // ---------------------------------------------------------------------------------------
-// Level parts per tile of a sliced GEMM (1 .. 6): the split that minimises the rounds of
-// `slots` concurrent work units times the costliest part (the same midpoint rule as
-// level_range), with 15% per extra part for the repeated passes over the tile (measured).
-static int choose_lsplit(int mode, const TcGemmParams &p, int tiles, int slots) {
-  if (mode == kPlain || slots < 1) return 1;
-  const int nl = num_levels(mode, p);
-  int total = 0;
-  for (int li = 0; li < nl; ++li) {
-    const Level v = level_of(mode, p, li);
-    total += v.npairs * v.kb;
-  }
-  if (total <= 0) return 1;
-  int best = 1;
-  double best_t = 0.0;
-  for (int s = 1; s <= 6 && s <= nl; ++s) {
-    int part_cost[6] = {0, 0, 0, 0, 0, 0}, cum = 0;
-    for (int li = 0; li < nl; ++li) {
-      const Level v = level_of(mode, p, li);
-      const int c = v.npairs * v.kb;
-      part_cost[(int)(((long long)(2 * cum + c) * s) / (2LL * total))] += c;
-      cum += c;
-    }
-    int mx = 0;
-    for (int i = 0; i < s; ++i) mx = std::max(mx, part_cost[i]);
-    const long long rounds = ((long long)tiles * s + slots - 1) / slots;
-    const double t = (double)rounds * mx * (1.0 + 0.15 * (s - 1));
-    if (s == 1 || t < best_t) {
-      best = s;
-      best_t = t;
-    }
-  }
-  return best;
+// Tail split of a sliced GEMM: with `slots` work units resident at once, the tiles of the last,
+// partly filled round are split into up to six level parts each (as many as the idle slots
+// take), so that the round's work spreads over the whole GPU; the whole tiles before them run
+// unsplit. Sets p.full_tiles and p.lsplit (1: no split).
+static void choose_tail_split(int mode, TcGemmParams &p, int tiles, int slots) {
+  p.lsplit = 1;
+  p.full_tiles = tiles;
+  if (mode == kPlain || slots < 1) return;
+  const int tail = tiles % slots;
+  if (tail == 0) return;
+  const int s = std::min(std::min(6, num_levels(mode, p)), slots / tail);
+  if (s < 2) return;
+  p.lsplit = s;
+  p.full_tiles = tiles - tail;
 }
 
 template <int MODE, int BN, int STAGES, bool PAIR>
@@ -532,8 +526,9 @@ static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
   TcGemmParams p = p0;
   const int tiles = p.m_tiles * p.n_tiles;
   if (!PAIR) {
-    p.lsplit = choose_lsplit(MODE, p, tiles, sms);
-    kern<<<std::min(tiles * p.lsplit, sms), kThreadsTc, smem, st>>>(tmX, tmW, p);
+    choose_tail_split(MODE, p, tiles, sms);
+    const int units = p.full_tiles + (tiles - p.full_tiles) * p.lsplit;
+    kern<<<std::min(units, sms), kThreadsTc, smem, st>>>(tmX, tmW, p);
     return cudaGetLastError();
   }
   // persistent clusters of two: no more than can be resident at once
@@ -557,8 +552,9 @@ static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
     if (n < 1) return cudaErrorInvalidConfiguration;
     max_clusters = n;
   }
-  p.lsplit = choose_lsplit(MODE, p, tiles, max_clusters);
-  cfg.gridDim = dim3(2 * std::min(tiles * p.lsplit, max_clusters));
+  choose_tail_split(MODE, p, tiles, max_clusters);
+  const int units = p.full_tiles + (tiles - p.full_tiles) * p.lsplit;
+  cfg.gridDim = dim3(2 * std::min(units, max_clusters));
   e = cudaLaunchKernelEx(&cfg, kern, tmX, tmW, p);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

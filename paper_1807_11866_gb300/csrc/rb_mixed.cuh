@@ -18,7 +18,8 @@ constexpr int kDigitBits = 7;  // base-128 balanced digits (|d| <= 64) of the sl
 struct TcGemmParams {
   int m_tiles, n_tiles;  // 128-row (query) and kTcBN-column tiles
   int group_m;           // row tiles per group of the tile order (set by launch_tc_gemm)
-  int lsplit;            // sliced: work units per tile, by level ranges (set by launch_tc_gemm)
+  int lsplit, full_tiles;  // sliced: tiles past full_tiles run as lsplit level parts each
+                           // (set by launch_tc_gemm)
   int kb[2];             // K blocks of 64 per segment (kb[1] = 0: no second segment)
   int S[2];              // digit slices per segment (sliced mode)
   int nsplit;            // plain mode: 1 (BF16) or 3 (split BF16: hi*hi + hi*lo + lo*hi)
