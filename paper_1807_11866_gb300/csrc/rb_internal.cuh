@@ -354,6 +354,11 @@ __device__ __forceinline__ float4 fms4(float4 a, float l, const float4 &u) {  //
 // up to 4) receives the pivot row of every step. Row k of the solution is returned in
 // x[k / 32] of lane k % 32 (n <= 32 R). Returns true if a pivot was zero or not finite.
 template <int R>
+__device__ __forceinline__ void backsub_warp_steps(const float *M, int ld, int n, const int *pseq,
+                                                   const int (&step)[R], const float (&dinv)[R],
+                                                   float (&y)[R], float (&x)[R]);
+
+template <int R>
 __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x)[R], int *pseq) {
   const int lane = threadIdx.x & 31;
   const int c_end = n >> 2;  // last float4 chunk: the one holding column n
@@ -407,6 +412,7 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
           lm[s][t] = l;
 #pragma unroll
           for (int t2 = t + 1; t2 < 4; ++t2) set4(pc[s], t2, fmaf(-l, comp4(pp, t2), comp4(pc[s], t2)));
+          set4(pc[s], t, l);  // the eliminated entry keeps its multiplier (L, for later solves)
         }
       }
     }
@@ -460,13 +466,26 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
     }
     __syncwarp();
   }
-  // back substitution in step order: the solution entry of column j comes from row pseq[j]
   float y[R];
 #pragma unroll
   for (int s = 0; s < R; ++s) {
     const int r = lane + 32 * s;
     y[s] = r < n ? M[r * ld + n] : 0.f;
   }
+  backsub_warp_steps<R>(M, ld, n, pseq, step, dinv, y, x);
+  return false;
+}
+
+// Back substitution in step order on the U rows left in place by gepp_aug_warp (row r pivoted
+// step[r], 1 / pivot in dinv), the eliminated right-hand side in y: the solution entry of
+// column j comes from row pseq[j]. Row k of the solution goes to x[k / 32] of lane k % 32.
+template <int R>
+__device__ __forceinline__ void backsub_warp_steps(const float *M, int ld, int n, const int *pseq,
+                                                   const int (&step)[R], const float (&dinv)[R],
+                                                   float (&y)[R], float (&x)[R]) {
+  const int lane = threadIdx.x & 31;
+  const float4 *M4 = reinterpret_cast<const float4 *>(M);
+  const int ld4 = ld >> 2;
   for (int c = (n - 1) >> 2; c >= 0; --c) {
     float4 mc[R];
 #pragma unroll
@@ -503,6 +522,52 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
     }
     x[s] = v;
   }
+}
+
+// Solve with factors that gepp_aug_warp left in place (chord step: a new right-hand side in
+// column n, the same Jacobian): forward elimination of the right-hand side in step order with
+// the stored multipliers (row r, column p < step[r]), then back substitution on U. pseq from
+// the factorisation; `stp` is shared scratch of n ints (the step of every row).
+template <int R>
+__device__ __forceinline__ bool chord_solve_warp(const float *M, int ld, int n, const int *pseq,
+                                                 int *stp, float (&x)[R]) {
+  const int lane = threadIdx.x & 31;
+  const float4 *M4 = reinterpret_cast<const float4 *>(M);
+  const int ld4 = ld >> 2;
+  for (int p = lane; p < n; p += 32) stp[pseq[p]] = p;
+  __syncwarp();
+  int step[R];
+  float dinv[R], y[R];
+  bool bad = false;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int r = lane + 32 * s;
+    step[s] = r < n ? stp[r] : -1;
+    y[s] = r < n ? M[r * ld + n] : 0.f;
+    const float pv = r < n ? M[r * ld + step[s]] : 1.f;
+    bad |= !(fabsf(pv) > 0.f) || !(fabsf(pv) < 0x1p126f);
+    dinv[s] = r < n ? __fdividef(1.0f, pv) : 0.f;
+  }
+  if (__any_sync(0xffffffffu, bad)) return true;
+  // forward: b[r] -= l(r, p) b[pseq[p]] for the rows pivoted after step p
+  for (int c = 0; 4 * c < n; ++c) {
+    float4 mc[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      mc[s] = step[s] >= 0 ? M4[(lane + 32 * s) * ld4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int4 pq = reinterpret_cast<const int4 *>(pseq)[c];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int p = 4 * c + t;
+      if (p >= n) break;
+      const int pr = t == 0 ? pq.x : (t == 1 ? pq.y : (t == 2 ? pq.z : pq.w));
+      const float bp = __shfl_sync(0xffffffffu, pick(y, pr >> 5), pr & 31);
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        if (step[s] > p) y[s] = fmaf(-comp4(mc[s], t), bp, y[s]);
+    }
+  }
+  backsub_warp_steps<R>(M, ld, n, pseq, step, dinv, y, x);
   return false;
 }
 

@@ -67,7 +67,8 @@ struct MixedState {
   float2 *Amu = nullptr;        // [bcap][nb * nb] A(mu) as double-float
   double *Asu = nullptr;        // [bcap][m] As(mu) u
   float2 *Bmu = nullptr;        // [bcap][m][m] B(mu) as double-float
-  float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices
+  float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices (or factors)
+  int *Piv = nullptr;           // [bcap][nb] pivot rows of the factors kept for chord steps
   double2 *Rn = nullptr;        // [bcap] (unused, max(1, ||f(mu)||)) of the queries
   double *Rg = nullptr;         // [bcap][(nb + 7) / 8] row-group sums of R^2 (in Rn's block)
   CUtensorMap tmXj, tmXd;
@@ -314,6 +315,7 @@ struct BuildXParams {
   const int *nsz;
   int nq, nb, Kpad0, Kpad, S0, S1, b_pad, max_iter, mode;  // mode 0: active, 1: converged
   int digits;       // 1: also write the digit slices, exponents and u pairs (sliced GEMM)
+  int split;        // 1: write the split BF16 operand of the Jacobian GEMM (mode 0)
   const double *u;  // [nq][n_max]
   const rb_query_info *info;
   __nv_bfloat16 *Xj, *Xd;
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
       const size_t off = (size_t)b * p.Kpad + kap;
       if (kap < p.Kpad0) {
         const double x0 = xval(kap), x1 = xval(kap + 1);
-        if (p.mode == 0) {
+        if (p.mode == 0 && p.split) {
           // split BF16 operand of the Jacobian GEMM: [x_hi | x_hi | x_lo]
           const float f0 = (float)x0, f1 = (float)x1;
           const __nv_bfloat162 hi = __floats2bfloat162_rn(f0, f1);
@@ -562,6 +564,8 @@ struct LuParams {
   double *R_out, *J_out;
   int rmode;             // residual source: kResZero, kResLow, kResExact, or -1: per query
                          // from its iteration count (0 -> zero, 1 -> low, >= 2 -> exact)
+  int chord;             // 1: the Jacobian factored at iteration 2 serves the later iterations
+  int *Piv;              // [nq][nb]: pivot rows of the kept factorisation (chord)
 };
 
 // Residual source of one Newton iteration (the precision ladder of the inexact Newton):
@@ -573,6 +577,17 @@ enum { kResZero = 0, kResLow = 1, kResExact = 2, kResLadder = -1 };
 
 __device__ __forceinline__ int rung_of(int rmode, int iters) {
   return rmode >= 0 ? rmode : (iters == 0 ? kResZero : (iters == 1 ? kResLow : kResExact));
+}
+
+// Chord steps (Jacobian reuse): from the second FP64-residual iteration on (iteration count
+// >= 3), a query reuses the factorisation of its first one (count 2), kept in its [J | -R]
+// block with the pivot rows in Piv and marked by Rn[b].x = 1 (0 from the query's start); only
+// the residual is new.
+__device__ __forceinline__ bool chord_step(const LuParams &p, int b, int iters) {
+  return p.chord && p.rmode < 0 && iters >= 3 && p.Rn[b].x == 1.0;
+}
+__device__ __forceinline__ bool chord_keep(const LuParams &p, int iters) {
+  return p.chord && p.rmode < 0 && iters == 2;
 }
 
 
@@ -591,7 +606,7 @@ __host__ __device__ inline int aug_ld(int nb) {
 // part - f[k] (residual source RM). The 8 rows' loads of a column block are issued before their
 // arithmetic, and the row sums are reduce-scattered over the warp (df_warp_reduce8). Rows
 // k >= n are skipped. Returns sum_k R[k]^2 of the group in lane 0 (not EVAL).
-template <int RM, bool EVAL>
+template <int RM, bool EVAL, bool JAC>
 __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, int k0) {
   const int lane = threadIdx.x & 31;
   const int nb = p.nb;
@@ -617,11 +632,12 @@ __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, 
         const float *cr = jc + (size_t)r * nb + j;
         if (two && vec) {
           a[r] = __ldg(reinterpret_cast<const float4 *>(ar));
-          if (RM != kResZero) c[r] = __ldg(reinterpret_cast<const float2 *>(cr));
+          if (RM != kResZero && (JAC || RM == kResLow)) c[r] = __ldg(reinterpret_cast<const float2 *>(cr));
         } else {
           const float2 a0 = __ldg(ar), a1 = two ? __ldg(ar + 1) : make_float2(0.f, 0.f);
           a[r] = make_float4(a0.x, a0.y, a1.x, a1.y);
-          if (RM != kResZero) c[r] = make_float2(__ldg(cr), two ? __ldg(cr + 1) : 0.f);
+          if (RM != kResZero && (JAC || RM == kResLow))
+            c[r] = make_float2(__ldg(cr), two ? __ldg(cr + 1) : 0.f);
         }
       }
     }
@@ -643,7 +659,7 @@ __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, 
           double *jo = p.J_out + ((size_t)b * n + k0 + r) * n + j;
           jo[0] = (double)v0;
           if (two) jo[1] = (double)v1;
-        } else {
+        } else if (JAC) {  // a chord step keeps the factors stored in J's place
           float *jr = J + (size_t)r * p.lda + j;
           if (two) *reinterpret_cast<float2 *>(jr) = make_float2(v0, v1);
           else jr[0] = v0;
@@ -692,9 +708,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_newton_system(LuParams p) {
     const int k0 = 8 * g;
     if (k0 >= n) continue;
     const int rm = rung_of(p.rmode, qi.iters);
-    const double r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL>(p, b, n, k0)
-                      : rm == kResLow ? newton_rows8<kResLow, EVAL>(p, b, n, k0)
-                                      : newton_rows8<kResExact, EVAL>(p, b, n, k0);
+    const double r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL, true>(p, b, n, k0)
+                      : rm == kResLow ? newton_rows8<kResLow, EVAL, true>(p, b, n, k0)
+                      : (!EVAL && chord_step(p, b, qi.iters)) ? newton_rows8<kResExact, EVAL, false>(p, b, n, k0)
+                                                           : newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
     if (!EVAL && lane == 0) p.Rg[(size_t)b * G + g] = r2;
   }
 }
@@ -710,10 +727,11 @@ __device__ __forceinline__ double residual_norm(const LuParams &p, int b, int n)
 // Warp-per-query elimination of the systems k_newton_system assembled: copy the query's
 // augmented matrix into the warp's shared slab, solve, update u, apply the stopping rule.
 struct WarpLuSmem {
-  int pseq, J, per_warp;  // byte offsets within a warp's slab
+  int pseq, stp, J, per_warp;  // byte offsets within a warp's slab
   __host__ __device__ WarpLuSmem(int nb, int lda) {
     int p = 0;
     pseq = p; p += 4 * ((nb + 3) & ~3);
+    stp = p; p += 4 * ((nb + 3) & ~3);
     p = (p + 15) & ~15;
     J = p; p += 4 * nb * lda;
     per_warp = (p + 15) & ~15;
@@ -731,6 +749,7 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
   uint8_t *slab = smb + (size_t)w * L.per_warp;
   float *J = reinterpret_cast<float *>(slab + L.J);
   int *pseq = reinterpret_cast<int *>(slab + L.pseq);
+  int *stp = reinterpret_cast<int *>(slab + L.stp);
   const int ld = p.lda;
   int my_active = 0;
   for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
@@ -739,13 +758,16 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
     const int n = p.nsz ? p.nsz[b] : p.nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
+    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, qi.iters);
     const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
+    float4 *gJ = reinterpret_cast<float4 *>(p.Jaug + (size_t)b * p.nb * ld);
+    const int n4 = n * ld / 4;
     {
-      const float4 *src = reinterpret_cast<const float4 *>(p.Jaug + (size_t)b * p.nb * ld);
       float4 *dst = reinterpret_cast<float4 *>(J);
-      const int n4 = n * ld / 4;
 #pragma unroll 4
-      for (int i = lane; i < n4; i += 32) dst[i] = __ldg(src + i);
+      for (int i = lane; i < n4; i += 32) dst[i] = gJ[i];
+      if (chord)
+        for (int i = lane; i < n; i += 32) pseq[i] = p.Piv[(size_t)b * p.nb + i];
     }
     __syncwarp();
     qi.iters += 1;
@@ -754,9 +776,16 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
     float x[R];
     if (!isfinite(rn)) {
       qi.status = RB_Q_NONFINITE;
-    } else if (gepp_aug_warp<R>(J, ld, n, x, pseq)) {
+    } else if (chord ? chord_solve_warp<R>(J, ld, n, pseq, stp, x) : gepp_aug_warp<R>(J, ld, n, x, pseq)) {
       qi.status = RB_Q_SINGULAR;
     } else {
+      if (keep) {  // the factors (L in the eliminated places, U) and pivots for the chord steps
+        __syncwarp();
+        const float4 *src = reinterpret_cast<const float4 *>(J);
+        for (int i = lane; i < n4; i += 32) gJ[i] = src[i];
+        for (int i = lane; i < n; i += 32) p.Piv[(size_t)b * p.nb + i] = pseq[i];
+        if (lane == 0) p.Rn[b].x = 1.0;
+      }
       double dl = 0.0;
 #pragma unroll
       for (int s = 0; s < R; ++s) {
@@ -1335,7 +1364,8 @@ static void release_state(rb_ctx *ctx, MixedState *M) {
   for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2,
                   (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
-                  (void *)M->Amu, (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn})
+                  (void *)M->Amu, (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn,
+                  (void *)M->Piv})
     ctx_free(ctx, q);
   if (M->root == M) {
     for (auto &kv : M->buckets) {
@@ -1534,9 +1564,10 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   if (b_pad <= M->bcap) return RB_OK;
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
                   (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
-                  (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn})
+                  (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn, (void *)M->Piv})
     ctx_free(ctx, q);
   M->Jaug = nullptr;
+  M->Piv = nullptr;
   M->Bmu = nullptr;
   M->Rn = nullptr;
   M->Rg = nullptr;
@@ -1575,6 +1606,8 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
       return rc;
     M->Bmu = (float2 *)p;
   }
+  if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb, "pivot rows")) != RB_OK) return rc;
+  M->Piv = (int *)p;
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
   M->Jaug = (float *)p;
   const size_t groups = (size_t)(M->nb + 7) / 8;
@@ -1597,8 +1630,9 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
 
 static int launch_build_x(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
                           const rb_query_info *d_info, int mode, int digits, double *out, int nout,
-                          cudaStream_t st) {
+                          cudaStream_t st, int split = 1) {
   BuildXParams bx{};
+  bx.split = split;
   bx.o = ctx->ops;
   bx.theta = M->Th;
   bx.nsz = d_n;
@@ -1676,9 +1710,12 @@ static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const dou
 }
 
 // One Newton step's contraction work for the whole batch: X build + both GEMMs.
+// The contractions one Newton iteration needs: the Jacobian GEMM (jac) and the FP64-accurate
+// residual's sliced GEMM (exact).
 static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
-                          const rb_query_info *d_info, bool exact, cudaStream_t st) {
-  int rc = launch_build_x(ctx, M, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st);
+                          const rb_query_info *d_info, bool jac, bool exact, cudaStream_t st) {
+  if (!jac && !exact) return RB_OK;
+  int rc = launch_build_x(ctx, M, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st, jac ? 1 : 0);
   if (rc != RB_OK) return rc;
   TcGemmParams g = gemm_params(M, nq);
   g.n_tiles = M->Npad / kTcBN;
@@ -1689,11 +1726,14 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.ldj = M->Npad;
   g.Jc = M->Jc;
   g.nsplit = 3;
-  int mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
-  cudaError_t e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain,
-                                 use_pairs_plain(M));
-  prof_end(ctx, mk, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (Jacobian)");
+  int mk;
+  cudaError_t e;
+  if (jac) {
+    mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
+    e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain, use_pairs_plain(M));
+    prof_end(ctx, mk, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (Jacobian)");
+  }
   if (!exact) return RB_OK;
   g.kb[1] = M->kb1;
   g.n_tiles = M->WR.Npad / kTcBN;
@@ -1710,6 +1750,20 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
 
 static int launch_elimination(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStream_t st,
                               int kind);
+
+// Elimination variant of a bucket: the tuned one, else the forced one, else the default.
+static int elim_kind(const MixedState *M) {
+  if (M->tune.lu) return M->tune.lu;
+  const int epol = elim_policy(M->nb);
+  return epol ? epol : (M->nb <= kWarpLuMaxN ? 1 : 2);
+}
+// Chord steps (Jacobian reuse from the second FP64-residual iteration on) for buckets whose
+// elimination keeps its factors (the warp kernel); RB_CHORD=0 turns them off.
+static bool bucket_chord(const MixedState *M) {
+  const char *e = getenv("RB_CHORD");
+  if (e && *e && atoi(e) == 0) return false;
+  return elim_kind(M) == 1 && M->nb <= kWarpLuMaxN;
+}
 
 // Newton step of the batch: k_newton_system assembles [J | -R] per query, then one warp
 // (nb <= 80) or one CTA (blocked elimination) per query solves it, as the autotuner chose.
@@ -1732,9 +1786,7 @@ static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStrea
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
   }
   if (lp.eval_only) return RB_OK;
-  const int epol = elim_policy(M->nb);
-  return launch_elimination(ctx, M, lp, nq, st,
-                            M->tune.lu ? M->tune.lu : (epol ? epol : (M->nb <= kWarpLuMaxN ? 1 : 2)));
+  return launch_elimination(ctx, M, lp, nq, st, elim_kind(M));
 }
 
 template <int PB>
@@ -1912,6 +1964,8 @@ static LuParams solve_lu_params(rb_ctx *ctx, MixedState *M, const SolveArgs &a) 
   lp.info = a.info;
   lp.active = M->root->dev_words;  // one active count over all buckets
   lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
+  lp.chord = bucket_chord(M) ? 1 : 0;
+  lp.Piv = M->Piv;
   return lp;
 }
 
@@ -1932,15 +1986,16 @@ static int solve_prologue(rb_ctx *ctx, const std::vector<Part> &parts, cudaStrea
   return RB_OK;
 }
 
-// Newton iteration `rung` of every bucket (0: u = 0, 1: low-precision residual, 2: FP64-accurate
-// residual; the kernels pick each query's rung from its own iteration count).
-static int solve_iteration(rb_ctx *ctx, const std::vector<Part> &parts, int rung, cudaStream_t st) {
+// Newton iteration `it` of every bucket (0: u = 0, 1: low-precision residual, 2: FP64-accurate
+// residual, 3: the same, a chord step where the bucket keeps its factors; the kernels pick each
+// query's rung from its own iteration count).
+static int solve_iteration(rb_ctx *ctx, const std::vector<Part> &parts, int it, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(ctx->mixed->dev_words, 0, 4, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
   int rc;
   for (const Part &pt : parts) {
-    if (rung >= 1 &&
-        (rc = mixed_contract(ctx, pt.M, pt.a.nq, pt.a.n, pt.a.u, pt.a.info, rung >= 2, st)) != RB_OK)
+    const bool jac = it >= 1 && !(it >= 3 && bucket_chord(pt.M));
+    if ((rc = mixed_contract(ctx, pt.M, pt.a.nq, pt.a.n, pt.a.u, pt.a.info, jac, it >= 2, st)) != RB_OK)
       return rc;
     LuParams lp = solve_lu_params(ctx, pt.M, pt.a);
     if ((rc = launch_lu(ctx, pt.M, lp, pt.a.nq, st)) != RB_OK) return rc;
@@ -2180,7 +2235,7 @@ static int build_solve_graph(rb_ctx *ctx, const SolvePlan &pl, const std::vector
   do {
     if ((rc = plan_edges(ctx, pl, true, cs)) != RB_OK) break;
     if ((rc = solve_prologue(ctx, pl.parts, cs)) != RB_OK) break;
-    for (int r = 0; r < 2 && rc == RB_OK; ++r) {
+    for (int r = 0; r < 3 && rc == RB_OK; ++r) {
       if ((rc = solve_iteration(ctx, pl.parts, r, cs)) != RB_OK) break;
       k_loop_cond<<<1, 1, 0, cs>>>(h, M->dev_words, ctx->cfg.max_iter);
     }
@@ -2201,7 +2256,7 @@ static int build_solve_graph(rb_ctx *ctx, const SolvePlan &pl, const std::vector
     if ((e = cudaStreamBeginCaptureToGraph(cb, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                            cudaStreamCaptureModeRelaxed)) != cudaSuccess) break;
     body_open = true;
-    if ((rc = solve_iteration(ctx, pl.parts, 2, cb)) != RB_OK) break;
+    if ((rc = solve_iteration(ctx, pl.parts, 3, cb)) != RB_OK) break;
     k_loop_cond<<<1, 1, 0, cb>>>(h, M->dev_words, ctx->cfg.max_iter);
     cudaGraph_t bg;
     body_open = false;
@@ -2350,7 +2405,7 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   if ((rc = plan_edges(ctx, pl, true, st)) != RB_OK) return rc;
   if ((rc = solve_prologue(ctx, pl.parts, st)) != RB_OK) return rc;
   for (int it = 0; it < ctx->cfg.max_iter; ++it) {
-    if ((rc = solve_iteration(ctx, pl.parts, std::min(it, 2), st)) != RB_OK) return rc;
+    if ((rc = solve_iteration(ctx, pl.parts, std::min(it, 3), st)) != RB_OK) return rc;
     if ((rc = check_words(ctx, st, "mixed Newton step")) != RB_OK) return rc;
     if (R->h_words[0] == 0) break;
   }
@@ -2389,7 +2444,7 @@ int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, dou
   int rc;
   cudaMemsetAsync(M->dev_words, 0, 4, st);
   if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, d_n, info, st)) != RB_OK) return rc;
-  if (need_jacobian && (rc = mixed_contract(ctx, M, nq, d_n, d_u, info, need_exact, st)) != RB_OK)
+  if ((rc = mixed_contract(ctx, M, nq, d_n, d_u, info, need_jacobian, need_exact, st)) != RB_OK)
     return rc;
   const SolveArgs a{d_mu, nullptr, nq, d_n, d_u, nullptr, info};
   LuParams lp = solve_lu_params(ctx, M, a);
@@ -2433,7 +2488,7 @@ int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
   cudaMemsetAsync(M->dev_words, 0, 8, st);
   if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, nsz, info, st)) != RB_OK) return rc;
-  if ((rc = mixed_contract(ctx, M, nq, nsz, uw, info, true, st)) != RB_OK) return rc;
+  if ((rc = mixed_contract(ctx, M, nq, nsz, uw, info, true, true, st)) != RB_OK) return rc;
   const SolveArgs a{d_mu, nullptr, nq, nsz, uw, nullptr, info};
   LuParams lp = solve_lu_params(ctx, M, a);
   lp.rmode = kResExact;

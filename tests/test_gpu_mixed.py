@@ -128,6 +128,29 @@ def test_cta_elimination(rb, n, monkeypatch):
     assert rel(p, p_ref).max() <= 10 * TOL_MIXED
 
 
+@pytest.mark.parametrize("n", [20, 50, 72])
+def test_chord_steps(rb, n, monkeypatch):
+    """Jacobian reuse from the second FP64-residual iteration on: the converged velocity and
+    pressure are the oracle's with and without it, and it costs at most one extra iteration."""
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl, n_max=n)
+    q = synth.make_queries(wl, batch=300, n_max=n)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    o = oracle.Oracle.from_set(ops)
+    u_ref, p_ref, _ = o.solve(mu, threads=8)
+    res = {}
+    for chord in ("0", "1"):
+        monkeypatch.setenv("RB_CHORD", chord)
+        with rb.Context(rb.RB_PREC_MIXED) as ctx:
+            ctx.load_set(ops)
+            res[chord] = ctx.rb_solve(mu)
+    for u, p, info in res.values():
+        assert np.all(info["status"] == 0)
+        assert rel(u, u_ref).max() <= TOL_MIXED
+        assert rel(p, p_ref).max() <= 10 * TOL_MIXED
+    assert np.all(res["1"][2]["iters"] <= res["0"][2]["iters"] + 1)
+
+
 def test_manufactured_mixed(rb):
     ops = synth.make_operators(synth.WORKLOADS["single_n20"])
     oracle.manufacture(ops, (10.0, 200.0))
