@@ -263,7 +263,7 @@ __device__ bool gepp_solve_block(T *M, int ld, int n, T *b, double *red) {
 }
 
 // ---- warp-level elimination for small systems (one warp per system, FP32) ----------------
-// Lane r % 32 owns row r of the register-held vectors below: kWarpRows slots per lane.
+// Lane r % 32 owns row r of the register-held vectors below: up to kWarpRows slots per lane.
 constexpr int kWarpRows = 3;  // n <= 96
 
 // Pivot key of |v| in row i (i < 256): the magnitude's leading 15 mantissa bits, then the lower
@@ -271,43 +271,6 @@ constexpr int kWarpRows = 3;  // n <= 96
 // a relative 2^-15 preference for the first row).
 __device__ __forceinline__ unsigned pivot_key(float v, int i) {
   return (__float_as_uint(fabsf(v)) & 0xFFFFFF00u) | (unsigned)(255 - i);
-}
-
-// The value that row k's owner lane holds in y[k / 32], broadcast to all lanes.
-__device__ __forceinline__ float row_value(const float (&y)[kWarpRows], int k) {
-  const int s = k >> 5;
-  const float v = s == 0 ? y[0] : (s == 1 ? y[1] : y[2]);
-  return __shfl_sync(0xffffffffu, v, k & 31);
-}
-
-// Back substitution with the upper triangle of M (row stride ld): y holds the right-hand side
-// (lane-owned rows) and receives the solution.
-__device__ __forceinline__ void backsub_warp(const float *M, int ld, int n, float (&y)[kWarpRows]) {
-  const int lane = threadIdx.x & 31;
-  float d[kWarpRows];
-#pragma unroll
-  for (int s = 0; s < kWarpRows; ++s) {
-    const int k = lane + 32 * s;
-    d[s] = k < n ? __frcp_rn(M[k * ld + k]) : 0.f;
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    float own[kWarpRows];
-#pragma unroll
-    for (int s = 0; s < kWarpRows; ++s) own[s] = y[s] * d[s];
-    const float xj = row_value(own, j);
-#pragma unroll
-    for (int s = 0; s < kWarpRows; ++s) {
-      const int k = lane + 32 * s;
-      if (k < j) y[s] = fmaf(-M[k * ld + j], xj, y[s]);
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < kWarpRows; ++s) y[s] *= d[s];
-}
-
-// Select lane-slot s of a 3-slot register vector (s warp-uniform or per lane).
-__device__ __forceinline__ float slot3(const float (&v)[kWarpRows], int s) {
-  return s == 0 ? v[0] : (s == 1 ? v[1] : v[2]);
 }
 
 // Element s of a register vector of R lane slots (s warp-uniform or per lane), without local
@@ -700,71 +663,6 @@ __device__ __forceinline__ bool gepp_aug_cta(float *M, int ld, int n, int *pseq,
   }
   __syncthreads();
   return false;
-}
-
-// Warp LU factorisation with partial pivoting (pivot_key) and whole-row swaps, kept for several
-// right-hand sides: M (row stride ld, odd for conflict-free column reads) receives U on and above
-// the diagonal and the unit-lower multipliers below it; perm[i] = original row now at row i.
-// Returns true if a pivot was zero or not finite.
-__device__ __forceinline__ bool lu_factor_warp(float *M, int ld, int n, int *perm) {
-  const int lane = threadIdx.x & 31;
-  for (int i = lane; i < n; i += 32) perm[i] = i;
-  __syncwarp();
-  for (int p = 0; p < n; ++p) {
-    unsigned key = 0;
-    for (int i = p + lane; i < n; i += 32) {
-      const unsigned k = pivot_key(M[i * ld + p], i);
-      key = k > key ? k : key;
-    }
-    key = __reduce_max_sync(0xffffffffu, key);
-    const int piv = 255 - (int)(key & 255u);
-    if (piv != p) {
-      for (int j = lane; j < n; j += 32) {
-        const float t = M[p * ld + j];
-        M[p * ld + j] = M[piv * ld + j];
-        M[piv * ld + j] = t;
-      }
-      if (lane == 0) {
-        const int t = perm[p];
-        perm[p] = perm[piv];
-        perm[piv] = t;
-      }
-      __syncwarp();
-    }
-    const float pv = M[p * ld + p];
-    if (!(fabsf(pv) > 0.f) || !isfinite(pv)) return true;
-    const float rinv = __frcp_rn(pv);
-    const float *mp = M + p * ld;
-    for (int i = p + 1 + lane; i < n; i += 32) {
-      float *mi = M + i * ld;
-      const float l = mi[p] * rinv;
-      mi[p] = l;
-      for (int j = p + 1; j < n; ++j) mi[j] = fmaf(-l, mp[j], mi[j]);
-    }
-    __syncwarp();
-  }
-  return false;
-}
-
-// Solve with the factors of lu_factor_warp: x = U^-1 L^-1 (b permuted by perm). b is in shared
-// memory (length n); row k of the solution is returned in x[k / 32] of lane k % 32.
-__device__ __forceinline__ void lu_solve_warp(const float *M, int ld, int n, const int *perm,
-                                              const float *b, float (&x)[kWarpRows]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < kWarpRows; ++s) {
-    const int k = lane + 32 * s;
-    x[s] = k < n ? b[perm[k]] : 0.f;
-  }
-  for (int j = 0; j + 1 < n; ++j) {  // unit lower triangle
-    const float xj = row_value(x, j);
-#pragma unroll
-    for (int s = 0; s < kWarpRows; ++s) {
-      const int k = lane + 32 * s;
-      if (k > j && k < n) x[s] = fmaf(-M[k * ld + j], xj, x[s]);
-    }
-  }
-  backsub_warp(M, ld, n, x);
 }
 
 }  // namespace rb

@@ -1213,26 +1213,33 @@ struct PresSolveParams {
 
 constexpr int kPresRefine = 2;
 
-// shared-memory slab of one warp's pressure solve (bytes)
+// shared-memory slab of one warp's pressure solve (bytes): B(mu) in double-float (for the
+// refinement residuals) and [B | r] in FP32 (row stride aug_ld(m)), factored in place.
 struct PresSmem {
-  int th, r, pv, pf, Bd, Bf, rf, perm, total, ldd, ldb;
+  int th, r, pv, pf, Bd, Ba, pseq, stp, total, ldd, lda;
   __host__ __device__ PresSmem(const DevOps &o) {
-    const int m = o.m;
+    const int m = o.m, m4 = (m + 3) & ~3;
     ldd = odd_ld(m);
-    ldb = odd_ld(m);
+    lda = aug_ld(m);
     int p = 0;
     th = p; p += 8 * ((o.n_theta + 1) & ~1);
     r = p; p += 8 * m;
     pv = p; p += 8 * m;
     pf = p; p += 8 * m;
     Bd = p; p += 8 * m * ldd;
-    Bf = p; p += 4 * m * ldb;
-    rf = p; p += 4 * m;
-    perm = p; p += 4 * m;
+    p = (p + 15) & ~15;
+    Ba = p; p += 4 * m * lda;
+    pseq = p; p += 4 * m4;
+    stp = p; p += 4 * m4;
     total = (p + 15) & ~15;
   }
 };
 
+// B(mu) p = r per converged query, one warp: [fl32(B) | fl32(r)] eliminated by the panel-4 warp
+// routine (gepp_aug_warp), which leaves its factors in place; each of the kPresRefine
+// refinement steps puts the residual r - B(mu) p (double-float) in the right-hand-side column
+// and solves with those factors (chord_solve_warp). R lane slots: m <= 32 R.
+template <int R>
 __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
   const DevOps &o = p.o;
@@ -1242,9 +1249,10 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParam
   uint8_t *slab = smb + (size_t)w * L.total;
   double *th = (double *)(slab + L.th), *r = (double *)(slab + L.r), *pv = (double *)(slab + L.pv);
   float2 *pf = (float2 *)(slab + L.pf), *Bd = (float2 *)(slab + L.Bd);
-  float *Bf = (float *)(slab + L.Bf), *rf = (float *)(slab + L.rf);
-  int *perm = (int *)(slab + L.perm);
-  const int ldd = L.ldd, ldb = L.ldb;
+  float *Ba = (float *)(slab + L.Ba);
+  int *pseq = (int *)(slab + L.pseq), *stp = (int *)(slab + L.stp);
+  const int ldd = L.ldd, lda = L.lda;
+  const int c_pad = ((m >> 2) << 2) + 4;  // right-hand side in column m, zero padding to c_pad
   for (int b = blockIdx.x * wpc + w; b < p.nq; b += gridDim.x * wpc) {
     double *prow = p.p_out + (size_t)b * m;
     if (p.info[b].status != RB_Q_OK) {
@@ -1258,33 +1266,34 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParam
       double sf = 0.0;
       for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
       r[k] = sf - p.Rp[(size_t)b * m + k] - p.Asu[(size_t)b * m + k];
-      rf[k] = (float)r[k];
+      float *row = Ba + k * lda;
+      row[m] = (float)r[k];
+      for (int c = m + 1; c < c_pad; ++c) row[c] = 0.f;
     }
-    __syncwarp();
-    // B(mu) (double-float, built at the query's start) and its FP32 rounding for the factorisation
+    // B(mu) (double-float, built at the query's start) and its FP32 rounding for the elimination
     {
       const float2 *bq = p.Bmu + (size_t)b * mm;
       for (int e = lane; e < mm; e += 32) {
         const float2 v = __ldg(bq + e);
         const int k = e / m, j = e - k * m;
         Bd[k * ldd + j] = v;
-        Bf[k * ldb + j] = v.x + v.y;
+        Ba[k * lda + j] = v.x + v.y;
       }
     }
     __syncwarp();
-    if (lu_factor_warp(Bf, ldb, m, perm)) {
+    float x[R];
+    if (gepp_aug_warp<R>(Ba, lda, m, x, pseq)) {
       for (int i = lane; i < m; i += 32) prow[i] = 0.0;
       if (lane == 0) p.info[b].status = RB_Q_SINGULAR;
       __syncwarp();
       continue;
     }
-    float x[kWarpRows];
-    lu_solve_warp(Bf, ldb, m, perm, rf, x);
 #pragma unroll
-    for (int s = 0; s < kWarpRows; ++s)
+    for (int s = 0; s < R; ++s)
       if (lane + 32 * s < m) pv[lane + 32 * s] = (double)x[s];
     __syncwarp();
-    for (int it = 0; it < kPresRefine; ++it) {
+    bool bad = false;
+    for (int it = 0; it < kPresRefine && !bad; ++it) {
       // residual r - B(mu) p, rows owned by lanes, p as double-float pairs
       for (int j = lane; j < m; j += 32) {
         float ph, pl;
@@ -1296,13 +1305,13 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParam
         float h = 0.f, l = 0.f;
         const float2 *bk = Bd + k * ldd;
         for (int j = 0; j < m; ++j) df_fma(h, l, bk[j].x, bk[j].y, pf[j].x, pf[j].y);
-        rf[k] = (float)(r[k] - ((double)h + (double)l));
+        Ba[k * lda + m] = (float)(r[k] - ((double)h + (double)l));
       }
       __syncwarp();
-      lu_solve_warp(Bf, ldb, m, perm, rf, x);
+      bad = chord_solve_warp<R>(Ba, lda, m, pseq, stp, x);
 #pragma unroll
-      for (int s = 0; s < kWarpRows; ++s)
-        if (lane + 32 * s < m) pv[lane + 32 * s] += (double)x[s];
+      for (int s = 0; s < R; ++s)
+        if (!bad && lane + 32 * s < m) pv[lane + 32 * s] += (double)x[s];
       __syncwarp();
     }
     for (int i = lane; i < m; i += 32) prow[i] = pv[i];
@@ -1916,9 +1925,10 @@ static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   if (o.m <= 32 * kWarpRows && per_warp <= 24 * 1024) {
     const int wpc = std::max(1, std::min(8, (int)((192 * 1024) / per_warp)));
     const size_t smem = wpc * per_warp;
-    e = cudaFuncSetAttribute(k_pressure_solve_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = o.m <= 32 ? k_pressure_solve_warp<1> : (o.m <= 64 ? k_pressure_solve_warp<2> : k_pressure_solve_warp<3>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_pressure_solve_warp attr");
-    k_pressure_solve_warp<<<std::max(1, std::min((nq + wpc - 1) / wpc, ctx->sms * 8)), 32 * wpc, smem, st>>>(pp);
+    kern<<<std::max(1, std::min((nq + wpc - 1) / wpc, ctx->sms * 8)), 32 * wpc, smem, st>>>(pp);
   } else {
     const size_t smem = PresBlockSmem(o).total;
     e = cudaFuncSetAttribute(k_pressure_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
