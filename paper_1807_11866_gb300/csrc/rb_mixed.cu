@@ -565,6 +565,8 @@ struct LuParams {
   int rmode;             // residual source: kResZero, kResLow, kResExact, or -1: per query
                          // from its iteration count (0 -> zero, 1 -> low, >= 2 -> exact)
   int chord;             // 1: the Jacobian factored at iteration 2 serves the later iterations
+  int rung_all;          // -1, or the rung every active query of the launch is on (0 zero,
+                         // 1 low, 2 FP64-accurate, 3 FP64-accurate chord step)
   int *Piv;              // [nq][nb]: pivot rows of the kept factorisation (chord)
 };
 
@@ -694,8 +696,11 @@ __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, 
 // [J | -R] (FP32, row stride lda, the right-hand side in column n, zero padding up to the next
 // multiple of 4) and the group's sum of R[k]^2 to Rg[b][g] (the elimination adds the groups in
 // order: deterministic). With EVAL, J and R go to J_out / R_out in FP64 instead.
-template <bool EVAL>
-__global__ void __launch_bounds__(kThreads, 2) k_newton_system(LuParams p) {
+// FIXED >= 0: every active query of the launch is on rung FIXED (LuParams::rung_all), so the
+// kernel holds one variant only (fewer registers, more resident warps); -1: per query.
+constexpr int system_blocks(int fixed) { return fixed == 0 || fixed == 3 ? 3 : 2; }
+template <bool EVAL, int FIXED>
+__global__ void __launch_bounds__(kThreads, system_blocks(FIXED)) k_newton_system(LuParams p) {
   const int lane = threadIdx.x & 31;
   const int G = (p.nb + 7) >> 3;
   const long long units = (long long)p.nq * G;
@@ -707,11 +712,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_newton_system(LuParams p) {
     const int n = p.nsz ? p.nsz[b] : p.nb;
     const int k0 = 8 * g;
     if (k0 >= n) continue;
-    const int rm = rung_of(p.rmode, qi.iters);
-    const double r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL, true>(p, b, n, k0)
-                      : rm == kResLow ? newton_rows8<kResLow, EVAL, true>(p, b, n, k0)
-                      : (!EVAL && chord_step(p, b, qi.iters)) ? newton_rows8<kResExact, EVAL, false>(p, b, n, k0)
-                                                           : newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
+    double r2;
+    if (FIXED == 0) {
+      r2 = newton_rows8<kResZero, EVAL, true>(p, b, n, k0);
+    } else if (FIXED == 1) {
+      r2 = newton_rows8<kResLow, EVAL, true>(p, b, n, k0);
+    } else if (FIXED == 2) {
+      r2 = newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
+    } else if (FIXED == 3) {
+      r2 = newton_rows8<kResExact, EVAL, false>(p, b, n, k0);
+    } else {
+      const int rm = rung_of(p.rmode, qi.iters);
+      r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL, true>(p, b, n, k0)
+           : rm == kResLow ? newton_rows8<kResLow, EVAL, true>(p, b, n, k0)
+           : (!EVAL && chord_step(p, b, qi.iters)) ? newton_rows8<kResExact, EVAL, false>(p, b, n, k0)
+                                                   : newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
+    }
     if (!EVAL && lane == 0) p.Rg[(size_t)b * G + g] = r2;
   }
 }
@@ -1788,8 +1804,15 @@ static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStrea
     const long long units = (long long)nq * ((M->nb + 7) / 8);
     const int grid = (int)std::max(1LL, std::min((units + kWarps - 1) / kWarps, 2LL * ctx->sms));
     const int mk = prof_begin(ctx, RB_K_SYSTEM, st);
-    if (lp.eval_only) k_newton_system<true><<<grid, kThreads, 0, st>>>(lp);
-    else k_newton_system<false><<<grid, kThreads, 0, st>>>(lp);
+    const int fixed = lp.eval_only ? -1 : lp.rung_all;
+    const long long per_sm = system_blocks(fixed);
+    const int grid2 = (int)std::max(1LL, std::min((units + kWarps - 1) / kWarps, per_sm * ctx->sms));
+    if (lp.eval_only) k_newton_system<true, -1><<<grid, kThreads, 0, st>>>(lp);
+    else if (fixed == 0) k_newton_system<false, 0><<<grid2, kThreads, 0, st>>>(lp);
+    else if (fixed == 1) k_newton_system<false, 1><<<grid2, kThreads, 0, st>>>(lp);
+    else if (fixed == 2) k_newton_system<false, 2><<<grid2, kThreads, 0, st>>>(lp);
+    else if (fixed == 3) k_newton_system<false, 3><<<grid2, kThreads, 0, st>>>(lp);
+    else k_newton_system<false, -1><<<grid, kThreads, 0, st>>>(lp);
     prof_end(ctx, mk, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
@@ -1976,6 +1999,7 @@ static LuParams solve_lu_params(rb_ctx *ctx, MixedState *M, const SolveArgs &a) 
   lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
   lp.chord = bucket_chord(M) ? 1 : 0;
   lp.Piv = M->Piv;
+  lp.rung_all = -1;
   return lp;
 }
 
@@ -2008,6 +2032,8 @@ static int solve_iteration(rb_ctx *ctx, const std::vector<Part> &parts, int it, 
     if ((rc = mixed_contract(ctx, pt.M, pt.a.nq, pt.a.n, pt.a.u, pt.a.info, jac, it >= 2, st)) != RB_OK)
       return rc;
     LuParams lp = solve_lu_params(ctx, pt.M, pt.a);
+    // every active query of a batch solve is on iteration `it`
+    lp.rung_all = it == 0 ? 0 : (it == 1 ? 1 : (it >= 3 && lp.chord ? 3 : 2));
     if ((rc = launch_lu(ctx, pt.M, lp, pt.a.nq, st)) != RB_OK) return rc;
   }
   return RB_OK;
