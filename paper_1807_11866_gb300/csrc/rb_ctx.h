@@ -46,10 +46,10 @@ bool serve_running(const rb_ctx *ctx);
 // mixed-path pieces used by the server
 int mixed_prepare(rb_ctx *ctx, int capacity, cudaStream_t st);
 size_t mixed_slot_bytes(const rb_ctx *ctx);
-int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, double *d_u,
-                    rb_query_info *info, bool need_jacobian, bool need_exact, cudaStream_t st);
-int mixed_pressure_ok(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, const double *d_u,
-                      double *d_p, rb_query_info *info, cudaStream_t st);
+int mixed_serve_step(rb_ctx *ctx, const double *d_mu, const int *d_n, double *d_u, double *d_p,
+                     rb_query_info *d_info, const std::vector<int> &slots,
+                     const std::vector<int> &slot_n, const std::vector<int> &slot_iters,
+                     std::vector<int> &perm, cudaStream_t st);
 int mixed_error_word(rb_ctx *ctx, cudaStream_t st);
 int mixed_tuning(rb_ctx *ctx, int i, int *out6, float *ms3);
 

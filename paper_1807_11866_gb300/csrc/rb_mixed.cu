@@ -231,6 +231,25 @@ __global__ void k_gather(int nq, const int *perm, const double *mu, const double
   }
 }
 
+// Serving slots into a size-bucketed batch: mu, n, u and info of slot perm[i] to row i (one
+// warp per query).
+__global__ void k_gather_slots(int nq, const int *perm, int nm, const double *mu, const int *n,
+                               const double *u, const rb_query_info *info, double *mu_g, int *n_g,
+                               double *u_g, rb_query_info *info_g) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nq; i += nw) {
+    const int s = perm[i];
+    for (int j = lane; j < nm; j += 32) u_g[(size_t)i * nm + j] = u[(size_t)s * nm + j];
+    if (lane == 0) {
+      mu_g[2 * i] = mu[2 * s];
+      mu_g[2 * i + 1] = mu[2 * s + 1];
+      n_g[i] = n[s];
+      info_g[i] = info[s];
+    }
+  }
+}
+
 // Results back to the caller's order: dst[perm[i]] = src[i] (one warp per query).
 __global__ void k_scatter(int nq, const int *perm, int nm, int m, const double *u_g,
                           const double *p_g, const rb_query_info *info_g, double *u, double *p,
@@ -450,10 +469,16 @@ struct PrepParams {
   double *Fm;                   // [nq][nb]
   const int *nsz;               // [nq] sizes, or null: all nb
   double2 *Rn;                  // [nq]: (0, max(1, ||f(mu)||)) of the starting queries
+  int all;                      // 1: every active query, not only the starting ones
 };
 
 __device__ __forceinline__ bool starts(const rb_query_info &q, int max_iter) {
   return is_active(q, max_iter) && q.iters == 0;
+}
+// queries whose per-query data (theta, f, A(mu), B(mu)) is built: those that start, or every
+// active one (all: the serving path rebuilds it in each step's size-bucketed batch)
+__device__ __forceinline__ bool prepares(const rb_query_info &q, int max_iter, int all) {
+  return is_active(q, max_iter) && (all || q.iters == 0);
 }
 
 // theta and f(mu) of the starting queries, one warp per query.
@@ -462,7 +487,7 @@ __global__ void k_prep_theta(PrepParams p) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < p.nq; b += nw) {
-    if (!starts(p.info[b], p.max_iter)) continue;
+    if (!prepares(p.info[b], p.max_iter, p.all)) continue;
     double *th = p.Th + (size_t)b * o.n_theta;
     if (p.theta_in) {
       for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta_in[(size_t)b * o.n_theta + i];
@@ -491,7 +516,7 @@ __global__ void k_prep_theta(PrepParams p) {
 constexpr int kAsmQ = 8;
 
 struct AffineParams {
-  int nq, max_iter, n_theta, th_off, qn;
+  int nq, max_iter, all, n_theta, th_off, qn;
   size_t nn;                  // elements per matrix
   const rb_query_info *info;
   const double *Th;           // [nq][n_theta]
@@ -509,7 +534,7 @@ __global__ void __launch_bounds__(256) k_affine_sum(AffineParams p) {
     __syncthreads();
     if (threadIdx.x < kAsmQ) {
       const int b = b0 + threadIdx.x;
-      flag[threadIdx.x] = b < p.nq && starts(p.info[b], p.max_iter);
+      flag[threadIdx.x] = b < p.nq && prepares(p.info[b], p.max_iter, p.all);
     }
     __syncthreads();
     int any = 0;
@@ -1444,14 +1469,18 @@ static int pair_policy() {
   return v <= 0 ? 0 : (v == 1 ? 1 : 2);
 }
 constexpr int kWideMinN = 32;  // the wide sliced variant needs nj >= 32 (two row changes per part)
+// Untuned defaults (the serving path, RB_AUTOTUNE=0): what the tuner picks on the benchmark
+// workloads — CTA pairs for the Jacobian GEMM from n = 40, the wide sliced tiles from n = 32.
 static bool use_pairs_plain(const MixedState *M) {
   if (M->tune.klass >= 0) return M->tune.pair_plain != 0;
-  return pair_policy() >= 1;
+  const int pol = pair_policy();
+  return pol >= 0 ? pol >= 1 : M->nb >= 40;
 }
 // sliced GEMM variant: 0 single CTAs, 1 CTA pairs, 2 CTA pairs with 256-column tiles
 static int sliced_variant(const MixedState *M) {
   if (M->tune.klass >= 0) return M->tune.pair_sliced;
   const int pol = pair_policy();
+  if (pol < 0) return M->nb >= kWideMinN ? 2 : 0;
   return pol == 2 ? (M->nb >= kWideMinN ? 2 : 1) : (pol == 1 ? 1 : 0);
 }
 static cudaError_t launch_sliced(const MixedState *M, const SlicedW &W, const TcGemmParams &g,
@@ -1703,7 +1732,8 @@ static TcGemmParams gemm_params(MixedState *M, int nq) {
 
 // theta rows, f(mu) and A(mu) of the queries that start (active, iteration count 0).
 static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const double *d_theta,
-                       int nq, const int *nsz, const rb_query_info *info, cudaStream_t st) {
+                       int nq, const int *nsz, const rb_query_info *info, cudaStream_t st,
+                       int all = 0) {
   const DevOps &o = ctx->ops;
   PrepParams pp{};
   pp.o = o;
@@ -1717,10 +1747,11 @@ static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const dou
   pp.Fm = M->Fm;
   pp.nsz = nsz;
   pp.Rn = M->Rn;
+  pp.all = all;
   const int mk = prof_begin(ctx, RB_K_PREP, st);
   k_prep_theta<<<std::max(1, std::min((nq + 7) / 8, ctx->sms * 16)), 256, 0, st>>>(pp);
   auto affine = [&](const float2 *Q2, int qn, int th_off, size_t nn, float2 *out) {
-    AffineParams ap{nq, ctx->cfg.max_iter, o.n_theta, th_off, qn, nn, info, M->Th, Q2, out};
+    AffineParams ap{nq, ctx->cfg.max_iter, all, o.n_theta, th_off, qn, nn, info, M->Th, Q2, out};
     dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024),
               (unsigned)std::max(1, std::min((nq + kAsmQ - 1) / kAsmQ, 65535)));
     k_affine_sum<<<grid, 256, sizeof(float2) * kAsmQ * qn, st>>>(ap);
@@ -1776,11 +1807,12 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
 static int launch_elimination(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStream_t st,
                               int kind);
 
-// Elimination variant of a bucket: the tuned one, else the forced one, else the default.
+// Elimination variant of a bucket: the tuned one, else the forced one, else the default (warp
+// per query up to n = 80, CTA per query up to 128, blocked above).
 static int elim_kind(const MixedState *M) {
   if (M->tune.lu) return M->tune.lu;
   const int epol = elim_policy(M->nb);
-  return epol ? epol : (M->nb <= kWarpLuMaxN ? 1 : 2);
+  return epol ? epol : (M->nb <= kWarpLuMaxN ? 1 : (M->nb <= kCtaLuMaxN ? 4 : 2));
 }
 // Chord steps (Jacobian reuse from the second FP64-residual iteration on) for buckets whose
 // elimination keeps its factors (the warp kernel); RB_CHORD=0 turns them off.
@@ -2472,27 +2504,81 @@ size_t mixed_slot_bytes(const rb_ctx *ctx) {
          4 * nb * (size_t)aug_ld((int)nb) + 16 + 8 * ((nb + 7) / 8) + 8 * (size_t)o.m * o.m;
 }
 
-// One Newton iteration for every live slot: the contraction work the slots' ladder rungs need,
-// then elimination and update (no host synchronisation).
-int mixed_iteration(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, double *d_u,
-                    rb_query_info *info, bool need_jacobian, bool need_exact, cudaStream_t st) {
-  MixedState *M = ctx->mixed;
+// One serving step, size-bucketed: the live slots (host lists of slot, size and iteration count)
+// are grouped by bucket size, adjacent buckets merged from the largest down until each group
+// holds at least kServeGroupMin queries (a group runs at its largest size: few live queries make
+// one batch, as many launches as a batch solve; many make one per size range), and gathered into
+// the groups' batches; each group rebuilds the
+// per-query data of its queries (theta, f, A(mu), B(mu); slots change places between steps, so
+// nothing per query is kept across steps and the Jacobian is refactored each iteration), runs
+// one Newton iteration with the contractions its queries' rungs need, recovers the pressure of
+// the queries that converge, and the slots get u, p and the status back.
+constexpr int kServeGroupMin = 512;
+int mixed_serve_step(rb_ctx *ctx, const double *d_mu, const int *d_n, double *d_u, double *d_p,
+                     rb_query_info *d_info, const std::vector<int> &slots,
+                     const std::vector<int> &slot_n, const std::vector<int> &slot_iters,
+                     std::vector<int> &perm, cudaStream_t st) {
+  MixedState *R = ctx->mixed;
+  const DevOps &o = ctx->ops;
+  const int nm = o.n_max, mm = std::max(o.m, 1);
+  struct Group { MixedState *M; int off, cnt; bool jac, exact; };
+  std::map<int, std::vector<int>> by;
+  for (size_t i = 0; i < slots.size(); ++i) {
+    const int n = slot_n[i];
+    if (n < 1 || n > nm) continue;  // rejected at admission: nothing to compute
+    by[bucket_size(n, nm)].push_back((int)i);
+  }
+  // merge adjacent buckets, largest first, into groups of at least kServeGroupMin queries
+  std::vector<std::pair<int, std::vector<int>>> merged;  // (group size nb, members)
+  for (auto it = by.rbegin(); it != by.rend(); ++it) {
+    if (merged.empty() || (int)merged.back().second.size() >= kServeGroupMin)
+      merged.push_back({it->first, {}});
+    auto &mem = merged.back().second;
+    mem.insert(mem.end(), it->second.begin(), it->second.end());
+  }
+  perm.clear();
+  std::vector<Group> groups;
   int rc;
-  cudaMemsetAsync(M->dev_words, 0, 4, st);
-  if ((rc = launch_prep(ctx, M, d_mu, nullptr, nq, d_n, info, st)) != RB_OK) return rc;
-  if ((rc = mixed_contract(ctx, M, nq, d_n, d_u, info, need_jacobian, need_exact, st)) != RB_OK)
-    return rc;
-  const SolveArgs a{d_mu, nullptr, nq, d_n, d_u, nullptr, info};
-  LuParams lp = solve_lu_params(ctx, M, a);
-  return launch_lu(ctx, M, lp, nq, st);
-}
-
-// Pressure for every slot whose status is RB_Q_OK.
-int mixed_pressure_ok(rb_ctx *ctx, const double *d_mu, int nq, const int *d_n, const double *d_u,
-                      double *d_p, rb_query_info *info, cudaStream_t st) {
-  if (!(ctx->ops.m > 0 && ctx->ops.B && d_p)) return RB_OK;
-  (void)d_mu;
-  return mixed_pressure(ctx, ctx->mixed, nq, d_n, d_u, d_p, info, st);
+  for (auto &kv : merged) {
+    MixedState *M = kv.first == nm ? R : bucket(ctx, kv.first);
+    if ((rc = mixed_layouts(ctx, M, st)) != RB_OK) return rc;
+    if ((rc = mixed_batch_scratch(ctx, M, (int)kv.second.size())) != RB_OK) return rc;
+    Group g{M, (int)perm.size(), (int)kv.second.size(), false, false};
+    for (int i : kv.second) {
+      perm.push_back(slots[i]);
+      g.jac |= slot_iters[i] >= 1;
+      g.exact |= slot_iters[i] >= 2;
+    }
+    groups.push_back(g);
+  }
+  const int total = (int)perm.size();
+  if (total == 0) return RB_OK;
+  if ((rc = gather_scratch(ctx, total, false)) != RB_OK) return rc;
+  // perm stays alive until the caller synchronises the stream at the end of the step
+  cudaError_t e = cudaMemcpyAsync(R->perm, perm.data(), 4 * (size_t)total, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "serve bucket order");
+  k_gather_slots<<<std::max(1, std::min((total + 7) / 8, ctx->sms * 8)), 256, 0, st>>>(
+      total, R->perm, nm, d_mu, d_n, d_u, d_info, R->mu_g, R->n_g, R->u_g, R->info_g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "k_gather_slots");
+  const bool pres = d_p && o.m > 0 && o.B;
+  for (const Group &g : groups) {
+    const SolveArgs a{R->mu_g + 2 * (size_t)g.off, nullptr, g.cnt, R->n_g + g.off,
+                      R->u_g + (size_t)g.off * nm, pres ? R->p_g + (size_t)g.off * mm : nullptr,
+                      R->info_g + g.off};
+    cudaMemsetAsync(R->dev_words, 0, 4, st);
+    if ((rc = launch_prep(ctx, g.M, a.mu, nullptr, g.cnt, a.n, a.info, st, 1)) != RB_OK) return rc;
+    if ((rc = mixed_contract(ctx, g.M, g.cnt, a.n, a.u, a.info, g.jac, g.exact, st)) != RB_OK) return rc;
+    LuParams lp = solve_lu_params(ctx, g.M, a);
+    lp.chord = 0;
+    if ((rc = launch_lu(ctx, g.M, lp, g.cnt, st)) != RB_OK) return rc;
+    if (pres && g.exact && (rc = mixed_pressure(ctx, g.M, g.cnt, a.n, a.u, a.p, a.info, st)) != RB_OK)
+      return rc;
+  }
+  k_scatter<<<std::max(1, std::min((total + 7) / 8, ctx->sms * 8)), 256, 0, st>>>(
+      total, R->perm, nm, mm, R->u_g, pres ? R->p_g : nullptr, R->info_g, d_u, pres ? d_p : nullptr,
+      d_info);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "k_scatter");
+  return RB_OK;
 }
 
 int mixed_error_word(rb_ctx *ctx, cudaStream_t st) {

@@ -57,6 +57,8 @@ struct ServeState {
   int cap = 0;
   std::vector<uint64_t> slot_ticket;
   std::vector<int> slot_iters;
+  std::vector<int> slot_n;
+  std::vector<int> live, live_n, live_it, perm;  // host scratch of one step
   std::vector<Clock::time_point> slot_t0;
   std::set<int> free_slots;   // lowest index first, so live slots stay packed at the front
   // device slot arrays
@@ -182,6 +184,7 @@ static int serve_step(rb_ctx *ctx, ServeState *S, bool &idle) {
       S->free_slots.erase(S->free_slots.begin());
       S->slot_ticket[s] = q.ticket;
       S->slot_iters[s] = 0;
+      S->slot_n[s] = q.n;
       S->slot_t0[s] = q.t0;
       S->h_idx[K] = s;
       S->h_mu[2 * K] = q.mu[0];
@@ -202,22 +205,22 @@ static int serve_step(rb_ctx *ctx, ServeState *S, bool &idle) {
   // 2. one Newton iteration for every live slot (the whole solve for FP64 contexts)
   int rc;
   if (mixed) {
-    // the step covers slots 0 .. live - 1 (admission fills the lowest free slots first)
-    bool need_j = false, need_x = false;
-    int live = 0;
+    // one Newton iteration of every live slot, in size buckets (pressure of the slots that
+    // converge in it included)
+    S->live.clear();
+    S->live_n.clear();
+    S->live_it.clear();
     for (int s = 0; s < S->cap; ++s)
       if (S->slot_ticket[s]) {
-        need_j |= S->slot_iters[s] >= 1;
-        need_x |= S->slot_iters[s] >= 2;
-        live = s + 1;
+        S->live.push_back(s);
+        S->live_n.push_back(S->slot_n[s]);
+        S->live_it.push_back(S->slot_iters[s]);
       }
-    rc = live ? mixed_iteration(ctx, S->d_mu, live, S->d_n, S->d_u, S->d_info, need_j, need_x, st) : RB_OK;
+    rc = mixed_serve_step(ctx, S->d_mu, S->d_n, S->d_u, m > 0 ? S->d_p : nullptr, S->d_info, S->live,
+                          S->live_n, S->live_it, S->perm, st);
     if (rc != RB_OK) return rc;
     for (int s = 0; s < S->cap; ++s)
       if (S->slot_ticket[s]) S->slot_iters[s] += 1;
-    // 3. pressure of the slots that converged in this step
-    if (m > 0 && live && (rc = mixed_pressure_ok(ctx, S->d_mu, live, S->d_n, S->d_u, S->d_p, S->d_info, st)) != RB_OK)
-      return rc;
     if ((rc = mixed_error_word(ctx, st)) != RB_OK) return rc;
   } else if (K > 0) {  // the admitted queries occupy slots 0..K-1
     rc = solve_fp64(ctx, S->d_mu, nullptr, K, S->d_n, S->d_u, S->d_p, S->d_info, st);
@@ -371,6 +374,7 @@ int rb_serve_start(rb_ctx *ctx) {
   }
   S->slot_ticket.assign(cap, 0);
   S->slot_iters.assign(cap, 0);
+  S->slot_n.assign(cap, 0);
   S->slot_t0.assign(cap, Clock::now());
   S->free_slots.clear();
   for (int s = 0; s < cap; ++s) S->free_slots.insert(s);

@@ -152,3 +152,32 @@ def test_fp64_server_and_sizes(rb, sweep):
     U = np.stack([r[0] for r in res])
     assert all(r[2]["status"] == 0 for r in res)
     assert rel(U, u_or).max() <= 1e-10
+
+
+def test_mixed_server_sizes_in_buckets(rb):
+    """Mixed-precision serving of queries of different sizes: every step runs each size bucket's
+    slots as one batch (gathered, iterated, scattered back); velocity and pressure match the
+    oracle per size, and a query gives the same result alone and among the others."""
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(wl, n_max=72)
+    q = synth.make_queries(wl, batch=240, n_max=72)
+    sizes = [72, 9, 33, 50, 64, 17, 1, 70]
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        ctx.rb_serve_start()
+        alone = wait(ctx, ctx.rb_serve_submit(q.mu[5], n=sizes[5]))
+        tickets = [ctx.rb_serve_submit(q.mu[k], n=sizes[k % len(sizes)]) for k in range(len(q.mu))]
+        res = [wait(ctx, t) for t in tickets]
+        ctx.rb_serve_stop(True)
+    n = np.array([sizes[k % len(sizes)] for k in range(len(q.mu))], dtype=np.int32)
+    o = oracle.Oracle.from_set(ops)
+    u_or, p_or, _ = o.solve(q.mu, n=n, threads=8)
+    U = np.stack([r[0] for r in res])
+    P = np.stack([r[1] for r in res])
+    assert all(r[2]["status"] == 0 for r in res)
+    for s in sizes:
+        k = n == s
+        assert rel(U[k][:, :s], u_or[k][:, :s]).max() <= TOL_MIXED, s
+        assert np.all(U[k][:, s:] == 0)
+    assert rel(P, p_or).max() <= 10 * TOL_MIXED
+    assert rel(res[5][0], alone[0]) <= TOL_MIXED and rel(res[5][1], alone[1]) <= 10 * TOL_MIXED
