@@ -356,14 +356,20 @@ FP64_PEAK_TFLOPS = 1.196  # FP64 FMA throughput measured on GB300 (152 SMs at 20
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DIGITS = int(os.environ.get("RB_DIGITS", "6"))  # digit slices of the sliced convection product
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels as they
-# stand, from one ncu capture each of a 4096-query n = 50 solve (profiles/kernels_sweep_n50.md);
-# a kernel changed since its capture has no entry.
+# stand, from ncu captures of a 4096-query n = 50 solve (profiles/kernels_sweep_n50.md) and of
+# the n = 300 dense regime; a kernel changed since its capture has no entry.
 NCU_TRAFFIC = {
     "sweep_n50": {
         "k_tc_gemm<sliced>": 29.06e6,
         "k_tc_gemm<plain>": 11.59e6,
         "k_newton_system": 150.45e6,
         "k_lu_mixed": 44.71e6,
+    },
+    # one-pass capture of the full-size workload (profiles/launches_dense_n300.md)
+    "dense_n300": {
+        "k_tc_gemm<sliced>": 1599.45e9,
+        "k_tc_gemm<plain>": 126.8e9,
+        "k_lu_mixed": 25.83e9,
     },
 }
 
