@@ -36,7 +36,7 @@ __device__ void contract_fp64(const DevOps &o, int n, const double *xs, double *
     for (int q = 0; q < o.q_c; ++q) {
       const double *Dq = o.Dt + (size_t)q * nm * nm2;
       const double *xq = xs + q * n;
-#pragma unroll 2
+#pragma unroll 8  // loads of 8 rows in flight: the stream is L2-latency bound at small n
       for (int l = 0; l < n; ++l) {
         const double x = xq[l];
         const double *row = Dq + (size_t)l * nm2;
@@ -53,16 +53,30 @@ __device__ void contract_fp64(const DevOps &o, int n, const double *xs, double *
   }
 }
 
-// J <- A(mu) + J^c and R = (A(mu) + J^c / 2) u - f(mu); one warp per row k.
+// A(mu)[k][j] = sum_q theta^a_q A_q[k][j] (row stride n).
+__device__ void assemble_a(const DevOps &o, int n, const double *th, double *Am) {
+  const size_t nm = (size_t)o.n_max;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int k = e / n, j = e - k * n;
+    double a = 0.0;
+    for (int q = 0; q < o.q_a; ++q) a = fma(th[q], __ldg(o.A + ((size_t)q * nm + k) * nm + j), a);
+    Am[e] = a;
+  }
+}
+
+// J <- A(mu) + J^c and R = (A(mu) + J^c / 2) u - f(mu); one warp per row k. Am: A(mu) built
+// once per query (shared memory), or null: summed here from the A_q.
 __device__ void row_pass_fp64(const DevOps &o, int n, const double *th, const double *u,
-                              const double *fm, double *J, double *R) {
+                              const double *fm, double *J, double *R, const double *Am) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const size_t nm = (size_t)o.n_max;
   for (int k = w; k < n; k += kWarps) {
     double r = 0.0;
     for (int j = lane; j < n; j += 32) {
       double a = 0.0;
-      for (int q = 0; q < o.q_a; ++q) a = fma(th[q], __ldg(o.A + ((size_t)q * nm + k) * nm + j), a);
+      if (Am) a = Am[k * n + j];
+      else
+        for (int q = 0; q < o.q_a; ++q) a = fma(th[q], __ldg(o.A + ((size_t)q * nm + k) * nm + j), a);
       const double jc = J[(size_t)k * n + j];
       r = fma(a + 0.5 * jc, u[j], r);
       J[(size_t)k * n + j] = a + jc;
@@ -91,9 +105,11 @@ __device__ void load_theta(const DevOps &o, const double *mu, const double *thet
   }
 }
 
-// shared-memory carve-up of the per-query FP64 kernels (in doubles)
+// shared-memory carve-up of the per-query FP64 kernels (in doubles); A(mu) is kept in shared
+// memory for small sets (n_max <= kFp64SmallN), where the per-iteration latency dominates
+constexpr int kFp64SmallN = 32;
 struct Fp64Smem {
-  int th, u, R, fm, xs, red, J, total;
+  int th, u, R, fm, xs, red, piv, J, Am, total;
   __host__ __device__ Fp64Smem(const DevOps &o, bool j_in_smem) {
     int p = 0;
     th = p; p += (o.n_theta + 1) & ~1;
@@ -102,9 +118,12 @@ struct Fp64Smem {
     fm = p; p += o.n_max;
     xs = p; p += o.q_c * o.n_max;
     red = p; p += 4 * kWarps;
+    piv = p; p += (o.n_max + 1) / 2;  // ints
     p = (p + 1) & ~1;
     J = p;
     if (j_in_smem) p += o.n_max * o.n_max;
+    Am = p;
+    if (j_in_smem && o.n_max <= kFp64SmallN) p += o.n_max * o.n_max;
     total = p;
   }
 };
@@ -119,7 +138,9 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
   const Fp64Smem L(o, p.j_in_smem != 0);
   double *th = sm + L.th, *u = sm + L.u, *R = sm + L.R, *fm = sm + L.fm, *xs = sm + L.xs;
   double *red = sm + L.red;
+  int *piv = reinterpret_cast<int *>(sm + L.piv);
   double *J = p.j_in_smem ? sm + L.J : p.jscratch + (size_t)blockIdx.x * o.n_max * o.n_max;
+  double *Am = (p.j_in_smem && o.n_max <= kFp64SmallN) ? sm + L.Am : nullptr;
   const int tid = threadIdx.x;
 
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
@@ -137,6 +158,7 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
     for (int i = tid; i < n; i += blockDim.x) u[i] = 0.0;
     __syncthreads();
     assemble_f(o, n, th, fm);
+    if (Am) assemble_a(o, n, th, Am);
     __syncthreads();
     double fl = 0.0;
     for (int i = tid; i < n; i += blockDim.x) fl += fm[i] * fm[i];
@@ -150,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
       __syncthreads();
       contract_fp64(o, n, xs, J);
       __syncthreads();
-      row_pass_fp64(o, n, th, u, fm, J, R);
+      row_pass_fp64(o, n, th, u, fm, J, R, Am);
       __syncthreads();
       double rl = 0.0;
       for (int i = tid; i < n; i += blockDim.x) rl += R[i] * R[i];
@@ -159,7 +181,19 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
       if (!isfinite(rn)) { status = RB_Q_NONFINITE; break; }
       for (int i = tid; i < n; i += blockDim.x) R[i] = -R[i];
       __syncthreads();
-      if (gepp_solve_block<double>(J, n, n, R, red)) { status = RB_Q_SINGULAR; break; }
+      bool sing;
+      if (n <= 32) {  // one warp eliminates, without CTA barriers per pivot
+        if (threadIdx.x < 32 && gepp_solve_warp32<double>(J, n, n, R, piv) && threadIdx.x == 0)
+          red[0] = 1.0;
+        else if (threadIdx.x == 0)
+          red[0] = 0.0;
+        __syncthreads();
+        sing = red[0] != 0.0;
+        __syncthreads();
+      } else {
+        sing = gepp_solve_block<double>(J, n, n, R, red);
+      }
+      if (sing) { status = RB_Q_SINGULAR; break; }
       double dl = 0.0;
       for (int i = tid; i < n; i += blockDim.x) {
         dl += R[i] * R[i];
@@ -287,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_fp64(EvalParams p) {
     __syncthreads();
     contract_fp64(o, n, xs, J);
     __syncthreads();
-    row_pass_fp64(o, n, th, u, fm, J, R);
+    row_pass_fp64(o, n, th, u, fm, J, R, nullptr);
     __syncthreads();
     for (int i = tid; i < n; i += blockDim.x) p.R_out[(size_t)b * n + i] = R[i];
     __syncthreads();

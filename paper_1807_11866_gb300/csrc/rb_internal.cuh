@@ -262,6 +262,55 @@ __device__ bool gepp_solve_block(T *M, int ld, int n, T *b, double *red) {
   return false;
 }
 
+// Solve M x = b in place for n <= 32 by the calling warp alone (no CTA barriers): Gaussian
+// elimination with partial pivoting (pivot = first row of largest magnitude), rows left in place
+// and owned by lane r; the elimination order goes to pseq (n ints of shared scratch), then back
+// substitution in that order; b (shared) receives x. Every operation in precision T. Returns
+// true (all lanes) if a pivot was zero or not finite.
+template <typename T>
+__device__ bool gepp_solve_warp32(T *M, int ld, int n, T *b, int *pseq) {
+  const int lane = threadIdx.x & 31;
+  T *row = M + (size_t)lane * ld;
+  int step = lane < n ? n : -1;  // step at which the row was the pivot
+  for (int p = 0; p < n; ++p) {
+    T best = step == n ? fabs(row[p]) : T(-1);
+    int brow = step == n ? lane : n;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int r2 = __shfl_xor_sync(0xffffffffu, brow, o);
+      argmax_merge<T>(best, brow, v2, r2);
+    }
+    if (!(best > T(0)) || !isfinite(best)) return true;  // uniform after the butterfly
+    const T *prow = M + (size_t)brow * ld;
+    const T pv = prow[p];
+    if (lane == brow) step = p;
+    if (lane == 0) pseq[p] = brow;
+    if (step == n) {
+      const T l = row[p] / pv;
+      for (int j = p + 1; j < n; ++j) row[j] -= l * prow[j];
+      b[lane] -= l * b[brow];
+    }
+    __syncwarp();
+  }
+  // back substitution in step order: unknown p from row pseq[p]
+  for (int p = n - 1; p >= 0; --p) {
+    const int r = pseq[p];
+    const T xp = b[r] / M[(size_t)r * ld + p];
+    __syncwarp();
+    if (step >= 0 && step < p) b[lane] -= M[(size_t)lane * ld + p] * xp;
+    if (lane == r) b[lane] = xp;
+    __syncwarp();
+  }
+  // b[pseq[p]] holds x_p: gather into column order
+  T xv = T(0);
+  if (lane < n) xv = b[pseq[lane]];
+  __syncwarp();
+  if (lane < n) b[lane] = xv;
+  __syncwarp();
+  return false;
+}
+
 // ---- warp-level elimination for small systems (one warp per system, FP32) ----------------
 // Lane r % 32 owns row r of the register-held vectors below: up to kWarpRows slots per lane.
 constexpr int kWarpRows = 3;  // n <= 96
