@@ -224,7 +224,7 @@ def main():
     sl = slice(rank * batch, (rank + 1) * batch)
     q = synth.QuerySet(qall.mu[sl].copy(), qall.n[sl].copy())
     prec = PREC[args.precision]
-    ctx = rb.Context(precision=prec, device=local)
+    ctx = rb.Context(precision=prec, device=local, theta_family=wl.theta_family)
     ctx.load_set(ops)
     m = ctx.m
     stream = torch.cuda.Stream(device=dev)
@@ -442,7 +442,7 @@ def run_serve(args, wl, rank, world, local):
         dist.barrier()
     ops = synth.make_operators(wl)
     q = synth.make_queries(wl, batch=wl.batch)
-    ctx = rb.Context(precision=PREC[args.precision], device=local)
+    ctx = rb.Context(precision=PREC[args.precision], device=local, theta_family=wl.theta_family)
     ctx.load_set(ops)
     B = len(q.mu)
 
@@ -534,7 +534,7 @@ def plain_fp64(rb, ops, q, batch, dev, flush, args):
     if 2.0 * wl.q_c * wl.n_max ** 3 > 1e9:
         batch = min(batch, 304)
         q = synth.QuerySet(q.mu[:batch].copy(), q.n[:batch].copy())
-    ctx = rb.Context(precision=rb.RB_PREC_FP64, device=dev.index)
+    ctx = rb.Context(precision=rb.RB_PREC_FP64, device=dev.index, theta_family=wl.theta_family)
     ctx.load_set(ops)
     stream = torch.cuda.Stream(device=dev)
     d_mu = torch.from_numpy(q.mu).to(dev)

@@ -24,7 +24,10 @@
  *
  * Parameter functions (RB_THETA_TRIG): a = alpha * pi / 180, trig_q(a) = cos(q a) for even q
  * and sin(q a) for odd q (trig_0 = 1); theta^a_q = trig_q / Re and
- * theta^c_q = theta^f_q = theta^b_q = trig_q. With RB_THETA_USER the caller passes theta.
+ * theta^c_q = theta^f_q = theta^b_q = trig_q. Polynomial functions (RB_THETA_POLY, the
+ * monomials of the truncated rotation series of Sec. 5, Eq. rotsum, in which every pulled-back
+ * form is affine): phi = alpha * pi / 180, theta^a_q = phi^q / Re and
+ * theta^c_q = theta^f_q = theta^b_q = phi^q. With rb_solve_theta the caller passes theta.
  * theta rows are laid out [theta^a (q_a) | theta^c (q_c) | theta^f (q_f) | theta^b (q_b)].
  *
  * Error behaviour: every function returns an rb_status. A failing call leaves a message for
@@ -76,7 +79,7 @@ enum {
 };
 
 /* parameter-function family */
-enum { RB_THETA_TRIG = 0, RB_THETA_USER = 1 };
+enum { RB_THETA_TRIG = 0, RB_THETA_USER = 1, RB_THETA_POLY = 2 };
 
 typedef struct rb_ctx rb_ctx; /* opaque; owns all device memory it allocates */
 
@@ -110,7 +113,9 @@ typedef struct {
   int use_graph;      /* capture per-iteration launches in CUDA graphs (default 1) */
   int autotune;       /* time kernel variants on first use per shape (default 1; the
                          environment variable RB_AUTOTUNE=0 makes the default 0) */
-  int theta_family;   /* RB_THETA_TRIG (default) or RB_THETA_USER */
+  int theta_family;   /* RB_THETA_TRIG (default) or RB_THETA_POLY: the functions that mu is
+                         mapped through by rb_solve, rb_solve_device and the server
+                         (RB_THETA_USER: as RB_THETA_TRIG; theta comes with rb_solve_theta) */
   int serve_slots;    /* serving: queries on the device at once (0: as many as the memory
                          budget admits, at most 4096) */
 } rb_config;

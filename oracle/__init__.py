@@ -31,7 +31,7 @@ class _Ops(ctypes.Structure):
                 ("c_is_f32", ctypes.c_int),
                 ("A", ctypes.c_void_p), ("C", ctypes.c_void_p), ("f", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("As", ctypes.c_void_p), ("Cs", ctypes.c_void_p),
-                ("fs", ctypes.c_void_p)]
+                ("fs", ctypes.c_void_p), ("theta_family", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -85,7 +85,7 @@ def _ptr(a):
 class Oracle:
     """Holds one operator set (host arrays, kept alive) for the C oracle."""
 
-    def __init__(self, A, C, f, B=None, As=None, Cs=None, fs=None):
+    def __init__(self, A, C, f, B=None, As=None, Cs=None, fs=None, theta_family=0):
         self.A = np.ascontiguousarray(A, dtype=np.float64)
         c_is_f32 = np.asarray(C).dtype == np.float32
         cdt = np.float32 if c_is_f32 else np.float64
@@ -107,12 +107,14 @@ class Oracle:
             self.q_b = self.m = 0
         self._ops = _Ops(self.n_max, self.m, self.q_a, self.q_c, self.q_f, self.q_b,
                          int(c_is_f32), _ptr(self.A), _ptr(self.C), _ptr(self.f),
-                         _ptr(self.B), _ptr(self.As), _ptr(self.Cs), _ptr(self.fs))
+                         _ptr(self.B), _ptr(self.As), _ptr(self.Cs), _ptr(self.fs),
+                         int(theta_family))
         self.n_theta = self.q_a + self.q_c + self.q_f + self.q_b
 
     @classmethod
     def from_set(cls, ops):
-        return cls(ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs)
+        return cls(ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs,
+                   theta_family=getattr(ops.wl, "theta_family", 0))
 
     @property
     def ref(self):

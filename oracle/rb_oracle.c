@@ -55,6 +55,7 @@ typedef struct {
   const double *As;      /* [q_a][m][n_max] or NULL */
   const void *Cs;        /* [q_c][n_max][n_max][m] or NULL, index [j][l][k'] */
   const double *fs;      /* [q_f][m] or NULL */
+  int theta_family;      /* 0: trigonometric family, 2: polynomial family (below) */
 } oracle_ops;
 
 typedef struct {
@@ -79,11 +80,28 @@ static double trig(int q, double a) {
   return (q % 2 == 0) ? cos((double)q * a) : sin((double)q * a);
 }
 
+/* Polynomial family: the truncated rotation series R(a) = sum_i phi^i R_i (Sec. 5, Eq. rotsum)
+   makes every pulled-back form affine in the monomials phi^i of the rotation angle
+   phi = alpha * pi / 180 (the forms a, b, c of Sec. 5.2 expand in phi^(i+j), phi^(i+j+1),
+   phi^(i+j+2)); the viscous form carries 1/Re (u_inf = 1). Term q is phi^q. */
+static double mono(int q, double phi) {
+  double v = 1.0;
+  for (int i = 0; i < q; ++i) v *= phi;
+  return v;
+}
+
 /* theta laid out as [theta^a (q_a) | theta^c (q_c) | theta^f (q_f) | theta^b (q_b)]. */
 void oracle_theta(const oracle_ops *o, double alpha_deg, double re, double *theta) {
   const double pi = 3.14159265358979323846;
   double a = alpha_deg * pi / 180.0;
   int p = 0;
+  if (o->theta_family == 2) {
+    for (int q = 0; q < o->q_a; ++q) theta[p++] = mono(q, a) / re;
+    for (int q = 0; q < o->q_c; ++q) theta[p++] = mono(q, a);
+    for (int q = 0; q < o->q_f; ++q) theta[p++] = mono(q, a);
+    for (int q = 0; q < o->q_b; ++q) theta[p++] = mono(q, a);
+    return;
+  }
   for (int q = 0; q < o->q_a; ++q) theta[p++] = trig(q, a) / re;
   for (int q = 0; q < o->q_c; ++q) theta[p++] = trig(q, a);
   for (int q = 0; q < o->q_f; ++q) theta[p++] = trig(q, a);

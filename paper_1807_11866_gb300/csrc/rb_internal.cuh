@@ -14,6 +14,7 @@ constexpr int kWarps = kThreads / 32;
 // Device-resident operator layouts (all owned by the context, built at load time).
 struct DevOps {
   int n_max, m, q_a, q_c, q_f, q_b, n_theta;
+  int theta_family;   // RB_THETA_POLY: monomials phi^q, otherwise the trigonometric family
   const double *A;    // [q_a][n_max][n_max]          row = test k
   const double *Dt;   // [q_c][n_max(l)][n_max(k)][n_max(j)]  D~_q[k][j][l] =
                       //   C_q[l][j][k] + C_q[j][l][k]  (both orders of Sec. 3.6 pre-summed)
@@ -46,7 +47,15 @@ __device__ __forceinline__ void theta_eval_strided(const DevOps &o, double alpha
         if (q >= o.q_f) q -= o.q_f;
       }
     }
-    th[i] = trig_q(q, a) * scale;
+    if (o.theta_family == RB_THETA_POLY) {
+      // monomial phi^q of the truncated rotation series (Sec. 5, Eq. rotsum), by repeated
+      // multiplication
+      double v = 1.0;
+      for (int k = 0; k < q; ++k) v *= a;
+      th[i] = v * scale;
+    } else {
+      th[i] = trig_q(q, a) * scale;
+    }
   }
 }
 

@@ -293,7 +293,8 @@ int rb_create(rb_ctx **out, const rb_config *cfg, int device) {
   rb_ctx *ctx = new rb_ctx();
   if (cfg) ctx->cfg = *cfg; else rb_config_default(&ctx->cfg);
   if (ctx->cfg.max_iter < 1 || ctx->cfg.precision < RB_PREC_FP64 || ctx->cfg.precision > RB_PREC_MIXED ||
-      ctx->cfg.serve_slots < 0 ||
+      ctx->cfg.serve_slots < 0 || ctx->cfg.theta_family < RB_THETA_TRIG ||
+      ctx->cfg.theta_family > RB_THETA_POLY ||
       !(ctx->cfg.tol_update >= 0) || !(ctx->cfg.tol_res >= 0)) {
     delete ctx;
     return RB_ERR_ARG;
@@ -370,6 +371,7 @@ int rb_load_operators(rb_ctx *ctx, const rb_operators *ops) {
   o.q_f = ops->q_f;
   o.q_b = pres ? ops->q_b : 0;
   o.n_theta = o.q_a + o.q_c + o.q_f + o.q_b;
+  o.theta_family = ctx->cfg.theta_family;
   const size_t nn = (size_t)n, ncube = nn * nn * nn;
   const int f32 = ops->dtype_c == RB_F32;
   const size_t csz = f32 ? sizeof(float) : sizeof(double);

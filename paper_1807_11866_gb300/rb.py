@@ -19,7 +19,7 @@ RB_ERR_ARG, RB_ERR_OOM, RB_ERR_CUDA, RB_ERR_STATE, RB_ERR_TIMEOUT = -1, -2, -3, 
 RB_Q_OK, RB_Q_NOT_CONVERGED, RB_Q_SINGULAR, RB_Q_NONFINITE, RB_Q_REJECTED = 0, 1, 2, 3, 4
 RB_F64, RB_F32 = 0, 1
 RB_PREC_FP64, RB_PREC_MIXED = 0, 1
-RB_THETA_TRIG, RB_THETA_USER = 0, 1
+RB_THETA_TRIG, RB_THETA_USER, RB_THETA_POLY = 0, 1, 2
 RB_N_MAX, RB_M_MAX, RB_Q_MAX = 320, 128, 64
 RB_STATIC_N_MAX, RB_STATIC_SCRATCH_BYTES = 512, 16 << 20
 
@@ -138,7 +138,8 @@ class Context:
     """An rb_ctx on one device. Methods mirror the C entry points one to one."""
 
     def __init__(self, precision=RB_PREC_FP64, tol_update=None, tol_res=None, max_iter=None,
-                 mem_budget=None, use_graph=None, device=0, serve_slots=None, autotune=None):
+                 mem_budget=None, use_graph=None, device=0, serve_slots=None, autotune=None,
+                 theta_family=None):
         L = library()
         cfg = rb_config_default()
         cfg.precision = precision
@@ -156,6 +157,8 @@ class Context:
             cfg.serve_slots = serve_slots
         if autotune is not None:
             cfg.autotune = autotune
+        if theta_family is not None:
+            cfg.theta_family = theta_family
         self.cfg = cfg
         h = ctypes.c_void_p()
         rc = L.rb_create(ctypes.byref(h), ctypes.byref(cfg), device)
@@ -208,7 +211,12 @@ class Context:
         self.q = (ops.q_a, ops.q_c, ops.q_f, ops.q_b)
 
     def load_set(self, ops):
-        """Load a synth.OperatorSet (or any object with the same fields)."""
+        """Load a synth.OperatorSet (or any object with the same fields). A set that names its
+        parameter-function family (wl.theta_family) must match the context's."""
+        fam = getattr(getattr(ops, "wl", None), "theta_family", None)
+        mine = RB_THETA_TRIG if self.cfg.theta_family == RB_THETA_USER else self.cfg.theta_family
+        if fam is not None and fam != mine:
+            raise ValueError(f"operator set uses theta family {fam}, the context {mine}")
         self.rb_load_operators(ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs)
 
     # --- solves -------------------------------------------------------------------------

@@ -16,15 +16,19 @@ structure the paper relies on:
   B_q (supremizer test x pressure trial; B_0 nonsymmetric, singular values in [1, 10],
   B_q>=1 small), As_q, Cs_q[j][l][k'] and fs_q;
 * queries mu = (alpha in degrees, Re): alpha ~ U[0, 35], log10 Re ~ U[2, 3];
-* reduced sizes per query (nested truncations of one n_max operator set).
+* reduced sizes per query (nested truncations of one n_max operator set);
+* for the polynomial parameter family (theta_family = 2: monomials phi^q of the rotation
+  angle, Sec. 5, Eq. rotsum) the q-th term of every operator is further scaled by 1/q!,
+  the factor of the q-th term of the truncated rotation series R = sum_i phi^i P^i / i!.
 
 Where a workload stores C in BF16 or FP32, the tensor is rounded here (round to nearest even)
 and the rounded values *are* the operator: every solver, exact or not, sees the same numbers.
 
 A global power-of-two scale s_A multiplies every A_q so that the problem sits in
 the small-data regime where the steady solution is unique and Newton from u = 0 converges.
-The bound used needs no parameter-function evaluation: |trig_q| <= 1 and
-theta^a_q = trig_q / Re with Re <= Re_max give
+The bound used needs no parameter-function evaluation: |trig_q| <= 1 (and |phi^q| <= 1 for
+|phi| <= 1 rad, which the polynomial workloads' angle range keeps) and
+theta^a_q = theta_q / Re with Re <= Re_max give
 lambda_min(A(mu)) >= s_A * lambda_min(A_0) / (2 Re_max).
 
 This module holds random draws and data conditioning only. It evaluates no parameter
@@ -65,6 +69,7 @@ class Workload:
     re_range: tuple = (100.0, 1000.0)
     mu0: Optional[tuple] = None     # single fixed query (manufactured workloads)
     manufactured: bool = False
+    theta_family: int = 0           # 0: trigonometric functions, 2: monomials of the angle
 
 
 WORKLOADS = {
@@ -83,6 +88,10 @@ WORKLOADS = {
     # large dense regime: n = 300, Q = 24, B = 16384, C BF16-exact
     "dense_n300": Workload("dense_n300", 4, n_max=300, q_a=24, q_c=24, q_f=3, batch=16384,
                            c_dtype="bf16"),
+    # rotation of the airfoil by a truncated series of 12 terms (Sec. 5): polynomial parameter
+    # functions with 4 * 12 + 2 viscous, 4 * 12 + 1 convective and 4 * 12 + 2 forcing terms
+    "rotation_n50": Workload("rotation_n50", 5, n_max=50, q_a=50, q_c=49, q_f=50, q_b=48,
+                             m=30, batch=4096, theta_family=2),
 }
 
 
@@ -179,6 +188,8 @@ def make_operators(wl: Workload, n_max: Optional[int] = None, c_dtype: Optional[
         q_f=q_f if q_f is not None else wl.q_f,
     )
     n, g = wl.n_max, rng(wl.wid, STREAM_OPS)
+    if wl.theta_family == 2 and max(abs(a) for a in wl.alpha_range) > 180.0 / math.pi:
+        raise ValueError("polynomial workloads keep |alpha| <= 1 rad")
 
     # A_0: lambda geometric in [1e-5, 10] plus 1e-2 I -> condition ~ 1e3
     lam0 = np.geomspace(1e-5, 10.0, n) if n > 1 else np.array([10.0])
@@ -210,6 +221,25 @@ def make_operators(wl: Workload, n_max: Optional[int] = None, c_dtype: Optional[
         for q in range(wl.q_c):
             Cs[q] = store(g.standard_normal((n, n, m)) * 0.1, wl.c_dtype)
         fs = g.standard_normal((wl.q_f, m))
+
+    if wl.theta_family == 2:
+        # term q of the truncated series carries 1/q!
+        def _fact(k, x):
+            for q in range(1, k):
+                x[q] *= 1.0 / math.factorial(q)
+        _fact(wl.q_a, A)
+        _fact(wl.q_c, C)
+        _fact(wl.q_f, f)
+        if B is not None:
+            _fact(wl.q_b, B)
+            _fact(wl.q_a, As)
+            _fact(wl.q_c, Cs)
+            _fact(wl.q_f, fs)
+        if wl.c_dtype != "f64":
+            for q in range(wl.q_c):
+                C[q] = store(C[q], wl.c_dtype)
+                if Cs is not None:
+                    Cs[q] = store(Cs[q], wl.c_dtype)
 
     # global power-of-two scale of the viscous terms (small-data regime)
     gamma = sum(_frob_c(C[q]) for q in range(wl.q_c))

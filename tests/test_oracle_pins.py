@@ -39,6 +39,55 @@ def test_theta_closed_forms(oracle_lib):
     np.testing.assert_allclose(t[8:12], [1.0, 1.0, -1.0, -1.0], atol=1e-15)
 
 
+def _rotation_series_set(q, m=2):
+    """Operators whose q-th terms are J^q / q! with J the 2 x 2 rotation generator, so that
+    sum_q phi^q J^q / q! is the rotation matrix R(phi) (Sec. 5, Eq. rotsum)."""
+    J = np.array([[0.0, -1.0], [1.0, 0.0]])
+    P = [np.linalg.matrix_power(J, k) / math.factorial(k) for k in range(q)]
+    A = np.stack(P)
+    f = np.stack([Pk @ np.array([1.0, 0.0]) for Pk in P])
+    C = np.zeros((1, 2, 2, 2))
+    B = np.stack(P)
+    As = np.zeros((q, m, 2))
+    Cs = np.zeros((1, 2, 2, m))
+    return A, C, f, B, As, Cs, f.copy()
+
+
+@pytest.mark.parametrize("alpha", [0.0, 7.5, 35.0, -20.0])
+def test_poly_theta_is_rotation_series(oracle_lib, alpha):
+    # Polynomial family: theta_q = phi^q (theta^a_q = phi^q / Re). With operators J^q / q! the
+    # assembled A(mu) and f(mu) are the rotation R(phi) / Re and R(phi) e_0, the closed form of
+    # the exponential series; 30 terms leave a truncation error below 1e-30.
+    A, C, f, B, As, Cs, fs = _rotation_series_set(30)
+    o = oracle_lib.Oracle(A, C, f, B, As, Cs, fs, theta_family=2)
+    re = 300.0
+    phi = math.radians(alpha)
+    t = o.theta(alpha, re)
+    Am, fm = o.assemble(2, t)
+    R = np.array([[math.cos(phi), -math.sin(phi)], [math.sin(phi), math.cos(phi)]])
+    np.testing.assert_allclose(Am, R / re, rtol=0, atol=1e-17)
+    np.testing.assert_allclose(fm, R[:, 0], rtol=0, atol=1e-15)
+    # pressure with u = 0: B(mu) p = fs(mu) is R(phi) p = R(phi) e_0, so p = e_0
+    p, rc = o.pressure(2, t, np.zeros(2))
+    assert rc == 0
+    np.testing.assert_allclose(p, [1.0, 0.0], rtol=0, atol=1e-14)
+
+
+def test_poly_theta_monomials(oracle_lib):
+    ops = small_set(n=3, q_a=4, q_c=4, q_f=4)
+    o = oracle_lib.Oracle(ops.A, ops.C, ops.f, theta_family=2)
+    # alpha = 0: only the constant monomial survives
+    t = o.theta(0.0, 250.0)
+    np.testing.assert_array_equal(t[:4], [1 / 250.0, 0.0, 0.0, 0.0])
+    np.testing.assert_array_equal(t[4:12], [1.0, 0.0, 0.0, 0.0] * 2)
+    # alpha = 180 / pi degrees: phi = 1, every monomial is 1
+    t = o.theta(180.0 / math.pi, 1.0)
+    np.testing.assert_allclose(t, np.ones(12), rtol=1e-15)
+    # alpha = -90 deg: phi = -pi/2, signs alternate
+    t = o.theta(-90.0, 1.0)
+    np.testing.assert_allclose(t[4:8], [(-math.pi / 2) ** k for k in range(4)], rtol=1e-15)
+
+
 def _golden_set():
     with open(os.path.join(GOLDEN, "n2_closed_form.json")) as fh:
         g = json.load(fh)
@@ -275,3 +324,23 @@ def test_sweep_workload_converges(oracle_lib):
     assert np.all(info["status"] == 0), info
     assert np.all(info["iters"] <= 15)
     assert np.all(np.isfinite(p))
+
+
+def test_rotation_workload_converges(oracle_lib):
+    """The polynomial-family workload (Sec. 5 rotation series) converges from u = 0, and its
+    theta row equals the one the trigonometric row of the same angle would give for phi = 0."""
+    wl = synth.WORKLOADS["rotation_n50"]
+    ops = synth.make_operators(wl)
+    q = synth.make_queries(wl, batch=12)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    o = oracle_lib.Oracle.from_set(ops)
+    u, p, info = o.solve(mu, threads=4)
+    assert np.all(info["status"] == 0), info
+    assert np.all(info["iters"] <= 15)
+    assert np.all(np.isfinite(p))
+    # at alpha = 0 both families reduce to (1/Re, 0, ..., | 1, 0, ... | ...)
+    t_poly = o.theta(0.0, 500.0)
+    t_trig = oracle_lib.Oracle(ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs).theta(0.0, 500.0)
+    nz = np.nonzero(t_poly)[0]
+    np.testing.assert_array_equal(nz, [0, wl.q_a, wl.q_a + wl.q_c, wl.q_a + wl.q_c + wl.q_f])
+    np.testing.assert_array_equal(t_poly[nz], t_trig[nz])

@@ -1,4 +1,7 @@
 """Checks of the seeded synthetic inputs (structure only; no method arithmetic)."""
+import dataclasses
+import math
+
 import numpy as np
 import pytest
 
@@ -55,3 +58,15 @@ def test_pressure_operator_nonsingular():
     ops = synth.make_operators(synth.WORKLOADS["sweep_n50"], n_max=8)
     sv = np.linalg.svd(ops.B[0], compute_uv=False)
     assert sv.min() > 0.9 and sv.max() < 11
+
+
+def test_rotation_workload_factorial_terms():
+    # term q of every operator of the polynomial workload carries 1/q! on top of the draw
+    wl = synth.WORKLOADS["rotation_n50"]
+    assert wl.theta_family == 2 and (wl.q_a, wl.q_c, wl.q_f) == (50, 49, 50)
+    ops = synth.make_operators(wl, n_max=6)
+    for q in (1, 5, 12):
+        assert np.max(np.abs(ops.f[q])) < 10.0 / math.factorial(q)
+        assert np.max(np.abs(ops.C[q])) < 1.0 / math.factorial(q)
+    with pytest.raises(ValueError):
+        synth.make_operators(dataclasses.replace(wl, alpha_range=(0.0, 90.0)), n_max=4)
