@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-recon", action="store_true",
+                    help="skip the pressure-reconstruction comparison (combined basis)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: saturation throughput of the continuous-batching server "
                          "and p50/p99 submit-to-completion latency under Poisson arrivals")
@@ -307,7 +309,8 @@ def main():
     d2h = batch * wl.n_max * 8 + (batch * m * 8 if m else 0) + batch * 32
 
     # roofline of the dominant kernel, measured live with events on the launching stream
-    roof, roofs, kernels = kernel_rooflines(prec, wl, q, info, kprof, args.steps)
+    chord = chord_queries(prec, wl, q, ctx.rb_tuning())
+    roof, roofs, kernels = kernel_rooflines(prec, wl, q, info, kprof, args.steps, chord)
 
     line = {
         "metric": "reduced Newton solves/s", "value": value, "unit": "solves/s",
@@ -332,6 +335,9 @@ def main():
     line["roofline"] = roof
     line["rooflines"] = roofs
     line["autotune"] = ctx.rb_tuning()
+    if rank == 0 and m and not args.no_recon:
+        line["pressure_reconstruction"] = pressure_reconstruction(
+            rb, ctx, wl, batch, d_u, d_n, p_gpu, kprof, stream, flush, args)
     if rank == 0 and not args.no_plain and prec != 0:
         line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, args)
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
@@ -374,20 +380,48 @@ NCU_TRAFFIC = {
 }
 
 
-def kernel_rooflines(prec, wl, q, info, kprof, steps):
+def chord_queries(prec, wl, q, tuning):
+    """Queries whose Newton iterations from the fourth on were chord steps: mixed path, size
+    buckets on the warp-per-query elimination with at most 80 rows (the library's rule)."""
+    if prec == 0 or os.environ.get("RB_CHORD", "") == "0":
+        return np.zeros(len(q.n), bool)
+
+    def bucket(n):
+        g = 8 if n <= 64 else (16 if n <= 128 else 32)
+        return min((n + g - 1) // g * g, wl.n_max)
+
+    tuned = {t["n_bucket"]: t["elimination"] == "warp per query" for t in tuning}
+    forced = os.environ.get("RB_ELIMINATION", "")
+    out = np.zeros(len(q.n), bool)
+    for i, n in enumerate(q.n):
+        nb = bucket(int(n))
+        warp = tuned.get(nb, (forced == "1") if forced else nb <= 80)
+        out[i] = warp and nb <= 80
+    return out
+
+
+def kernel_rooflines(prec, wl, q, info, kprof, steps, chord):
     """Roofline of every timed kernel kind, and of the one with the largest device time.
-    Algorithmic work counts only the useful part, per active query-iteration of size n:
+    Algorithmic work counts only the useful part, per active query-iteration of size n
+    (`chord` queries factor at their first three iterations and reuse the third factorisation
+    from the fourth on, without a Jacobian contraction):
       fused FP64 Newton: 2 (Q_c n^3 + Q_a n^2) + 2 n^3 / 3 + 2 n^2 FLOP (FP64 ALU);
-      Jacobian GEMM: 3 x 2 Q_c n^3 FLOP of split-BF16 products (tensor);
-      sliced residual GEMM: P 2 Q_c n^3 FLOP of BF16 digit products, P = S (S + 1) / 2 (tensor);
+      Jacobian GEMM: 3 x 2 Q_c n^3 FLOP of split-BF16 products, iterations with a new Jacobian
+        after the first (tensor);
+      sliced residual GEMM: P 2 Q_c n^3 FLOP of BF16 digit products, P = S (S + 1) / 2, from the
+        third iteration on (tensor);
       sliced pressure GEMM: P 2 Q_c m n^2 per converged query (tensor);
-      elimination: 2 n^3 / 3 + 2 n^2 FLOP in FP32 (ALU);
-      system assembly: 8 n^2 (A(mu)) + 4 n^2 (J^c, after the first iteration) bytes read and
-        4 n (n + 1) bytes written (HBM);
+      elimination: 2 n^3 / 3 + 2 n^2 FLOP in FP32 per factorisation, 2 n^2 per chord solve (ALU);
+      system assembly: 8 n^2 (A(mu)) + 4 n^2 (J^c, iterations with a new Jacobian after the
+        first) bytes read and 4 n (n + 1) bytes written; a chord step reads A(mu) and writes the
+        right-hand side, 8 n^2 + 4 n (HBM);
       per-query preparation: 8 n^2 bytes of A(mu) written, once per query (HBM)."""
     peaks, kind = measured_peaks()
     n = q.n.astype(np.float64)
     it = info["iters"].astype(np.float64)
+    full = np.where(chord, np.minimum(it, 3), it)   # iterations that factor a new Jacobian
+    chs = it - full                                 # chord steps
+    jac = np.maximum(full - 1, 0)                   # Jacobian contractions
     tot_ms = sum(v[0] for v in kprof.values()) or 1.0
     kernels = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps,
                    "share": v[0] / tot_ms} for k, v in kprof.items() if v[1]}
@@ -397,15 +431,17 @@ def kernel_rooflines(prec, wl, q, info, kprof, steps):
     work = {  # kernel -> (bound, algorithmic units per step, peak, unit, peak source)
         "k_newton_fp64": ("alu", float(np.sum(it * (2 * (wl.q_c * n ** 3 + wl.q_a * n ** 2) + 2 * n ** 3 / 3 + 2 * n ** 2))),
                           FP64_PEAK_TFLOPS, "TFLOP/s", "measured FP64 FMA throughput (152 SMs, 2070 MHz)"),
-        "k_tc_gemm<plain>": ("tensor", float(np.sum(np.maximum(it - 1, 0) * 3 * 2.0 * wl.q_c * n ** 3)),
+        "k_tc_gemm<plain>": ("tensor", float(np.sum(jac * 3 * 2.0 * wl.q_c * n ** 3)),
                              bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
         "k_tc_gemm<sliced>": ("tensor", float(np.sum(np.maximum(it - 2, 0) * 2.0 * n ** 2 * p0 * wl.q_c * n)),
                               bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
         "k_tc_gemm<sliced,pressure>": ("tensor", float(np.sum(2.0 * (wl.m or 0) * n * p0 * wl.q_c * n)),
                                        bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
-        "k_lu_mixed": ("alu", float(np.sum(it * (2 * n ** 3 / 3 + 2 * n ** 2))), FP32_PEAK_TFLOPS, "TFLOP/s",
+        "k_lu_mixed": ("alu", float(np.sum(full * (2 * n ** 3 / 3 + 2 * n ** 2) + chs * 2 * n ** 2)),
+                       FP32_PEAK_TFLOPS, "TFLOP/s",
                        "FP32 FMA peak from unit counts and clock (152 x 128 x 2 x 2.07 GHz)"),
-        "k_newton_system": ("hbm", float(np.sum(it * (8 * n ** 2 + 4 * n * (n + 1)) + np.maximum(it - 1, 0) * 4 * n ** 2)),
+        "k_newton_system": ("hbm", float(np.sum(full * (8 * n ** 2 + 4 * n * (n + 1)) + jac * 4 * n ** 2
+                                                + chs * (8 * n ** 2 + 4 * n))),
                             hbm, "GB/s",
                             f"HBM copy, {kind} (MEASURED_PEAKS.json)"),
         "k_prep": ("hbm", float(np.sum(8 * n ** 2)), hbm, "GB/s", f"HBM copy, {kind} (MEASURED_PEAKS.json)"),
@@ -524,6 +560,54 @@ def run_serve(args, wl, rank, world, local):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def combined_pressure_modes(U, Pp):
+    """Pressure data of the velocity basis by the second construction of Sec. 4.2: POD of the
+    velocity snapshots U [K][n] by the method of snapshots (eigenvectors of U U^T scaled to
+    orthonormal modes psi_j = sum_i v^j_i u_i), pressure functions p^_j = sum_i v^j_i p_i from
+    their pressures Pp [K][m] with the same coefficients. Returned in the coordinates of the
+    reduced velocity basis the solver uses: P_hat [m][n] with p = P_hat u."""
+    n = U.shape[1]
+    lam, W = np.linalg.eigh(U @ U.T)
+    keep = np.argsort(lam)[::-1][:n]
+    V = W[:, keep] / np.sqrt(lam[keep])[None, :]
+    Psi = U.T @ V          # [n][n] orthonormal POD modes in reduced coordinates
+    return (Pp.T @ V) @ Psi.T
+
+
+def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, flush, args):
+    """Pressure reconstruction (Sec. 4.2) against recovery on the same batch: the modes fitted
+    from training queries of the same workload (solved, pressure recovered), then p = P_hat u for
+    the timed batch's velocities; kernel time by CUDA events, error against recovery."""
+    import torch
+    K = 1024
+    qt = synth.make_queries(wl, batch=batch * max(1, int(os.environ.get("WORLD_SIZE", "1"))) + K)
+    mu_t, n_t = qt.mu[-K:], qt.n[-K:]
+    full = n_t == wl.n_max
+    U, Pp, info = ctx.rb_solve(mu_t[full], n_t[full])
+    good = info["status"] == 0
+    P_hat = combined_pressure_modes(U[good], Pp[good])
+    ctx.rb_load_pressure_modes(P_hat)
+    d_pr = torch.empty((batch, P_hat.shape[0]), dtype=torch.float64, device=d_u.device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.warmup + args.steps)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            ctx.rb_reconstruct_pressure_device(d_u, batch, d_n, d_pr, stream.cuda_stream)
+            b.record(stream)
+    torch.cuda.synchronize()
+    t = [a.elapsed_time(b) for a, b in ev[args.warmup:]]
+    p_r = d_pr.cpu().numpy()
+    err = np.linalg.norm(p_r - p_rec, axis=1) / np.linalg.norm(p_rec, axis=1)
+    rec_ms = sum(kprof.get(k, (0.0, 0))[0] for k in ("k_pressure", "k_tc_gemm<sliced,pressure>"))
+    rec_ms /= args.steps
+    return {"ms_per_step": float(np.mean(t)), "recovery_ms_per_step": rec_ms,
+            "rel_err_vs_recovery": {"median": float(np.median(err)), "max": float(err.max())},
+            "modes": f"m_r = {P_hat.shape[0]}, from {int(good.sum())} training queries of the "
+                     "workload (combined basis, second construction of Sec. 4.2)"}
 
 
 def plain_fp64(rb, ops, q, batch, dev, flush, args):

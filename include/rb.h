@@ -78,6 +78,15 @@ enum {
                         convergence test FP64-accurate */
 };
 
+/* pressure stage of rb_solve, rb_solve_theta and rb_solve_device */
+enum {
+  RB_PRESSURE_RECOVER = 0,     /* a-posteriori recovery from the supremizer system
+                                  (Sec. 2.2, Eq. sup-vvar; Sec. 4.1, Eq. blocksolve-2) */
+  RB_PRESSURE_RECONSTRUCT = 1  /* reconstruction from the velocity coefficients with the
+                                  pressure modes of a combined basis (Sec. 4.2):
+                                  p = sum_j u_j p^_j, see rb_load_pressure_modes */
+};
+
 /* parameter-function family */
 enum { RB_THETA_TRIG = 0, RB_THETA_USER = 1, RB_THETA_POLY = 2 };
 
@@ -118,6 +127,9 @@ typedef struct {
                          (RB_THETA_USER: as RB_THETA_TRIG; theta comes with rb_solve_theta) */
   int serve_slots;    /* serving: queries on the device at once (0: as many as the memory
                          budget admits, at most 4096) */
+  int pressure_method;  /* RB_PRESSURE_RECOVER (default) or RB_PRESSURE_RECONSTRUCT: then
+                           p_out of the solves is [n_queries][m_r] from the loaded pressure
+                           modes, and the server refuses to start */
 } rb_config;
 
 typedef struct {
@@ -169,6 +181,32 @@ int rb_solve_theta(rb_ctx *ctx, const double *theta, int n_queries, const int *n
  * reused by the next call on any stream, so calls on one context must be ordered. */
 int rb_solve_device(rb_ctx *ctx, const double *d_mu, int n_queries, const int *d_n,
                     double *d_u, double *d_p, rb_query_info *d_info, void *cuda_stream);
+
+/* ---- pressure reconstruction (Sec. 4.2, combined velocity-pressure basis) -----------------
+ * With a combined basis every velocity basis function j carries pressure data p^_j, and the
+ * pressure of a solution with velocity coefficients u is p = sum_{j < n} u_j p^_j (the
+ * velocity system is unchanged). This assumes that pressure depends linearly on velocity, which
+ * the Navier-Stokes equations do not satisfy (Sec. 4.2, remark on linearity): it suits linear
+ * models or small parameter ranges; recovery (RB_PRESSURE_RECOVER) has no such restriction.
+ *
+ * rb_load_pressure_modes copies P_hat [m_r][n_max] (host, row-major, caller-owned): column j
+ * holds the coefficients of p^_j in any pressure space of m_r functions (reduced or
+ * high-fidelity), 1 <= m_r <= RB_MR_MAX. Queries of size n use the first n columns (nested
+ * truncation). Replaces earlier modes; loading new operators drops them. RB_ERR_STATE without
+ * operators, RB_ERR_ARG on bad sizes, RB_ERR_OOM over the memory budget. */
+#define RB_MR_MAX (1 << 22)
+int rb_load_pressure_modes(rb_ctx *ctx, const double *P_hat, int m_r);
+
+/* p_out[b][k] = sum_{j < n_b} P_hat[k][j] u[b][j] in FP64 for b < n_queries, from host buffers:
+ * u [n_queries][n_max] (entries from n_b on are not read), n [n_queries] (NULL: n_max),
+ * p_out [n_queries][m_r]. A query with n_b outside 1..n_max gets NaN in every entry.
+ * RB_ERR_STATE when no modes are loaded. Synchronous. */
+int rb_reconstruct_pressure(rb_ctx *ctx, const double *u, int n_queries, const int *n,
+                            double *p_out);
+
+/* The same from device buffers, asynchronously on cuda_stream (NULL: the legacy stream). */
+int rb_reconstruct_pressure_device(rb_ctx *ctx, const double *d_u, int n_queries,
+                                   const int *d_n, double *d_p, void *cuda_stream);
 
 /* Evaluate the residual R(u; mu) (FP64) and, if J_out != NULL, the Jacobian J(u; mu) at
  * caller-given coefficient vectors, for n_queries queries of size n (all equal, <= n_max),
@@ -222,7 +260,8 @@ enum {
   RB_K_GEMM_PRES = 7,    /* mixed: tcgen05 sliced pressure right-hand side (-> FP64) */
   RB_K_SYSTEM = 8,       /* mixed: Newton system assembly [J | -R] and residual norms */
   RB_K_PREP = 9,         /* mixed: per-query theta, f(mu), A(mu) at the start of a solve */
-  RB_K_COUNT = 10
+  RB_K_RECONSTRUCT = 10, /* pressure reconstruction p = P_hat u (either precision) */
+  RB_K_COUNT = 11
 };
 int rb_profile(rb_ctx *ctx, int enable);
 int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launches);

@@ -67,6 +67,8 @@ def lib():
         L.oracle_newton_theta.argtypes = [P, ctypes.c_int, P, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, P, P, P, P]
         L.oracle_pressure_theta.argtypes = [P, ctypes.c_int, P, P, P]
+        L.oracle_reconstruct.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+        L.oracle_reconstruct.restype = None
         L.oracle_pressure_theta.restype = ctypes.c_int
         L.oracle_solve_batch.argtypes = [P, ctypes.c_int, P, P, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int, P, P, P, ctypes.c_int]
@@ -193,6 +195,18 @@ class Oracle:
         lib().oracle_solve_theta_batch(self.ref, nq, _ptr(theta), _ptr(nsz), tol_upd, tol_res,
                                        max_iter, _ptr(u), _ptr(p), info, threads)
         return u, p, _info_arrays(info, nq)
+
+
+def reconstruct(P_hat, u, n=None):
+    """Pressure reconstruction p = sum_{j < n} u_j P_hat[:, j] (Sec. 4.2), one query per row of u."""
+    P_hat = np.ascontiguousarray(P_hat, dtype=np.float64)
+    m_r, n_max = P_hat.shape
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, n_max)
+    nn = np.full(u.shape[0], n_max, np.int32) if n is None else np.asarray(n, np.int32).reshape(-1)
+    p = np.empty((u.shape[0], m_r))
+    for b in range(u.shape[0]):
+        lib().oracle_reconstruct(_ptr(P_hat), m_r, n_max, int(nn[b]), _ptr(u[b]), _ptr(p[b]))
+    return p
 
 
 def _info_arrays(info, nq):

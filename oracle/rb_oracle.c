@@ -28,6 +28,11 @@
  *   pressure   a posteriori recovery (Sec. 2.2, Eq. sup-vvar; Sec. 4.1, Eq. blocksolve-2):
  *              B(mu) p = fs(mu) - As(mu) u - Cs_mu(u, u), B(mu) = sum_q theta^b_q B_q,
  *              solved by the same elimination. Convection is included (Eq. sup-vvar).
+ *   theta (polynomial family) monomials phi^q of the rotation angle from the truncated
+ *              rotation series (Sec. 5, Eq. rotsum), theta^a_q = phi^q / Re.
+ *   reconstruction  pressure from the velocity coefficients with the pressure data attached
+ *              to every velocity basis function of a combined basis (Sec. 4.2):
+ *              p = sum_j u_j p^_j, column j of P_hat holding p^_j.
  *
  * Nested truncation: a query of size n <= n_max uses the leading n x n (x n) blocks of every
  * operator, with the full leading dimensions of the stored arrays as strides.
@@ -348,6 +353,17 @@ void oracle_solve_theta_batch(const oracle_ops *o, int nq, const double *theta,
     for (int i = 0; i < o->n_max; ++i) u_row[i] = 0.0;
     solve_one(o, n, theta + (size_t)b * nt, tol_upd, tol_res, max_iter, u_row,
               p_out ? p_out + (size_t)b * o->m : NULL, &info[b]);
+  }
+}
+
+/* Pressure reconstruction (Sec. 4.2): p[k] = sum_{j < n} P_hat[k][j] u[j] for P_hat [m_r][n_max]
+   (column j = the pressure data of velocity basis function j), j ascending. */
+void oracle_reconstruct(const double *P_hat, int m_r, int n_max, int n, const double *u,
+                        double *p) {
+  for (int k = 0; k < m_r; ++k) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += P_hat[(size_t)k * n_max + j] * u[j];
+    p[k] = s;
   }
 }
 

@@ -52,6 +52,10 @@ int mixed_serve_step(rb_ctx *ctx, const double *d_mu, const int *d_n, double *d_
                      std::vector<int> &perm, cudaStream_t st);
 int mixed_error_word(rb_ctx *ctx, cudaStream_t st);
 int mixed_tuning(rb_ctx *ctx, int i, int *out6, float *ms3);
+// pressure reconstruction (combined basis): p = P_hat u for every query
+int reconstruct_impl(rb_ctx *ctx, const double *d_u, int nq, const int *d_n, double *d_p,
+                     cudaStream_t st);
+void drop_pressure_modes(rb_ctx *ctx);
 
 // per-kernel event timing (active only while profiling is enabled)
 struct ProfMark {
@@ -76,6 +80,8 @@ struct rb_ctx {
   std::vector<void *> op_allocs;
   void *d_C = nullptr;  // C in its storage type [q_c][n][n][n]
   int c_is_f32 = 0;
+  double *d_PT = nullptr;  // pressure modes of a combined basis, transposed [n_max][m_r]
+  int m_r = 0;
   // scratch
   rb::Scratch stage, jscratch, info_scratch, eval_scratch;
   rb::MixedState *mixed = nullptr;

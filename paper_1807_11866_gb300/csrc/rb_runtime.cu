@@ -82,6 +82,7 @@ void Scratch::release(rb_ctx *ctx) {
 }
 
 static void free_ops(rb_ctx *ctx) {
+  drop_pressure_modes(ctx);
   for (void *p : ctx->op_allocs) ctx_free(ctx, p);
   ctx->op_allocs.clear();
   ctx->loaded = false;
@@ -210,7 +211,16 @@ int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, in
   if (!ctx->loaded) return set_error(ctx, RB_ERR_STATE, "no operators loaded");
   if (serve_running(ctx))
     return set_error(ctx, RB_ERR_STATE, "the server owns this context's batch state; stop it first");
+  // pressure by reconstruction (Sec. 4.2): the velocity solve without recovery, then p = P_hat u
+  const bool recon = ctx->cfg.pressure_method == RB_PRESSURE_RECONSTRUCT && d_p;
+  if (recon && !ctx->d_PT)
+    return set_error(ctx, RB_ERR_STATE, "pressure reconstruction needs rb_load_pressure_modes");
   if (nq == 0) return RB_OK;
+  if (recon) {
+    int rc = solve_device_impl(ctx, d_mu, d_theta, nq, d_n, d_u, nullptr, d_info, st, h_n);
+    if (rc != RB_OK) return rc;
+    return reconstruct_impl(ctx, d_u, nq, d_n, d_p, st);
+  }
   // per-query status is needed to gate pressure recovery
   rb_query_info *info = d_info;
   if (!info && d_p && ctx->ops.m > 0) {
@@ -235,7 +245,10 @@ int stage_solve(rb_ctx *ctx, const double *mu, const double *theta, int nq, cons
   if (nq == 0) return RB_OK;
   const DevOps &o = ctx->ops;
   const int in_w = theta ? o.n_theta : 2;
-  const int m = (p_out && o.m > 0) ? o.m : 0;
+  const bool recon = ctx->cfg.pressure_method == RB_PRESSURE_RECONSTRUCT;
+  if (recon && p_out && !ctx->d_PT)
+    return set_error(ctx, RB_ERR_STATE, "pressure reconstruction needs rb_load_pressure_modes");
+  const int m = !p_out ? 0 : (recon ? ctx->m_r : (o.m > 0 ? o.m : 0));
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t b_in = al(sizeof(double) * (size_t)nq * in_w), b_n = al(sizeof(int) * (size_t)nq);
   const size_t b_u = al(sizeof(double) * (size_t)nq * o.n_max), b_p = al(sizeof(double) * (size_t)nq * m);
@@ -285,6 +298,7 @@ void rb_config_default(rb_config *cfg) {
   cfg->autotune = (at && *at) ? (atoi(at) != 0) : 1;
   cfg->theta_family = RB_THETA_TRIG;
   cfg->serve_slots = 0;
+  cfg->pressure_method = RB_PRESSURE_RECOVER;
 }
 
 int rb_create(rb_ctx **out, const rb_config *cfg, int device) {
@@ -294,7 +308,8 @@ int rb_create(rb_ctx **out, const rb_config *cfg, int device) {
   if (cfg) ctx->cfg = *cfg; else rb_config_default(&ctx->cfg);
   if (ctx->cfg.max_iter < 1 || ctx->cfg.precision < RB_PREC_FP64 || ctx->cfg.precision > RB_PREC_MIXED ||
       ctx->cfg.serve_slots < 0 || ctx->cfg.theta_family < RB_THETA_TRIG ||
-      ctx->cfg.theta_family > RB_THETA_POLY ||
+      ctx->cfg.theta_family > RB_THETA_POLY || ctx->cfg.pressure_method < RB_PRESSURE_RECOVER ||
+      ctx->cfg.pressure_method > RB_PRESSURE_RECONSTRUCT ||
       !(ctx->cfg.tol_update >= 0) || !(ctx->cfg.tol_res >= 0)) {
     delete ctx;
     return RB_ERR_ARG;

@@ -315,6 +315,9 @@ int rb_serve_start(rb_ctx *ctx) {
   if (!ctx) return RB_ERR_ARG;
   if (!ctx->loaded) return set_error(ctx, RB_ERR_STATE, "no operators loaded");
   if (serve_running(ctx)) return set_error(ctx, RB_ERR_STATE, "server already running");
+  if (ctx->cfg.pressure_method != RB_PRESSURE_RECOVER)
+    return set_error(ctx, RB_ERR_STATE, "the server recovers the pressure; reconstruct it from "
+                                        "the polled velocities with rb_reconstruct_pressure");
   serve_shutdown(ctx);  // reap a previous server
   cudaSetDevice(ctx->device);
   ServeState *S = new ServeState();

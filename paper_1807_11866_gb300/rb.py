@@ -20,16 +20,18 @@ RB_Q_OK, RB_Q_NOT_CONVERGED, RB_Q_SINGULAR, RB_Q_NONFINITE, RB_Q_REJECTED = 0, 1
 RB_F64, RB_F32 = 0, 1
 RB_PREC_FP64, RB_PREC_MIXED = 0, 1
 RB_THETA_TRIG, RB_THETA_USER, RB_THETA_POLY = 0, 1, 2
+RB_PRESSURE_RECOVER, RB_PRESSURE_RECONSTRUCT = 0, 1
 RB_N_MAX, RB_M_MAX, RB_Q_MAX = 320, 128, 64
 RB_STATIC_N_MAX, RB_STATIC_SCRATCH_BYTES = 512, 16 << 20
 
 EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
            "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
            "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
-           "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots", "rb_tuning"]
+           "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots", "rb_tuning",
+           "rb_load_pressure_modes", "rb_reconstruct_pressure", "rb_reconstruct_pressure_device"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>",
-              "k_newton_system", "k_prep"]
+              "k_newton_system", "k_prep", "k_reconstruct"]
 
 
 class rb_operators(ctypes.Structure):
@@ -46,7 +48,7 @@ class rb_config(ctypes.Structure):
                 ("tol_res", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("mem_budget", ctypes.c_size_t), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("theta_family", ctypes.c_int),
-                ("serve_slots", ctypes.c_int)]
+                ("serve_slots", ctypes.c_int), ("pressure_method", ctypes.c_int)]
 
 
 class rb_query_info(ctypes.Structure):
@@ -81,6 +83,9 @@ def library():
         L.rb_solve_theta.argtypes = [P, P, I, P, P, P, P]
         L.rb_solve_device.argtypes = [P, P, I, P, P, P, P, P]
         L.rb_eval.argtypes = [P, P, I, I, P, I, P, P]
+        L.rb_load_pressure_modes.argtypes = [P, P, I]
+        L.rb_reconstruct_pressure.argtypes = [P, P, I, P, P]
+        L.rb_reconstruct_pressure_device.argtypes = [P, P, I, P, P, P]
         L.rb_gepp_solve.argtypes = [P, I, I, P, P, P, P]
         L.rb_gepp_solve_static.argtypes = [I, I, P, P, P, P, P]
         L.rb_profile.argtypes = [P, I]
@@ -139,7 +144,7 @@ class Context:
 
     def __init__(self, precision=RB_PREC_FP64, tol_update=None, tol_res=None, max_iter=None,
                  mem_budget=None, use_graph=None, device=0, serve_slots=None, autotune=None,
-                 theta_family=None):
+                 theta_family=None, pressure_method=None):
         L = library()
         cfg = rb_config_default()
         cfg.precision = precision
@@ -159,13 +164,15 @@ class Context:
             cfg.autotune = autotune
         if theta_family is not None:
             cfg.theta_family = theta_family
+        if pressure_method is not None:
+            cfg.pressure_method = pressure_method
         self.cfg = cfg
         h = ctypes.c_void_p()
         rc = L.rb_create(ctypes.byref(h), ctypes.byref(cfg), device)
         if rc != RB_OK:
             raise RbError(rc, "rb_create failed")
         self.h = h
-        self.n_max = self.m = 0
+        self.n_max = self.m = self.m_r = 0
         self._keep = None
 
     def close(self):
@@ -208,7 +215,41 @@ class Context:
             keep += [B, As, Cs, fs]
         self._check(library().rb_load_operators(self.h, ctypes.byref(ops)), "rb_load_operators")
         self.n_max, self.m = n, (ops.m if B is not None else 0)
+        self.m_r = 0
         self.q = (ops.q_a, ops.q_c, ops.q_f, ops.q_b)
+
+    def rb_load_pressure_modes(self, P_hat):
+        """P_hat [m_r][n_max]: column j = pressure data of velocity basis function j."""
+        P_hat = _f64(P_hat)
+        self._check(library().rb_load_pressure_modes(self.h, _ptr(P_hat), P_hat.shape[0]),
+                    "rb_load_pressure_modes")
+        self.m_r = P_hat.shape[0]
+
+    def rb_reconstruct_pressure(self, u, n=None):
+        u = _f64(u).reshape(-1, self.n_max)
+        nq = u.shape[0]
+        nn = None if n is None else np.ascontiguousarray(n, dtype=np.int32)
+        p = np.empty((nq, self.m_r))
+        self._check(library().rb_reconstruct_pressure(self.h, _ptr(u), nq, _ptr(nn), _ptr(p)),
+                    "rb_reconstruct_pressure")
+        return p
+
+    def rb_reconstruct_pressure_device(self, d_u, n_queries, d_n, d_p, stream):
+        return self._check(library().rb_reconstruct_pressure_device(
+            self.h, _ptr(d_u), n_queries, _ptr(d_n), _ptr(d_p), stream),
+            "rb_reconstruct_pressure_device")
+
+    def _p_out(self, nq, pressure):
+        # in reconstruction mode a buffer always goes down, so that missing modes are an error
+        recon = self.cfg.pressure_method == RB_PRESSURE_RECONSTRUCT
+        if not pressure or (self.p_width == 0 and not recon):
+            return None
+        return np.empty((nq, max(self.p_width, 1)))
+
+    @property
+    def p_width(self):
+        """Columns of p_out of the solves (m, or m_r when reconstructing)."""
+        return self.m_r if self.cfg.pressure_method == RB_PRESSURE_RECONSTRUCT else self.m
 
     def load_set(self, ops):
         """Load a synth.OperatorSet (or any object with the same fields). A set that names its
@@ -225,7 +266,7 @@ class Context:
         nq = mu.shape[0]
         nn = None if n is None else np.ascontiguousarray(n, dtype=np.int32)
         u = np.empty((nq, self.n_max))
-        p = np.empty((nq, self.m)) if (pressure and self.m > 0) else None
+        p = self._p_out(nq, pressure)
         info = np.zeros(nq, dtype=INFO_DTYPE)
         self._check(library().rb_solve(self.h, _ptr(mu), nq, _ptr(nn), _ptr(u), _ptr(p),
                                        _ptr(info)), "rb_solve")
@@ -236,7 +277,7 @@ class Context:
         nq = theta.shape[0]
         nn = None if n is None else np.ascontiguousarray(n, dtype=np.int32)
         u = np.empty((nq, self.n_max))
-        p = np.empty((nq, self.m)) if (pressure and self.m > 0) else None
+        p = self._p_out(nq, pressure)
         info = np.zeros(nq, dtype=INFO_DTYPE)
         self._check(library().rb_solve_theta(self.h, _ptr(theta), nq, _ptr(nn), _ptr(u),
                                              _ptr(p), _ptr(info)), "rb_solve_theta")

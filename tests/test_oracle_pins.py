@@ -344,3 +344,39 @@ def test_rotation_workload_converges(oracle_lib):
     nz = np.nonzero(t_poly)[0]
     np.testing.assert_array_equal(nz, [0, wl.q_a, wl.q_a + wl.q_c, wl.q_a + wl.q_c + wl.q_f])
     np.testing.assert_array_equal(t_poly[nz], t_trig[nz])
+
+
+def test_reconstruct_unit_vectors_and_truncation(oracle_lib):
+    """Pressure reconstruction (Sec. 4.2): u = e_j gives column j of P_hat exactly (the pressure
+    data of basis function j); columns from n on are never read (NaN there stays out)."""
+    g = np.random.default_rng(5)
+    P = g.standard_normal((7, 5))
+    for j in range(5):
+        e = np.zeros(5)
+        e[j] = 1.0
+        np.testing.assert_array_equal(oracle_lib.reconstruct(P, e)[0], P[:, j])
+    Pn = P.copy()
+    Pn[:, 3:] = np.nan
+    u = g.standard_normal(5)
+    p = oracle_lib.reconstruct(Pn, u, n=[3])[0]
+    brute = [math.fsum(P[k, j] * u[j] for j in range(3)) for k in range(7)]
+    np.testing.assert_allclose(p, brute, rtol=1e-15, atol=1e-15)
+
+
+def test_combined_basis_reproduces_its_snapshots(oracle_lib):
+    """Second construction of Sec. 4.2: POD of the velocity snapshots (method of snapshots,
+    Sec. 3.2), the pressure functions combined with the same snapshot coefficients. With as many
+    independent snapshots as modes, reconstructing a snapshot from its coefficients in the POD
+    basis returns that snapshot's own pressure."""
+    g = np.random.default_rng(11)
+    K, n_h, m_h = 6, 9, 4                  # snapshots, velocity / pressure dofs
+    U = g.standard_normal((K, n_h))        # velocity snapshots (rows)
+    Pp = g.standard_normal((K, m_h))       # their pressures
+    lam, W = np.linalg.eigh(U @ U.T)       # correlation matrix of the snapshots
+    V = W / np.sqrt(lam)[None, :]          # coefficient vectors v^j (columns)
+    Psi = U.T @ V                          # orthonormal velocity modes psi_j = sum_i v^j_i u_i
+    np.testing.assert_allclose(Psi.T @ Psi, np.eye(K), atol=1e-12)
+    P_hat = Pp.T @ V                       # p^_j = sum_i v^j_i p_i, column j
+    for i in range(K):
+        eta = Psi.T @ U[i]                 # velocity coefficients of snapshot i
+        np.testing.assert_allclose(oracle_lib.reconstruct(P_hat, eta)[0], Pp[i], atol=1e-11)
