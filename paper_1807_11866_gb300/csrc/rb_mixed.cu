@@ -389,41 +389,54 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
     const int n = p.nsz ? p.nsz[b] : o.n_max;
     const double *ta = p.theta + (size_t)b * o.n_theta, *tc = ta + o.q_a;
     const double *ub = p.u + (size_t)b * o.n_max;
-    const int nk = o.q_c * p.nb;
-    auto xval = [&](int kap) -> double {  // (theta^c (x) u)[kap], zero past the query's size
-      if (kap >= nk) return 0.0;
-      const int q = kap / p.nb, l = kap - q * p.nb;
-      return l < n ? tc[q] * ub[l] : 0.0;
+    // (theta^c (x) u)[kap] at kap = q nb + l, zero past the query's size
+    auto xval = [&](int q, int l) -> double {
+      return (q < o.q_c && l < n) ? tc[q] * ub[l] : 0.0;
     };
-    // grid exponents from the integer bit patterns (|x| orders like its bits)
+    // grid exponents from the integer bit patterns (|x| orders like its bits). The largest
+    // |theta^c_q u_l| is the rounded product of the largest factors (rounding is monotone),
+    // so the maximum over the row needs only the maxima of theta^c and u.
     const unsigned long long absmask = 0x7FFFFFFFFFFFFFFFull;
     unsigned long long m0 = 0, m1 = 0;
     if (p.digits) {
-      for (int kap = lane; kap < nk; kap += 32) {
-        const unsigned long long v = (unsigned long long)__double_as_longlong(xval(kap)) & absmask;
-        m0 = v > m0 ? v : m0;
+      unsigned long long mt = 0, mu = 0;
+      for (int q = lane; q < o.q_c; q += 32) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(tc[q]) & absmask;
+        mt = v > mt ? v : mt;
+      }
+      for (int l = lane; l < n; l += 32) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(ub[l]) & absmask;
+        mu = v > mu ? v : mu;
       }
       for (int q = lane; q < o.q_a; q += 32) {
         const unsigned long long v = (unsigned long long)__double_as_longlong(ta[q]) & absmask;
         m1 = v > m1 ? v : m1;
       }
       for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long a = __shfl_xor_sync(0xffffffffu, m0, off);
-        const unsigned long long c = __shfl_xor_sync(0xffffffffu, m1, off);
-        m0 = a > m0 ? a : m0;
-        m1 = c > m1 ? c : m1;
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, mt, off);
+        const unsigned long long c = __shfl_xor_sync(0xffffffffu, mu, off);
+        const unsigned long long d = __shfl_xor_sync(0xffffffffu, m1, off);
+        mt = a > mt ? a : mt;
+        mu = c > mu ? c : mu;
+        m1 = d > m1 ? d : m1;
       }
+      m0 = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)mt) *
+                                                    __longlong_as_double((long long)mu)) & absmask;
     }
     // digits on the grid with one binade of headroom (balanced digits); the sliced operand holds
     // x / 2: the same digits recorded one binade lower
     const int ex0 = exp_of_bits(m0) + 1, e0 = ex0 - 1, e1 = exp_of_bits(m1) + 1;
     const size_t sstride = (size_t)p.b_pad * p.Kpad;
     const size_t jstride = (size_t)p.b_pad * p.Kpad0;
-    // Kpad0 and Kpad are multiples of 64: a pair never straddles the segment boundary
+    // Kpad0 and Kpad are multiples of 64: a pair never straddles the segment boundary. The
+    // lane's (q, l) of kap = 2 lane + 64 i advance without a division per step.
+    int q = (2 * lane) / p.nb, l = 2 * lane - q * p.nb;
+#pragma unroll 2
     for (int kap = 2 * lane; kap < p.Kpad; kap += 64) {
       const size_t off = (size_t)b * p.Kpad + kap;
       if (kap < p.Kpad0) {
-        const double x0 = xval(kap), x1 = xval(kap + 1);
+        const int q1 = l + 1 < p.nb ? q : q + 1, l1 = l + 1 < p.nb ? l + 1 : 0;
+        const double x0 = xval(q, l), x1 = xval(q1, l1);
         if (p.mode == 0 && p.split) {
           // split BF16 operand of the Jacobian GEMM: [x_hi | x_hi | x_lo]
           const float f0 = (float)x0, f1 = (float)x1;
@@ -437,9 +450,14 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
         }
         if (p.digits) digits_pair(x0, x1, ex0, p.S0, p.Xd + off, sstride);
       } else if (p.digits) {
-        const int q = kap - p.Kpad0;
-        digits_pair(q < o.q_a ? ta[q] : 0.0, q + 1 < o.q_a ? ta[q + 1] : 0.0, e1, p.S1, p.Xd + off,
-                    sstride);
+        const int qa = kap - p.Kpad0;
+        digits_pair(qa < o.q_a ? ta[qa] : 0.0, qa + 1 < o.q_a ? ta[qa + 1] : 0.0, e1, p.S1,
+                    p.Xd + off, sstride);
+      }
+      l += 64;
+      while (l >= p.nb) {
+        l -= p.nb;
+        ++q;
       }
     }
     if (!p.digits) continue;
