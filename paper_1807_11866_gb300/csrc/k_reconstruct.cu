@@ -64,6 +64,34 @@ __global__ void __launch_bounds__(kRecT) k_reconstruct(const double *__restrict_
   }
 }
 
+// Small pressure spaces (m_r <= kRecFlatMax): one thread per (query, coefficient) with the
+// coefficient fastest, so a launch keeps nq m_r threads in flight (the tiled kernel would leave
+// most of its 256 threads idle); the same sums in the same order as k_reconstruct.
+constexpr int kRecFlatMax = 128;
+__global__ void __launch_bounds__(256) k_reconstruct_flat(const double *__restrict__ PT,
+                                                          int n_max, int m_r,
+                                                          const double *__restrict__ u, int nq,
+                                                          const int *__restrict__ nsz,
+                                                          double *__restrict__ p) {
+  const long long total = (long long)nq * m_r;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / m_r;
+    const int k = (int)(i - b * m_r);
+    const int n = nsz ? nsz[b] : n_max;
+    if (n < 1 || n > n_max) {
+      p[i] = __longlong_as_double(0x7ff8000000000000LL);
+      continue;
+    }
+    const double *ub = u + (size_t)b * n_max;
+    const double *col = PT + k;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int j = 0; j < n; ++j) acc = fma(__ldg(col + (size_t)j * m_r), __ldg(ub + j), acc);
+    p[i] = acc;
+  }
+}
+
 // PT[j][k] = P[k][j] for P [m_r][n_max], 32 x 32 tiles through shared memory.
 __global__ void k_transpose_modes(const double *__restrict__ P, int m_r, int n_max,
                                   double *__restrict__ PT) {
@@ -93,10 +121,16 @@ int reconstruct_impl(rb_ctx *ctx, const double *d_u, int nq, const int *d_n, dou
                      cudaStream_t st) {
   if (!ctx->d_PT) return set_error(ctx, RB_ERR_STATE, "no pressure modes loaded");
   if (nq == 0) return RB_OK;
-  const long long k_tiles = (ctx->m_r + kRecT - 1) / kRecT;
-  dim3 grid((unsigned)((nq + kRecQ - 1) / kRecQ), (unsigned)std::min<long long>(k_tiles, 65535));
   const int mk = prof_begin(ctx, RB_K_RECONSTRUCT, st);
-  k_reconstruct<<<grid, kRecT, 0, st>>>(ctx->d_PT, ctx->ops.n_max, ctx->m_r, d_u, nq, d_n, d_p);
+  if (ctx->m_r <= kRecFlatMax) {
+    const long long total = (long long)nq * ctx->m_r;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)ctx->sms * 16);
+    k_reconstruct_flat<<<blocks, 256, 0, st>>>(ctx->d_PT, ctx->ops.n_max, ctx->m_r, d_u, nq, d_n, d_p);
+  } else {
+    const long long k_tiles = (ctx->m_r + kRecT - 1) / kRecT;
+    dim3 grid((unsigned)((nq + kRecQ - 1) / kRecQ), (unsigned)std::min<long long>(k_tiles, 65535));
+    k_reconstruct<<<grid, kRecT, 0, st>>>(ctx->d_PT, ctx->ops.n_max, ctx->m_r, d_u, nq, d_n, d_p);
+  }
   prof_end(ctx, mk, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_reconstruct");

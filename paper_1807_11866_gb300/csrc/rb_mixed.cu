@@ -510,7 +510,7 @@ __global__ void k_prep_theta(PrepParams p) {
     if (p.theta_in) {
       for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta_in[(size_t)b * o.n_theta + i];
     } else {
-      theta_eval_strided(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane, 32);
+      theta_eval_warp(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane);
     }
     __syncwarp();
     const double *tf = th + o.q_a + o.q_c;
