@@ -362,16 +362,18 @@ FP64_PEAK_TFLOPS = 1.196  # FP64 FMA throughput measured on GB300 (152 SMs at 20
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DIGITS = int(os.environ.get("RB_DIGITS", "6"))  # digit slices of the sliced convection product
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels as they
-# stand, from ncu captures of a 4096-query n = 50 solve (profiles/kernels_sweep_n50.md) and of
-# the n = 300 dense regime; a kernel changed since its capture has no entry.
+# stand, from ncu captures of this bench command on the n = 50 sweep (4096 queries) and on the
+# n = 300 dense regime; a kernel changed since its capture has no entry.
 NCU_TRAFFIC = {
+    # per-launch averages over the launches the bench times (one-pass launch list; the sliced
+    # residual GEMM from its --set full capture, the launch list mixing in the pressure launches)
     "sweep_n50": {
-        "k_tc_gemm<sliced>": 29.06e6,
-        "k_tc_gemm<plain>": 11.59e6,
-        "k_newton_system": 150.45e6,
-        "k_lu_mixed": 44.71e6,
+        "k_tc_gemm<sliced>": 29.10e6,
+        "k_tc_gemm<plain>": 11.48e6,
+        "k_newton_system": 113.9e6,
+        "k_lu_mixed": 42.57e6,
     },
-    # one-pass capture of the full-size workload (profiles/launches_dense_n300.md)
+    # one-pass capture of the full-size workload
     "dense_n300": {
         "k_tc_gemm<sliced>": 1599.45e9,
         "k_tc_gemm<plain>": 126.8e9,
@@ -562,18 +564,20 @@ def run_serve(args, wl, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
-def combined_pressure_modes(U, Pp):
+def combined_pressure_modes(U, Pp, rtol=1e-10):
     """Pressure data of the velocity basis by the second construction of Sec. 4.2: POD of the
     velocity snapshots U [K][n] by the method of snapshots (eigenvectors of U U^T scaled to
-    orthonormal modes psi_j = sum_i v^j_i u_i), pressure functions p^_j = sum_i v^j_i p_i from
-    their pressures Pp [K][m] with the same coefficients. Returned in the coordinates of the
-    reduced velocity basis the solver uses: P_hat [m][n] with p = P_hat u."""
+    orthonormal modes psi_j = sum_i v^j_i u_i, the modes with eigenvalue below rtol times the
+    largest dropped), pressure functions p^_j = sum_i v^j_i p_i from their pressures Pp [K][m]
+    with the same coefficients. Returned in the coordinates of the reduced velocity basis the
+    solver uses, P_hat [m][n] with p = P_hat u, and the number of POD modes kept."""
     n = U.shape[1]
     lam, W = np.linalg.eigh(U @ U.T)
-    keep = np.argsort(lam)[::-1][:n]
+    order = np.argsort(lam)[::-1][:n]
+    keep = order[lam[order] > rtol * lam[order[0]]]
     V = W[:, keep] / np.sqrt(lam[keep])[None, :]
-    Psi = U.T @ V          # [n][n] orthonormal POD modes in reduced coordinates
-    return (Pp.T @ V) @ Psi.T
+    Psi = U.T @ V          # [n][r] orthonormal POD modes in reduced coordinates
+    return (Pp.T @ V) @ Psi.T, len(keep)
 
 
 def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, flush, args):
@@ -587,7 +591,7 @@ def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, 
     full = n_t == wl.n_max
     U, Pp, info = ctx.rb_solve(mu_t[full], n_t[full])
     good = info["status"] == 0
-    P_hat = combined_pressure_modes(U[good], Pp[good])
+    P_hat, r = combined_pressure_modes(U[good], Pp[good])
     ctx.rb_load_pressure_modes(P_hat)
     d_pr = torch.empty((batch, P_hat.shape[0]), dtype=torch.float64, device=d_u.device)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -606,8 +610,9 @@ def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, 
     rec_ms /= args.steps
     return {"ms_per_step": float(np.mean(t)), "recovery_ms_per_step": rec_ms,
             "rel_err_vs_recovery": {"median": float(np.median(err)), "max": float(err.max())},
-            "modes": f"m_r = {P_hat.shape[0]}, from {int(good.sum())} training queries of the "
-                     "workload (combined basis, second construction of Sec. 4.2)"}
+            "modes": f"m_r = {P_hat.shape[0]}, {r} POD modes (eigenvalues above 1e-10 of the "
+                     f"largest) of {int(good.sum())} training queries of the workload (combined "
+                     "basis, second construction of Sec. 4.2)"}
 
 
 def plain_fp64(rb, ops, q, batch, dev, flush, args):
