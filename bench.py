@@ -347,6 +347,10 @@ def main():
         err = np.linalg.norm(u_gpu[idx] - u_ref, axis=1) / np.linalg.norm(u_ref, axis=1)
         line["rel_err_vs_oracle"] = {"u_max": float(err.max()), "u_mean": float(err.mean()),
                                      "queries": int(len(idx))}
+        sizes = q.n[idx]
+        if len(np.unique(sizes)) > 1:  # per reduced size (nested truncations)
+            line["rel_err_vs_oracle"]["u_max_per_n"] = {
+                int(v): float(err[sizes == v].max()) for v in np.unique(sizes)}
         if p_gpu is not None and p_ref is not None:
             perr = np.linalg.norm(p_gpu[idx] - p_ref, axis=1) / np.linalg.norm(p_ref, axis=1)
             line["rel_err_vs_oracle"]["p_max"] = float(perr.max())
@@ -384,7 +388,8 @@ NCU_TRAFFIC = {
 
 def chord_queries(prec, wl, q, tuning):
     """Queries whose Newton iterations from the fourth on were chord steps: mixed path, size
-    buckets on the warp-per-query elimination with at most 80 rows (the library's rule)."""
+    buckets on the warp-per-query elimination (at most 80 rows) or the CTA-per-query one (at
+    most 128 rows), the library's rule."""
     if prec == 0 or os.environ.get("RB_CHORD", "") == "0":
         return np.zeros(len(q.n), bool)
 
@@ -392,13 +397,17 @@ def chord_queries(prec, wl, q, tuning):
         g = 8 if n <= 64 else (16 if n <= 128 else 32)
         return min((n + g - 1) // g * g, wl.n_max)
 
-    tuned = {t["n_bucket"]: t["elimination"] == "warp per query" for t in tuning}
+    names = {"warp per query": 1, "CTA per query, row per thread": 4}
+    tuned = {t["n_bucket"]: names.get(t["elimination"], 2) for t in tuning}
     forced = os.environ.get("RB_ELIMINATION", "")
     out = np.zeros(len(q.n), bool)
     for i, n in enumerate(q.n):
         nb = bucket(int(n))
-        warp = tuned.get(nb, (forced == "1") if forced else nb <= 80)
-        out[i] = warp and nb <= 80
+        k = int(forced) if forced else 0
+        applies = (k == 1 and nb <= 80) or k in (2, 3) or (k == 4 and 32 < nb <= 128)
+        default = k if applies else (1 if nb <= 80 else (4 if nb <= 128 else 2))
+        kind = tuned.get(nb, default)
+        out[i] = (kind == 1 and nb <= 80) or (kind == 4 and nb <= 128)
     return out
 
 

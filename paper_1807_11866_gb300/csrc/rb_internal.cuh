@@ -681,6 +681,7 @@ __device__ __forceinline__ bool gepp_aug_cta(float *M, int ld, int n, int *pseq,
         lm[t] = l;
 #pragma unroll
         for (int t2 = t + 1; t2 < 4; ++t2) set4(pc, t2, fmaf(-l, comp4(pp, t2), comp4(pc, t2)));
+        set4(pc, t, l);           // the eliminated entry keeps its multiplier (L, for chord solves)
         M4[tid * ld4 + c0] = pc;  // current chunk for the next pivot step
       }
     }

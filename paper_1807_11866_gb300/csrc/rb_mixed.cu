@@ -892,6 +892,44 @@ struct CtaLuSmem {
   }
 };
 
+// Chord step of the CTA kernel: warp 0 solves with the factors kept in shared memory (forward
+// substitution in pivot order, back substitution on U; chord_solve_warp with ceil(n / 32) row
+// slots), the solution goes to xs; returns, uniformly over the CTA, whether a pivot was unusable.
+__device__ __forceinline__ bool chord_solve_cta(const float *J, int ld, int n, const int *pseq,
+                                                int *stp, unsigned *flag, float *xs) {
+  const int lane = threadIdx.x & 31;
+  if ((threadIdx.x >> 5) == 0) {
+    bool bad;
+    if (n <= 64) {
+      float x[2];
+      bad = chord_solve_warp<2>(J, ld, n, pseq, stp, x);
+      if (!bad)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if (lane + 32 * s < n) xs[lane + 32 * s] = x[s];
+    } else if (n <= 96) {
+      float x[3];
+      bad = chord_solve_warp<3>(J, ld, n, pseq, stp, x);
+      if (!bad)
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+          if (lane + 32 * s < n) xs[lane + 32 * s] = x[s];
+    } else {
+      float x[4];
+      bad = chord_solve_warp<4>(J, ld, n, pseq, stp, x);
+      if (!bad)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (lane + 32 * s < n) xs[lane + 32 * s] = x[s];
+    }
+    if (lane == 0) flag[0] = bad ? 1u : 0u;
+  }
+  __syncthreads();
+  const bool bad = flag[0] != 0u;
+  __syncthreads();  // flag and xs are read before the next query reuses them
+  return bad;
+}
+
 __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
   extern __shared__ __align__(16) uint8_t smb[];
   const CtaLuSmem L(p.nb, p.lda);
@@ -912,13 +950,16 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
     const int n = p.nsz ? p.nsz[b] : p.nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
+    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, qi.iters);
     const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
+    float4 *gJ = reinterpret_cast<float4 *>(p.Jaug + (size_t)b * p.nb * ld);
+    const int n4 = n * ld / 4;
     {
-      const float4 *src = reinterpret_cast<const float4 *>(p.Jaug + (size_t)b * p.nb * ld);
       float4 *dst = reinterpret_cast<float4 *>(J);
-      const int n4 = n * ld / 4;
 #pragma unroll 4
-      for (int i = tid; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+      for (int i = tid; i < n4; i += blockDim.x) dst[i] = gJ[i];
+      if (chord)
+        for (int i = tid; i < n; i += blockDim.x) pseq[i] = p.Piv[(size_t)b * p.nb + i];
     }
     __syncthreads();
     qi.iters += 1;
@@ -926,9 +967,16 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
     qi.precision_used = RB_PREC_MIXED;
     if (!isfinite(rn)) {
       qi.status = RB_Q_NONFINITE;
-    } else if (gepp_aug_cta(J, ld, n, pseq, keys, lmp, stepv, dinvv, xs)) {
+    } else if (chord ? chord_solve_cta(J, ld, n, pseq, stepv, keys, xs)
+                     : gepp_aug_cta(J, ld, n, pseq, keys, lmp, stepv, dinvv, xs)) {
       qi.status = RB_Q_SINGULAR;
     } else {
+      if (keep) {  // the factors (L in the eliminated places, U) and pivots for the chord steps
+        const float4 *src = reinterpret_cast<const float4 *>(J);
+        for (int i = tid; i < n4; i += blockDim.x) gJ[i] = src[i];
+        for (int i = tid; i < n; i += blockDim.x) p.Piv[(size_t)b * p.nb + i] = pseq[i];
+        if (tid == 0) p.Rn[b].x = 1.0;
+      }
       double dl = 0.0;
       if (tid < n) {
         const double d = (double)xs[tid];
@@ -1833,11 +1881,13 @@ static int elim_kind(const MixedState *M) {
   return epol ? epol : (M->nb <= kWarpLuMaxN ? 1 : (M->nb <= kCtaLuMaxN ? 4 : 2));
 }
 // Chord steps (Jacobian reuse from the second FP64-residual iteration on) for buckets whose
-// elimination keeps its factors (the warp kernel); RB_CHORD=0 turns them off.
+// elimination keeps its factors (the warp and the CTA-per-query kernels); RB_CHORD=0 turns
+// them off.
 static bool bucket_chord(const MixedState *M) {
   const char *e = getenv("RB_CHORD");
   if (e && *e && atoi(e) == 0) return false;
-  return elim_kind(M) == 1 && M->nb <= kWarpLuMaxN;
+  const int k = elim_kind(M);
+  return (k == 1 && M->nb <= kWarpLuMaxN) || (k == 4 && M->nb <= kCtaLuMaxN);
 }
 
 // Newton step of the batch: k_newton_system assembles [J | -R] per query, then one warp

@@ -107,7 +107,7 @@ def test_cta_pair_gemms_solve(rb, n, nq, pairs, monkeypatch):
     assert rel(p, p_ref).max() <= 10 * TOL_MIXED
 
 
-@pytest.mark.parametrize("n", [33, 64, 100, 128])
+@pytest.mark.parametrize("n", [33, 64, 90, 100, 128])
 def test_cta_elimination(rb, n, monkeypatch):
     """The CTA-per-query elimination (one row per thread, ceil(n / 32) warps, one barrier per
     pivot step) forced where it applies: velocity and pressure match the oracle."""
@@ -128,10 +128,15 @@ def test_cta_elimination(rb, n, monkeypatch):
     assert rel(p, p_ref).max() <= 10 * TOL_MIXED
 
 
-@pytest.mark.parametrize("n", [20, 50, 72])
-def test_chord_steps(rb, n, monkeypatch):
-    """Jacobian reuse from the second FP64-residual iteration on: the converged velocity and
-    pressure are the oracle's with and without it, and it costs at most one extra iteration."""
+@pytest.mark.parametrize("n,elim", [(20, ""), (50, ""), (72, ""), (40, "4"), (90, "4"),
+                                    (120, "4")])
+def test_chord_steps(rb, n, elim, monkeypatch):
+    """Jacobian reuse from the second FP64-residual iteration on, with the factors kept by the
+    warp-per-query elimination or (elim = 4) by the CTA-per-query one, whose chord solve runs
+    with 2, 3 or 4 row slots: the converged velocity and pressure are the oracle's with and
+    without it, and it costs at most one extra iteration."""
+    if elim:
+        monkeypatch.setenv("RB_ELIMINATION", elim)
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n)
     q = synth.make_queries(wl, batch=300, n_max=n)
