@@ -387,28 +387,10 @@ NCU_TRAFFIC = {
 
 
 def chord_queries(prec, wl, q, tuning):
-    """Queries whose Newton iterations from the fourth on were chord steps: mixed path, size
-    buckets on the warp-per-query elimination (at most 80 rows) or the CTA-per-query one (at
-    most 128 rows), the library's rule."""
-    if prec == 0 or os.environ.get("RB_CHORD", "") == "0":
-        return np.zeros(len(q.n), bool)
-
-    def bucket(n):
-        g = 8 if n <= 64 else (16 if n <= 128 else 32)
-        return min((n + g - 1) // g * g, wl.n_max)
-
-    names = {"warp per query": 1, "CTA per query, row per thread": 4}
-    tuned = {t["n_bucket"]: names.get(t["elimination"], 2) for t in tuning}
-    forced = os.environ.get("RB_ELIMINATION", "")
-    out = np.zeros(len(q.n), bool)
-    for i, n in enumerate(q.n):
-        nb = bucket(int(n))
-        k = int(forced) if forced else 0
-        applies = (k == 1 and nb <= 80) or k in (2, 3) or (k == 4 and 32 < nb <= 128)
-        default = k if applies else (1 if nb <= 80 else (4 if nb <= 128 else 2))
-        kind = tuned.get(nb, default)
-        out[i] = (kind == 1 and nb <= 80) or (kind == 4 and nb <= 128)
-    return out
+    """Queries whose Newton iterations from the fourth on were chord steps: every query of the
+    mixed path (each elimination kernel keeps its factors), unless RB_CHORD=0."""
+    on = prec != 0 and os.environ.get("RB_CHORD", "") != "0"
+    return np.full(len(q.n), on, bool)
 
 
 def kernel_rooflines(prec, wl, q, info, kprof, steps, chord):

@@ -1055,10 +1055,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
     const int n = p.nsz ? p.nsz[b] : nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
+    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, qi.iters);
     const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
     float *M = p.Jaug + (size_t)b * nb * lda;
     bool sing = !isfinite(rn);
-    for (int k0 = 0; k0 < n && !sing; k0 += kPB) {
+    if (chord && !sing) {
+      // forward substitution with the kept factors, panel by panel as they were made: the
+      // panel's row interchanges on b, L11 (unit lower) by warp 0, then b -= L21 b_panel with a
+      // thread per row below
+      for (int i = tid; i < n; i += blockDim.x) xs[i] = M[(size_t)i * lda + n];
+      __syncthreads();
+      for (int k0 = 0; k0 < n; k0 += kPB) {
+        const int kb = min(kPB, n - k0);
+        if (tid == 0)
+          for (int j = 0; j < kb; ++j) {
+            const int pr = p.Piv[(size_t)b * nb + k0 + j];
+            if (pr != k0 + j) {
+              const float t = xs[k0 + j];
+              xs[k0 + j] = xs[pr];
+              xs[pr] = t;
+            }
+          }
+        __syncthreads();
+        if (w == 0) {
+          const bool own = lane < kb;
+          float mrow[kPB];
+#pragma unroll
+          for (int jj = 0; jj < kPB; ++jj)
+            mrow[jj] = (own && jj < lane) ? M[(size_t)(k0 + lane) * lda + k0 + jj] : 0.f;
+          float y = own ? xs[k0 + lane] : 0.f;
+#pragma unroll
+          for (int jj = 0; jj < kPB; ++jj) {
+            if (jj >= kb) break;
+            const float xj = __shfl_sync(0xffffffffu, y, jj);
+            if (own && lane > jj) y = fmaf(-mrow[jj], xj, y);
+          }
+          if (own) xs[k0 + lane] = y;
+        }
+        __syncthreads();
+        for (int r = k0 + kb + tid; r < n; r += blockDim.x) {
+          const float *row = M + (size_t)r * lda + k0;
+          float s = xs[r];
+          for (int j = 0; j < kb; ++j) s = fmaf(-row[j], xs[k0 + j], s);
+          xs[r] = s;
+        }
+        __syncthreads();
+      }
+    }
+    for (int k0 = 0; k0 < n && !sing && !chord; k0 += kPB) {
       const int kb = min(kPB, n - k0), rows = n - k0;
       // (a) load and factor the panel: rows k0 .. n-1, columns k0 .. k0+kb-1
       for (int e = tid; e < rows * kPB; e += blockDim.x) {
@@ -1101,11 +1145,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
         __syncthreads();
       }
       if (sing) break;
-      // U11 (the panel's top rows) back to the matrix for the back substitution
-      for (int e = tid; e < kb * kb; e += blockDim.x) {
+      // U11 (the panel's top rows, L11 in their strict lower part) back to the matrix for the
+      // back substitution; when the factors are kept, L21 and the panel's pivots as well
+      const int kept_rows = keep ? rows : kb;
+      for (int e = tid; e < kept_rows * kb; e += blockDim.x) {
         const int r = e / kb, c = e - r * kb;
         M[(size_t)(k0 + r) * lda + k0 + c] = P[r * kPLd + c];
       }
+      if (keep && tid < kb) p.Piv[(size_t)b * nb + k0 + tid] = k0 + perm[tid];
       // (b) row interchanges on the columns right of the panel, then (c) U12 = L11^-1 A12;
       // one thread per column
       const int c_lo = k0 + kb;
@@ -1179,9 +1226,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
     } else if (sing) {
       qi.status = RB_Q_SINGULAR;
     } else {
+      if (keep && tid == 0) p.Rn[b].x = 1.0;  // factors and pivots kept for the chord steps
       // back substitution, blocks of 32 rows from the bottom: warp 0 solves the diagonal block,
-      // then every thread updates the right-hand side of one row above it
-      for (int i = tid; i < n; i += blockDim.x) xs[i] = M[(size_t)i * lda + n];
+      // then every thread updates the right-hand side of one row above it (a chord step has
+      // its forward-substituted right-hand side in xs already)
+      if (!chord)
+        for (int i = tid; i < n; i += blockDim.x) xs[i] = M[(size_t)i * lda + n];
       __syncthreads();
       for (int i1 = n; i1 > 0; i1 -= 32) {
         const int i0 = max(0, i1 - 32);
@@ -1880,14 +1930,14 @@ static int elim_kind(const MixedState *M) {
   const int epol = elim_policy(M->nb);
   return epol ? epol : (M->nb <= kWarpLuMaxN ? 1 : (M->nb <= kCtaLuMaxN ? 4 : 2));
 }
-// Chord steps (Jacobian reuse from the second FP64-residual iteration on) for buckets whose
-// elimination keeps its factors (the warp and the CTA-per-query kernels); RB_CHORD=0 turns
-// them off.
+// Chord steps (Jacobian reuse from the second FP64-residual iteration on): every elimination
+// kernel keeps its factors and pivots when asked (warp, CTA per query, blocked); RB_CHORD=0
+// turns them off.
 static bool bucket_chord(const MixedState *M) {
   const char *e = getenv("RB_CHORD");
   if (e && *e && atoi(e) == 0) return false;
   const int k = elim_kind(M);
-  return (k == 1 && M->nb <= kWarpLuMaxN) || (k == 4 && M->nb <= kCtaLuMaxN);
+  return (k == 1 && M->nb <= kWarpLuMaxN) || (k == 4 && M->nb <= kCtaLuMaxN) || k == 2 || k == 3;
 }
 
 // Newton step of the batch: k_newton_system assembles [J | -R] per query, then one warp

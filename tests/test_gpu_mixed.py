@@ -129,12 +129,13 @@ def test_cta_elimination(rb, n, monkeypatch):
 
 
 @pytest.mark.parametrize("n,elim", [(20, ""), (50, ""), (72, ""), (40, "4"), (90, "4"),
-                                    (120, "4")])
+                                    (120, "4"), (100, "2"), (150, "3")])
 def test_chord_steps(rb, n, elim, monkeypatch):
     """Jacobian reuse from the second FP64-residual iteration on, with the factors kept by the
-    warp-per-query elimination or (elim = 4) by the CTA-per-query one, whose chord solve runs
-    with 2, 3 or 4 row slots: the converged velocity and pressure are the oracle's with and
-    without it, and it costs at most one extra iteration."""
+    warp-per-query elimination, by the CTA-per-query one (elim = 4; chord solve with 2, 3 or 4
+    row slots) or by the blocked one (elim = 2, 3: 32- and 16-column panels, the forward
+    substitution panel by panel with each panel's interchanges): the converged velocity and
+    pressure are the oracle's with and without it, and it costs at most one extra iteration."""
     if elim:
         monkeypatch.setenv("RB_ELIMINATION", elim)
     wl = synth.WORKLOADS["sweep_n50"]
