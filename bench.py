@@ -377,11 +377,18 @@ NCU_TRAFFIC = {
         "k_newton_system": 113.9e6,
         "k_lu_mixed": 42.57e6,
     },
-    # one-pass capture of the full-size workload
+    # one-pass captures of the full-size workloads
     "dense_n300": {
-        "k_tc_gemm<sliced>": 1599.45e9,
-        "k_tc_gemm<plain>": 126.8e9,
-        "k_lu_mixed": 25.83e9,
+        "k_tc_gemm<sliced>": 1534.5e9,
+        "k_tc_gemm<plain>": 84.73e9,
+        "k_newton_system": 19.77e9,
+        "k_lu_mixed": 21.28e9,
+    },
+    "uneven_n120": {
+        "k_tc_gemm<sliced>": 171.8e6,
+        "k_tc_gemm<plain>": 56.0e6,
+        "k_newton_system": 133.7e6,
+        "k_lu_mixed": 49.57e6,
     },
 }
 
