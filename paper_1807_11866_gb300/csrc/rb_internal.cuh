@@ -103,6 +103,17 @@ __device__ __forceinline__ void theta_eval(const DevOps &o, double alpha_deg, do
   theta_eval_strided(o, alpha_deg, re, th, threadIdx.x, blockDim.x);
 }
 
+// Asynchronous 16-byte copies global -> shared (cp.async, cached in L2 only): every copy of a
+// thread is in flight at once; cp_async_wait_all waits for the calling thread's copies (a warp
+// or block barrier then makes them visible to the others). Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -823,10 +823,10 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
     const int n4 = n * ld / 4;
     {
       float4 *dst = reinterpret_cast<float4 *>(J);
-#pragma unroll 4
-      for (int i = lane; i < n4; i += 32) dst[i] = gJ[i];
+      for (int i = lane; i < n4; i += 32) cp_async16(dst + i, gJ + i);
       if (chord)
         for (int i = lane; i < n; i += 32) pseq[i] = p.Piv[(size_t)b * p.nb + i];
+      cp_async_wait_all();
     }
     __syncwarp();
     qi.iters += 1;
@@ -956,10 +956,10 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
     const int n4 = n * ld / 4;
     {
       float4 *dst = reinterpret_cast<float4 *>(J);
-#pragma unroll 4
-      for (int i = tid; i < n4; i += blockDim.x) dst[i] = gJ[i];
+      for (int i = tid; i < n4; i += blockDim.x) cp_async16(dst + i, gJ + i);
       if (chord)
         for (int i = tid; i < n; i += blockDim.x) pseq[i] = p.Piv[(size_t)b * p.nb + i];
+      cp_async_wait_all();
     }
     __syncthreads();
     qi.iters += 1;
