@@ -61,6 +61,22 @@ def dist_env():
     return rank, world, local
 
 
+def rank_queries(wl, batch, rank, world):
+    """This rank's share of the job: queries [rank * batch, (rank + 1) * batch) of one seeded
+    draw of world * batch queries (independent problems; no exchange between ranks)."""
+    qall = synth.make_queries(wl, batch=batch * world)
+    sl = slice(rank * batch, (rank + 1) * batch)
+    return synth.QuerySet(qall.mu[sl].copy(), qall.n[sl].copy())
+
+
+def max_over_ranks(value, device):
+    """The largest value over the ranks of the default process group (the job's time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -222,9 +238,7 @@ def main():
 
     batch = args.batch or wl.batch
     ops = synth.make_operators(wl)
-    qall = synth.make_queries(wl, batch=batch * world)
-    sl = slice(rank * batch, (rank + 1) * batch)
-    q = synth.QuerySet(qall.mu[sl].copy(), qall.n[sl].copy())
+    q = rank_queries(wl, batch, rank, world)
     prec = PREC[args.precision]
     ctx = rb.Context(precision=prec, device=local, theta_family=wl.theta_family)
     ctx.load_set(ops)
@@ -274,9 +288,7 @@ def main():
     ctx.rb_profile(False)
     t_dev = sum(step_ms) / 1e3
     if world > 1:
-        t = torch.tensor([t_dev], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(t.item())
+        t_dev = max_over_ranks(t_dev, dev)
     value = batch * world * args.steps / t_dev
 
     info = d_info.cpu().numpy().view(rb.INFO_DTYPE).reshape(batch)
