@@ -160,6 +160,22 @@ const char *rb_last_error(rb_ctx *ctx);
  * RB_ERR_OOM if the layouts do not fit in the memory budget. */
 int rb_load_operators(rb_ctx *ctx, const rb_operators *ops);
 
+/* ---- operator files (the output of the offline stage, Sec. 3.5-3.6) ---------------------
+ * A versioned binary file: a 64-byte header (magic "RBOPS\0\0\0", u32 version 1, u32 header
+ * size 64, i32 n_max, m, q_a, q_c, q_f, q_b, dtype_c, u32 flags with bit 0 set when pressure
+ * operators are present, u64 payload bytes, u64 checksum) and the arrays of rb_operators in
+ * field order (A, C, f, then B, As, Cs, fs when present), each C-contiguous in the layout
+ * rb_operators documents, C and Cs in their storage type; all little-endian. The checksum is
+ * FNV-1a (64-bit) over the payload taken as 8-byte words, a last partial word zero-padded.
+ *
+ * rb_save_operators writes ops (host arrays, not modified) to path; context-free, errors go
+ * to rb_last_error(NULL): RB_ERR_ARG on bad sizes, missing arrays or a failed write.
+ * rb_load_operator_file reads path, checks magic, version, sizes, file length and checksum
+ * (RB_ERR_ARG naming the failed check; nothing is loaded then) and loads the operators as
+ * rb_load_operators does. */
+int rb_save_operators(const rb_operators *ops, const char *path);
+int rb_load_operator_file(rb_ctx *ctx, const char *path);
+
 /* Solve n_queries queries from host buffers (synchronous).
  *   mu     [n_queries][2] (alpha_deg, Re)
  *   n      [n_queries] reduced sizes 1..n_max, or NULL for n_max

@@ -28,7 +28,8 @@ EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_
            "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
            "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
            "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots", "rb_tuning",
-           "rb_load_pressure_modes", "rb_reconstruct_pressure", "rb_reconstruct_pressure_device"]
+           "rb_load_pressure_modes", "rb_reconstruct_pressure", "rb_reconstruct_pressure_device",
+           "rb_save_operators", "rb_load_operator_file"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>",
               "k_newton_system", "k_prep", "k_reconstruct"]
@@ -84,6 +85,8 @@ def library():
         L.rb_solve_device.argtypes = [P, P, I, P, P, P, P, P]
         L.rb_eval.argtypes = [P, P, I, I, P, I, P, P]
         L.rb_load_pressure_modes.argtypes = [P, P, I]
+        L.rb_save_operators.argtypes = [P, ctypes.c_char_p]
+        L.rb_load_operator_file.argtypes = [P, ctypes.c_char_p]
         L.rb_reconstruct_pressure.argtypes = [P, P, I, P, P]
         L.rb_reconstruct_pressure_device.argtypes = [P, P, I, P, P, P]
         L.rb_gepp_solve.argtypes = [P, I, I, P, P, P, P]
@@ -131,6 +134,39 @@ def rb_gepp_solve_static(n, batch, d_M, d_rhs, d_x, d_status, stream=None):
 def rb_last_error_global() -> str:
     """Last error of a context-free call on this thread."""
     return library().rb_last_error(None).decode()
+
+
+def _operators(A, C, f, B=None, As=None, Cs=None, fs=None):
+    """rb_operators over host arrays (kept alive by the returned list)."""
+    A, f = _f64(A), _f64(f)
+    C = np.ascontiguousarray(C)
+    dt = RB_F32 if C.dtype == np.float32 else RB_F64
+    if dt == RB_F64:
+        C = _f64(C)
+    q_a, n, _ = A.shape
+    ops = rb_operators(n_max=n, q_a=q_a, q_c=C.shape[0], q_f=f.shape[0], dtype_c=dt,
+                       A=_ptr(A), C=_ptr(C), f=_ptr(f))
+    keep = [A, C, f]
+    if B is not None:
+        B, As, fs = _f64(B), _f64(As), _f64(fs)
+        Cs = np.ascontiguousarray(Cs, dtype=C.dtype)
+        ops.m, ops.q_b = B.shape[1], B.shape[0]
+        ops.B, ops.As, ops.Cs, ops.fs = _ptr(B), _ptr(As), _ptr(Cs), _ptr(fs)
+        keep += [B, As, Cs, fs]
+    return ops, keep
+
+
+def rb_save_operators(path, A, C, f, B=None, As=None, Cs=None, fs=None):
+    """Write an operator file (host arrays as for rb_load_operators)."""
+    ops, keep = _operators(A, C, f, B, As, Cs, fs)
+    rc = library().rb_save_operators(ctypes.byref(ops), os.fsencode(path))
+    if rc != RB_OK:
+        raise RbError(rc, f"rb_save_operators: {rb_last_error_global()}")
+
+
+def save_set(path, ops):
+    """Write a synth.OperatorSet (or any object with the same fields) to an operator file."""
+    rb_save_operators(path, ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs)
 
 
 def rb_config_default() -> rb_config:
@@ -198,25 +234,22 @@ class Context:
 
     # --- operators ----------------------------------------------------------------------
     def rb_load_operators(self, A, C, f, B=None, As=None, Cs=None, fs=None):
-        A, f = _f64(A), _f64(f)
-        C = np.ascontiguousarray(C)
-        dt = RB_F32 if C.dtype == np.float32 else RB_F64
-        if dt == RB_F64:
-            C = _f64(C)
-        q_a, n, _ = A.shape
-        ops = rb_operators(n_max=n, q_a=q_a, q_c=C.shape[0], q_f=f.shape[0], dtype_c=dt,
-                           A=_ptr(A), C=_ptr(C), f=_ptr(f))
-        keep = [A, C, f]
-        if B is not None:
-            B, As, fs = _f64(B), _f64(As), _f64(fs)
-            Cs = np.ascontiguousarray(Cs, dtype=C.dtype)
-            ops.m, ops.q_b = B.shape[1], B.shape[0]
-            ops.B, ops.As, ops.Cs, ops.fs = _ptr(B), _ptr(As), _ptr(Cs), _ptr(fs)
-            keep += [B, As, Cs, fs]
+        ops, keep = _operators(A, C, f, B, As, Cs, fs)
         self._check(library().rb_load_operators(self.h, ctypes.byref(ops)), "rb_load_operators")
-        self.n_max, self.m = n, (ops.m if B is not None else 0)
+        self.n_max, self.m = ops.n_max, (ops.m if B is not None else 0)
         self.m_r = 0
         self.q = (ops.q_a, ops.q_c, ops.q_f, ops.q_b)
+
+    def rb_load_operator_file(self, path):
+        self._check(library().rb_load_operator_file(self.h, os.fsencode(path)),
+                    "rb_load_operator_file")
+        with open(path, "rb") as fh:  # sizes for the output buffers, from the file's header
+            h = np.frombuffer(fh.read(64), dtype="<i4")
+        n, m, q_a, q_c, q_f, q_b = (int(v) for v in h[4:10])
+        pres = int(h[11]) & 1
+        self.n_max, self.m = n, (m if pres else 0)
+        self.m_r = 0
+        self.q = (q_a, q_c, q_f, q_b if pres else 0)
 
     def rb_load_pressure_modes(self, P_hat):
         """P_hat [m_r][n_max]: column j = pressure data of velocity basis function j."""
