@@ -10,9 +10,11 @@
 //      exact digit products, contracted in double-float -> FP64.
 //   4. k_newton_system: [J | -R] with J = fl32(A(mu)) + J^c and R = A(mu) u (double-float)
 //      + C_mu(u, u) - f(mu); residual norms.
-//   5. k_lu_mixed_warp (warp per query, n <= 80) or k_lu_blocked (CTA per query, blocked
-//      right-looking elimination): FP32 GEPP on [J | -R]; u += delta in FP64; stopping rule
-//      (Sec. 6) on the FP64 norms.
+//   5. k_lu_mixed_warp (warp per query, n <= 80), k_lu_cta (CTA per query, row per thread,
+//      n <= 128) or k_lu_blocked (CTA per query, blocked right-looking elimination), as the
+//      autotuner picks: FP32 GEPP on [J | -R]; u += delta in FP64; stopping rule (Sec. 6) on the
+//      FP64 norms. Iteration 2 keeps its factors; from iteration 3 on (chord steps) steps 1-2
+//      skip the Jacobian, step 4 assembles only -R and step 5 solves with the kept factors.
 // The Jacobian is inexact (BF16 convection part, FP32 elimination); the residual and the test
 // are FP64-accurate, so the iteration converges to the FP64 solution at the linear rate
 // ||J~^-1 (J~ - J)||. After the last iteration the pressure right-hand side
