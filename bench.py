@@ -528,7 +528,9 @@ def run_serve(args, wl, rank, world, local):
                 "server_solves_per_s": sps, "p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99,
                 "ok": int(sum(1 for s in status if s == 0))}
 
-    point(None, min(256, args.serve_burst), 1)  # warm-up: layouts, slot tables, first graphs
+    # warm-up: one burst of the measured size (layouts, slot tables, each size bucket's scratch
+    # grown to its working size), as a server in steady state has seen
+    point(None, args.serve_burst, 1)
     clocks = ClockSampler(local)
     clocks.start()
     ctx.rb_profile(True)  # counts the server's launches (events on its stream, read after stop)

@@ -91,6 +91,7 @@ struct MixedState {
   std::map<int, MixedState *> buckets;  // nb < n_max
   // gather scratch of a bucketed batch (query order sorted by bucket)
   int gcap = 0;
+  int serve_cap = 0;  // root only: slots of the running server (0: not serving)
   int *perm = nullptr, *n_g = nullptr;
   double *mu_g = nullptr, *theta_g = nullptr, *u_g = nullptr, *p_g = nullptr;
   rb_query_info *info_g = nullptr;
@@ -2610,6 +2611,9 @@ int mixed_prepare(rb_ctx *ctx, int capacity, cudaStream_t st) {
   if (rc != RB_OK) return rc;
   if ((rc = mixed_layouts(ctx, ctx->mixed, st)) != RB_OK) return rc;
   if ((rc = mixed_batch_scratch(ctx, ctx->mixed, capacity)) != RB_OK) return rc;
+  // the server's gather buffers at full capacity, so that no step reallocates them
+  ctx->mixed->serve_cap = capacity;
+  if ((rc = gather_scratch(ctx, capacity, false)) != RB_OK) return rc;
   return own_info(ctx, 1) ? RB_OK : set_error(ctx, RB_ERR_OOM, "info scratch");
 }
 
@@ -2662,7 +2666,14 @@ int mixed_serve_step(rb_ctx *ctx, const double *d_mu, const int *d_n, double *d_
   for (auto &kv : merged) {
     MixedState *M = kv.first == nm ? R : bucket(ctx, kv.first);
     if ((rc = mixed_layouts(ctx, M, st)) != RB_OK) return rc;
-    if ((rc = mixed_batch_scratch(ctx, M, (int)kv.second.size())) != RB_OK) return rc;
+    // a bucket's batch scratch is sized for all of the server's slots when it first has to
+    // grow, so that the changing group sizes of a busy server do not reallocate it again (each
+    // reallocation synchronises the device); where that does not fit, exactly what is needed
+    const int cnt = (int)kv.second.size();
+    const int want = cnt <= M->bcap ? cnt : std::max(cnt, R->serve_cap);
+    rc = mixed_batch_scratch(ctx, M, want);
+    if (rc == RB_ERR_OOM && want > cnt) rc = mixed_batch_scratch(ctx, M, cnt);
+    if (rc != RB_OK) return rc;
     Group g{M, (int)perm.size(), (int)kv.second.size(), false, false};
     for (int i : kv.second) {
       perm.push_back(slots[i]);
