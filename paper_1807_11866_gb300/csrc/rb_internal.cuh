@@ -59,44 +59,6 @@ __device__ __forceinline__ void theta_eval_strided(const DevOps &o, double alpha
   }
 }
 
-// theta row of one query by one warp (all 32 lanes call it): every distinct function value
-// (term q < the largest term count) is evaluated once, by lane q % 32, and shuffled to the
-// entries that use it; the values are those of theta_eval_strided, bit for bit.
-__device__ __forceinline__ void theta_eval_warp(const DevOps &o, double alpha_deg, double re,
-                                                double *th, int lane) {
-  const double a = alpha_deg * 0.017453292519943295769;  // pi / 180
-  const int qmax = max(max(o.q_a, o.q_c), max(o.q_f, o.q_b));
-  auto fval = [&](int q) -> double {
-    if (o.theta_family == RB_THETA_POLY) {
-      double v = 1.0;
-      for (int k = 0; k < q; ++k) v *= a;
-      return v;
-    }
-    return trig_q(q, a);
-  };
-  const double v0 = lane < qmax ? fval(lane) : 0.0;
-  const double v1 = lane + 32 < qmax ? fval(lane + 32) : 0.0;
-  const double inv_re = 1.0 / re;
-  for (int base = 0; base < o.n_theta; base += 32) {
-    const int i = base + lane;
-    int q = i;
-    double scale = 1.0;
-    if (q < o.q_a) {
-      scale = inv_re;
-    } else {
-      q -= o.q_a;
-      if (q >= o.q_c) {
-        q -= o.q_c;
-        if (q >= o.q_f) q -= o.q_f;
-      }
-    }
-    if (i >= o.n_theta) q = 0;
-    const double x0 = __shfl_sync(0xffffffffu, v0, q & 31);
-    const double x1 = __shfl_sync(0xffffffffu, v1, q & 31);
-    if (i < o.n_theta) th[i] = (q < 32 ? x0 : x1) * scale;
-  }
-}
-
 // theta row of one query, all threads of the block
 __device__ __forceinline__ void theta_eval(const DevOps &o, double alpha_deg, double re,
                                            double *th) {

@@ -503,31 +503,77 @@ __device__ __forceinline__ bool prepares(const rb_query_info &q, int max_iter, i
 }
 
 // theta and f(mu) of the starting queries, one warp per query.
-__global__ void k_prep_theta(PrepParams p) {
+// A block takes 8 queries at a time. The FP64 pipe of this GPU issues about two operations per
+// clock per SM, a cost paid per warp instruction whatever the number of active lanes, so every
+// distinct parameter-function value (term q < the largest term count) of the 8 queries is
+// evaluated by its own thread first (all lanes busy), then each warp assembles one query's theta
+// row from them, f(mu) and max(1, ||f(mu)||); the values are theta_eval_strided's, bit for bit.
+constexpr int kPrepQ = 8;
+__global__ void __launch_bounds__(256) k_prep_theta(PrepParams p) {
   const DevOps &o = p.o;
-  const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < p.nq; b += nw) {
-    if (!prepares(p.info[b], p.max_iter, p.all)) continue;
-    double *th = p.Th + (size_t)b * o.n_theta;
-    if (p.theta_in) {
-      for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta_in[(size_t)b * o.n_theta + i];
-    } else {
-      theta_eval_warp(o, p.mu[2 * b], p.mu[2 * b + 1], th, lane);
+  __shared__ double tv[kPrepQ][RB_Q_MAX];
+  __shared__ double inv_re[kPrepQ];
+  __shared__ int flag[kPrepQ];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int qmax = max(max(o.q_a, o.q_c), max(o.q_f, o.q_b));
+  for (int b0 = blockIdx.x * kPrepQ; b0 < p.nq; b0 += gridDim.x * kPrepQ) {
+    if (threadIdx.x < kPrepQ) {
+      const int b = b0 + threadIdx.x;
+      const bool f = b < p.nq && prepares(p.info[b], p.max_iter, p.all);
+      flag[threadIdx.x] = f;
+      if (f && !p.theta_in) inv_re[threadIdx.x] = 1.0 / p.mu[2 * b + 1];
     }
-    __syncwarp();
-    const double *tf = th + o.q_a + o.q_c;
-    const int n = p.nsz ? p.nsz[b] : p.nb;
-    double ff = 0.0;
-    for (int k = lane; k < p.nb; k += 32) {
-      double s = 0.0;
-      for (int q = 0; q < o.q_f; ++q) s = fma(tf[q], o.f[(size_t)q * o.n_max + k], s);
-      p.Fm[(size_t)b * p.nb + k] = s;
-      if (k < n) ff += s * s;
+    __syncthreads();
+    if (!p.theta_in)
+      for (int t = threadIdx.x; t < kPrepQ * qmax; t += blockDim.x) {
+        const int qi = t / qmax, q = t - qi * qmax;
+        if (!flag[qi]) continue;
+        const double a = p.mu[2 * (b0 + qi)] * 0.017453292519943295769;  // pi / 180
+        double v;
+        if (o.theta_family == RB_THETA_POLY) {
+          v = 1.0;
+          for (int k = 0; k < q; ++k) v *= a;
+        } else {
+          v = trig_q(q, a);
+        }
+        tv[qi][q] = v;
+      }
+    __syncthreads();
+    const int b = b0 + w;
+    if (w < kPrepQ && flag[w]) {
+      double *th = p.Th + (size_t)b * o.n_theta;
+      if (p.theta_in) {
+        for (int i = lane; i < o.n_theta; i += 32) th[i] = p.theta_in[(size_t)b * o.n_theta + i];
+      } else {
+        for (int i = lane; i < o.n_theta; i += 32) {
+          int q = i;
+          double scale = 1.0;
+          if (q < o.q_a) {
+            scale = inv_re[w];
+          } else {
+            q -= o.q_a;
+            if (q >= o.q_c) {
+              q -= o.q_c;
+              if (q >= o.q_f) q -= o.q_f;
+            }
+          }
+          th[i] = tv[w][q] * scale;
+        }
+      }
+      __syncwarp();
+      const double *tf = th + o.q_a + o.q_c;
+      const int n = p.nsz ? p.nsz[b] : p.nb;
+      double ff = 0.0;
+      for (int k = lane; k < p.nb; k += 32) {
+        double s = 0.0;
+        for (int q = 0; q < o.q_f; ++q) s = fma(tf[q], o.f[(size_t)q * o.n_max + k], s);
+        p.Fm[(size_t)b * p.nb + k] = s;
+        if (k < n) ff += s * s;
+      }
+      ff = warp_sum(ff);
+      if (lane == 0) p.Rn[b] = make_double2(0.0, fmax(1.0, sqrt(ff)));  // scale of the residual test
     }
-    ff = warp_sum(ff);
-    if (lane == 0) p.Rn[b] = make_double2(0.0, fmax(1.0, sqrt(ff)));  // scale of the residual test
-    __syncwarp();
+    __syncthreads();  // tv and flag are reused by the next 8 queries
   }
 }
 
@@ -1868,7 +1914,7 @@ static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const dou
   pp.Rn = M->Rn;
   pp.all = all;
   const int mk = prof_begin(ctx, RB_K_PREP, st);
-  k_prep_theta<<<std::max(1, std::min((nq + 7) / 8, ctx->sms * 16)), 256, 0, st>>>(pp);
+  k_prep_theta<<<std::max(1, std::min((nq + kPrepQ - 1) / kPrepQ, ctx->sms * 16)), 256, 0, st>>>(pp);
   auto affine = [&](const float2 *Q2, int qn, int th_off, size_t nn, float2 *out) {
     AffineParams ap{nq, ctx->cfg.max_iter, all, o.n_theta, th_off, qn, nn, info, M->Th, Q2, out};
     dim3 grid((unsigned)std::min<size_t>((nn + 255) / 256, 1024),
