@@ -397,10 +397,10 @@ NCU_TRAFFIC = {
         "k_lu_mixed": 21.28e9,
     },
     "uneven_n120": {
-        "k_tc_gemm<sliced>": 171.8e6,
-        "k_tc_gemm<plain>": 56.0e6,
+        "k_tc_gemm<sliced>": 179.2e6,
+        "k_tc_gemm<plain>": 56.45e6,
         "k_newton_system": 133.7e6,
-        "k_lu_mixed": 49.57e6,
+        "k_lu_mixed": 49.63e6,
     },
 }
 
