@@ -321,3 +321,33 @@ def test_autotuner_choices(rb):
     for u, info in ((u1, i1), (u0, i0)):
         assert np.all(info["status"] == 0)
         assert rel(u, u_ref).max() <= TOL_MIXED
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_maximum_sizes(rb, prec):
+    """The largest sizes the library accepts: n = RB_N_MAX (320) velocity modes, and m =
+    RB_M_MAX (128) pressure modes (the CTA pressure solver), both against the oracle."""
+    import dataclasses
+    P = rb.RB_PREC_FP64 if prec == "fp64" else rb.RB_PREC_MIXED
+    tol = 1e-10 if prec == "fp64" else TOL_MIXED
+    wl = synth.WORKLOADS["sweep_n50"]
+    ops = synth.make_operators(dataclasses.replace(wl, q_b=0, m=0), n_max=320, q_a=1, q_c=1, q_f=1)
+    q = synth.make_queries(wl, batch=3, n_max=320)
+    o = oracle.Oracle.from_set(ops)
+    u_ref, _, _ = o.solve(q.mu, threads=8)
+    with rb.Context(P) as ctx:
+        ctx.load_set(ops)
+        u, _, info = ctx.rb_solve(q.mu)
+    assert np.all(info["status"] == 0)
+    assert rel(u, u_ref).max() <= tol
+    wlm = dataclasses.replace(wl, m=128, q_b=2)
+    ops = synth.make_operators(wlm, n_max=20, q_a=2, q_c=2, q_f=2)
+    q = synth.make_queries(wlm, batch=40, n_max=20)
+    o = oracle.Oracle.from_set(ops)
+    u_ref, p_ref, _ = o.solve(q.mu, threads=8)
+    with rb.Context(P) as ctx:
+        ctx.load_set(ops)
+        u, p, info = ctx.rb_solve(q.mu)
+    assert np.all(info["status"] == 0)
+    assert rel(u, u_ref).max() <= tol
+    assert rel(p, p_ref).max() <= 10 * tol
