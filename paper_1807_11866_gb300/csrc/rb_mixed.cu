@@ -1933,12 +1933,17 @@ static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const dou
 // One Newton step's contraction work for the whole batch: X build + both GEMMs.
 // The contractions one Newton iteration needs: the Jacobian GEMM (jac) and the FP64-accurate
 // residual's sliced GEMM (exact).
+// The Jacobian and sliced GEMMs cover the first nq_jac / nq_exact rows of the batch (all nq by
+// default): the server orders a group's queries by iteration count, so only the rows that need
+// a contraction get one (rows past them may take overhanging tile rows, which their rung never
+// reads).
 static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
-                          const rb_query_info *d_info, bool jac, bool exact, cudaStream_t st) {
+                          const rb_query_info *d_info, bool jac, bool exact, cudaStream_t st,
+                          int nq_jac = -1, int nq_exact = -1) {
   if (!jac && !exact) return RB_OK;
   int rc = launch_build_x(ctx, M, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st, jac ? 1 : 0);
   if (rc != RB_OK) return rc;
-  TcGemmParams g = gemm_params(M, nq);
+  TcGemmParams g = gemm_params(M, nq_jac >= 0 ? nq_jac : nq);
   g.n_tiles = M->Npad / kTcBN;
   g.kb[0] = M->kb0;
   g.kb[1] = 0;
@@ -1956,6 +1961,15 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (Jacobian)");
   }
   if (!exact) return RB_OK;
+  if (nq_exact >= 0) {
+    const TcGemmParams ge = gemm_params(M, nq_exact);
+    g.m_tiles = ge.m_tiles;
+    g.nq = ge.nq;
+  } else {
+    const TcGemmParams ge = gemm_params(M, nq);
+    g.m_tiles = ge.m_tiles;
+    g.nq = ge.nq;
+  }
   g.kb[1] = M->kb1;
   g.n_tiles = M->WR.Npad / kTcBN;
   g.n_pad = M->WR.Npad;
@@ -2691,7 +2705,7 @@ int mixed_serve_step(rb_ctx *ctx, const double *d_mu, const int *d_n, double *d_
   MixedState *R = ctx->mixed;
   const DevOps &o = ctx->ops;
   const int nm = o.n_max, mm = std::max(o.m, 1);
-  struct Group { MixedState *M; int off, cnt; bool jac, exact; };
+  struct Group { MixedState *M; int off, cnt; bool jac, exact; int c1, c2; };
   std::map<int, std::vector<int>> by;
   for (size_t i = 0; i < slots.size(); ++i) {
     const int n = slot_n[i];
@@ -2720,12 +2734,18 @@ int mixed_serve_step(rb_ctx *ctx, const double *d_mu, const int *d_n, double *d_
     rc = mixed_batch_scratch(ctx, M, want);
     if (rc == RB_ERR_OOM && want > cnt) rc = mixed_batch_scratch(ctx, M, cnt);
     if (rc != RB_OK) return rc;
-    Group g{M, (int)perm.size(), (int)kv.second.size(), false, false};
+    // members by iteration count, highest first: the rows that need the sliced residual
+    // (count >= 2) lead, then those that need the Jacobian (count >= 1)
+    std::stable_sort(kv.second.begin(), kv.second.end(),
+                     [&](int x, int y) { return slot_iters[x] > slot_iters[y]; });
+    Group g{M, (int)perm.size(), (int)kv.second.size(), false, false, 0, 0};
     for (int i : kv.second) {
       perm.push_back(slots[i]);
-      g.jac |= slot_iters[i] >= 1;
-      g.exact |= slot_iters[i] >= 2;
+      g.c1 += slot_iters[i] >= 1;
+      g.c2 += slot_iters[i] >= 2;
     }
+    g.jac = g.c1 > 0;
+    g.exact = g.c2 > 0;
     groups.push_back(g);
   }
   const int total = (int)perm.size();
@@ -2744,11 +2764,13 @@ int mixed_serve_step(rb_ctx *ctx, const double *d_mu, const int *d_n, double *d_
                       R->info_g + g.off};
     cudaMemsetAsync(R->dev_words, 0, 4, st);
     if ((rc = launch_prep(ctx, g.M, a.mu, nullptr, g.cnt, a.n, a.info, st, 1)) != RB_OK) return rc;
-    if ((rc = mixed_contract(ctx, g.M, g.cnt, a.n, a.u, a.info, g.jac, g.exact, st)) != RB_OK) return rc;
+    if ((rc = mixed_contract(ctx, g.M, g.cnt, a.n, a.u, a.info, g.jac, g.exact, st, g.c1, g.c2)) != RB_OK)
+      return rc;
     LuParams lp = solve_lu_params(ctx, g.M, a);
     lp.chord = 0;
     if ((rc = launch_lu(ctx, g.M, lp, g.cnt, st)) != RB_OK) return rc;
-    if (pres && g.exact && (rc = mixed_pressure(ctx, g.M, g.cnt, a.n, a.u, a.p, a.info, st)) != RB_OK)
+    // only rows with an FP64-accurate residual (the first c2) can have converged
+    if (pres && g.exact && (rc = mixed_pressure(ctx, g.M, g.c2, a.n, a.u, a.p, a.info, st)) != RB_OK)
       return rc;
   }
   k_scatter<<<std::max(1, std::min((total + 7) / 8, ctx->sms * 8)), 256, 0, st>>>(
