@@ -73,6 +73,23 @@ def test_poly_theta_is_rotation_series(oracle_lib, alpha):
     np.testing.assert_allclose(p, [1.0, 0.0], rtol=0, atol=1e-14)
 
 
+def test_rotation_pin_detects_shifted_powers(oracle_lib):
+    """The rotation pin is sensitive: a θ row with every power shifted by one (φ^(q+1)) or with
+    1/Re left off θᵃ assembles something other than R(φ)/Re."""
+    A, C, f, B, As, Cs, fs = _rotation_series_set(30)
+    o = oracle_lib.Oracle(A, C, f, B, As, Cs, fs, theta_family=2)
+    phi, re = math.radians(20.0), 300.0
+    R = np.array([[math.cos(phi), -math.sin(phi)], [math.sin(phi), math.cos(phi)]])
+    good = o.theta(20.0, re)
+    shifted = good.copy()
+    shifted[:30] = [phi ** (q + 1) / re for q in range(30)]
+    no_re = good.copy()
+    no_re[:30] *= re
+    for t in (shifted, no_re):
+        Am, _ = o.assemble(2, t)
+        assert np.abs(Am - R / re).max() > 1e-4
+
+
 def test_poly_theta_monomials(oracle_lib):
     ops = small_set(n=3, q_a=4, q_c=4, q_f=4)
     o = oracle_lib.Oracle(ops.A, ops.C, ops.f, theta_family=2)
