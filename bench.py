@@ -181,7 +181,9 @@ def run_reference(args, wl, rank, world):
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n_max, "q_a": wl.q_a, "q_c": wl.q_c,
-                   "batch": len(q.mu), "sample_per_step": sample},
+                   "q_f": wl.q_f, "m": wl.m, "batch_per_gpu": len(q.mu), "precision": "fp64",
+                   "l2": "host caches (CPU oracle)", "parallelism": f"replicas x{world}",
+                   "sample_per_step": sample},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
                          "sample": f"{sample} queries of the {wl.name} workload per step"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
