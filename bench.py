@@ -355,7 +355,7 @@ def main():
     if rank == 0 and not args.no_plain and prec != 0:
         line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, args)
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline at N = 1 only
         cb, idx, u_ref, p_ref, inf_ref = cpu_baseline(wl, ops, q, args.cpu_seconds)
         line["cpu_baseline"] = cb
         err = np.linalg.norm(u_gpu[idx] - u_ref, axis=1) / np.linalg.norm(u_ref, axis=1)
