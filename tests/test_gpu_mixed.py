@@ -351,3 +351,22 @@ def test_maximum_sizes(rb, prec):
     assert np.all(info["status"] == 0)
     assert rel(u, u_ref).max() <= tol
     assert rel(p, p_ref).max() <= 10 * tol
+
+
+@pytest.mark.timeout(900)
+def test_dense_n300_full_batch_sampled(rb):
+    """The n = 300 dense regime at its full size and in bench.py's configuration (16384 queries,
+    Q = 24, C BF16-exact, one mixed-precision solve): every query converges, and two sampled
+    queries (first and last of the batch) match the oracle."""
+    wl = synth.WORKLOADS["dense_n300"]
+    ops = synth.make_operators(wl)
+    q = synth.make_queries(wl)
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, _, info = ctx.rb_solve(q.mu)
+    assert np.all(info["status"] == 0), np.unique(info["status"], return_counts=True)
+    idx = np.array([0, len(q.mu) - 1])
+    o = oracle.Oracle.from_set(ops)
+    u_ref, _, inf_ref = o.solve(q.mu[idx], threads=2)
+    assert np.all(inf_ref["status"] == 0)
+    assert rel(u[idx], u_ref).max() <= TOL_MIXED
