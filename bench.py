@@ -136,18 +136,6 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def algorithmic_flops(wl, n, q_c, q_a, iters, iters_fp64r=None):
-    """Per-query algorithmic FLOPs of the solve: per Newton iteration the Jacobian contraction
-    2 (Q_c n^3 + Q_a n^2), the LU 2 n^3 / 3 and the triangular solves 2 n^2; the FP64-accurate
-    residual adds 2 (Q_c n^3 + (Q_a + 1) n^2) where it is evaluated separately."""
-    n = n.astype(np.float64)
-    per_it = 2 * (q_c * n ** 3 + q_a * n ** 2) + 2 * n ** 3 / 3 + 2 * n ** 2
-    total = per_it * iters
-    if iters_fp64r is not None:
-        total = total + 2 * (q_c * n ** 3 + (q_a + 1) * n ** 2) * iters_fp64r
-    return float(total.sum())
-
-
 def run_reference(args, wl, rank, world):
     """The FP64 CPU oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
