@@ -54,3 +54,36 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(rb.rb_query_info) == 32
     assert ctypes.sizeof(rb.rb_operators) == 7 * 4 + 4 + 7 * 8
     assert rb.INFO_DTYPE.itemsize == 32
+
+
+def test_struct_layouts_match_c_compiler(tmp_path):
+    """Every field offset of the ctypes mirrors equals the C compiler's for include/rb.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1807_11866_gb300 import rb
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"rb_config": rb.rb_config, "rb_operators": rb.rb_operators,
+               "rb_query_info": rb.rb_query_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            got[(name, key)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
