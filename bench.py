@@ -51,6 +51,9 @@ def parse():
                          "and p50/p99 submit-to-completion latency under Poisson arrivals")
     ap.add_argument("--serve-burst", type=int, default=2048)
     ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--large", action=argparse.BooleanOptionalAction, default=True,
+                    help="also measure the largest configuration (dense_n300: n = 300, Q = 24, "
+                         "16384 queries) in the same run and report it as its own block")
     return ap.parse_args()
 
 
@@ -180,11 +183,21 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(wl, ops, q, seconds):
-    """Oracle (as is) on the host cores on a bounded sample; also returns its results."""
+def cpu_baseline(wl, ops, q, seconds, idx=None):
+    """Oracle (as is) on the host cores on a bounded sample; also returns its results. With
+    `idx` the sample is those queries; otherwise evenly spaced queries, as many as about
+    `seconds` of oracle time allows."""
     import oracle
     o = oracle.Oracle.from_set(ops)
     threads = oracle.max_threads()
+    if idx is not None:
+        t0 = time.perf_counter()
+        u, p, info = o.solve(q.mu[idx], q.n[idx], threads=threads)
+        dt = time.perf_counter() - t0
+        return {"value": len(idx) / dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                "sample": f"{len(idx)} queries of the {len(q.mu)}-query {wl.name} batch (the 4 "
+                          f"corners of the parameter box and queries stratified over alpha and "
+                          f"log Re; {dt:.1f} s on {threads} threads)"}, idx, u, p, info
     probe = max(threads, 8)
     idx = np.linspace(0, len(q.mu) - 1, probe).astype(int)
     t0 = time.perf_counter()
@@ -226,9 +239,42 @@ def main():
         torch.distributed.barrier()
     rb.library()
 
-    batch = args.batch or wl.batch
+    line = measure(args, wl, args.batch or wl.batch, args.steps, args.warmup, rank, world, local,
+                   dev, recon=not args.no_recon, cpu_seconds=args.cpu_seconds)
+    if args.large and wl.name != LARGEST and world == 1:
+        # the largest configuration of the metric's range, measured in the same run (its own
+        # steps and warm-up; the operators of the first workload are freed by then)
+        big = synth.WORKLOADS[LARGEST]
+        sub = measure(args, big, big.batch, LARGE_STEPS, LARGE_WARMUP, 0, 1, local, dev,
+                      recon=False, cpu_seconds=args.cpu_seconds, parity_sample=True)
+        keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config",
+                "latency_ms", "iters", "status_ok", "e2e", "gpu_launches", "kernels", "clocks",
+                "roofline", "rooflines", "autotune", "plain_fp64", "speedup_vs_plain_fp64",
+                "cpu_baseline", "rel_err_vs_oracle")
+        line[LARGEST] = {k: sub[k] for k in keep if k in sub}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+LARGEST = "dense_n300"        # the largest configuration of the metric's range (n = 300)
+LARGE_STEPS, LARGE_WARMUP = 3, 3
+
+
+def measure(args, wl, batch, steps, warmup, rank, world, local, dev, recon, cpu_seconds,
+            parity_sample=False):
+    """One workload: `warmup` untimed and `steps` timed solves of the batch resident in HBM,
+    L2 flushed between steps; a kernel-by-kernel pass for the per-kernel breakdown and the
+    roofline; the same solves end to end through rb_solve with pinned host buffers; the plain
+    FP64 GPU path and the oracle on the host cores (rank 0, N = 1). Returns the JSON dict."""
+    import torch
+    from paper_1807_11866_gb300 import rb
+
     ops = synth.make_operators(wl)
     q = rank_queries(wl, batch, rank, world)
+    if parity_sample:  # the corners of the parameter box take the last four queries
+        q.mu[-4:] = synth.corner_queries(wl)
     prec = PREC[args.precision]
     ctx = rb.Context(precision=prec, device=local, theta_family=wl.theta_family)
     ctx.load_set(ops)
@@ -245,19 +291,19 @@ def main():
         ctx.rb_solve_device(d_mu, batch, d_n, d_u, d_p, d_info, s.cuda_stream)
 
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()  # write > L2 between timed steps
             starts[i].record(stream)
             step(stream)
@@ -270,7 +316,7 @@ def main():
     # launching stream (these launch kernel by kernel instead of replaying the solve graph)
     ctx.rb_profile(True)
     with torch.cuda.stream(stream):
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             step(stream)
     torch.cuda.synchronize()
@@ -279,14 +325,14 @@ def main():
     t_dev = sum(step_ms) / 1e3
     if world > 1:
         t_dev = max_over_ranks(t_dev, dev)
-    value = batch * world * args.steps / t_dev
+    value = batch * world * steps / t_dev
 
     info = d_info.cpu().numpy().view(rb.INFO_DTYPE).reshape(batch)
     u_gpu = d_u.cpu().numpy()
     p_gpu = d_p.cpu().numpy() if d_p is not None else None
     # kernels of one step: those the profiled pass counted plus the graph's loop-condition kernel
     # (one per Newton iteration of the batch)
-    launches_total = sum(v[1] for v in kprof.values()) + args.steps * int(info["iters"].max())
+    launches_total = sum(v[1] for v in kprof.values()) + steps * int(info["iters"].max())
 
     # end-to-end through the public host-buffer API, pinned host memory
     h_mu = torch.from_numpy(q.mu).pin_memory()
@@ -296,7 +342,7 @@ def main():
     h_info = torch.empty((batch, 4), dtype=torch.float64).pin_memory()
     L = rb.library()
     e2e_t = []
-    for i in range(args.warmup + args.steps):
+    for i in range(warmup + steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -304,7 +350,7 @@ def main():
                         h_p.data_ptr() if h_p is not None else None, h_info.data_ptr())
         t1 = time.perf_counter()
         assert rc == 0, ctx.last_error()
-        if i >= args.warmup:
+        if i >= warmup:
             e2e_t.append(t1 - t0)
     e2e_val = batch * world * len(e2e_t) / sum(e2e_t)
     h2d = q.mu.nbytes + q.n.nbytes
@@ -312,16 +358,17 @@ def main():
 
     # roofline of the dominant kernel, measured live with events on the launching stream
     chord = chord_queries(prec, wl, q, ctx.rb_tuning())
-    roof, roofs, kernels = kernel_rooflines(prec, wl, q, info, kprof, args.steps, chord)
+    roof, roofs, kernels = kernel_rooflines(prec, wl, q, info, kprof, steps, chord)
 
     line = {
         "metric": "reduced Newton solves/s", "value": value, "unit": "solves/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1e3 * t_dev / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16+f32+f64" if prec == 1 else "f64",
         "data": "synthetic",
         "config": {"workload": wl.name, "n": wl.n_max, "q_a": wl.q_a, "q_c": wl.q_c,
-                   "q_f": wl.q_f, "m": m, "batch_per_gpu": batch, "precision": args.precision,
+                   "q_f": wl.q_f, "m": m, "c_storage": wl.c_dtype, "batch_per_gpu": batch,
+                   "precision": args.precision,
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
@@ -337,18 +384,29 @@ def main():
     line["roofline"] = roof
     line["rooflines"] = roofs
     line["autotune"] = ctx.rb_tuning()
-    if rank == 0 and m and not args.no_recon:
+    if rank == 0 and m and recon:
         line["pressure_reconstruction"] = pressure_reconstruction(
-            rb, ctx, wl, batch, d_u, d_n, p_gpu, kprof, stream, flush, args)
+            rb, ctx, wl, batch, d_u, d_n, p_gpu, kprof, stream, flush, args, steps, warmup)
+    ctx.close()
+    del d_mu, d_n, d_u, d_p, d_info
     if rank == 0 and not args.no_plain and prec != 0:
-        line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, args)
+        line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, steps)
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
+    del flush
+    torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline at N = 1 only
-        cb, idx, u_ref, p_ref, inf_ref = cpu_baseline(wl, ops, q, args.cpu_seconds)
+        if parity_sample:  # 4 corners and 12 queries stratified over the parameter box
+            idx = np.concatenate([synth.stratified_indices(wl, q.mu[:-4], cells=(3, 4)),
+                                  np.arange(batch - 4, batch)])
+            cb, idx, u_ref, p_ref, inf_ref = cpu_baseline(wl, ops, q, cpu_seconds, idx=idx)
+        else:
+            cb, idx, u_ref, p_ref, inf_ref = cpu_baseline(wl, ops, q, cpu_seconds)
         line["cpu_baseline"] = cb
         err = np.linalg.norm(u_gpu[idx] - u_ref, axis=1) / np.linalg.norm(u_ref, axis=1)
         line["rel_err_vs_oracle"] = {"u_max": float(err.max()), "u_mean": float(err.mean()),
-                                     "queries": int(len(idx))}
+                                     "queries": int(len(idx)),
+                                     "sample": "corners + stratified over alpha, log Re" if parity_sample
+                                     else "evenly spaced over the batch"}
         sizes = q.n[idx]
         if len(np.unique(sizes)) > 1:  # per reduced size (nested truncations)
             line["rel_err_vs_oracle"]["u_max_per_n"] = {
@@ -356,11 +414,7 @@ def main():
         if p_gpu is not None and p_ref is not None:
             perr = np.linalg.norm(p_gpu[idx] - p_ref, axis=1) / np.linalg.norm(p_ref, axis=1)
             line["rel_err_vs_oracle"]["p_max"] = float(perr.max())
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return line
 
 
 FP64_PEAK_TFLOPS = 1.196  # FP64 FMA throughput measured on GB300 (152 SMs at 2070 MHz)
@@ -404,60 +458,76 @@ def chord_queries(prec, wl, q, tuning):
 
 def kernel_rooflines(prec, wl, q, info, kprof, steps, chord):
     """Roofline of every timed kernel kind, and of the one with the largest device time.
-    Algorithmic work counts only the useful part, per active query-iteration of size n
-    (`chord` queries factor at their first three iterations and reuse the third factorisation
-    from the fourth on, without a Jacobian contraction):
-      fused FP64 Newton: 2 (Q_c n^3 + Q_a n^2) + 2 n^3 / 3 + 2 n^2 FLOP (FP64 ALU);
-      Jacobian GEMM: 3 x 2 Q_c n^3 FLOP of split-BF16 products, iterations with a new Jacobian
-        after the first (tensor);
-      sliced residual GEMM: P 2 Q_c n^3 FLOP of BF16 digit products, P = S (S + 1) / 2, from the
-        third iteration on (tensor);
-      sliced pressure GEMM: P 2 Q_c m n^2 per converged query (tensor);
+
+    `achieved` counts the method's ALGORITHMIC work only (the multiply-adds of the contraction
+    the kernel stands for, per active query-iteration of size n, padding excluded), so `frac`
+    says how close the kernel comes to the time that work alone would take at the peak:
+      fused FP64 Newton: 2 (Q_c n^3 + Q_a n^2) (Jacobian) + 2 Q_c n^3 (residual)
+        + 2 n^3 / 3 + 2 n^2 (LU and solves) FLOP per iteration (FP64 ALU);
+      Jacobian GEMM: 2 Q_c n^3 FLOP per new Jacobian (the iterations after the first, up to the
+        third for queries on chord steps) (tensor);
+      sliced residual GEMM: 2 Q_c n^3 FLOP per FP64-accurate residual (from the third iteration
+        on) (tensor);
+      sliced pressure GEMM: 2 Q_c n^2 m FLOP per query (tensor);
       elimination: 2 n^3 / 3 + 2 n^2 FLOP in FP32 per factorisation, 2 n^2 per chord solve (ALU);
       system assembly: 8 n^2 (A(mu)) + 4 n^2 (J^c, iterations with a new Jacobian after the
         first) bytes read and 4 n (n + 1) bytes written; a chord step reads A(mu) and writes the
         right-hand side, 8 n^2 + 4 n (HBM);
-      per-query preparation: 8 n^2 bytes of A(mu) written, once per query (HBM)."""
+      per-query preparation: 8 n^2 bytes of A(mu) written, once per query (HBM).
+    The tensor kernels ISSUE more products than that: the Jacobian GEMM 3 split-BF16 products
+    (hi hi, hi lo, lo hi) and the sliced GEMMs P = S (S + 1) / 2 digit-pair products for an
+    FP64-accurate result; `issued_tflops` / `issued_frac` report that rate (how busy the tensor
+    pipe is), separately from `frac`."""
     peaks, kind = measured_peaks()
     n = q.n.astype(np.float64)
     it = info["iters"].astype(np.float64)
     full = np.where(chord, np.minimum(it, 3), it)   # iterations that factor a new Jacobian
     chs = it - full                                 # chord steps
     jac = np.maximum(full - 1, 0)                   # Jacobian contractions
+    res = np.maximum(it - 2, 0)                     # FP64-accurate (sliced) residuals
     tot_ms = sum(v[0] for v in kprof.values()) or 1.0
     kernels = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps,
                    "share": v[0] / tot_ms} for k, v in kprof.items() if v[1]}
     p0 = DIGITS * (DIGITS + 1) // 2
     bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     hbm = peaks.get("hbm_gbs")
-    work = {  # kernel -> (bound, algorithmic units per step, peak, unit, peak source)
-        "k_newton_fp64": ("alu", float(np.sum(it * (2 * (wl.q_c * n ** 3 + wl.q_a * n ** 2) + 2 * n ** 3 / 3 + 2 * n ** 2))),
-                          FP64_PEAK_TFLOPS, "TFLOP/s", "measured FP64 FMA throughput (152 SMs, 2070 MHz)"),
-        "k_tc_gemm<plain>": ("tensor", float(np.sum(jac * 3 * 2.0 * wl.q_c * n ** 3)),
-                             bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
-        "k_tc_gemm<sliced>": ("tensor", float(np.sum(np.maximum(it - 2, 0) * 2.0 * n ** 2 * p0 * wl.q_c * n)),
-                              bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
-        "k_tc_gemm<sliced,pressure>": ("tensor", float(np.sum(2.0 * (wl.m or 0) * n * p0 * wl.q_c * n)),
-                                       bf16, "TFLOP/s", f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"),
+    bf16_src = f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"
+    hbm_src = f"HBM copy, {kind} (MEASURED_PEAKS.json)"
+    work = {  # kernel -> (bound, algorithmic units per step, issued / algorithmic, peak, unit, src)
+        "k_newton_fp64": ("alu", float(np.sum(it * (2 * (2 * wl.q_c * n ** 3 + wl.q_a * n ** 2)
+                                                     + 2 * n ** 3 / 3 + 2 * n ** 2))), None,
+                          FP64_PEAK_TFLOPS, "TFLOP/s",
+                          "FP64 FMA throughput of a probe kernel of this project on GB300 (152 SMs, "
+                          "2070 MHz); not a MEASURED_PEAKS.json figure"),
+        "k_tc_gemm<plain>": ("tensor", float(np.sum(jac * 2.0 * wl.q_c * n ** 3)), 3.0,
+                             bf16, "TFLOP/s", bf16_src),
+        "k_tc_gemm<sliced>": ("tensor", float(np.sum(res * 2.0 * wl.q_c * n ** 3)), float(p0),
+                              bf16, "TFLOP/s", bf16_src),
+        "k_tc_gemm<sliced,pressure>": ("tensor", float(np.sum(2.0 * (wl.m or 0) * wl.q_c * n ** 2)),
+                                       float(p0), bf16, "TFLOP/s", bf16_src),
         "k_lu_mixed": ("alu", float(np.sum(full * (2 * n ** 3 / 3 + 2 * n ** 2) + chs * 2 * n ** 2)),
-                       FP32_PEAK_TFLOPS, "TFLOP/s",
+                       None, FP32_PEAK_TFLOPS, "TFLOP/s",
                        "FP32 FMA peak from unit counts and clock (152 x 128 x 2 x 2.07 GHz)"),
         "k_newton_system": ("hbm", float(np.sum(full * (8 * n ** 2 + 4 * n * (n + 1)) + jac * 4 * n ** 2
-                                                + chs * (8 * n ** 2 + 4 * n))),
-                            hbm, "GB/s",
-                            f"HBM copy, {kind} (MEASURED_PEAKS.json)"),
-        "k_prep": ("hbm", float(np.sum(8 * n ** 2)), hbm, "GB/s", f"HBM copy, {kind} (MEASURED_PEAKS.json)"),
+                                                + chs * (8 * n ** 2 + 4 * n))), None,
+                            hbm, "GB/s", hbm_src),
+        "k_prep": ("hbm", float(np.sum(8 * n ** 2)), None, hbm, "GB/s", hbm_src),
     }
     rl = {}
     for k, (ms, launches) in kprof.items():
         if not launches or k not in work:
             continue
-        bound, units, peak, unit, src = work[k]
+        bound, units, issued, peak, unit, src = work[k]
         scale = 1e12 if unit == "TFLOP/s" else 1e9
         ach = steps * units / (ms * 1e-3) / scale
         traffic = NCU_TRAFFIC.get(wl.name, {}).get(k)
         rl[k] = {"bound": bound, "kernel": k, "achieved": ach, "peak": peak, "unit": unit,
-                 "frac": ach / peak, "traffic": traffic, "peak_source": src, "launches": launches}
+                 "frac": ach / peak, "traffic": traffic, "peak_source": src,
+                 "work": "algorithmic", "launches": launches}
+        if issued:
+            rl[k]["issued_tflops"] = ach * issued
+            rl[k]["issued_frac"] = ach * issued / peak
+            rl[k]["issued_per_algorithmic"] = issued
     dom = max(kprof, key=lambda k: kprof[k][0])
     return rl.get(dom), rl, kernels
 
@@ -582,7 +652,8 @@ def combined_pressure_modes(U, Pp, rtol=1e-10):
     return (Pp.T @ V) @ Psi.T, len(keep)
 
 
-def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, flush, args):
+def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, flush, args,
+                            steps, warmup):
     """Pressure reconstruction (Sec. 4.2) against recovery on the same batch: the modes fitted
     from training queries of the same workload (solved, pressure recovered), then p = P_hat u for
     the timed batch's velocities; kernel time by CUDA events, error against recovery."""
@@ -597,7 +668,7 @@ def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, 
     ctx.rb_load_pressure_modes(P_hat)
     d_pr = torch.empty((batch, P_hat.shape[0]), dtype=torch.float64, device=d_u.device)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.warmup + args.steps)]
+          for _ in range(warmup + steps)]
     with torch.cuda.stream(stream):
         for a, b in ev:
             flush.zero_()
@@ -605,11 +676,11 @@ def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, 
             ctx.rb_reconstruct_pressure_device(d_u, batch, d_n, d_pr, stream.cuda_stream)
             b.record(stream)
     torch.cuda.synchronize()
-    t = [a.elapsed_time(b) for a, b in ev[args.warmup:]]
+    t = [a.elapsed_time(b) for a, b in ev[warmup:]]
     p_r = d_pr.cpu().numpy()
     err = np.linalg.norm(p_r - p_rec, axis=1) / np.linalg.norm(p_rec, axis=1)
     rec_ms = sum(kprof.get(k, (0.0, 0))[0] for k in ("k_pressure", "k_tc_gemm<sliced,pressure>"))
-    rec_ms /= args.steps
+    rec_ms /= steps
     return {"ms_per_step": float(np.mean(t)), "recovery_ms_per_step": rec_ms,
             "rel_err_vs_recovery": {"median": float(np.median(err)), "max": float(err.max())},
             "modes": f"m_r = {P_hat.shape[0]}, {r} POD modes (eigenvalues above 1e-10 of the "
@@ -617,7 +688,7 @@ def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, 
                      "basis, second construction of Sec. 4.2)"}
 
 
-def plain_fp64(rb, ops, q, batch, dev, flush, args):
+def plain_fp64(rb, ops, q, batch, dev, flush, steps):
     """The plain FP64 GPU path (one CTA per query, every step in FP64) on the same batch, or on
     its first two waves (2 x 152 queries) when one FP64 query-iteration exceeds 1 GFLOP."""
     import torch
@@ -633,7 +704,7 @@ def plain_fp64(rb, ops, q, batch, dev, flush, args):
     d_u = torch.empty((batch, ctx.n_max), dtype=torch.float64, device=dev)
     d_p = torch.empty((batch, max(ctx.m, 1)), dtype=torch.float64, device=dev) if ctx.m else None
     d_info = torch.empty((batch, 4), dtype=torch.float64, device=dev)
-    steps = max(2, min(args.steps, 3))
+    steps = max(2, min(steps, 3))
     with torch.cuda.stream(stream):
         ctx.rb_solve_device(d_mu, batch, d_n, d_u, d_p, d_info, stream.cuda_stream)
         ev = []

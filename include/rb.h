@@ -253,7 +253,8 @@ int rb_gepp_solve(rb_ctx *ctx, int n, int batch, const double *M, const double *
  * exits; the call makes no cudaMalloc, cudaFree or other allocating call. n outside
  * 1..RB_STATIC_N_MAX or batch < 0 returns RB_ERR_ARG with a message for rb_last_error(NULL).
  * The first call on a device looks up the array's device address with that device current, so
- * make that first call before any stream capture. Every call uses the same array and it keeps
+ * make that first call before any stream capture; the address is looked up again when the
+ * device's context has changed since (after cudaDeviceReset). Every call uses the same array and it keeps
  * the previous call's contents (each system is copied in before use): calls whose GPU work
  * overlaps (other streams or threads) race on it, so the caller must order them. */
 #define RB_STATIC_N_MAX 512

@@ -209,6 +209,21 @@ def reconstruct(P_hat, u, n=None):
     return p
 
 
+def gepp_solve(M, rhs):
+    """Solve M_s x_s = rhs_s for every system s of a batch by the oracle's Gaussian elimination
+    with partial pivoting (first row of largest magnitude). M [batch][n][n], rhs [batch][n].
+    Returns x [batch][n] (0 for a singular system) and status [batch] (0 ok, 2 singular)."""
+    M = np.array(M, dtype=np.float64, copy=True, order="C")
+    x = np.array(rhs, dtype=np.float64, copy=True, order="C")
+    batch, n = x.shape
+    st = np.zeros(batch, np.int32)
+    for s in range(batch):
+        if lib().oracle_gepp_solve(n, _ptr(M[s]), _ptr(x[s])):
+            st[s] = Q_SINGULAR
+            x[s] = 0.0
+    return x, st
+
+
 def _info_arrays(info, nq):
     return {
         "status": np.array([info[i].status for i in range(nq)], dtype=np.int32),

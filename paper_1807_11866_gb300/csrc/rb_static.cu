@@ -6,6 +6,7 @@
 // path. For them this entry point takes device pointers to its inputs and outputs and uses, as
 // the working copy of each matrix, a file-scope device array that exists for as long as the
 // library is loaded. It calls no allocating CUDA or library routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -24,6 +25,37 @@ std::mutex g_static_mu;
 constexpr int kMaxDevices = 64;
 double *g_static_ptr[kMaxDevices] = {};
 int g_static_sms[kMaxDevices] = {};
+// Unique id of the context the cached address belongs to. A device reset (or a new primary
+// context) reloads the module and may place the array elsewhere, so a changed id redoes the
+// lookup instead of handing the kernel a stale address.
+unsigned long long g_static_ctx[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (0 if the driver entry points are unavailable).
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {  // called under g_static_mu
+    looked = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_cur = (CtxGetCurrentFn)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+  }
+  if (!get_cur || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 }  // namespace
 
 // One system per CTA at a time: copy M_s into this CTA's slice of the scratch, eliminate there
@@ -67,9 +99,11 @@ extern "C" int rb_gepp_solve_static(int n, int batch, const double *d_M, const d
   double *scratch;
   int sms;
   {
-    // once per device, with that device current: the device address of the scratch array
+    // once per device (and again after a device reset), with that device current: the device
+    // address of the scratch array
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    const unsigned long long cid = current_ctx_id();
+    if (!g_static_ptr[dev] || g_static_ctx[dev] != cid) {
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_static_scratch);
       if (e != cudaSuccess) return cuda_fail(nullptr, e, "rb_gepp_solve_static: cudaGetSymbolAddress");
@@ -78,6 +112,8 @@ extern "C" int rb_gepp_solve_static(int n, int batch, const double *d_M, const d
       if (e != cudaSuccess) return cuda_fail(nullptr, e, "rb_gepp_solve_static: SM count");
       g_static_ptr[dev] = (double *)p;
       g_static_sms[dev] = s;
+      // the lookup made the device's context current on this thread if it was not yet
+      g_static_ctx[dev] = cid ? cid : current_ctx_id();
     }
     scratch = g_static_ptr[dev];
     sms = g_static_sms[dev];

@@ -295,3 +295,21 @@ def corner_queries(wl: Workload) -> np.ndarray:
     a0, a1 = wl.alpha_range
     r0, r1 = min(wl.re_range), max(wl.re_range)
     return np.array([[a0, r0], [a0, r1], [a1, r0], [a1, r1]], dtype=np.float64)
+
+
+def stratified_indices(wl: Workload, mu: np.ndarray, cells=(6, 10)) -> np.ndarray:
+    """Indices of queries spread over the parameter box, for parity samples: the box is cut into
+    cells[0] x cells[1] cells (alpha linear, log10 Re), and from each cell the query nearest its
+    centre is taken (cells without a query are skipped). Sorted, distinct."""
+    a0, a1 = wl.alpha_range
+    r0, r1 = math.log10(min(wl.re_range)), math.log10(max(wl.re_range))
+    na, nr = cells
+    x = (mu[:, 0] - a0) / max(a1 - a0, 1e-300) * na
+    y = (np.log10(mu[:, 1]) - r0) / max(r1 - r0, 1e-300) * nr
+    ca = np.clip(np.floor(x), 0, na - 1).astype(int)
+    cr = np.clip(np.floor(y), 0, nr - 1).astype(int)
+    d = (x - ca - 0.5) ** 2 + (y - cr - 0.5) ** 2
+    pick = {}
+    for i in np.argsort(d, kind="stable"):
+        pick.setdefault((ca[i], cr[i]), int(i))
+    return np.array(sorted(pick.values()), dtype=np.int64)

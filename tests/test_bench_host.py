@@ -31,14 +31,21 @@ def test_roofline_work_counts_chord_steps():
         chs = it - full
         lu = np.sum(full * (2 * n ** 3 / 3 + 2 * n ** 2) + chs * 2 * n ** 2)
         jac = np.maximum(full - 1, 0)
-        plain = np.sum(jac * 6 * wl.q_c * n ** 3)
+        # algorithmic work: Q_c n^3 multiply-adds per Jacobian and per FP64 residual
+        plain = np.sum(jac * 2 * wl.q_c * n ** 3)
         sysb = np.sum(full * (8 * n ** 2 + 4 * n * (n + 1)) + jac * 4 * n ** 2 + chs * (8 * n ** 2 + 4 * n))
-        sliced = np.sum(np.maximum(it - 2, 0) * 2 * n ** 2 * 21 * wl.q_c * n)
+        sliced = np.sum(np.maximum(it - 2, 0) * 2 * wl.q_c * n ** 3)
         # 1 ms per step: achieved = units / 1e-3 / scale
         assert np.isclose(rl["k_lu_mixed"]["achieved"], lu / 1e-3 / 1e12)
         assert np.isclose(rl["k_tc_gemm<plain>"]["achieved"], plain / 1e-3 / 1e12)
         assert np.isclose(rl["k_newton_system"]["achieved"], sysb / 1e-3 / 1e9)
         assert np.isclose(rl["k_tc_gemm<sliced>"]["achieved"], sliced / 1e-3 / 1e12)
+        # the products issued: 3 split-BF16 products per Jacobian, 21 digit pairs per residual
+        assert np.isclose(rl["k_tc_gemm<plain>"]["issued_tflops"], 3 * plain / 1e-3 / 1e12)
+        assert np.isclose(rl["k_tc_gemm<sliced>"]["issued_tflops"], 21 * sliced / 1e-3 / 1e12)
+        assert rl["k_tc_gemm<sliced>"]["work"] == "algorithmic"
+        assert np.isclose(rl["k_tc_gemm<sliced>"]["frac"],
+                          rl["k_tc_gemm<sliced>"]["achieved"] / rl["k_tc_gemm<sliced>"]["peak"])
     # the chord steps of the first two queries replace a factorisation by two triangular solves
     _, a, _ = bench.kernel_rooflines(1, wl, q, info, kprof, 1, np.full(4, True))
     _, b, _ = bench.kernel_rooflines(1, wl, q, info, kprof, 1, np.full(4, False))
@@ -69,3 +76,22 @@ def test_combined_modes_are_exact_for_a_linear_pressure():
     P2, r2 = bench.combined_pressure_modes(U2, U2 @ M.T)
     assert r2 == 3
     np.testing.assert_allclose(U2 @ P2.T, U2 @ M.T, atol=1e-9)
+
+
+def test_stratified_indices_cover_the_box():
+    """Parity samples: one query per occupied cell of the alpha x log Re grid, the one nearest the
+    cell's centre, so the sample spreads over the whole parameter box."""
+    wl = synth.WORKLOADS["dense_n300"]
+    q = synth.make_queries(wl)
+    idx = synth.stratified_indices(wl, q.mu, cells=(6, 10))
+    assert len(idx) == 60 and len(np.unique(idx)) == 60
+    a = q.mu[idx, 0]
+    r = np.log10(q.mu[idx, 1])
+    ca = np.floor(a / 35.0 * 6).astype(int)
+    cr = np.floor((r - 2.0) * 10).astype(int)
+    assert len(set(zip(ca, cr))) == 60
+    # nearest to the centre of its own cell
+    for i, c1, c2 in zip(idx, ca, cr):
+        d = ((q.mu[:, 0] / 35.0 * 6 - c1 - 0.5) ** 2 + ((np.log10(q.mu[:, 1]) - 2) * 10 - c2 - 0.5) ** 2)
+        inside = (np.floor(q.mu[:, 0] / 35.0 * 6) == c1) & (np.floor((np.log10(q.mu[:, 1]) - 2) * 10) == c2)
+        assert d[i] == d[inside].min()

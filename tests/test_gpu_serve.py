@@ -181,3 +181,34 @@ def test_mixed_server_sizes_in_buckets(rb):
         assert np.all(U[k][:, s:] == 0)
     assert rel(P, p_or).max() <= 10 * TOL_MIXED
     assert rel(res[5][0], alone[0]) <= TOL_MIXED and rel(res[5][1], alone[1]) <= 10 * TOL_MIXED
+
+
+@pytest.mark.timeout(900)
+def test_serve_n160_shape_batch_and_server(rb):
+    """The serving workload's own shape (n_max = 160, Q_a = Q_c = 16, Q_f = 4, C FP32-exact): 72
+    queries with sizes spread over [16, 160] (both ends included) and parameters over the box
+    (corners included), solved as one batch and through the server, both against the oracle."""
+    wl = synth.WORKLOADS["serve_n160"]
+    ops = synth.make_operators(wl)
+    q = synth.make_queries(wl, batch=68)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    sizes = np.linspace(16, 160, len(mu)).round().astype(np.int32)
+    sizes = np.random.default_rng(7).permutation(sizes)
+    assert sizes.min() == 16 and sizes.max() == 160
+    o = oracle.Oracle.from_set(ops)
+    u_or, _, inf_or = o.solve(mu, n=sizes, threads=oracle.max_threads())
+    assert np.all(inf_or["status"] == 0)
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u_b, _, info_b = ctx.rb_solve(mu, n=sizes)
+        ctx.rb_serve_start()
+        tickets = [ctx.rb_serve_submit(mu[k], n=int(sizes[k])) for k in range(len(mu))]
+        res = [wait(ctx, t, timeout=300.0) for t in tickets]
+        ctx.rb_serve_stop(True)
+    U = np.stack([r[0] for r in res])
+    assert np.all(info_b["status"] == 0)
+    assert all(r[2]["status"] == 0 for r in res)
+    for got in (u_b, U):
+        for b, s in enumerate(sizes):
+            assert rel(got[b, :s], u_or[b, :s]) <= TOL_MIXED, (b, s)
+            assert np.all(got[b, s:] == 0.0)
