@@ -67,8 +67,9 @@ enum {
   RB_Q_REJECTED = 4        /* query size out of range or cancelled */
 };
 
-/* storage type of the convection tensors C and Cs (values are taken as exact) */
-enum { RB_F64 = 0, RB_F32 = 1 };
+/* storage type of the convection tensors C and Cs (values are taken as exact): IEEE binary64,
+ * binary32, or bfloat16 (the upper 16 bits of a binary32, as uint16_t) */
+enum { RB_F64 = 0, RB_F32 = 1, RB_BF16 = 2 };
 
 /* precision of the Newton solve */
 enum {
@@ -99,7 +100,8 @@ typedef struct {
   int n_max;          /* reduced velocity size, 1..RB_N_MAX */
   int m;              /* pressure / supremizer reduced size, 0..RB_M_MAX (0 if B == NULL) */
   int q_a, q_c, q_f, q_b;  /* affine term counts, q_a, q_c, q_f >= 1 */
-  int dtype_c;        /* RB_F64 or RB_F32: storage of C and Cs */
+  int dtype_c;        /* RB_F64, RB_F32 or RB_BF16: storage of C and Cs (kept on the device in
+                         that type; BF16 halves the upload and the device copy of FP32) */
   const double *A;    /* [q_a][n_max][n_max], row = test k, column = trial j */
   const void *C;      /* [q_c][n_max][n_max][n_max], index [j][l][k] */
   const double *f;    /* [q_f][n_max] */
@@ -193,10 +195,34 @@ int rb_solve_theta(rb_ctx *ctx, const double *theta, int n_queries, const int *n
 /* Solve from device buffers owned by the caller, asynchronously on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream). The buffers must stay valid until
  * the stream reaches the end of the work enqueued here. d_n may be NULL (all n_max);
- * d_p and d_info may be NULL. Returns after enqueueing; the context's internal scratch is
- * reused by the next call on any stream, so calls on one context must be ordered. */
+ * d_p and d_info may be NULL. The context's internal scratch is reused by the next call on any
+ * stream, so calls on one context must be ordered.
+ * The call returns once the solve is enqueued, without waiting for it, except:
+ *   - d_n != NULL: the sizes are copied to the host to group the queries by size, which waits
+ *     for the work already on cuda_stream (rb_solve_device_sized avoids this);
+ *   - the first solve of a new batch shape (batch size, size mix or buffers) sizes its scratch,
+ *     runs the autotuner (cfg.autotune) and captures the solve graph, which synchronises;
+ *   - with cfg.use_graph == 0 or profiling on, every Newton iteration is checked on the host;
+ *   - the FP64 path (RB_PREC_FP64) never waits.
+ * A device-side wait of the mixed path that gives up (RB_ERR_TIMEOUT: the results of that solve
+ * are invalid) is reported by rb_solve_device_status, by rb_solve, or by the next solve call on
+ * the context, once. */
 int rb_solve_device(rb_ctx *ctx, const double *d_mu, int n_queries, const int *d_n,
                     double *d_u, double *d_p, rb_query_info *d_info, void *cuda_stream);
+
+/* rb_solve_device with the query sizes also given on the host: h_n [n_queries] (caller-owned,
+ * read during the call only) must hold the same values as d_n; then no copy of d_n to the host
+ * is needed and a solve of a batch shape seen before only enqueues. h_n == NULL behaves as
+ * rb_solve_device; h_n != NULL with d_n == NULL is RB_ERR_ARG. */
+int rb_solve_device_sized(rb_ctx *ctx, const double *d_mu, int n_queries, const int *d_n,
+                          const int *h_n, double *d_u, double *d_p, rb_query_info *d_info,
+                          void *cuda_stream);
+
+/* Outcome of the solves enqueued on this context so far: RB_OK when they have completed without
+ * a device-side failure; RB_PENDING when wait == 0 and the last one has not completed yet;
+ * RB_ERR_TIMEOUT (once) when a device-side wait of one of them gave up. wait != 0 blocks until
+ * the last solve has completed. */
+int rb_solve_device_status(rb_ctx *ctx, int wait);
 
 /* ---- pressure reconstruction (Sec. 4.2, combined velocity-pressure basis) -----------------
  * With a combined basis every velocity basis function j carries pressure data p^_j, and the

@@ -9,6 +9,8 @@
 //  * k_pressure: a posteriori pressure recovery (Sec. 2.2, Eq. sup-vvar; Eq. blocksolve-2).
 //  * k_eval_fp64, k_gepp_fp64: single steps exposed through rb_eval / rb_gepp_solve.
 //  * k_build_dt, k_convert: load-time layout builders.
+#include <cuda_bf16.h>
+
 #include "rb_kernels.cuh"
 
 namespace rb {
@@ -346,6 +348,11 @@ __global__ void __launch_bounds__(kThreads) k_gepp_fp64(double *M, double *rhs, 
 // ---------------------------------------------------------------------------------------
 // Load-time builders.
 // Dt[q][l][k][j] = C[q][l][j][k] + C[q][j][l][k] (index [j][l][k] of C as stored).
+// storage types of C and Cs (RB_F64, RB_F32, RB_BF16) to FP64, exactly
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
 template <typename TC>
 __global__ void k_build_dt(const TC *C, double *Dt, int nm, int qc) {
   const size_t nm1 = nm, total = (size_t)qc * nm1 * nm1 * nm1;
@@ -354,8 +361,8 @@ __global__ void k_build_dt(const TC *C, double *Dt, int nm, int qc) {
     const size_t j = e % nm1, k = (e / nm1) % nm1, l = (e / (nm1 * nm1)) % nm1;
     const size_t q = e / (nm1 * nm1 * nm1);
     const size_t cq = q * nm1 * nm1 * nm1;
-    const double a = (double)C[cq + (l * nm1 + j) * nm1 + k];
-    const double c = (double)C[cq + (j * nm1 + l) * nm1 + k];
+    const double a = to_f64(C[cq + (l * nm1 + j) * nm1 + k]);
+    const double c = to_f64(C[cq + (j * nm1 + l) * nm1 + k]);
     Dt[e] = a + c;
   }
 }
@@ -364,7 +371,7 @@ template <typename TS>
 __global__ void k_convert(const TS *src, double *dst, size_t count) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
        e += (size_t)gridDim.x * blockDim.x)
-    dst[e] = (double)src[e];
+    dst[e] = to_f64(src[e]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -408,19 +415,23 @@ cudaError_t launch_gepp_fp64(double *M, double *rhs, int n, int batch, int *stat
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_dt(const void *C, int c_is_f32, double *Dt, int nm, int qc, int sms,
+cudaError_t launch_build_dt(const void *C, int dtype, double *Dt, int nm, int qc, int sms,
                             cudaStream_t st) {
-  if (c_is_f32)
+  if (dtype == RB_F32)
     k_build_dt<float><<<sms * 8, 256, 0, st>>>((const float *)C, Dt, nm, qc);
+  else if (dtype == RB_BF16)
+    k_build_dt<__nv_bfloat16><<<sms * 8, 256, 0, st>>>((const __nv_bfloat16 *)C, Dt, nm, qc);
   else
     k_build_dt<double><<<sms * 8, 256, 0, st>>>((const double *)C, Dt, nm, qc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert(const void *src, int src_is_f32, double *dst, size_t count, int sms,
+cudaError_t launch_convert(const void *src, int dtype, double *dst, size_t count, int sms,
                            cudaStream_t st) {
-  if (src_is_f32)
+  if (dtype == RB_F32)
     k_convert<float><<<sms * 8, 256, 0, st>>>((const float *)src, dst, count);
+  else if (dtype == RB_BF16)
+    k_convert<__nv_bfloat16><<<sms * 8, 256, 0, st>>>((const __nv_bfloat16 *)src, dst, count);
   else
     k_convert<double><<<sms * 8, 256, 0, st>>>((const double *)src, dst, count);
   return cudaGetLastError();

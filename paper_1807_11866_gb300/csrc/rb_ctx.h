@@ -41,6 +41,8 @@ int solve_device_impl(rb_ctx *ctx, const double *d_mu, const double *d_theta, in
 int eval_mixed(rb_ctx *ctx, const double *d_mu, int nq, int n, const double *d_u, int precision,
                double *d_R, double *d_J, cudaStream_t st);
 void mixed_release(rb_ctx *ctx);
+// outcome of the asynchronous mixed solves enqueued so far (RB_OK, RB_PENDING, RB_ERR_TIMEOUT)
+int mixed_solve_status(rb_ctx *ctx, int wait);
 void serve_shutdown(rb_ctx *ctx);
 bool serve_running(const rb_ctx *ctx);
 // mixed-path pieces used by the server
@@ -79,7 +81,7 @@ struct rb_ctx {
   rb::DevOps ops{};
   std::vector<void *> op_allocs;
   void *d_C = nullptr;  // C in its storage type [q_c][n][n][n]
-  int c_is_f32 = 0;
+  int c_dtype = RB_F64;  // RB_F64, RB_F32 or RB_BF16
   double *d_PT = nullptr;  // pressure modes of a combined basis, transposed [n_max][m_r]
   int m_r = 0;
   // scratch

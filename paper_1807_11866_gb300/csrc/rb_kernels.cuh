@@ -43,9 +43,9 @@ cudaError_t launch_pressure(const PressureParams &p, int sms, cudaStream_t st);
 cudaError_t launch_eval_fp64(const EvalParams &p, int sms, cudaStream_t st);
 cudaError_t launch_gepp_fp64(double *M, double *rhs, int n, int batch, int *status, int sms,
                              cudaStream_t st);
-cudaError_t launch_build_dt(const void *C, int c_is_f32, double *Dt, int nm, int qc, int sms,
+cudaError_t launch_build_dt(const void *C, int dtype, double *Dt, int nm, int qc, int sms,
                             cudaStream_t st);
-cudaError_t launch_convert(const void *src, int src_is_f32, double *dst, size_t count, int sms,
+cudaError_t launch_convert(const void *src, int dtype, double *dst, size_t count, int sms,
                            cudaStream_t st);
 
 }  // namespace rb

@@ -84,8 +84,16 @@ struct MixedState {
     float ms[4] = {0, 0, 0, 0};       // best times: elimination, plain GEMM, sliced GEMM
   } tune;
   // shared, owned by the root
-  int *dev_words = nullptr;     // [0] active count, [1] error word, [2] iterations, [8..] scratch
-  int *h_words = nullptr;       // pinned mirror
+  int *dev_words = nullptr;     // [0] active count, [1] error word, [2] iterations,
+                                // [5] sticky error word of graph solves, [8..] scratch
+  int *h_words = nullptr;       // pinned mirror; [12..15] copy of words [4..7] after a graph solve
+  // asynchronous graph solves: the last one's completion event and whether its words are unread
+  cudaEvent_t done_ev = nullptr;
+  bool pending = false;
+  cudaStream_t pending_st = nullptr;
+  int *h_perm = nullptr;        // pinned bucket order of the last solve (capacity h_perm_cap)
+  int h_perm_cap = 0;
+  cudaEvent_t perm_ev = nullptr;  // its upload has completed
   rb_query_info *info_own = nullptr;
   int info_cap = 0;
   std::map<int, MixedState *> buckets;  // nb < n_max
@@ -1592,6 +1600,9 @@ static void release_state(rb_ctx *ctx, MixedState *M) {
                     (void *)M->info_g})
       ctx_free(ctx, q);
     if (M->h_words) cudaFreeHost(M->h_words);
+    if (M->h_perm) cudaFreeHost(M->h_perm);
+    if (M->done_ev) cudaEventDestroy(M->done_ev);
+    if (M->perm_ev) cudaEventDestroy(M->perm_ev);
     if (M->gexec) cudaGraphExecDestroy(M->gexec);
     for (cudaStream_t c : M->cap)
       if (c) cudaStreamDestroy(c);
@@ -1716,6 +1727,10 @@ static int mixed_root(rb_ctx *ctx, cudaStream_t st) {
   M->dev_words = (int *)p;
   cudaMemsetAsync(M->dev_words, 0, 64, st);
   if (cudaMallocHost(&M->h_words, 64) != cudaSuccess) return set_error(ctx, RB_ERR_OOM, "pinned words");
+  memset(M->h_words, 0, 64);
+  if (cudaEventCreateWithFlags(&M->done_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&M->perm_ev, cudaEventDisableTiming) != cudaSuccess)
+    return set_error(ctx, RB_ERR_CUDA, "solve events");
   return RB_OK;
 }
 
@@ -2266,6 +2281,10 @@ __global__ void k_loop_cond(cudaGraphConditionalHandle h, int *words, int max_it
   cudaGraphSetConditional(h, (words[0] > 0 && it < max_iter) ? 1u : 0u);
 }
 
+// End of a graph solve: the error word of this solve into the sticky word 5, which only the host
+// clears once it has reported it (a solve that gave up is reported by a later call).
+__global__ void k_latch_error(int *words) { words[5] |= words[1]; }
+
 // ---- autotuner ------------------------------------------------------------------------------
 // Synthetic, well-conditioned systems of the bucket's shape for timing the elimination variants:
 // [J | -R] = [4 I + noise | 1], unit norms, every query active on the FP64-residual rung.
@@ -2512,6 +2531,7 @@ static int build_solve_graph(rb_ctx *ctx, const SolvePlan &pl, const std::vector
     if ((e = cudaStreamEndCapture(cb, &bg)) != cudaSuccess) break;
     if (pl.pres && (rc = solve_pressure(ctx, pl.parts, cs)) != RB_OK) break;
     if ((rc = plan_edges(ctx, pl, false, cs)) != RB_OK) break;
+    k_latch_error<<<1, 1, 0, cs>>>(M->dev_words);
   } while (false);
   if (body_open) {
     cudaGraph_t bg;
@@ -2577,10 +2597,33 @@ static int gather_scratch(rb_ctx *ctx, int nq, bool theta) {
   return RB_OK;
 }
 
+// Outcome of the graph solves enqueued so far: RB_OK, RB_PENDING (wait == 0 and the last one
+// has not completed) or RB_ERR_TIMEOUT (a device-side wait of one of them gave up; reported once).
+int mixed_solve_status(rb_ctx *ctx, int wait) {
+  MixedState *R = ctx->mixed;
+  if (!R || !R->pending) return RB_OK;
+  cudaError_t e = wait ? cudaEventSynchronize(R->done_ev) : cudaEventQuery(R->done_ev);
+  if (e == cudaErrorNotReady) return RB_PENDING;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve completion");
+  R->pending = false;
+  const int w = R->h_words[13];
+  if (w) {
+    R->h_words[13] = 0;
+    e = cudaMemsetAsync(R->dev_words + 5, 0, 4, R->pending_st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
+    return set_error(ctx, RB_ERR_TIMEOUT,
+                     "mixed solve: tensor-core pipeline wait gave up (code %d); the results of "
+                     "that solve are not valid", w);
+  }
+  return RB_OK;
+}
+
 int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
                 const int *h_n, double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st) {
   int rc = mixed_root(ctx, st);
   if (rc != RB_OK) return rc;
+  // an earlier asynchronous solve that has completed and failed is reported now
+  if ((rc = mixed_solve_status(ctx, 0)) != RB_OK && rc != RB_PENDING) return rc;
   MixedState *R = ctx->mixed;
   const DevOps &o = ctx->ops;
   rb_query_info *info = d_info ? d_info : own_info(ctx, nq);
@@ -2623,8 +2666,21 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
       ranges.push_back({M, {(int)perm.size(), (int)kv.second.size()}});
       perm.insert(perm.end(), kv.second.begin(), kv.second.end());
     }
-    cudaError_t e = cudaMemcpyAsync(R->perm, perm.data(), 4 * (size_t)nq, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vector goes out of scope
+    // the order goes up from pinned memory without a synchronisation; the previous solve's
+    // upload from the same buffer has completed before it is overwritten
+    cudaError_t e = cudaEventSynchronize(R->perm_ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bucket order");
+    if (R->h_perm_cap < nq) {
+      if (R->h_perm) cudaFreeHost(R->h_perm);
+      R->h_perm = nullptr;
+      R->h_perm_cap = 0;
+      if (cudaMallocHost(&R->h_perm, 4 * (size_t)nq) != cudaSuccess)
+        return set_error(ctx, RB_ERR_OOM, "pinned bucket order");
+      R->h_perm_cap = nq;
+    }
+    std::copy(perm.begin(), perm.end(), R->h_perm);
+    e = cudaMemcpyAsync(R->perm, R->h_perm, 4 * (size_t)nq, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(R->perm_ev, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bucket order");
     const int mm = std::max(o.m, 1);
     for (auto &r : ranges) {
@@ -2647,9 +2703,16 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
         k.info != info || k.nq != nq || k.epoch != R->epoch || k.parts != key_parts) {
       if ((rc = build_solve_graph(ctx, pl, key_parts)) != RB_OK) return rc;
     }
-    const cudaError_t e = cudaGraphLaunch(R->gexec, st);
+    cudaError_t e = cudaGraphLaunch(R->gexec, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve graph launch");
-    return check_words(ctx, st, "mixed solve");
+    // no synchronisation: the error words come back to pinned memory behind the solve and are
+    // read by mixed_solve_status (rb_solve_device_status, rb_solve, or the next solve)
+    e = cudaMemcpyAsync(R->h_words + 12, R->dev_words + 4, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(R->done_ev, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve completion");
+    R->pending = true;
+    R->pending_st = st;
+    return RB_OK;
   }
   if ((rc = plan_edges(ctx, pl, true, st)) != RB_OK) return rc;
   if ((rc = solve_prologue(ctx, pl.parts, st)) != RB_OK) return rc;

@@ -28,7 +28,7 @@ constexpr uint32_t kOpVersion = 1, kOpHeader = 64;
 struct OpShape {
   int n, m, q_a, q_c, q_f, q_b, dtype_c;
   bool pres;
-  size_t csz() const { return dtype_c == RB_F32 ? 4 : 8; }
+  size_t csz() const { return dtype_c == RB_F64 ? 8 : (dtype_c == RB_F32 ? 4 : 2); }
   // byte sizes of the arrays in file order
   void sizes(size_t out[7]) const {
     const size_t nn = (size_t)n, mm = (size_t)m;
@@ -93,7 +93,8 @@ static int check_shape(const rb_ctx *ctx, const OpShape &s) {
   if (s.q_a < 1 || s.q_c < 1 || s.q_f < 1 || s.q_a > RB_Q_MAX || s.q_c > RB_Q_MAX ||
       s.q_f > RB_Q_MAX || s.q_b < 0 || s.q_b > RB_Q_MAX)
     return set_error(ctx, RB_ERR_ARG, "affine term counts out of range");
-  if (s.dtype_c != RB_F64 && s.dtype_c != RB_F32) return set_error(ctx, RB_ERR_ARG, "bad dtype_c");
+  if (s.dtype_c != RB_F64 && s.dtype_c != RB_F32 && s.dtype_c != RB_BF16)
+    return set_error(ctx, RB_ERR_ARG, "bad dtype_c");
   if (s.pres && (s.m < 1 || s.m > RB_M_MAX || s.q_b < 1))
     return set_error(ctx, RB_ERR_ARG, "pressure sizes out of range");
   return RB_OK;

@@ -274,7 +274,7 @@ int stage_solve(rb_ctx *ctx, const double *mu, const double *theta, int nq, cons
   if (e == cudaSuccess && info) e = cudaMemcpyAsync(info, d_info, sizeof(rb_query_info) * (size_t)nq, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "rb_solve");
-  return RB_OK;
+  return mixed_solve_status(ctx, 1);
 }
 
 }  // namespace rb
@@ -370,7 +370,8 @@ int rb_load_operators(rb_ctx *ctx, const rb_operators *ops) {
   if (ops->q_a < 1 || ops->q_c < 1 || ops->q_f < 1 || ops->q_a > RB_Q_MAX || ops->q_c > RB_Q_MAX ||
       ops->q_f > RB_Q_MAX || ops->q_b < 0 || ops->q_b > RB_Q_MAX)
     return set_error(ctx, RB_ERR_ARG, "affine term counts out of range 1..%d", RB_Q_MAX);
-  if (ops->dtype_c != RB_F64 && ops->dtype_c != RB_F32) return set_error(ctx, RB_ERR_ARG, "bad dtype_c");
+  if (ops->dtype_c != RB_F64 && ops->dtype_c != RB_F32 && ops->dtype_c != RB_BF16)
+    return set_error(ctx, RB_ERR_ARG, "bad dtype_c");
   if (!ops->A || !ops->C || !ops->f) return set_error(ctx, RB_ERR_ARG, "A, C and f are required");
   const bool pres = ops->B != nullptr;
   if (pres && (ops->m < 1 || ops->m > RB_M_MAX || ops->q_b < 1 || !ops->As || !ops->Cs || !ops->fs))
@@ -388,8 +389,8 @@ int rb_load_operators(rb_ctx *ctx, const rb_operators *ops) {
   o.n_theta = o.q_a + o.q_c + o.q_f + o.q_b;
   o.theta_family = ctx->cfg.theta_family;
   const size_t nn = (size_t)n, ncube = nn * nn * nn;
-  const int f32 = ops->dtype_c == RB_F32;
-  const size_t csz = f32 ? sizeof(float) : sizeof(double);
+  const int dt = ops->dtype_c;
+  const size_t csz = dt == RB_F64 ? sizeof(double) : (dt == RB_F32 ? sizeof(float) : 2);
   int rc = RB_OK;
   void *p = nullptr;
   if ((rc = upload(ctx, &p, ops->A, sizeof(double) * o.q_a * nn * nn, "A")) != RB_OK) goto fail;
@@ -398,11 +399,11 @@ int rb_load_operators(rb_ctx *ctx, const rb_operators *ops) {
   o.f = (const double *)p;
   if ((rc = upload(ctx, &p, ops->C, csz * o.q_c * ncube, "C")) != RB_OK) goto fail;
   ctx->d_C = p;
-  ctx->c_is_f32 = f32;
+  ctx->c_dtype = dt;
   if ((rc = op_alloc(ctx, &p, sizeof(double) * o.q_c * ncube, "Dt (FP64)")) != RB_OK) goto fail;
   o.Dt = (const double *)p;
   {
-    cudaError_t e = launch_build_dt(ctx->d_C, f32, (double *)o.Dt, n, o.q_c, ctx->sms, ctx->stream);
+    cudaError_t e = launch_build_dt(ctx->d_C, dt, (double *)o.Dt, n, o.q_c, ctx->sms, ctx->stream);
     if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "build Dt"); goto fail; }
   }
   if (pres) {
@@ -415,9 +416,9 @@ int rb_load_operators(rb_ctx *ctx, const rb_operators *ops) {
     o.fs = (const double *)p;
     void *cs_store = nullptr;
     if ((rc = upload(ctx, &cs_store, ops->Cs, csz * o.q_c * nn * nn * m, "Cs")) != RB_OK) goto fail;
-    if (f32) {
+    if (dt != RB_F64) {
       if ((rc = op_alloc(ctx, &p, sizeof(double) * o.q_c * nn * nn * m, "Cs (FP64)")) != RB_OK) goto fail;
-      cudaError_t e = launch_convert(cs_store, 1, (double *)p, o.q_c * nn * nn * m, ctx->sms, ctx->stream);
+      cudaError_t e = launch_convert(cs_store, dt, (double *)p, o.q_c * nn * nn * m, ctx->sms, ctx->stream);
       if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "convert Cs"); goto fail; }
       o.Cs = (const double *)p;
     } else {
@@ -455,12 +456,24 @@ int rb_solve_theta(rb_ctx *ctx, const double *theta, int n_queries, const int *n
 
 int rb_solve_device(rb_ctx *ctx, const double *d_mu, int n_queries, const int *d_n, double *d_u,
                     double *d_p, rb_query_info *d_info, void *cuda_stream) {
+  return rb_solve_device_sized(ctx, d_mu, n_queries, d_n, nullptr, d_u, d_p, d_info, cuda_stream);
+}
+
+int rb_solve_device_sized(rb_ctx *ctx, const double *d_mu, int n_queries, const int *d_n,
+                          const int *h_n, double *d_u, double *d_p, rb_query_info *d_info,
+                          void *cuda_stream) {
   if (!ctx) return RB_ERR_ARG;
-  if (n_queries < 0 || (n_queries > 0 && (!d_mu || !d_u)))
+  if (n_queries < 0 || (n_queries > 0 && (!d_mu || !d_u)) || (h_n && !d_n))
     return set_error(ctx, RB_ERR_ARG, "bad arguments to rb_solve_device");
   cudaSetDevice(ctx->device);
   return solve_device_impl(ctx, d_mu, nullptr, n_queries, d_n, d_u, d_p, d_info,
-                           (cudaStream_t)cuda_stream);
+                           (cudaStream_t)cuda_stream, h_n);
+}
+
+int rb_solve_device_status(rb_ctx *ctx, int wait) {
+  if (!ctx) return RB_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  return mixed_solve_status(ctx, wait);
 }
 
 int rb_eval(rb_ctx *ctx, const double *mu, int n_queries, int n, const double *u, int precision,

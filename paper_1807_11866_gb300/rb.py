@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "librb.so")
 RB_OK, RB_PENDING = 0, 1
 RB_ERR_ARG, RB_ERR_OOM, RB_ERR_CUDA, RB_ERR_STATE, RB_ERR_TIMEOUT = -1, -2, -3, -4, -5
 RB_Q_OK, RB_Q_NOT_CONVERGED, RB_Q_SINGULAR, RB_Q_NONFINITE, RB_Q_REJECTED = 0, 1, 2, 3, 4
-RB_F64, RB_F32 = 0, 1
+RB_F64, RB_F32, RB_BF16 = 0, 1, 2
 RB_PREC_FP64, RB_PREC_MIXED = 0, 1
 RB_THETA_TRIG, RB_THETA_USER, RB_THETA_POLY = 0, 1, 2
 RB_PRESSURE_RECOVER, RB_PRESSURE_RECONSTRUCT = 0, 1
@@ -25,7 +25,8 @@ RB_N_MAX, RB_M_MAX, RB_Q_MAX = 320, 128, 64
 RB_STATIC_N_MAX, RB_STATIC_SCRATCH_BYTES = 512, 16 << 20
 
 EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
-           "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_eval", "rb_gepp_solve",
+           "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_solve_device_sized",
+           "rb_solve_device_status", "rb_eval", "rb_gepp_solve",
            "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
            "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots", "rb_tuning",
            "rb_load_pressure_modes", "rb_reconstruct_pressure", "rb_reconstruct_pressure_device",
@@ -83,6 +84,8 @@ def library():
         L.rb_solve.argtypes = [P, P, I, P, P, P, P]
         L.rb_solve_theta.argtypes = [P, P, I, P, P, P, P]
         L.rb_solve_device.argtypes = [P, P, I, P, P, P, P, P]
+        L.rb_solve_device_sized.argtypes = [P, P, I, P, P, P, P, P, P]
+        L.rb_solve_device_status.argtypes = [P, I]
         L.rb_eval.argtypes = [P, P, I, I, P, I, P, P]
         L.rb_load_pressure_modes.argtypes = [P, P, I]
         L.rb_save_operators.argtypes = [P, ctypes.c_char_p]
@@ -140,7 +143,7 @@ def _operators(A, C, f, B=None, As=None, Cs=None, fs=None):
     """rb_operators over host arrays (kept alive by the returned list)."""
     A, f = _f64(A), _f64(f)
     C = np.ascontiguousarray(C)
-    dt = RB_F32 if C.dtype == np.float32 else RB_F64
+    dt = {np.dtype(np.float32): RB_F32, np.dtype(np.uint16): RB_BF16}.get(C.dtype, RB_F64)
     if dt == RB_F64:
         C = _f64(C)
     q_a, n, _ = A.shape
@@ -156,6 +159,27 @@ def _operators(A, C, f, B=None, As=None, Cs=None, fs=None):
     return ops, keep
 
 
+def bf16_bits(x):
+    """BF16 storage of an array whose values are all BF16 numbers (float32 or float64 holding
+    them): the upper 16 bits of each binary32, as uint16. Raises if a value is not a BF16
+    number (no rounding happens here)."""
+    x = np.asarray(x)
+    x32 = np.ascontiguousarray(x, dtype=np.float32)
+    if x.dtype != np.float32 and not np.array_equal(x32.astype(x.dtype), x):
+        raise ValueError("values are not BF16 numbers")
+    bits = x32.view(np.uint32)
+    if np.any(bits & 0xFFFF):
+        raise ValueError("values are not BF16 numbers")
+    return (bits >> 16).astype(np.uint16)
+
+
+def _c_storage(ops, C):
+    """C (or Cs) as the operator set stores it: BF16 bits for a BF16 workload."""
+    if C is not None and getattr(getattr(ops, "wl", None), "c_dtype", None) == "bf16":
+        return bf16_bits(C)
+    return C
+
+
 def rb_save_operators(path, A, C, f, B=None, As=None, Cs=None, fs=None):
     """Write an operator file (host arrays as for rb_load_operators)."""
     ops, keep = _operators(A, C, f, B, As, Cs, fs)
@@ -166,7 +190,8 @@ def rb_save_operators(path, A, C, f, B=None, As=None, Cs=None, fs=None):
 
 def save_set(path, ops):
     """Write a synth.OperatorSet (or any object with the same fields) to an operator file."""
-    rb_save_operators(path, ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs)
+    rb_save_operators(path, ops.A, _c_storage(ops, ops.C), ops.f, ops.B, ops.As,
+                      _c_storage(ops, ops.Cs), ops.fs)
 
 
 def rb_config_default() -> rb_config:
@@ -291,7 +316,8 @@ class Context:
         mine = RB_THETA_TRIG if self.cfg.theta_family == RB_THETA_USER else self.cfg.theta_family
         if fam is not None and fam != mine:
             raise ValueError(f"operator set uses theta family {fam}, the context {mine}")
-        self.rb_load_operators(ops.A, ops.C, ops.f, ops.B, ops.As, ops.Cs, ops.fs)
+        self.rb_load_operators(ops.A, _c_storage(ops, ops.C), ops.f, ops.B, ops.As,
+                               _c_storage(ops, ops.Cs), ops.fs)
 
     # --- solves -------------------------------------------------------------------------
     def rb_solve(self, mu, n=None, pressure=True):
@@ -321,6 +347,20 @@ class Context:
         return self._check(library().rb_solve_device(
             self.h, _ptr(d_mu), n_queries, _ptr(d_n), _ptr(d_u), _ptr(d_p), _ptr(d_info),
             stream), "rb_solve_device")
+
+    def rb_solve_device_sized(self, d_mu, n_queries, d_n, h_n, d_u, d_p, d_info, stream):
+        """rb_solve_device with the sizes also on the host (h_n: int32 numpy array)."""
+        hn = None if h_n is None else np.ascontiguousarray(h_n, dtype=np.int32)
+        return self._check(library().rb_solve_device_sized(
+            self.h, _ptr(d_mu), n_queries, _ptr(d_n), _ptr(hn), _ptr(d_u), _ptr(d_p),
+            _ptr(d_info), stream), "rb_solve_device_sized")
+
+    def rb_solve_device_status(self, wait=True):
+        """RB_OK or RB_PENDING (wait=False); raises RbError on RB_ERR_TIMEOUT."""
+        rc = library().rb_solve_device_status(self.h, 1 if wait else 0)
+        if rc == RB_PENDING:
+            return rc
+        return self._check(rc, "rb_solve_device_status")
 
     def rb_eval(self, mu, n, u, precision=RB_PREC_FP64, jacobian=True):
         mu = _f64(mu).reshape(-1, 2)

@@ -36,7 +36,7 @@ def read_file(path):
     body = raw[64:]
     assert version == 1 and hsize == 64 and payload == len(body)
     assert csum == fnv1a_words(body)
-    cdt = np.float32 if dt == 1 else np.float64
+    cdt = {0: np.float64, 1: np.float32, 2: np.uint16}[int(dt)]  # 2: BF16 bit patterns
     shapes = [((q_a, n, n), np.float64), ((q_c, n, n, n), cdt), ((q_f, n), np.float64)]
     if flags & 1:
         shapes += [((q_b, m, m), np.float64), ((q_a, m, n), np.float64), ((q_c, n, n, m), cdt),
@@ -50,10 +50,17 @@ def read_file(path):
     return out
 
 
-@pytest.mark.parametrize("c_dtype,pres", [("f64", True), ("f32", True), ("f64", False)])
+def bf16_values(bits):
+    """float32 values of BF16 bit patterns (independent of the binding's conversion)."""
+    return (bits.astype(np.uint32) << 16).view(np.float32)
+
+
+@pytest.mark.parametrize("c_dtype,pres", [("f64", True), ("f32", True), ("f64", False),
+                                          ("bf16", True)])
 def test_written_file_reads_back(rb, tmp_path, c_dtype, pres):
-    wl = synth.WORKLOADS["sweep_n50"]
-    ops = synth.make_operators(wl, n_max=7, q_c=3, c_dtype=c_dtype)
+    import dataclasses
+    wl = dataclasses.replace(synth.WORKLOADS["sweep_n50"], c_dtype=c_dtype)
+    ops = synth.make_operators(wl, n_max=7, q_c=3)
     if not pres:
         ops.B = ops.As = ops.Cs = ops.fs = None
     path = tmp_path / "ops.rbops"
@@ -62,6 +69,8 @@ def test_written_file_reads_back(rb, tmp_path, c_dtype, pres):
     want = [ops.A, ops.C, ops.f] + ([ops.B, ops.As, ops.Cs, ops.fs] if pres else [])
     assert len(arrs) == len(want)
     for a, w in zip(arrs, want):
+        if a.dtype == np.uint16:  # BF16 storage: 2 bytes per value, the values unchanged
+            a = bf16_values(a)
         np.testing.assert_array_equal(a, w)
 
 
