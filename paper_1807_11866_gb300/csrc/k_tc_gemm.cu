@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_levels = num_levels(MODE, p);
+  int n_levels = num_levels(MODE, p);
+  if (MODE != kPlain && p.lmax && p.kb[1] == 0)  // a truncated launch: levels 2 .. *lmax
+    n_levels = min(n_levels, max(1, *(volatile const int *)p.lmax - 1));
   const int chunk_steps = (MODE == kPlain) ? (1 << 30) : kChunkSteps;
   // work units: tiles [0, full) whole, the tail tiles split into lsplit level parts each
   const int num_tiles = p.m_tiles * p.n_tiles;

@@ -71,6 +71,7 @@ struct MixedState {
   float2 *Bmu = nullptr;        // [bcap][m][m] B(mu) as double-float
   float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices (or factors)
   int *Piv = nullptr;           // [bcap][nb] pivot rows of the factors kept for chord steps
+  double *dU = nullptr;         // [bcap][nb] each query's last update (chord steps' residual)
   double2 *Rn = nullptr;        // [bcap] (unused, max(1, ||f(mu)||)) of the queries
   double *Rg = nullptr;         // [bcap][(nb + 7) / 8] row-group sums of R^2 (in Rn's block)
   CUtensorMap tmXj, tmXd;
@@ -351,8 +352,15 @@ struct BuildXParams {
   __nv_bfloat16 *Xj, *Xd;
   int *xexp;        // [2][b_pad]
   float2 *ufT;      // [nb][b_pad]
-  double *out;      // [b_pad][nout], zeroed for each built query
+  double *out;      // [b_pad][nout], zeroed for each built query (not in increment mode)
   int nout;
+  // increment mode (chord steps): the operand of C(u, u) - C(u - d, u - d) = J^c(d) (u - d / 2)
+  // instead of C(u, u): X = theta^c (x) d on its own grid, the contraction vector u - d / 2,
+  // the output accumulated onto the previous C(u - d, u - d); the digit level the launch needs
+  // is raised into *lmax (see k_build_x)
+  int incr;
+  const double *dU;  // [nq][nb] the last update d of each query
+  int *lmax;
 };
 
 __device__ __forceinline__ bool is_active(const rb_query_info &q, int max_iter) {
@@ -400,17 +408,19 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
     const int n = p.nsz ? p.nsz[b] : o.n_max;
     const double *ta = p.theta + (size_t)b * o.n_theta, *tc = ta + o.q_a;
     const double *ub = p.u + (size_t)b * o.n_max;
-    // (theta^c (x) u)[kap] at kap = q nb + l, zero past the query's size
+    // the vector in the operand: u, or the last update d in increment mode
+    const double *vb = p.incr ? p.dU + (size_t)b * p.nb : ub;
+    // (theta^c (x) v)[kap] at kap = q nb + l, zero past the query's size
     auto xval = [&](int q, int l) -> double {
-      return (q < o.q_c && l < n) ? tc[q] * ub[l] : 0.0;
+      return (q < o.q_c && l < n) ? tc[q] * vb[l] : 0.0;
     };
     // grid exponents from the integer bit patterns (|x| orders like its bits). The largest
     // |theta^c_q u_l| is the rounded product of the largest factors (rounding is monotone),
     // so the maximum over the row needs only the maxima of theta^c and u.
     const unsigned long long absmask = 0x7FFFFFFFFFFFFFFFull;
-    unsigned long long m0 = 0, m1 = 0;
+    unsigned long long m0 = 0, m1 = 0, mu = 0, mt = 0;
     if (p.digits) {
-      unsigned long long mt = 0, mu = 0;
+      unsigned long long mv = 0;
       for (int q = lane; q < o.q_c; q += 32) {
         const unsigned long long v = (unsigned long long)__double_as_longlong(tc[q]) & absmask;
         mt = v > mt ? v : mt;
@@ -418,6 +428,8 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
       for (int l = lane; l < n; l += 32) {
         const unsigned long long v = (unsigned long long)__double_as_longlong(ub[l]) & absmask;
         mu = v > mu ? v : mu;
+        const unsigned long long w = (unsigned long long)__double_as_longlong(vb[l]) & absmask;
+        mv = w > mv ? w : mv;
       }
       for (int q = lane; q < o.q_a; q += 32) {
         const unsigned long long v = (unsigned long long)__double_as_longlong(ta[q]) & absmask;
@@ -427,16 +439,33 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
         const unsigned long long a = __shfl_xor_sync(0xffffffffu, mt, off);
         const unsigned long long c = __shfl_xor_sync(0xffffffffu, mu, off);
         const unsigned long long d = __shfl_xor_sync(0xffffffffu, m1, off);
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, mv, off);
         mt = a > mt ? a : mt;
         mu = c > mu ? c : mu;
         m1 = d > m1 ? d : m1;
+        mv = w > mv ? w : mv;
       }
       m0 = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)mt) *
-                                                    __longlong_as_double((long long)mu)) & absmask;
+                                                    __longlong_as_double((long long)mv)) & absmask;
     }
-    // digits on the grid with one binade of headroom (balanced digits); the sliced operand holds
-    // x / 2: the same digits recorded one binade lower
-    const int ex0 = exp_of_bits(m0) + 1, e0 = ex0 - 1, e1 = exp_of_bits(m1) + 1;
+    // digits on the grid with one binade of headroom (balanced digits); the operand of C(u, u)
+    // holds x / 2: the same digits recorded one binade lower (increment mode: x itself)
+    const int ex0 = exp_of_bits(m0) + 1, e0 = p.incr ? ex0 : ex0 - 1, e1 = exp_of_bits(m1) + 1;
+    if (p.incr && lane == 0) {
+      // Digit levels the increment needs: its truncation (pairs i + j > L dropped, on the grid of
+      // d) must stay below that of the full product on the grid of u (pairs i + j > S + 1). Every
+      // 7 binary digits by which d lies below u saves one level.
+      const unsigned long long mtu = (unsigned long long)__double_as_longlong(
+          __longlong_as_double((long long)mt) * __longlong_as_double((long long)mu)) & absmask;
+      const int e0u = exp_of_bits(mtu);  // the grid exponent of the full product's x / 2
+      int need = 2;
+      if (m0 != 0) {
+        const int below = e0u - ex0;
+        need = p.S0 + 1 - (below > 0 ? below / kDigitBits : 0);
+        need = max(2, min(p.S0 + 1, need));
+      }
+      atomicMax(p.lmax, need);
+    }
     const size_t sstride = (size_t)p.b_pad * p.Kpad;
     const size_t jstride = (size_t)p.b_pad * p.Kpad0;
     // Kpad0 and Kpad are multiples of 64: a pair never straddles the segment boundary. The
@@ -472,12 +501,14 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
       }
     }
     if (!p.digits) continue;
+    // the contraction vector: u, or u - d / 2 in increment mode
     for (int j = lane; j < p.nb; j += 32) {
-      const double v = j < n ? ub[j] : 0.0;
+      const double v = j < n ? (p.incr ? ub[j] - 0.5 * vb[j] : ub[j]) : 0.0;
       const float hi = (float)v;
       p.ufT[(size_t)j * p.b_pad + b] = make_float2(hi, (float)(v - (double)hi));
     }
-    for (int k = lane; k < p.nout; k += 32) p.out[(size_t)b * p.nout + k] = 0.0;
+    if (!p.incr)
+      for (int k = lane; k < p.nout; k += 32) p.out[(size_t)b * p.nout + k] = 0.0;
     if (lane == 0) {
       p.xexp[b] = e0;
       p.xexp[p.b_pad + b] = e1;
@@ -668,6 +699,7 @@ struct LuParams {
   int rung_all;          // -1, or the rung every active query of the launch is on (0 zero,
                          // 1 low, 2 FP64-accurate, 3 FP64-accurate chord step)
   int *Piv;              // [nq][nb]: pivot rows of the kept factorisation (chord)
+  double *dU;            // [nq][nb]: the update of each query's last iteration, or null
 };
 
 // Residual source of one Newton iteration (the precision ladder of the inexact Newton):
@@ -910,6 +942,7 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
           const double d = (double)x[s];
           dl += d * d;
           ub[k] += d;
+          if (p.dU) p.dU[(size_t)b * p.nb + k] = d;
         }
       }
       const double dn = sqrt(warp_sum(dl));
@@ -1039,6 +1072,7 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
         const double d = (double)xs[tid];
         dl = d * d;
         ub[tid] += d;
+        if (p.dU) p.dU[(size_t)b * p.nb + tid] = d;
       }
       dl = warp_sum(dl);
       if (lane == 0) red[w] = dl;
@@ -1323,6 +1357,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
         const double d = (double)xs[i];
         dl += d * d;
         ub[i] += d;
+        if (p.dU) p.dU[(size_t)b * p.nb + i] = d;
       }
       const double dn = sqrt(block_sum(dl, dred));
       qi.upd_norm = dn;
@@ -1588,7 +1623,7 @@ static void release_state(rb_ctx *ctx, MixedState *M) {
                   (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
                   (void *)M->Amu, (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn,
-                  (void *)M->Piv})
+                  (void *)M->Piv, (void *)M->dU})
     ctx_free(ctx, q);
   if (M->root == M) {
     for (auto &kv : M->buckets) {
@@ -1798,10 +1833,12 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   if (b_pad <= M->bcap) return RB_OK;
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
                   (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
-                  (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn, (void *)M->Piv})
+                  (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn, (void *)M->Piv,
+                  (void *)M->dU})
     ctx_free(ctx, q);
   M->Jaug = nullptr;
   M->Piv = nullptr;
+  M->dU = nullptr;
   M->Bmu = nullptr;
   M->Rn = nullptr;
   M->Rg = nullptr;
@@ -1842,6 +1879,8 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   }
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb, "pivot rows")) != RB_OK) return rc;
   M->Piv = (int *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "last updates")) != RB_OK) return rc;
+  M->dU = (double *)p;
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
   M->Jaug = (float *)p;
   const size_t groups = (size_t)(M->nb + 7) / 8;
@@ -1864,9 +1903,12 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
 
 static int launch_build_x(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
                           const rb_query_info *d_info, int mode, int digits, double *out, int nout,
-                          cudaStream_t st, int split = 1) {
+                          cudaStream_t st, int split = 1, int incr = 0) {
   BuildXParams bx{};
   bx.split = split;
+  bx.incr = incr;
+  bx.dU = M->dU;
+  bx.lmax = M->root->dev_words + 6;
   bx.o = ctx->ops;
   bx.theta = M->Th;
   bx.nsz = d_n;
@@ -1952,11 +1994,19 @@ static int launch_prep(rb_ctx *ctx, MixedState *M, const double *d_mu, const dou
 // default): the server orders a group's queries by iteration count, so only the rows that need
 // a contraction get one (rows past them may take overhanging tile rows, which their rung never
 // reads).
+// incr (chord steps, no Jacobian): the residual's convection part is updated by the increment
+// C(u, u) = C(u - d, u - d) + J^c(d) (u - d / 2) from the previous iteration's one (exact in
+// exact arithmetic: C is quadratic), with as many digit levels as d's size needs.
 static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, const double *d_u,
                           const rb_query_info *d_info, bool jac, bool exact, cudaStream_t st,
-                          int nq_jac = -1, int nq_exact = -1) {
+                          int nq_jac = -1, int nq_exact = -1, bool incr = false) {
   if (!jac && !exact) return RB_OK;
-  int rc = launch_build_x(ctx, M, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st, jac ? 1 : 0);
+  if (incr) {
+    cudaError_t e0 = cudaMemsetAsync(M->root->dev_words + 6, 0, 4, st);
+    if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "words");
+  }
+  int rc = launch_build_x(ctx, M, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st,
+                          jac ? 1 : 0, incr && exact && !jac ? 1 : 0);
   if (rc != RB_OK) return rc;
   TcGemmParams g = gemm_params(M, nq_jac >= 0 ? nq_jac : nq);
   g.n_tiles = M->Npad / kTcBN;
@@ -1991,6 +2041,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[0] = M->WR.wexp[0];
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
+  if (incr && !jac) g.lmax = M->root->dev_words + 6;
   mk = prof_begin(ctx, RB_K_GEMM_RES, st);
   e = launch_sliced(M, M->WR, g, ctx->sms, st, M->tune.st_sliced, sliced_variant(M));
   prof_end(ctx, mk, st);
@@ -2011,6 +2062,16 @@ static int elim_kind(const MixedState *M) {
 // Chord steps (Jacobian reuse from the second FP64-residual iteration on): every elimination
 // kernel keeps its factors and pivots when asked (warp, CTA per query, blocked); RB_CHORD=0
 // turns them off.
+// Chord steps take the residual's convection part as an increment on the previous one
+// (RB_INCREMENT=0: the full product at every step).
+static bool incr_residual() {
+  static const int on = [] {
+    const char *e = getenv("RB_INCREMENT");
+    return (e && *e) ? atoi(e) : 1;
+  }();
+  return on != 0;
+}
+
 static bool bucket_chord(const MixedState *M) {
   const char *e = getenv("RB_CHORD");
   if (e && *e && atoi(e) == 0) return false;
@@ -2227,6 +2288,7 @@ static LuParams solve_lu_params(rb_ctx *ctx, MixedState *M, const SolveArgs &a) 
   lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
   lp.chord = bucket_chord(M) ? 1 : 0;
   lp.Piv = M->Piv;
+  lp.dU = lp.chord && incr_residual() ? M->dU : nullptr;
   lp.rung_all = -1;
   return lp;
 }
@@ -2256,8 +2318,10 @@ static int solve_iteration(rb_ctx *ctx, const std::vector<Part> &parts, int it, 
   if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
   int rc;
   for (const Part &pt : parts) {
-    const bool jac = it >= 1 && !(it >= 3 && bucket_chord(pt.M));
-    if ((rc = mixed_contract(ctx, pt.M, pt.a.nq, pt.a.n, pt.a.u, pt.a.info, jac, it >= 2, st)) != RB_OK)
+    const bool chord = it >= 3 && bucket_chord(pt.M);
+    const bool jac = it >= 1 && !chord;
+    if ((rc = mixed_contract(ctx, pt.M, pt.a.nq, pt.a.n, pt.a.u, pt.a.info, jac, it >= 2, st, -1, -1,
+                             chord && incr_residual())) != RB_OK)
       return rc;
     LuParams lp = solve_lu_params(ctx, pt.M, pt.a);
     // every active query of a batch solve is on iteration `it`

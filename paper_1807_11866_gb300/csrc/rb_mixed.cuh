@@ -33,6 +33,8 @@ struct TcGemmParams {
   const float2 *ufT;     // sliced: u_b[j] as (hi, lo) floats, transposed [nj][b_pad]
   double *out;           // sliced: [b_pad][nk], accumulated with atomics
   int *err;              // device error word (bounded waits)
+  const int *lmax;       // sliced, one segment: if set, the highest digit level L = i + j of
+                         // the launch, read on the device (levels 2..*lmax, at most S[0] + 1)
 };
 
 cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &tmW,

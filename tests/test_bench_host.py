@@ -42,7 +42,8 @@ def test_roofline_work_counts_chord_steps():
         assert np.isclose(rl["k_tc_gemm<sliced>"]["achieved"], sliced / 1e-3 / 1e12)
         # the products issued: 3 split-BF16 products per Jacobian, 21 digit pairs per residual
         assert np.isclose(rl["k_tc_gemm<plain>"]["issued_tflops"], 3 * plain / 1e-3 / 1e12)
-        assert np.isclose(rl["k_tc_gemm<sliced>"]["issued_tflops"], 21 * sliced / 1e-3 / 1e12)
+        key = "issued_tflops_max" if bench.incremental_residual(1) else "issued_tflops"
+        assert np.isclose(rl["k_tc_gemm<sliced>"][key], 21 * sliced / 1e-3 / 1e12)
         assert rl["k_tc_gemm<sliced>"]["work"] == "algorithmic"
         assert np.isclose(rl["k_tc_gemm<sliced>"]["frac"],
                           rl["k_tc_gemm<sliced>"]["achieved"] / rl["k_tc_gemm<sliced>"]["peak"])

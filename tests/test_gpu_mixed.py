@@ -135,7 +135,9 @@ def test_chord_steps(rb, n, elim, monkeypatch):
     warp-per-query elimination, by the CTA-per-query one (elim = 4; chord solve with 2, 3 or 4
     row slots) or by the blocked one (elim = 2, 3: 32- and 16-column panels, the forward
     substitution panel by panel with each panel's interchanges): the converged velocity and
-    pressure are the oracle's with and without it, and it costs at most one extra iteration."""
+    pressure are the oracle's with and without it, and it costs at most one extra iteration.
+    The chord steps' residual is also taken as an increment on the previous one (RB_INCREMENT=1,
+    the default) or as the full product (0): the same iterations and accuracy."""
     if elim:
         monkeypatch.setenv("RB_ELIMINATION", elim)
     wl = synth.WORKLOADS["sweep_n50"]
@@ -145,16 +147,22 @@ def test_chord_steps(rb, n, elim, monkeypatch):
     o = oracle.Oracle.from_set(ops)
     u_ref, p_ref, _ = o.solve(mu, threads=8)
     res = {}
-    for chord in ("0", "1"):
+    for chord, incr in (("0", "1"), ("1", "0"), ("1", "1")):
         monkeypatch.setenv("RB_CHORD", chord)
+        monkeypatch.setenv("RB_INCREMENT", incr)
         with rb.Context(rb.RB_PREC_MIXED) as ctx:
             ctx.load_set(ops)
-            res[chord] = ctx.rb_solve(mu)
+            res[chord + incr] = ctx.rb_solve(mu)
     for u, p, info in res.values():
         assert np.all(info["status"] == 0)
         assert rel(u, u_ref).max() <= TOL_MIXED
         assert rel(p, p_ref).max() <= 10 * TOL_MIXED
-    assert np.all(res["1"][2]["iters"] <= res["0"][2]["iters"] + 1)
+    assert np.all(res["11"][2]["iters"] <= res["01"][2]["iters"] + 1)
+    # the chord steps' residual as an increment on the previous one (C quadratic: exact up to
+    # the digit levels it keeps) costs no iteration and keeps the velocity at the full product's
+    # accuracy
+    assert np.array_equal(res["11"][2]["iters"], res["10"][2]["iters"])
+    assert rel(res["11"][0], u_ref).max() <= 10 * max(rel(res["10"][0], u_ref).max(), 1e-13)
 
 
 def test_manufactured_mixed(rb):
