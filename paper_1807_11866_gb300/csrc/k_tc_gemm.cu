@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
               tma_load_2d_pair(sa, &tmX, cbar, kk * kBK, xi * p.b_pad + mr);
               tma_load_2d_pair(sb, &tmW, cbar, kk * kBK, wj * p.n_pad + nr);
             } else {
-              mbar_expect_tx(&full[s], SM::kStage);
+              mbar_expect_tx(&full[s], SM::kStage + ((step == 0 && blockIdx.x == 0) ? p.tx_extra : 0u));
               tma_load_2d(sa, &tmX, &full[s], kk * kBK, xi * p.b_pad + mr);
               tma_load_2d(sb, &tmW, &full[s], kk * kBK, wj * p.n_pad + nr);
             }

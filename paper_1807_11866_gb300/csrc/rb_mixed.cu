@@ -2020,6 +2020,10 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   int mk;
   cudaError_t e;
   if (jac) {
+    // RB_TEST_WAIT_DEFICIT=1 (tests of the failure path only): the single-CTA Jacobian GEMM's
+    // first stage waits for 16 bytes that never come, so the bounded wait gives up
+    const char *td = getenv("RB_TEST_WAIT_DEFICIT");
+    g.tx_extra = (td && atoi(td) == 1 && !use_pairs_plain(M)) ? 16u : 0u;
     mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
     e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain, use_pairs_plain(M));
     prof_end(ctx, mk, st);
@@ -2035,6 +2039,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
     g.m_tiles = ge.m_tiles;
     g.nq = ge.nq;
   }
+  g.tx_extra = 0;
   g.kb[1] = M->kb1;
   g.n_tiles = M->WR.Npad / kTcBN;
   g.n_pad = M->WR.Npad;

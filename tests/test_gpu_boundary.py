@@ -111,6 +111,7 @@ def test_solve_device_returns_before_the_work_completes(rb, sized):
     u = d_u.cpu().numpy()
     p = d_p.cpu().numpy()
     info = d_info.cpu().numpy().view(rb.INFO_DTYPE).reshape(1000)
+    # the same solve as rb_solve's, up to the order of the sliced GEMM's FP64 atomic additions
     np.testing.assert_array_equal(info["status"], info_ref["status"])
-    np.testing.assert_array_equal(u, u_ref)
-    np.testing.assert_array_equal(p, p_ref)
+    assert rel(u, u_ref).max() <= 1e-13
+    assert rel(p, p_ref).max() <= 1e-12
