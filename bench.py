@@ -252,6 +252,16 @@ def main():
                 "roofline", "rooflines", "autotune", "plain_fp64", "speedup_vs_plain_fp64",
                 "cpu_baseline", "rel_err_vs_oracle")
         line[LARGEST] = {k: sub[k] for k in keep if k in sub}
+    if args.large and wl.name != SMALLEST and world == 1:
+        # the plain single query (latency): one query of the n = 20 set solved to 1e-12
+        small = synth.WORKLOADS[SMALLEST]
+        sub = measure(args, small, 1, 50, 5, 0, 1, local, dev, recon=False, cpu_seconds=2.0)
+        line[SMALLEST] = {k: sub[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                              "config", "latency_ms", "iters", "status_ok", "e2e",
+                                              "gpu_launches", "kernels", "plain_fp64",
+                                              "speedup_vs_plain_fp64", "cpu_baseline",
+                                              "rel_err_vs_oracle") if k in sub}
+        line[SMALLEST]["latency_us"] = 1e3 * sub["ms_per_step"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -259,6 +269,7 @@ def main():
 
 
 LARGEST = "dense_n300"        # the largest configuration of the metric's range (n = 300)
+SMALLEST = "single_n20"       # the plain single query (latency)
 LARGE_STEPS, LARGE_WARMUP = 3, 3
 
 
@@ -276,7 +287,8 @@ def measure(args, wl, batch, steps, warmup, rank, world, local, dev, recon, cpu_
     if parity_sample:  # the corners of the parameter box take the last four queries
         q.mu[-4:] = synth.corner_queries(wl)
     prec = PREC[args.precision]
-    ctx = rb.Context(precision=prec, device=local, theta_family=wl.theta_family)
+    tol_res = 1e-12 if wl.manufactured else None  # the single query is solved to 1e-12
+    ctx = rb.Context(precision=prec, device=local, theta_family=wl.theta_family, tol_res=tol_res)
     ctx.load_set(ops)
     m = ctx.m
     stream = torch.cuda.Stream(device=dev)
@@ -390,7 +402,7 @@ def measure(args, wl, batch, steps, warmup, rank, world, local, dev, recon, cpu_
     ctx.close()
     del d_mu, d_n, d_u, d_p, d_info
     if rank == 0 and not args.no_plain and prec != 0:
-        line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, steps)
+        line["plain_fp64"] = plain_fp64(rb, ops, q, batch, dev, flush, steps, tol_res)
         line["speedup_vs_plain_fp64"] = value / line["plain_fp64"]["value"]
     del flush
     torch.cuda.empty_cache()
@@ -697,7 +709,7 @@ def pressure_reconstruction(rb, ctx, wl, batch, d_u, d_n, p_rec, kprof, stream, 
                      "basis, second construction of Sec. 4.2)"}
 
 
-def plain_fp64(rb, ops, q, batch, dev, flush, steps):
+def plain_fp64(rb, ops, q, batch, dev, flush, steps, tol_res=None):
     """The plain FP64 GPU path (one CTA per query, every step in FP64) on the same batch, or on
     its first two waves (2 x 152 queries) when one FP64 query-iteration exceeds 1 GFLOP."""
     import torch
@@ -705,7 +717,8 @@ def plain_fp64(rb, ops, q, batch, dev, flush, steps):
     if 2.0 * wl.q_c * wl.n_max ** 3 > 1e9:
         batch = min(batch, 304)
         q = synth.QuerySet(q.mu[:batch].copy(), q.n[:batch].copy())
-    ctx = rb.Context(precision=rb.RB_PREC_FP64, device=dev.index, theta_family=wl.theta_family)
+    ctx = rb.Context(precision=rb.RB_PREC_FP64, device=dev.index, theta_family=wl.theta_family,
+                     tol_res=tol_res)
     ctx.load_set(ops)
     stream = torch.cuda.Stream(device=dev)
     d_mu = torch.from_numpy(q.mu).to(dev)

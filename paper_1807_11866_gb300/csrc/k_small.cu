@@ -1,0 +1,232 @@
+// k_small.cu -- the whole mixed-precision Newton solve of a small system (n <= 32) in one launch,
+// one CTA per query, on the CUDA cores.
+//
+// For small reduced sizes the tensor-core pipeline (operand builds, two GEMMs, assembly and
+// elimination launched per iteration) is bound by launch latency; a single query at n = 20 then
+// costs far more than its arithmetic. Here one CTA keeps its query's state in shared memory and
+// runs every Newton iteration (Sec. 3.6 tensor Jacobian, Sec. 4.1 dense solve, Sec. 6 stopping
+// rule) without leaving the kernel:
+//   J^c[k][j] = sum_{q,l} theta^c_q u_l D~_q[k][j][l]        (double-float, D~ from L2)
+//   R[k]      = sum_j (A(mu)[k][j] + J^c[k][j] / 2) u_j - f(mu)[k]   (Euler identity of the
+//               quadratic term: C_mu(u, u) = J^c(u) u / 2; double-float, FP64-accurate)
+//   [fl32(A(mu) + J^c) | -R] eliminated in FP32 by one warp (partial pivoting), u += delta.
+// The Jacobian is exact up to FP32 rounding and the residual FP64-accurate, so the iteration
+// converges quadratically to the FP64 solution until the FP32 factorisation's rate ~kappa 2^-24
+// takes over; the stopping rule is tested on the FP64 norms as on every other path.
+#include <cuda_runtime.h>
+
+#include "rb_ctx.h"
+#include "rb_small.cuh"
+
+namespace rb {
+
+namespace {
+
+constexpr int kSmallThreads = 512;
+constexpr int kSmallWarps = kSmallThreads / 32;
+
+// ld of the augmented matrix [J | -R] in shared memory (the warp elimination's layout)
+__host__ __device__ inline int small_ld(int nb) {
+  int ld = (nb + 1 + 3) & ~3;
+  if (((ld >> 2) & 1) == 0) ld += 4;
+  return ld;
+}
+
+// shared-memory carve-up (bytes); every block 16-byte aligned
+struct SmallSmem {
+  int th, u, fm, xs, am, t, jaug, pseq, red, total;
+  __host__ __device__ SmallSmem(const DevOps &o, int nb) {
+    auto al = [](int b) { return (b + 15) & ~15; };
+    int p = 0;
+    th = p; p += al(8 * o.n_theta);
+    u = p; p += al(8 * nb);
+    fm = p; p += al(8 * nb);
+    xs = p; p += al(8 * o.q_c * nb);        // theta^c_q u_l as double-float
+    am = p; p += al(8 * nb * nb);           // A(mu) as double-float
+    t = p; p += al(8 * nb * nb);            // A(mu) + J^c / 2 as double-float
+    jaug = p; p += al(4 * nb * small_ld(nb));
+    pseq = p; p += al(4 * ((nb + 3) & ~3));
+    red = p; p += al(8 * 2 * kSmallWarps + 16);
+    total = p;
+  }
+};
+
+// sum over the block (kSmallWarps warps) in a fixed order, valid in every thread; red holds
+// kSmallWarps doubles
+__device__ __forceinline__ double small_block_sum(double v, double *red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kSmallWarps; ++i) s += red[i];
+  return s;
+}
+
+}  // namespace
+
+size_t small_smem_bytes(const DevOps &o, int nb) { return (size_t)SmallSmem(o, nb).total; }
+
+__global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const DevOps &o = p.o;
+  const int nb = p.nb;
+  const SmallSmem L(o, nb);
+  double *th = reinterpret_cast<double *>(sm + L.th);
+  double *u = reinterpret_cast<double *>(sm + L.u);
+  double *fm = reinterpret_cast<double *>(sm + L.fm);
+  float2 *xs = reinterpret_cast<float2 *>(sm + L.xs);
+  float2 *am = reinterpret_cast<float2 *>(sm + L.am);
+  float2 *tm = reinterpret_cast<float2 *>(sm + L.t);
+  float *J = reinterpret_cast<float *>(sm + L.jaug);
+  int *pseq = reinterpret_cast<int *>(sm + L.pseq);
+  double *red = reinterpret_cast<double *>(sm + L.red);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ld = small_ld(nb);
+  const size_t nn = (size_t)nb * nb;
+
+  for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
+    const int n = p.nsz ? p.nsz[b] : o.n_max;
+    if (n < 1 || n > nb) {  // outside this launch's size range: rejected, untouched otherwise
+      if (tid == 0 && p.info) {
+        rb_query_info q = {RB_Q_REJECTED, 0, RB_PREC_MIXED, 0, 0.0, 0.0};
+        p.info[b] = q;
+      }
+      for (int i = tid; i < o.n_max; i += blockDim.x) p.u[(size_t)b * o.n_max + i] = 0.0;
+      continue;
+    }
+    // per-query data: theta, f(mu), A(mu) (Sec. 2.4, Sec. 3.5), u = 0
+    if (p.theta) {
+      for (int i = tid; i < o.n_theta; i += blockDim.x) th[i] = p.theta[(size_t)b * o.n_theta + i];
+    } else {
+      theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
+    }
+    __syncthreads();
+    double fn2 = 0.0;
+    for (int k = tid; k < nb; k += blockDim.x) {
+      double s = 0.0;
+      if (k < n)
+        for (int q = 0; q < o.q_f; ++q) s = fma(th[o.q_a + o.q_c + q], o.f[(size_t)q * o.n_max + k], s);
+      fm[k] = s;
+      fn2 += s * s;
+      u[k] = 0.0;
+    }
+    for (size_t e = tid; e < nn; e += blockDim.x) {
+      float h = 0.f, l = 0.f;
+      const int k = (int)(e / nb), j = (int)(e - (size_t)k * nb);
+      if (k < n && j < n)
+        for (int q = 0; q < o.q_a; ++q) {
+          float th_h, th_l;
+          df_split(th[q], th_h, th_l);
+          const float2 a = p.A2[(size_t)q * nn + e];
+          df_fma(h, l, a.x, a.y, th_h, th_l);
+        }
+      float s, ee;
+      two_sum(h, l, s, ee);
+      am[e] = make_float2(s, ee);
+    }
+    const double fscale = fmax(1.0, sqrt(small_block_sum(fn2, red)));  // block_sum syncs
+    rb_query_info qi = {RB_Q_NOT_CONVERGED, 0, RB_PREC_MIXED, 0, 0.0, 0.0};
+    bool done = false;
+    while (!done) {
+      // xs = theta^c (x) u in double-float
+      for (int i = tid; i < o.q_c * nb; i += blockDim.x) {
+        const int q = i / nb, l = i - q * nb;
+        const double v = l < n ? th[o.q_a + q] * u[l] : 0.0;
+        float h, lo;
+        df_split(v, h, lo);
+        xs[i] = make_float2(h, lo);
+      }
+      __syncthreads();
+      // J^c and T = A(mu) + J^c / 2; J = fl32(A(mu) + J^c) into the augmented matrix
+      const bool zero = qi.iters == 0;  // u = 0: J^c = 0
+      for (size_t e = tid; e < nn; e += blockDim.x) {
+        const int k = (int)(e / nb), j = (int)(e - (size_t)k * nb);
+        float h = 0.f, l = 0.f;
+        if (!zero && k < n && j < n) {
+          const float2 *D = p.Dt2 + e;
+          const int K = o.q_c * nb;
+#pragma unroll 4
+          for (int i = 0; i < K; ++i) {
+            const float2 x = xs[i];
+            const float2 d = __ldg(D + (size_t)i * nn);
+            df_fma(h, l, d.x, d.y, x.x, x.y);
+          }
+        }
+        float s, ee;
+        two_sum(h, l, s, ee);  // J^c[k][j] = s + ee
+        const float2 a = am[e];
+        float th2 = a.x, tl2 = a.y;
+        df_add(th2, tl2, 0.5f * s, 0.5f * ee);
+        tm[e] = make_float2(th2, tl2);
+        float jh = a.x, jl = a.y;
+        df_add(jh, jl, s, ee);
+        if (k < n && j < n) J[k * ld + j] = jh + jl;
+      }
+      __syncthreads();
+      // R[k] = sum_j T[k][j] u_j - f[k], one warp per row; -R into column n
+      double r2 = 0.0;
+      for (int k = w; k < n; k += kSmallWarps) {
+        float h = 0.f, l = 0.f;
+        for (int j = lane; j < n; j += 32) {
+          float uh, ul;
+          df_split(u[j], uh, ul);
+          const float2 t = tm[(size_t)k * nb + j];
+          df_fma(h, l, t.x, t.y, uh, ul);
+        }
+        const double r = df_warp_sum(h, l) - fm[k];
+        if (lane == 0) {
+          J[k * ld + n] = (float)(-r);
+          r2 += r * r;
+        }
+      }
+      const double rn = sqrt(small_block_sum(r2, red));  // syncs: J complete
+      qi.iters += 1;
+      qi.res_norm = rn;
+      // elimination and update by warp 0 (n <= 32: one row per lane)
+      if (w == 0) {
+        int status = RB_Q_NOT_CONVERGED;
+        double dn = 0.0;
+        if (!isfinite(rn)) {
+          status = RB_Q_NONFINITE;
+        } else {
+          float x[1];
+          if (gepp_aug_warp<1>(J, ld, n, x, pseq)) {
+            status = RB_Q_SINGULAR;
+          } else {
+            const double d = lane < n ? (double)x[0] : 0.0;
+            if (lane < n) u[lane] += d;
+            dn = sqrt(warp_sum(d * d));
+            if (!isfinite(dn)) status = RB_Q_NONFINITE;
+            else if (dn <= p.tol_upd && rn <= p.tol_res * fscale) status = RB_Q_OK;
+          }
+        }
+        if (lane == 0) {
+          red[2 * kSmallWarps] = dn;
+          reinterpret_cast<int *>(red + 2 * kSmallWarps + 1)[0] = status;
+        }
+      }
+      __syncthreads();
+      qi.upd_norm = red[2 * kSmallWarps];
+      qi.status = reinterpret_cast<const int *>(red + 2 * kSmallWarps + 1)[0];
+      done = qi.status != RB_Q_NOT_CONVERGED || qi.iters >= p.max_iter;
+      __syncthreads();  // red and the shared state are reused
+    }
+    for (int i = tid; i < o.n_max; i += blockDim.x) p.u[(size_t)b * o.n_max + i] = i < n ? u[i] : 0.0;
+    if (tid == 0 && p.info) p.info[b] = qi;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_newton_small(const SmallParams &p, int sms, cudaStream_t st) {
+  const size_t smem = small_smem_bytes(p.o, p.nb);
+  cudaError_t e = cudaFuncSetAttribute(k_newton_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = p.nq < 4 * sms ? (p.nq > 0 ? p.nq : 1) : 4 * sms;
+  k_newton_small<<<grid, kSmallThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace rb

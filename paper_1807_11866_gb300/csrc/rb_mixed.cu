@@ -33,6 +33,7 @@
 
 #include "rb_ctx.h"
 #include "rb_mixed.cuh"
+#include "rb_small.cuh"
 
 namespace rb {
 
@@ -56,6 +57,7 @@ struct MixedState {
   float2 *A2 = nullptr;         // [q_a][nb][nb] A_q as double-float (hi, lo)
   float2 *As2 = nullptr;        // [q_a][m][nb] As_q as double-float
   float2 *B2 = nullptr;         // [q_b][m][m] B_q as double-float
+  float2 *Dt2 = nullptr;        // root, n_max <= kSmallMaxN: D~ as double-float [q_c][l][k][j]
   // batch scratch
   int bcap = 0;
   __nv_bfloat16 *Xj = nullptr, *Xd = nullptr;  // Xj: [3][bcap][Kpad0] (hi, hi, lo)
@@ -1620,7 +1622,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve(PresSolveParams p) 
 // host side
 static void release_state(rb_ctx *ctx, MixedState *M) {
   for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2,
-                  (void *)M->B2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
+                  (void *)M->B2, (void *)M->Dt2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
                   (void *)M->Amu, (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn,
                   (void *)M->Piv, (void *)M->dU})
@@ -2687,6 +2689,57 @@ int mixed_solve_status(rb_ctx *ctx, int wait) {
   return RB_OK;
 }
 
+// Small operator sets (n_max <= kSmallMaxN) and batches of at most a few queries per SM: the
+// whole Newton solve of each query in one launch (k_newton_small, one CTA per query) instead of
+// the tensor-core pipeline, whose per-iteration launches dominate there; pressure by the FP64
+// recovery kernel. RB_SMALL = 0 / 1 turns the choice off / forces it for any small set.
+static bool use_small_path(const rb_ctx *ctx, int nq) {
+  if (ctx->ops.n_max > kSmallMaxN) return false;
+  const char *e = getenv("RB_SMALL");
+  if (e && *e) return atoi(e) != 0;
+  return nq <= 2 * ctx->sms;
+}
+
+static int solve_small(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq,
+                       const int *d_n, double *d_u, double *d_p, rb_query_info *info,
+                       cudaStream_t st) {
+  MixedState *R = ctx->mixed;
+  const DevOps &o = ctx->ops;
+  int rc;
+  if ((rc = mixed_layouts(ctx, R, st)) != RB_OK) return rc;
+  const int nb = o.n_max;
+  if (!R->Dt2) {  // D~ as double-float, [q_c][l][k][j] with the n_max strides
+    void *p;
+    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_c * nb * nb * nb, "D~ (double-float)")) != RB_OK)
+      return rc;
+    R->Dt2 = (float2 *)p;
+    k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.Dt, R->Dt2, (size_t)o.q_c * nb * nb * nb);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "D~ (double-float)");
+  }
+  SmallParams sp{};
+  sp.o = o;
+  sp.mu = d_theta ? nullptr : d_mu;
+  sp.theta = d_theta;
+  sp.nsz = d_n;
+  sp.nq = nq;
+  sp.nb = nb;
+  sp.max_iter = ctx->cfg.max_iter;
+  sp.tol_upd = ctx->cfg.tol_update;
+  sp.tol_res = ctx->cfg.tol_res;
+  sp.Dt2 = R->Dt2;
+  sp.A2 = R->A2;
+  sp.u = d_u;
+  sp.info = info;
+  const int mk = prof_begin(ctx, RB_K_NEWTON_SMALL, st);
+  const cudaError_t e = launch_newton_small(sp, ctx->sms, st);
+  prof_end(ctx, mk, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_small");
+  if (d_p && o.m > 0 && o.B)  // the FP64 recovery of Eq. sup-vvar for the converged queries
+    return solve_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
+  return RB_OK;
+}
+
 int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, const int *d_n,
                 const int *h_n, double *d_u, double *d_p, rb_query_info *d_info, cudaStream_t st) {
   int rc = mixed_root(ctx, st);
@@ -2697,6 +2750,7 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   const DevOps &o = ctx->ops;
   rb_query_info *info = d_info ? d_info : own_info(ctx, nq);
   if (!info) return set_error(ctx, RB_ERR_OOM, "info scratch");
+  if (use_small_path(ctx, nq)) return solve_small(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
   SolvePlan pl;
   pl.caller = {d_mu, d_theta, nq, d_n, d_u, d_p, info};
   pl.pres = d_p && o.m > 0 && o.B;

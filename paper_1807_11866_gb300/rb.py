@@ -33,7 +33,7 @@ EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_
            "rb_save_operators", "rb_load_operator_file"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>",
-              "k_newton_system", "k_prep", "k_reconstruct"]
+              "k_newton_system", "k_prep", "k_reconstruct", "k_newton_small"]
 
 
 class rb_operators(ctypes.Structure):
