@@ -22,7 +22,8 @@ namespace rb {
 
 namespace {
 
-constexpr int kSmallThreads = 512;
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallUnroll = 8;  // loads of D~ in flight per thread (the loop is L2-latency bound)
 constexpr int kSmallWarps = kSmallThreads / 32;
 
 // ld of the augmented matrix [J | -R] in shared memory (the warp elimination's layout)
@@ -34,7 +35,7 @@ __host__ __device__ inline int small_ld(int nb) {
 
 // shared-memory carve-up (bytes); every block 16-byte aligned
 struct SmallSmem {
-  int th, u, fm, xs, am, t, jaug, pseq, red, total;
+  int th, u, fm, xs, am, t, jaug, part, pseq, red, total;
   __host__ __device__ SmallSmem(const DevOps &o, int nb) {
     auto al = [](int b) { return (b + 15) & ~15; };
     int p = 0;
@@ -45,6 +46,7 @@ struct SmallSmem {
     am = p; p += al(8 * nb * nb);           // A(mu) as double-float
     t = p; p += al(8 * nb * nb);            // A(mu) + J^c / 2 as double-float
     jaug = p; p += al(4 * nb * small_ld(nb));
+    part = p; p += al(8 * kSmallThreads);   // partial sums of J^c over parts of the (q, l) range
     pseq = p; p += al(4 * ((nb + 3) & ~3));
     red = p; p += al(8 * 2 * kSmallWarps + 16);
     total = p;
@@ -80,11 +82,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   float2 *am = reinterpret_cast<float2 *>(sm + L.am);
   float2 *tm = reinterpret_cast<float2 *>(sm + L.t);
   float *J = reinterpret_cast<float *>(sm + L.jaug);
+  float2 *part = reinterpret_cast<float2 *>(sm + L.part);
   int *pseq = reinterpret_cast<int *>(sm + L.pseq);
   double *red = reinterpret_cast<double *>(sm + L.red);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int ld = small_ld(nb);
   const size_t nn = (size_t)nb * nb;
+  // J^c: thread t sums element e = t % E over part t / E of the (q, l) range (E = nn rounded up
+  // to a warp; P parts fill the block), then the parts add up in a fixed order
+  const int E = (int)((nn + 31) & ~(size_t)31);
+  const int P = kSmallThreads / E > 0 ? kSmallThreads / E : 1;
+  const int Kc = o.q_c * nb;
 
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
     const int n = p.nsz ? p.nsz[b] : o.n_max;
@@ -141,19 +149,33 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       __syncthreads();
       // J^c and T = A(mu) + J^c / 2; J = fl32(A(mu) + J^c) into the augmented matrix
       const bool zero = qi.iters == 0;  // u = 0: J^c = 0
+      if (!zero) {
+        for (int t = tid; t < P * E; t += blockDim.x) {
+          const int e = t % E, pt = t / E;
+          const int k = e / nb, j = e - k * nb;
+          float h = 0.f, l = 0.f;
+          if (e < (int)nn && k < n && j < n) {
+            const int i0 = (int)(((long long)Kc * pt) / P), i1 = (int)(((long long)Kc * (pt + 1)) / P);
+            const float2 *D = p.Dt2 + e;
+#pragma unroll kSmallUnroll
+            for (int i = i0; i < i1; ++i) {
+              const float2 x = xs[i];
+              const float2 d = __ldg(D + (size_t)i * nn);
+              df_fma(h, l, d.x, d.y, x.x, x.y);
+            }
+          }
+          part[t] = make_float2(h, l);
+        }
+        __syncthreads();
+      }
       for (size_t e = tid; e < nn; e += blockDim.x) {
         const int k = (int)(e / nb), j = (int)(e - (size_t)k * nb);
         float h = 0.f, l = 0.f;
-        if (!zero && k < n && j < n) {
-          const float2 *D = p.Dt2 + e;
-          const int K = o.q_c * nb;
-#pragma unroll 4
-          for (int i = 0; i < K; ++i) {
-            const float2 x = xs[i];
-            const float2 d = __ldg(D + (size_t)i * nn);
-            df_fma(h, l, d.x, d.y, x.x, x.y);
+        if (!zero)
+          for (int pt = 0; pt < P; ++pt) {
+            const float2 v = part[pt * E + e];
+            df_add(h, l, v.x, v.y);
           }
-        }
         float s, ee;
         two_sum(h, l, s, ee);  // J^c[k][j] = s + ee
         const float2 a = am[e];

@@ -141,6 +141,7 @@ template <int MODE, int BN, int STAGES, bool PAIR>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
               TcGemmParams p) {
+  if (p.run_if && *(volatile const int *)p.run_if == 0) return;  // uniform over the grid
   extern __shared__ uint8_t smem_raw[];
   using SM = TcSmem<BN, STAGES, PAIR>;
   constexpr int kBMT = PAIR ? 2 * kBM : kBM;  // rows of an output tile

@@ -74,6 +74,7 @@ struct MixedState {
   float *Jaug = nullptr;        // [bcap][nb][aug_ld(nb)] augmented Newton matrices (or factors)
   int *Piv = nullptr;           // [bcap][nb] pivot rows of the factors kept for chord steps
   double *dU = nullptr;         // [bcap][nb] each query's last update (chord steps' residual)
+  int *refresh = nullptr;       // raised by a chord step that contracts too slowly
   double2 *Rn = nullptr;        // [bcap] (unused, max(1, ||f(mu)||)) of the queries
   double *Rg = nullptr;         // [bcap][(nb + 7) / 8] row-group sums of R^2 (in Rn's block)
   CUtensorMap tmXj, tmXd;
@@ -480,8 +481,10 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
         const int q1 = l + 1 < p.nb ? q : q + 1, l1 = l + 1 < p.nb ? l + 1 : 0;
         const double x0 = xval(q, l), x1 = xval(q1, l1);
         if (p.mode == 0 && p.split) {
-          // split BF16 operand of the Jacobian GEMM: [x_hi | x_hi | x_lo]
-          const float f0 = (float)x0, f1 = (float)x1;
+          // split BF16 operand of the Jacobian GEMM: [x_hi | x_hi | x_lo], always from u
+          const double y0 = p.incr ? ((q < o.q_c && l < n) ? tc[q] * ub[l] : 0.0) : x0;
+          const double y1 = p.incr ? ((q1 < o.q_c && l1 < n) ? tc[q1] * ub[l1] : 0.0) : x1;
+          const float f0 = (float)y0, f1 = (float)y1;
           const __nv_bfloat162 hi = __floats2bfloat162_rn(f0, f1);
           const __nv_bfloat162 lo =
               __floats2bfloat162_rn(f0 - __low2float(hi), f1 - __high2float(hi));
@@ -702,6 +705,9 @@ struct LuParams {
                          // 1 low, 2 FP64-accurate, 3 FP64-accurate chord step)
   int *Piv;              // [nq][nb]: pivot rows of the kept factorisation (chord)
   double *dU;            // [nq][nb]: the update of each query's last iteration, or null
+  int *refresh;          // chord steps: raised when a query's chord step contracts too slowly
+                         // (that query factors a fresh Jacobian at its next iteration), or null
+  const int *run_if;     // k_newton_system<., 4>: runs only if *run_if != 0
 };
 
 // Residual source of one Newton iteration (the precision ladder of the inexact Newton):
@@ -719,11 +725,23 @@ __device__ __forceinline__ int rung_of(int rmode, int iters) {
 // >= 3), a query reuses the factorisation of its first one (count 2), kept in its [J | -R]
 // block with the pivot rows in Piv and marked by Rn[b].x = 1 (0 from the query's start); only
 // the residual is new.
+// A chord step that shrinks the update by less than kChordSlow (a Jacobian that has drifted
+// from the iterate, far from the root) marks its query with Rn[b].x = 2: its next iteration
+// factors the Jacobian at its current iterate and keeps those factors instead.
 __device__ __forceinline__ bool chord_step(const LuParams &p, int b, int iters) {
   return p.chord && p.rmode < 0 && iters >= 3 && p.Rn[b].x == 1.0;
 }
-__device__ __forceinline__ bool chord_keep(const LuParams &p, int iters) {
-  return p.chord && p.rmode < 0 && iters == 2;
+__device__ __forceinline__ bool chord_keep(const LuParams &p, int b, int iters) {
+  return p.chord && p.rmode < 0 && (iters == 2 || (iters >= 3 && p.Rn[b].x == 2.0));
+}
+constexpr double kChordSlow = 0.25;
+// after a chord step of query b (one thread): dn = ||delta_k||, prev = ||delta_{k-1}||
+__device__ __forceinline__ void chord_watch(const LuParams &p, int b, bool chord, bool converged,
+                                            double dn, double prev) {
+  if (chord && !converged && p.refresh && dn > kChordSlow * prev) {
+    p.Rn[b].x = 2.0;
+    atomicOr(p.refresh, 1);
+  }
 }
 
 
@@ -835,6 +853,7 @@ __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, 
 constexpr int system_blocks(int fixed) { return fixed == 0 || fixed == 3 ? 3 : 2; }
 template <bool EVAL, int FIXED>
 __global__ void __launch_bounds__(kThreads, system_blocks(FIXED)) k_newton_system(LuParams p) {
+  if (FIXED == 4 && *(volatile const int *)p.run_if == 0) return;  // no query refreshes
   const int lane = threadIdx.x & 31;
   const int G = (p.nb + 7) >> 3;
   const long long units = (long long)p.nq * G;
@@ -853,8 +872,12 @@ __global__ void __launch_bounds__(kThreads, system_blocks(FIXED)) k_newton_syste
       r2 = newton_rows8<kResLow, EVAL, true>(p, b, n, k0);
     } else if (FIXED == 2) {
       r2 = newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
-    } else if (FIXED == 3) {
+    } else if (FIXED == 3) {  // chord steps; a query refreshing its Jacobian is left to FIXED 4
+      if (!chord_step(p, b, qi.iters)) continue;
       r2 = newton_rows8<kResExact, EVAL, false>(p, b, n, k0);
+    } else if (FIXED == 4) {  // the queries of a chord launch that refresh their Jacobian
+      if (chord_step(p, b, qi.iters)) continue;
+      r2 = newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
     } else {
       const int rm = rung_of(p.rmode, qi.iters);
       r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL, true>(p, b, n, k0)
@@ -908,7 +931,7 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
     const int n = p.nsz ? p.nsz[b] : p.nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
-    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, qi.iters);
+    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, b, qi.iters);
     const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
     float4 *gJ = reinterpret_cast<float4 *>(p.Jaug + (size_t)b * p.nb * ld);
     const int n4 = n * ld / 4;
@@ -948,9 +971,11 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
         }
       }
       const double dn = sqrt(warp_sum(dl));
+      const double prev = qi.upd_norm;
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
       else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+      if (lane == 0) chord_watch(p, b, chord, qi.status != RB_Q_NOT_CONVERGED, dn, prev);
     }
     if (lane == 0) {
       p.info[b] = qi;
@@ -1042,7 +1067,7 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
     const int n = p.nsz ? p.nsz[b] : p.nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
-    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, qi.iters);
+    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, b, qi.iters);
     const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
     float4 *gJ = reinterpret_cast<float4 *>(p.Jaug + (size_t)b * p.nb * ld);
     const int n4 = n * ld / 4;
@@ -1082,9 +1107,11 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
       double tot = 0.0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
       const double dn = sqrt(tot);
+      const double prev = qi.upd_norm;
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
       else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+      if (tid == 0) chord_watch(p, b, chord, qi.status != RB_Q_NOT_CONVERGED, dn, prev);
     }
     if (tid == 0) {
       p.info[b] = qi;
@@ -1148,7 +1175,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
     const int n = p.nsz ? p.nsz[b] : nb;
     double *ub = p.u + (size_t)b * p.o.n_max;
     const int rm = rung_of(p.rmode, qi.iters);
-    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, qi.iters);
+    const bool chord = chord_step(p, b, qi.iters), keep = chord_keep(p, b, qi.iters);
     const double rn = residual_norm(p, b, n), fscale = p.Rn[b].y;
     float *M = p.Jaug + (size_t)b * nb * lda;
     bool sing = !isfinite(rn);
@@ -1362,9 +1389,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
         if (p.dU) p.dU[(size_t)b * p.nb + i] = d;
       }
       const double dn = sqrt(block_sum(dl, dred));
+      const double prev = qi.upd_norm;
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
       else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
+      if (tid == 0) chord_watch(p, b, chord, qi.status != RB_Q_NOT_CONVERGED, dn, prev);
     }
     if (tid == 0) {
       p.info[b] = qi;
@@ -1625,7 +1654,7 @@ static void release_state(rb_ctx *ctx, MixedState *M) {
                   (void *)M->B2, (void *)M->Dt2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
                   (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
                   (void *)M->Amu, (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn,
-                  (void *)M->Piv, (void *)M->dU})
+                  (void *)M->Piv, (void *)M->dU, (void *)M->refresh})
     ctx_free(ctx, q);
   if (M->root == M) {
     for (auto &kv : M->buckets) {
@@ -1836,11 +1865,12 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
                   (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
                   (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn, (void *)M->Piv,
-                  (void *)M->dU})
+                  (void *)M->dU, (void *)M->refresh})
     ctx_free(ctx, q);
   M->Jaug = nullptr;
   M->Piv = nullptr;
   M->dU = nullptr;
+  M->refresh = nullptr;
   M->Bmu = nullptr;
   M->Rn = nullptr;
   M->Rg = nullptr;
@@ -1883,6 +1913,9 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   M->Piv = (int *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "last updates")) != RB_OK) return rc;
   M->dU = (double *)p;
+  if ((rc = ctx_alloc(ctx, &p, 16, "refresh word")) != RB_OK) return rc;
+  M->refresh = (int *)p;
+  cudaMemsetAsync(M->refresh, 0, 16, ctx->stream);
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->nb * aug_ld(M->nb), "Newton systems")) != RB_OK) return rc;
   M->Jaug = (float *)p;
   const size_t groups = (size_t)(M->nb + 7) / 8;
@@ -2007,8 +2040,11 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
     cudaError_t e0 = cudaMemsetAsync(M->root->dev_words + 6, 0, 4, st);
     if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "words");
   }
+  // a chord step (incr, no Jacobian) still contracts the Jacobian when one of its queries asked
+  // for a fresh one (the bucket's refresh word, read on the device)
+  const bool cond_jac = incr && !jac && M->refresh;
   int rc = launch_build_x(ctx, M, nq, d_n, d_u, d_info, 0, exact ? 1 : 0, M->Rc, M->nb, st,
-                          jac ? 1 : 0, incr && exact && !jac ? 1 : 0);
+                          (jac || cond_jac) ? 1 : 0, incr && exact && !jac ? 1 : 0);
   if (rc != RB_OK) return rc;
   TcGemmParams g = gemm_params(M, nq_jac >= 0 ? nq_jac : nq);
   g.n_tiles = M->Npad / kTcBN;
@@ -2021,7 +2057,8 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.nsplit = 3;
   int mk;
   cudaError_t e;
-  if (jac) {
+  if (cond_jac) g.run_if = M->refresh;
+  if (jac || cond_jac) {
     // RB_TEST_WAIT_DEFICIT=1 (tests of the failure path only): the single-CTA Jacobian GEMM's
     // first stage waits for 16 bytes that never come, so the bounded wait gives up
     const char *td = getenv("RB_TEST_WAIT_DEFICIT");
@@ -2042,6 +2079,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
     g.nq = ge.nq;
   }
   g.tx_extra = 0;
+  g.run_if = nullptr;
   g.kb[1] = M->kb1;
   g.n_tiles = M->WR.Npad / kTcBN;
   g.n_pad = M->WR.Npad;
@@ -2109,6 +2147,14 @@ static int launch_lu(rb_ctx *ctx, MixedState *M, LuParams &lp, int nq, cudaStrea
     else if (fixed == 2) k_newton_system<false, 2><<<grid2, kThreads, 0, st>>>(lp);
     else if (fixed == 3) k_newton_system<false, 3><<<grid2, kThreads, 0, st>>>(lp);
     else k_newton_system<false, -1><<<grid, kThreads, 0, st>>>(lp);
+    if (fixed == 3 && lp.refresh) {
+      // the queries whose last chord step asked for a fresh Jacobian; then the word is cleared
+      // for the chord steps of this iteration to raise again
+      LuParams lr = lp;
+      lr.run_if = lp.refresh;
+      k_newton_system<false, 4><<<grid, kThreads, 0, st>>>(lr);
+      cudaMemsetAsync(lp.refresh, 0, 4, st);
+    }
     prof_end(ctx, mk, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_system");
@@ -2296,6 +2342,7 @@ static LuParams solve_lu_params(rb_ctx *ctx, MixedState *M, const SolveArgs &a) 
   lp.chord = bucket_chord(M) ? 1 : 0;
   lp.Piv = M->Piv;
   lp.dU = lp.chord && incr_residual() ? M->dU : nullptr;
+  lp.refresh = lp.chord && incr_residual() ? M->refresh : nullptr;
   lp.rung_all = -1;
   return lp;
 }
@@ -2313,6 +2360,8 @@ static int solve_prologue(rb_ctx *ctx, const std::vector<Part> &parts, cudaStrea
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
     const int rc = launch_prep(ctx, pt.M, a.mu, a.theta, a.nq, a.n, a.info, st);
     if (rc != RB_OK) return rc;
+    if (pt.M->refresh && (e = cudaMemsetAsync(pt.M->refresh, 0, 4, st)) != cudaSuccess)
+      return cuda_fail(ctx, e, "refresh word");
   }
   return RB_OK;
 }

@@ -35,6 +35,8 @@ struct TcGemmParams {
   int *err;              // device error word (bounded waits)
   const int *lmax;       // sliced, one segment: if set, the highest digit level L = i + j of
                          // the launch, read on the device (levels 2..*lmax, at most S[0] + 1)
+  const int *run_if;     // if set, the launch does nothing unless *run_if != 0 (read on the
+                         // device: a Jacobian that only some chord steps ask for)
   unsigned tx_extra;     // single-CTA variants, tests of the bounded waits only: bytes the first
                          // stage of CTA 0 expects beyond what its copies bring (0 normally), so
                          // that its consumer's wait runs out and raises the error word
