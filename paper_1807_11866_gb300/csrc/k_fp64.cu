@@ -144,8 +144,15 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
   double *J = p.j_in_smem ? sm + L.J : p.jscratch + (size_t)blockIdx.x * o.n_max * o.n_max;
   double *Am = (p.j_in_smem && o.n_max <= kFp64SmallN) ? sm + L.Am : nullptr;
   const int tid = threadIdx.x;
+  if (p.run_if && *(volatile const int *)p.run_if == 0) return;  // nothing handed over
 
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
+    int it0 = 0;
+    if (p.resume) {  // only the queries the mixed path handed over, from their iterate
+      const rb_query_info qe = p.info[b];
+      if (qe.status != kQEscalate) continue;  // uniform over the CTA
+      it0 = qe.iters;
+    }
     const int n = p.nsz ? p.nsz[b] : o.n_max;
     double *urow = p.u_out + (size_t)b * o.n_max;
     if (n < 1 || n > o.n_max) {
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
       continue;
     }
     load_theta(o, p.mu, p.theta, b, th);
-    for (int i = tid; i < n; i += blockDim.x) u[i] = 0.0;
+    for (int i = tid; i < n; i += blockDim.x) u[i] = p.resume ? urow[i] : 0.0;
     __syncthreads();
     assemble_f(o, n, th, fm);
     if (Am) assemble_a(o, n, th, Am);
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
     __syncthreads();
     for (int i = tid; i < o.n_max; i += blockDim.x) urow[i] = (i < n) ? u[i] : 0.0;
     if (tid == 0 && p.info) {
-      rb_query_info q = {status, iters, RB_PREC_FP64, 0, rn, dn};
+      rb_query_info q = {status, it0 + iters, RB_PREC_FP64, 0, rn, dn};
       p.info[b] = q;
     }
     __syncthreads();

@@ -35,12 +35,14 @@ __host__ __device__ inline int small_ld(int nb) {
 
 // shared-memory carve-up (bytes); every block 16-byte aligned
 struct SmallSmem {
-  int th, u, fm, xs, am, t, jaug, part, pseq, red, total;
+  int th, th2, u, u2, fm, xs, am, t, jaug, part, pseq, red, total;
   __host__ __device__ SmallSmem(const DevOps &o, int nb) {
     auto al = [](int b) { return (b + 15) & ~15; };
     int p = 0;
     th = p; p += al(8 * o.n_theta);
+    th2 = p; p += al(8 * o.n_theta);        // theta as double-float
     u = p; p += al(8 * nb);
+    u2 = p; p += al(8 * nb);                // u as double-float
     fm = p; p += al(8 * nb);
     xs = p; p += al(8 * o.q_c * nb);        // theta^c_q u_l as double-float
     am = p; p += al(8 * nb * nb);           // A(mu) as double-float
@@ -77,6 +79,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   const SmallSmem L(o, nb);
   double *th = reinterpret_cast<double *>(sm + L.th);
   double *u = reinterpret_cast<double *>(sm + L.u);
+  float2 *th2 = reinterpret_cast<float2 *>(sm + L.th2);
+  float2 *u2 = reinterpret_cast<float2 *>(sm + L.u2);
   double *fm = reinterpret_cast<double *>(sm + L.fm);
   float2 *xs = reinterpret_cast<float2 *>(sm + L.xs);
   float2 *am = reinterpret_cast<float2 *>(sm + L.am);
@@ -111,6 +115,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       theta_eval(o, p.mu[2 * b], p.mu[2 * b + 1], th);
     }
     __syncthreads();
+    // the FP64 pipe is narrow: every later product works on double-float copies
+    for (int i = tid; i < o.n_theta; i += blockDim.x) {
+      float h, lo;
+      df_split(th[i], h, lo);
+      th2[i] = make_float2(h, lo);
+    }
     double fn2 = 0.0;
     for (int k = tid; k < nb; k += blockDim.x) {
       double s = 0.0;
@@ -119,16 +129,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       fm[k] = s;
       fn2 += s * s;
       u[k] = 0.0;
+      u2[k] = make_float2(0.f, 0.f);
     }
+    __syncthreads();
     for (size_t e = tid; e < nn; e += blockDim.x) {
       float h = 0.f, l = 0.f;
       const int k = (int)(e / nb), j = (int)(e - (size_t)k * nb);
       if (k < n && j < n)
         for (int q = 0; q < o.q_a; ++q) {
-          float th_h, th_l;
-          df_split(th[q], th_h, th_l);
+          const float2 t = th2[q];
           const float2 a = p.A2[(size_t)q * nn + e];
-          df_fma(h, l, a.x, a.y, th_h, th_l);
+          df_fma(h, l, a.x, a.y, t.x, t.y);
         }
       float s, ee;
       two_sum(h, l, s, ee);
@@ -141,9 +152,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       // xs = theta^c (x) u in double-float
       for (int i = tid; i < o.q_c * nb; i += blockDim.x) {
         const int q = i / nb, l = i - q * nb;
-        const double v = l < n ? th[o.q_a + q] * u[l] : 0.0;
-        float h, lo;
-        df_split(v, h, lo);
+        float h = 0.f, lo = 0.f;
+        if (l < n) {
+          const float2 t = th2[o.q_a + q], v = u2[l];
+          df_fma(h, lo, t.x, t.y, v.x, v.y);
+        }
         xs[i] = make_float2(h, lo);
       }
       __syncthreads();
@@ -192,10 +205,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       for (int k = w; k < n; k += kSmallWarps) {
         float h = 0.f, l = 0.f;
         for (int j = lane; j < n; j += 32) {
-          float uh, ul;
-          df_split(u[j], uh, ul);
+          const float2 uu = u2[j];
           const float2 t = tm[(size_t)k * nb + j];
-          df_fma(h, l, t.x, t.y, uh, ul);
+          df_fma(h, l, t.x, t.y, uu.x, uu.y);
         }
         const double r = df_warp_sum(h, l) - fm[k];
         if (lane == 0) {
@@ -218,7 +230,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
             status = RB_Q_SINGULAR;
           } else {
             const double d = lane < n ? (double)x[0] : 0.0;
-            if (lane < n) u[lane] += d;
+            if (lane < n) {
+              const double un = u[lane] + d;
+              u[lane] = un;
+              float h, lo;
+              df_split(un, h, lo);
+              u2[lane] = make_float2(h, lo);
+            }
             dn = sqrt(warp_sum(d * d));
             if (!isfinite(dn)) status = RB_Q_NONFINITE;
             else if (dn <= p.tol_upd && rn <= p.tol_res * fscale) status = RB_Q_OK;

@@ -14,7 +14,15 @@ struct NewtonParams {
   double *u_out;        // [nq][n_max]
   rb_query_info *info;  // [nq] or nullptr
   double *jscratch;     // [grid][n_max^2] when the Jacobian does not fit in shared memory
+  // escalation of the mixed path: only the queries it handed over (status kQEscalate) are
+  // solved, from their current u, and only if *run_if != 0 (nullptr: a plain FP64 solve)
+  const int *run_if;
+  int resume;
 };
+
+// internal per-query status of the mixed path: its chord steps stalled even with a fresh
+// Jacobian, so the FP64 Newton finishes the query from its current iterate (never returned)
+constexpr int kQEscalate = 16;
 
 struct PressureParams {
   DevOps o;

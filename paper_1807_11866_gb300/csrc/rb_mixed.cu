@@ -707,6 +707,7 @@ struct LuParams {
   double *dU;            // [nq][nb]: the update of each query's last iteration, or null
   int *refresh;          // chord steps: raised when a query's chord step contracts too slowly
                          // (that query factors a fresh Jacobian at its next iteration), or null
+  int *escalate;         // raised when a query is handed to the FP64 Newton (kQEscalate)
   const int *run_if;     // k_newton_system<., 4>: runs only if *run_if != 0
 };
 
@@ -725,23 +726,38 @@ __device__ __forceinline__ int rung_of(int rmode, int iters) {
 // >= 3), a query reuses the factorisation of its first one (count 2), kept in its [J | -R]
 // block with the pivot rows in Piv and marked by Rn[b].x = 1 (0 from the query's start); only
 // the residual is new.
-// A chord step that shrinks the update by less than kChordSlow (a Jacobian that has drifted
-// from the iterate, far from the root) marks its query with Rn[b].x = 2: its next iteration
-// factors the Jacobian at its current iterate and keeps those factors instead.
+// Per-query escalation. Rn[b].x holds the query's state: 0 no factors yet, 1 factors kept at
+// iteration 2, 2 a fresh Jacobian requested, 3 factors kept from such a refresh. A chord step
+// that shrinks the update by less than kChordSlow (a Jacobian that has drifted from the
+// iterate) requests a refresh: the next iteration factors the Jacobian at the current iterate.
+// If a chord step with the refreshed factors is slow again, the low-precision Jacobian itself
+// is too inexact for this query (kappa 2^-16 not small): the query leaves the mixed loop with
+// status kQEscalate and the FP64 Newton finishes it from its current iterate.
 __device__ __forceinline__ bool chord_step(const LuParams &p, int b, int iters) {
-  return p.chord && p.rmode < 0 && iters >= 3 && p.Rn[b].x == 1.0;
+  const double s = p.Rn[b].x;
+  return p.chord && p.rmode < 0 && iters >= 3 && (s == 1.0 || s == 3.0);
 }
 __device__ __forceinline__ bool chord_keep(const LuParams &p, int b, int iters) {
   return p.chord && p.rmode < 0 && (iters == 2 || (iters >= 3 && p.Rn[b].x == 2.0));
 }
 constexpr double kChordSlow = 0.25;
-// after a chord step of query b (one thread): dn = ||delta_k||, prev = ||delta_{k-1}||
-__device__ __forceinline__ void chord_watch(const LuParams &p, int b, bool chord, bool converged,
-                                            double dn, double prev) {
-  if (chord && !converged && p.refresh && dn > kChordSlow * prev) {
-    p.Rn[b].x = 2.0;
-    atomicOr(p.refresh, 1);
+// after a chord step of query b (one thread): dn = ||delta_k||, prev = ||delta_{k-1}||; returns
+// the query's new status (kQEscalate when handed to the FP64 Newton)
+__device__ __forceinline__ int chord_watch(const LuParams &p, int b, bool chord, int status,
+                                           double dn, double prev) {
+  if (!chord || status != RB_Q_NOT_CONVERGED || !p.refresh || !(dn > kChordSlow * prev))
+    return status;
+  if (p.Rn[b].x == 3.0 && p.escalate) {
+    atomicOr(p.escalate, 1);
+    return kQEscalate;
   }
+  p.Rn[b].x = 2.0;
+  atomicOr(p.refresh, 1);
+  return status;
+}
+// the state after keeping factors: 1 at iteration 2, 3 after a refresh
+__device__ __forceinline__ double kept_state(const LuParams &p, int b) {
+  return p.Rn[b].x == 2.0 ? 3.0 : 1.0;
 }
 
 
@@ -957,7 +973,7 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
         const float4 *src = reinterpret_cast<const float4 *>(J);
         for (int i = lane; i < n4; i += 32) gJ[i] = src[i];
         for (int i = lane; i < n; i += 32) p.Piv[(size_t)b * p.nb + i] = pseq[i];
-        if (lane == 0) p.Rn[b].x = 1.0;
+        if (lane == 0) p.Rn[b].x = kept_state(p, b);
       }
       double dl = 0.0;
 #pragma unroll
@@ -975,7 +991,7 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
       else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
-      if (lane == 0) chord_watch(p, b, chord, qi.status != RB_Q_NOT_CONVERGED, dn, prev);
+      if (lane == 0) qi.status = chord_watch(p, b, chord, qi.status, dn, prev);
     }
     if (lane == 0) {
       p.info[b] = qi;
@@ -1092,7 +1108,7 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
         const float4 *src = reinterpret_cast<const float4 *>(J);
         for (int i = tid; i < n4; i += blockDim.x) gJ[i] = src[i];
         for (int i = tid; i < n; i += blockDim.x) p.Piv[(size_t)b * p.nb + i] = pseq[i];
-        if (tid == 0) p.Rn[b].x = 1.0;
+        if (tid == 0) p.Rn[b].x = kept_state(p, b);
       }
       double dl = 0.0;
       if (tid < n) {
@@ -1111,7 +1127,7 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
       else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
-      if (tid == 0) chord_watch(p, b, chord, qi.status != RB_Q_NOT_CONVERGED, dn, prev);
+      if (tid == 0) qi.status = chord_watch(p, b, chord, qi.status, dn, prev);
     }
     if (tid == 0) {
       p.info[b] = qi;
@@ -1346,7 +1362,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
     } else if (sing) {
       qi.status = RB_Q_SINGULAR;
     } else {
-      if (keep && tid == 0) p.Rn[b].x = 1.0;  // factors and pivots kept for the chord steps
+      if (keep && tid == 0) p.Rn[b].x = kept_state(p, b);  // factors and pivots kept for chords
       // back substitution, blocks of 32 rows from the bottom: warp 0 solves the diagonal block,
       // then every thread updates the right-hand side of one row above it (a chord step has
       // its forward-substituted right-hand side in xs already)
@@ -1393,7 +1409,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
       else if (rm != kResLow && dn <= p.tol_upd && rn <= p.tol_res * fscale) qi.status = RB_Q_OK;
-      if (tid == 0) chord_watch(p, b, chord, qi.status != RB_Q_NOT_CONVERGED, dn, prev);
+      if (tid == 0) qi.status = chord_watch(p, b, chord, qi.status, dn, prev);
     }
     if (tid == 0) {
       p.info[b] = qi;
@@ -2343,6 +2359,7 @@ static LuParams solve_lu_params(rb_ctx *ctx, MixedState *M, const SolveArgs &a) 
   lp.Piv = M->Piv;
   lp.dU = lp.chord && incr_residual() ? M->dU : nullptr;
   lp.refresh = lp.chord && incr_residual() ? M->refresh : nullptr;
+  lp.escalate = lp.refresh ? M->refresh + 1 : nullptr;
   lp.rung_all = -1;
   return lp;
 }
@@ -2360,7 +2377,7 @@ static int solve_prologue(rb_ctx *ctx, const std::vector<Part> &parts, cudaStrea
     if (e != cudaSuccess) return cuda_fail(ctx, e, "k_mixed_init");
     const int rc = launch_prep(ctx, pt.M, a.mu, a.theta, a.nq, a.n, a.info, st);
     if (rc != RB_OK) return rc;
-    if (pt.M->refresh && (e = cudaMemsetAsync(pt.M->refresh, 0, 4, st)) != cudaSuccess)
+    if (pt.M->refresh && (e = cudaMemsetAsync(pt.M->refresh, 0, 8, st)) != cudaSuccess)
       return cuda_fail(ctx, e, "refresh word");
   }
   return RB_OK;
@@ -2383,6 +2400,53 @@ static int solve_iteration(rb_ctx *ctx, const std::vector<Part> &parts, int it, 
     // every active query of a batch solve is on iteration `it`
     lp.rung_all = it == 0 ? 0 : (it == 1 ? 1 : (it >= 3 && lp.chord ? 3 : 2));
     if ((rc = launch_lu(ctx, pt.M, lp, pt.a.nq, st)) != RB_OK) return rc;
+  }
+  return RB_OK;
+}
+
+// The queries whose chord steps stalled even with a refreshed Jacobian (status kQEscalate) are
+// finished by the FP64 Newton from their current iterate, one CTA per query; a bucket where no
+// query was handed over returns at once (its escalation word is 0).
+static int escalation_grid(const rb_ctx *ctx, int nq) { return std::max(1, std::min(nq, ctx->sms)); }
+
+// the FP64 Jacobians of the escalation's CTAs, when they do not fit in shared memory: sized for
+// the largest grid once, so that a captured graph's pointer stays valid
+static int escalation_scratch(rb_ctx *ctx) {
+  const DevOps &o = ctx->ops;
+  if (fp64_smem_bytes(o, true) <= (size_t)ctx->max_smem) return RB_OK;
+  void *before = ctx->jscratch.ptr;
+  const int rc = ctx->jscratch.reserve(ctx, sizeof(double) * (size_t)ctx->sms * o.n_max * o.n_max,
+                                       "FP64 Jacobian scratch");
+  if (rc == RB_OK && ctx->jscratch.ptr != before) ctx->mixed->epoch += 1;
+  return rc;
+}
+
+static int solve_escalated(rb_ctx *ctx, const std::vector<Part> &parts, cudaStream_t st) {
+  const DevOps &o = ctx->ops;
+  for (const Part &pt : parts) {
+    if (!pt.M->refresh || !bucket_chord(pt.M) || !incr_residual()) continue;
+    NewtonParams np{};
+    np.o = o;
+    np.mu = pt.a.theta ? nullptr : pt.a.mu;
+    np.theta = pt.a.theta;
+    np.nsz = pt.a.n;
+    np.nq = pt.a.nq;
+    np.max_iter = ctx->cfg.max_iter;
+    np.tol_upd = ctx->cfg.tol_update;
+    np.tol_res = ctx->cfg.tol_res;
+    np.u_out = pt.a.u;
+    np.info = pt.a.info;
+    np.j_in_smem = fp64_smem_bytes(o, true) <= (size_t)ctx->max_smem ? 1 : 0;
+    if (!np.j_in_smem) {
+      if (ctx->jscratch.cap < sizeof(double) * (size_t)escalation_grid(ctx, pt.a.nq) * o.n_max * o.n_max)
+        return set_error(ctx, RB_ERR_STATE, "escalation scratch not reserved");
+      np.jscratch = (double *)ctx->jscratch.ptr;
+    }
+    np.grid = escalation_grid(ctx, pt.a.nq);
+    np.run_if = pt.M->refresh + 1;
+    np.resume = 1;
+    const cudaError_t e = launch_newton_fp64(np, ctx->sms, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_fp64 (escalation)");
   }
   return RB_OK;
 }
@@ -2649,6 +2713,7 @@ static int build_solve_graph(rb_ctx *ctx, const SolvePlan &pl, const std::vector
     cudaGraph_t bg;
     body_open = false;
     if ((e = cudaStreamEndCapture(cb, &bg)) != cudaSuccess) break;
+    if ((rc = solve_escalated(ctx, pl.parts, cs)) != RB_OK) break;
     if (pl.pres && (rc = solve_pressure(ctx, pl.parts, cs)) != RB_OK) break;
     if ((rc = plan_edges(ctx, pl, false, cs)) != RB_OK) break;
     k_latch_error<<<1, 1, 0, cs>>>(M->dev_words);
@@ -2869,6 +2934,7 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
   if (ctx->cfg.autotune)
     for (const Part &pt : pl.parts)
       if ((rc = autotune(ctx, pt.M, pt.a.nq, st)) != RB_OK) return rc;
+  if ((rc = escalation_scratch(ctx)) != RB_OK) return rc;  // before any capture
   if (ctx->cfg.use_graph && !ctx->prof) {
     const auto &k = R->gkey;
     if (!R->gexec || k.mu != d_mu || k.theta != d_theta || k.p != d_p || k.n != d_n || k.u != d_u ||
@@ -2893,6 +2959,7 @@ int solve_mixed(rb_ctx *ctx, const double *d_mu, const double *d_theta, int nq, 
     if ((rc = check_words(ctx, st, "mixed Newton step")) != RB_OK) return rc;
     if (R->h_words[0] == 0) break;
   }
+  if ((rc = solve_escalated(ctx, pl.parts, st)) != RB_OK) return rc;
   if (pl.pres && (rc = solve_pressure(ctx, pl.parts, st)) != RB_OK) return rc;
   if ((rc = plan_edges(ctx, pl, false, st)) != RB_OK) return rc;
   if ((rc = check_words(ctx, st, "mixed solve")) != RB_OK) return rc;

@@ -67,8 +67,12 @@ def test_eval_residual_and_jacobian(rb, n, qc, c_dtype, pairs, monkeypatch):
         assert np.abs(Jc - Jcr).max() <= 2 ** -12 * np.abs(Jcr).max() + 2e-7 * np.abs(A).max()
 
 
+@pytest.mark.parametrize("small", ["0", "1"])
 @pytest.mark.parametrize("n", [2, 20, 50])
-def test_sweep_parity(rb, n):
+def test_sweep_parity(rb, n, small, monkeypatch):
+    """Velocity and pressure of a sweep against the oracle; for n <= 32 through both the
+    tensor-core pipeline (RB_SMALL=0) and the single-launch small-system solve (1)."""
+    monkeypatch.setenv("RB_SMALL", small)
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n)
     q = synth.make_queries(wl, batch=200, n_max=n)
@@ -90,6 +94,7 @@ def test_cta_pair_gemms_solve(rb, n, nq, pairs, monkeypatch):
     pairs = 2, the 256-column sliced tiles): the tuner records them, and the result is the
     oracle's; batches not a multiple of 256 rows."""
     monkeypatch.setenv("RB_GEMM_PAIRS", pairs)
+    monkeypatch.setenv("RB_SMALL", "0")  # the tensor-core pipeline also for n <= 32
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n)
     q = synth.make_queries(wl, batch=nq, n_max=n)
@@ -140,6 +145,7 @@ def test_chord_steps(rb, n, elim, monkeypatch):
     the default) or as the full product (0): the same iterations and accuracy."""
     if elim:
         monkeypatch.setenv("RB_ELIMINATION", elim)
+    monkeypatch.setenv("RB_SMALL", "0")
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n)
     q = synth.make_queries(wl, batch=300, n_max=n)
@@ -194,7 +200,8 @@ def test_nested_sizes_and_theta_user(rb):
         assert np.all(u[b, n:] == 0.0)
 
 
-def test_status_codes_mixed(rb):
+def test_status_codes_mixed(rb, monkeypatch):
+    monkeypatch.setenv("RB_SMALL", "0")  # the tensor-core pipeline's statuses
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=12)
     mu = np.array([[10.0, 200.0], [20.0, 300.0], [1.0, 900.0]])
@@ -254,12 +261,13 @@ def test_large_n_mixed(rb, n, q, nq, pairs, monkeypatch):
     assert rel(u[idx], u_ref).max() <= TOL_MIXED
 
 
-def test_graph_and_stream_paths_agree(rb):
+def test_graph_and_stream_paths_agree(rb, monkeypatch):
     """The captured whole-solve graph (device-side while loop over FP64-residual iterations)
     gives the results of the stream path that checks convergence on the host after every
     iteration (identical but for the order in which the sliced GEMM's tiles add into the FP64
     residual with atomics: a few units in the last place); the graph is rebuilt when the batch
     changes, and honours the iteration cap."""
+    monkeypatch.setenv("RB_SMALL", "0")
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=30)
     q = synth.make_queries(wl, batch=300, n_max=30)
@@ -335,10 +343,11 @@ def test_autotuner_choices(rb):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_maximum_sizes(rb, prec):
+def test_maximum_sizes(rb, prec, monkeypatch):
     """The largest sizes the library accepts: n = RB_N_MAX (320) velocity modes, and m =
     RB_M_MAX (128) pressure modes (the CTA pressure solver), both against the oracle."""
     import dataclasses
+    monkeypatch.setenv("RB_SMALL", "0")  # the mixed path's own pressure solver at m = 128
     P = rb.RB_PREC_FP64 if prec == "fp64" else rb.RB_PREC_MIXED
     tol = 1e-10 if prec == "fp64" else TOL_MIXED
     wl = synth.WORKLOADS["sweep_n50"]

@@ -27,12 +27,13 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("n,damp", [(30, 64.0), (48, 64.0), (40, 256.0)])
-def test_weakly_damped_mixed(rb, n, damp):
+def test_weakly_damped_mixed(rb, n, damp, monkeypatch):
     """A/64 (A/256) leaves the small-data regime the workloads are scaled into: the first Newton
     steps are far from the root and the inexact Jacobian's chord steps contract slowly. Every
     query must either match the oracle within the mixed tolerance or report that it did not
     converge (never a wrong answer with status OK); where the oracle converges, the mixed path
     must too."""
+    monkeypatch.setenv("RB_SMALL", "0")  # the tensor-core pipeline's inexact Newton
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=n)
     ops.A = ops.A / damp
@@ -48,10 +49,15 @@ def test_weakly_damped_mixed(rb, n, damp):
     both = ok & (inf_ref["status"] == 0)
     assert rel(u[both], u_ref[both]).max() <= TOL_MIXED
     assert rel(p[both], p_ref[both]).max() <= 10 * TOL_MIXED
-    # the mixed path converges wherever the oracle does
+    # the mixed path converges wherever the oracle does: a query whose chord steps stall asks
+    # for a fresh Jacobian, and one that stalls with it too is finished by the FP64 Newton from
+    # its iterate (reported as precision_used = RB_PREC_FP64)
     assert np.all(ok[inf_ref["status"] == 0]), (np.sum(~ok), info["iters"].max())
+    assert set(np.unique(info["precision_used"])) <= {rb.RB_PREC_MIXED, rb.RB_PREC_FP64}
     # more iterations than the damped workloads (3-4): the problem is harder, not broken
     assert info["iters"][both].max() >= 5
+    if damp >= 256:
+        assert np.any(info["precision_used"] == rb.RB_PREC_FP64)
 
 
 @pytest.mark.parametrize("graph", [0, 1])
@@ -61,6 +67,7 @@ def test_bounded_wait_runs_out(rb, monkeypatch, graph):
     the kernel leaves, and the solve reports RB_ERR_TIMEOUT. The same context then solves
     correctly, and so does a fresh one."""
     monkeypatch.setenv("RB_GEMM_PAIRS", "0")  # single CTAs: no cluster barriers involved
+    monkeypatch.setenv("RB_SMALL", "0")  # the tensor-core pipeline also at n = 16
     wl = synth.WORKLOADS["sweep_n50"]
     ops = synth.make_operators(wl, n_max=16)
     q = synth.make_queries(wl, batch=8, n_max=16)
