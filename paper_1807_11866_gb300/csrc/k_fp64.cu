@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
 
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
     int it0 = 0;
-    if (p.resume) {  // only the queries the mixed path handed over, from their iterate
+    if (p.resume) {  // only the queries the mixed path handed over, solved again from u = 0
       const rb_query_info qe = p.info[b];
       if (qe.status != kQEscalate) continue;  // uniform over the CTA
       it0 = qe.iters;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_newton_fp64(NewtonParams p) {
       continue;
     }
     load_theta(o, p.mu, p.theta, b, th);
-    for (int i = tid; i < n; i += blockDim.x) u[i] = p.resume ? urow[i] : 0.0;
+    for (int i = tid; i < n; i += blockDim.x) u[i] = 0.0;
     __syncthreads();
     assemble_f(o, n, th, fm);
     if (Am) assemble_a(o, n, th, Am);

@@ -22,8 +22,14 @@ namespace rb {
 
 namespace {
 
-constexpr int kSmallThreads = 1024;
-constexpr int kSmallUnroll = 8;  // loads of D~ in flight per thread (the loop is L2-latency bound)
+#ifndef RB_SMALL_THREADS
+#define RB_SMALL_THREADS 512
+#endif
+#ifndef RB_SMALL_UNROLL
+#define RB_SMALL_UNROLL 8
+#endif
+constexpr int kSmallThreads = RB_SMALL_THREADS;
+constexpr int kSmallUnroll = RB_SMALL_UNROLL;  // loads of D~ in flight per thread (L2 latency)
 constexpr int kSmallWarps = kSmallThreads / 32;
 
 // ld of the augmented matrix [J | -R] in shared memory (the warp elimination's layout)

@@ -15,13 +15,14 @@ struct NewtonParams {
   rb_query_info *info;  // [nq] or nullptr
   double *jscratch;     // [grid][n_max^2] when the Jacobian does not fit in shared memory
   // escalation of the mixed path: only the queries it handed over (status kQEscalate) are
-  // solved, from their current u, and only if *run_if != 0 (nullptr: a plain FP64 solve)
+  // solved (again from u = 0: the exact Newton of the FP64 path), and only if *run_if != 0
+  // (nullptr: a plain FP64 solve); their iteration counts add to the mixed ones
   const int *run_if;
   int resume;
 };
 
 // internal per-query status of the mixed path: its chord steps stalled even with a fresh
-// Jacobian, so the FP64 Newton finishes the query from its current iterate (never returned)
+// Jacobian, so the FP64 Newton solves the query (never returned)
 constexpr int kQEscalate = 16;
 
 struct PressureParams {

@@ -732,7 +732,8 @@ __device__ __forceinline__ int rung_of(int rmode, int iters) {
 // iterate) requests a refresh: the next iteration factors the Jacobian at the current iterate.
 // If a chord step with the refreshed factors is slow again, the low-precision Jacobian itself
 // is too inexact for this query (kappa 2^-16 not small): the query leaves the mixed loop with
-// status kQEscalate and the FP64 Newton finishes it from its current iterate.
+// status kQEscalate and the FP64 Newton (the exact Newton of the plain path) solves it from
+// u = 0, as the oracle does: a stalled iterate may lie where Newton converges poorly.
 __device__ __forceinline__ bool chord_step(const LuParams &p, int b, int iters) {
   const double s = p.Rn[b].x;
   return p.chord && p.rmode < 0 && iters >= 3 && (s == 1.0 || s == 3.0);
@@ -2405,8 +2406,8 @@ static int solve_iteration(rb_ctx *ctx, const std::vector<Part> &parts, int it, 
 }
 
 // The queries whose chord steps stalled even with a refreshed Jacobian (status kQEscalate) are
-// finished by the FP64 Newton from their current iterate, one CTA per query; a bucket where no
-// query was handed over returns at once (its escalation word is 0).
+// solved by the FP64 Newton, one CTA per query; a bucket where no query was handed over returns
+// at once (its escalation word is 0).
 static int escalation_grid(const rb_ctx *ctx, int nq) { return std::max(1, std::min(nq, ctx->sms)); }
 
 // the FP64 Jacobians of the escalation's CTAs, when they do not fit in shared memory: sized for

@@ -50,8 +50,8 @@ def test_weakly_damped_mixed(rb, n, damp, monkeypatch):
     assert rel(u[both], u_ref[both]).max() <= TOL_MIXED
     assert rel(p[both], p_ref[both]).max() <= 10 * TOL_MIXED
     # the mixed path converges wherever the oracle does: a query whose chord steps stall asks
-    # for a fresh Jacobian, and one that stalls with it too is finished by the FP64 Newton from
-    # its iterate (reported as precision_used = RB_PREC_FP64)
+    # for a fresh Jacobian, and one that stalls with it too is solved by the FP64 Newton
+    # (reported as precision_used = RB_PREC_FP64)
     assert np.all(ok[inf_ref["status"] == 0]), (np.sum(~ok), info["iters"].max())
     assert set(np.unique(info["precision_used"])) <= {rb.RB_PREC_MIXED, rb.RB_PREC_FP64}
     # more iterations than the damped workloads (3-4): the problem is harder, not broken
