@@ -39,9 +39,17 @@ __host__ __device__ inline int small_ld(int nb) {
   return ld;
 }
 
+// The contraction's work split: element e = t % E (E = nb^2 rounded up to a warp) and part
+// t / E of the (q, l) range, P parts (P E >= the block when E is smaller than the block).
+__host__ __device__ inline int small_elems(int nb) { return (nb * nb + 31) & ~31; }
+__host__ __device__ inline int small_parts(int nb) {
+  const int E = small_elems(nb);
+  return kSmallThreads / E > 0 ? kSmallThreads / E : 1;
+}
+
 // shared-memory carve-up (bytes); every block 16-byte aligned
 struct SmallSmem {
-  int th, th2, u, u2, fm, xs, am, t, jaug, part, pseq, red, total;
+  int th, th2, u, u2, fm, rv, xs, am, t, jaug, part, pseq, red, total;
   __host__ __device__ SmallSmem(const DevOps &o, int nb) {
     auto al = [](int b) { return (b + 15) & ~15; };
     int p = 0;
@@ -50,29 +58,17 @@ struct SmallSmem {
     u = p; p += al(8 * nb);
     u2 = p; p += al(8 * nb);                // u as double-float
     fm = p; p += al(8 * nb);
+    rv = p; p += al(8 * nb);                // the residual R (FP64)
     xs = p; p += al(8 * o.q_c * nb);        // theta^c_q u_l as double-float
     am = p; p += al(8 * nb * nb);           // A(mu) as double-float
     t = p; p += al(8 * nb * nb);            // A(mu) + J^c / 2 as double-float
     jaug = p; p += al(4 * nb * small_ld(nb));
-    part = p; p += al(8 * kSmallThreads);   // partial sums of J^c over parts of the (q, l) range
+    part = p; p += al(8 * small_parts(nb) * small_elems(nb));  // partial sums of J^c
     pseq = p; p += al(4 * ((nb + 3) & ~3));
-    red = p; p += al(8 * 2 * kSmallWarps + 16);
+    red = p; p += al(8 * 4);                 // the step's norms and status
     total = p;
   }
 };
-
-// sum over the block (kSmallWarps warps) in a fixed order, valid in every thread; red holds
-// kSmallWarps doubles
-__device__ __forceinline__ double small_block_sum(double v, double *red) {
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < kSmallWarps; ++i) s += red[i];
-  return s;
-}
 
 }  // namespace
 
@@ -88,6 +84,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   float2 *th2 = reinterpret_cast<float2 *>(sm + L.th2);
   float2 *u2 = reinterpret_cast<float2 *>(sm + L.u2);
   double *fm = reinterpret_cast<double *>(sm + L.fm);
+  double *rv = reinterpret_cast<double *>(sm + L.rv);
   float2 *xs = reinterpret_cast<float2 *>(sm + L.xs);
   float2 *am = reinterpret_cast<float2 *>(sm + L.am);
   float2 *tm = reinterpret_cast<float2 *>(sm + L.t);
@@ -100,8 +97,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   const size_t nn = (size_t)nb * nb;
   // J^c: thread t sums element e = t % E over part t / E of the (q, l) range (E = nn rounded up
   // to a warp; P parts fill the block), then the parts add up in a fixed order
-  const int E = (int)((nn + 31) & ~(size_t)31);
-  const int P = kSmallThreads / E > 0 ? kSmallThreads / E : 1;
+  const int E = small_elems(nb), P = small_parts(nb);
   const int Kc = o.q_c * nb;
 
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
@@ -127,13 +123,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       df_split(th[i], h, lo);
       th2[i] = make_float2(h, lo);
     }
-    double fn2 = 0.0;
     for (int k = tid; k < nb; k += blockDim.x) {
       double s = 0.0;
       if (k < n)
         for (int q = 0; q < o.q_f; ++q) s = fma(th[o.q_a + o.q_c + q], o.f[(size_t)q * o.n_max + k], s);
       fm[k] = s;
-      fn2 += s * s;
       u[k] = 0.0;
       u2[k] = make_float2(0.f, 0.f);
     }
@@ -151,7 +145,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       two_sum(h, l, s, ee);
       am[e] = make_float2(s, ee);
     }
-    const double fscale = fmax(1.0, sqrt(small_block_sum(fn2, red)));  // block_sum syncs
+    // FP64 reductions by warp 0 alone (n <= 32: one entry per lane)
+    double fscale = 1.0;
+    if (w == 0) {
+      const double fk = lane < n ? fm[lane] : 0.0;
+      fscale = fmax(1.0, sqrt(warp_sum(fk * fk)));
+    }
     rb_query_info qi = {RB_Q_NOT_CONVERGED, 0, RB_PREC_MIXED, 0, 0.0, 0.0};
     bool done = false;
     while (!done) {
@@ -207,7 +206,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       }
       __syncthreads();
       // R[k] = sum_j T[k][j] u_j - f[k], one warp per row; -R into column n
-      double r2 = 0.0;
       for (int k = w; k < n; k += kSmallWarps) {
         float h = 0.f, l = 0.f;
         for (int j = lane; j < n; j += 32) {
@@ -218,16 +216,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
         const double r = df_warp_sum(h, l) - fm[k];
         if (lane == 0) {
           J[k * ld + n] = (float)(-r);
-          r2 += r * r;
+          rv[k] = r;
         }
       }
-      const double rn = sqrt(small_block_sum(r2, red));  // syncs: J complete
+      __syncthreads();
       qi.iters += 1;
-      qi.res_norm = rn;
-      // elimination and update by warp 0 (n <= 32: one row per lane)
+      // residual norm, elimination and update by warp 0 (n <= 32: one row per lane)
       if (w == 0) {
         int status = RB_Q_NOT_CONVERGED;
         double dn = 0.0;
+        const double rk = lane < n ? rv[lane] : 0.0;
+        const double rn = sqrt(warp_sum(rk * rk));
         if (!isfinite(rn)) {
           status = RB_Q_NONFINITE;
         } else {
@@ -249,13 +248,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
           }
         }
         if (lane == 0) {
-          red[2 * kSmallWarps] = dn;
-          reinterpret_cast<int *>(red + 2 * kSmallWarps + 1)[0] = status;
+          red[0] = dn;
+          red[1] = rn;
+          reinterpret_cast<int *>(red + 2)[0] = status;
         }
       }
       __syncthreads();
-      qi.upd_norm = red[2 * kSmallWarps];
-      qi.status = reinterpret_cast<const int *>(red + 2 * kSmallWarps + 1)[0];
+      qi.upd_norm = red[0];
+      qi.res_norm = red[1];
+      qi.status = reinterpret_cast<const int *>(red + 2)[0];
       done = qi.status != RB_Q_NOT_CONVERGED || qi.iters >= p.max_iter;
       __syncthreads();  // red and the shared state are reused
     }
