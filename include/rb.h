@@ -288,6 +288,51 @@ int rb_gepp_solve(rb_ctx *ctx, int n, int batch, const double *M, const double *
 int rb_gepp_solve_static(int n, int batch, const double *d_M, const double *d_rhs, double *d_x,
                          int *d_status, void *cuda_stream);
 
+/* ---- offline stage: the reduced operators from high-fidelity data (Sec. 3.2, 3.5, 3.6) -----
+ * All synchronous, FP64 on the context's device, from caller-owned host arrays (read only;
+ * outputs written in full). Device scratch is allocated within the context's memory budget for
+ * the call and freed before it returns. RB_ERR_ARG on bad sizes or indices (message for
+ * rb_last_error), RB_ERR_OOM over the budget. */
+typedef struct {           /* a sparse high-fidelity matrix in CSR form, rows x cols */
+  int rows, cols;
+  const int *indptr;       /* [rows + 1], non-decreasing, indptr[0] = 0 */
+  const int *indices;      /* [indptr[rows]] column of each entry, 0 <= column < cols */
+  const double *values;    /* [indptr[rows]] */
+} rb_csr;
+
+typedef struct {           /* one quadrature term of a pointwise trilinear form:           */
+  rb_csr P, Q, R;          /*   c(a, v, w) += sum_x weight(x) (P a)(x) (Q v)(x) (R w)(x),    */
+  const double *weight;    /*   P, Q, R points x N_h; weight [points] or NULL (all 1)       */
+} rb_trilinear_term;
+
+#define RB_POD_K_MAX 128   /* snapshots of one POD */
+
+/* POD by the method of snapshots (Sec. 3.2, Eqs. covmx and spd): the covariance matrix
+ * C_ij = phi_i^T Z phi_j of the snapshots S [K][N] (row i = snapshot i) in the inner product Z
+ * (N x N, symmetric positive semidefinite, e.g. the H1-seminorm stiffness), its eigenpairs
+ * (cyclic Jacobi, FP64) in decreasing order, and the n modes
+ * psi_j = lambda_j^(-1/2) sum_i v^j_i phi_i into V_out [n][N] (row j = mode j, orthonormal in Z);
+ * lambda_out [K] (or NULL) all K eigenvalues, decreasing. 1 <= n <= K <= RB_POD_K_MAX; n must
+ * not exceed the number of positive eigenvalues (RB_ERR_ARG). Eigenvectors, and so modes, are
+ * determined up to sign. */
+int rb_offline_pod(rb_ctx *ctx, const double *S, int K, int N, const rb_csr *Z, int n,
+                   double *V_out, double *lambda_out);
+
+/* Galerkin projection of a high-fidelity matrix (Sec. 3.5, Eq. redorth-final):
+ * Mr_out [n][n] = V M V^T for the modes V [n][N] (rows) and M (N x N). 1 <= n <= 128. */
+int rb_offline_project(rb_ctx *ctx, const double *V, int n, int N, const rb_csr *M,
+                       double *Mr_out);
+/* fr_out [n] = V f for f [N]: the reduced right-hand side. 1 <= n <= 128. */
+int rb_offline_project_vector(rb_ctx *ctx, const double *V, int n, int N, const double *f,
+                              double *fr_out);
+
+/* The third-order tensor of a trilinear form on the modes (Sec. 3.6, Eq. tensor):
+ * C_out[j][l][k] = c(psi_j, psi_l, psi_k) = sum_terms sum_x weight(x) (P psi_j)(x) (Q psi_l)(x)
+ * (R psi_k)(x), the index order of rb_operators.C (j advecting, l advected, k test), for the
+ * modes V [n][N] and n_terms quadrature terms. 1 <= n <= RB_N_MAX. */
+int rb_offline_tensor(rb_ctx *ctx, const double *V, int n, int N, const rb_trilinear_term *terms,
+                      int n_terms, double *C_out);
+
 /* ---- per-kernel timing ------------------------------------------------------------------
  * While enabled, every kernel the context launches is bracketed by CUDA events on its
  * launching stream; rb_profile_read returns the accumulated device time and launch count of

@@ -49,16 +49,15 @@ __host__ __device__ inline int small_parts(int nb) {
 
 // shared-memory carve-up (bytes); every block 16-byte aligned
 struct SmallSmem {
-  int th, th2, u, u2, fm, rv, xs, am, t, jaug, part, pseq, red, total;
+  int th, th2, u2, fm, rv, xs, am, t, jaug, part, pseq, red, total;
   __host__ __device__ SmallSmem(const DevOps &o, int nb) {
     auto al = [](int b) { return (b + 15) & ~15; };
     int p = 0;
     th = p; p += al(8 * o.n_theta);
     th2 = p; p += al(8 * o.n_theta);        // theta as double-float
-    u = p; p += al(8 * nb);
     u2 = p; p += al(8 * nb);                // u as double-float
     fm = p; p += al(8 * nb);
-    rv = p; p += al(8 * nb);                // the residual R (FP64)
+    rv = p; p += al(8 * nb);                // the residual R (double-float)
     xs = p; p += al(8 * o.q_c * nb);        // theta^c_q u_l as double-float
     am = p; p += al(8 * nb * nb);           // A(mu) as double-float
     t = p; p += al(8 * nb * nb);            // A(mu) + J^c / 2 as double-float
@@ -80,11 +79,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   const int nb = p.nb;
   const SmallSmem L(o, nb);
   double *th = reinterpret_cast<double *>(sm + L.th);
-  double *u = reinterpret_cast<double *>(sm + L.u);
   float2 *th2 = reinterpret_cast<float2 *>(sm + L.th2);
   float2 *u2 = reinterpret_cast<float2 *>(sm + L.u2);
-  double *fm = reinterpret_cast<double *>(sm + L.fm);
-  double *rv = reinterpret_cast<double *>(sm + L.rv);
+  float2 *fm2 = reinterpret_cast<float2 *>(sm + L.fm);  // f(mu) as double-float
+  float2 *rv = reinterpret_cast<float2 *>(sm + L.rv);   // R as double-float
   float2 *xs = reinterpret_cast<float2 *>(sm + L.xs);
   float2 *am = reinterpret_cast<float2 *>(sm + L.am);
   float2 *tm = reinterpret_cast<float2 *>(sm + L.t);
@@ -98,6 +96,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   // J^c: thread t sums element e = t % E over part t / E of the (q, l) range (E = nn rounded up
   // to a warp; P parts fill the block), then the parts add up in a fixed order
   const int E = small_elems(nb), P = small_parts(nb);
+  const float tol_upd = (float)p.tol_upd, tol_res = (float)p.tol_res;
   const int Kc = o.q_c * nb;
 
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
@@ -127,8 +126,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       double s = 0.0;
       if (k < n)
         for (int q = 0; q < o.q_f; ++q) s = fma(th[o.q_a + o.q_c + q], o.f[(size_t)q * o.n_max + k], s);
-      fm[k] = s;
-      u[k] = 0.0;
+      float h, lo;
+      df_split(s, h, lo);
+      fm2[k] = make_float2(h, lo);
       u2[k] = make_float2(0.f, 0.f);
     }
     __syncthreads();
@@ -145,11 +145,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       two_sum(h, l, s, ee);
       am[e] = make_float2(s, ee);
     }
-    // FP64 reductions by warp 0 alone (n <= 32: one entry per lane)
-    double fscale = 1.0;
+    // norms for the stopping test in FP32 (relative accuracy 1e-7 of a norm is ample for a test
+    // against 1e-10), by warp 0 (n <= 32: one entry per lane): the FP64 pipe is narrow
+    float fscale = 1.f;
     if (w == 0) {
-      const double fk = lane < n ? fm[lane] : 0.0;
-      fscale = fmax(1.0, sqrt(warp_sum(fk * fk)));
+      const float fk = lane < n ? fm2[lane].x : 0.f;
+      fscale = fmaxf(1.f, sqrtf(warp_sum(fk * fk)));
     }
     rb_query_info qi = {RB_Q_NOT_CONVERGED, 0, RB_PREC_MIXED, 0, 0.0, 0.0};
     bool done = false;
@@ -213,10 +214,20 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
           const float2 t = tm[(size_t)k * nb + j];
           df_fma(h, l, t.x, t.y, uu.x, uu.y);
         }
-        const double r = df_warp_sum(h, l) - fm[k];
+        // (h, l) summed over the warp in double-float, minus f(mu)[k]
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+          df_add(h, l, h2, l2);
+        }
         if (lane == 0) {
-          J[k * ld + n] = (float)(-r);
-          rv[k] = r;
+          const float2 f = fm2[k];
+          df_add(h, l, -f.x, -f.y);
+          float rh, rl;
+          two_sum(h, l, rh, rl);
+          J[k * ld + n] = -rh;
+          rv[k] = make_float2(rh, rl);
         }
       }
       __syncthreads();
@@ -224,9 +235,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       // residual norm, elimination and update by warp 0 (n <= 32: one row per lane)
       if (w == 0) {
         int status = RB_Q_NOT_CONVERGED;
-        double dn = 0.0;
-        const double rk = lane < n ? rv[lane] : 0.0;
-        const double rn = sqrt(warp_sum(rk * rk));
+        float dn = 0.f;
+        const float rk = lane < n ? rv[lane].x : 0.f;
+        const float rn = sqrtf(warp_sum(rk * rk));
         if (!isfinite(rn)) {
           status = RB_Q_NONFINITE;
         } else {
@@ -234,17 +245,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
           if (gepp_aug_warp<1>(J, ld, n, x, pseq)) {
             status = RB_Q_SINGULAR;
           } else {
-            const double d = lane < n ? (double)x[0] : 0.0;
-            if (lane < n) {
-              const double un = u[lane] + d;
-              u[lane] = un;
-              float h, lo;
-              df_split(un, h, lo);
-              u2[lane] = make_float2(h, lo);
+            const float d = lane < n ? x[0] : 0.f;
+            if (lane < n) {  // u += delta in double-float
+              float2 uu = u2[lane];
+              df_add(uu.x, uu.y, d, 0.f);
+              float s2, e2;
+              two_sum(uu.x, uu.y, s2, e2);
+              u2[lane] = make_float2(s2, e2);
             }
-            dn = sqrt(warp_sum(d * d));
+            dn = sqrtf(warp_sum(d * d));
             if (!isfinite(dn)) status = RB_Q_NONFINITE;
-            else if (dn <= p.tol_upd && rn <= p.tol_res * fscale) status = RB_Q_OK;
+            else if (dn <= tol_upd && rn <= tol_res * fscale) status = RB_Q_OK;
           }
         }
         if (lane == 0) {
@@ -260,7 +271,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       done = qi.status != RB_Q_NOT_CONVERGED || qi.iters >= p.max_iter;
       __syncthreads();  // red and the shared state are reused
     }
-    for (int i = tid; i < o.n_max; i += blockDim.x) p.u[(size_t)b * o.n_max + i] = i < n ? u[i] : 0.0;
+    for (int i = tid; i < o.n_max; i += blockDim.x)
+      p.u[(size_t)b * o.n_max + i] = i < n ? (double)u2[i].x + (double)u2[i].y : 0.0;
     if (tid == 0 && p.info) p.info[b] = qi;
     __syncthreads();
   }
