@@ -340,7 +340,7 @@ bool csr_ok(const rb_csr *M, int rows, int cols) {
 int upload_csr(rb_ctx *ctx, Buffers &B, const rb_csr *M, int **ip, int **ix, double **v,
                const char *what) {
   const int nnz = M->indptr[M->rows];
-  if (nnz < 0) return set_error(ctx, RB_ERR_ARG, "%s: negative entry count", what);
+  if (M->indptr[0] != 0 || nnz < 0) return set_error(ctx, RB_ERR_ARG, "%s: indptr[0] must be 0", what);
   for (int r = 0; r < M->rows; ++r)
     if (M->indptr[r + 1] < M->indptr[r]) return set_error(ctx, RB_ERR_ARG, "%s: indptr not monotone", what);
   for (int e = 0; e < nnz; ++e)

@@ -30,7 +30,8 @@ EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_
            "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
            "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots", "rb_tuning",
            "rb_load_pressure_modes", "rb_reconstruct_pressure", "rb_reconstruct_pressure_device",
-           "rb_save_operators", "rb_load_operator_file"]
+           "rb_save_operators", "rb_load_operator_file", "rb_offline_pod", "rb_offline_project",
+           "rb_offline_project_vector", "rb_offline_tensor"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>",
               "k_newton_system", "k_prep", "k_reconstruct", "k_newton_small"]
@@ -51,6 +52,28 @@ class rb_config(ctypes.Structure):
                 ("mem_budget", ctypes.c_size_t), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("theta_family", ctypes.c_int),
                 ("serve_slots", ctypes.c_int), ("pressure_method", ctypes.c_int)]
+
+
+class rb_csr(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int), ("cols", ctypes.c_int), ("indptr", ctypes.c_void_p),
+                ("indices", ctypes.c_void_p), ("values", ctypes.c_void_p)]
+
+
+class rb_trilinear_term(ctypes.Structure):
+    _fields_ = [("P", rb_csr), ("Q", rb_csr), ("R", rb_csr), ("weight", ctypes.c_void_p)]
+
+
+RB_POD_K_MAX = 128
+
+
+def _csr(M, keep):
+    """rb_csr over a scipy-style CSR matrix (indptr, indices, data kept alive in `keep`)."""
+    indptr = np.ascontiguousarray(M.indptr, dtype=np.int32)
+    indices = np.ascontiguousarray(M.indices, dtype=np.int32)
+    values = np.ascontiguousarray(M.data, dtype=np.float64)
+    keep += [indptr, indices, values]
+    return rb_csr(M.shape[0], M.shape[1], indptr.ctypes.data, indices.ctypes.data,
+                  values.ctypes.data)
 
 
 class rb_query_info(ctypes.Structure):
@@ -103,6 +126,10 @@ def library():
         L.rb_serve_stats.argtypes = [P, P, P, P]
         L.rb_serve_slots.argtypes = [P]
         L.rb_tuning.argtypes = [P, I, P, P]
+        L.rb_offline_pod.argtypes = [P, P, I, I, P, I, P, P]
+        L.rb_offline_project.argtypes = [P, P, I, I, P, P]
+        L.rb_offline_project_vector.argtypes = [P, P, I, I, P, P]
+        L.rb_offline_tensor.argtypes = [P, P, I, I, P, I, P]
         for name in EXPORTS:
             if name not in ("rb_config_default", "rb_destroy", "rb_last_error"):
                 getattr(L, name).restype = I
@@ -361,6 +388,53 @@ class Context:
         if rc == RB_PENDING:
             return rc
         return self._check(rc, "rb_solve_device_status")
+
+    # --- offline stage ------------------------------------------------------------------
+    def rb_offline_pod(self, S, Z, n):
+        """Modes V [n][N] (rows, orthonormal in Z) and eigenvalues [K] of the snapshots S [K][N]."""
+        S = _f64(S)
+        K, N = S.shape
+        keep = []
+        z = _csr(Z, keep)
+        V = np.empty((n, N))
+        lam = np.empty(K)
+        self._check(library().rb_offline_pod(self.h, _ptr(S), K, N, ctypes.byref(z), n, _ptr(V),
+                                             _ptr(lam)), "rb_offline_pod")
+        return lam, V
+
+    def rb_offline_project(self, V, M):
+        V = _f64(V)
+        n, N = V.shape
+        keep = []
+        m = _csr(M, keep)
+        out = np.empty((n, n))
+        self._check(library().rb_offline_project(self.h, _ptr(V), n, N, ctypes.byref(m), _ptr(out)),
+                    "rb_offline_project")
+        return out
+
+    def rb_offline_project_vector(self, V, f):
+        V, f = _f64(V), _f64(f)
+        n, N = V.shape
+        out = np.empty(n)
+        self._check(library().rb_offline_project_vector(self.h, _ptr(V), n, N, _ptr(f), _ptr(out)),
+                    "rb_offline_project_vector")
+        return out
+
+    def rb_offline_tensor(self, V, terms):
+        """C [n][n][n] (index [j][l][k]) of the form given by terms [(P, Q, R, weight or None)]."""
+        V = _f64(V)
+        n, N = V.shape
+        keep = []
+        arr = (rb_trilinear_term * len(terms))()
+        for i, (Pm, Qm, Rm, w) in enumerate(terms):
+            wt = None if w is None else _f64(w)
+            keep.append(wt)
+            arr[i] = rb_trilinear_term(_csr(Pm, keep), _csr(Qm, keep), _csr(Rm, keep),
+                                       None if wt is None else wt.ctypes.data)
+        out = np.empty((n, n, n))
+        self._check(library().rb_offline_tensor(self.h, _ptr(V), n, N, arr, len(terms), _ptr(out)),
+                    "rb_offline_tensor")
+        return out
 
     def rb_eval(self, mu, n, u, precision=RB_PREC_FP64, jacobian=True):
         mu = _f64(mu).reshape(-1, 2)

@@ -65,7 +65,8 @@ def test_struct_layouts_match_c_compiler(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     structs = {"rb_config": rb.rb_config, "rb_operators": rb.rb_operators,
-               "rb_query_info": rb.rb_query_info}
+               "rb_query_info": rb.rb_query_info, "rb_csr": rb.rb_csr,
+               "rb_trilinear_term": rb.rb_trilinear_term}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rb.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
