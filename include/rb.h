@@ -350,7 +350,9 @@ enum {
   RB_K_PREP = 9,         /* mixed: per-query theta, f(mu), A(mu) at the start of a solve */
   RB_K_RECONSTRUCT = 10, /* pressure reconstruction p = P_hat u (either precision) */
   RB_K_NEWTON_SMALL = 11, /* mixed, n_max <= 32: the whole Newton solve, one CTA per query */
-  RB_K_COUNT = 12
+  RB_K_OFFLINE_EIG = 12,  /* offline: covariance Gram product and Jacobi eigensolver */
+  RB_K_OFFLINE_TENSOR = 13, /* offline: the tensor's triple contraction over the points */
+  RB_K_COUNT = 14
 };
 int rb_profile(rb_ctx *ctx, int enable);
 int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launches);

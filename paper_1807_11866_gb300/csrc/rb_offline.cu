@@ -437,12 +437,14 @@ int rb_offline_pod(rb_ctx *ctx, const double *S, int K, int N, const rb_csr *Z, 
   if (e != cudaSuccess) return cuda_fail(ctx, e, "snapshots upload");
   if ((rc = transpose(ctx, K, N, dS, ST)) != RB_OK) return rc;            // ST [N][K]
   if ((rc = spmm(ctx, N, K, ip, ix, zv, ST, ZS)) != RB_OK) return rc;      // Z S   [N][K]
-  if ((rc = gram(ctx, B, N, K, K, ST, ZS, C)) != RB_OK) return rc;         // S^T Z S (Eq. covmx)
   const size_t js = jacobi_smem_bytes(K);
   e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)js);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_jacobi attribute");
+  const int mk = prof_begin(ctx, RB_K_OFFLINE_EIG, ctx->stream);
+  if ((rc = gram(ctx, B, N, K, K, ST, ZS, C)) != RB_OK) return rc;         // S^T Z S (Eq. covmx)
   k_jacobi<<<1, kJacThreads, js, ctx->stream>>>(K, C, W, lam, 40, sweeps);
   k_rank<<<1, 256, 0, ctx->stream>>>(K, lam, perm, lams);
+  prof_end(ctx, mk, ctx->stream);
   const size_t ms = 8 * (size_t)K * n;
   if (ms > (size_t)ctx->max_smem) return set_error(ctx, RB_ERR_ARG, "rb_offline_pod: K n too large");
   e = cudaFuncSetAttribute(k_modes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ms);
@@ -569,7 +571,9 @@ int rb_offline_tensor(rb_ctx *ctx, const double *V, int n, int N, const rb_trili
     const int kblocks = (n + kTriK - 1) / kTriK;
     const int chunk_pts = (pts + chunks - 1) / chunks;
     dim3 grid((n + kTriJ - 1) / kTriJ, (n + kTriJ - 1) / kTriJ, kblocks * chunks);
+    const int mk = prof_begin(ctx, RB_K_OFFLINE_TENSOR, ctx->stream);
     k_triple<<<grid, 256, 0, ctx->stream>>>(pts, n, chunk_pts, EP, EQ, ER, part);
+    prof_end(ctx, mk, ctx->stream);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "k_triple");
     // the term's buffers are freed after its kernels have run
     if ((rc = finish(ctx, "rb_offline_tensor term")) != RB_OK) return rc;

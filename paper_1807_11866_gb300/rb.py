@@ -34,7 +34,8 @@ EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_
            "rb_offline_project_vector", "rb_offline_tensor"]
 RB_K_NAMES = ["k_newton_fp64", "k_pressure", "k_build_x", "k_tc_gemm<plain>",
               "k_tc_gemm<sliced>", "k_lu_mixed", "k_mixed_init", "k_tc_gemm<sliced,pressure>",
-              "k_newton_system", "k_prep", "k_reconstruct", "k_newton_small"]
+              "k_newton_system", "k_prep", "k_reconstruct", "k_newton_small", "k_offline_eig",
+              "k_offline_tensor"]
 
 
 class rb_operators(ctypes.Structure):

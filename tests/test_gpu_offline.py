@@ -47,7 +47,10 @@ def test_pod_matches_oracle(rb, case):
     d = V - s[:, None] * V_o
     err = np.sqrt(np.einsum("jn,jn->j", d, (m.Z @ d.T).T))
     # eigenvector accuracy of either side: eps lambda_max / gap
-    gap = np.minimum(np.abs(np.diff(lam_o[: n + 1])), np.abs(np.diff(lam_o[:n + 1], prepend=np.inf)))[:n]
+    lo = lam_o[: n + 1]
+    below = lo[:n] - lo[1:]
+    above = np.concatenate([[np.inf], lo[: n - 1] - lo[1:n]])
+    gap = np.minimum(above, below)
     assert np.all(err <= 1e-12 * lam_o[0] / gap + 1e-12), (err, gap)
 
 
