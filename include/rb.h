@@ -312,9 +312,9 @@ typedef struct {           /* one quadrature term of a pointwise trilinear form:
  * (N x N, symmetric positive semidefinite, e.g. the H1-seminorm stiffness), its eigenpairs
  * (cyclic Jacobi, FP64) in decreasing order, and the n modes
  * psi_j = lambda_j^(-1/2) sum_i v^j_i phi_i into V_out [n][N] (row j = mode j, orthonormal in Z);
- * lambda_out [K] (or NULL) all K eigenvalues, decreasing. 1 <= n <= K <= RB_POD_K_MAX; n must
- * not exceed the number of positive eigenvalues (RB_ERR_ARG). Eigenvectors, and so modes, are
- * determined up to sign. */
+ * lambda_out [K] (or NULL) all K eigenvalues, decreasing. 1 <= n <= K <= RB_POD_K_MAX; lambda_n
+ * must exceed K eps lambda_1 (the numerical rank, RB_ERR_ARG otherwise). Eigenvectors, and so
+ * modes, are determined up to sign. */
 int rb_offline_pod(rb_ctx *ctx, const double *S, int K, int N, const rb_csr *Z, int n,
                    double *V_out, double *lambda_out);
 

@@ -455,9 +455,10 @@ int rb_offline_pod(rb_ctx *ctx, const double *S, int K, int N, const rb_csr *Z, 
   e = cudaMemcpyAsync(hl.data(), lams, 8 * (size_t)K, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "eigenvalues");
-  if (!(hl[n - 1] > 0.0) || !std::isfinite(hl[0]))
-    return set_error(ctx, RB_ERR_ARG, "rb_offline_pod: eigenvalue %d is %g: n exceeds the rank of "
-                     "the snapshots", n, hl[n - 1]);
+  // an eigenvalue within rounding of zero (K eps of the largest) has no meaningful mode
+  if (!(hl[n - 1] > (double)K * 2.220446049250313e-16 * hl[0]) || !std::isfinite(hl[0]))
+    return set_error(ctx, RB_ERR_ARG, "rb_offline_pod: eigenvalue %d is %g (largest %g): n exceeds "
+                     "the numerical rank of the snapshots", n, hl[n - 1], hl[0]);
   k_modes<<<std::max(1, std::min((N + 7) / 8, ctx->sms * 4)), 256, ms, ctx->stream>>>(N, K, n, ST, W,
                                                                                   lam, perm, VT);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "k_modes");
