@@ -482,22 +482,17 @@ __device__ __forceinline__ bool gepp_aug_warp(float *M, int ld, int n, float (&x
       }
     }
     __syncwarp();
-    // rank-`steps` update of the rows not yet used as pivots: the pivot rows' chunk is loaded
-    // once per column chunk and serves all of the lane's rows
+    // rank-`steps` update of the rows not yet used as pivots
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      if (step[s] != n) continue;
+      float4 *row = M4 + (lane + 32 * s) * ld4;
 #pragma unroll 2
-    for (int c = c0 + 1; c <= c_end; ++c) {
-      float4 pv[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        pv[t] = t < steps ? M4[prow[t] * ld4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int s = 0; s < R; ++s) {
-        if (step[s] != n) continue;
-        float4 *row = M4 + (lane + 32 * s) * ld4;
+      for (int c = c0 + 1; c <= c_end; ++c) {
         float4 a = row[c];
 #pragma unroll
         for (int t = 0; t < 4; ++t)
-          if (t < steps) a = fms4(a, lm[s][t], pv[t]);
+          if (t < steps) a = fms4(a, lm[s][t], M4[prow[t] * ld4 + c]);
         row[c] = a;
       }
     }
