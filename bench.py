@@ -504,7 +504,7 @@ def measure(args, wl, batch, steps, warmup, rank, world, local, dev, recon, cpu_
 FP64_PEAK_TFLOPS = 1.196  # FP64 FMA throughput measured on GB300 (152 SMs at 2070 MHz)
 # FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-DIGITS = int(os.environ.get("RB_DIGITS", "6"))  # digit slices of the sliced convection product
+DIGITS = int(os.environ.get("RB_DIGITS", "5"))  # digit slices of the sliced convection product
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels as they
 # stand, from ncu captures of this bench command on the n = 50 sweep (4096 queries) and on the
 # n = 300 dense regime; a kernel changed since its capture has no entry.

@@ -1318,25 +1318,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
       if (nrow > 0) {
         const int cc_lo = c_lo >> 2, cc_hi = n >> 2;  // float4 chunks covering columns c_lo .. n
         const int nch = cc_hi - cc_lo + 1, nrb = (nrow + 3) >> 2;
-        for (int t = tid; t < nch * nrb; t += blockDim.x) {
-          const int rb4 = t / nch, cc = cc_lo + (t - rb4 * nch);
-          const int r0 = r_lo + 4 * rb4;
-          float4 acc[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            acc[i] = r0 + i < rows ? reinterpret_cast<const float4 *>(M + (size_t)(k0 + r0 + i) * lda)[cc]
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int j = 0; j < kb; ++j) {
-            const float4 u = reinterpret_cast<const float4 *>(U + j * lda)[cc];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const float l = r0 + i < rows ? P[(r0 + i) * kPLd + j] : 0.f;
-              acc[i].x = fmaf(-l, u.x, acc[i].x);
-              acc[i].y = fmaf(-l, u.y, acc[i].y);
-              acc[i].z = fmaf(-l, u.z, acc[i].z);
-              acc[i].w = fmaf(-l, u.w, acc[i].w);
-            }
-          }
+        // store the 4 x 4 tile acc of rows r0.. and chunk cc (only columns c_lo .. n)
+        auto store_tile = [&](int r0, int cc, const float4 (&acc)[4]) {
           const int c4 = 4 * cc;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -1350,6 +1333,63 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
               if (c4 + 2 >= c_lo && c4 + 2 <= n) row[2] = acc[i].z;
               if (c4 + 3 >= c_lo && c4 + 3 <= n) row[3] = acc[i].w;
             }
+          }
+        };
+        if (PB <= 16 && nrb <= (int)blockDim.x) {
+          // a thread keeps one row block's multipliers in registers and walks a strided set of
+          // column chunks: one shared-memory load of U per 16 multiply-adds
+          const int G = blockDim.x / nrb;  // threads per row block
+          if (tid < G * nrb) {
+            const int rb4 = tid % nrb, g = tid / nrb;
+            const int r0 = r_lo + 4 * rb4;
+            float l[4][PB <= 16 ? PB : 1];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < (PB <= 16 ? PB : 1); ++j)
+                l[i][j] = (j < kb && r0 + i < rows) ? P[(r0 + i) * kPLd + j] : 0.f;
+            for (int cc = cc_lo + g; cc <= cc_hi; cc += G) {
+              float4 acc[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                acc[i] = r0 + i < rows ? reinterpret_cast<const float4 *>(M + (size_t)(k0 + r0 + i) * lda)[cc]
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int j = 0; j < (PB <= 16 ? PB : 1); ++j) {
+                if (j >= kb) break;
+                const float4 u = reinterpret_cast<const float4 *>(U + j * lda)[cc];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  acc[i].x = fmaf(-l[i][j], u.x, acc[i].x);
+                  acc[i].y = fmaf(-l[i][j], u.y, acc[i].y);
+                  acc[i].z = fmaf(-l[i][j], u.z, acc[i].z);
+                  acc[i].w = fmaf(-l[i][j], u.w, acc[i].w);
+                }
+              }
+              store_tile(r0, cc, acc);
+            }
+          }
+        } else {
+          for (int t = tid; t < nch * nrb; t += blockDim.x) {
+            const int rb4 = t / nch, cc = cc_lo + (t - rb4 * nch);
+            const int r0 = r_lo + 4 * rb4;
+            float4 acc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              acc[i] = r0 + i < rows ? reinterpret_cast<const float4 *>(M + (size_t)(k0 + r0 + i) * lda)[cc]
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < kb; ++j) {
+              const float4 u = reinterpret_cast<const float4 *>(U + j * lda)[cc];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const float l = r0 + i < rows ? P[(r0 + i) * kPLd + j] : 0.f;
+                acc[i].x = fmaf(-l, u.x, acc[i].x);
+                acc[i].y = fmaf(-l, u.y, acc[i].y);
+                acc[i].z = fmaf(-l, u.z, acc[i].z);
+                acc[i].w = fmaf(-l, u.w, acc[i].w);
+              }
+            }
+            store_tile(r0, cc, acc);
           }
         }
       }
@@ -1828,7 +1868,7 @@ static int mixed_layouts(rb_ctx *ctx, MixedState *M, cudaStream_t st) {
   M->kb1 = 0;
   M->Kpad = M->Kpad0 + 64 * M->kb1;
   M->Npad = round_up(M->nb * M->nb, kTcBN);
-  M->S0 = sliced_digits("RB_DIGITS", 6);
+  M->S0 = sliced_digits("RB_DIGITS", 5);
   M->S1 = sliced_digits("RB_DIGITS_LINEAR", 7);
   M->Smax = M->kb1 ? std::max(M->S0, M->S1) : M->S0;
   int rc;

@@ -40,10 +40,12 @@ def test_roofline_work_counts_chord_steps():
         assert np.isclose(rl["k_tc_gemm<plain>"]["achieved"], plain / 1e-3 / 1e12)
         assert np.isclose(rl["k_newton_system"]["achieved"], sysb / 1e-3 / 1e9)
         assert np.isclose(rl["k_tc_gemm<sliced>"]["achieved"], sliced / 1e-3 / 1e12)
-        # the products issued: 3 split-BF16 products per Jacobian, 21 digit pairs per residual
+        # the products issued: 3 split-BF16 products per Jacobian, S (S + 1) / 2 digit pairs per
+        # residual (S = 5 digit slices: 15)
         assert np.isclose(rl["k_tc_gemm<plain>"]["issued_tflops"], 3 * plain / 1e-3 / 1e12)
         key = "issued_tflops_max" if bench.incremental_residual(1) else "issued_tflops"
-        assert np.isclose(rl["k_tc_gemm<sliced>"][key], 21 * sliced / 1e-3 / 1e12)
+        P = bench.DIGITS * (bench.DIGITS + 1) // 2
+        assert np.isclose(rl["k_tc_gemm<sliced>"][key], P * sliced / 1e-3 / 1e12)
         assert rl["k_tc_gemm<sliced>"]["work"] == "algorithmic"
         assert np.isclose(rl["k_tc_gemm<sliced>"]["frac"],
                           rl["k_tc_gemm<sliced>"]["achieved"] / rl["k_tc_gemm<sliced>"]["peak"])
