@@ -2863,13 +2863,15 @@ static int solve_small(rb_ctx *ctx, const double *d_mu, const double *d_theta, i
   int rc;
   if ((rc = mixed_layouts(ctx, R, st)) != RB_OK) return rc;
   const int nb = o.n_max;
-  if (!R->Dt2) {  // D~ as double-float, [q_c][l][k][j] with the n_max strides
+  if (!R->Dt2) {  // D~ as double-float, rows (q, l) of nb^2, padded to whole bulk-copy chunks
     void *p;
-    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_c * nb * nb * nb, "D~ (double-float)")) != RB_OK)
-      return rc;
+    const size_t rows = (size_t)small_dt_rows(o.q_c, nb), nn = (size_t)nb * nb;
+    if ((rc = ctx_alloc(ctx, &p, 8 * rows * nn, "D~ (double-float)")) != RB_OK) return rc;
     R->Dt2 = (float2 *)p;
-    k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.Dt, R->Dt2, (size_t)o.q_c * nb * nb * nb);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(R->Dt2, 0, 8 * rows * nn, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "D~ (double-float)");
+    k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.Dt, R->Dt2, (size_t)o.q_c * nb * nn);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "D~ (double-float)");
   }
   SmallParams sp{};
@@ -2886,12 +2888,23 @@ static int solve_small(rb_ctx *ctx, const double *d_mu, const double *d_theta, i
   sp.A2 = R->A2;
   sp.u = d_u;
   sp.info = info;
+  sp.err = R->dev_words + 1;  // this launch's error word, latched into the sticky one below
+  cudaError_t e = cudaMemsetAsync(R->dev_words + 1, 0, 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
   const int mk = prof_begin(ctx, RB_K_NEWTON_SMALL, st);
-  const cudaError_t e = launch_newton_small(sp, ctx->sms, st);
+  e = launch_newton_small(sp, ctx->sms, st);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_small");
+  k_latch_error<<<1, 1, 0, st>>>(R->dev_words);
   if (d_p && o.m > 0 && o.B)  // the FP64 recovery of Eq. sup-vvar for the converged queries
-    return solve_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st);
+    if ((rc = solve_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st)) != RB_OK) return rc;
+  // as for a graph solve: the error words come back behind the solve, read by
+  // mixed_solve_status without a synchronisation here
+  e = cudaMemcpyAsync(R->h_words + 12, R->dev_words + 4, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(R->done_ev, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve completion");
+  R->pending = true;
+  R->pending_st = st;
   return RB_OK;
 }
 
