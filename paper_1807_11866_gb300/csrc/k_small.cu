@@ -17,7 +17,6 @@
 
 #include "rb_ctx.h"
 #include "rb_small.cuh"
-#include "tc_ptx.cuh"
 
 namespace rb {
 
@@ -50,7 +49,7 @@ __host__ __device__ inline int small_parts(int nb) {
 
 // shared-memory carve-up (bytes); every block 16-byte aligned
 struct SmallSmem {
-  int th, th2, u2, fm, rv, xs, am, t, jaug, ring, bars, pseq, red, total;
+  int th, th2, u2, fm, rv, xs, am, t, jaug, part, pseq, red, total;
   __host__ __device__ SmallSmem(const DevOps &o, int nb) {
     auto al = [](int b) { return (b + 15) & ~15; };
     int p = 0;
@@ -63,66 +62,12 @@ struct SmallSmem {
     am = p; p += al(8 * nb * nb);           // A(mu) as double-float
     t = p; p += al(8 * nb * nb);            // A(mu) + J^c / 2 as double-float
     jaug = p; p += al(4 * nb * small_ld(nb));
-    ring = p; p += kSmallStages * small_chunk_rows(nb) * 8 * nb * nb;  // the D~ stream
-    bars = p; p += al(8 * kSmallStages);
+    part = p; p += al(8 * small_parts(nb) * small_elems(nb));  // partial sums of J^c
     pseq = p; p += al(4 * ((nb + 3) & ~3));
     red = p; p += al(8 * 4);                 // the step's norms and status
     total = p;
   }
 };
-
-// Gaussian elimination with partial pivoting of [M | b] (n <= 32) by one warp, the rows in
-// registers: lane r holds row r (a[j] = M[r][j], j < 32; rhs = b[r]). Every step is unrolled at
-// compile time so that the row stays in registers: the pivot of column p is the first row of
-// largest magnitude among the rows not used yet (one unsigned warp maximum over pivot_key), the
-// pivot row is broadcast entry by entry with shuffles, and the other free rows are updated; then
-// back substitution in step order. Returns true (all lanes) on a zero or non-finite pivot;
-// otherwise x (lane r: solution entry r).
-__device__ __forceinline__ bool gepp_rows_warp32(float (&a)[32], float rhs, int n, float &x) {
-  const int lane = threadIdx.x & 31;
-  bool free_row = lane < n;  // not yet used as a pivot row
-  int my_step = -1;          // the step at which this row was the pivot
-  float dinv = 0.f;
-  int plane[32];             // pivot lane of every step
-#pragma unroll
-  for (int p = 0; p < 32; ++p) {
-    plane[p] = 0;
-    if (p < n) {
-      const unsigned key = free_row ? pivot_key(a[p], lane) : 0u;
-      const unsigned best = __reduce_max_sync(0xffffffffu, key);
-      const int piv = 255 - (int)(best & 255u);
-      const float pv = __shfl_sync(0xffffffffu, a[p], piv);
-      if (!(fabsf(pv) > 0.f) || !(fabsf(pv) < 0x1p126f)) return true;  // uniform
-      const float rinv = __fdividef(1.0f, pv);
-      plane[p] = piv;
-      if (lane == piv) {
-        free_row = false;
-        my_step = p;
-        dinv = rinv;
-      }
-      const float l = free_row ? a[p] * rinv : 0.f;
-#pragma unroll
-      for (int j = p + 1; j < 32; ++j) {
-        const float pj = __shfl_sync(0xffffffffu, a[j], piv);
-        a[j] = fmaf(-l, pj, a[j]);
-      }
-      const float pb = __shfl_sync(0xffffffffu, rhs, piv);
-      rhs = fmaf(-l, pb, rhs);
-    }
-  }
-  // back substitution: x_p from the pivot row of step p, then the earlier pivot rows' rhs
-  float xv = 0.f;
-#pragma unroll
-  for (int p = 31; p >= 0; --p) {
-    if (p < n) {
-      const float xp = __shfl_sync(0xffffffffu, rhs * dinv, plane[p]);
-      if (lane == p) xv = xp;
-      if (my_step >= 0 && my_step < p) rhs = fmaf(-a[p], xp, rhs);
-    }
-  }
-  x = xv;
-  return false;
-}
 
 }  // namespace
 
@@ -142,8 +87,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   float2 *am = reinterpret_cast<float2 *>(sm + L.am);
   float2 *tm = reinterpret_cast<float2 *>(sm + L.t);
   float *J = reinterpret_cast<float *>(sm + L.jaug);
-  float2 *ring = reinterpret_cast<float2 *>(sm + L.ring);
-  uint64_t *full = reinterpret_cast<uint64_t *>(sm + L.bars);
+  float2 *part = reinterpret_cast<float2 *>(sm + L.part);
   int *pseq = reinterpret_cast<int *>(sm + L.pseq);
   double *red = reinterpret_cast<double *>(sm + L.red);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -151,24 +95,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
   const size_t nn = (size_t)nb * nb;
   // J^c: thread t sums element e = t % E over part t / E of the (q, l) range (E = nn rounded up
   // to a warp; P parts fill the block), then the parts add up in a fixed order
+  const int E = small_elems(nb), P = small_parts(nb);
   const float tol_upd = (float)p.tol_upd, tol_res = (float)p.tol_res;
   const int Kc = o.q_c * nb;
-  // the D~ stream: chunks of CH rows (q, l) by bulk copies into a ring of kSmallStages stages,
-  // one mbarrier per stage; g counts the chunks this CTA has consumed (phase of every stage)
-  const int CH = small_chunk_rows(nb), nchunks = (Kc + CH - 1) / CH;
-  const uint32_t cbytes = (uint32_t)(CH * nn * sizeof(float2));
-  if (tid == 0) {
-    for (int st = 0; st < kSmallStages; ++st) tc::mbar_init(&full[st], 1);
-    tc::fence_barrier_init();
-  }
-  __syncthreads();
-  unsigned g = 0, g_end = 0;
-  bool failed = false;
-  auto issue = [&](unsigned gc, int c) {  // chunk c of the stream as global chunk gc (thread 0)
-    uint64_t *bar = &full[gc % kSmallStages];
-    tc::mbar_expect_tx(bar, cbytes);
-    tc::bulk_load(ring + (size_t)(gc % kSmallStages) * CH * nn, p.Dt2 + (size_t)c * CH * nn, cbytes, bar);
-  };
 
   for (int b = blockIdx.x; b < p.nq; b += gridDim.x) {
     const int n = p.nsz ? p.nsz[b] : o.n_max;
@@ -239,53 +168,42 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       __syncthreads();
       // J^c and T = A(mu) + J^c / 2; J = fl32(A(mu) + J^c) into the augmented matrix
       const bool zero = qi.iters == 0;  // u = 0: J^c = 0
-      float jh[2] = {0.f, 0.f}, jl[2] = {0.f, 0.f};  // J^c of elements tid, tid + blockDim
       if (!zero) {
-        if (tid == 0)
-          for (int c = 0; c < kSmallStages && c < nchunks; ++c) issue(g + c, c);
-        g_end = g + nchunks;  // the chunks of this pass (all issued by its end)
-        for (int c = 0; c < nchunks; ++c, ++g) {
-          // every thread waits (bounded) for the chunk; a wait that gives up ends the kernel
-          const bool ok = tc::mbar_wait(&full[g % kSmallStages], (g / kSmallStages) & 1, p.err, 7);
-          if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-          }
-          const float2 *D = ring + (size_t)(g % kSmallStages) * CH * nn;
-          const int i0 = c * CH, i1 = min(Kc, i0 + CH);
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int e = tid + r * (int)blockDim.x;
-            if (e >= (int)nn) break;
-            const int k = e / nb, j = e - k * nb;
-            if (k >= n || j >= n) continue;
-            float h = jh[r], l = jl[r];
+        for (int t = tid; t < P * E; t += blockDim.x) {
+          const int e = t % E, pt = t / E;
+          const int k = e / nb, j = e - k * nb;
+          float h = 0.f, l = 0.f;
+          if (e < (int)nn && k < n && j < n) {
+            const int i0 = (int)(((long long)Kc * pt) / P), i1 = (int)(((long long)Kc * (pt + 1)) / P);
+            const float2 *D = p.Dt2 + e;
+#pragma unroll kSmallUnroll
             for (int i = i0; i < i1; ++i) {
               const float2 x = xs[i];
-              const float2 d = D[(size_t)(i - i0) * nn + e];
+              const float2 d = __ldg(D + (size_t)i * nn);
               df_fma(h, l, d.x, d.y, x.x, x.y);
             }
-            jh[r] = h;
-            jl[r] = l;
           }
-          __syncthreads();  // the stage is free again
-          if (tid == 0 && c + kSmallStages < nchunks) issue(g + kSmallStages, c + kSmallStages);
+          part[t] = make_float2(h, l);
         }
-        if (failed) break;
+        __syncthreads();
       }
       for (size_t e = tid; e < nn; e += blockDim.x) {
         const int k = (int)(e / nb), j = (int)(e - (size_t)k * nb);
-        const int r = (int)(e / blockDim.x);
-        float h = r == 0 ? jh[0] : jh[1], l = r == 0 ? jl[0] : jl[1];
+        float h = 0.f, l = 0.f;
+        if (!zero)
+          for (int pt = 0; pt < P; ++pt) {
+            const float2 v = part[pt * E + e];
+            df_add(h, l, v.x, v.y);
+          }
         float s, ee;
         two_sum(h, l, s, ee);  // J^c[k][j] = s + ee
         const float2 a = am[e];
         float th2 = a.x, tl2 = a.y;
         df_add(th2, tl2, 0.5f * s, 0.5f * ee);
         tm[e] = make_float2(th2, tl2);
-        float jsh = a.x, jsl = a.y;
-        df_add(jsh, jsl, s, ee);
-        if (k < n && j < n) J[k * ld + j] = jsh + jsl;
+        float jh = a.x, jl = a.y;
+        df_add(jh, jl, s, ee);
+        if (k < n && j < n) J[k * ld + j] = jh + jl;
       }
       __syncthreads();
       // R[k] = sum_j T[k][j] u_j - f[k], one warp per row; -R into column n
@@ -323,15 +241,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
         if (!isfinite(rn)) {
           status = RB_Q_NONFINITE;
         } else {
-          float row[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) row[j] = (lane < n && j < n) ? J[lane * ld + j] : 0.f;
-          const float rhs = lane < n ? J[lane * ld + n] : 0.f;
-          float xs1;
-          if (gepp_rows_warp32(row, rhs, n, xs1)) {
+          float x[1];
+          if (gepp_aug_warp<1>(J, ld, n, x, pseq)) {
             status = RB_Q_SINGULAR;
           } else {
-            const float d = lane < n ? xs1 : 0.f;
+            const float d = lane < n ? x[0] : 0.f;
             if (lane < n) {  // u += delta in double-float
               float2 uu = u2[lane];
               df_add(uu.x, uu.y, d, 0.f);
@@ -357,16 +271,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_newton_small(SmallParams p) {
       done = qi.status != RB_Q_NOT_CONVERGED || qi.iters >= p.max_iter;
       __syncthreads();  // red and the shared state are reused
     }
-    if (failed) break;  // a bounded wait gave up: no result, the error word is raised
     for (int i = tid; i < o.n_max; i += blockDim.x)
       p.u[(size_t)b * o.n_max + i] = i < n ? (double)u2[i].x + (double)u2[i].y : 0.0;
     if (tid == 0 && p.info) p.info[b] = qi;
     __syncthreads();
-  }
-  if (failed && tid == 0) {  // let the copies already issued land (each wait bounded) before exit
-    const unsigned last = min(g_end, g + (unsigned)kSmallStages);
-    for (unsigned gc = g; gc < last; ++gc)
-      tc::mbar_wait(&full[gc % kSmallStages], (gc / kSmallStages) & 1, nullptr, 0);
   }
 }
 

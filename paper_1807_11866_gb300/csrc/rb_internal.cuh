@@ -121,9 +121,54 @@ __device__ __forceinline__ void df_fma(float &ah, float &al, float xh, float xl,
   al += e + pe;
 }
 
+// v = h + l with h = v rounded to FP32 (nearest, ties to even) and l = v - h rounded to FP32,
+// from v's bit pattern with integer operations. GB300's FP64 pipe issues about 1/64 of the FP32
+// rate and a warp instruction on it occupies it for the whole warp, so the two FP64 conversions
+// and the subtraction of the plain split cost far more than these integer steps. The significand
+// 1.m (53 bits) is t (its top 24 bits) followed by r (29 bits); rounding t up leaves r - 2^29, and
+// l = +-r 2^(e - 52) is r rounded to 24 bits by the integer conversion, scaled by a power of two
+// that is a normal FP32 value for 2^-74 <= |v| < 2^127. Zero is exact; other magnitudes,
+// infinities and NaN take the FP64 conversions (same results: the split is unique).
 __device__ __forceinline__ void df_split(double v, float &h, float &l) {
-  h = (float)v;
-  l = (float)(v - (double)h);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sgn = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
+  if (e >= -74 && e <= 126) {
+    unsigned t = 0x800000u | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    int r = (int)(lo & 0x1FFFFFFFu);
+    if (r > 0x10000000 || (r == 0x10000000 && (t & 1u))) {
+      t += 1u;
+      r -= 0x20000000;
+    }
+    int eh = e;
+    if (t == 0x1000000u) {  // rounded up into the next binade
+      t = 0x800000u;
+      eh += 1;
+    }
+    h = __uint_as_float(sgn | ((unsigned)(eh + 127) << 23) | (t & 0x7FFFFFu));
+    l = __int2float_rn(sgn ? -r : r) * __uint_as_float((unsigned)(e + 75) << 23);
+  } else if ((b << 1) == 0ull) {
+    h = __uint_as_float(sgn);
+    l = 0.f;
+  } else {
+    h = (float)v;
+    l = (float)(v - (double)h);
+  }
+}
+
+// The FP32 value x as a double, from its bit pattern (exact; zero and normal x by integer
+// operations, other values by the FP64 conversion).
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  if (ex != 0u && ex != 0xFFu) {
+    const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+    const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+    return __longlong_as_double((long long)(s | ((unsigned long long)(ex + 896u) << 52) | m));
+  }
+  if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+  return (double)x;
 }
 
 // warp-wide sum of double-float values, result in every lane as a double

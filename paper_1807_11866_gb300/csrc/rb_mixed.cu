@@ -63,6 +63,7 @@ struct MixedState {
   __nv_bfloat16 *Xj = nullptr, *Xd = nullptr;  // Xj: [3][bcap][Kpad0] (hi, hi, lo)
   int *xexp = nullptr;          // [2][bcap]
   float2 *ufT = nullptr;        // [nb][bcap]
+  float2 *u2 = nullptr;         // [bcap][nb] u as double-float (hi, lo), for the assembly
   float *Jc = nullptr;          // [bcap][Npad]
   double *Rc = nullptr;         // [bcap][nb]
   double *Rp = nullptr;         // [bcap][m]
@@ -355,6 +356,7 @@ struct BuildXParams {
   __nv_bfloat16 *Xj, *Xd;
   int *xexp;        // [2][b_pad]
   float2 *ufT;      // [nb][b_pad]
+  float2 *u2;       // [b_pad][nb] u as double-float (mode 0), read by the assembly
   double *out;      // [b_pad][nout], zeroed for each built query (not in increment mode)
   int nout;
   // increment mode (chord steps): the operand of C(u, u) - C(u - d, u - d) = J^c(d) (u - d / 2)
@@ -380,7 +382,8 @@ __device__ __forceinline__ int exp_of_max(double m) {
 __device__ __forceinline__ void digits_pair(double v0, double v1, int e, int S, __nv_bfloat16 *out,
                                             size_t slice_stride) {
   long long F0 = fixed_bits(v0, e, S), F1 = fixed_bits(v1, e, S);
-  const float s0 = v0 < 0 ? -1.f : 1.f, s1 = v1 < 0 ? -1.f : 1.f;
+  const float s0 = __double_as_longlong(v0) < 0 ? -1.f : 1.f;  // sign bits (no FP64 compare)
+  const float s1 = __double_as_longlong(v1) < 0 ? -1.f : 1.f;
   for (int i = S; i >= 1; --i) {
     int r0 = (int)F0, r1 = (int)F1;
     if (i > 1) {
@@ -404,6 +407,8 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
   const DevOps &o = p.o;
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  __shared__ float thh_s[kWarps][RB_Q_MAX];  // theta^c rounded to FP32, per warp
+  float *thh = thh_s[threadIdx.x >> 5];
   for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < p.nq; b += nw) {
     const rb_query_info qi = p.info[b];
     const bool want = p.mode == 0 ? is_active(qi, p.max_iter) : qi.status == RB_Q_OK;
@@ -411,6 +416,24 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
     const int n = p.nsz ? p.nsz[b] : o.n_max;
     const double *ta = p.theta + (size_t)b * o.n_theta, *tc = ta + o.q_a;
     const double *ub = p.u + (size_t)b * o.n_max;
+    const bool jsplit = p.mode == 0 && p.split;
+    float2 *u2b = p.u2 + (size_t)b * p.nb;
+    if (p.mode == 0) {
+      // u as double-float for the system assembly (and the Jacobian operand below), theta^c
+      // rounded to FP32: no FP64 conversion in the loops that follow
+      for (int j = lane; j < p.nb; j += 32) {
+        float h = 0.f, lo = 0.f;
+        if (j < n) df_split(ub[j], h, lo);
+        u2b[j] = make_float2(h, lo);
+      }
+      if (jsplit)
+        for (int q = lane; q < o.q_c; q += 32) {
+          float h, lo;
+          df_split(tc[q], h, lo);
+          thh[q] = h;
+        }
+      __syncwarp();
+    }
     // the vector in the operand: u, or the last update d in increment mode
     const double *vb = p.incr ? p.dU + (size_t)b * p.nb : ub;
     // (theta^c (x) v)[kap] at kap = q nb + l, zero past the query's size
@@ -479,12 +502,12 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
       const size_t off = (size_t)b * p.Kpad + kap;
       if (kap < p.Kpad0) {
         const int q1 = l + 1 < p.nb ? q : q + 1, l1 = l + 1 < p.nb ? l + 1 : 0;
-        const double x0 = xval(q, l), x1 = xval(q1, l1);
-        if (p.mode == 0 && p.split) {
-          // split BF16 operand of the Jacobian GEMM: [x_hi | x_hi | x_lo], always from u
-          const double y0 = p.incr ? ((q < o.q_c && l < n) ? tc[q] * ub[l] : 0.0) : x0;
-          const double y1 = p.incr ? ((q1 < o.q_c && l1 < n) ? tc[q1] * ub[l1] : 0.0) : x1;
-          const float f0 = (float)y0, f1 = (float)y1;
+        if (jsplit) {
+          // split BF16 operand of the Jacobian GEMM: [x_hi | x_hi | x_lo], always from u, from
+          // the FP32 product of the rounded factors (within 2 FP32 ulps of theta^c_q u_l: far
+          // below the 16 bits that the split keeps)
+          const float f0 = (q < o.q_c && l < n) ? thh[q] * u2b[l].x : 0.f;
+          const float f1 = (q1 < o.q_c && l1 < n) ? thh[q1] * u2b[l1].x : 0.f;
           const __nv_bfloat162 hi = __floats2bfloat162_rn(f0, f1);
           const __nv_bfloat162 lo =
               __floats2bfloat162_rn(f0 - __low2float(hi), f1 - __high2float(hi));
@@ -493,7 +516,7 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
           xj[jstride / 2] = hi;
           xj[jstride] = lo;
         }
-        if (p.digits) digits_pair(x0, x1, ex0, p.S0, p.Xd + off, sstride);
+        if (p.digits) digits_pair(xval(q, l), xval(q1, l1), ex0, p.S0, p.Xd + off, sstride);
       } else if (p.digits) {
         const int qa = kap - p.Kpad0;
         digits_pair(qa < o.q_a ? ta[qa] : 0.0, qa + 1 < o.q_a ? ta[qa + 1] : 0.0, e1, p.S1,
@@ -509,8 +532,9 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
     // the contraction vector: u, or u - d / 2 in increment mode
     for (int j = lane; j < p.nb; j += 32) {
       const double v = j < n ? (p.incr ? ub[j] - 0.5 * vb[j] : ub[j]) : 0.0;
-      const float hi = (float)v;
-      p.ufT[(size_t)j * p.b_pad + b] = make_float2(hi, (float)(v - (double)hi));
+      float hi, lo;
+      df_split(v, hi, lo);
+      p.ufT[(size_t)j * p.b_pad + b] = make_float2(hi, lo);
     }
     if (!p.incr)
       for (int k = lane; k < p.nout; k += 32) p.out[(size_t)b * p.nout + k] = 0.0;
@@ -694,6 +718,7 @@ struct LuParams {
   const float *Jc;       // [b_pad][ldj]
   const double *Rc;      // [b_pad][nb]: C_mu(u, u)
   double *u;             // [nq][n_max], updated in place
+  const float2 *u2;      // [nq][nb] u as double-float, written by k_build_x this iteration
   rb_query_info *info;   // [nq]
   int *active;           // count of queries still active after this iteration
   int eval_only;         // 1: write R and J (FP64) to R_out / J_out instead of solving
@@ -784,7 +809,7 @@ __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, 
   const bool vec = (nb & 1) == 0;  // even rows: 16-byte A(mu) and 8-byte J^c pairs are aligned
   const float2 *am = p.Amu + ((size_t)b * nb + k0) * nb;
   const float *jc = p.Jc + (size_t)b * p.ldj + (size_t)k0 * nb;
-  const double *ub = p.u + (size_t)b * p.o.n_max;
+  const float2 *u2 = p.u2 + (size_t)b * nb;
   float *J = EVAL ? nullptr : p.Jaug + ((size_t)b * nb + k0) * p.lda;
   const int rows = min(8, n - k0);
   float rh[8], rl[8], ch[8], cl[8];
@@ -814,8 +839,17 @@ __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, 
     }
     float uh0 = 0.f, ul0 = 0.f, uh1 = 0.f, ul1 = 0.f;
     if (RM != kResZero) {
-      df_split(ub[j], uh0, ul0);
-      if (two) df_split(ub[j + 1], uh1, ul1);
+      if (two && vec) {
+        const float4 uu = __ldg(reinterpret_cast<const float4 *>(u2 + j));
+        uh0 = uu.x, ul0 = uu.y, uh1 = uu.z, ul1 = uu.w;
+      } else {
+        const float2 u0 = __ldg(u2 + j);
+        uh0 = u0.x, ul0 = u0.y;
+        if (two) {
+          const float2 u1 = __ldg(u2 + j + 1);
+          uh1 = u1.x, ul1 = u1.y;
+        }
+      }
     }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -841,23 +875,44 @@ __device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, 
   if (RM != kResZero) df_warp_reduce8(rh, rl);
   if (RM == kResLow) df_warp_reduce8(ch, cl);
   const int r = lane >> 2, k = k0 + r;
-  double r2 = 0.0;
-  if ((lane & 3) == 0 && r < rows) {
-    const double rlin = RM != kResZero ? (double)rh[0] + (double)rl[0] : 0.0;
-    const double conv = RM == kResExact ? p.Rc[(size_t)b * nb + k]
-                                        : (RM == kResLow ? (double)ch[0] + (double)cl[0] : 0.0);
-    const double R = rlin + conv - p.Fm[(size_t)b * nb + k];
-    if (EVAL) {
-      p.R_out[(size_t)b * n + k] = R;
-    } else {
-      float *row = J + (size_t)r * p.lda;
-      row[n] = (float)(-R);
-      const int c_pad = ((n >> 2) << 2) + 4;  // columns n + 1 .. c_pad - 1 pad the last chunk
-      for (int c = n + 1; c < c_pad; ++c) row[c] = 0.f;
-      r2 = R * R;
+  if (EVAL) {  // R in FP64 for the caller
+    if ((lane & 3) == 0 && r < rows) {
+      const double rlin = RM != kResZero ? (double)rh[0] + (double)rl[0] : 0.0;
+      const double conv = RM == kResExact ? p.Rc[(size_t)b * nb + k]
+                                          : (RM == kResLow ? (double)ch[0] + (double)cl[0] : 0.0);
+      p.R_out[(size_t)b * n + k] = rlin + conv - p.Fm[(size_t)b * nb + k];
     }
+    return 0.0;
   }
-  return warp_sum(r2);
+  // R = A(mu) u + C_mu(u, u) - f(mu) in double-float (no FP64 instruction per row: each would
+  // occupy the narrow FP64 pipe for the whole warp); -R rounded to FP32 into column n
+  float Rs = 0.f;
+  if ((lane & 3) == 0 && r < rows) {
+    float Rh = 0.f, Rl = 0.f;
+    if (RM != kResZero) Rh = rh[0], Rl = rl[0];
+    if (RM == kResExact) {
+      float a, c;
+      df_split(p.Rc[(size_t)b * nb + k], a, c);
+      df_add(Rh, Rl, a, c);
+    } else if (RM == kResLow) {
+      df_add(Rh, Rl, ch[0], cl[0]);
+    }
+    float fh, fl;
+    df_split(p.Fm[(size_t)b * nb + k], fh, fl);
+    df_add(Rh, Rl, -fh, -fl);
+    float e;
+    two_sum(Rh, Rl, Rs, e);
+    float *row = J + (size_t)r * p.lda;
+    row[n] = -Rs;
+    const int c_pad = ((n >> 2) << 2) + 4;  // columns n + 1 .. c_pad - 1 pad the last chunk
+    for (int c = n + 1; c < c_pad; ++c) row[c] = 0.f;
+  }
+  // the group's sum of R[k]^2 in FP32 (the stopping test needs a few digits of the norm), unless
+  // some |R[k]| lies outside [2^-60, 2^60], where squares could leave the FP32 range
+  const float a = fabsf(Rs);
+  if (__any_sync(0xffffffffu, a > 0x1p60f || (a > 0.f && a < 0x1p-60f)))
+    return warp_sum((double)Rs * (double)Rs);
+  return f32_to_f64(warp_sum(Rs * Rs));
 }
 
 // Newton systems of the active queries: one warp per (query, group of 8 rows), so the work
@@ -906,12 +961,25 @@ __global__ void __launch_bounds__(kThreads, system_blocks(FIXED)) k_newton_syste
   }
 }
 
-// ||R|| of query b from its row groups' sums of squares, added in group order.
+// ||R|| of query b from its row groups' sums of squares (every lane of the calling warps, all
+// 32 present): the lanes take the groups, rounded to FP32 by integer operations, and add them
+// in FP32 (the stopping test needs a few digits of the norm); sums outside [2^-100, 2^100] are
+// added in FP64 instead, in group order.
 __device__ __forceinline__ double residual_norm(const LuParams &p, int b, int n) {
   const int G = (p.nb + 7) >> 3, gn = (n + 7) >> 3;
-  double s = 0.0;
-  for (int g = 0; g < gn; ++g) s += p.Rg[(size_t)b * G + g];
-  return sqrt(s);
+  const double *rg = p.Rg + (size_t)b * G;
+  float s = 0.f;
+  bool wide = false;
+  for (int g = threadIdx.x & 31; g < gn; g += 32) {
+    float h, l;
+    df_split(rg[g], h, l);
+    s += h;
+    wide |= !(h == 0.f || (h >= 0x1p-100f && h < 0x1p100f));
+  }
+  if (!__any_sync(0xffffffffu, wide)) return f32_to_f64(sqrtf(warp_sum(s)));
+  double t = 0.0;
+  for (int g = 0; g < gn; ++g) t += rg[g];
+  return sqrt(t);
 }
 
 // Warp-per-query elimination of the systems k_newton_system assembled: copy the query's
@@ -976,18 +1044,30 @@ __global__ void __launch_bounds__(kLuWarpBlock, R == 2 ? 5 : 2) k_lu_mixed_warp(
         for (int i = lane; i < n; i += 32) p.Piv[(size_t)b * p.nb + i] = pseq[i];
         if (lane == 0) p.Rn[b].x = kept_state(p, b);
       }
-      double dl = 0.0;
+      // u += delta in FP64; ||delta|| in FP32 unless some |delta_k| exceeds 2^60
+      float dl = 0.f;
+      bool wide = false;
 #pragma unroll
       for (int s = 0; s < R; ++s) {
         const int k = lane + 32 * s;
         if (k < n) {
-          const double d = (double)x[s];
-          dl += d * d;
+          const double d = f32_to_f64(x[s]);
+          dl = fmaf(x[s], x[s], dl);
+          wide |= !(fabsf(x[s]) <= 0x1p60f);
           ub[k] += d;
           if (p.dU) p.dU[(size_t)b * p.nb + k] = d;
         }
       }
-      const double dn = sqrt(warp_sum(dl));
+      double dn;
+      if (!__any_sync(0xffffffffu, wide)) {
+        dn = f32_to_f64(sqrtf(warp_sum(dl)));
+      } else {
+        double dd = 0.0;
+#pragma unroll
+        for (int s = 0; s < R; ++s)
+          if (lane + 32 * s < n) dd += (double)x[s] * (double)x[s];
+        dn = sqrt(warp_sum(dd));
+      }
       const double prev = qi.upd_norm;
       qi.upd_norm = dn;
       if (!isfinite(dn)) qi.status = RB_Q_NONFINITE;
@@ -1709,7 +1789,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve(PresSolveParams p) 
 static void release_state(rb_ctx *ctx, MixedState *M) {
   for (void *q : {(void *)M->Wj, (void *)M->WR.d, (void *)M->WP.d, (void *)M->A2, (void *)M->As2,
                   (void *)M->B2, (void *)M->Dt2, (void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT,
-                  (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
+                  (void *)M->u2, (void *)M->Jc, (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm,
                   (void *)M->Amu, (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn,
                   (void *)M->Piv, (void *)M->dU, (void *)M->refresh})
     ctx_free(ctx, q);
@@ -1919,7 +1999,7 @@ static MixedState *bucket(rb_ctx *ctx, int nb) {
 static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   const int b_pad = round_up(std::max(nq, 1), 256);  // whole 256-row tiles of a CTA pair
   if (b_pad <= M->bcap) return RB_OK;
-  for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->Jc,
+  for (void *q : {(void *)M->Xj, (void *)M->Xd, (void *)M->xexp, (void *)M->ufT, (void *)M->u2, (void *)M->Jc,
                   (void *)M->Rc, (void *)M->Rp, (void *)M->Th, (void *)M->Fm, (void *)M->Amu,
                   (void *)M->Asu, (void *)M->Bmu, (void *)M->Jaug, (void *)M->Rn, (void *)M->Piv,
                   (void *)M->dU, (void *)M->refresh})
@@ -1931,7 +2011,7 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   M->Bmu = nullptr;
   M->Rn = nullptr;
   M->Rg = nullptr;
-  M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->ufT = nullptr; M->Jc = nullptr;
+  M->Xj = M->Xd = nullptr; M->xexp = nullptr; M->ufT = nullptr; M->u2 = nullptr; M->Jc = nullptr;
   M->Rc = M->Rp = M->Th = M->Fm = M->Asu = nullptr;
   M->Amu = nullptr;
   M->bcap = 0;
@@ -1947,6 +2027,8 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   M->xexp = (int *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "u (float pairs)")) != RB_OK) return rc;
   M->ufT = (float2 *)p;
+  if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "u (double-float)")) != RB_OK) return rc;
+  M->u2 = (float2 *)p;
   if ((rc = ctx_alloc(ctx, &p, 4 * (size_t)b_pad * M->Npad, "J^c (FP32)")) != RB_OK) return rc;
   M->Jc = (float *)p;
   if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)b_pad * M->nb, "R (FP64)")) != RB_OK) return rc;
@@ -1985,6 +2067,7 @@ static int mixed_batch_scratch(rb_ctx *ctx, MixedState *M, int nq) {
   cudaMemsetAsync(M->Xd, 0, 2 * xs * M->Smax, ctx->stream);
   cudaMemsetAsync(M->xexp, 0, 8 * (size_t)b_pad, ctx->stream);
   cudaMemsetAsync(M->ufT, 0, 8 * (size_t)b_pad * M->nb, ctx->stream);
+  cudaMemsetAsync(M->u2, 0, 8 * (size_t)b_pad * M->nb, ctx->stream);
   if (!make_map(&M->tmXj, M->Xj, 3 * (uint64_t)b_pad, M->Kpad0, 128) ||
       !make_map(&M->tmXd, M->Xd, (uint64_t)M->Smax * b_pad, M->Kpad, 128))
     return set_error(ctx, RB_ERR_CUDA, "tensor map encode (X)");
@@ -2020,6 +2103,7 @@ static int launch_build_x(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   bx.Xd = M->Xd;
   bx.xexp = M->xexp;
   bx.ufT = M->ufT;
+  bx.u2 = M->u2;
   bx.out = out;
   bx.nout = nout;
   const int mk = prof_begin(ctx, RB_K_BUILD_X, st);
@@ -2393,6 +2477,7 @@ static LuParams solve_lu_params(rb_ctx *ctx, MixedState *M, const SolveArgs &a) 
   lp.Jc = M->Jc;
   lp.Rc = M->Rc;
   lp.u = a.u;
+  lp.u2 = M->u2;
   lp.info = a.info;
   lp.active = M->root->dev_words;  // one active count over all buckets
   lp.rmode = kResLadder;  // every query climbs zero -> low -> exact with its own iterations
@@ -2863,15 +2948,13 @@ static int solve_small(rb_ctx *ctx, const double *d_mu, const double *d_theta, i
   int rc;
   if ((rc = mixed_layouts(ctx, R, st)) != RB_OK) return rc;
   const int nb = o.n_max;
-  if (!R->Dt2) {  // D~ as double-float, rows (q, l) of nb^2, padded to whole bulk-copy chunks
+  if (!R->Dt2) {  // D~ as double-float, [q_c][l][k][j] with the n_max strides
     void *p;
-    const size_t rows = (size_t)small_dt_rows(o.q_c, nb), nn = (size_t)nb * nb;
-    if ((rc = ctx_alloc(ctx, &p, 8 * rows * nn, "D~ (double-float)")) != RB_OK) return rc;
+    const size_t nn = (size_t)nb * nb;
+    if ((rc = ctx_alloc(ctx, &p, 8 * (size_t)o.q_c * nb * nn, "D~ (double-float)")) != RB_OK) return rc;
     R->Dt2 = (float2 *)p;
-    cudaError_t e = cudaMemsetAsync(R->Dt2, 0, 8 * rows * nn, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "D~ (double-float)");
     k_split_f2<<<ctx->sms * 4, 256, 0, st>>>(o.Dt, R->Dt2, (size_t)o.q_c * nb * nn);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "D~ (double-float)");
   }
   SmallParams sp{};
@@ -2888,14 +2971,10 @@ static int solve_small(rb_ctx *ctx, const double *d_mu, const double *d_theta, i
   sp.A2 = R->A2;
   sp.u = d_u;
   sp.info = info;
-  sp.err = R->dev_words + 1;  // this launch's error word, latched into the sticky one below
-  cudaError_t e = cudaMemsetAsync(R->dev_words + 1, 0, 4, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "words");
   const int mk = prof_begin(ctx, RB_K_NEWTON_SMALL, st);
-  e = launch_newton_small(sp, ctx->sms, st);
+  cudaError_t e = launch_newton_small(sp, ctx->sms, st);
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_newton_small");
-  k_latch_error<<<1, 1, 0, st>>>(R->dev_words);
   if (d_p && o.m > 0 && o.B)  // the FP64 recovery of Eq. sup-vvar for the converged queries
     if ((rc = solve_pressure(ctx, d_mu, d_theta, nq, d_n, d_u, d_p, info, st)) != RB_OK) return rc;
   // as for a graph solve: the error words come back behind the solve, read by
