@@ -802,15 +802,16 @@ __host__ __device__ inline int aug_ld(int nb) {
 // part - f[k] (residual source RM). The 8 rows' loads of a column block are issued before their
 // arithmetic, and the row sums are reduce-scattered over the warp (df_warp_reduce8). Rows
 // k >= n are skipped. Returns sum_k R[k]^2 of the group in lane 0 (not EVAL).
+// J: the destination of rows k0 .. k0 + 7 of [J | -R] (row stride p.lda; global memory or the
+// elimination's shared slab), unused with EVAL.
 template <int RM, bool EVAL, bool JAC>
-__device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, int k0) {
+__device__ __forceinline__ double newton_rows8(const LuParams &p, int b, int n, int k0, float *J) {
   const int lane = threadIdx.x & 31;
   const int nb = p.nb;
   const bool vec = (nb & 1) == 0;  // even rows: 16-byte A(mu) and 8-byte J^c pairs are aligned
   const float2 *am = p.Amu + ((size_t)b * nb + k0) * nb;
   const float *jc = p.Jc + (size_t)b * p.ldj + (size_t)k0 * nb;
   const float2 *u2 = p.u2 + (size_t)b * nb;
-  float *J = EVAL ? nullptr : p.Jaug + ((size_t)b * nb + k0) * p.lda;
   const int rows = min(8, n - k0);
   float rh[8], rl[8], ch[8], cl[8];
 #pragma unroll
@@ -937,37 +938,36 @@ __global__ void __launch_bounds__(kThreads, system_blocks(FIXED)) k_newton_syste
     const int n = p.nsz ? p.nsz[b] : p.nb;
     const int k0 = 8 * g;
     if (k0 >= n) continue;
+    float *Jg = EVAL ? nullptr : p.Jaug + ((size_t)b * p.nb + k0) * p.lda;
     double r2;
     if (FIXED == 0) {
-      r2 = newton_rows8<kResZero, EVAL, true>(p, b, n, k0);
+      r2 = newton_rows8<kResZero, EVAL, true>(p, b, n, k0, Jg);
     } else if (FIXED == 1) {
-      r2 = newton_rows8<kResLow, EVAL, true>(p, b, n, k0);
+      r2 = newton_rows8<kResLow, EVAL, true>(p, b, n, k0, Jg);
     } else if (FIXED == 2) {
-      r2 = newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
+      r2 = newton_rows8<kResExact, EVAL, true>(p, b, n, k0, Jg);
     } else if (FIXED == 3) {  // chord steps; a query refreshing its Jacobian is left to FIXED 4
       if (!chord_step(p, b, qi.iters)) continue;
-      r2 = newton_rows8<kResExact, EVAL, false>(p, b, n, k0);
+      r2 = newton_rows8<kResExact, EVAL, false>(p, b, n, k0, Jg);
     } else if (FIXED == 4) {  // the queries of a chord launch that refresh their Jacobian
       if (chord_step(p, b, qi.iters)) continue;
-      r2 = newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
+      r2 = newton_rows8<kResExact, EVAL, true>(p, b, n, k0, Jg);
     } else {
       const int rm = rung_of(p.rmode, qi.iters);
-      r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL, true>(p, b, n, k0)
-           : rm == kResLow ? newton_rows8<kResLow, EVAL, true>(p, b, n, k0)
-           : (!EVAL && chord_step(p, b, qi.iters)) ? newton_rows8<kResExact, EVAL, false>(p, b, n, k0)
-                                                   : newton_rows8<kResExact, EVAL, true>(p, b, n, k0);
+      r2 = rm == kResZero  ? newton_rows8<kResZero, EVAL, true>(p, b, n, k0, Jg)
+           : rm == kResLow ? newton_rows8<kResLow, EVAL, true>(p, b, n, k0, Jg)
+           : (!EVAL && chord_step(p, b, qi.iters)) ? newton_rows8<kResExact, EVAL, false>(p, b, n, k0, Jg)
+                                                   : newton_rows8<kResExact, EVAL, true>(p, b, n, k0, Jg);
     }
     if (!EVAL && lane == 0) p.Rg[(size_t)b * G + g] = r2;
   }
 }
 
-// ||R|| of query b from its row groups' sums of squares (every lane of the calling warps, all
-// 32 present): the lanes take the groups, rounded to FP32 by integer operations, and add them
+// ||R|| from the sums of squares of a query's gn row groups (every lane of the calling warps,
+// all 32 present): the lanes take the groups, rounded to FP32 by integer operations, and add them
 // in FP32 (the stopping test needs a few digits of the norm); sums outside [2^-100, 2^100] are
 // added in FP64 instead, in group order.
-__device__ __forceinline__ double residual_norm(const LuParams &p, int b, int n) {
-  const int G = (p.nb + 7) >> 3, gn = (n + 7) >> 3;
-  const double *rg = p.Rg + (size_t)b * G;
+__device__ __forceinline__ double norm_of_groups(const double *rg, int gn) {
   float s = 0.f;
   bool wide = false;
   for (int g = threadIdx.x & 31; g < gn; g += 32) {
@@ -980,6 +980,9 @@ __device__ __forceinline__ double residual_norm(const LuParams &p, int b, int n)
   double t = 0.0;
   for (int g = 0; g < gn; ++g) t += rg[g];
   return sqrt(t);
+}
+__device__ __forceinline__ double residual_norm(const LuParams &p, int b, int n) {
+  return norm_of_groups(p.Rg + (size_t)b * ((p.nb + 7) >> 3), (n + 7) >> 3);
 }
 
 // Warp-per-query elimination of the systems k_newton_system assembled: copy the query's
@@ -2251,11 +2254,8 @@ static int elim_kind(const MixedState *M) {
 // Chord steps take the residual's convection part as an increment on the previous one
 // (RB_INCREMENT=0: the full product at every step).
 static bool incr_residual() {
-  static const int on = [] {
-    const char *e = getenv("RB_INCREMENT");
-    return (e && *e) ? atoi(e) : 1;
-  }();
-  return on != 0;
+  const char *e = getenv("RB_INCREMENT");
+  return !(e && *e && atoi(e) == 0);
 }
 
 static bool bucket_chord(const MixedState *M) {
