@@ -61,6 +61,19 @@ struct TcSmem {
   static constexpr int kBytes = kBarOff + 256 + 1024;  // barriers + alignment slack
 };
 
+// The plain epilogue stages each warp's 16 x 32 blocks of T through shared memory (rows padded
+// to 33 floats: conflict-free both ways), so that a global store writes 4 rows x 128 bytes
+// instead of 32 rows x 16 bytes; only where it fits beside the ring (not with 7 stages of 32 KB,
+// which then store from registers).
+constexpr int kEpiStageBytes = kEpiWarps * 16 * 33 * 4;
+constexpr int kMaxSmem = 232448;  // 227 KB per CTA
+template <int MODE, int BN, int STAGES, bool PAIR>
+struct TcLaunchSmem {
+  static constexpr bool kStaged =
+      MODE == kPlain && TcSmem<BN, STAGES, PAIR>::kBytes + kEpiStageBytes <= kMaxSmem;
+  static constexpr int kBytes = TcSmem<BN, STAGES, PAIR>::kBytes + (kStaged ? kEpiStageBytes : 0);
+};
+
 // Output tile t -> (first row, first column). Tiles run in groups of group_m row tiles, rows
 // fastest inside a group: the CTAs resident at one time share the operand tiles of a few row
 // and column tiles, so both operands stream from L2 when neither fits in it.
@@ -346,7 +359,38 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           if (!ok) { bad = true; break; }
           tc_fence_after();
           const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + buf * BN + half * HC;
-          if (MODE == kPlain) {
+          if (MODE == kPlain && TcLaunchSmem<MODE, BN, STAGES, PAIR>::kStaged) {
+            // columns past n_pad (a ragged last tile of a 256-column pair tile) are not stored;
+            // cend is a multiple of 32 (n_pad and n0 are multiples of 128, HC of 32)
+            const int cend = min(HC, p.n_pad - (n0 + half * HC));
+            float *stg = reinterpret_cast<float *>(smem + SM::kBarOff + 256) + (warp - 2) * (16 * 33);
+            // this warp's rows b - lane .. b - lane + 31 (within b_pad)
+            float *out = p.Jc + (size_t)(b - lane) * p.ldj + n0 + half * HC;
+#pragma unroll 1
+            for (int c = 0; c < cend; c += 32) {
+              uint32_t r[32];
+              tmem_ld_x32(taddr + c, r);
+              tmem_ld_wait();
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                if ((lane >> 4) == h) {
+                  float *sr = stg + (lane & 15) * 33;
+#pragma unroll
+                  for (int v = 0; v < 32; ++v) sr[v] = __uint_as_float(r[v]);
+                }
+                __syncwarp();
+                // lane l: row 4 i + l / 8 of the half, columns 4 (l % 8) .. + 3
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  const int rr = 4 * i + (lane >> 3), cc = 4 * (lane & 7);
+                  const float *sr = stg + rr * 33 + cc;
+                  *reinterpret_cast<float4 *>(out + (size_t)(16 * h + rr) * p.ldj + c + cc) =
+                      make_float4(sr[0], sr[1], sr[2], sr[3]);
+                }
+                __syncwarp();
+              }
+            }
+          } else if (MODE == kPlain) {
             float *out = p.Jc + (size_t)b * p.ldj + n0 + half * HC;
             // columns past n_pad (a ragged last tile of a 256-column pair tile) are not stored
             const int cend = min(HC, p.n_pad - (n0 + half * HC));
@@ -522,7 +566,7 @@ static void choose_tail_split(int mode, TcGemmParams &p, int tiles, int slots) {
 template <int MODE, int BN, int STAGES, bool PAIR>
 static cudaError_t launch_impl(const CUtensorMap &tmX, const CUtensorMap &tmW,
                                const TcGemmParams &p0, int sms, cudaStream_t st) {
-  const int smem = TcSmem<BN, STAGES, PAIR>::kBytes;
+  const int smem = TcLaunchSmem<MODE, BN, STAGES, PAIR>::kBytes;
   auto kern = k_tc_gemm<MODE, BN, STAGES, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
