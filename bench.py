@@ -405,6 +405,7 @@ def measure(args, wl, batch, steps, warmup, rank, world, local, dev, recon, cpu_
             step(stream)
     torch.cuda.synchronize()
     kprof = ctx.rb_profile_read()
+    issued = ctx.rb_profile_issued()
     ctx.rb_profile(False)
     t_dev = sum(step_ms) / 1e3
     if world > 1:
@@ -442,7 +443,7 @@ def measure(args, wl, batch, steps, warmup, rank, world, local, dev, recon, cpu_
 
     # roofline of the dominant kernel, measured live with events on the launching stream
     chord = chord_queries(prec, wl, q, ctx.rb_tuning())
-    roof, roofs, kernels = kernel_rooflines(prec, wl, q, info, kprof, steps, chord)
+    roof, roofs, kernels = kernel_rooflines(prec, wl, q, info, kprof, steps, chord, issued)
 
     line = {
         "metric": "reduced Newton solves/s", "value": value, "unit": "solves/s",
@@ -504,31 +505,22 @@ def measure(args, wl, batch, steps, warmup, rank, world, local, dev, recon, cpu_
 FP64_PEAK_TFLOPS = 1.196  # FP64 FMA throughput measured on GB300 (152 SMs at 2070 MHz)
 # FP32 FMA peak from the unit counts and the clock: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-DIGITS = int(os.environ.get("RB_DIGITS", "5"))  # digit slices of the sliced convection product
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the kernels as they
 # stand, from ncu captures of this bench command on the n = 50 sweep (4096 queries) and on the
 # n = 300 dense regime; a kernel changed since its capture has no entry.
 NCU_TRAFFIC = {
-    # per-launch averages over the launches the bench times (one-pass launch list; the sliced
-    # residual GEMM from its --set full capture, the launch list mixing in the pressure launches)
+    # DRAM read + write bytes per launch of each timed kernel kind, averaged as the bench counts
+    # its launches (the residual GEMM: full product and increment; the assembly: rungs 0-3 with
+    # the gated refresh launch; the elimination: three factorisations and a chord solve), from
+    # one ncu capture of the same bench command. Workloads without a capture of the current
+    # kernels report null.
     "sweep_n50": {
-        "k_tc_gemm<sliced>": 29.10e6,
-        "k_tc_gemm<plain>": 11.48e6,
+        "k_tc_gemm<sliced>": 16.14e6,
+        "k_tc_gemm<plain>": 7.46e6,
+        "k_tc_gemm<sliced,pressure>": 20.73e6,
         "k_newton_system": 113.9e6,
-        "k_lu_mixed": 42.57e6,
-    },
-    # one-pass captures of the full-size workloads
-    "dense_n300": {
-        "k_tc_gemm<sliced>": 1534.5e9,
-        "k_tc_gemm<plain>": 84.73e9,
-        "k_newton_system": 19.77e9,
-        "k_lu_mixed": 21.28e9,
-    },
-    "uneven_n120": {
-        "k_tc_gemm<sliced>": 179.2e6,
-        "k_tc_gemm<plain>": 56.45e6,
-        "k_newton_system": 133.7e6,
-        "k_lu_mixed": 49.63e6,
+        "k_lu_mixed": 42.54e6,
+        "k_prep": 21.20e6,
     },
 }
 
@@ -540,13 +532,7 @@ def chord_queries(prec, wl, q, tuning):
     return np.full(len(q.n), on, bool)
 
 
-def incremental_residual(prec):
-    """Whether the mixed path's chord steps take the residual as an increment (RB_INCREMENT)."""
-    return prec != 0 and os.environ.get("RB_CHORD", "") != "0" and \
-        os.environ.get("RB_INCREMENT", "") != "0"
-
-
-def kernel_rooflines(prec, wl, q, info, kprof, steps, chord):
+def kernel_rooflines(prec, wl, q, info, kprof, steps, chord, issued=None):
     """Roofline of every timed kernel kind, and of the one with the largest device time.
 
     `achieved` counts the method's ALGORITHMIC work only (the multiply-adds of the contraction
@@ -565,9 +551,11 @@ def kernel_rooflines(prec, wl, q, info, kprof, steps, chord):
         right-hand side, 8 n^2 + 4 n (HBM);
       per-query preparation: 8 n^2 bytes of A(mu) written, once per query (HBM).
     The tensor kernels ISSUE more products than that: the Jacobian GEMM 3 split-BF16 products
-    (hi hi, hi lo, lo hi) and the sliced GEMMs P = S (S + 1) / 2 digit-pair products for an
-    FP64-accurate result; `issued_tflops` / `issued_frac` report that rate (how busy the tensor
-    pipe is), separately from `frac`."""
+    (hi hi, hi lo, lo hi) and the sliced GEMMs up to P = S (S + 1) / 2 digit-pair products for an
+    FP64-accurate result (fewer for the chord steps' increments), over padded tiles;
+    `issued_tflops` / `issued_frac` report that rate (how busy the tensor pipe is), separately
+    from `frac`, from the FLOPs of the MMAs the kernels executed, counted on the device
+    (`issued`: kernel -> FLOPs over the profiled steps)."""
     peaks, kind = measured_peaks()
     n = q.n.astype(np.float64)
     it = info["iters"].astype(np.float64)
@@ -578,23 +566,22 @@ def kernel_rooflines(prec, wl, q, info, kprof, steps, chord):
     tot_ms = sum(v[0] for v in kprof.values()) or 1.0
     kernels = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps,
                    "share": v[0] / tot_ms} for k, v in kprof.items() if v[1]}
-    p0 = DIGITS * (DIGITS + 1) // 2
     bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     hbm = peaks.get("hbm_gbs")
     bf16_src = f"bf16 sustained, {kind} (MEASURED_PEAKS.json)"
     hbm_src = f"HBM copy, {kind} (MEASURED_PEAKS.json)"
-    work = {  # kernel -> (bound, algorithmic units per step, issued / algorithmic, peak, unit, src)
+    work = {  # kernel -> (bound, algorithmic units per step, tensor kernel, peak, unit, src)
         "k_newton_fp64": ("alu", float(np.sum(it * (2 * (2 * wl.q_c * n ** 3 + wl.q_a * n ** 2)
                                                      + 2 * n ** 3 / 3 + 2 * n ** 2))), None,
                           FP64_PEAK_TFLOPS, "TFLOP/s",
                           "FP64 FMA throughput of a probe kernel of this project on GB300 (152 SMs, "
                           "2070 MHz); not a MEASURED_PEAKS.json figure"),
-        "k_tc_gemm<plain>": ("tensor", float(np.sum(jac * 2.0 * wl.q_c * n ** 3)), 3.0,
+        "k_tc_gemm<plain>": ("tensor", float(np.sum(jac * 2.0 * wl.q_c * n ** 3)), True,
                              bf16, "TFLOP/s", bf16_src),
-        "k_tc_gemm<sliced>": ("tensor", float(np.sum(res * 2.0 * wl.q_c * n ** 3)), float(p0),
+        "k_tc_gemm<sliced>": ("tensor", float(np.sum(res * 2.0 * wl.q_c * n ** 3)), True,
                               bf16, "TFLOP/s", bf16_src),
         "k_tc_gemm<sliced,pressure>": ("tensor", float(np.sum(2.0 * (wl.m or 0) * wl.q_c * n ** 2)),
-                                       float(p0), bf16, "TFLOP/s", bf16_src),
+                                       True, bf16, "TFLOP/s", bf16_src),
         "k_lu_mixed": ("alu", float(np.sum(full * (2 * n ** 3 / 3 + 2 * n ** 2) + chs * 2 * n ** 2)),
                        None, FP32_PEAK_TFLOPS, "TFLOP/s",
                        "FP32 FMA peak from unit counts and clock (152 x 128 x 2 x 2.07 GHz)"),
@@ -607,20 +594,20 @@ def kernel_rooflines(prec, wl, q, info, kprof, steps, chord):
     for k, (ms, launches) in kprof.items():
         if not launches or k not in work:
             continue
-        bound, units, issued, peak, unit, src = work[k]
+        bound, units, tensor, peak, unit, src = work[k]
         scale = 1e12 if unit == "TFLOP/s" else 1e9
         ach = steps * units / (ms * 1e-3) / scale
         traffic = NCU_TRAFFIC.get(wl.name, {}).get(k)
         rl[k] = {"bound": bound, "kernel": k, "achieved": ach, "peak": peak, "unit": unit,
                  "frac": ach / peak, "traffic": traffic, "peak_source": src,
                  "work": "algorithmic", "launches": launches}
-        if issued:
-            # the chord steps' residual (an increment on the previous one) issues fewer digit
-            # pairs than a full product; the figures below count full products: upper bounds
-            bound_only = k == "k_tc_gemm<sliced>" and incremental_residual(prec)
-            rl[k]["issued_tflops" + ("_max" if bound_only else "")] = ach * issued
-            rl[k]["issued_frac" + ("_max" if bound_only else "")] = ach * issued / peak
-            rl[k]["issued_per_algorithmic" + ("_max" if bound_only else "")] = issued
+        flops = (issued or {}).get(k, 0.0)
+        if tensor and flops > 0:
+            # the MMAs the launches executed (digit or split products, padding tiles), counted
+            # on the device over the same profiled steps
+            rl[k]["issued_tflops"] = flops / (ms * 1e-3) / 1e12
+            rl[k]["issued_frac"] = rl[k]["issued_tflops"] / peak
+            rl[k]["issued_per_algorithmic"] = flops / (steps * units) if units else None
     dom = max(kprof, key=lambda k: kprof[k][0])
     return rl.get(dom), rl, kernels
 

@@ -356,6 +356,12 @@ enum {
 };
 int rb_profile(rb_ctx *ctx, int enable);
 int rb_profile_read(rb_ctx *ctx, int kernel, double *total_ms, long long *launches);
+/* Tensor-core work issued while profiling was enabled by the kernels of one kind
+ * (RB_K_GEMM_JAC, RB_K_GEMM_RES, RB_K_GEMM_PRES): the multiply-add FLOPs (2 M N K) of every
+ * tcgen05.mma the launches executed, padding tiles and every digit or split product included,
+ * counted on the device. This is the work the tensor pipe did, as against the method's own
+ * contraction count; 0 for the other kinds. Synchronises the device. *flops: host pointer. */
+int rb_profile_issued(rb_ctx *ctx, int kernel, double *flops);
 
 /* ---- autotuner (no counterpart in the paper) -----------------------------------------------
  * With cfg.autotune, the first mixed-precision solve of each size bucket and batch-size class

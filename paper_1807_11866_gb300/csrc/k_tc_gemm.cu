@@ -312,6 +312,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           }
         }
       }
+      // the tensor work this CTA (pair) issued: 2 kBMT BN kBK FLOPs per K step
+      if (p.issued && step) atomicAdd(p.issued, (unsigned long long)step * (2ull * kBMT * BN * kBK));
       // all issued MMAs complete before TMEM is released (pair: in both CTAs)
       if (PAIR) mma_commit_pair(mdone);
       else mma_commit(mdone);

@@ -67,6 +67,8 @@ struct ProfMark {
 int prof_begin(rb_ctx *ctx, int kind, cudaStream_t st);  // returns a mark index or -1
 void prof_end(rb_ctx *ctx, int mark, cudaStream_t st);
 void prof_collect(rb_ctx *ctx);  // waits for recorded marks and accumulates them
+// the device counter of the tensor FLOPs issued by kernels of `kind`, or null when not profiling
+unsigned long long *prof_issued(rb_ctx *ctx, int kind);
 
 }  // namespace rb
 
@@ -93,5 +95,6 @@ struct rb_ctx {
   std::vector<cudaEvent_t> event_pool;
   double prof_ms[RB_K_COUNT] = {};
   long long prof_n[RB_K_COUNT] = {};
+  unsigned long long *d_issued = nullptr;  // [RB_K_COUNT] tensor FLOPs issued (device counters)
   rb::ServeState *serve = nullptr;
 };

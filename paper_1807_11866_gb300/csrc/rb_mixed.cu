@@ -2207,6 +2207,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
     // first stage waits for 16 bytes that never come, so the bounded wait gives up
     const char *td = getenv("RB_TEST_WAIT_DEFICIT");
     g.tx_extra = (td && atoi(td) == 1 && !use_pairs_plain(M)) ? 16u : 0u;
+    g.issued = prof_issued(ctx, RB_K_GEMM_JAC);
     mk = prof_begin(ctx, RB_K_GEMM_JAC, st);
     e = launch_tc_gemm(kPlain, M->tmXj, M->tmWj, g, ctx->sms, st, M->tune.st_plain, use_pairs_plain(M));
     prof_end(ctx, mk, st);
@@ -2231,6 +2232,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[1] = M->WR.wexp[1];
   g.out = M->Rc;
   if (incr && !jac) g.lmax = M->root->dev_words + 6;
+  g.issued = prof_issued(ctx, RB_K_GEMM_RES);
   mk = prof_begin(ctx, RB_K_GEMM_RES, st);
   e = launch_sliced(M, M->WR, g, ctx->sms, st, M->tune.st_sliced, sliced_variant(M));
   prof_end(ctx, mk, st);
@@ -2415,6 +2417,7 @@ static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   g.wexp[0] = M->WP.wexp[0];
   g.wexp[1] = M->WP.wexp[1];
   g.out = M->Rp;
+  g.issued = prof_issued(ctx, RB_K_GEMM_PRES);
   int mk = prof_begin(ctx, RB_K_GEMM_PRES, st);
   cudaError_t e = launch_sliced(M, M->WP, g, ctx->sms, st, M->tune.st_sliced, sliced_variant(M));
   prof_end(ctx, mk, st);

@@ -40,6 +40,7 @@ struct TcGemmParams {
   unsigned tx_extra;     // single-CTA variants, tests of the bounded waits only: bytes the first
                          // stage of CTA 0 expects beyond what its copies bring (0 normally), so
                          // that its consumer's wait runs out and raises the error word
+  unsigned long long *issued;  // if set (profiling): += the FLOPs (2 M N K) of the MMAs issued
 };
 
 cudaError_t launch_tc_gemm(int mode, const CUtensorMap &tmX, const CUtensorMap &tmW,

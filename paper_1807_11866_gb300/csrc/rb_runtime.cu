@@ -126,6 +126,10 @@ int prof_begin(rb_ctx *ctx, int kind, cudaStream_t st) {
   return (int)ctx->marks.size() - 1;
 }
 
+unsigned long long *prof_issued(rb_ctx *ctx, int kind) {
+  return ctx->prof && ctx->d_issued ? ctx->d_issued + kind : nullptr;
+}
+
 void prof_end(rb_ctx *ctx, int mark, cudaStream_t st) {
   if (mark < 0 || mark >= (int)ctx->marks.size()) return;
   cudaEventRecord(ctx->marks[mark].b, st);
@@ -524,7 +528,30 @@ int rb_profile(rb_ctx *ctx, int enable) {
     ctx->prof_ms[k] = 0.0;
     ctx->prof_n[k] = 0;
   }
+  if (enable && !ctx->d_issued) {
+    void *p = nullptr;
+    const int rc = ctx_alloc(ctx, &p, 8 * RB_K_COUNT, "profile counters");
+    if (rc != RB_OK) return rc;
+    ctx->d_issued = (unsigned long long *)p;
+  }
+  if (ctx->d_issued) {
+    const cudaError_t e = cudaMemset(ctx->d_issued, 0, 8 * RB_K_COUNT);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "profile counters");
+  }
   ctx->prof = enable != 0;
+  return RB_OK;
+}
+
+int rb_profile_issued(rb_ctx *ctx, int kernel, double *flops) {
+  if (!ctx || !flops) return RB_ERR_ARG;
+  if (kernel < 0 || kernel >= RB_K_COUNT) return set_error(ctx, RB_ERR_ARG, "kernel id %d", kernel);
+  cudaSetDevice(ctx->device);
+  unsigned long long v = 0;
+  if (ctx->d_issued) {
+    const cudaError_t e = cudaMemcpy(&v, ctx->d_issued + kernel, 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "profile counters");
+  }
+  *flops = (double)v;
   return RB_OK;
 }
 

@@ -27,7 +27,7 @@ RB_STATIC_N_MAX, RB_STATIC_SCRATCH_BYTES = 512, 16 << 20
 EXPORTS = ["rb_config_default", "rb_create", "rb_destroy", "rb_last_error", "rb_load_operators",
            "rb_solve", "rb_solve_theta", "rb_solve_device", "rb_solve_device_sized",
            "rb_solve_device_status", "rb_eval", "rb_gepp_solve",
-           "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_serve_start", "rb_serve_stop",
+           "rb_gepp_solve_static", "rb_profile", "rb_profile_read", "rb_profile_issued", "rb_serve_start", "rb_serve_stop",
            "rb_serve_submit", "rb_serve_poll", "rb_serve_stats", "rb_serve_slots", "rb_tuning",
            "rb_load_pressure_modes", "rb_reconstruct_pressure", "rb_reconstruct_pressure_device",
            "rb_save_operators", "rb_load_operator_file", "rb_offline_pod", "rb_offline_project",
@@ -120,6 +120,7 @@ def library():
         L.rb_gepp_solve_static.argtypes = [I, I, P, P, P, P, P]
         L.rb_profile.argtypes = [P, I]
         L.rb_profile_read.argtypes = [P, I, P, P]
+        L.rb_profile_issued.argtypes = [P, I, P]
         L.rb_serve_start.argtypes = [P]
         L.rb_serve_stop.argtypes = [P, I]
         L.rb_serve_submit.argtypes = [P, P, I, ctypes.POINTER(ctypes.c_uint64)]
@@ -468,6 +469,15 @@ class Context:
             self._check(library().rb_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)),
                         "rb_profile_read")
             out[name] = (ms.value, n.value)
+        return out
+
+    def rb_profile_issued(self):
+        """{kernel name: tensor FLOPs issued} of the GEMM kinds since rb_profile(1)."""
+        out = {}
+        for k in (3, 4, 7):  # RB_K_GEMM_JAC, RB_K_GEMM_RES, RB_K_GEMM_PRES
+            f = ctypes.c_double()
+            self._check(library().rb_profile_issued(self.h, k, ctypes.byref(f)), "rb_profile_issued")
+            out[RB_K_NAMES[k]] = f.value
         return out
 
     # --- autotuner ----------------------------------------------------------------------

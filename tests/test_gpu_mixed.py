@@ -171,6 +171,40 @@ def test_chord_steps(rb, n, elim, monkeypatch):
     assert rel(res["11"][0], u_ref).max() <= 10 * max(rel(res["10"][0], u_ref).max(), 1e-13)
 
 
+def test_issued_tensor_work_is_counted(rb, monkeypatch):
+    """rb_profile_issued counts the MMAs the GEMM launches executed. With single-CTA tiles
+    (128 x 128, K blocks of 64) and without chord steps every Jacobian launch issues the 3 split
+    products and every residual launch the 15 digit pairs of S = 5 slices, over every K block
+    of every output tile (padding included): exactly launches x tiles x products x K blocks x
+    2 x 128 x 128 x 64 FLOPs."""
+    for k, v in (("RB_SMALL", "0"), ("RB_AUTOTUNE", "0"), ("RB_GEMM_PAIRS", "0"), ("RB_CHORD", "0")):
+        monkeypatch.setenv(k, v)
+    wl = synth.WORKLOADS["sweep_n50"]
+    n, nq = 40, 300
+    ops = synth.make_operators(wl, n_max=n)
+    mu = synth.make_queries(wl, batch=nq, n_max=n).mu
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        ctx.rb_solve(mu)
+        ctx.rb_profile(True)
+        _, _, info = ctx.rb_solve(mu)
+        prof = ctx.rb_profile_read()
+        issued = ctx.rb_profile_issued()
+        ctx.rb_profile(False)
+    assert np.all(info["status"] == 0)
+
+    def up(a, b):
+        return (a + b - 1) // b * b
+
+    tiles = (up(nq, 128) // 128) * (up(n * n, 128) // 128)
+    kb0 = up(wl.q_c * n, 64) // 64
+    per_step = 2 * 128 * 128 * 64
+    assert prof["k_tc_gemm<plain>"][1] > 0 and prof["k_tc_gemm<sliced>"][1] > 0
+    assert issued["k_tc_gemm<plain>"] == prof["k_tc_gemm<plain>"][1] * tiles * 3 * kb0 * per_step
+    assert issued["k_tc_gemm<sliced>"] == prof["k_tc_gemm<sliced>"][1] * tiles * 15 * kb0 * per_step
+    assert issued["k_tc_gemm<sliced,pressure>"] > 0
+
+
 def test_manufactured_mixed(rb):
     ops = synth.make_operators(synth.WORKLOADS["single_n20"])
     oracle.manufacture(ops, (10.0, 200.0))
