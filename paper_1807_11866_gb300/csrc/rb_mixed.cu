@@ -1235,13 +1235,15 @@ __global__ void __launch_bounds__(kCtaLuMaxN) k_lu_cta(LuParams p) {
 template <int PB>
 struct BlkLuSmem {
   static constexpr int kPLd = PB + 1;
-  int P, U, perm, red, x, dred, total;  // byte offsets
+  int P, U, perm, rmap, tl, red, x, dred, total;  // byte offsets
   __host__ __device__ BlkLuSmem(int nb, int lda) {
     int p = 0;
     P = p; p += 4 * nb * kPLd;
     p = (p + 15) & ~15;
     U = p; p += 4 * PB * lda;
     perm = p; p += 4 * PB;
+    rmap = p; p += 4 * nb;     // a panel's row interchanges as one permutation
+    tl = p; p += 4 * (PB + 1); // rows at or past the panel's height that it moves, and their count
     red = p; p += 4 * kWarps;
     x = p; p += 4 * ((nb + 3) & ~3);
     p = (p + 7) & ~7;
@@ -1264,6 +1266,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
   float *P = reinterpret_cast<float *>(smb + L.P);
   float *U = reinterpret_cast<float *>(smb + L.U);
   int *perm = reinterpret_cast<int *>(smb + L.perm);
+  int *rmap = reinterpret_cast<int *>(smb + L.rmap);
+  int *tl = reinterpret_cast<int *>(smb + L.tl);
   unsigned *red = reinterpret_cast<unsigned *>(smb + L.red);
   float *xs = reinterpret_cast<float *>(smb + L.x);
   double *dred = reinterpret_cast<double *>(smb + L.dred);
@@ -1373,27 +1377,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
         M[(size_t)(k0 + r) * lda + k0 + c] = P[r * kPLd + c];
       }
       if (keep && tid < kb) p.Piv[(size_t)b * nb + k0 + tid] = k0 + perm[tid];
-      // (b) row interchanges on the columns right of the panel, then (c) U12 = L11^-1 A12;
-      // one thread per column
-      const int c_lo = k0 + kb;
-      for (int c = c_lo + tid; c <= n; c += blockDim.x) {
+      // (b) the panel's row interchanges on the columns right of it, as one permutation: row r
+      // of the panel's rows takes the old row rmap[r]; tl lists the rows r >= kb it changes
+      for (int r = tid; r < rows; r += blockDim.x) rmap[r] = r;
+      __syncthreads();
+      if (tid == 0) {
+        for (int j = 0; j < kb; ++j) {
+          const int pr = perm[j], t = rmap[j];
+          rmap[j] = rmap[pr];
+          rmap[pr] = t;
+        }
+        int cnt = 0;
         for (int j = 0; j < kb; ++j) {
           const int pr = perm[j];
-          if (pr != j) {
-            float *a = M + (size_t)(k0 + j) * lda + c, *q = M + (size_t)(k0 + pr) * lda + c;
-            const float t = *a;
-            *a = *q;
-            *q = t;
+          if (pr < kb || rmap[pr] == pr) continue;
+          bool dup = false;
+          for (int t = 0; t < cnt; ++t) dup = dup || tl[t] == pr;
+          if (!dup) tl[cnt++] = pr;
+        }
+        tl[kPB] = cnt;
+      }
+      __syncthreads();
+      // (c) U12 = L11^-1 A12, one thread per column, the column's kb entries in registers: all
+      // its loads issued at once, the solve a chain of FMAs on registers. A row at or past kb that
+      // the interchanges move receives a row above kb (each swap hands the pivot position's
+      // current row, by induction one of the rows above kb, to the pivot row's place), so those
+      // rows are copied before the rows above kb are overwritten, and after every pivot row has
+      // been read into v.
+      const int c_lo = k0 + kb, nt = tl[kPB];
+      for (int c = c_lo + tid; c <= n; c += blockDim.x) {
+        float v[kPB];
+#pragma unroll
+        for (int j = 0; j < kPB; ++j) v[j] = j < kb ? M[(size_t)(k0 + rmap[j]) * lda + c] : 0.f;
+        for (int t = 0; t < nt; ++t)
+          M[(size_t)(k0 + tl[t]) * lda + c] = M[(size_t)(k0 + rmap[tl[t]]) * lda + c];
+#pragma unroll
+        for (int j = 1; j < kPB; ++j) {
+          if (j < kb) {  // P holds the panel's rows only (kb <= rows <= nb)
+            float s = v[j];
+#pragma unroll
+            for (int i = 0; i < j; ++i) s = fmaf(-P[j * kPLd + i], v[i], s);
+            v[j] = s;
           }
         }
-        // the column's kb entries in this thread's column of U (shared), solved in place
-        for (int j = 0; j < kb; ++j) U[j * lda + c] = M[(size_t)(k0 + j) * lda + c];
-        for (int j = 1; j < kb; ++j) {
-          float v = U[j * lda + c];
-          for (int i = 0; i < j; ++i) v = fmaf(-P[j * kPLd + i], U[i * lda + c], v);
-          U[j * lda + c] = v;
-        }
-        for (int j = 0; j < kb; ++j) M[(size_t)(k0 + j) * lda + c] = U[j * lda + c];
+#pragma unroll
+        for (int j = 0; j < kPB; ++j)
+          if (j < kb) {
+            U[j * lda + c] = v[j];
+            M[(size_t)(k0 + j) * lda + c] = v[j];
+          }
       }
       __syncthreads();
       // (d) trailing update of rows k0+kb .. n-1, columns c_lo .. n, in tiles of 4 rows x 4 columns
