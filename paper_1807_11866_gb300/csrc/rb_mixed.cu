@@ -1334,21 +1334,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
         P[r * kPLd + c] = c < kb ? M[(size_t)(k0 + r) * lda + k0 + c] : 0.f;
       }
       __syncthreads();
-      for (int j = 0; j < kb; ++j) {
+      // pivot keys of column 0, per warp into red; each step below then needs two barriers:
+      // after the interchange, and after the update, which also finds the next column's keys
+      // (the threads update the same rows j + 1 + tid, ... that the next search covers)
+      {
         unsigned key = 0;
-        for (int r = j + tid; r < rows; r += blockDim.x) {
-          const unsigned k = pivot_key9(P[r * kPLd + j], r);
+        for (int r = tid; r < rows; r += blockDim.x) {
+          const unsigned k = pivot_key9(P[r * kPLd], r);
           key = k > key ? k : key;
         }
         key = __reduce_max_sync(0xffffffffu, key);
         if (lane == 0) red[w] = key;
         __syncthreads();
-        key = red[0];
+      }
+      for (int j = 0; j < kb; ++j) {
+        unsigned key = red[0];
 #pragma unroll
         for (int i = 1; i < kWarps; ++i) key = red[i] > key ? red[i] : key;
         const int pr = 511 - (int)(key & 511u);
         const float pv = P[pr * kPLd + j];
-        if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+        if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {  // the same in every thread
           sing = true;
           break;
         }
@@ -1358,13 +1363,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_blocked(LuParams p) {
           P[pr * kPLd + tid] = t;
         }
         if (tid == 0) perm[j] = pr;
-        __syncthreads();
+        __syncthreads();  // the interchange done and red read by every thread
         const float rinv = __frcp_rn(pv);
+        unsigned nkey = 0;
         for (int r = j + 1 + tid; r < rows; r += blockDim.x) {
           float *Pr = P + r * kPLd;
           const float l = Pr[j] * rinv;
           Pr[j] = l;
           for (int c = j + 1; c < kb; ++c) Pr[c] = fmaf(-l, P[j * kPLd + c], Pr[c]);
+          if (j + 1 < kb) {
+            const unsigned k = pivot_key9(Pr[j + 1], r);
+            nkey = k > nkey ? k : nkey;
+          }
+        }
+        if (j + 1 < kb) {
+          nkey = __reduce_max_sync(0xffffffffu, nkey);
+          if (lane == 0) red[w] = nkey;
         }
         __syncthreads();
       }
