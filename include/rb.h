@@ -269,8 +269,9 @@ int rb_gepp_solve(rb_ctx *ctx, int n, int batch, const double *M, const double *
 
 /* ---- batched solve without allocation -----------------------------------------------------
  * No counterpart in the paper: this entry point serves callers that cannot allocate device
- * memory when they solve -- work recorded into a CUDA graph capture, processes held to a fixed
- * memory budget, or hosts that only lend the library pre-allocated buffers. It solves
+ * memory when they solve -- processes held to a fixed memory budget, hosts that only lend the
+ * library pre-allocated buffers, or runtimes that must not take the allocator's locks on their
+ * hot path. It solves
  * M_s x_s = rhs_s for s < batch with the same partial pivoting as rb_gepp_solve, from DEVICE
  * buffers: d_M [batch][n][n] row-major (not modified), d_rhs [batch][n], d_x [batch][n],
  * d_status [batch] (0 or RB_Q_SINGULAR), asynchronously on cuda_stream (NULL: legacy stream).

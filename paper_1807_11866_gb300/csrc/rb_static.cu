@@ -1,9 +1,8 @@
 // rb_static.cu -- rb_gepp_solve_static: the batched partial-pivot solve with no allocation.
 //
-// Some callers cannot allocate device memory at the time they solve: code running inside a
-// CUDA-graph capture or a memory pool budget that forbids cudaMalloc, hosts that hand the library
-// pre-allocated buffers only, or runtimes that must not take the allocator's locks on their hot
-// path. For them this entry point takes device pointers to its inputs and outputs and uses, as
+// Some callers cannot allocate device memory at the time they solve: code held to a memory
+// budget that forbids cudaMalloc, hosts that hand the library pre-allocated buffers only, or
+// runtimes that must not take the allocator's locks on their hot path. For them this entry point takes device pointers to its inputs and outputs and uses, as
 // the working copy of each matrix, a file-scope device array that exists for as long as the
 // library is loaded. It calls no allocating CUDA or library routine.
 #include <cuda.h>

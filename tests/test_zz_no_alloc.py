@@ -1,7 +1,8 @@
 """rb_gepp_solve_static: the batched partial-pivot solve that allocates nothing.
 
-Callers that cannot allocate device memory while they solve (inside a graph capture, under a
-fixed memory budget, or with only lent buffers) use this entry point; its working matrices live
+Callers that cannot allocate device memory while they solve (under a fixed memory budget, with
+only lent buffers, or on a hot path that must not take the allocator's locks) use this entry
+point; its working matrices live
 in a file-scope device array that every call shares. The test calls it through the C ABI on
 caller-owned device buffers, several times in a row with different sizes (the shared array
 keeps the previous call's contents), and compares each result with the allocating entry point
