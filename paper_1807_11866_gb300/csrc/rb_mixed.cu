@@ -1671,8 +1671,8 @@ struct PresSolveParams {
   const double *theta;  // [nq][n_theta]
   int nq;
   const float2 *Bmu;    // [nq][m][m] B(mu) double-float (k_affine_sum)
-  const double *Rp;     // [b_pad][m]: Cs_mu(u, u) (sliced GEMM)
-  const double *Asu;    // [b_pad][m]: As(mu) u (k_as_u)
+  const double *Rp;     // [b_pad][m]: Cs_mu(u, u), + As(mu) u when Asu is null (sliced GEMM)
+  const double *Asu;    // [b_pad][m]: As(mu) u (k_as_u), or null when Rp includes it
   double *p_out;        // [nq][m]
   rb_query_info *info;
 };
@@ -1731,7 +1731,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve_warp(PresSolveParam
     for (int k = lane; k < m; k += 32) {
       double sf = 0.0;
       for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
-      r[k] = sf - p.Rp[(size_t)b * m + k] - p.Asu[(size_t)b * m + k];
+      r[k] = sf - p.Rp[(size_t)b * m + k] - (p.Asu ? p.Asu[(size_t)b * m + k] : 0.0);
       float *row = Ba + k * lda;
       row[m] = (float)r[k];
       for (int c = m + 1; c < c_pad; ++c) row[c] = 0.f;
@@ -1823,7 +1823,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_solve(PresSolveParams p) 
     for (int k = tid; k < m; k += blockDim.x) {
       double sf = 0.0;
       for (int q = 0; q < o.q_f; ++q) sf = fma(tf[q], o.fs[(size_t)q * m + k], sf);
-      r[k] = sf - p.Rp[(size_t)b * m + k] - p.Asu[(size_t)b * m + k];
+      r[k] = sf - p.Rp[(size_t)b * m + k] - (p.Asu ? p.Asu[(size_t)b * m + k] : 0.0);
     }
     __syncthreads();
     const bool sing = gepp_solve_block<double>(Bm, m, m, r, red);
@@ -1992,13 +1992,19 @@ static int mixed_layouts(rb_ctx *ctx, MixedState *M, cudaStream_t st) {
   const DevOps &o = ctx->ops;
   M->Kpad0 = round_up(o.q_c * M->nb, 64);
   M->kb0 = M->Kpad0 / 64;
-  // the linear affine term A(mu) u is evaluated in double-float on the CUDA cores, so the
-  // sliced GEMM carries the convection segment only (the kernel also supports a second one)
-  M->kb1 = 0;
-  M->Kpad = M->Kpad0 + 64 * M->kb1;
-  M->Npad = round_up(M->nb * M->nb, kTcBN);
   M->S0 = sliced_digits("RB_DIGITS", 5);
   M->S1 = sliced_digits("RB_DIGITS_LINEAR", 7);
+  // K segment 1 (theta^a (x) the linear operator, one block of 64: Q_a <= RB_Q_MAX) serves the
+  // pressure right-hand side only: there the sliced GEMM gives Cs_mu(u, u) + As(mu) u in one
+  // launch, where the CUDA cores would take Q_a m n double-float multiply-adds per query
+  // (about 6 us per unit of Q_a at n = 50, m = 30, 4096 queries) and the GEMM pays one tile
+  // contraction per digit level of the segment (about 12 us each): taken when Q_a > 2 S1. The
+  // residual's linear term A(mu) u stays in double-float on the CUDA cores (its launches use
+  // segment 0 only): a chord step's increment would need that segment contracted with d and all
+  // of its digit pairs at every step.
+  M->kb1 = (o.m > 0 && o.B && o.As && o.q_a > 2 * M->S1) ? 1 : 0;
+  M->Kpad = M->Kpad0 + 64 * M->kb1;
+  M->Npad = round_up(M->nb * M->nb, kTcBN);
   M->Smax = M->kb1 ? std::max(M->S0, M->S1) : M->S0;
   int rc;
   void *p;
@@ -2271,7 +2277,7 @@ static int mixed_contract(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   }
   g.tx_extra = 0;
   g.run_if = nullptr;
-  g.kb[1] = M->kb1;
+  g.kb[1] = 0;  // convection only: A(mu) u is added in the assembly
   g.n_tiles = M->WR.Npad / kTcBN;
   g.n_pad = M->WR.Npad;
   g.wexp[0] = M->WR.wexp[0];
@@ -2469,13 +2475,15 @@ static int mixed_pressure(rb_ctx *ctx, MixedState *M, int nq, const int *d_n, co
   prof_end(ctx, mk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_tc_gemm (pressure)");
   mk = prof_begin(ctx, RB_K_PRESSURE, st);
-  AsuParams ap{o, M->Th, d_n, nq, M->nb, d_u, info, M->As2, M->Asu};
-  const size_t asmem = sizeof(float2) * (size_t)(kAsQ + kAsR) * odd_ld(M->nb);
-  e = cudaFuncSetAttribute(k_as_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_as_u attr");
-  dim3 agrid((unsigned)((o.m + kAsR - 1) / kAsR), (unsigned)std::max(1, std::min((nq + kAsQ - 1) / kAsQ, 65535)));
-  k_as_u<<<agrid, 256, asmem, st>>>(ap);
-  PresSolveParams pp{o, M->Th, nq, M->Bmu, M->Rp, M->Asu, d_p, info};
+  if (!M->kb1) {  // As(mu) u not in the GEMM's output: in double-float on the CUDA cores
+    AsuParams ap{o, M->Th, d_n, nq, M->nb, d_u, info, M->As2, M->Asu};
+    const size_t asmem = sizeof(float2) * (size_t)(kAsQ + kAsR) * odd_ld(M->nb);
+    e = cudaFuncSetAttribute(k_as_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "k_as_u attr");
+    dim3 agrid((unsigned)((o.m + kAsR - 1) / kAsR), (unsigned)std::max(1, std::min((nq + kAsQ - 1) / kAsQ, 65535)));
+    k_as_u<<<agrid, 256, asmem, st>>>(ap);
+  }
+  PresSolveParams pp{o, M->Th, nq, M->Bmu, M->Rp, M->kb1 ? nullptr : M->Asu, d_p, info};
   const size_t per_warp = PresSmem(o).total;
   if (o.m <= 32 * kWarpRows && per_warp <= 24 * 1024) {
     const int wpc = std::max(1, std::min(8, (int)((192 * 1024) / per_warp)));
