@@ -497,8 +497,10 @@ __global__ void __launch_bounds__(kThreads) k_build_x(BuildXParams p) {
     // Kpad0 and Kpad are multiples of 64: a pair never straddles the segment boundary. The
     // lane's (q, l) of kap = 2 lane + 64 i advance without a division per step.
     int q = (2 * lane) / p.nb, l = 2 * lane - q * p.nb;
+    // the linear segment (theta^a digits) serves the pressure GEMM only (mode 1)
+    const int kend = p.mode == 0 ? p.Kpad0 : p.Kpad;
 #pragma unroll 2
-    for (int kap = 2 * lane; kap < p.Kpad; kap += 64) {
+    for (int kap = 2 * lane; kap < kend; kap += 64) {
       const size_t off = (size_t)b * p.Kpad + kap;
       if (kap < p.Kpad0) {
         const int q1 = l + 1 < p.nb ? q : q + 1, l1 = l + 1 < p.nb ? l + 1 : 0;
