@@ -205,6 +205,29 @@ def test_issued_tensor_work_is_counted(rb, monkeypatch):
     assert issued["k_tc_gemm<sliced,pressure>"] > 0
 
 
+@pytest.mark.parametrize("s1", ["7", "8"])
+def test_pressure_linear_term_in_gemm_or_cuda_cores(rb, s1, monkeypatch):
+    """As(mu) u of the pressure right-hand side (Eq. sup-vvar): from the sliced pressure GEMM's
+    second K segment, theta^a digits against As digits (Q_a = 16 > 2 S1 with S1 = 7 slices), or
+    in double-float on the CUDA cores (S1 = 8: 16 <= 2 S1). Both recover the oracle's pressure
+    to rounding."""
+    monkeypatch.setenv("RB_SMALL", "0")
+    monkeypatch.setenv("RB_DIGITS_LINEAR", s1)
+    wl = synth.WORKLOADS["sweep_n50"]
+    n = 40
+    ops = synth.make_operators(wl, n_max=n, q_a=16)
+    q = synth.make_queries(wl, batch=300, n_max=n)
+    mu = np.concatenate([q.mu, synth.corner_queries(wl)])
+    o = oracle.Oracle.from_set(ops)
+    u_ref, p_ref, _ = o.solve(mu, threads=8)
+    with rb.Context(rb.RB_PREC_MIXED) as ctx:
+        ctx.load_set(ops)
+        u, p, info = ctx.rb_solve(mu)
+    assert np.all(info["status"] == 0)
+    assert rel(u, u_ref).max() <= TOL_MIXED
+    assert rel(p, p_ref).max() <= 1e-10
+
+
 def test_manufactured_mixed(rb):
     ops = synth.make_operators(synth.WORKLOADS["single_n20"])
     oracle.manufacture(ops, (10.0, 200.0))
