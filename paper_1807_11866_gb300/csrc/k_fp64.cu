@@ -19,38 +19,64 @@ namespace rb {
 // J^c[k][j] = sum_{q,l} xs[q*n + l] * D~_q[k][j][l] into J (ld = n), xs = theta^c_q u_l.
 // Streams D~ from L2/HBM: for fixed (q, l) the n x n block is read row by row, so
 // consecutive threads read consecutive j (coalesced); no reuse, FP64-ALU bound.
+// A thread takes P elements (base + i kThreads + tid), P a compile-time count matched to the
+// elements left: FP64 instructions occupy the pipe whether or not their predicate is on, so
+// a fixed unrolled count with a run-time guard would issue every slot (16 of them where a
+// single small query needs 2).
 constexpr int kP = 16;
-__device__ void contract_fp64(const DevOps &o, int n, const double *xs, double *J) {
+template <int P>
+__device__ __forceinline__ void contract_fp64_part(const DevOps &o, int n, const double *xs,
+                                                   double *J, int base) {
   const int tid = threadIdx.x;
   const int nn = n * n;
   const size_t nm = (size_t)o.n_max, nm2 = nm * nm;
-  for (int base = 0; base < nn; base += kThreads * kP) {
-    const int pcount = min(kP, (nn - base + kThreads - 1) / kThreads);
-    int off[kP];
-    double acc[kP];
+  int off[P];
+  double acc[P];
 #pragma unroll
-    for (int i = 0; i < kP; ++i) {
-      const int e = base + i * kThreads + tid;
-      const int k = e / n, j = e - (e / n) * n;
-      off[i] = (e < nn) ? (int)(k * nm + j) : 0;
-      acc[i] = 0.0;
-    }
-    for (int q = 0; q < o.q_c; ++q) {
-      const double *Dq = o.Dt + (size_t)q * nm * nm2;
-      const double *xq = xs + q * n;
+  for (int i = 0; i < P; ++i) {
+    const int e = base + i * kThreads + tid;
+    const int k = e / n, j = e - (e / n) * n;
+    off[i] = (e < nn) ? (int)(k * nm + j) : 0;
+    acc[i] = 0.0;
+  }
+  for (int q = 0; q < o.q_c; ++q) {
+    const double *Dq = o.Dt + (size_t)q * nm * nm2;
+    const double *xq = xs + q * n;
 #pragma unroll 8  // loads of 8 rows in flight: the stream is L2-latency bound at small n
-      for (int l = 0; l < n; ++l) {
-        const double x = xq[l];
-        const double *row = Dq + (size_t)l * nm2;
+    for (int l = 0; l < n; ++l) {
+      const double x = xq[l];
+      const double *row = Dq + (size_t)l * nm2;
 #pragma unroll
-        for (int i = 0; i < kP; ++i)
-          if (i < pcount) acc[i] = fma(x, __ldg(row + off[i]), acc[i]);
-      }
+      for (int i = 0; i < P; ++i) acc[i] = fma(x, __ldg(row + off[i]), acc[i]);
     }
+  }
 #pragma unroll
-    for (int i = 0; i < kP; ++i) {
-      const int e = base + i * kThreads + tid;
-      if (i < pcount && e < nn) J[e] = acc[i];
+  for (int i = 0; i < P; ++i) {
+    const int e = base + i * kThreads + tid;
+    if (e < nn) J[e] = acc[i];
+  }
+}
+
+__device__ void contract_fp64(const DevOps &o, int n, const double *xs, double *J) {
+  const int nn = n * n;
+  for (int base = 0; base < nn; base += kThreads * kP) {
+    switch (min(kP, (nn - base + kThreads - 1) / kThreads)) {  // uniform over the block
+      case 1: contract_fp64_part<1>(o, n, xs, J, base); break;
+      case 2: contract_fp64_part<2>(o, n, xs, J, base); break;
+      case 3: contract_fp64_part<3>(o, n, xs, J, base); break;
+      case 4: contract_fp64_part<4>(o, n, xs, J, base); break;
+      case 5: contract_fp64_part<5>(o, n, xs, J, base); break;
+      case 6: contract_fp64_part<6>(o, n, xs, J, base); break;
+      case 7: contract_fp64_part<7>(o, n, xs, J, base); break;
+      case 8: contract_fp64_part<8>(o, n, xs, J, base); break;
+      case 9: contract_fp64_part<9>(o, n, xs, J, base); break;
+      case 10: contract_fp64_part<10>(o, n, xs, J, base); break;
+      case 11: contract_fp64_part<11>(o, n, xs, J, base); break;
+      case 12: contract_fp64_part<12>(o, n, xs, J, base); break;
+      case 13: contract_fp64_part<13>(o, n, xs, J, base); break;
+      case 14: contract_fp64_part<14>(o, n, xs, J, base); break;
+      case 15: contract_fp64_part<15>(o, n, xs, J, base); break;
+      default: contract_fp64_part<16>(o, n, xs, J, base); break;
     }
   }
 }
