@@ -31,7 +31,8 @@
 // a chunk drains in a quarter of the MMA time it took to fill).
 // Persistent over output tiles, in groups of kGroupM row tiles (rows fastest inside a group).
 // The sliced epilogue reads u_b[j] straight from L2 at the end of a tile, so all shared memory
-// but the barriers goes to the TMA ring.
+// but the barriers goes to the TMA ring; the plain epilogue adds a small staging area for
+// coalesced stores where the ring leaves room.
 #include <cuda.h>
 
 #include <algorithm>
