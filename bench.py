@@ -544,7 +544,8 @@ def kernel_rooflines(prec, wl, q, info, kprof, steps, chord, issued=None):
         third for queries on chord steps) (tensor);
       sliced residual GEMM: 2 Q_c n^3 FLOP per FP64-accurate residual (from the third iteration
         on) (tensor);
-      sliced pressure GEMM: 2 Q_c n^2 m FLOP per query (tensor);
+      sliced pressure GEMM: 2 Q_c n^2 m FLOP per query (tensor; where the library folds
+        As(mu) u into it, large Q_a, its 2 Q_a n m FLOP are left out: a lower bound);
       elimination: 2 n^3 / 3 + 2 n^2 FLOP in FP32 per factorisation, 2 n^2 per chord solve (ALU);
       system assembly: 8 n^2 (A(mu)) + 4 n^2 (J^c, iterations with a new Jacobian after the
         first) bytes read and 4 n (n + 1) bytes written; a chord step reads A(mu) and writes the
